@@ -1,0 +1,189 @@
+/*
+ * bemgb.h -- C ABI of the GB300 differential-BEM library.
+ *
+ * Per-iteration hot path of the Levenberg-Marquardt fit of diffusion-curve
+ * handles to noisy Monte Carlo colour samples ("Monte Carlo Rendering to
+ * Diffusion Curves with Differential BEM"):
+ *   - evaluate the boundary-integral colour at every sample     (Sec. 3.1, Eq. (bie))
+ *   - its adjoint with respect to handle positions and jumps   (Sec. 3.2, Eq. (diffbie))
+ *   - the Gauss-Newton products J^T J, J^T r and the LM step   (Sec. 4.3, Eq. (optimstep))
+ * against the dense BEM matrix of the image boundary, factored once (Sec. 3.1.3).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a bem_status (0 = BEM_OK); nothing aborts.  On
+ *     failure bem_last_error() holds a one-line reason.
+ *   - Pointers marked "device" are CUDA device pointers on the context's
+ *     device; "host" pointers are ordinary host memory.  The caller owns
+ *     every buffer it passes; the context owns all of its internal device
+ *     buffers (panels, factors, Gram matrices, partial sums) and frees them
+ *     in bem_destroy().
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Work is enqueued on it in order; entry points that return
+ *     host-visible results (lm_step, bem_loss) synchronise that stream.
+ *   - Per-sample arrays (xy, target, rgb, resid) are row-major
+ *     [n][2] / [n][3] in the context's sample type: double for
+ *     BEM_FP64 contexts, float for BEM_MIXED contexts.
+ *   - Parameter vectors theta are double [n_theta], n_theta = 32 * n_curves,
+ *     laid out [curve][control handle 0..3][x, y, wd_r, wd_g, wd_b, wc_r, wc_g, wc_b].
+ *     wd is the colour jump (left side minus right side of the curve's
+ *     direction of travel) and wc the jump of the normal derivative
+ *     (Eq. (handleterm)).  A closed curve reuses control point 0 as its
+ *     last point; the last point's x, y are then not free (their gradient is 0).
+ *   - The image domain is the unit square; its boundary carries the zero
+ *     Neumann condition of Eq. (neumann).
+ */
+#ifndef BEMGB_H
+#define BEMGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BEM_OK = 0,
+    BEM_EINVAL = -1,      /* bad argument (size, pointer, option) */
+    BEM_ESTATE = -2,      /* call out of order, e.g. eval before factor */
+    BEM_ESINGULAR = -3,   /* boundary matrix factorisation failed */
+    BEM_ENOTSPD = -4,     /* LM matrix not positive definite at every trial lambda */
+    BEM_ECUDA = -5,       /* a CUDA runtime call failed (message in bem_last_error) */
+    BEM_ETIMEDOUT = -6,   /* a bounded device-side wait ran out */
+    BEM_ENOMEM = -7       /* device allocation failed */
+} bem_status;
+
+enum { BEM_FP64 = 0, BEM_MIXED = 1 };                         /* bem_opts.precision */
+enum { BEM_JTJ_FP64 = 0, BEM_JTJ_BF16 = 1, BEM_JTJ_3XTF32 = 2 }; /* bem_opts.jtj_mode */
+
+typedef struct {
+    int precision;        /* BEM_FP64: every step in double.  BEM_MIXED: float
+                             sample/panel arithmetic, double near field and
+                             refined double boundary solves */
+    double eps_d;         /* regularisation of the w_d (double-layer) handle
+                             term, Sec. 3.1.3 / 3.2.1; default 1e-2 */
+    double eps_c;         /* regularisation of the w_c (single-layer) term; default 1e-2 */
+    int segs_per_side;    /* boundary segments per side of the square, Sec. 3.1.3; default 256 */
+    double near_factor;   /* BEM_MIXED: pairs closer than near_factor panel
+                             lengths are evaluated in double; default 2; 0 = never */
+    int jtj_mode;         /* arithmetic of the J^T J contraction (BEM_JTJ_*) */
+    int reserved[8];
+} bem_opts;
+
+typedef struct {
+    double loss_before;   /* L(theta) = (1/2n) sum |u - min(t,1)|^2 at the current theta */
+    double loss_after;    /* L at the best trial theta' (same samples, Sec. 4.3) */
+    int accepted;         /* 1 if loss_after < loss_before (theta updated) */
+    int best_trial;       /* index into lambdas of the trial that was taken (or -1) */
+    double lambda_next;   /* damping proposal for the next step */
+    double grad_norm;     /* |g|_2 of the gradient at theta */
+} lm_result;
+
+typedef struct bem_ctx bem_ctx;
+
+/* Fill *opts with the defaults above.  Never fails for a non-NULL opts. */
+int bem_default_opts(bem_opts *opts);
+
+/* Create a context on CUDA device `device`.  *out receives the handle (NULL
+ * on failure).  opts may be NULL for the defaults.  Errors: BEM_EINVAL for
+ * bad options, BEM_ECUDA if the device cannot be used. */
+int bem_create(bem_ctx **out, const bem_opts *opts, int device);
+
+/* Release every device buffer of the context.  ctx may be NULL. */
+void bem_destroy(bem_ctx *ctx);
+
+/* Last error message of this context (or of the last failed bem_create if
+ * ctx is NULL); never NULL. */
+const char *bem_last_error(const bem_ctx *ctx);
+
+/* Describe the handle set (Sec. 4.1: handles with endpoints and constant
+ * jumps; here cubic Bezier curves cut into straight panels, Sec. 6).
+ *   n_curves >= 1; panels_per_curve[n_curves] >= 1 (host int32);
+ *   closed[n_curves] (host uint8, 1 = loop);
+ *   theta[32*n_curves] host double initial parameters;
+ *   mean_color[3] host double: the per-domain constant colour added to the
+ *   zero-mean BEM solution (Sec. 3.1.3, 4.3).
+ * Allocates the per-scene buffers.  May be called again to replace the scene. */
+int bem_setup(bem_ctx *ctx, int n_curves, const int32_t *panels_per_curve,
+              const uint8_t *closed, const double *theta, const double *mean_color);
+
+/* Assemble the Galerkin matrix of the image boundary (Eq. (bie_galerkin),
+ * 3-point Gauss outer rule, exact inner integral, zero coincident term) and
+ * factor it once in double (Sec. 3.1.3): LU with partial pivoting of the
+ * system bordered by the constant null vector, left null vector from the
+ * transposed solve, then the pseudo-inverse that discards the null space.
+ * Independent of theta (Sec. 3.1.3 last paragraph).  Synchronises `stream`.
+ * Errors: BEM_ESINGULAR if a pivot vanishes. */
+int bem_factor(bem_ctx *ctx, void *stream);
+
+/* Replace theta (double [n_theta]); `theta_is_device` selects a device or
+ * host pointer.  Stream-ordered. */
+int bem_set_params(bem_ctx *ctx, const double *theta, int theta_is_device, void *stream);
+
+/* Copy the current theta to host memory theta_out[n_theta] (synchronises). */
+int bem_get_params(bem_ctx *ctx, double *theta_out, void *stream);
+
+/* Set the per-domain mean colour (host double[3]). */
+int bem_set_mean_color(bem_ctx *ctx, const double *mean_color);
+
+/* Mean over n samples of min(target, 1) per channel (Sec. 4.3, last
+ * paragraph) into host double[3].  target: device [n][3] sample type. */
+int bem_sample_mean(bem_ctx *ctx, int64_t n, const void *target, double *mean_out, void *stream);
+
+/* Colours u(x) = mean + sum_j phi_j(x)/(2 pi) u_b,j + f(x; theta) at n
+ * interior sample points (Eq. (bie) with alpha = 1, Sec. 3.1.3 last
+ * paragraph; f from Eq. (handleterm) regularised as in Sec. 3.1.3).
+ *   xy: device [n][2], rgb_out: device [n][3] (sample type).  n >= 0. */
+int bem_eval(bem_ctx *ctx, int64_t n, const void *xy, void *rgb_out, void *stream);
+
+/* Loss (1/2n) sum |u - min(t,1)|^2 (Eq. (squaredl2loss) as a Monte Carlo
+ * mean with uniform density, clamp of Sec. 4.3) into host *loss_out; if
+ * resid_out is not NULL it receives r = u - min(t,1), device [n][3].
+ * Synchronises `stream`. */
+int bem_loss(bem_ctx *ctx, int64_t n, const void *xy, const void *target,
+             void *resid_out, double *loss_out, void *stream);
+
+/* Vector-Jacobian product grad_out = J^T resid = sum_s sum_c resid[s][c]
+ * du_c(x_s)/dtheta (no 1/n), computed in reverse mode through the handle
+ * term and the boundary solve (Sec. 3.2, Eq. (diffbie)); kernel values are
+ * recomputed, no n x P matrix is stored.
+ *   xy: device [n][2]; resid: device [n][3] (sample type);
+ *   grad_out: device double [n_theta]. */
+int bem_vjp(bem_ctx *ctx, int64_t n, const void *xy, const void *resid,
+            double *grad_out, void *stream);
+
+/* Gauss-Newton matrix H = (1/n) sum_s J_s^T J_s (Eq. (losshessian), uniform
+ * density, same samples as the gradient) into device double
+ * H_out[n_theta][n_theta] (row-major, full symmetric).  The boundary part
+ * of J uses the stacked right-hand sides of Sec. 3.2.3.  Arithmetic per
+ * bem_opts.jtj_mode.  H_out may be NULL to only refresh the context's copy. */
+int bem_jtj(bem_ctx *ctx, int64_t n, const void *xy, double *H_out, void *stream);
+
+/* One Levenberg-Marquardt iteration (Eq. (optimstep)) on the n samples:
+ * loss and gradient at theta, H (bem_jtj), then for each of the n_trials
+ * damping values lambdas[] (host double): solve
+ *   (H + lambda D) delta = -g,  D = diag(H) (floored at 1e-12 max),
+ * restricted to steps that keep the compatibility condition with endpoints
+ * fixed (Sec. 4.3), re-project w_c with the new lengths, and evaluate the
+ * loss on the same samples.  The trial with the lowest loss is taken if it
+ * lowers the loss (theta updated in the context).  lambda_next: lambda/3
+ * after an accepted single trial, 2 lambda after a rejected one; with
+ * several trials the accepted lambda / 3, or 10 max(lambdas) if none helps.
+ *   xy, target: device (sample type); out: host.  Synchronises `stream`.
+ * Errors: BEM_ENOTSPD if no trial matrix could be factored. */
+int lm_step(bem_ctx *ctx, int64_t n, const void *xy, const void *target,
+            int n_trials, const double *lambdas, lm_result *out, void *stream);
+
+/* Sizes of the current scene (host ints; any pointer may be NULL). */
+int bem_sizes(const bem_ctx *ctx, int *n_theta, int *n_panels, int *n_boundary);
+
+/* Copy the boundary solution u_b (double [n_boundary][3]) of the current
+ * theta to host memory (diagnostics and tests; synchronises). */
+int bem_boundary_values(bem_ctx *ctx, double *ub_out, void *stream);
+
+/* Number of this library's kernels launched by the context so far. */
+int64_t bem_launch_count(const bem_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEMGB_H */

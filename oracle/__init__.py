@@ -23,8 +23,11 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
+    import platform
     src = os.path.join(_HERE, "oracle.c")
-    if (not force and os.path.exists(_SO)
+    stamp = os.path.join(_BUILD, "machine.txt")
+    same_machine = os.path.exists(stamp) and open(stamp).read() == platform.machine()
+    if (not force and same_machine and os.path.exists(_SO)
             and os.path.getmtime(_SO) >= os.path.getmtime(src)):
         return _SO
     os.makedirs(_BUILD, exist_ok=True)
@@ -33,6 +36,8 @@ def build(force: bool = False) -> str:
            "-shared", src, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
+    with open(stamp, "w") as f:
+        f.write(platform.machine())
     return _SO
 
 

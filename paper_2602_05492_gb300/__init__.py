@@ -1,0 +1,251 @@
+"""GB300 differential-BEM hot path: thin Python binding of libbemgb.
+
+Every computation runs in the CUDA library behind the C ABI declared in
+include/bemgb.h; this module only marshals arguments (torch tensors'
+device pointers, the current CUDA stream, host numpy arrays).  There is no
+CPU fallback: importing the binding without the built library raises.
+
+The raw entry points are exposed under their C names (bem_create, bem_setup,
+bem_factor, bem_eval, bem_loss, bem_vjp, bem_jtj, lm_step, ...); `BEM` wraps
+one context for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbemgb.so")
+
+BEM_OK, BEM_EINVAL, BEM_ESTATE, BEM_ESINGULAR, BEM_ENOTSPD, BEM_ECUDA, BEM_ETIMEDOUT, BEM_ENOMEM = \
+    0, -1, -2, -3, -4, -5, -6, -7
+BEM_FP64, BEM_MIXED = 0, 1
+BEM_JTJ_FP64, BEM_JTJ_BF16, BEM_JTJ_3XTF32 = 0, 1, 2
+
+_STATUS = {0: "BEM_OK", -1: "BEM_EINVAL", -2: "BEM_ESTATE", -3: "BEM_ESINGULAR",
+           -4: "BEM_ENOTSPD", -5: "BEM_ECUDA", -6: "BEM_ETIMEDOUT", -7: "BEM_ENOMEM"}
+
+
+class bem_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("eps_d", ctypes.c_double),
+                ("eps_c", ctypes.c_double), ("segs_per_side", ctypes.c_int),
+                ("near_factor", ctypes.c_double), ("jtj_mode", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class lm_result(ctypes.Structure):
+    _fields_ = [("loss_before", ctypes.c_double), ("loss_after", ctypes.c_double),
+                ("accepted", ctypes.c_int), ("best_trial", ctypes.c_int),
+                ("lambda_next", ctypes.c_double), ("grad_norm", ctypes.c_double)]
+
+
+class BemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            "libbemgb.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+            f"(expected at {LIB_PATH})")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, ci, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "bem_default_opts": (ci, [ctypes.POINTER(bem_opts)]),
+        "bem_create": (ci, [ctypes.POINTER(vp), ctypes.POINTER(bem_opts), ci]),
+        "bem_destroy": (None, [vp]),
+        "bem_last_error": (ctypes.c_char_p, [vp]),
+        "bem_setup": (ci, [vp, ci, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint8),
+                           dp, dp]),
+        "bem_factor": (ci, [vp, vp]),
+        "bem_set_params": (ci, [vp, vp, ci, vp]),
+        "bem_get_params": (ci, [vp, dp, vp]),
+        "bem_set_mean_color": (ci, [vp, dp]),
+        "bem_sample_mean": (ci, [vp, i64, vp, dp, vp]),
+        "bem_eval": (ci, [vp, i64, vp, vp, vp]),
+        "bem_loss": (ci, [vp, i64, vp, vp, vp, dp, vp]),
+        "bem_vjp": (ci, [vp, i64, vp, vp, vp, vp]),
+        "bem_jtj": (ci, [vp, i64, vp, vp, vp]),
+        "lm_step": (ci, [vp, i64, vp, vp, ci, dp, ctypes.POINTER(lm_result), vp]),
+        "bem_sizes": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]),
+        "bem_boundary_values": (ci, [vp, dp, vp]),
+        "bem_launch_count": (i64, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+_lib = _load()
+EXPORTED = [
+    "bem_default_opts", "bem_create", "bem_destroy", "bem_last_error", "bem_setup", "bem_factor",
+    "bem_set_params", "bem_get_params", "bem_set_mean_color", "bem_sample_mean", "bem_eval",
+    "bem_loss", "bem_vjp", "bem_jtj", "lm_step", "bem_sizes", "bem_boundary_values",
+    "bem_launch_count",
+]
+globals().update({name: getattr(_lib, name) for name in EXPORTED})
+
+
+def lib():
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class BEM:
+    """One library context (scene + factored boundary) on one CUDA device."""
+
+    def __init__(self, precision=BEM_FP64, eps_d=1e-2, eps_c=1e-2, segs_per_side=256,
+                 near_factor=2.0, jtj_mode=None, device=0):
+        o = bem_opts()
+        _lib.bem_default_opts(ctypes.byref(o))
+        o.precision = precision
+        o.eps_d, o.eps_c = eps_d, eps_c
+        o.segs_per_side = segs_per_side
+        o.near_factor = near_factor
+        o.jtj_mode = (BEM_JTJ_FP64 if precision == BEM_FP64 else BEM_JTJ_BF16) \
+            if jtj_mode is None else jtj_mode
+        self.opts = o
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = _lib.bem_create(ctypes.byref(h), ctypes.byref(o), device)
+        if rc:
+            raise BemError(rc, _lib.bem_last_error(None).decode())
+        self.h = h
+        self.n_theta = 0
+        self.Nb = 4 * segs_per_side
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.opts.precision == BEM_FP64 else torch.float32
+
+    def _check(self, rc):
+        if rc:
+            raise BemError(rc, _lib.bem_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.bem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- setup --------------------------------------------------------------
+    def setup(self, n_curves, panels_per_curve, closed, theta, mean_color):
+        K = np.ascontiguousarray(panels_per_curve, np.int32)
+        cl = np.ascontiguousarray(closed, np.uint8)
+        th = np.ascontiguousarray(theta, np.float64)
+        m = np.ascontiguousarray(mean_color, np.float64)
+        self._check(_lib.bem_setup(self.h, int(n_curves),
+                                   K.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   cl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                   _dp(th), _dp(m)))
+        self.n_theta = 32 * int(n_curves)
+
+    def factor(self, stream=None):
+        self._check(_lib.bem_factor(self.h, _stream(stream)))
+
+    def set_params(self, theta, stream=None):
+        import torch
+        if isinstance(theta, torch.Tensor):
+            assert theta.dtype == torch.float64 and theta.is_cuda and theta.is_contiguous()
+            self._check(_lib.bem_set_params(self.h, _ptr(theta), 1, _stream(stream)))
+        else:
+            th = np.ascontiguousarray(theta, np.float64)
+            self._check(_lib.bem_set_params(self.h, th.ctypes.data_as(ctypes.c_void_p), 0,
+                                            _stream(stream)))
+
+    def get_params(self, stream=None) -> np.ndarray:
+        out = np.empty(self.n_theta)
+        self._check(_lib.bem_get_params(self.h, _dp(out), _stream(stream)))
+        return out
+
+    def set_mean_color(self, mean):
+        m = np.ascontiguousarray(mean, np.float64)
+        self._check(_lib.bem_set_mean_color(self.h, _dp(m)))
+
+    # ---- hot path -------------------------------------------------------------
+    def _samples(self, *ts):
+        for t in ts:
+            assert t.is_cuda and t.dtype == self.dtype and t.is_contiguous(), \
+                f"expected contiguous CUDA {self.dtype}, got {t.dtype} {t.device}"
+
+    def sample_mean(self, target, stream=None) -> np.ndarray:
+        self._samples(target)
+        out = np.empty(3)
+        self._check(_lib.bem_sample_mean(self.h, target.shape[0], _ptr(target), _dp(out),
+                                         _stream(stream)))
+        return out
+
+    def eval(self, xy, out=None, stream=None):
+        import torch
+        self._samples(xy)
+        if out is None:
+            out = torch.empty((xy.shape[0], 3), dtype=self.dtype, device=xy.device)
+        self._check(_lib.bem_eval(self.h, xy.shape[0], _ptr(xy), _ptr(out), _stream(stream)))
+        return out
+
+    def loss(self, xy, target, resid=None, stream=None) -> float:
+        self._samples(xy, target)
+        v = ctypes.c_double()
+        self._check(_lib.bem_loss(self.h, xy.shape[0], _ptr(xy), _ptr(target),
+                                  _ptr(resid) if resid is not None else None,
+                                  ctypes.byref(v), _stream(stream)))
+        return v.value
+
+    def vjp(self, xy, resid, grad=None, stream=None):
+        import torch
+        self._samples(xy, resid)
+        if grad is None:
+            grad = torch.empty(self.n_theta, dtype=torch.float64, device=xy.device)
+        self._check(_lib.bem_vjp(self.h, xy.shape[0], _ptr(xy), _ptr(resid), _ptr(grad),
+                                 _stream(stream)))
+        return grad
+
+    def jtj(self, xy, H=None, stream=None):
+        import torch
+        self._samples(xy)
+        if H is None:
+            H = torch.empty((self.n_theta, self.n_theta), dtype=torch.float64, device=xy.device)
+        self._check(_lib.bem_jtj(self.h, xy.shape[0], _ptr(xy), _ptr(H), _stream(stream)))
+        return H
+
+    def lm_step(self, xy, target, lambdas, stream=None) -> dict:
+        self._samples(xy, target)
+        lam = np.ascontiguousarray(np.atleast_1d(lambdas), np.float64)
+        r = lm_result()
+        self._check(_lib.lm_step(self.h, xy.shape[0], _ptr(xy), _ptr(target), len(lam), _dp(lam),
+                                 ctypes.byref(r), _stream(stream)))
+        return dict(loss_before=r.loss_before, loss_after=r.loss_after, accepted=bool(r.accepted),
+                    best_trial=r.best_trial, lambda_next=r.lambda_next, grad_norm=r.grad_norm)
+
+    def boundary_values(self, stream=None) -> np.ndarray:
+        out = np.empty((self.Nb, 3))
+        self._check(_lib.bem_boundary_values(self.h, _dp(out), _stream(stream)))
+        return out
+
+    def launch_count(self) -> int:
+        return int(_lib.bem_launch_count(self.h))

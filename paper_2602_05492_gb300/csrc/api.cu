@@ -1,0 +1,430 @@
+// C ABI of libbemgb: context lifecycle and the hot-path entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ctx.h"
+
+namespace bem {
+
+static std::string g_create_err = "no error";
+
+int fail(bem_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+int cuda_check(bem_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return BEM_OK;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  return fail(c, e == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA, buf);
+}
+
+int grow(bem_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes <= b.cap) return BEM_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return cuda_check(c, e, "device allocation");
+  }
+  b.cap = want;
+  return BEM_OK;
+}
+
+template <typename T>
+static int alloc(bem_ctx* c, T*& p, size_t count) {
+  if (p) cudaFree(p);
+  p = nullptr;
+  if (count == 0) count = 1;
+  return cuda_check(c, cudaMalloc((void**)&p, sizeof(T) * count), "device allocation");
+}
+
+static void free_buf(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+static int set_device(bem_ctx* c) { return cuda_check(c, cudaSetDevice(c->device), "cudaSetDevice"); }
+
+// panels, compatibility weights and boundary solution of the current theta
+static int refresh(bem_ctx* c, const double* theta) {
+  int rc;
+  if ((rc = geom_panelize(c, theta))) return rc;
+  if ((rc = field_rhs(c))) return rc;
+  return field_solve(c);
+}
+
+static int need_ready(bem_ctx* c) {
+  if (!c->have_scene) return fail(c, BEM_ESTATE, "bem_setup has not been called");
+  if (!c->bd.factored) return fail(c, BEM_ESTATE, "bem_factor has not been called");
+  return BEM_OK;
+}
+
+// out = a + b
+__global__ void k_axpy(const double* __restrict__ a, const double* __restrict__ b, int n,
+                       double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] + b[i];
+}
+
+// v *= s; *norm2 = |v|^2 after scaling (one block)
+__global__ void k_scale_norm(double* __restrict__ v, int n, double s, double* __restrict__ norm2) {
+  __shared__ double red[32];
+  double acc = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double x = v[i] * s;
+    v[i] = x;
+    acc += x * x;
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    *norm2 = t;
+  }
+}
+
+}  // namespace bem
+
+using namespace bem;
+
+extern "C" {
+
+int bem_default_opts(bem_opts* o) {
+  if (!o) return BEM_EINVAL;
+  memset(o, 0, sizeof(*o));
+  o->precision = BEM_FP64;
+  o->eps_d = 1e-2;
+  o->eps_c = 1e-2;
+  o->segs_per_side = 256;
+  o->near_factor = 2.0;
+  o->jtj_mode = BEM_JTJ_FP64;
+  return BEM_OK;
+}
+
+int bem_create(bem_ctx** out, const bem_opts* opts, int device) {
+  if (!out) return fail(nullptr, BEM_EINVAL, "out is NULL");
+  *out = nullptr;
+  bem_opts o;
+  if (opts) o = *opts;
+  else bem_default_opts(&o);
+  if (o.precision != BEM_FP64 && o.precision != BEM_MIXED)
+    return fail(nullptr, BEM_EINVAL, "precision must be BEM_FP64 or BEM_MIXED");
+  if (!(o.eps_d > 0) || !(o.eps_c > 0) || !std::isfinite(o.eps_d) || !std::isfinite(o.eps_c))
+    return fail(nullptr, BEM_EINVAL, "eps_d and eps_c must be positive");
+  if (o.segs_per_side < 1 || o.segs_per_side > 4096)
+    return fail(nullptr, BEM_EINVAL, "segs_per_side must be in [1, 4096]");
+  if (!(o.near_factor >= 0)) return fail(nullptr, BEM_EINVAL, "near_factor must be >= 0");
+  if (o.jtj_mode < BEM_JTJ_FP64 || o.jtj_mode > BEM_JTJ_3XTF32)
+    return fail(nullptr, BEM_EINVAL, "unknown jtj_mode");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fail(nullptr, BEM_ECUDA, "no such CUDA device");
+  bem_ctx* c = new (std::nothrow) bem_ctx();
+  if (!c) return fail(nullptr, BEM_ENOMEM, "host allocation");
+  c->device = device;
+  c->opts = o;
+  int rc;
+  if ((rc = set_device(c))) { g_create_err = c->err; delete c; return rc; }
+  c->bd.M = o.segs_per_side;
+  c->bd.Nb = 4 * o.segs_per_side;
+  int Nb = c->bd.Nb;
+  if ((rc = alloc(c, c->bd.d_vert, 2 * (size_t)(Nb + 1))) || (rc = alloc(c, c->bd.d_vert32, 2 * (size_t)(Nb + 1))) ||
+      (rc = alloc(c, c->bd.d_gp, 6 * (size_t)Nb)) || (rc = alloc(c, c->bd.d_gp32, 6 * (size_t)Nb)) ||
+      (rc = alloc(c, c->bd.d_A, (size_t)Nb * Nb)) || (rc = alloc(c, c->bd.d_W, (size_t)Nb * Nb)) ||
+      (rc = alloc(c, c->bd.d_WT, (size_t)Nb * Nb)) || (rc = alloc(c, c->bd.d_W32, (size_t)Nb * Nb)) ||
+      (rc = alloc(c, c->bd.d_WT32, (size_t)Nb * Nb)) || (rc = alloc(c, c->d_ub, 3 * (size_t)Nb)) ||
+      (rc = alloc(c, c->d_fb, 3 * (size_t)Nb)) || (rc = alloc(c, c->d_q, 3 * (size_t)Nb)) ||
+      (rc = alloc(c, c->d_lb, 3 * (size_t)Nb)) || (rc = alloc(c, c->d_scal, 64)) ||
+      (rc = alloc(c, c->d_status, 4))) {
+    g_create_err = c->err;
+    bem_destroy(c);
+    return rc;
+  }
+  if ((rc = geom_boundary_tables(c))) { g_create_err = c->err; bem_destroy(c); return rc; }
+  *out = c;
+  return BEM_OK;
+}
+
+void bem_destroy(bem_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  void* ptrs[] = {c->bd.d_vert, c->bd.d_vert32, c->bd.d_gp, c->bd.d_gp32, c->bd.d_A, c->bd.d_W,
+                  c->bd.d_WT, c->bd.d_W32, c->bd.d_WT32, c->d_ub, c->d_fb, c->d_q, c->d_lb,
+                  c->d_scal, c->d_status, c->d_theta, c->d_trial, c->d_delta, c->d_pan64,
+                  c->d_pan32, c->d_compat, c->sc.d_pcurve, c->sc.d_pk, c->sc.d_off, c->sc.d_K,
+                  c->sc.d_closed};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  DevBuf* bufs[] = {&c->part, &c->part2, &c->loss, &c->gpart, &c->jrow, &c->phi, &c->Hc, &c->Mc,
+                    &c->Dfc, &c->Fg, &c->lmK, &c->lmL, &c->lmLt, &c->lmW, &c->H, &c->g};
+  for (DevBuf* b : bufs) free_buf(*b);
+  delete c;
+}
+
+const char* bem_last_error(const bem_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+int bem_setup(bem_ctx* c, int n_curves, const int32_t* ppc, const uint8_t* closed,
+              const double* theta, const double* mean_color) {
+  if (!c) return BEM_EINVAL;
+  if (n_curves < 1 || !ppc || !closed || !theta || !mean_color)
+    return fail(c, BEM_EINVAL, "bem_setup: n_curves >= 1 and non-NULL arrays required");
+  int rc;
+  if ((rc = set_device(c))) return rc;
+  Scene& s = c->sc;
+  s.C = n_curves;
+  s.K.assign(ppc, ppc + n_curves);
+  s.closed.assign(closed, closed + n_curves);
+  s.off.assign(n_curves + 1, 0);
+  for (int i = 0; i < n_curves; ++i) {
+    if (s.K[i] < 1 || s.K[i] > (1 << 20)) return fail(c, BEM_EINVAL, "panels_per_curve out of range");
+    s.off[i + 1] = s.off[i] + s.K[i];
+  }
+  for (int i = 0; i < 32 * n_curves; ++i)
+    if (!std::isfinite(theta[i])) return fail(c, BEM_EINVAL, "theta has a non-finite entry");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(mean_color[k])) return fail(c, BEM_EINVAL, "mean colour not finite");
+  s.P = s.off[n_curves];
+  s.nth = 32 * n_curves;
+  s.nc = 16 * n_curves;
+  std::vector<int> pc(s.P), pk(s.P);
+  for (int i = 0; i < n_curves; ++i)
+    for (int k = 0; k < s.K[i]; ++k) { pc[s.off[i] + k] = i; pk[s.off[i] + k] = k; }
+  if ((rc = alloc(c, s.d_pcurve, s.P)) || (rc = alloc(c, s.d_pk, s.P)) ||
+      (rc = alloc(c, s.d_off, n_curves + 1)) || (rc = alloc(c, s.d_K, n_curves)) ||
+      (rc = alloc(c, s.d_closed, n_curves)) || (rc = alloc(c, c->d_theta, s.nth)) ||
+      (rc = alloc(c, c->d_trial, s.nth)) || (rc = alloc(c, c->d_delta, s.nth)) ||
+      (rc = alloc(c, c->d_pan64, s.P)) || (rc = alloc(c, c->d_pan32, s.P)) ||
+      (rc = alloc(c, c->d_compat, 4 * (size_t)n_curves)))
+    return rc;
+  if ((rc = cuda_check(c, cudaMemcpy(s.d_pcurve, pc.data(), 4 * s.P, cudaMemcpyHostToDevice), "copy")) ||
+      (rc = cuda_check(c, cudaMemcpy(s.d_pk, pk.data(), 4 * s.P, cudaMemcpyHostToDevice), "copy")) ||
+      (rc = cuda_check(c, cudaMemcpy(s.d_off, s.off.data(), 4 * (n_curves + 1), cudaMemcpyHostToDevice), "copy")) ||
+      (rc = cuda_check(c, cudaMemcpy(s.d_K, s.K.data(), 4 * n_curves, cudaMemcpyHostToDevice), "copy")) ||
+      (rc = cuda_check(c, cudaMemcpy(s.d_closed, s.closed.data(), n_curves, cudaMemcpyHostToDevice), "copy")) ||
+      (rc = cuda_check(c, cudaMemcpy(c->d_theta, theta, 8 * s.nth, cudaMemcpyHostToDevice), "copy")))
+    return rc;
+  memcpy(c->mean, mean_color, sizeof(c->mean));
+  c->have_scene = true;
+  return BEM_OK;
+}
+
+int bem_factor(bem_ctx* c, void* stream) {
+  if (!c) return BEM_EINVAL;
+  int rc;
+  if ((rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  c->bd.factored = false;
+  if ((rc = geom_assemble(c))) return rc;
+  if ((rc = la_pinv(c))) return rc;
+  c->bd.factored = true;
+  return BEM_OK;
+}
+
+int bem_set_params(bem_ctx* c, const double* theta, int on_dev, void* stream) {
+  if (!c || !theta) return c ? fail(c, BEM_EINVAL, "theta is NULL") : BEM_EINVAL;
+  if (!c->have_scene) return fail(c, BEM_ESTATE, "bem_setup has not been called");
+  int rc;
+  if ((rc = set_device(c))) return rc;
+  return cuda_check(c, cudaMemcpyAsync(c->d_theta, theta, 8 * (size_t)c->sc.nth,
+                                       on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                       (cudaStream_t)stream),
+                    "set params");
+}
+
+int bem_get_params(bem_ctx* c, double* out, void* stream) {
+  if (!c || !out) return c ? fail(c, BEM_EINVAL, "out is NULL") : BEM_EINVAL;
+  if (!c->have_scene) return fail(c, BEM_ESTATE, "bem_setup has not been called");
+  int rc;
+  if ((rc = set_device(c))) return rc;
+  if ((rc = cuda_check(c, cudaMemcpyAsync(out, c->d_theta, 8 * (size_t)c->sc.nth,
+                                          cudaMemcpyDeviceToHost, (cudaStream_t)stream), "get params")))
+    return rc;
+  return cuda_check(c, cudaStreamSynchronize((cudaStream_t)stream), "sync");
+}
+
+int bem_set_mean_color(bem_ctx* c, const double* m) {
+  if (!c || !m) return c ? fail(c, BEM_EINVAL, "mean is NULL") : BEM_EINVAL;
+  memcpy(c->mean, m, sizeof(c->mean));
+  return BEM_OK;
+}
+
+int bem_sample_mean(bem_ctx* c, int64_t n, const void* target, double* mean_out, void* stream) {
+  if (!c || !mean_out || n < 0 || (n > 0 && !target)) return c ? fail(c, BEM_EINVAL, "bad arguments") : BEM_EINVAL;
+  int rc;
+  if ((rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  return field_sample_mean(c, n, target, mean_out);
+}
+
+int bem_eval(bem_ctx* c, int64_t n, const void* xy, void* rgb, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (n < 0 || (n > 0 && (!xy || !rgb))) return fail(c, BEM_EINVAL, "bem_eval: bad arguments");
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  if ((rc = refresh(c, c->d_theta))) return rc;
+  return field_eval(c, n, xy, rgb, nullptr, nullptr, false);
+}
+
+int bem_loss(bem_ctx* c, int64_t n, const void* xy, const void* target, void* resid, double* loss,
+             void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (n < 0 || !loss || (n > 0 && (!xy || !target))) return fail(c, BEM_EINVAL, "bem_loss: bad arguments");
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  if ((rc = refresh(c, c->d_theta))) return rc;
+  if ((rc = field_eval(c, n, xy, nullptr, target, resid, true))) return rc;
+  double s = 0;
+  if ((rc = cuda_check(c, cudaMemcpyAsync(&s, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
+    return rc;
+  if ((rc = cuda_check(c, cudaStreamSynchronize(S(c)), "sync"))) return rc;
+  *loss = n > 0 ? 0.5 * s / double(n) : 0.0;
+  return BEM_OK;
+}
+
+int bem_vjp(bem_ctx* c, int64_t n, const void* xy, const void* resid, double* grad, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (n < 0 || !grad || (n > 0 && (!xy || !resid))) return fail(c, BEM_EINVAL, "bem_vjp: bad arguments");
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  if ((rc = geom_panelize(c, c->d_theta))) return rc;
+  return adj_vjp(c, n, xy, resid, grad);
+}
+
+int bem_jtj(bem_ctx* c, int64_t n, const void* xy, double* H, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (n < 0 || (n > 0 && !xy)) return fail(c, BEM_EINVAL, "bem_jtj: bad arguments");
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  size_t nn = sizeof(double) * (size_t)c->sc.nth * c->sc.nth;
+  if ((rc = grow(c, c->H, nn))) return rc;
+  if ((rc = geom_panelize(c, c->d_theta))) return rc;
+  if ((rc = jtj_build(c, n, xy, (double*)c->H.p))) return rc;
+  if (H)
+    return cuda_check(c, cudaMemcpyAsync(H, c->H.p, nn, cudaMemcpyDeviceToDevice, S(c)), "copy H");
+  return BEM_OK;
+}
+
+int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_trials,
+            const double* lambdas, lm_result* out, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (n <= 0 || !xy || !target || n_trials < 1 || n_trials > 64 || !lambdas || !out)
+    return fail(c, BEM_EINVAL, "lm_step: bad arguments");
+  for (int t = 0; t < n_trials; ++t)
+    if (!(lambdas[t] >= 0) || !std::isfinite(lambdas[t]))
+      return fail(c, BEM_EINVAL, "lambda must be finite and >= 0");
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  const int nth = c->sc.nth;
+  const size_t es = c->opts.precision == BEM_FP64 ? 8 : 4;
+  const size_t nn = sizeof(double) * (size_t)nth * nth;
+  if ((rc = grow(c, c->H, nn))) return rc;
+  // residual (sample type), gradient, best trial theta
+  const size_t roff = ((es * 3 * (size_t)n + 255) / 256) * 256;
+  if ((rc = grow(c, c->phi, roff + 8 * (size_t)nth * 2 + 64))) return rc;
+  void* resid = c->phi.p;
+  double* g = (double*)((char*)c->phi.p + roff);
+  double* best_theta = g + nth;
+  // loss, residual and gradient at theta; compatibility weights with the
+  // current lengths (the fixed-endpoint constraint of the step)
+  if ((rc = refresh(c, c->d_theta))) return rc;
+  if ((rc = geom_compat(c, c->d_theta, false))) return rc;
+  if ((rc = field_eval(c, n, xy, nullptr, target, resid, true))) return rc;
+  double s0 = 0;
+  if ((rc = cuda_check(c, cudaMemcpyAsync(&s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
+    return rc;
+  if ((rc = adj_vjp(c, n, xy, resid, g))) return rc;
+  k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0 / double(n), c->d_scal + 1);
+  BEM_LAUNCHED(c);
+  if ((rc = jtj_build(c, n, xy, (double*)c->H.p))) return rc;
+  double gn2 = 0;
+  if ((rc = cuda_check(c, cudaMemcpyAsync(&gn2, c->d_scal + 1, 8, cudaMemcpyDeviceToHost, S(c)), "norm")) ||
+      (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "sync")))
+    return rc;
+  const double L0 = 0.5 * s0 / double(n);
+  out->grad_norm = std::sqrt(gn2);
+  double best = INFINITY;
+  int best_t = -1;
+  bool any_spd = false;
+  for (int t = 0; t < n_trials; ++t) {
+    rc = la_lm_solve(c, (const double*)c->H.p, g, lambdas[t], c->d_delta);
+    if (rc == BEM_ENOTSPD) continue;
+    if (rc) return rc;
+    any_spd = true;
+    // trial theta = theta + delta, then w_c re-projected with the new lengths (Sec. 4.3)
+    k_axpy<<<(nth + 255) / 256, 256, 0, S(c)>>>(c->d_theta, c->d_delta, nth, c->d_trial);
+    BEM_LAUNCHED(c);
+    if ((rc = geom_panelize(c, c->d_trial))) return rc;
+    if ((rc = geom_compat(c, c->d_trial, true))) return rc;
+    if ((rc = refresh(c, c->d_trial))) return rc;
+    if ((rc = field_eval(c, n, xy, nullptr, target, nullptr, true))) return rc;
+    double s1 = 0;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(&s1, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")) ||
+        (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "sync")))
+      return rc;
+    const double L1 = 0.5 * s1 / double(n);
+    if (L1 < best) {
+      best = L1;
+      best_t = t;
+      if ((rc = cuda_check(c, cudaMemcpyAsync(best_theta, c->d_trial, 8 * (size_t)nth,
+                                              cudaMemcpyDeviceToDevice, S(c)), "keep")))
+        return rc;
+    }
+  }
+  if (!any_spd) return fail(c, BEM_ENOTSPD, "LM matrix not positive definite for any trial lambda");
+  out->loss_before = L0;
+  out->loss_after = best;
+  out->accepted = best < L0 ? 1 : 0;
+  out->best_trial = out->accepted ? best_t : -1;
+  if (out->accepted) {
+    if ((rc = cuda_check(c, cudaMemcpyAsync(c->d_theta, best_theta, 8 * (size_t)nth,
+                                            cudaMemcpyDeviceToDevice, S(c)), "theta")))
+      return rc;
+    out->lambda_next = lambdas[best_t] / 3.0;
+  } else {
+    double mx = 0;
+    for (int t = 0; t < n_trials; ++t) mx = std::fmax(mx, lambdas[t]);
+    out->lambda_next = n_trials == 1 ? 2.0 * lambdas[0] : 10.0 * mx;
+  }
+  // leave panels and boundary solution consistent with the kept theta
+  if ((rc = refresh(c, c->d_theta))) return rc;
+  return cuda_check(c, cudaStreamSynchronize(S(c)), "sync");
+}
+
+int bem_sizes(const bem_ctx* c, int* n_theta, int* n_panels, int* n_boundary) {
+  if (!c) return BEM_EINVAL;
+  if (n_theta) *n_theta = c->sc.nth;
+  if (n_panels) *n_panels = c->sc.P;
+  if (n_boundary) *n_boundary = c->bd.Nb;
+  return BEM_OK;
+}
+
+int bem_boundary_values(bem_ctx* c, double* ub, void* stream) {
+  if (!c || !ub) return c ? fail(c, BEM_EINVAL, "ub is NULL") : BEM_EINVAL;
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  if ((rc = refresh(c, c->d_theta))) return rc;
+  if ((rc = cuda_check(c, cudaMemcpyAsync(ub, c->d_ub, 24 * (size_t)c->bd.Nb, cudaMemcpyDeviceToHost, S(c)), "ub")))
+    return rc;
+  return cuda_check(c, cudaStreamSynchronize(S(c)), "sync");
+}
+
+int64_t bem_launch_count(const bem_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// Internal state of a bem_ctx and the host-side launchers of every kernel.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bemgb.h"
+#include "common.cuh"
+
+namespace bem {
+
+// Device buffer that grows on demand (never shrinks until the context dies).
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct Scene {
+  int C = 0;          // curves
+  int P = 0;          // panels
+  int nth = 0;        // parameters, 32 C
+  int nc = 0;         // active parameters per colour channel, 16 C
+  std::vector<int> K, off;        // panels per curve, panel offset of each curve
+  std::vector<uint8_t> closed;
+  // device metadata
+  int* d_pcurve = nullptr;   // [P] curve of each panel
+  int* d_pk = nullptr;       // [P] index within its curve
+  int* d_off = nullptr;      // [C+1] panel offsets
+  int* d_K = nullptr;        // [C]
+  uint8_t* d_closed = nullptr;  // [C]
+};
+
+struct Boundary {
+  int M = 0;      // segments per side
+  int Nb = 0;     // 4 M
+  double* d_vert = nullptr;    // [(Nb+1)][2] CCW vertices, vert[Nb] = vert[0]
+  float* d_vert32 = nullptr;
+  double* d_gp = nullptr;      // [3 Nb][2] Gauss points
+  float* d_gp32 = nullptr;
+  double* d_A = nullptr;       // [Nb][Nb] Galerkin matrix
+  double* d_W = nullptr;       // [Nb][Nb] pseudo-inverse A^+
+  double* d_WT = nullptr;      // [Nb][Nb] (A^+)^T
+  float* d_W32 = nullptr;      // float copy of A^+ (mixed solves)
+  float* d_WT32 = nullptr;
+  bool factored = false;
+};
+
+}  // namespace bem
+
+struct bem_ctx {
+  int device = 0;
+  bem_opts opts{};
+  std::string err;
+  cudaStream_t cur = nullptr;
+  int64_t launches = 0;
+
+  bem::Scene sc;
+  bem::Boundary bd;
+  double mean[3] = {0, 0, 0};
+  bool have_scene = false;
+
+  // parameters and panels
+  double* d_theta = nullptr;       // [nth]
+  double* d_trial = nullptr;       // [nth] trial parameters of the LM step
+  double* d_delta = nullptr;       // [nth]
+  bem::Panel<double>* d_pan64 = nullptr;   // [P]
+  bem::Panel<float>* d_pan32 = nullptr;    // [P]
+  double* d_compat = nullptr;      // [4C] compatibility weights a_h
+  double* d_ub = nullptr;          // [Nb][3] boundary solution of the current panels
+  double* d_fb = nullptr;          // [Nb][3] right-hand side
+  double* d_q = nullptr;           // [Nb][3] adjoint boundary source
+  double* d_lb = nullptr;          // [Nb][3] adjoint boundary solution
+  double* d_scal = nullptr;        // small device scalars (loss, sums)
+  int* d_status = nullptr;         // device error word (0 = fine)
+
+  // growable scratch
+  bem::DevBuf part, part2, loss, gpart, jrow, phi, Hc, Mc, Dfc, Fg, lmK, lmL, lmLt, lmW, H, g;
+};
+
+namespace bem {
+
+// ---- error plumbing (api.cu) ------------------------------------------------
+int fail(bem_ctx* c, int code, const std::string& msg);
+int cuda_check(bem_ctx* c, cudaError_t e, const char* what);
+int grow(bem_ctx* c, DevBuf& b, size_t bytes);
+inline cudaStream_t S(bem_ctx* c) { return c->cur; }
+
+// ---- geometry (k_geom.cu) -----------------------------------------------------
+int geom_panelize(bem_ctx* c, const double* d_theta);
+// compatibility weights a_h of the current panels; with project, w_c of
+// theta is projected onto the compatibility hyperplane in place
+int geom_compat(bem_ctx* c, double* d_theta, bool project);
+int geom_boundary_tables(bem_ctx* c);                  // vertices, Gauss points
+int geom_assemble(bem_ctx* c);                         // d_A
+
+// ---- linear algebra (k_linalg.cu) -------------------------------------------
+int la_pinv(bem_ctx* c);   // factor bordered system, W = A^+ (double, float copies)
+// y[Nb][3] = W x[Nb][3] (transpose: W^T)
+int la_apply3(bem_ctx* c, const double* W, const double* x, double* y);
+// refined float solve: y = A^+ x via float W and a double residual
+int la_apply3_refined(bem_ctx* c, const float* W32, const double* A, const double* x, double* y,
+                      bool transpose);
+void la_dgemm(bem_ctx* c, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
+              int lda, const double* B, int ldb, double beta, double* C, int ldc);
+// LM solve: delta for (H + lam D) delta = -g with the compatibility KKT;
+// returns BEM_ENOTSPD if the Cholesky fails
+int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double* delta);
+
+// ---- forward field (k_field.cu) --------------------------------------------------
+// u at n points into out (sample type), optional residual/loss; loss sum -> d_scal[0]
+int field_eval(bem_ctx* c, int64_t n, const void* xy, void* out, const void* target,
+               void* resid, bool want_loss);
+int field_rhs(bem_ctx* c);           // d_fb from the current panels
+int field_solve(bem_ctx* c);         // d_ub = A^+ d_fb
+int field_sample_mean(bem_ctx* c, int64_t n, const void* target, double* host_mean);
+
+// ---- adjoint (k_adjoint.cu) ------------------------------------------------------
+int adj_vjp(bem_ctx* c, int64_t n, const void* xy, const void* resid, double* grad);
+
+// ---- Gauss-Newton matrix (k_jtj.cu) ----------------------------------------------
+int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H);
+
+}  // namespace bem
+
+#define BEM_LAUNCHED(c) ((c)->launches++)

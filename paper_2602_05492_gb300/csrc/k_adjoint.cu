@@ -1,0 +1,326 @@
+// Reverse-mode gradient of sum_s r_s . u(x_s) (Sec. 3.2, Eq. (diffbie)).
+//
+//   sum_s r_s.u(x_s) = sum_s r_s.f(x_s) + q^T u_b,      q_j = sum_s phi_j(x_s)/(2pi) r_s
+//   u_b = A^+ f_b  =>  q^T u_b = lambda^T f_b,           lambda = (A^+)^T q
+//   f_b,i = |G_i| sum_k w_k f(x_ik)
+// so the gradient is the handle-term adjoint over the samples (weights r_s)
+// plus the same adjoint over the boundary Gauss points (weights
+// lambda_i |G_i| w_k).  Kernel values are recomputed, nothing of size
+// samples x panels is stored.
+//
+// Per (point, panel) pair the weighted handle term is
+//   F = alpha Dl + beta S,  alpha = -r.w_d, beta = r.w_c,
+// and its endpoint gradient is assembled from five per-panel sums of frame
+// partials (see common.cuh):
+//   A1 = sum F_t1, A2 = sum F_t2, A3 = sum h (F_t1+F_t2), A5 = sum t1 F_h, A6 = sum F_h
+//   dF/da = tau A1 + n (-A3 + A5 + L A6)/L,   dF/db = tau A2 + n (A3 - A5)/L
+// plus the jump derivatives sum -r_c Dl and sum r_c S: 11 sums per panel.
+// One thread owns one panel and walks the points of its block's chunk, so
+// these sums stay in registers (no cross-thread reduction per pair).
+#include <algorithm>
+#include <cmath>
+
+#include "ctx.h"
+
+namespace bem {
+
+constexpr int kVB = 128;     // threads per block (panels per block)
+constexpr int kNP = 11;      // sums per panel
+
+template <typename T>
+struct VjpArgs {
+  const T* xy;
+  const T* w;          // weights [n][3]
+  int64_t n;
+  const Panel<T>* pan;
+  const Panel<double>* pan64;
+  int P;
+  const T* vert;
+  int Nb;              // boundary segments handled by the extra blocks (0 = none)
+  T ec2, ed2;
+  double ec2d, ed2d;
+  T near2;
+  int64_t chunk;       // points per blockIdx.y
+  double* part;        // [gridDim.y][P][11]
+  double* qpart;       // [gridDim.y][Nb][3]
+};
+
+template <typename T>
+struct Acc11 {
+  T v[kNP];
+};
+
+template <typename T, bool SAME>
+__device__ __forceinline__ void pair_adj(const Panel<T>& p, T x, T y, T r0, T r1, T r2, T ec2,
+                                         T ed2, T* acc) {
+  Frame<T> f = frame(p, x, y);
+  LayerGrad<T> g = layer_grad(f, ec2, ed2, SAME);
+  T al = -(r0 * p.wd[0] + r1 * p.wd[1] + r2 * p.wd[2]);
+  T be = r0 * p.wc[0] + r1 * p.wc[1] + r2 * p.wc[2];
+  T gt1 = al * g.D_t1 + be * g.S_t1;
+  T gt2 = al * g.D_t2 + be * g.S_t2;
+  T gh = al * g.D_h + be * g.S_h;
+  acc[0] += gt1;
+  acc[1] += gt2;
+  acc[2] += f.h * (gt1 + gt2);
+  acc[3] += f.t1 * gh;
+  acc[4] += gh;
+  acc[5] -= r0 * g.Dl;
+  acc[6] -= r1 * g.Dl;
+  acc[7] -= r2 * g.Dl;
+  acc[8] += r0 * g.S;
+  acc[9] += r1 * g.S;
+  acc[10] += r2 * g.S;
+}
+
+template <typename T, bool SAME, bool NEAR>
+__global__ void __launch_bounds__(kVB) k_vjp(VjpArgs<T> a) {
+  __shared__ T sx[kVB], sy[kVB], sr[3 * kVB];
+  const int tid = threadIdx.x;
+  const int ptiles = (a.P + kVB - 1) / kVB;
+  const bool is_pan = (int)blockIdx.x < ptiles;
+  const int idx = is_pan ? blockIdx.x * kVB + tid : (blockIdx.x - ptiles) * kVB + tid;
+  const bool live = is_pan ? idx < a.P : idx < a.Nb;
+  const int64_t s0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t s1 = min(a.n, s0 + a.chunk);
+
+  Panel<T> p{};
+  Panel<double> pd{};
+  T bax = 0, bay = 0, bbx = 0, bby = 0;
+  if (live) {
+    if (is_pan) {
+      p = a.pan[idx];
+      if (NEAR) pd = a.pan64[idx];
+    } else {
+      bax = a.vert[2 * idx]; bay = a.vert[2 * idx + 1];
+      bbx = a.vert[2 * idx + 2]; bby = a.vert[2 * idx + 3];
+    }
+  }
+  double tot[kNP];
+#pragma unroll
+  for (int k = 0; k < kNP; ++k) tot[k] = 0.0;
+
+  for (int64_t base = s0; base < s1; base += kVB) {
+    int cnt = (int)min((int64_t)kVB, s1 - base);
+    __syncthreads();
+    if (tid < cnt) {
+      sx[tid] = a.xy[2 * (base + tid)];
+      sy[tid] = a.xy[2 * (base + tid) + 1];
+      sr[3 * tid] = a.w[3 * (base + tid)];
+      sr[3 * tid + 1] = a.w[3 * (base + tid) + 1];
+      sr[3 * tid + 2] = a.w[3 * (base + tid) + 2];
+    }
+    __syncthreads();
+    if (!live) continue;
+    T acc[kNP];
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) acc[k] = T(0);
+    if (is_pan) {
+      for (int k = 0; k < cnt; ++k) {
+        T x = sx[k], y = sy[k];
+        if (NEAR) {
+          Frame<T> f = frame(p, x, y);
+          T dt = f.t1 > T(0) ? f.t1 : (f.t2 < T(0) ? f.t2 : T(0));
+          if (dt * dt + f.h * f.h < a.near2 * f.L * f.L) {
+            double dacc[kNP];
+#pragma unroll
+            for (int q = 0; q < kNP; ++q) dacc[q] = 0.0;
+            pair_adj<double, SAME>(pd, double(x), double(y), double(sr[3 * k]),
+                                   double(sr[3 * k + 1]), double(sr[3 * k + 2]), a.ec2d, a.ed2d,
+                                   dacc);
+#pragma unroll
+            for (int q = 0; q < kNP; ++q) tot[q] += dacc[q];
+            continue;
+          }
+        }
+        pair_adj<T, SAME>(p, x, y, sr[3 * k], sr[3 * k + 1], sr[3 * k + 2], a.ec2, a.ed2, acc);
+      }
+    } else {
+      for (int k = 0; k < cnt; ++k) {
+        T phi = seg_angle(bax, bay, bbx, bby, sx[k], sy[k]);
+        acc[0] += phi * sr[3 * k];
+        acc[1] += phi * sr[3 * k + 1];
+        acc[2] += phi * sr[3 * k + 2];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) tot[k] += double(acc[k]);
+  }
+  if (!live) return;
+  if (is_pan) {
+    double* o = a.part + ((size_t)blockIdx.y * a.P + idx) * kNP;
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) o[k] = tot[k];
+  } else {
+    double* o = a.qpart + ((size_t)blockIdx.y * a.Nb + idx) * 3;
+    for (int k = 0; k < 3; ++k) o[k] = tot[k] * kInv2Pi;
+  }
+}
+
+// out[m] (+)= sum over slices of part[slice][m], fixed order
+__global__ void k_reduce_slices(const double* __restrict__ part, int slices, int64_t m,
+                                double* __restrict__ out, int accumulate) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  double s = 0;
+  for (int k = 0; k < slices; ++k) s += part[(size_t)k * m + t];
+  out[t] = accumulate ? out[t] + s : s;
+}
+
+// weights of the boundary Gauss points: lambda_i |G_i| w_k
+template <typename T>
+__global__ void k_gauss_weights(const double* __restrict__ lam, int Nb,
+                                const double* __restrict__ vert, T* __restrict__ w) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * Nb) return;
+  int i = t / 3, q = t % 3;
+  double ex = vert[2 * (i + 1)] - vert[2 * i], ey = vert[2 * (i + 1) + 1] - vert[2 * i + 1];
+  double s = sqrt(ex * ex + ey * ey) * gauss_weight(q);
+  for (int c = 0; c < 3; ++c) w[3 * t + c] = T(lam[3 * i + c] * s);
+}
+
+// Panel sums -> parameter gradient through the Bernstein maps.
+__global__ void k_chain(const double* __restrict__ ps, const Panel<double>* __restrict__ pan,
+                        const int* __restrict__ off, const int* __restrict__ Kc,
+                        const uint8_t* __restrict__ closed, int C, double scale,
+                        double* __restrict__ grad) {
+  int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= 4 * C) return;
+  int i = h / 4, j = h % 4, K = Kc[i];
+  bool cl = closed[i];
+  double gx = 0, gy = 0, gd[3] = {0, 0, 0}, gc[3] = {0, 0, 0};
+  for (int k = 0; k < K; ++k) {
+    int p = off[i] + k;
+    const double* q = ps + (size_t)p * kNP;
+    double t0 = double(k) / K, t1 = double(k + 1) / K;
+    double wa = bern3(j, t0), wb = bern3(j, t1);
+    if (cl && j == 0) { wa += bern3(3, t0); wb += bern3(3, t1); }
+    if (cl && j == 3) { wa = 0; wb = 0; }
+    double L = pan[p].L;
+    if (L > 0 && (wa != 0 || wb != 0)) {
+      double tx = pan[p].tx, ty = pan[p].ty, iL = 1.0 / L;
+      double na = (-q[2] + q[3] + L * q[4]) * iL;
+      double nb = (q[2] - q[3]) * iL;
+      double dax = q[0] * tx + na * ty, day = q[0] * ty - na * tx;
+      double dbx = q[1] * tx + nb * ty, dby = q[1] * ty - nb * tx;
+      gx += wa * dax + wb * dbx;
+      gy += wa * day + wb * dby;
+    }
+    double wm = bern3(j, (k + 0.5) / K);
+    for (int c = 0; c < 3; ++c) {
+      gd[c] += wm * q[5 + c];
+      gc[c] += wm * q[8 + c];
+    }
+  }
+  double* g = grad + (size_t)h * 8;
+  g[0] = scale * gx;
+  g[1] = scale * gy;
+  for (int c = 0; c < 3; ++c) {
+    g[2 + c] = scale * gd[c];
+    g[5 + c] = scale * gc[c];
+  }
+}
+
+template <typename T>
+static int vjp_pass(bem_ctx* c, int64_t n, const T* xy, const T* w, bool boundary, int accumulate) {
+  int rc;
+  int P = c->sc.P, Nb = boundary ? c->bd.Nb : 0;
+  int ptiles = (P + kVB - 1) / kVB, btiles = (Nb + kVB - 1) / kVB;
+  int tiles = ptiles + btiles;
+  // about four blocks per SM in total, chunks of at least one point tile
+  int64_t want = (4 * 152 + tiles - 1) / tiles;
+  int64_t maxs = (n + kVB - 1) / kVB;
+  int slices = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxs));
+  int64_t chunk = ((n + slices - 1) / slices + kVB - 1) / kVB * kVB;
+  slices = (int)std::max<int64_t>(1, (n + chunk - 1) / chunk);
+  size_t pbytes = sizeof(double) * (size_t)slices * P * kNP;
+  size_t qbytes = sizeof(double) * (size_t)slices * (Nb > 0 ? Nb : 1) * 3;
+  if ((rc = grow(c, c->part, pbytes + qbytes))) return rc;
+  VjpArgs<T> a{};
+  a.xy = xy;
+  a.w = w;
+  a.n = n;
+  a.pan = (const Panel<T>*)(sizeof(T) == 8 ? (const void*)c->d_pan64 : (const void*)c->d_pan32);
+  a.pan64 = c->d_pan64;
+  a.P = P;
+  a.vert = (const T*)(sizeof(T) == 8 ? (const void*)c->bd.d_vert : (const void*)c->bd.d_vert32);
+  a.Nb = Nb;
+  a.ec2 = T(c->opts.eps_c * c->opts.eps_c);
+  a.ed2 = T(c->opts.eps_d * c->opts.eps_d);
+  a.ec2d = c->opts.eps_c * c->opts.eps_c;
+  a.ed2d = c->opts.eps_d * c->opts.eps_d;
+  a.near2 = T(c->opts.near_factor * c->opts.near_factor);
+  a.chunk = chunk;
+  a.part = (double*)c->part.p;
+  a.qpart = (double*)((char*)c->part.p + pbytes);
+  if (n > 0) {
+    dim3 grid(tiles, slices);
+    bool same = c->opts.eps_c == c->opts.eps_d;
+    bool near = sizeof(T) == 4 && c->opts.near_factor > 0;
+    if (same) {
+      if (near) k_vjp<T, true, true><<<grid, kVB, 0, S(c)>>>(a);
+      else k_vjp<T, true, false><<<grid, kVB, 0, S(c)>>>(a);
+    } else {
+      if (near) k_vjp<T, false, true><<<grid, kVB, 0, S(c)>>>(a);
+      else k_vjp<T, false, false><<<grid, kVB, 0, S(c)>>>(a);
+    }
+    BEM_LAUNCHED(c);
+  } else {
+    slices = 0;
+  }
+  // panel sums (accumulated into part2[P][11]) and q (into d_q)
+  int64_t m = (int64_t)P * kNP;
+  if (slices > 0) {
+    k_reduce_slices<<<(unsigned)((m + 255) / 256), 256, 0, S(c)>>>(a.part, slices, m,
+                                                                     (double*)c->part2.p,
+                                                                     accumulate);
+    BEM_LAUNCHED(c);
+  } else if (!accumulate) {
+    if ((rc = cuda_check(c, cudaMemsetAsync(c->part2.p, 0, sizeof(double) * m, S(c)), "memset")))
+      return rc;
+  }
+  if (boundary) {
+    if (slices > 0) {
+      k_reduce_slices<<<(3 * Nb + 255) / 256, 256, 0, S(c)>>>(a.qpart, slices, 3 * (int64_t)Nb,
+                                                               c->d_q, 0);
+      BEM_LAUNCHED(c);
+    } else if ((rc = cuda_check(c, cudaMemsetAsync(c->d_q, 0, sizeof(double) * 3 * Nb, S(c)),
+                                "memset"))) {
+      return rc;
+    }
+  }
+  return cuda_check(c, cudaGetLastError(), "k_vjp");
+}
+
+template <typename T>
+static int adj_vjp_t(bem_ctx* c, int64_t n, const T* xy, const T* resid, double* grad) {
+  int rc;
+  int P = c->sc.P, Nb = c->bd.Nb;
+  if ((rc = grow(c, c->part2, sizeof(double) * (size_t)P * kNP))) return rc;
+  // samples: panel sums and q
+  if ((rc = vjp_pass<T>(c, n, xy, resid, true, 0))) return rc;
+  // lambda = (A^+)^T q
+  if (c->opts.precision == BEM_FP64) rc = la_apply3(c, c->bd.d_WT, c->d_q, c->d_lb);
+  else rc = la_apply3_refined(c, c->bd.d_WT32, c->bd.d_A, c->d_q, c->d_lb, true);
+  if (rc) return rc;
+  // boundary Gauss points with weights lambda_i |G_i| w_k
+  if ((rc = grow(c, c->g, sizeof(double) * 9 * (size_t)Nb))) return rc;
+  T* gw = (T*)c->g.p;
+  k_gauss_weights<T><<<(3 * Nb + 255) / 256, 256, 0, S(c)>>>(c->d_lb, Nb, c->bd.d_vert, gw);
+  BEM_LAUNCHED(c);
+  const T* gp = (const T*)(sizeof(T) == 8 ? (const void*)c->bd.d_gp : (const void*)c->bd.d_gp32);
+  if ((rc = vjp_pass<T>(c, 3 * (int64_t)Nb, gp, gw, false, 1))) return rc;
+  k_chain<<<(4 * c->sc.C + 127) / 128, 128, 0, S(c)>>>((const double*)c->part2.p, c->d_pan64,
+                                                        c->sc.d_off, c->sc.d_K, c->sc.d_closed,
+                                                        c->sc.C, 1.0, grad);
+  BEM_LAUNCHED(c);
+  return cuda_check(c, cudaGetLastError(), "vjp chain");
+}
+
+int adj_vjp(bem_ctx* c, int64_t n, const void* xy, const void* resid, double* grad) {
+  if (c->opts.precision == BEM_FP64)
+    return adj_vjp_t<double>(c, n, (const double*)xy, (const double*)resid, grad);
+  return adj_vjp_t<float>(c, n, (const float*)xy, (const float*)resid, grad);
+}
+
+}  // namespace bem

@@ -1,0 +1,340 @@
+// Forward evaluation (Sec. 3.1.3, Eq. (bie) with alpha = 1):
+//   u(x) = mean + sum_j phi_j(x)/(2 pi) u_b,j + sum_p [ -w_d,p Dl_p(x) + w_c,p S_p(x) ]
+// One thread per point; panels (and boundary vertices) are staged block-wide
+// in shared memory and broadcast to every warp.  In mixed precision the
+// pair terms are float, except for pairs closer than near_factor panel
+// lengths, which are recomputed in double from the double panel table.
+#include <cmath>
+
+#include "ctx.h"
+
+namespace bem {
+
+constexpr int kFB = 128;   // threads per block = panels per shared-memory tile
+
+template <typename T>
+struct FieldArgs {
+  const T* xy;
+  int64_t n;
+  const Panel<T>* pan;
+  const Panel<double>* pan64;
+  int P;
+  int pchunk;          // panels per blockIdx.y slice (split mode)
+  const T* vert;       // boundary vertices [(Nb+1)][2] or null
+  const double* ub;    // boundary solution [Nb][3] or null
+  int Nb;
+  double mean0, mean1, mean2;
+  T ec2, ed2;          // eps_c^2, eps_d^2
+  double ec2d, ed2d;
+  T near2;             // (near_factor)^2, mixed precision only
+  const T* target;     // clamp target or null
+  T* out;              // colours [n][3] or null
+  T* resid;            // residual [n][3] or null
+  double* loss_part;   // per-block sum of |r|^2 or null
+  double* split_out;   // split mode: [gridDim.y][n][3] handle-term partials
+};
+
+// Pair contribution of one panel at (x, y) in double.
+template <bool SAME>
+__device__ __forceinline__ void pair_f64(const Panel<double>& p, double x, double y, double ec2,
+                                         double ed2, double& a0, double& a1, double& a2) {
+  Frame<double> f = frame(p, x, y);
+  LayerVals<double> v = layer_values(f, ec2, ed2, SAME);
+  a0 += -p.wd[0] * v.Dl + p.wc[0] * v.S;
+  a1 += -p.wd[1] * v.Dl + p.wc[1] * v.S;
+  a2 += -p.wd[2] * v.Dl + p.wc[2] * v.S;
+}
+
+// Sum over one shared-memory tile of panels.
+template <typename T, bool SAME, bool NEAR>
+__device__ __forceinline__ void tile_accum(const Panel<T>* tile, int base, int cnt, T x, T y,
+                                           const FieldArgs<T>& a, T& s0, T& s1, T& s2,
+                                           double& d0, double& d1, double& d2) {
+  for (int k = 0; k < cnt; ++k) {
+    const Panel<T>& p = tile[k];
+    Frame<T> f = frame(p, x, y);
+    if (NEAR) {
+      // squared distance from x to the panel segment vs (near_factor L)^2
+      T dt = f.t1 > T(0) ? f.t1 : (f.t2 < T(0) ? f.t2 : T(0));
+      if (dt * dt + f.h * f.h < a.near2 * f.L * f.L) {
+        pair_f64<SAME>(a.pan64[base + k], double(x), double(y), a.ec2d, a.ed2d, d0, d1, d2);
+        continue;
+      }
+    }
+    LayerVals<T> v = layer_values(f, a.ec2, a.ed2, SAME);
+    s0 += -p.wd[0] * v.Dl + p.wc[0] * v.S;
+    s1 += -p.wd[1] * v.Dl + p.wc[1] * v.S;
+    s2 += -p.wd[2] * v.Dl + p.wc[2] * v.S;
+  }
+}
+
+template <typename T, bool SAME, bool NEAR>
+__global__ void __launch_bounds__(kFB) k_field(FieldArgs<T> a) {
+  __shared__ Panel<T> tile[kFB];
+  __shared__ T sv[2 * (kFB + 1)];
+  __shared__ T su[3 * kFB];
+  __shared__ double red[kFB / 32];
+  const int tid = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * kFB + tid;
+  const bool live = i < a.n;
+  T x = T(0.5), y = T(0.5);
+  if (live) { x = a.xy[2 * i]; y = a.xy[2 * i + 1]; }
+  T s0 = 0, s1 = 0, s2 = 0;
+  double d0 = 0, d1 = 0, d2 = 0;
+  const int p0 = a.split_out ? blockIdx.y * a.pchunk : 0;
+  const int p1 = a.split_out ? min(a.P, p0 + a.pchunk) : a.P;
+  for (int base = p0; base < p1; base += kFB) {
+    __syncthreads();
+    if (base + tid < p1) tile[tid] = a.pan[base + tid];
+    __syncthreads();
+    tile_accum<T, SAME, NEAR>(tile, base, min(kFB, p1 - base), x, y, a, s0, s1, s2, d0, d1, d2);
+  }
+  if (a.split_out) {
+    if (live) {
+      double* o = a.split_out + ((size_t)blockIdx.y * a.n + i) * 3;
+      o[0] = double(s0) + d0;
+      o[1] = double(s1) + d1;
+      o[2] = double(s2) + d2;
+    }
+    return;
+  }
+  // boundary double layer with the (double) boundary solution
+  T b0 = 0, b1 = 0, b2 = 0;
+  if (a.ub) {
+    for (int base = 0; base < a.Nb; base += kFB) {
+      __syncthreads();
+      int cnt = min(kFB, a.Nb - base);
+      if (tid < cnt) {
+        sv[2 * tid] = a.vert[2 * (base + tid)];
+        sv[2 * tid + 1] = a.vert[2 * (base + tid) + 1];
+        su[3 * tid] = T(a.ub[3 * (base + tid)]);
+        su[3 * tid + 1] = T(a.ub[3 * (base + tid) + 1]);
+        su[3 * tid + 2] = T(a.ub[3 * (base + tid) + 2]);
+      }
+      if (tid == 0) {
+        sv[2 * cnt] = a.vert[2 * (base + cnt)];
+        sv[2 * cnt + 1] = a.vert[2 * (base + cnt) + 1];
+      }
+      __syncthreads();
+      for (int k = 0; k < cnt; ++k) {
+        T phi = seg_angle(sv[2 * k], sv[2 * k + 1], sv[2 * k + 2], sv[2 * k + 3], x, y);
+        b0 += phi * su[3 * k];
+        b1 += phi * su[3 * k + 1];
+        b2 += phi * su[3 * k + 2];
+      }
+    }
+  }
+  double u0 = a.mean0 + double(b0) * kInv2Pi + double(s0) + d0;
+  double u1 = a.mean1 + double(b1) * kInv2Pi + double(s1) + d1;
+  double u2 = a.mean2 + double(b2) * kInv2Pi + double(s2) + d2;
+  double r2 = 0.0;
+  if (live) {
+    if (a.out) {
+      a.out[3 * i] = T(u0);
+      a.out[3 * i + 1] = T(u1);
+      a.out[3 * i + 2] = T(u2);
+    }
+    if (a.target) {
+      double r0 = u0 - fmin(double(a.target[3 * i]), 1.0);
+      double r1 = u1 - fmin(double(a.target[3 * i + 1]), 1.0);
+      double rr = u2 - fmin(double(a.target[3 * i + 2]), 1.0);
+      if (a.resid) {
+        a.resid[3 * i] = T(r0);
+        a.resid[3 * i + 1] = T(r1);
+        a.resid[3 * i + 2] = T(rr);
+      }
+      r2 = r0 * r0 + r1 * r1 + rr * rr;
+    }
+  }
+  if (a.loss_part) {
+    for (int o = 16; o; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
+    if ((tid & 31) == 0) red[tid >> 5] = r2;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0;
+      for (int w = 0; w < kFB / 32; ++w) s += red[w];
+      a.loss_part[blockIdx.x] = s;
+    }
+  }
+}
+
+// sum of per-block partials in fixed order -> out[0]
+__global__ void k_sum_fixed(const double* __restrict__ part, int64_t m, double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0;
+  // each thread sums a contiguous range so the order is fixed
+  int64_t per = (m + blockDim.x - 1) / blockDim.x;
+  int64_t b = threadIdx.x * per, e = b + per < m ? b + per : m;
+  for (int64_t k = b; k < e; ++k) s += part[k];
+  for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    *out = t;
+  }
+}
+
+// f_b,i = |G_i| sum_q w_q f(x_iq) from split partials
+__global__ void k_rhs_reduce(const double* __restrict__ part, int nsplit, int Nb,
+                             const double* __restrict__ vert, double* __restrict__ fb) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * Nb) return;
+  int i = t / 3, c = t % 3;
+  double ex = vert[2 * (i + 1)] - vert[2 * i], ey = vert[2 * (i + 1) + 1] - vert[2 * i + 1];
+  double ell = sqrt(ex * ex + ey * ey);
+  int64_t n = 3 * (int64_t)Nb;
+  double s = 0;
+  for (int q = 0; q < 3; ++q) {
+    double f = 0;
+    for (int sp = 0; sp < nsplit; ++sp) f += part[((size_t)sp * n + 3 * i + q) * 3 + c];
+    s += gauss_weight(q) * f;
+  }
+  fb[3 * i + c] = ell * s;
+}
+
+template <typename T>
+__global__ void k_mean_part(const T* __restrict__ t, int64_t n, double* __restrict__ part) {
+  __shared__ double red[3][32];
+  double s[3] = {0, 0, 0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < 3; ++c) s[c] += fmin(double(t[3 * i + c]), 1.0);
+  for (int c = 0; c < 3; ++c)
+    for (int o = 16; o; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int c = 0; c < 3; ++c) red[c][threadIdx.x >> 5] = s[c];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) v += red[threadIdx.x][w];
+    part[blockIdx.x * 3 + threadIdx.x] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static FieldArgs<T> make_args(bem_ctx* c) {
+  FieldArgs<T> a{};
+  a.pan = (const Panel<T>*)(sizeof(T) == 8 ? (const void*)c->d_pan64 : (const void*)c->d_pan32);
+  a.pan64 = c->d_pan64;
+  a.P = c->sc.P;
+  a.pchunk = c->sc.P;
+  a.vert = (const T*)(sizeof(T) == 8 ? (const void*)c->bd.d_vert : (const void*)c->bd.d_vert32);
+  a.Nb = c->bd.Nb;
+  a.ec2 = T(c->opts.eps_c * c->opts.eps_c);
+  a.ed2 = T(c->opts.eps_d * c->opts.eps_d);
+  a.ec2d = c->opts.eps_c * c->opts.eps_c;
+  a.ed2d = c->opts.eps_d * c->opts.eps_d;
+  a.near2 = T(c->opts.near_factor * c->opts.near_factor);
+  return a;
+}
+
+template <typename T>
+static void launch_field(bem_ctx* c, const FieldArgs<T>& a, dim3 grid) {
+  bool same = c->opts.eps_c == c->opts.eps_d;
+  bool near = sizeof(T) == 4 && c->opts.near_factor > 0;
+  if (same) {
+    if (near) k_field<T, true, true><<<grid, kFB, 0, S(c)>>>(a);
+    else k_field<T, true, false><<<grid, kFB, 0, S(c)>>>(a);
+  } else {
+    if (near) k_field<T, false, true><<<grid, kFB, 0, S(c)>>>(a);
+    else k_field<T, false, false><<<grid, kFB, 0, S(c)>>>(a);
+  }
+  BEM_LAUNCHED(c);
+}
+
+template <typename T>
+static int field_eval_t(bem_ctx* c, int64_t n, const void* xy, void* out, const void* target,
+                        void* resid, bool want_loss) {
+  int rc;
+  FieldArgs<T> a = make_args<T>(c);
+  a.xy = (const T*)xy;
+  a.n = n;
+  a.ub = c->d_ub;
+  a.mean0 = c->mean[0]; a.mean1 = c->mean[1]; a.mean2 = c->mean[2];
+  a.target = (const T*)target;
+  a.out = (T*)out;
+  a.resid = (T*)resid;
+  int64_t nblk = (n + kFB - 1) / kFB;
+  if (want_loss) {
+    if ((rc = grow(c, c->loss, sizeof(double) * (nblk + 1)))) return rc;
+    a.loss_part = (double*)c->loss.p;
+  }
+  if (nblk > 0) launch_field<T>(c, a, dim3((unsigned)nblk));
+  if (want_loss) {
+    if (nblk > 0) {
+      k_sum_fixed<<<1, 1024, 0, S(c)>>>(a.loss_part, nblk, c->d_scal);
+      BEM_LAUNCHED(c);
+    } else if ((rc = cuda_check(c, cudaMemsetAsync(c->d_scal, 0, 8, S(c)), "memset"))) {
+      return rc;
+    }
+  }
+  return cuda_check(c, cudaGetLastError(), "k_field");
+}
+
+int field_eval(bem_ctx* c, int64_t n, const void* xy, void* out, const void* target, void* resid,
+               bool want_loss) {
+  if (c->opts.precision == BEM_FP64)
+    return field_eval_t<double>(c, n, xy, out, target, resid, want_loss);
+  return field_eval_t<float>(c, n, xy, out, target, resid, want_loss);
+}
+
+template <typename T>
+static int field_rhs_t(bem_ctx* c) {
+  int rc;
+  int Nb = c->bd.Nb, P = c->sc.P;
+  int64_t n = 3 * (int64_t)Nb;
+  int nsplit = (P + kFB - 1) / kFB;
+  if (nsplit > 64) nsplit = 64;
+  int pchunk = ((P + nsplit - 1) / nsplit + kFB - 1) / kFB * kFB;
+  nsplit = (P + pchunk - 1) / pchunk;
+  if ((rc = grow(c, c->gpart, sizeof(double) * (size_t)nsplit * n * 3))) return rc;
+  FieldArgs<T> a = make_args<T>(c);
+  a.xy = (const T*)(sizeof(T) == 8 ? (const void*)c->bd.d_gp : (const void*)c->bd.d_gp32);
+  a.n = n;
+  a.pchunk = pchunk;
+  a.split_out = (double*)c->gpart.p;
+  launch_field<T>(c, a, dim3((unsigned)((n + kFB - 1) / kFB), nsplit));
+  k_rhs_reduce<<<(3 * Nb + 255) / 256, 256, 0, S(c)>>>(a.split_out, nsplit, Nb, c->bd.d_vert,
+                                                        c->d_fb);
+  BEM_LAUNCHED(c);
+  return cuda_check(c, cudaGetLastError(), "rhs");
+}
+
+int field_rhs(bem_ctx* c) {
+  if (c->opts.precision == BEM_FP64) return field_rhs_t<double>(c);
+  return field_rhs_t<float>(c);
+}
+
+int field_solve(bem_ctx* c) {
+  if (c->opts.precision == BEM_FP64) return la_apply3(c, c->bd.d_W, c->d_fb, c->d_ub);
+  return la_apply3_refined(c, c->bd.d_W32, c->bd.d_A, c->d_fb, c->d_ub, false);
+}
+
+int field_sample_mean(bem_ctx* c, int64_t n, const void* target, double* host_mean) {
+  int rc;
+  const int nb = 256;
+  if ((rc = grow(c, c->loss, sizeof(double) * 3 * nb))) return rc;
+  double* part = (double*)c->loss.p;
+  if (c->opts.precision == BEM_FP64)
+    k_mean_part<double><<<nb, 256, 0, S(c)>>>((const double*)target, n, part);
+  else
+    k_mean_part<float><<<nb, 256, 0, S(c)>>>((const float*)target, n, part);
+  BEM_LAUNCHED(c);
+  double h[3 * nb];
+  if ((rc = cuda_check(c, cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, S(c)),
+                       "mean")))
+    return rc;
+  if ((rc = cuda_check(c, cudaStreamSynchronize(S(c)), "mean sync"))) return rc;
+  for (int k = 0; k < 3; ++k) {
+    double s = 0;
+    for (int b = 0; b < nb; ++b) s += h[3 * b + k];
+    host_mean[k] = n > 0 ? s / double(n) : 0.0;
+  }
+  return BEM_OK;
+}
+
+}  // namespace bem

@@ -1,0 +1,271 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GPU only).
+
+Tolerances (stated per result, from the accuracy targets of this project):
+  FP64 GPU path       <= 1e-10 relative to the oracle
+  mixed path colours  <= 1e-4 RMSE on [0,1] colours
+  mixed path gradient <= 1e-4 relative (2-norm)
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _bg():
+    import paper_2602_05492_gb300 as bg
+    return bg
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    sc = gen.make_scene(1)
+    xy = gen.make_samples(sc.W, sc.spp, sc.seed)
+    o = oracle.Oracle.from_scene(sc)
+    truth = o.eval(oracle.project_compat(o.geo, sc.theta_true), xy)
+    target = gen.add_noise(truth, sc.noise, sc.seed)
+    mean = np.minimum(target, 1.0).mean(0)
+    o.mean = mean
+    return sc, xy, target, mean, o
+
+
+def _ctx(sc, mean, prec, theta=None, **kw):
+    bg = _bg()
+    m = bg.BEM(precision=prec, **kw)
+    m.setup(sc.n_curves, sc.panels_per_curve, sc.closed,
+            sc.theta_init if theta is None else theta, mean)
+    m.factor()
+    return m
+
+
+def _t(a, dt):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda:0")
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# ---- FP64 path --------------------------------------------------------------
+
+def test_eval_fp64_cfg1_full(cfg1):
+    sc, xy, target, mean, o = cfg1
+    m = _ctx(sc, mean, _bg().BEM_FP64)
+    u = m.eval(_t(xy, torch.float64)).cpu().numpy()
+    want = o.eval(sc.theta_init, xy)
+    assert _rel(u, want) < 1e-10
+
+
+def test_boundary_values_fp64(cfg1):
+    sc, xy, target, mean, o = cfg1
+    m = _ctx(sc, mean, _bg().BEM_FP64)
+    assert _rel(m.boundary_values(), o.boundary_values(sc.theta_init)) < 1e-10
+
+
+def test_loss_and_residual_fp64(cfg1):
+    sc, xy, target, mean, o = cfg1
+    m = _ctx(sc, mean, _bg().BEM_FP64)
+    res = torch.empty((xy.shape[0], 3), dtype=torch.float64, device="cuda:0")
+    L = m.loss(_t(xy, torch.float64), _t(target, torch.float64), res)
+    r = o.eval(sc.theta_init, xy) - np.minimum(target, 1.0)
+    assert _rel(res.cpu().numpy(), r) < 1e-9
+    assert L == pytest.approx(o.loss(sc.theta_init, xy, target), rel=1e-12)
+
+
+def test_vjp_fp64(cfg1):
+    sc, xy, target, mean, o = cfg1
+    sub = xy[::8]
+    r = np.random.default_rng(0).normal(size=(sub.shape[0], 3))
+    m = _ctx(sc, mean, _bg().BEM_FP64)
+    g = m.vjp(_t(sub, torch.float64), _t(r, torch.float64)).cpu().numpy()
+    want = o.grad(sc.theta_init, sub, r)
+    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-10
+
+
+def test_jtj_fp64(cfg1):
+    sc, xy, target, mean, o = cfg1
+    sub = xy[::16]
+    m = _ctx(sc, mean, _bg().BEM_FP64)
+    H = m.jtj(_t(sub, torch.float64)).cpu().numpy()
+    _, _, want = o.gauss_newton(sc.theta_init, sub, target[::16])
+    assert np.linalg.norm(H - want) / np.linalg.norm(want) < 1e-10
+
+
+def test_lm_step_fp64(cfg1):
+    sc, xy, target, mean, o = cfg1
+    sub, tsub = xy[::16], target[::16]
+    m = _ctx(sc, mean, _bg().BEM_FP64)
+    res = m.lm_step(_t(sub, torch.float64), _t(tsub, torch.float64), [1e-3])
+    want = o.lm_step(sc.theta_init, sub, tsub, 1e-3)
+    assert res["loss_before"] == pytest.approx(want["loss_before"], rel=1e-11)
+    assert res["loss_after"] == pytest.approx(want["loss_after"], rel=1e-9)
+    assert res["accepted"] == want["accepted"]
+    th = m.get_params()
+    assert _rel(th, want["theta"]) < 1e-9
+
+
+def test_fd_gradient_fp64_on_gpu(cfg1):
+    """Central differences of the GPU loss against the GPU adjoint (no oracle)."""
+    sc, xy, target, mean, o = cfg1
+    sub, tsub = xy[::32], target[::32]
+    m = _ctx(sc, mean, _bg().BEM_FP64)
+    xt, tt = _t(sub, torch.float64), _t(tsub, torch.float64)
+    res = torch.empty((sub.shape[0], 3), dtype=torch.float64, device="cuda:0")
+    m.loss(xt, tt, res)
+    g = m.vjp(xt, res).cpu().numpy() / sub.shape[0]
+    th0 = sc.theta_init.copy()
+    h = 1e-6
+    for k in np.random.default_rng(1).choice(len(th0), 12, replace=False):
+        if k % 32 in (24, 25) and sc.closed[k // 32]:
+            continue
+        tp, tm = th0.copy(), th0.copy()
+        tp[k] += h
+        tm[k] -= h
+        m.set_params(tp)
+        Lp = m.loss(xt, tt)
+        m.set_params(tm)
+        Lm = m.loss(xt, tt)
+        fd = (Lp - Lm) / (2 * h)
+        assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-9)
+
+
+def test_unequal_eps_fp64(cfg1):
+    sc, xy, target, mean, o = cfg1
+    sub = xy[::4]
+    m = _ctx(sc, mean, _bg().BEM_FP64, eps_d=3e-3, eps_c=2e-2)
+    o2 = oracle.Oracle.from_scene(sc, mean_color=mean, eps_d=3e-3, eps_c=2e-2)
+    u = m.eval(_t(sub, torch.float64)).cpu().numpy()
+    assert _rel(u, o2.eval(sc.theta_init, sub)) < 1e-10
+    r = np.random.default_rng(2).normal(size=(sub.shape[0], 3))
+    g = m.vjp(_t(sub, torch.float64), _t(r, torch.float64)).cpu().numpy()
+    want = o2.grad(sc.theta_init, sub, r)
+    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-10
+
+
+@pytest.mark.parametrize("n", [0, 1, 127, 129, 1000])
+def test_ragged_sizes_fp64(cfg1, n):
+    sc, xy, target, mean, o = cfg1
+    sub = xy[:n]
+    m = _ctx(sc, mean, _bg().BEM_FP64)
+    xt = _t(sub.reshape(-1, 2), torch.float64)
+    u = m.eval(xt).cpu().numpy()
+    r = np.random.default_rng(n).normal(size=(n, 3))
+    g = m.vjp(xt, _t(r.reshape(-1, 3), torch.float64)).cpu().numpy()
+    if n == 0:
+        assert u.shape == (0, 3) and np.abs(g).max() == 0.0
+        return
+    assert _rel(u, o.eval(sc.theta_init, sub)) < 1e-10
+    want = o.grad(sc.theta_init, sub, r)
+    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-10
+
+
+# ---- mixed path -----------------------------------------------------------------
+
+def test_eval_mixed_cfg1_full(cfg1):
+    sc, xy, target, mean, o = cfg1
+    m = _ctx(sc, mean, _bg().BEM_MIXED)
+    u = m.eval(_t(xy, torch.float32)).double().cpu().numpy()
+    want = o.eval(sc.theta_init, xy)
+    rmse = np.sqrt(np.mean((u - want) ** 2))
+    assert rmse < 1e-4, rmse
+
+
+def test_vjp_mixed(cfg1):
+    sc, xy, target, mean, o = cfg1
+    sub = xy[::8]
+    r = np.random.default_rng(0).normal(size=(sub.shape[0], 3))
+    m = _ctx(sc, mean, _bg().BEM_MIXED)
+    g = m.vjp(_t(sub, torch.float32), _t(r, torch.float32)).cpu().numpy()
+    want = o.grad(sc.theta_init, sub, r.astype(np.float32).astype(np.float64))
+    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-4
+
+
+def test_jtj_mixed(cfg1):
+    sc, xy, target, mean, o = cfg1
+    sub = xy[::16]
+    m = _ctx(sc, mean, _bg().BEM_MIXED)
+    H = m.jtj(_t(sub, torch.float32)).cpu().numpy()
+    _, _, want = o.gauss_newton(sc.theta_init, sub, target[::16])
+    assert np.linalg.norm(H - want) / np.linalg.norm(want) < 2e-2
+
+
+def test_mixed_without_near_field(cfg1):
+    sc, xy, target, mean, o = cfg1
+    m = _ctx(sc, mean, _bg().BEM_MIXED, near_factor=0.0)
+    u = m.eval(_t(xy, torch.float32)).double().cpu().numpy()
+    rmse = np.sqrt(np.mean((u - o.eval(sc.theta_init, xy)) ** 2))
+    assert rmse < 1e-4, rmse
+
+
+# ---- full-size configurations, sampled outputs -----------------------------------
+
+@pytest.fixture(scope="module")
+def cfg2():
+    sc = gen.make_scene(2)
+    xy = gen.make_samples(sc.W, sc.spp, sc.seed)
+    target = gen.add_noise(gen.analytic_truth(xy, sc.seed), sc.noise, sc.seed)
+    mean = np.minimum(target, 1.0).mean(0)
+    o = oracle.Oracle.from_scene(sc, mean_color=mean)
+    idx = np.random.default_rng(5).choice(xy.shape[0], 1500, replace=False)
+    return sc, xy, target, mean, o, idx
+
+
+def test_eval_fp64_cfg2_sampled(cfg2):
+    sc, xy, target, mean, o, idx = cfg2
+    m = _ctx(sc, mean, _bg().BEM_FP64)
+    u = m.eval(_t(xy, torch.float64)).cpu().numpy()
+    assert _rel(u[idx], o.eval(sc.theta_init, xy[idx])) < 1e-10
+
+
+def test_eval_mixed_cfg2_sampled(cfg2):
+    sc, xy, target, mean, o, idx = cfg2
+    m = _ctx(sc, mean, _bg().BEM_MIXED)
+    u = m.eval(_t(xy, torch.float32)).double().cpu().numpy()
+    rmse = np.sqrt(np.mean((u[idx] - o.eval(sc.theta_init, xy[idx])) ** 2))
+    assert rmse < 1e-4, rmse
+
+
+def test_vjp_mixed_cfg2_linear_in_residual(cfg2):
+    """At full size the adjoint is checked by a property that holds at any
+    size: linearity in the residual, J^T(a r1 + b r2) = a J^T r1 + b J^T r2,
+    plus a sampled oracle comparison for the residual supported on few samples."""
+    sc, xy, target, mean, o, idx = cfg2
+    m = _ctx(sc, mean, _bg().BEM_MIXED)
+    xt = _t(xy, torch.float32)
+    rng = np.random.default_rng(9)
+    r = np.zeros((xy.shape[0], 3), np.float32)
+    r[idx] = rng.normal(size=(len(idx), 3))
+    g = m.vjp(xt, _t(r, torch.float32)).cpu().numpy()
+    want = o.grad(sc.theta_init, xy[idx], r[idx].astype(np.float64))
+    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-4
+
+
+# ---- errors ------------------------------------------------------------------------
+
+def test_state_and_argument_errors(cfg1):
+    bg = _bg()
+    sc, xy, target, mean, o = cfg1
+    with pytest.raises(bg.BemError) as e:
+        bg.BEM(eps_d=0.0)
+    assert e.value.code == bg.BEM_EINVAL
+    m = bg.BEM(precision=bg.BEM_FP64)
+    m.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, mean)
+    with pytest.raises(bg.BemError) as e:
+        m.eval(_t(xy[:10], torch.float64))
+    assert e.value.code == bg.BEM_ESTATE
+    bad = sc.theta_init.copy()
+    bad[3] = np.nan
+    with pytest.raises(bg.BemError) as e:
+        m.setup(sc.n_curves, sc.panels_per_curve, sc.closed, bad, mean)
+    assert e.value.code == bg.BEM_EINVAL
+
+
+def test_sample_mean(cfg1):
+    sc, xy, target, mean, o = cfg1
+    m = _ctx(sc, mean, _bg().BEM_FP64)
+    got = m.sample_mean(_t(target, torch.float64))
+    np.testing.assert_allclose(got, mean, rtol=1e-13)
