@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Throughput of the differential-BEM Levenberg-Marquardt hot path on GB300.
+
+One step = one LM iteration of the mixed-precision path (panelize, boundary
+right-hand side and solve, evaluation + residual + loss at every sample,
+adjoint gradient, Gauss-Newton matrix, damped KKT solve, trial evaluation)
+on the 32-curve / 2,048-panel / 1,048,576-sample workload.  Prints one JSON
+line.  `--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, one independent replica per GPU (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = ("LM iters/s & sample×panel evals/s (fwd+adjoint), mixed vs FP64 GPU at "
+          "≤1e-4 RMSE")
+UNIT = "LM iter/s"
+CFG = 2
+L2_FLUSH_BYTES = 256 << 20
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 lanes x 2 flops per FMA x SMs x max SM clock (GB300: 128, 152, 2070 MHz)
+FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12
+
+
+def workload_desc(sc):
+    return (f"cfg{CFG}: {sc.n_curves} cubic Bezier curves x {int(sc.panels_per_curve[0])} panels "
+            f"({sc.n_panels} panels), {sc.W}x{sc.W} px x {sc.spp} spp ({sc.n_samples} samples), "
+            f"1024 boundary segments, lognormal noise with 1% fireflies")
+
+
+def make_inputs(rank: int):
+    sc = gen.make_scene(CFG)
+    seed = sc.seed + 7919 * rank        # independent sample set per replica
+    xy = gen.make_samples(sc.W, sc.spp, seed, dtype=np.float32)
+    truth = gen.analytic_truth(xy, sc.seed)
+    target = gen.add_noise(truth, sc.noise, seed).astype(np.float32)
+    return sc, xy, target
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per unit (counted from the source formulas)
+
+# FP32 flops per handle pair (FMA = 2): frame 9, layer values 21, three
+# transcendentals (log, log1p, atan2) and one sqrt counted as 1 each, two
+# divisions as 1 each, 3-channel accumulation 12
+FLOP_FWD_HANDLE = 9 + 21 + 4 + 2 + 12
+# boundary pair: 4 sub, cross 3, dot 3, atan2 1, 3-channel accumulation 6
+FLOP_FWD_BOUND = 4 + 3 + 3 + 1 + 6
+# adjoint handle pair: frame 9, layer values and frame partials 45,
+# 4 transcendentals + 2 sqrt/div + 4 reciprocals, weights 10, 11 sums 26
+FLOP_ADJ_HANDLE = 9 + 45 + 10 + 10 + 26
+FLOP_ADJ_BOUND = 4 + 3 + 3 + 1 + 6
+
+
+def kernel_work(name, n, P, Nb, nc):
+    """(flops per launch, unit) of the profiled kernels."""
+    if name == "k_field":
+        return n * (P * FLOP_FWD_HANDLE + Nb * FLOP_FWD_BOUND), "alu"
+    if name == "k_vjp":
+        return n * (P * FLOP_ADJ_HANDLE + Nb * FLOP_ADJ_BOUND), "alu"
+    return None, None
+
+
+# ---------------------------------------------------------------------------
+
+def oracle_rate(sc, xy, target, n_sub: int, steps: int, warmup: int = 0) -> dict:
+    """The oracle as it stands, timed on bounded samples of the same workload.
+
+    One LM step costs a + b n on n samples (a: boundary Jacobian and other
+    per-iteration work, b: per-sample evaluation and Jacobian rows).  One step
+    on n_sub/2 samples and `steps` steps on n_sub samples fit a and b; the full
+    workload's time per iteration is a + b S.
+    """
+    import oracle
+    mean = np.minimum(target, 1.0).mean(0)
+    o = oracle.Oracle.from_scene(sc, mean_color=mean)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(xy.shape[0], n_sub, replace=False))
+    x, t = xy[idx].astype(np.float64), target[idx].astype(np.float64)
+    th, lam = sc.theta_init.copy(), 1e-3
+    for _ in range(warmup):
+        res = o.lm_step(th, x, t, lam)
+        th, lam = res["theta"], res["lambda_next"]
+    h = n_sub // 2
+    t0 = time.perf_counter()
+    o.lm_step(th, x[:h], t[:h], lam)
+    t_half = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(max(steps, 1)):
+        res = o.lm_step(th, x, t, lam)
+        th, lam = res["theta"], res["lambda_next"]
+    t_full = (time.perf_counter() - t0) / max(steps, 1)
+    b = max((t_full - t_half) / (n_sub - h), t_full / n_sub * 0.5)
+    a = max(t_full - b * n_sub, 0.0)
+    per_iter = a + b * xy.shape[0]
+    return {"value": 1.0 / per_iter, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"FP64 oracle LM steps on {h} and {n_sub} of {xy.shape[0]} samples "
+                       f"({t_half:.2f} s, {t_full:.2f} s); per-iteration time a + b S with "
+                       f"a = {a:.2f} s, b = {b * 1e3:.3f} ms/sample"),
+            "ms_per_step": per_iter * 1e3}
+
+
+def cpu_baseline(sc, xy, target, n_sub: int) -> dict:
+    r = oracle_rate(sc, xy, target, n_sub, steps=1)
+    r.pop("ms_per_step")
+    return r
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sc, xy, target = make_inputs(0)
+    r = oracle_rate(sc, xy, target, args.cpu_samples, steps=args.steps, warmup=args.warmup)
+    v = r["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(sc)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    import paper_2602_05492_gb300 as bg
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc, xy, target = make_inputs(rank)
+    if args.samples:                     # profiling aid: leading part of the workload
+        xy, target = xy[:args.samples].copy(), target[:args.samples].copy()
+    n = xy.shape[0]
+    m = bg.BEM(precision=bg.BEM_MIXED, device=local)
+    xt = torch.from_numpy(xy).to(dev)
+    tt = torch.from_numpy(target).to(dev)
+    m.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, np.zeros(3))
+    mean = m.sample_mean(tt)
+    m.set_mean_color(mean)
+    m.factor()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    lam = [1e-3]
+
+    def step():
+        r = m.lm_step(xt, tt, lam)
+        lam[0] = r["lambda_next"]
+        return r
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = m.launch_count()
+    m.profile(True)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                              # evict L2 between steps
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    prof = m.profile_read()
+    m.profile(False)
+    launches = m.launch_count() - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        tt_ = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt_, op=dist.ReduceOp.MAX)
+        total_ms = float(tt_.item())
+        dist.barrier()
+    value = world * args.steps / (total_ms / 1e3)
+
+    if rank != 0:
+        return
+    # ---- per-kernel live timing -> roofline of the dominant kernel
+    P, Nb, nc = sc.n_panels, 1024, 16 * sc.n_curves
+    top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else (None, (0.0, 0))
+    top_name, (top_ms, top_cnt) = top
+    work, kind = kernel_work(top_name, n, P, Nb, nc)
+    roof = None
+    if work is not None and top_cnt:
+        per_launch_s = top_ms / top_cnt / 1e3
+        ach = work / per_launch_s / 1e12
+        roof = {"bound": kind, "kernel": top_name, "achieved": ach,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "FP32 FMA lanes x max SM clock (derived)"}
+    elif top_name is not None:
+        roof = {"bound": "fp64", "kernel": top_name, "achieved": None, "peak": None,
+                "unit": "TFLOP/s", "frac": None, "traffic": None}
+    kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
+                   "share": v[0] / total_ms} for k, v in sorted(prof.items())}
+
+    # ---- sample x panel throughput, forward and adjoint, measured separately
+    out = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    res = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    m.loss(xt, tt, res)
+    reps = 3
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * reps)]
+    fwd_ms = adj_ms = 0.0
+    for r in range(reps):
+        flush.zero_()
+        ev[4 * r].record(stream)
+        m.eval(xt, out)
+        ev[4 * r + 1].record(stream)
+        flush.zero_()
+        ev[4 * r + 2].record(stream)
+        g = m.vjp(xt, res)
+        ev[4 * r + 3].record(stream)
+    torch.cuda.synchronize()
+    for r in range(reps):
+        fwd_ms += ev[4 * r].elapsed_time(ev[4 * r + 1]) / reps
+        adj_ms += ev[4 * r + 2].elapsed_time(ev[4 * r + 3]) / reps
+    pairs = n * (P + Nb)
+    pairs_per_s = 2 * pairs / ((fwd_ms + adj_ms) / 1e3)
+
+    # ---- FP64 GPU path: one LM iteration (after one warm-up iteration)
+    fp64 = None
+    if args.fp64_steps > 0:
+        m64 = bg.BEM(precision=bg.BEM_FP64, device=local)
+        x64, t64 = xt.double(), tt.double()
+        m64.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, mean)
+        m64.factor()
+        u64 = m64.eval(x64)
+        m.set_params(sc.theta_init)
+        u32 = m.eval(xt, out).double()
+        rmse = float(torch.sqrt(torch.mean((u32 - u64) ** 2)).item())
+        r64 = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        m64.loss(x64, t64, r64)
+        g64 = m64.vjp(x64, r64)
+        m.loss(xt, tt, res)
+        g32 = m.vjp(xt, res)
+        gerr = float((torch.linalg.norm(g32 - g64) / torch.linalg.norm(g64)).item())
+        lam64 = [1e-3]
+        m64.lm_step(x64, t64, lam64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t64_ms = 0.0
+        for _ in range(args.fp64_steps):
+            m64.set_params(sc.theta_init)
+            flush.zero_()
+            e0.record(stream)
+            m64.lm_step(x64, t64, [1e-3])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64_ms += e0.elapsed_time(e1) / args.fp64_steps
+        fp64 = {"lm_iters_per_s": 1e3 / t64_ms, "ms_per_iter": t64_ms,
+                "mixed_over_fp64": (value / world) / (1e3 / t64_ms),
+                "timed": f"{args.fp64_steps} full FP64 LM iteration(s) after one warm-up"}
+        accuracy = {"colour_rmse_mixed_vs_fp64_gpu": rmse, "grad_rel_err_mixed_vs_fp64_gpu": gerr,
+                    "at": "theta_init, all samples"}
+        m64.close()
+    else:
+        accuracy = None
+
+    # ---- end to end through the public API with host buffers
+    xy_h = torch.from_numpy(xy).pin_memory()
+    t_h = torch.from_numpy(target).pin_memory()
+    xe = torch.empty_like(xt)
+    te = torch.empty_like(tt)
+    m.set_params(sc.theta_init)
+    lam_e = [1e-3]
+    torch.cuda.synchronize()
+    e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        xe.copy_(xy_h, non_blocking=True)
+        te.copy_(t_h, non_blocking=True)
+        r = m.lm_step(xe, te, lam_e)          # returns losses to the host
+        lam_e[0] = r["lambda_next"]
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e_steps
+    e2e = {"value": 1.0 / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(xy.nbytes + target.nbytes),
+           "d2h_bytes_per_step": 8 * 3}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc, xy, target, n_sub=args.cpu_samples)
+        cpu.pop("seconds_per_sample_step", None)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(sc), "precision": "mixed (f32 pairs, f64 near "
+                       "field and refined solves)", "lm_trials_per_step": 1,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "wall_s_timed_region": t_wall},
+            "pairs_per_s": {"value": pairs_per_s, "unit": "sample x panel evals/s (fwd+adjoint)",
+                            "fwd_ms": fwd_ms, "adj_ms": adj_ms, "pairs_per_pass": pairs},
+            "fp64_gpu": fp64, "accuracy": accuracy, "kernels": kernels,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--cpu-samples", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--samples", type=int, default=0,
+                    help="profiling aid: time only the first N samples of the workload")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        tdist.init_process_group(backend=backend)
+        dist = tdist
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

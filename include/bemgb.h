@@ -183,6 +183,19 @@ int bem_boundary_values(bem_ctx *ctx, double *ub_out, void *stream);
 /* Number of this library's kernels launched by the context so far. */
 int64_t bem_launch_count(const bem_ctx *ctx);
 
+/* Per-kernel timing (tracing support; no counterpart in the paper).  While
+ * enabled, every hot kernel launch (field evaluation, adjoint, J rows, J^T J
+ * products, LM solve) is bracketed by CUDA events recorded on the stream it
+ * is launched on.  Enabling or disabling clears the totals. */
+int bem_profile_enable(bem_ctx *ctx, int on);
+
+/* Resolve the recorded events (synchronises them) and copy up to
+ * max_entries totals: names (host char[max_entries][32], NUL-terminated),
+ * total_ms (host double[]), counts (host int64[]; any of the three may be
+ * NULL); *n_entries receives the number written. */
+int bem_profile_read(bem_ctx *ctx, int max_entries, char *names, double *total_ms,
+                     int64_t *counts, int *n_entries);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,9 @@ def _load():
         "bem_sizes": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]),
         "bem_boundary_values": (ci, [vp, dp, vp]),
         "bem_launch_count": (i64, [vp]),
+        "bem_profile_enable": (ci, [vp, ci]),
+        "bem_profile_read": (ci, [vp, ci, ctypes.c_char_p, dp, ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ci)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -87,7 +90,7 @@ EXPORTED = [
     "bem_default_opts", "bem_create", "bem_destroy", "bem_last_error", "bem_setup", "bem_factor",
     "bem_set_params", "bem_get_params", "bem_set_mean_color", "bem_sample_mean", "bem_eval",
     "bem_loss", "bem_vjp", "bem_jtj", "lm_step", "bem_sizes", "bem_boundary_values",
-    "bem_launch_count",
+    "bem_launch_count", "bem_profile_enable", "bem_profile_read",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -249,3 +252,22 @@ class BEM:
 
     def launch_count(self) -> int:
         return int(_lib.bem_launch_count(self.h))
+
+    def profile(self, on: bool = True):
+        self._check(_lib.bem_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} recorded since profile(True)."""
+        mx = 64
+        names = ctypes.create_string_buffer(32 * mx)
+        ms = np.zeros(mx)
+        cnt = np.zeros(mx, np.int64)
+        n = ctypes.c_int()
+        self._check(_lib.bem_profile_read(self.h, mx, names, _dp(ms),
+                                          cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                          ctypes.byref(n)))
+        out = {}
+        for k in range(n.value):
+            nm = names.raw[32 * k:32 * k + 32].split(b"\0", 1)[0].decode()
+            out[nm] = (float(ms[k]), int(cnt[k]))
+        return out

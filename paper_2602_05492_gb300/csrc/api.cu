@@ -68,6 +68,43 @@ static int need_ready(bem_ctx* c) {
   return BEM_OK;
 }
 
+static cudaEvent_t prof_event(bem_ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(bem_ctx* ctx, const char* name) : c(ctx) {
+  if (!c->prof) return;
+  bem_ctx::ProfRec r{name, prof_event(c), prof_event(c)};
+  cudaEventRecord(r.a, S(c));
+  c->prof_pending.push_back(r);
+  idx = (int)c->prof_pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (idx >= 0) cudaEventRecord(c->prof_pending[idx].b, S(c));
+}
+
+static void prof_resolve(bem_ctx* c) {
+  for (auto& r : c->prof_pending) {
+    cudaEventSynchronize(r.b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto& t = c->prof_tot[r.name];
+    t.first += ms;
+    t.second += 1;
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_pending.clear();
+}
+
 // out = a + b
 __global__ void k_axpy(const double* __restrict__ a, const double* __restrict__ b, int n,
                        double* __restrict__ out) {
@@ -166,6 +203,8 @@ void bem_destroy(bem_ctx* c) {
                   c->sc.d_closed};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  prof_resolve(c);
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   DevBuf* bufs[] = {&c->part, &c->part2, &c->loss, &c->gpart, &c->jrow, &c->phi, &c->Hc, &c->Mc,
                     &c->Dfc, &c->Fg, &c->lmK, &c->lmL, &c->lmLt, &c->lmW, &c->H, &c->g};
   for (DevBuf* b : bufs) free_buf(*b);
@@ -426,5 +465,34 @@ int bem_boundary_values(bem_ctx* c, double* ub, void* stream) {
 }
 
 int64_t bem_launch_count(const bem_ctx* c) { return c ? c->launches : 0; }
+
+int bem_profile_enable(bem_ctx* c, int on) {
+  if (!c) return BEM_EINVAL;
+  if (set_device(c)) return BEM_ECUDA;
+  prof_resolve(c);
+  c->prof_tot.clear();
+  c->prof = on != 0;
+  return BEM_OK;
+}
+
+int bem_profile_read(bem_ctx* c, int max_entries, char* names, double* total_ms, int64_t* counts,
+                     int* n_entries) {
+  if (!c || max_entries < 0 || !n_entries) return c ? fail(c, BEM_EINVAL, "bad arguments") : BEM_EINVAL;
+  if (set_device(c)) return BEM_ECUDA;
+  prof_resolve(c);
+  int k = 0;
+  for (auto& kv : c->prof_tot) {
+    if (k >= max_entries) break;
+    if (names) {
+      strncpy(names + 32 * k, kv.first.c_str(), 31);
+      names[32 * k + 31] = 0;
+    }
+    if (total_ms) total_ms[k] = kv.second.first;
+    if (counts) counts[k] = kv.second.second;
+    ++k;
+  }
+  *n_entries = k;
+  return BEM_OK;
+}
 
 }  // extern "C"

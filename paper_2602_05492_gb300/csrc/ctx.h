@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -75,6 +76,13 @@ struct bem_ctx {
   double* d_scal = nullptr;        // small device scalars (loss, sums)
   int* d_status = nullptr;         // device error word (0 = fine)
 
+  // per-kernel event timing (bem_profile_enable)
+  bool prof = false;
+  struct ProfRec { std::string name; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  std::map<std::string, std::pair<double, int64_t>> prof_tot;
+
   // growable scratch
   bem::DevBuf part, part2, loss, gpart, jrow, phi, Hc, Mc, Dfc, Fg, lmK, lmL, lmLt, lmW, H, g;
 };
@@ -121,6 +129,14 @@ int adj_vjp(bem_ctx* c, int64_t n, const void* xy, const void* resid, double* gr
 
 // ---- Gauss-Newton matrix (k_jtj.cu) ----------------------------------------------
 int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H);
+
+// Brackets the kernel launches of its lifetime with events when profiling.
+struct ProfScope {
+  bem_ctx* c;
+  int idx = -1;
+  ProfScope(bem_ctx* ctx, const char* name);
+  ~ProfScope();
+};
 
 }  // namespace bem
 

@@ -255,6 +255,7 @@ static int vjp_pass(bem_ctx* c, int64_t n, const T* xy, const T* w, bool boundar
   a.qpart = (double*)((char*)c->part.p + pbytes);
   if (n > 0) {
     dim3 grid(tiles, slices);
+    ProfScope _ps(c, Nb > 0 ? "k_vjp" : "k_vjp_gauss");
     bool same = c->opts.eps_c == c->opts.eps_d;
     bool near = sizeof(T) == 4 && c->opts.near_factor > 0;
     if (same) {

@@ -234,6 +234,7 @@ static FieldArgs<T> make_args(bem_ctx* c) {
 
 template <typename T>
 static void launch_field(bem_ctx* c, const FieldArgs<T>& a, dim3 grid) {
+  ProfScope _ps(c, a.split_out ? "k_field_rhs" : "k_field");
   bool same = c->opts.eps_c == c->opts.eps_d;
   bool near = sizeof(T) == 4 && c->opts.near_factor > 0;
   if (same) {

@@ -137,6 +137,7 @@ static void launch_frows(bem_ctx* c, const T* xy, int ns, double* F) {
   const Panel<T>* pan =
       (const Panel<T>*)(sizeof(T) == 8 ? (const void*)c->d_pan64 : (const void*)c->d_pan32);
   T ec2 = T(c->opts.eps_c * c->opts.eps_c), ed2 = T(c->opts.eps_d * c->opts.eps_d);
+  ProfScope _ps(c, "k_frows");
   if (c->opts.eps_c == c->opts.eps_d)
     k_frows<T, true><<<grid, 128, 0, S(c)>>>(xy, ns, pan, c->sc.d_off, c->sc.d_K, c->sc.d_closed,
                                              C, ec2, ed2, F);
@@ -180,10 +181,14 @@ static int jtj_t(bem_ctx* c, int64_t n, const T* xy, double* Hout) {
     return rc;
   for (int64_t s0 = 0; s0 < n; s0 += ns) {
     int m = (int)std::min<int64_t>(ns, n - s0);
-    k_phi_rows<T><<<(unsigned)(((int64_t)m * Nb + 255) / 256), 256, 0, S(c)>>>(xy + 2 * s0, m,
-                                                                                  vert, Nb, phi);
-    BEM_LAUNCHED(c);
+    {
+      ProfScope _pp(c, "k_phi_rows");
+      k_phi_rows<T><<<(unsigned)(((int64_t)m * Nb + 255) / 256), 256, 0, S(c)>>>(xy + 2 * s0, m,
+                                                                                    vert, Nb, phi);
+      BEM_LAUNCHED(c);
+    }
     launch_frows<T>(c, xy + 2 * s0, m, F);
+    ProfScope _pg(c, "jtj_gemm");
     for (int ch = 0; ch < 3; ++ch) {
       double* Fc = F + (size_t)ch * m * nc;
       la_dgemm(c, false, false, m, nc, Nb, 1.0, phi, Nb, Mc + (size_t)ch * Nb * nc, nc, 1.0, Fc,

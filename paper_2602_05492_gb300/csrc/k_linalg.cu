@@ -558,6 +558,7 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
   double* mx = cons + 4 * (size_t)n;
   double* gn = mx + 1;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
+  ProfScope _ps(c, "lm_solve");
   k_diag_max<<<1, 1024, 0, S(c)>>>(H, n, mx);
   dim3 grid((n + 127) / 128, n);
   k_lm_build<<<grid, 128, 0, S(c)>>>(H, g, n, c->sc.C, c->sc.d_closed, c->d_compat, mx, lam, Km, R);
