@@ -173,6 +173,16 @@ int bem_jtj(bem_ctx *ctx, int64_t n, const void *xy, double *H_out, void *stream
 int lm_step(bem_ctx *ctx, int64_t n, const void *xy, const void *target,
             int n_trials, const double *lambdas, lm_result *out, void *stream);
 
+/* D[M][N] = A[M][K] B[N][K]^T on the tensor cores (tcgen05, fp32
+ * accumulate): the contraction behind bem_jtj in BEM_MIXED contexts with
+ * BEM_JTJ_BF16, exposed for validation.  A, B: device bf16, row-major, row
+ * strides lda, ldb in elements (multiples of 8, 16-byte aligned bases);
+ * D: device fp32 row-major, stride ldd.  M, N, K >= 1.  Errors: BEM_EINVAL
+ * for bad sizes or alignment, BEM_ETIMEDOUT if a bounded device wait ran
+ * out (synchronises `stream`). */
+int bem_gemm_bf16(bem_ctx *ctx, int M, int N, int K, const void *A, int lda, const void *B,
+                  int ldb, float *D, int ldd, void *stream);
+
 /* Sizes of the current scene (host ints; any pointer may be NULL). */
 int bem_sizes(const bem_ctx *ctx, int *n_theta, int *n_panels, int *n_boundary);
 

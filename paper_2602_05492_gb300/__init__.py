@@ -75,6 +75,7 @@ def _load():
         "bem_boundary_values": (ci, [vp, dp, vp]),
         "bem_launch_count": (i64, [vp]),
         "bem_profile_enable": (ci, [vp, ci]),
+        "bem_gemm_bf16": (ci, [vp, ci, ci, ci, vp, ci, vp, ci, vp, ci, vp]),
         "bem_profile_read": (ci, [vp, ci, ctypes.c_char_p, dp, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ci)]),
     }
@@ -90,7 +91,7 @@ EXPORTED = [
     "bem_default_opts", "bem_create", "bem_destroy", "bem_last_error", "bem_setup", "bem_factor",
     "bem_set_params", "bem_get_params", "bem_set_mean_color", "bem_sample_mean", "bem_eval",
     "bem_loss", "bem_vjp", "bem_jtj", "lm_step", "bem_sizes", "bem_boundary_values",
-    "bem_launch_count", "bem_profile_enable", "bem_profile_read",
+    "bem_launch_count", "bem_profile_enable", "bem_profile_read", "bem_gemm_bf16",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -252,6 +253,17 @@ class BEM:
 
     def launch_count(self) -> int:
         return int(_lib.bem_launch_count(self.h))
+
+    def gemm_bf16(self, A, B, stream=None):
+        """D = A B^T on the tensor cores (A [M][K], B [N][K] bf16 CUDA tensors)."""
+        import torch
+        assert A.dtype == B.dtype == torch.bfloat16 and A.is_cuda and B.is_cuda
+        M, K = A.shape
+        N = B.shape[0]
+        D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+        self._check(_lib.bem_gemm_bf16(self.h, M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0),
+                                       _ptr(D), N, _stream(stream)))
+        return D
 
     def profile(self, on: bool = True):
         self._check(_lib.bem_profile_enable(self.h, 1 if on else 0))

@@ -206,7 +206,8 @@ void bem_destroy(bem_ctx* c) {
   prof_resolve(c);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   DevBuf* bufs[] = {&c->part, &c->part2, &c->loss, &c->gpart, &c->jrow, &c->phi, &c->Hc, &c->Mc,
-                    &c->Dfc, &c->Fg, &c->lmK, &c->lmL, &c->lmLt, &c->lmW, &c->H, &c->g};
+                    &c->Dfc, &c->Fg, &c->lmK, &c->lmL, &c->lmLt, &c->lmW, &c->H, &c->g,
+                    &c->tcJ, &c->tcPart, &c->tcMt};
   for (DevBuf* b : bufs) free_buf(*b);
   delete c;
 }
@@ -443,6 +444,25 @@ int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_tri
   // leave panels and boundary solution consistent with the kept theta
   if ((rc = refresh(c, c->d_theta))) return rc;
   return cuda_check(c, cudaStreamSynchronize(S(c)), "sync");
+}
+
+int bem_gemm_bf16(bem_ctx* c, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                  float* D, int ldd, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !D || lda < K || ldb < K || ldd < N || lda % 8 ||
+      ldb % 8)
+    return fail(c, BEM_EINVAL, "bem_gemm_bf16: bad sizes or strides");
+  int rc;
+  if ((rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
+  if ((rc = tc_gemm_store(c, M, N, K, A, lda, B, ldb, D, ldd))) return rc;
+  int st = 0;
+  if ((rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, S(c)), "status")) ||
+      (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "sync")))
+    return rc;
+  if (st) return fail(c, BEM_ETIMEDOUT, "tensor-core GEMM: a bounded device wait ran out");
+  return BEM_OK;
 }
 
 int bem_sizes(const bem_ctx* c, int* n_theta, int* n_panels, int* n_boundary) {

@@ -84,7 +84,8 @@ struct bem_ctx {
   std::map<std::string, std::pair<double, int64_t>> prof_tot;
 
   // growable scratch
-  bem::DevBuf part, part2, loss, gpart, jrow, phi, Hc, Mc, Dfc, Fg, lmK, lmL, lmLt, lmW, H, g;
+  bem::DevBuf part, part2, loss, gpart, jrow, phi, Hc, Mc, Dfc, Fg, lmK, lmL, lmLt, lmW, H, g,
+      tcJ, tcPart, tcMt;
 };
 
 namespace bem {
@@ -129,6 +130,14 @@ int adj_vjp(bem_ctx* c, int64_t n, const void* xy, const void* resid, double* gr
 
 // ---- Gauss-Newton matrix (k_jtj.cu) ----------------------------------------------
 int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H);
+
+// ---- tensor-core contractions (k_gemm_tc.cu) ----------------------------------------
+int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                  float* D, int ldd);
+int tc_jrows(bem_ctx* c, int rows, int m, int Nb, const void* Mt, int ldm, const void* Phi,
+             int ldp, const float* F, int ldf, void* J, int ldj);
+int tc_syrk(bem_ctx* c, int nc, int m, const void* J, int ldj, float* part, int splits);
+int tc_syrk_splits(int nc);
 
 // Brackets the kernel launches of its lifetime with events when profiling.
 struct ProfScope {

@@ -11,6 +11,8 @@
 // Samples are processed in chunks; J rows exist only for the current chunk.
 // Column order inside a channel: position x, y of control handle h at 2h, 2h+1;
 // w_d,c of h at 8C + h; w_c,c of h at 12C + h.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -29,12 +31,13 @@ __global__ void k_phi_rows(const T* __restrict__ xy, int ns, const T* __restrict
   phi[(size_t)s * Nb + j] = double(a) * kInv2Pi;
 }
 
-// F rows of ns points for one curve per blockIdx.y: out F[c][s][nc].
-template <typename T, bool SAME>
+// F rows of ns points for one curve per blockIdx.y.  TR = false: double
+// F[c][s][nc]; TR = true: float F^T[c*nc + col][s] with row stride ldf.
+template <typename T, bool SAME, bool TR>
 __global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __restrict__ pan,
                         const int* __restrict__ off, const int* __restrict__ Kc,
                         const uint8_t* __restrict__ closed, int C, T ec2, T ed2,
-                        double* __restrict__ F) {
+                        void* __restrict__ Fout, int ldf) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y;
   if (s >= ns) return;
@@ -81,6 +84,23 @@ __global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __rest
 #pragma unroll
       for (int c = 0; c < 3; ++c) { pos[0][e][c] += pos[3][e][c]; pos[3][e][c] = 0; }
   }
+  if (TR) {
+    float* F = (float*)Fout;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float* base = F + (size_t)c * nc * ldf + s;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int h = 4 * i + j;
+        base[(size_t)(2 * h) * ldf] = float(pos[j][0][c]);
+        base[(size_t)(2 * h + 1) * ldf] = float(pos[j][1][c]);
+        base[(size_t)(8 * C + h) * ldf] = float(cd[j]);
+        base[(size_t)(12 * C + h) * ldf] = float(cs[j]);
+      }
+    }
+    return;
+  }
+  double* F = (double*)Fout;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     double* row = F + ((size_t)c * ns + s) * nc;
@@ -93,6 +113,44 @@ __global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __rest
       row[12 * C + h] = double(cs[j]);
     }
   }
+}
+
+// bf16 rows phi_j(x_s)/(2 pi): Phi[s][j], row stride Nb
+__global__ void k_phi_rows_bf16(const float* __restrict__ xy, int ns, const float* __restrict__ vert,
+                                int Nb, __nv_bfloat16* __restrict__ phi) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ns * Nb) return;
+  int s = (int)(t / Nb), j = (int)(t % Nb);
+  float a = seg_angle(vert[2 * j], vert[2 * j + 1], vert[2 * j + 2], vert[2 * j + 3], xy[2 * s],
+                      xy[2 * s + 1]);
+  phi[t] = __float2bfloat16_rn(a * float(kInv2Pi));
+}
+
+// Mt[c*nc + col][j] = bf16(Mc[c][j][col])
+__global__ void k_mt_bf16(const double* __restrict__ Mc, int Nb, int nc,
+                          __nv_bfloat16* __restrict__ Mt) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = blockIdx.y;             // c*nc + col
+  if (j >= Nb) return;
+  int c = row / nc, col = row % nc;
+  Mt[(size_t)row * Nb + j] = __float2bfloat16_rn((float)Mc[((size_t)c * Nb + j) * nc + col]);
+}
+
+// Hc[c][i][j] = sum over splits of part[split][c][i][j] (upper blocks) in
+// fixed order, mirrored to the lower triangle
+__global__ void k_syrk_reduce(const float* __restrict__ part, int splits, int nc,
+                              double* __restrict__ Hc) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y, c = blockIdx.z;
+  if (j >= nc) return;
+  int a = min(i, j), b = max(i, j);
+  // a block (ti, tj) with ti <= tj holds entry (a, b) when a's tile <= b's tile
+  size_t off = ((size_t)c * nc + a) * nc + b;
+  if ((a / 128) > (b / 128)) off = ((size_t)c * nc + b) * nc + a;
+  double s = 0;
+  size_t stride = (size_t)3 * nc * nc;
+  for (int k = 0; k < splits; ++k) s += (double)part[k * stride + off];
+  Hc[((size_t)c * nc + i) * nc + j] = s;
 }
 
 // Df[c][i][col] = |G_i| sum_k w_k Fg[c][3i+k][col]
@@ -130,8 +188,8 @@ __global__ void k_h_assemble(const double* __restrict__ Hc, int C, double scale,
   H[(size_t)a * nth + b] = scale * s;
 }
 
-template <typename T>
-static void launch_frows(bem_ctx* c, const T* xy, int ns, double* F) {
+template <typename T, bool TR = false>
+static void launch_frows(bem_ctx* c, const T* xy, int ns, void* F, int ldf = 0) {
   int C = c->sc.C;
   dim3 grid((ns + 127) / 128, C);
   const Panel<T>* pan =
@@ -139,11 +197,11 @@ static void launch_frows(bem_ctx* c, const T* xy, int ns, double* F) {
   T ec2 = T(c->opts.eps_c * c->opts.eps_c), ed2 = T(c->opts.eps_d * c->opts.eps_d);
   ProfScope _ps(c, "k_frows");
   if (c->opts.eps_c == c->opts.eps_d)
-    k_frows<T, true><<<grid, 128, 0, S(c)>>>(xy, ns, pan, c->sc.d_off, c->sc.d_K, c->sc.d_closed,
-                                             C, ec2, ed2, F);
+    k_frows<T, true, TR><<<grid, 128, 0, S(c)>>>(xy, ns, pan, c->sc.d_off, c->sc.d_K,
+                                                 c->sc.d_closed, C, ec2, ed2, F, ldf);
   else
-    k_frows<T, false><<<grid, 128, 0, S(c)>>>(xy, ns, pan, c->sc.d_off, c->sc.d_K, c->sc.d_closed,
-                                              C, ec2, ed2, F);
+    k_frows<T, false, TR><<<grid, 128, 0, S(c)>>>(xy, ns, pan, c->sc.d_off, c->sc.d_K,
+                                                  c->sc.d_closed, C, ec2, ed2, F, ldf);
   BEM_LAUNCHED(c);
 }
 
@@ -202,8 +260,85 @@ static int jtj_t(bem_ctx* c, int64_t n, const T* xy, double* Hout) {
   return cuda_check(c, cudaGetLastError(), "jtj");
 }
 
+// Stacked right-hand sides M_c = A^+ df_b,c/dtheta in double (shared by both paths).
+template <typename T>
+static int jtj_stacked_rhs(bem_ctx* c) {
+  int rc;
+  int C = c->sc.C, nc = 16 * C, Nb = c->bd.Nb, n3 = 3 * Nb;
+  if ((rc = grow(c, c->Fg, sizeof(double) * 3 * (size_t)n3 * nc))) return rc;
+  if ((rc = grow(c, c->Dfc, sizeof(double) * 3 * (size_t)Nb * nc))) return rc;
+  if ((rc = grow(c, c->Mc, sizeof(double) * 3 * (size_t)Nb * nc))) return rc;
+  const T* gp = (const T*)(sizeof(T) == 8 ? (const void*)c->bd.d_gp : (const void*)c->bd.d_gp32);
+  launch_frows<T>(c, gp, n3, c->Fg.p);
+  k_df_reduce<<<dim3((nc + 127) / 128, Nb, 3), 128, 0, S(c)>>>((const double*)c->Fg.p, Nb, nc,
+                                                                c->bd.d_vert, (double*)c->Dfc.p);
+  BEM_LAUNCHED(c);
+  double* Mc = (double*)c->Mc.p;
+  double* Df = (double*)c->Dfc.p;
+  for (int ch = 0; ch < 3; ++ch)
+    la_dgemm(c, false, false, Nb, nc, Nb, 1.0, c->bd.d_W, Nb, Df + (size_t)ch * Nb * nc, nc, 0.0,
+             Mc + (size_t)ch * Nb * nc, nc);
+  return cuda_check(c, cudaGetLastError(), "stacked rhs");
+}
+
+// Mixed precision: J^T rows on the tensor cores in bf16 (fp32 accumulate),
+// Gram blocks accumulated per K slice in fp32, slices summed in double.
+static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout) {
+  int rc;
+  int C = c->sc.C, nc = 16 * C, Nb = c->bd.Nb, nth = c->sc.nth;
+  if ((rc = jtj_stacked_rhs<float>(c))) return rc;
+  // M_c^T in bf16, [3 nc][Nb]
+  if ((rc = grow(c, c->tcMt, sizeof(__nv_bfloat16) * 3 * (size_t)nc * Nb))) return rc;
+  k_mt_bf16<<<dim3((Nb + 127) / 128, 3 * nc), 128, 0, S(c)>>>((const double*)c->Mc.p, Nb, nc,
+                                                               (__nv_bfloat16*)c->tcMt.p);
+  BEM_LAUNCHED(c);
+  // per-chunk buffers: Phi bf16 [m][Nb], F^T f32 [3nc][ld], J^T bf16 [3nc][ld]
+  const int64_t chunk = std::min<int64_t>(std::max<int64_t>(n, 1), 262144);
+  const int ld = (int)((chunk + 63) / 64 * 64);
+  const size_t phi_b = sizeof(__nv_bfloat16) * (size_t)chunk * Nb;
+  const size_t f_b = sizeof(float) * 3 * (size_t)nc * ld;
+  const size_t j_b = sizeof(__nv_bfloat16) * 3 * (size_t)nc * ld;
+  if ((rc = grow(c, c->jrow, phi_b + 256 + f_b + 256))) return rc;
+  if ((rc = grow(c, c->tcJ, j_b))) return rc;
+  const int splits = tc_syrk_splits(nc);
+  const size_t part_b = sizeof(float) * (size_t)splits * 3 * nc * nc;
+  if ((rc = grow(c, c->tcPart, part_b))) return rc;
+  if ((rc = grow(c, c->Hc, sizeof(double) * 3 * (size_t)nc * nc))) return rc;
+  __nv_bfloat16* phi = (__nv_bfloat16*)c->jrow.p;
+  float* F = (float*)((char*)c->jrow.p + (phi_b + 255) / 256 * 256);
+  float* part = (float*)c->tcPart.p;
+  if ((rc = cuda_check(c, cudaMemsetAsync(part, 0, part_b, S(c)), "memset"))) return rc;
+  if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
+  for (int64_t s0 = 0; s0 < n; s0 += chunk) {
+    const int m = (int)std::min<int64_t>(chunk, n - s0);
+    {
+      ProfScope _pp(c, "k_phi_rows");
+      k_phi_rows_bf16<<<(unsigned)(((int64_t)m * Nb + 255) / 256), 256, 0, S(c)>>>(
+          xy + 2 * s0, m, c->bd.d_vert32, Nb, phi);
+      BEM_LAUNCHED(c);
+    }
+    launch_frows<float, true>(c, xy + 2 * s0, m, F, ld);
+    if ((rc = tc_jrows(c, 3 * nc, m, Nb, c->tcMt.p, Nb, phi, Nb, F, ld, c->tcJ.p, ld))) return rc;
+    if ((rc = tc_syrk(c, nc, m, c->tcJ.p, ld, part, splits))) return rc;
+  }
+  k_syrk_reduce<<<dim3((nc + 127) / 128, nc, 3), 128, 0, S(c)>>>(part, splits, nc,
+                                                                  (double*)c->Hc.p);
+  k_h_assemble<<<dim3((nth + 127) / 128, nth), 128, 0, S(c)>>>((const double*)c->Hc.p, C,
+                                                                n > 0 ? 1.0 / double(n) : 0.0, Hout);
+  c->launches += 2;
+  if ((rc = cuda_check(c, cudaGetLastError(), "jtj tc"))) return rc;
+  int st = 0;
+  if ((rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                                          S(c)), "status")) ||
+      (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "sync")))
+    return rc;
+  if (st) return fail(c, BEM_ETIMEDOUT, "tensor-core J^T J: a bounded device wait ran out");
+  return BEM_OK;
+}
+
 int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H) {
   if (c->opts.precision == BEM_FP64) return jtj_t<double>(c, n, (const double*)xy, H);
+  if (c->opts.jtj_mode == BEM_JTJ_BF16) return jtj_tc(c, n, (const float*)xy, H);
   return jtj_t<float>(c, n, (const float*)xy, H);
 }
 

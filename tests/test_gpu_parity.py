@@ -269,3 +269,22 @@ def test_sample_mean(cfg1):
     m = _ctx(sc, mean, _bg().BEM_FP64)
     got = m.sample_mean(_t(target, torch.float64))
     np.testing.assert_allclose(got, mean, rtol=1e-13)
+
+
+# ---- tensor-core contraction --------------------------------------------------------
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 1024), (192, 300, 200),
+                                   (64, 1000, 2048)])
+def test_tensor_core_gemm(M, N, K):
+    bg = _bg()
+    m = bg.BEM(precision=bg.BEM_MIXED)
+    g = torch.Generator(device="cuda:0").manual_seed(M * 7 + N)
+    Kp = (K + 7) // 8 * 8
+    A = torch.zeros((M, Kp), dtype=torch.bfloat16, device="cuda:0")
+    B = torch.zeros((N, Kp), dtype=torch.bfloat16, device="cuda:0")
+    A[:, :K] = torch.randn((M, K), generator=g, device="cuda:0").bfloat16()
+    B[:, :K] = torch.randn((N, K), generator=g, device="cuda:0").bfloat16()
+    D = m.gemm_bf16(A[:, :K] if Kp == K else A, B[:, :K] if Kp == K else B)
+    want = A.double() @ B.double().T
+    err = (D.double() - want).abs().max().item() / want.abs().max().item()
+    assert err < 1e-5, err
