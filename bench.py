@@ -206,7 +206,8 @@ def run_ours(args, rank, world, dist):
     if args.samples:                     # profiling aid: leading part of the workload
         xy, target = xy[:args.samples].copy(), target[:args.samples].copy()
     n = xy.shape[0]
-    m = bg.BEM(precision=bg.BEM_MIXED, device=local)
+    jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32}[args.jtj]
+    m = bg.BEM(precision=bg.BEM_MIXED, device=local, jtj_mode=jm)
     xt = torch.from_numpy(xy).to(dev)
     tt = torch.from_numpy(target).to(dev)
     m.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, np.zeros(3))
@@ -368,7 +369,7 @@ def run_ours(args, rank, world, dist):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": workload_desc(sc), "precision": "mixed (f32 pairs, f64 near "
-                       "field and refined solves)", "lm_trials_per_step": 1,
+                       "field and refined solves)", "jtj": args.jtj, "lm_trials_per_step": 1,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "wall_s_timed_region": t_wall},
             "pairs_per_s": {"value": pairs_per_s, "unit": "sample x panel evals/s (fwd+adjoint)",
@@ -388,6 +389,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-samples", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--jtj", default="bf16", choices=["bf16", "3xtf32"],
+                    help="tensor-core scheme of the J^T J contraction")
     ap.add_argument("--samples", type=int, default=0,
                     help="profiling aid: time only the first N samples of the workload")
     args = ap.parse_args()

@@ -164,10 +164,13 @@ int bem_jtj(bem_ctx *ctx, int64_t n, const void *xy, double *H_out, void *stream
  *   (H + lambda D) delta = -g,  D = diag(H) (floored at 1e-12 max),
  * restricted to steps that keep the compatibility condition with endpoints
  * fixed (Sec. 4.3), re-project w_c with the new lengths, and evaluate the
- * loss on the same samples.  The trial with the lowest loss is taken if it
- * lowers the loss (theta updated in the context).  lambda_next: lambda/3
- * after an accepted single trial, 2 lambda after a rejected one; with
- * several trials the accepted lambda / 3, or 10 max(lambdas) if none helps.
+ * loss on the same samples.  H is positive semi-definite only up to
+ * rounding: if H + lambda D does not factor, that trial's lambda is raised
+ * tenfold until it does (at most 12 times).  The trial with the lowest loss
+ * is taken if it lowers the loss (theta updated in the context).
+ * lambda_next: the (raised) lambda / 3 after an accepted trial; after a
+ * rejected single trial 2 lambda, after several rejected trials 10 times the
+ * largest.
  *   xy, target: device (sample type); out: host.  Synchronises `stream`.
  * Errors: BEM_ENOTSPD if no trial matrix could be factored. */
 int lm_step(bem_ctx *ctx, int64_t n, const void *xy, const void *target,

@@ -401,8 +401,16 @@ class Oracle:
         ga = g[act]
         dg = np.diag(Ha).copy()
         D = np.maximum(dg, 1e-12 * dg.max())
-        Kmat = Ha + lam * np.diag(D)
-        cf = scipy.linalg.cho_factor(Kmat, lower=True)
+        # H is PSD only up to rounding: raise lambda tenfold until H + lam D factors
+        for attempt in range(13):
+            try:
+                cf = scipy.linalg.cho_factor(Ha + lam * np.diag(D), lower=True)
+                break
+            except np.linalg.LinAlgError:
+                if attempt == 12:
+                    raise
+                lam = 10.0 * lam if lam > 0 else 1e-9
+        self.last_lambda = lam
         Ac = self.constraint_matrix(theta)[act]
         y = scipy.linalg.cho_solve(cf, -ga)
         Z = scipy.linalg.cho_solve(cf, Ac)
@@ -416,6 +424,7 @@ class Oracle:
         """One LM iteration (Eq. optimstep) with the paper's two-stage projection."""
         L0, g, H = self.gauss_newton(theta, xy, target)
         delta = self.solve_step(theta, H, g, lam)
+        lam = self.last_lambda
         th_new = project_compat(self.geo, theta + delta)
         L1 = self.loss(th_new, xy, target)
         accept = L1 < L0

@@ -401,8 +401,17 @@ int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_tri
   double best = INFINITY;
   int best_t = -1;
   bool any_spd = false;
+  double used[64];
   for (int t = 0; t < n_trials; ++t) {
-    rc = la_lm_solve(c, (const double*)c->H.p, g, lambdas[t], c->d_delta);
+    // H is positive semi-definite only up to rounding; if H + lambda D does
+    // not factor, lambda is raised tenfold (at most 12 times) as LM does
+    double lam = lambdas[t];
+    for (int r = 0;; ++r) {
+      rc = la_lm_solve(c, (const double*)c->H.p, g, lam, c->d_delta);
+      if (rc != BEM_ENOTSPD || r == 12) break;
+      lam = lam > 0 ? 10.0 * lam : 1e-9;
+    }
+    used[t] = lam;
     if (rc == BEM_ENOTSPD) continue;
     if (rc) return rc;
     any_spd = true;
@@ -435,11 +444,11 @@ int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_tri
     if ((rc = cuda_check(c, cudaMemcpyAsync(c->d_theta, best_theta, 8 * (size_t)nth,
                                             cudaMemcpyDeviceToDevice, S(c)), "theta")))
       return rc;
-    out->lambda_next = lambdas[best_t] / 3.0;
+    out->lambda_next = used[best_t] / 3.0;
   } else {
     double mx = 0;
-    for (int t = 0; t < n_trials; ++t) mx = std::fmax(mx, lambdas[t]);
-    out->lambda_next = n_trials == 1 ? 2.0 * lambdas[0] : 10.0 * mx;
+    for (int t = 0; t < n_trials; ++t) mx = std::fmax(mx, used[t]);
+    out->lambda_next = n_trials == 1 ? 2.0 * used[0] : 10.0 * mx;
   }
   // leave panels and boundary solution consistent with the kept theta
   if ((rc = refresh(c, c->d_theta))) return rc;

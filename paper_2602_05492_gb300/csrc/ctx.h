@@ -134,10 +134,11 @@ int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H);
 // ---- tensor-core contractions (k_gemm_tc.cu) ----------------------------------------
 int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                   float* D, int ldd);
-int tc_jrows(bem_ctx* c, int rows, int m, int Nb, const void* Mt, int ldm, const void* Phi,
-             int ldp, const float* F, int ldf, void* J, int ldj);
-int tc_syrk(bem_ctx* c, int nc, int m, const void* J, int ldj, float* part, int splits);
-int tc_syrk_splits(int nc);
+int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt, int ldm,
+             const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj);
+int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, float* part,
+            int splits);
+int tc_syrk_splits(int nc, bool x3);
 
 // Brackets the kernel launches of its lifetime with events when profiling.
 struct ProfScope {

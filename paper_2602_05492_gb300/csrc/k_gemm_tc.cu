@@ -2,14 +2,21 @@
 //
 // Every product here has the form D[M][N] = sum_k A[m][k] B[n][k] with both
 // operands K-major in global memory (row-major, k contiguous).  One CTA of 4
-// warps computes one 128 x 128 tile: lane 0 of warp 0 streams 64-wide K slabs
-// of A and B into a 3-stage shared-memory ring with TMA (128-byte swizzle),
-// lane 0 of warp 1 issues tcgen05.mma (M = N = 128, K = 16 per instruction)
-// into a 128-column fp32 accumulator in TMEM and releases ring slots with
+// warps computes one 128 x 128 tile: lane 0 of warp 0 streams 128-byte-wide
+// K slabs of A and B into a 3-stage shared-memory ring with TMA (128-byte
+// swizzle), lane 0 of warp 1 issues tcgen05.mma (M = N = 128) into a
+// 128-column fp32 accumulator in TMEM and releases ring slots with
 // tcgen05.commit, and all four warps drain the accumulator (warp w owns TMEM
-// lanes 32w..32w+31) through the epilogue of the launch mode:
+// lanes 32w..32w+31) through the epilogue of the launch mode.
+// Two operand schemes:
+//   bf16   one kind::f16 product, 64-element slabs, K = 16 per instruction
+//   3xtf32 fp32 operands stored as tf32 hi + lo parts (x = hi + lo, both
+//          rounded to tf32); three kind::tf32 products hi.hi + hi.lo + lo.hi
+//          accumulate into the same TMEM tile (32-element slabs, K = 8)
+// Epilogues:
 //   EPI_STORE  D -> fp32 [M][N]
-//   EPI_JROWS  J^T = M_c^T Phi^T + F^T: D + F (fp32) -> bf16 [M][N]
+//   EPI_JROWS  J^T = M_c^T Phi^T + F^T: D + F (fp32) -> bf16 [M][N], or the
+//              tf32 hi/lo pair of D + F in the 3xtf32 scheme
 //   EPI_SYRK   one upper-triangular 128 x 128 block of J_c^T J_c over a K
 //              slice of samples, added to that slice's fp32 partial sum
 // Every wait is bounded (about one second); a timeout sets *err and the CTA
@@ -26,10 +33,20 @@ namespace bem {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int BM = 128, BN = 128;
 constexpr int STAGES = 3;
-constexpr int TILE_BYTES = BM * BK * 2;     // 16 KB per operand per stage
-constexpr int SMEM_BYTES = 1024 + STAGES * 2 * TILE_BYTES + 256;
+constexpr int TILE_BYTES = BM * 128;        // 16 KB: 128 rows x 128 bytes per operand part
+template <bool X3> struct Scheme {
+  static constexpr int BK = X3 ? 32 : 64;             // elements per 128-byte row
+  static constexpr int PARTS = X3 ? 4 : 2;            // A(hi, lo), B(hi, lo) / A, B
+  static constexpr int SMEM = 1024 + STAGES * PARTS * TILE_BYTES + 256;
+};
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 
 enum { EPI_STORE = 0, EPI_JROWS = 1, EPI_SYRK = 2 };
 
@@ -40,7 +57,9 @@ struct TcArgs {
   int ldd;
   const float* F;           // EPI_JROWS
   int ldf;
-  __nv_bfloat16* J;
+  __nv_bfloat16* J;          // bf16 scheme
+  float* Jhi;                 // 3xtf32 scheme
+  float* Jlo;
   int ldj;
   int nc, tiles, npairs;    // EPI_SYRK
   int k_per_split;
@@ -48,14 +67,17 @@ struct TcArgs {
   int* err;
 };
 
-__global__ void __launch_bounds__(128, 2)
+template <bool X3>
+__global__ void __launch_bounds__(128, X3 ? 1 : 2)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+              const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB2,
               TcArgs g) {
+  constexpr int BK = Scheme<X3>::BK, PARTS = Scheme<X3>::PARTS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * TILE_BYTES;
-  uint64_t* full = (uint64_t*)(sB + STAGES * TILE_BYTES);
+  // stage s holds parts p = 0..PARTS-1 at smem + (s * PARTS + p) * TILE_BYTES:
+  // bf16: A, B;  3xtf32: A hi, B hi, A lo, B lo
+  uint64_t* full = (uint64_t*)(smem + STAGES * PARTS * TILE_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
@@ -80,7 +102,7 @@ __global__ void __launch_bounds__(128, 2)
     kb = 0;
     ke = g.K;
   }
-  const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;
+  const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;   // BK of the scheme
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -102,25 +124,41 @@ __global__ void __launch_bounds__(128, 2)
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
       if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err)) break;
-      umma::mbar_expect_tx(&full[s], 2 * TILE_BYTES);
+      umma::mbar_expect_tx(&full[s], PARTS * TILE_BYTES);
       const int kc = kb + it * BK;
-      umma::tma_load_2d(sA + s * TILE_BYTES, &tA, &full[s], kc, arow);
-      umma::tma_load_2d(sB + s * TILE_BYTES, &tB, &full[s], kc, brow);
+      uint8_t* st = smem + (size_t)s * PARTS * TILE_BYTES;
+      umma::tma_load_2d(st, &tA, &full[s], kc, arow);
+      umma::tma_load_2d(st + TILE_BYTES, &tB, &full[s], kc, brow);
+      if (X3) {
+        umma::tma_load_2d(st + 2 * TILE_BYTES, &tA2, &full[s], kc, arow);
+        umma::tma_load_2d(st + 3 * TILE_BYTES, &tB2, &full[s], kc, brow);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    const uint32_t id = umma::idesc(1, BM, BN);
+    const uint32_t id = umma::idesc(X3 ? 2 : 1, BM, BN);
     for (int it = 0; it < nk; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
       if (!umma::mbar_wait(&full[s], ph, g.err)) break;
       umma::fence_after();
-      const uint32_t a0 = umma::smem_u32(sA + s * TILE_BYTES);
-      const uint32_t b0 = umma::smem_u32(sB + s * TILE_BYTES);
+      const uint32_t a0 = umma::smem_u32(smem + (size_t)s * PARTS * TILE_BYTES);
+      const uint32_t b0 = a0 + TILE_BYTES;
+      // each instruction consumes 32 bytes of every row (16 bf16 or 8 tf32)
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk)
-        umma::mma_bf16(tmem, umma::sdesc_sw128(a0 + kk * 32), umma::sdesc_sw128(b0 + kk * 32), id,
-                       (it | kk) != 0);
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t da = umma::sdesc_sw128(a0 + kk * 32);
+        const uint64_t db = umma::sdesc_sw128(b0 + kk * 32);
+        if (X3) {
+          const uint64_t dal = umma::sdesc_sw128(a0 + 2 * TILE_BYTES + kk * 32);
+          const uint64_t dbl = umma::sdesc_sw128(b0 + 2 * TILE_BYTES + kk * 32);
+          umma::mma_tf32(tmem, dal, db, id, (it | kk) != 0);   // lo . hi
+          umma::mma_tf32(tmem, da, dbl, id, 1);                 // hi . lo
+          umma::mma_tf32(tmem, da, db, id, 1);                  // hi . hi
+        } else {
+          umma::mma_bf16(tmem, da, db, id, (it | kk) != 0);
+        }
+      }
       umma::mma_commit(&empty[s]);
     }
     umma::mma_commit(done);
@@ -146,6 +184,20 @@ __global__ void __launch_bounds__(128, 2)
 #pragma unroll
         for (int j = 0; j < 32; ++j)
           if (brow + cb + j < g.N) d[j] = v[j];
+      }
+    } else if (g.mode == EPI_JROWS && X3) {
+      const int row = arow + r;
+      if (row < g.M) {
+        const float* f = g.F + (size_t)row * g.ldf + brow + cb;
+        float* oh = g.Jhi + (size_t)row * g.ldj + brow + cb;
+        float* ol = g.Jlo + (size_t)row * g.ldj + brow + cb;
+        for (int j = 0; j < 32; ++j)
+          if (brow + cb + j < g.N) {
+            const float x = v[j] + f[j];
+            const float hi = tf32_rna(x);
+            oh[j] = hi;
+            ol[j] = tf32_rna(x - hi);
+          }
       }
     } else if (g.mode == EPI_JROWS) {
       const int row = arow + r;
@@ -198,33 +250,37 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-// bf16 K-major operand [rows][ld], inner extent k, boxes of 64 x 128
+// K-major operand [rows][ld] (elements), inner extent k, 128-byte x 128-row boxes
 int make_map(bem_ctx* c, CUtensorMap* m, const void* base, uint64_t k, uint64_t rows,
-             uint64_t ld) {
+             uint64_t ld, bool f32) {
   auto enc = encoder();
   if (!enc) return fail(c, BEM_ECUDA, "cuTensorMapEncodeTiled is not available");
-  if (((uintptr_t)base & 15) || (ld * 2) % 16)
+  const uint64_t es = f32 ? 4 : 2;
+  if (((uintptr_t)base & 15) || (ld * es) % 16)
     return fail(c, BEM_EINVAL, "tensor-core operand not 16-byte aligned");
   cuuint64_t dims[2] = {k, rows};
-  cuuint64_t strides[1] = {ld * 2};
-  cuuint32_t box[2] = {BK, BM};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
-                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  cuuint64_t strides[1] = {ld * es};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), BM};
+  cuuint32_t est[2] = {1, 1};
+  CUresult r = enc(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, est, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(c, BEM_ECUDA, "cuTensorMapEncodeTiled failed");
   return BEM_OK;
 }
 
-int launch(bem_ctx* c, const CUtensorMap& a, const CUtensorMap& b, const TcArgs& g, dim3 grid) {
+template <bool X3>
+int launch(bem_ctx* c, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& a2,
+           const CUtensorMap& b2, const TcArgs& g, dim3 grid) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Scheme<X3>::SMEM);
     if (e != cudaSuccess) return cuda_check(c, e, "tc gemm smem attribute");
     attr = true;
   }
-  k_tc_gemm<<<grid, 128, SMEM_BYTES, S(c)>>>(a, b, g);
+  k_tc_gemm<X3><<<grid, 128, Scheme<X3>::SMEM, S(c)>>>(a, b, a2, b2, g);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_tc_gemm");
 }
@@ -236,48 +292,64 @@ int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const
                   float* D, int ldd) {
   int rc;
   CUtensorMap ta, tb;
-  if ((rc = make_map(c, &ta, A, K, M, lda)) || (rc = make_map(c, &tb, B, K, N, ldb))) return rc;
+  if ((rc = make_map(c, &ta, A, K, M, lda, false)) || (rc = make_map(c, &tb, B, K, N, ldb, false)))
+    return rc;
   TcArgs g{};
   g.M = M; g.N = N; g.K = K; g.mode = EPI_STORE; g.D = D; g.ldd = ldd; g.err = c->d_status;
-  return launch(c, ta, tb, g, dim3((M + BM - 1) / BM, (N + BN - 1) / BN));
+  return launch<false>(c, ta, tb, ta, tb, g, dim3((M + BM - 1) / BM, (N + BN - 1) / BN));
 }
 
-// J[rows][m] = bf16(Mt[rows][Nb] Phi[m][Nb]^T + F[rows][m])
-int tc_jrows(bem_ctx* c, int rows, int m, int Nb, const void* Mt, int ldm, const void* Phi,
-             int ldp, const float* F, int ldf, void* J, int ldj) {
+// J^T rows: J[rows][m] = Mt[rows][Nb] Phi[m][Nb]^T + F[rows][m].
+//   bf16:   Mt, Phi bf16; J bf16 (Jout[0])
+//   3xtf32: Mt = (Mt[0] hi, Mt[1] lo), Phi likewise, fp32; J hi/lo fp32 (Jout[0], Jout[1])
+int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt, int ldm,
+             const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj) {
   int rc;
-  CUtensorMap ta, tb;
-  if ((rc = make_map(c, &ta, Mt, Nb, rows, ldm)) || (rc = make_map(c, &tb, Phi, Nb, m, ldp)))
+  CUtensorMap ta, tb, ta2, tb2;
+  if ((rc = make_map(c, &ta, Mt[0], Nb, rows, ldm, x3)) ||
+      (rc = make_map(c, &tb, Phi[0], Nb, m, ldp, x3)))
+    return rc;
+  if (x3 && ((rc = make_map(c, &ta2, Mt[1], Nb, rows, ldm, true)) ||
+             (rc = make_map(c, &tb2, Phi[1], Nb, m, ldp, true))))
     return rc;
   if ((ldf % 4) || ((uintptr_t)F & 15)) return fail(c, BEM_EINVAL, "F rows not 16-byte aligned");
   TcArgs g{};
-  g.M = rows; g.N = m; g.K = Nb; g.mode = EPI_JROWS; g.F = F; g.ldf = ldf;
-  g.J = (__nv_bfloat16*)J; g.ldj = ldj; g.err = c->d_status;
+  g.M = rows; g.N = m; g.K = Nb; g.mode = EPI_JROWS; g.F = F; g.ldf = ldf; g.ldj = ldj;
+  g.err = c->d_status;
+  if (x3) { g.Jhi = (float*)Jout[0]; g.Jlo = (float*)Jout[1]; }
+  else g.J = (__nv_bfloat16*)Jout[0];
   ProfScope _ps(c, "tc_jrows");
-  return launch(c, ta, tb, g, dim3((rows + BM - 1) / BM, (m + BN - 1) / BN));
+  dim3 grid((rows + BM - 1) / BM, (m + BN - 1) / BN);
+  return x3 ? launch<true>(c, ta, tb, ta2, tb2, g, grid) : launch<false>(c, ta, tb, ta, tb, g, grid);
 }
 
 // part[split][ch][nc][nc] += upper blocks of J_ch^T J_ch over the m samples of J
 // (J rows ch*nc .. ch*nc+nc-1 hold channel ch), K split into `splits` slices.
-int tc_syrk(bem_ctx* c, int nc, int m, const void* J, int ldj, float* part, int splits) {
+// bf16: J[0] bf16.  3xtf32: J[0] hi, J[1] lo, fp32.
+int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, float* part,
+            int splits) {
   int rc;
-  CUtensorMap tj;
-  if ((rc = make_map(c, &tj, J, m, 3 * nc, ldj))) return rc;
+  CUtensorMap tj, tj2;
+  if ((rc = make_map(c, &tj, J[0], m, 3 * nc, ldj, x3))) return rc;
+  if (x3 && (rc = make_map(c, &tj2, J[1], m, 3 * nc, ldj, true))) return rc;
   TcArgs g{};
   g.M = g.N = nc; g.K = m; g.mode = EPI_SYRK; g.nc = nc;
   g.tiles = (nc + BM - 1) / BM;
   g.npairs = g.tiles * (g.tiles + 1) / 2;
-  g.k_per_split = ((m + splits - 1) / splits + BK - 1) / BK * BK;
+  const int bk = x3 ? Scheme<true>::BK : Scheme<false>::BK;
+  g.k_per_split = ((m + splits - 1) / splits + bk - 1) / bk * bk;
   g.part = part; g.err = c->d_status;
   int sp = (m + g.k_per_split - 1) / g.k_per_split;
   ProfScope _ps(c, "tc_syrk");
-  return launch(c, tj, tj, g, dim3(3 * g.npairs, sp));
+  dim3 grid(3 * g.npairs, sp);
+  return x3 ? launch<true>(c, tj, tj, tj2, tj2, g, grid) : launch<false>(c, tj, tj, tj, tj, g, grid);
 }
 
-int tc_syrk_splits(int nc) {
+int tc_syrk_splits(int nc, bool x3) {
   int tiles = (nc + BM - 1) / BM;
   int ctas = 3 * tiles * (tiles + 1) / 2;
-  return std::max(1, std::min(64, (2 * 152 + ctas - 1) / ctas));
+  int slots = (x3 ? 1 : 2) * 152;
+  return std::max(1, std::min(64, (slots + ctas - 1) / ctas));
 }
 
 }  // namespace bem

@@ -126,6 +126,39 @@ __global__ void k_phi_rows_bf16(const float* __restrict__ xy, int ns, const floa
   phi[t] = __float2bfloat16_rn(a * float(kInv2Pi));
 }
 
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// tf32 hi/lo split of phi_j(x_s)/(2 pi): hi[s][j], lo[s][j]
+__global__ void k_phi_rows_x3(const float* __restrict__ xy, int ns, const float* __restrict__ vert,
+                              int Nb, float* __restrict__ hi, float* __restrict__ lo) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ns * Nb) return;
+  int s = (int)(t / Nb), j = (int)(t % Nb);
+  float a = seg_angle(vert[2 * j], vert[2 * j + 1], vert[2 * j + 2], vert[2 * j + 3], xy[2 * s],
+                      xy[2 * s + 1]) *
+            float(kInv2Pi);
+  float h = tf32_round(a);
+  hi[t] = h;
+  lo[t] = tf32_round(a - h);
+}
+
+// tf32 hi/lo split of Mt[c*nc + col][j] = Mc[c][j][col]
+__global__ void k_mt_x3(const double* __restrict__ Mc, int Nb, int nc, float* __restrict__ hi,
+                        float* __restrict__ lo) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = blockIdx.y;
+  if (j >= Nb) return;
+  int c = row / nc, col = row % nc;
+  double v = Mc[((size_t)c * Nb + j) * nc + col];
+  float h = tf32_round((float)v);
+  hi[(size_t)row * Nb + j] = h;
+  lo[(size_t)row * Nb + j] = tf32_round((float)(v - (double)h));
+}
+
 // Mt[c*nc + col][j] = bf16(Mc[c][j][col])
 __global__ void k_mt_bf16(const double* __restrict__ Mc, int Nb, int nc,
                           __nv_bfloat16* __restrict__ Mt) {
@@ -281,31 +314,42 @@ static int jtj_stacked_rhs(bem_ctx* c) {
   return cuda_check(c, cudaGetLastError(), "stacked rhs");
 }
 
-// Mixed precision: J^T rows on the tensor cores in bf16 (fp32 accumulate),
-// Gram blocks accumulated per K slice in fp32, slices summed in double.
-static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout) {
+// Mixed precision: J^T rows and the Gram blocks on the tensor cores, either
+// in bf16 (fp32 accumulate) or in the 3xtf32 split; Gram blocks accumulate
+// per K slice in fp32 and the slices are summed in double.
+static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3) {
   int rc;
   int C = c->sc.C, nc = 16 * C, Nb = c->bd.Nb, nth = c->sc.nth;
   if ((rc = jtj_stacked_rhs<float>(c))) return rc;
-  // M_c^T in bf16, [3 nc][Nb]
-  if ((rc = grow(c, c->tcMt, sizeof(__nv_bfloat16) * 3 * (size_t)nc * Nb))) return rc;
-  k_mt_bf16<<<dim3((Nb + 127) / 128, 3 * nc), 128, 0, S(c)>>>((const double*)c->Mc.p, Nb, nc,
-                                                               (__nv_bfloat16*)c->tcMt.p);
+  const size_t es = x3 ? 2 * sizeof(float) : sizeof(__nv_bfloat16);   // bytes per element (all parts)
+  // M_c^T, [3 nc][Nb]
+  const size_t mt_part = (x3 ? 4 : 2) * 3 * (size_t)nc * Nb;
+  if ((rc = grow(c, c->tcMt, es * 3 * (size_t)nc * Nb))) return rc;
+  const void* Mt[2] = {c->tcMt.p, (char*)c->tcMt.p + mt_part};
+  if (x3)
+    k_mt_x3<<<dim3((Nb + 127) / 128, 3 * nc), 128, 0, S(c)>>>((const double*)c->Mc.p, Nb, nc,
+                                                               (float*)Mt[0], (float*)Mt[1]);
+  else
+    k_mt_bf16<<<dim3((Nb + 127) / 128, 3 * nc), 128, 0, S(c)>>>((const double*)c->Mc.p, Nb, nc,
+                                                                 (__nv_bfloat16*)Mt[0]);
   BEM_LAUNCHED(c);
-  // per-chunk buffers: Phi bf16 [m][Nb], F^T f32 [3nc][ld], J^T bf16 [3nc][ld]
+  // per-chunk buffers: Phi [m][Nb], F^T f32 [3nc][ld], J^T [3nc][ld]
   const int64_t chunk = std::min<int64_t>(std::max<int64_t>(n, 1), 262144);
   const int ld = (int)((chunk + 63) / 64 * 64);
-  const size_t phi_b = sizeof(__nv_bfloat16) * (size_t)chunk * Nb;
+  const size_t phi_part = (x3 ? 4 : 2) * (size_t)chunk * Nb;
+  const size_t phi_b = (x3 ? 2 : 1) * phi_part;
   const size_t f_b = sizeof(float) * 3 * (size_t)nc * ld;
-  const size_t j_b = sizeof(__nv_bfloat16) * 3 * (size_t)nc * ld;
+  const size_t j_part = (x3 ? 4 : 2) * 3 * (size_t)nc * ld;
+  const size_t j_b = (x3 ? 2 : 1) * j_part;
   if ((rc = grow(c, c->jrow, phi_b + 256 + f_b + 256))) return rc;
   if ((rc = grow(c, c->tcJ, j_b))) return rc;
-  const int splits = tc_syrk_splits(nc);
+  const int splits = tc_syrk_splits(nc, x3);
   const size_t part_b = sizeof(float) * (size_t)splits * 3 * nc * nc;
   if ((rc = grow(c, c->tcPart, part_b))) return rc;
   if ((rc = grow(c, c->Hc, sizeof(double) * 3 * (size_t)nc * nc))) return rc;
-  __nv_bfloat16* phi = (__nv_bfloat16*)c->jrow.p;
+  const void* phi[2] = {c->jrow.p, (char*)c->jrow.p + phi_part};
   float* F = (float*)((char*)c->jrow.p + (phi_b + 255) / 256 * 256);
+  void* J[2] = {c->tcJ.p, (char*)c->tcJ.p + j_part};
   float* part = (float*)c->tcPart.p;
   if ((rc = cuda_check(c, cudaMemsetAsync(part, 0, part_b, S(c)), "memset"))) return rc;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
@@ -313,13 +357,19 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout) {
     const int m = (int)std::min<int64_t>(chunk, n - s0);
     {
       ProfScope _pp(c, "k_phi_rows");
-      k_phi_rows_bf16<<<(unsigned)(((int64_t)m * Nb + 255) / 256), 256, 0, S(c)>>>(
-          xy + 2 * s0, m, c->bd.d_vert32, Nb, phi);
+      const unsigned blocks = (unsigned)(((int64_t)m * Nb + 255) / 256);
+      if (x3)
+        k_phi_rows_x3<<<blocks, 256, 0, S(c)>>>(xy + 2 * s0, m, c->bd.d_vert32, Nb,
+                                                (float*)phi[0], (float*)phi[1]);
+      else
+        k_phi_rows_bf16<<<blocks, 256, 0, S(c)>>>(xy + 2 * s0, m, c->bd.d_vert32, Nb,
+                                                  (__nv_bfloat16*)phi[0]);
       BEM_LAUNCHED(c);
     }
     launch_frows<float, true>(c, xy + 2 * s0, m, F, ld);
-    if ((rc = tc_jrows(c, 3 * nc, m, Nb, c->tcMt.p, Nb, phi, Nb, F, ld, c->tcJ.p, ld))) return rc;
-    if ((rc = tc_syrk(c, nc, m, c->tcJ.p, ld, part, splits))) return rc;
+    if ((rc = tc_jrows(c, x3, 3 * nc, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld))) return rc;
+    const void* Jc[2] = {J[0], J[1]};
+    if ((rc = tc_syrk(c, x3, nc, m, Jc, ld, part, splits))) return rc;
   }
   k_syrk_reduce<<<dim3((nc + 127) / 128, nc, 3), 128, 0, S(c)>>>(part, splits, nc,
                                                                   (double*)c->Hc.p);
@@ -338,7 +388,8 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout) {
 
 int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H) {
   if (c->opts.precision == BEM_FP64) return jtj_t<double>(c, n, (const double*)xy, H);
-  if (c->opts.jtj_mode == BEM_JTJ_BF16) return jtj_tc(c, n, (const float*)xy, H);
+  if (c->opts.jtj_mode == BEM_JTJ_BF16) return jtj_tc(c, n, (const float*)xy, H, false);
+  if (c->opts.jtj_mode == BEM_JTJ_3XTF32) return jtj_tc(c, n, (const float*)xy, H, true);
   return jtj_t<float>(c, n, (const float*)xy, H);
 }
 

@@ -184,13 +184,35 @@ def test_vjp_mixed(cfg1):
     assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-4
 
 
-def test_jtj_mixed(cfg1):
+@pytest.mark.parametrize("mode,tol", [("bf16", 2e-2), ("3xtf32", 1e-5), ("fp64", 1e-6)])
+def test_jtj_mixed(cfg1, mode, tol):
+    bg = _bg()
+    jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32, "fp64": bg.BEM_JTJ_FP64}[mode]
     sc, xy, target, mean, o = cfg1
     sub = xy[::16]
-    m = _ctx(sc, mean, _bg().BEM_MIXED)
+    m = _ctx(sc, mean, bg.BEM_MIXED, jtj_mode=jm)
     H = m.jtj(_t(sub, torch.float32)).cpu().numpy()
     _, _, want = o.gauss_newton(sc.theta_init, sub, target[::16])
-    assert np.linalg.norm(H - want) / np.linalg.norm(want) < 2e-2
+    assert np.linalg.norm(H - want) / np.linalg.norm(want) < tol
+
+
+@pytest.mark.parametrize("mode", ["bf16", "3xtf32"])
+def test_lm_step_mixed(cfg1, mode):
+    """One mixed LM step: the loss it reports at the new theta matches the
+    oracle's loss there, and the step lowers the loss like the FP64 step."""
+    bg = _bg()
+    jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32}[mode]
+    sc, xy, target, mean, o = cfg1
+    sub, tsub = xy[::8], target[::8]
+    m = _ctx(sc, mean, bg.BEM_MIXED, jtj_mode=jm)
+    res = m.lm_step(_t(sub, torch.float32), _t(tsub, torch.float32), [1e-3])
+    th = m.get_params()
+    assert res["loss_before"] == pytest.approx(o.loss(sc.theta_init, sub, tsub), rel=1e-5)
+    if res["accepted"]:
+        assert res["loss_after"] == pytest.approx(o.loss(th, sub, tsub), rel=1e-4)
+    want = o.lm_step(sc.theta_init, sub, tsub, 1e-3)
+    assert res["accepted"] == want["accepted"]
+    assert res["loss_after"] == pytest.approx(want["loss_after"], rel=2e-2 if mode == "bf16" else 1e-4)
 
 
 def test_mixed_without_near_field(cfg1):
