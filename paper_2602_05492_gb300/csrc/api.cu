@@ -207,7 +207,7 @@ void bem_destroy(bem_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   DevBuf* bufs[] = {&c->part, &c->part2, &c->loss, &c->gpart, &c->jrow, &c->phi, &c->Hc, &c->Mc,
                     &c->Dfc, &c->Fg, &c->lmK, &c->lmL, &c->lmLt, &c->lmW, &c->H, &c->g,
-                    &c->tcJ, &c->tcPart, &c->tcMt};
+                    &c->tcJ, &c->tcPart, &c->tcMt, &c->nearP, &c->nearS, &c->nearF};
   for (DevBuf* b : bufs) free_buf(*b);
   delete c;
 }
@@ -450,8 +450,7 @@ int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_tri
     for (int t = 0; t < n_trials; ++t) mx = std::fmax(mx, used[t]);
     out->lambda_next = n_trials == 1 ? 2.0 * used[0] : 10.0 * mx;
   }
-  // leave panels and boundary solution consistent with the kept theta
-  if ((rc = refresh(c, c->d_theta))) return rc;
+  // panels and boundary solution are rebuilt from theta by the next call
   return cuda_check(c, cudaStreamSynchronize(S(c)), "sync");
 }
 

@@ -89,6 +89,21 @@ __device__ __forceinline__ Frame<T> frame(const Panel<T>& p, T x, T y) {
   return f;
 }
 
+// Near-field test of the mixed-precision path: the distance from x to the
+// panel segment is below near_factor * L (compared squared).  The frame is
+// recomputed here with explicitly rounded operations so that every kernel
+// (the float main loops that skip these pairs and the double near-field
+// kernels that take them) reaches the same decision bit for bit.
+__device__ __forceinline__ bool near_pair(const Panel<float>& p, float x, float y, float near2) {
+  const float dax = __fsub_rn(p.ax, x), day = __fsub_rn(p.ay, y);
+  const float t1 = __fmaf_rn(dax, p.tx, __fmul_rn(day, p.ty));
+  const float h = __fmaf_rn(dax, p.ty, -__fmul_rn(day, p.tx));
+  const float t2 = __fadd_rn(t1, p.L);
+  const float dt = t1 > 0.f ? t1 : (t2 < 0.f ? t2 : 0.f);
+  const float d2 = __fmaf_rn(dt, dt, __fmul_rn(h, h));
+  return d2 < __fmul_rn(near2, __fmul_rn(p.L, p.L));
+}
+
 // One regularised layer pair: S with eps_c, Dl with eps_d.
 template <typename T>
 struct LayerVals {

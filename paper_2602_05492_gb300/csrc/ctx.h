@@ -85,7 +85,8 @@ struct bem_ctx {
 
   // growable scratch
   bem::DevBuf part, part2, loss, gpart, jrow, phi, Hc, Mc, Dfc, Fg, lmK, lmL, lmLt, lmW, H, g,
-      tcJ, tcPart, tcMt;
+      tcJ, tcPart, tcMt, nearP, nearS, nearF;
+  bool pbins_valid = false;        // panel -> cell bins match the current panels
 };
 
 namespace bem {
@@ -124,6 +125,12 @@ int field_eval(bem_ctx* c, int64_t n, const void* xy, void* out, const void* tar
 int field_rhs(bem_ctx* c);           // d_fb from the current panels
 int field_solve(bem_ctx* c);         // d_ub = A^+ d_fb
 int field_sample_mean(bem_ctx* c, int64_t n, const void* target, double* host_mean);
+
+// ---- near field of the mixed path (k_near.cu) ------------------------------------
+// out[n][3] = double sum over the near panels of each point
+int near_forward(bem_ctx* c, int64_t n, const float* xy, double* out);
+// out[P][11] = double adjoint sums of each panel over its near points
+int near_adjoint(bem_ctx* c, int64_t n, const float* xy, const float* w, double* out);
 
 // ---- adjoint (k_adjoint.cu) ------------------------------------------------------
 int adj_vjp(bem_ctx* c, int64_t n, const void* xy, const void* resid, double* grad);

@@ -157,6 +157,80 @@ __global__ void __launch_bounds__(kVB) k_vjp(VjpArgs<T> a) {
   }
 }
 
+// Float adjoint of the mixed path: one thread per panel (or boundary
+// segment), the block's points staged 256 at a time as (x, y, r0, r1), r2;
+// float sums per tile are added to double totals kept in shared memory
+// (thread-owned columns), so the registers hold only the panel, the tile sums
+// and the pair's temporaries.  Near pairs are skipped (evaluated in double by
+// k_near_adjoint).
+constexpr int kVT = 256;
+
+template <bool SAME, bool NEAR>
+__global__ void __launch_bounds__(kVB) k_vjp_f32(VjpArgs<float> a) {
+  __shared__ float4 sq[kVT];
+  __shared__ float sr2[kVT];
+  __shared__ double stot[kNP][kVB];
+  const int tid = threadIdx.x;
+  const int ptiles = (a.P + kVB - 1) / kVB;
+  const bool is_pan = (int)blockIdx.x < ptiles;
+  const int idx = is_pan ? blockIdx.x * kVB + tid : (blockIdx.x - ptiles) * kVB + tid;
+  const bool live = is_pan ? idx < a.P : idx < a.Nb;
+  const int64_t s0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t s1 = min(a.n, s0 + a.chunk);
+  Panel<float> p{};
+  float bax = 0, bay = 0, bbx = 0, bby = 0;
+  if (live) {
+    if (is_pan) {
+      p = a.pan[idx];
+    } else {
+      bax = a.vert[2 * idx]; bay = a.vert[2 * idx + 1];
+      bbx = a.vert[2 * idx + 2]; bby = a.vert[2 * idx + 3];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kNP; ++k) stot[k][tid] = 0.0;
+  for (int64_t base = s0; base < s1; base += kVT) {
+    const int cnt = (int)min((int64_t)kVT, s1 - base);
+    __syncthreads();
+    for (int e = tid; e < cnt; e += kVB) {
+      const int64_t i = base + e;
+      sq[e] = make_float4(a.xy[2 * i], a.xy[2 * i + 1], a.w[3 * i], a.w[3 * i + 1]);
+      sr2[e] = a.w[3 * i + 2];
+    }
+    __syncthreads();
+    if (!live) continue;
+    float acc[kNP];
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) acc[k] = 0.f;
+    if (is_pan) {
+      for (int k = 0; k < cnt; ++k) {
+        const float4 q = sq[k];
+        if (NEAR && near_pair(p, q.x, q.y, a.near2)) continue;
+        pair_adj<float, SAME>(p, q.x, q.y, q.z, q.w, sr2[k], a.ec2, a.ed2, acc);
+      }
+    } else {
+      for (int k = 0; k < cnt; ++k) {
+        const float4 q = sq[k];
+        const float phi = seg_angle(bax, bay, bbx, bby, q.x, q.y);
+        acc[0] += phi * q.z;
+        acc[1] += phi * q.w;
+        acc[2] += phi * sr2[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) stot[k][tid] += (double)acc[k];
+  }
+  if (!live) return;
+  if (is_pan) {
+    double* o = a.part + ((size_t)blockIdx.y * a.P + idx) * kNP;
+#pragma unroll
+    for (int k = 0; k < kNP; ++k) o[k] = stot[k][tid];
+  } else {
+    double* o = a.qpart + ((size_t)blockIdx.y * a.Nb + idx) * 3;
+    for (int k = 0; k < 3; ++k) o[k] = stot[k][tid] * kInv2Pi;
+  }
+}
+
 // out[m] (+)= sum over slices of part[slice][m], fixed order
 __global__ void k_reduce_slices(const double* __restrict__ part, int slices, int64_t m,
                                 double* __restrict__ out, int accumulate) {
@@ -224,26 +298,32 @@ __global__ void k_chain(const double* __restrict__ ps, const Panel<double>* __re
 template <typename T>
 static int vjp_pass(bem_ctx* c, int64_t n, const T* xy, const T* w, bool boundary, int accumulate) {
   int rc;
+  const bool f32 = sizeof(T) == 4;
+  const bool near = f32 && c->opts.near_factor > 0;
   int P = c->sc.P, Nb = boundary ? c->bd.Nb : 0;
   int ptiles = (P + kVB - 1) / kVB, btiles = (Nb + kVB - 1) / kVB;
   int tiles = ptiles + btiles;
-  // about four blocks per SM in total, chunks of at least one point tile
-  int64_t want = (4 * 152 + tiles - 1) / tiles;
-  int64_t maxs = (n + kVB - 1) / kVB;
+  // double kernel: about four resident blocks per SM; float kernel: about
+  // three waves of seven resident blocks per SM
+  const int step = f32 ? kVT : kVB;
+  int64_t want = f32 ? (3 * 7 * 152 + tiles - 1) / tiles : (4 * 152 + tiles - 1) / tiles;
+  int64_t maxs = (n + step - 1) / step;
   int slices = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxs));
-  int64_t chunk = ((n + slices - 1) / slices + kVB - 1) / kVB * kVB;
+  int64_t chunk = ((n + slices - 1) / slices + step - 1) / step * step;
   slices = (int)std::max<int64_t>(1, (n + chunk - 1) / chunk);
-  size_t pbytes = sizeof(double) * (size_t)slices * P * kNP;
-  size_t qbytes = sizeof(double) * (size_t)slices * (Nb > 0 ? Nb : 1) * 3;
+  if (n <= 0) slices = 0;
+  const int pslices = slices + (near && n > 0 ? 1 : 0);     // near sums in the last slice
+  size_t pbytes = sizeof(double) * (size_t)std::max(pslices, 1) * P * kNP;
+  size_t qbytes = sizeof(double) * (size_t)std::max(slices, 1) * (Nb > 0 ? Nb : 1) * 3;
   if ((rc = grow(c, c->part, pbytes + qbytes))) return rc;
   VjpArgs<T> a{};
   a.xy = xy;
   a.w = w;
   a.n = n;
-  a.pan = (const Panel<T>*)(sizeof(T) == 8 ? (const void*)c->d_pan64 : (const void*)c->d_pan32);
+  a.pan = (const Panel<T>*)(f32 ? (const void*)c->d_pan32 : (const void*)c->d_pan64);
   a.pan64 = c->d_pan64;
   a.P = P;
-  a.vert = (const T*)(sizeof(T) == 8 ? (const void*)c->bd.d_vert : (const void*)c->bd.d_vert32);
+  a.vert = (const T*)(f32 ? (const void*)c->bd.d_vert32 : (const void*)c->bd.d_vert);
   a.Nb = Nb;
   a.ec2 = T(c->opts.eps_c * c->opts.eps_c);
   a.ed2 = T(c->opts.eps_d * c->opts.eps_d);
@@ -257,22 +337,29 @@ static int vjp_pass(bem_ctx* c, int64_t n, const T* xy, const T* w, bool boundar
     dim3 grid(tiles, slices);
     ProfScope _ps(c, Nb > 0 ? "k_vjp" : "k_vjp_gauss");
     bool same = c->opts.eps_c == c->opts.eps_d;
-    bool near = sizeof(T) == 4 && c->opts.near_factor > 0;
-    if (same) {
-      if (near) k_vjp<T, true, true><<<grid, kVB, 0, S(c)>>>(a);
-      else k_vjp<T, true, false><<<grid, kVB, 0, S(c)>>>(a);
+    if constexpr (sizeof(T) == 4) {
+      if (same) {
+        if (near) k_vjp_f32<true, true><<<grid, kVB, 0, S(c)>>>(a);
+        else k_vjp_f32<true, false><<<grid, kVB, 0, S(c)>>>(a);
+      } else {
+        if (near) k_vjp_f32<false, true><<<grid, kVB, 0, S(c)>>>(a);
+        else k_vjp_f32<false, false><<<grid, kVB, 0, S(c)>>>(a);
+      }
     } else {
-      if (near) k_vjp<T, false, true><<<grid, kVB, 0, S(c)>>>(a);
+      if (same) k_vjp<T, true, false><<<grid, kVB, 0, S(c)>>>(a);
       else k_vjp<T, false, false><<<grid, kVB, 0, S(c)>>>(a);
     }
     BEM_LAUNCHED(c);
-  } else {
-    slices = 0;
+  }
+  if (near && n > 0) {
+    if ((rc = near_adjoint(c, n, (const float*)xy, (const float*)w,
+                           a.part + (size_t)slices * P * kNP)))
+      return rc;
   }
   // panel sums (accumulated into part2[P][11]) and q (into d_q)
   int64_t m = (int64_t)P * kNP;
-  if (slices > 0) {
-    k_reduce_slices<<<(unsigned)((m + 255) / 256), 256, 0, S(c)>>>(a.part, slices, m,
+  if (pslices > 0) {
+    k_reduce_slices<<<(unsigned)((m + 255) / 256), 256, 0, S(c)>>>(a.part, pslices, m,
                                                                      (double*)c->part2.p,
                                                                      accumulate);
     BEM_LAUNCHED(c);

@@ -2,8 +2,8 @@
 //   u(x) = mean + sum_j phi_j(x)/(2 pi) u_b,j + sum_p [ -w_d,p Dl_p(x) + w_c,p S_p(x) ]
 // One thread per point; panels (and boundary vertices) are staged block-wide
 // in shared memory and broadcast to every warp.  In mixed precision the
-// pair terms are float, except for pairs closer than near_factor panel
-// lengths, which are recomputed in double from the double panel table.
+// pair terms are float; pairs closer than near_factor panel lengths are
+// skipped here and their double sum (k_near.cu) is added per point.
 #include <cmath>
 
 #include "ctx.h"
@@ -32,35 +32,19 @@ struct FieldArgs {
   T* resid;            // residual [n][3] or null
   double* loss_part;   // per-block sum of |r|^2 or null
   double* split_out;   // split mode: [gridDim.y][n][3] handle-term partials
+  const double* near_add;  // double near-field sum [n][3] or null
 };
 
-// Pair contribution of one panel at (x, y) in double.
-template <bool SAME>
-__device__ __forceinline__ void pair_f64(const Panel<double>& p, double x, double y, double ec2,
-                                         double ed2, double& a0, double& a1, double& a2) {
-  Frame<double> f = frame(p, x, y);
-  LayerVals<double> v = layer_values(f, ec2, ed2, SAME);
-  a0 += -p.wd[0] * v.Dl + p.wc[0] * v.S;
-  a1 += -p.wd[1] * v.Dl + p.wc[1] * v.S;
-  a2 += -p.wd[2] * v.Dl + p.wc[2] * v.S;
-}
-
-// Sum over one shared-memory tile of panels.
+// Sum over one shared-memory tile of panels (near pairs skipped when NEAR).
 template <typename T, bool SAME, bool NEAR>
-__device__ __forceinline__ void tile_accum(const Panel<T>* tile, int base, int cnt, T x, T y,
-                                           const FieldArgs<T>& a, T& s0, T& s1, T& s2,
-                                           double& d0, double& d1, double& d2) {
+__device__ __forceinline__ void tile_accum(const Panel<T>* tile, int cnt, T x, T y,
+                                           const FieldArgs<T>& a, T& s0, T& s1, T& s2) {
   for (int k = 0; k < cnt; ++k) {
     const Panel<T>& p = tile[k];
-    Frame<T> f = frame(p, x, y);
-    if (NEAR) {
-      // squared distance from x to the panel segment vs (near_factor L)^2
-      T dt = f.t1 > T(0) ? f.t1 : (f.t2 < T(0) ? f.t2 : T(0));
-      if (dt * dt + f.h * f.h < a.near2 * f.L * f.L) {
-        pair_f64<SAME>(a.pan64[base + k], double(x), double(y), a.ec2d, a.ed2d, d0, d1, d2);
-        continue;
-      }
+    if constexpr (NEAR) {
+      if (near_pair(p, x, y, a.near2)) continue;
     }
+    Frame<T> f = frame(p, x, y);
     LayerVals<T> v = layer_values(f, a.ec2, a.ed2, SAME);
     s0 += -p.wd[0] * v.Dl + p.wc[0] * v.S;
     s1 += -p.wd[1] * v.Dl + p.wc[1] * v.S;
@@ -80,21 +64,20 @@ __global__ void __launch_bounds__(kFB) k_field(FieldArgs<T> a) {
   T x = T(0.5), y = T(0.5);
   if (live) { x = a.xy[2 * i]; y = a.xy[2 * i + 1]; }
   T s0 = 0, s1 = 0, s2 = 0;
-  double d0 = 0, d1 = 0, d2 = 0;
   const int p0 = a.split_out ? blockIdx.y * a.pchunk : 0;
   const int p1 = a.split_out ? min(a.P, p0 + a.pchunk) : a.P;
   for (int base = p0; base < p1; base += kFB) {
     __syncthreads();
     if (base + tid < p1) tile[tid] = a.pan[base + tid];
     __syncthreads();
-    tile_accum<T, SAME, NEAR>(tile, base, min(kFB, p1 - base), x, y, a, s0, s1, s2, d0, d1, d2);
+    tile_accum<T, SAME, NEAR>(tile, min(kFB, p1 - base), x, y, a, s0, s1, s2);
   }
   if (a.split_out) {
     if (live) {
       double* o = a.split_out + ((size_t)blockIdx.y * a.n + i) * 3;
-      o[0] = double(s0) + d0;
-      o[1] = double(s1) + d1;
-      o[2] = double(s2) + d2;
+      o[0] = double(s0);
+      o[1] = double(s1);
+      o[2] = double(s2);
     }
     return;
   }
@@ -124,9 +107,14 @@ __global__ void __launch_bounds__(kFB) k_field(FieldArgs<T> a) {
       }
     }
   }
-  double u0 = a.mean0 + double(b0) * kInv2Pi + double(s0) + d0;
-  double u1 = a.mean1 + double(b1) * kInv2Pi + double(s1) + d1;
-  double u2 = a.mean2 + double(b2) * kInv2Pi + double(s2) + d2;
+  double u0 = a.mean0 + double(b0) * kInv2Pi + double(s0);
+  double u1 = a.mean1 + double(b1) * kInv2Pi + double(s1);
+  double u2 = a.mean2 + double(b2) * kInv2Pi + double(s2);
+  if (a.near_add && live) {
+    u0 += a.near_add[3 * i];
+    u1 += a.near_add[3 * i + 1];
+    u2 += a.near_add[3 * i + 2];
+  }
   double r2 = 0.0;
   if (live) {
     if (a.out) {
@@ -176,9 +164,10 @@ __global__ void k_sum_fixed(const double* __restrict__ part, int64_t m, double* 
   }
 }
 
-// f_b,i = |G_i| sum_q w_q f(x_iq) from split partials
+// f_b,i = |G_i| sum_q w_q f(x_iq) from split partials (+ near-field sums)
 __global__ void k_rhs_reduce(const double* __restrict__ part, int nsplit, int Nb,
-                             const double* __restrict__ vert, double* __restrict__ fb) {
+                             const double* __restrict__ vert, const double* __restrict__ near_add,
+                             double* __restrict__ fb) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * Nb) return;
   int i = t / 3, c = t % 3;
@@ -189,6 +178,7 @@ __global__ void k_rhs_reduce(const double* __restrict__ part, int nsplit, int Nb
   for (int q = 0; q < 3; ++q) {
     double f = 0;
     for (int sp = 0; sp < nsplit; ++sp) f += part[((size_t)sp * n + 3 * i + q) * 3 + c];
+    if (near_add) f += near_add[(3 * i + q) * 3 + c];
     s += gauss_weight(q) * f;
   }
   fb[3 * i + c] = ell * s;
@@ -235,13 +225,18 @@ static FieldArgs<T> make_args(bem_ctx* c) {
 template <typename T>
 static void launch_field(bem_ctx* c, const FieldArgs<T>& a, dim3 grid) {
   ProfScope _ps(c, a.split_out ? "k_field_rhs" : "k_field");
-  bool same = c->opts.eps_c == c->opts.eps_d;
-  bool near = sizeof(T) == 4 && c->opts.near_factor > 0;
-  if (same) {
-    if (near) k_field<T, true, true><<<grid, kFB, 0, S(c)>>>(a);
-    else k_field<T, true, false><<<grid, kFB, 0, S(c)>>>(a);
+  const bool same = c->opts.eps_c == c->opts.eps_d;
+  if constexpr (sizeof(T) == 4) {
+    const bool near = c->opts.near_factor > 0;
+    if (same) {
+      if (near) k_field<T, true, true><<<grid, kFB, 0, S(c)>>>(a);
+      else k_field<T, true, false><<<grid, kFB, 0, S(c)>>>(a);
+    } else {
+      if (near) k_field<T, false, true><<<grid, kFB, 0, S(c)>>>(a);
+      else k_field<T, false, false><<<grid, kFB, 0, S(c)>>>(a);
+    }
   } else {
-    if (near) k_field<T, false, true><<<grid, kFB, 0, S(c)>>>(a);
+    if (same) k_field<T, true, false><<<grid, kFB, 0, S(c)>>>(a);
     else k_field<T, false, false><<<grid, kFB, 0, S(c)>>>(a);
   }
   BEM_LAUNCHED(c);
@@ -260,6 +255,11 @@ static int field_eval_t(bem_ctx* c, int64_t n, const void* xy, void* out, const 
   a.out = (T*)out;
   a.resid = (T*)resid;
   int64_t nblk = (n + kFB - 1) / kFB;
+  if (sizeof(T) == 4 && c->opts.near_factor > 0 && n > 0) {
+    if ((rc = grow(c, c->nearF, sizeof(double) * 3 * (size_t)n))) return rc;
+    if ((rc = near_forward(c, n, (const float*)xy, (double*)c->nearF.p))) return rc;
+    a.near_add = (const double*)c->nearF.p;
+  }
   if (want_loss) {
     if ((rc = grow(c, c->loss, sizeof(double) * (nblk + 1)))) return rc;
     a.loss_part = (double*)c->loss.p;
@@ -299,8 +299,14 @@ static int field_rhs_t(bem_ctx* c) {
   a.pchunk = pchunk;
   a.split_out = (double*)c->gpart.p;
   launch_field<T>(c, a, dim3((unsigned)((n + kFB - 1) / kFB), nsplit));
+  const double* near_add = nullptr;
+  if (sizeof(T) == 4 && c->opts.near_factor > 0) {
+    if ((rc = grow(c, c->nearF, sizeof(double) * 3 * (size_t)n))) return rc;
+    if ((rc = near_forward(c, n, (const float*)a.xy, (double*)c->nearF.p))) return rc;
+    near_add = (const double*)c->nearF.p;
+  }
   k_rhs_reduce<<<(3 * Nb + 255) / 256, 256, 0, S(c)>>>(a.split_out, nsplit, Nb, c->bd.d_vert,
-                                                        c->d_fb);
+                                                        near_add, c->d_fb);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "rhs");
 }

@@ -115,6 +115,7 @@ __global__ void k_assemble(const double* __restrict__ vert, const double* __rest
 
 int geom_panelize(bem_ctx* c, const double* d_theta) {
   int P = c->sc.P;
+  c->pbins_valid = false;
   k_panelize<<<(P + 127) / 128, 128, 0, S(c)>>>(d_theta, c->sc.d_pcurve, c->sc.d_pk, c->sc.d_K,
                                                 c->sc.d_closed, P, c->d_pan64, c->d_pan32);
   BEM_LAUNCHED(c);

@@ -215,6 +215,21 @@ def test_lm_step_mixed(cfg1, mode):
     assert res["loss_after"] == pytest.approx(want["loss_after"], rel=2e-2 if mode == "bf16" else 1e-4)
 
 
+def test_mixed_all_pairs_near(cfg1):
+    """near_factor = 1000 sends every handle pair through the double near-field
+    kernels: colours and gradient then match the oracle to float rounding of
+    the boundary term only."""
+    sc, xy, target, mean, o = cfg1
+    sub = xy[::8]
+    m = _ctx(sc, mean, _bg().BEM_MIXED, near_factor=1000.0)
+    u = m.eval(_t(sub, torch.float32)).double().cpu().numpy()
+    assert np.sqrt(np.mean((u - o.eval(sc.theta_init, sub)) ** 2)) < 2e-6
+    r = np.random.default_rng(3).normal(size=(sub.shape[0], 3)).astype(np.float32)
+    g = m.vjp(_t(sub, torch.float32), _t(r, torch.float32)).cpu().numpy()
+    want = o.grad(sc.theta_init, sub, r.astype(np.float64))
+    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-5
+
+
 def test_mixed_without_near_field(cfg1):
     sc, xy, target, mean, o = cfg1
     m = _ctx(sc, mean, _bg().BEM_MIXED, near_factor=0.0)
