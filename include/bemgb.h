@@ -186,6 +186,13 @@ int lm_step(bem_ctx *ctx, int64_t n, const void *xy, const void *target,
 int bem_gemm_bf16(bem_ctx *ctx, int M, int N, int K, const void *A, int lda, const void *B,
                   int ldb, float *D, int ldd, void *stream);
 
+/* The float approximations the mixed-precision kernels use, next to CUDA's
+ * accurate float functions, for validation (no counterpart in the paper):
+ * which = 0: atan2(a[i], b[i]); 1: log(a[i]); 2: log1p(a[i]).  a, b,
+ * out_fast, out_ref: device float [n] (b only for which = 0). */
+int bem_fastmath_eval(bem_ctx *ctx, int which, int64_t n, const float *a, const float *b,
+                      float *out_fast, float *out_ref, void *stream);
+
 /* Sizes of the current scene (host ints; any pointer may be NULL). */
 int bem_sizes(const bem_ctx *ctx, int *n_theta, int *n_panels, int *n_boundary);
 

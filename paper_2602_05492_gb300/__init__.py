@@ -76,6 +76,7 @@ def _load():
         "bem_launch_count": (i64, [vp]),
         "bem_profile_enable": (ci, [vp, ci]),
         "bem_gemm_bf16": (ci, [vp, ci, ci, ci, vp, ci, vp, ci, vp, ci, vp]),
+        "bem_fastmath_eval": (ci, [vp, ci, i64, vp, vp, vp, vp, vp]),
         "bem_profile_read": (ci, [vp, ci, ctypes.c_char_p, dp, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ci)]),
     }
@@ -92,6 +93,7 @@ EXPORTED = [
     "bem_set_params", "bem_get_params", "bem_set_mean_color", "bem_sample_mean", "bem_eval",
     "bem_loss", "bem_vjp", "bem_jtj", "lm_step", "bem_sizes", "bem_boundary_values",
     "bem_launch_count", "bem_profile_enable", "bem_profile_read", "bem_gemm_bf16",
+    "bem_fastmath_eval",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -264,6 +266,16 @@ class BEM:
         self._check(_lib.bem_gemm_bf16(self.h, M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0),
                                        _ptr(D), N, _stream(stream)))
         return D
+
+    def fastmath(self, which: int, a, b=None, stream=None):
+        """(library approximation, CUDA accurate) of atan2 (0), log (1), log1p (2)."""
+        import torch
+        fast = torch.empty_like(a)
+        ref = torch.empty_like(a)
+        self._check(_lib.bem_fastmath_eval(self.h, which, a.numel(), _ptr(a),
+                                           _ptr(b) if b is not None else None, _ptr(fast),
+                                           _ptr(ref), _stream(stream)))
+        return fast, ref
 
     def profile(self, on: bool = True):
         self._check(_lib.bem_profile_enable(self.h, 1 if on else 0))

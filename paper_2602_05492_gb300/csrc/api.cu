@@ -131,6 +131,26 @@ __global__ void k_scale_norm(double* __restrict__ v, int n, double s, double* __
   }
 }
 
+// which = 0: atan2(a, b); 1: log(a); 2: log1p(a).  Library approximation and
+// CUDA's accurate float function side by side.
+__global__ void k_fastmath(int which, int64_t n, const float* __restrict__ a,
+                           const float* __restrict__ b, float* __restrict__ fast,
+                           float* __restrict__ ref) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x = a[i];
+  if (which == 0) {
+    fast[i] = fm_atan2(x, b[i]);
+    ref[i] = atan2f(x, b[i]);
+  } else if (which == 1) {
+    fast[i] = fm_log(x);
+    ref[i] = logf(x);
+  } else {
+    fast[i] = fm_log1p(x);
+    ref[i] = log1pf(x);
+  }
+}
+
 }  // namespace bem
 
 using namespace bem;
@@ -471,6 +491,21 @@ int bem_gemm_bf16(bem_ctx* c, int M, int N, int K, const void* A, int lda, const
     return rc;
   if (st) return fail(c, BEM_ETIMEDOUT, "tensor-core GEMM: a bounded device wait ran out");
   return BEM_OK;
+}
+
+int bem_fastmath_eval(bem_ctx* c, int which, int64_t n, const float* a, const float* b,
+                      float* out_fast, float* out_ref, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (which < 0 || which > 2 || n < 0 || (n > 0 && (!a || !out_fast || !out_ref || (which == 0 && !b))))
+    return fail(c, BEM_EINVAL, "bem_fastmath_eval: bad arguments");
+  int rc;
+  if ((rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  if (n > 0) {
+    k_fastmath<<<(unsigned)((n + 255) / 256), 256, 0, S(c)>>>(which, n, a, b, out_fast, out_ref);
+    BEM_LAUNCHED(c);
+  }
+  return cuda_check(c, cudaGetLastError(), "k_fastmath");
 }
 
 int bem_sizes(const bem_ctx* c, int* n_theta, int* n_panels, int* n_boundary) {

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fastmath.cuh"
+
 namespace bem {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -135,6 +137,34 @@ __device__ __forceinline__ LayerVals<T> layer_values(const Frame<T>& f, T eps_c2
   return v;
 }
 
+// Float versions: own transcendentals (fastmath.cuh), one rsqrt for both
+// h' and h/h', approximate divisions.
+template <>
+__device__ __forceinline__ LayerVals<float> layer_values<float>(const Frame<float>& f, float eps_c2,
+                                                               float eps_d2, bool same_eps) {
+  LayerVals<float> v;
+  const float hh = f.h * f.h;
+  const float hc2 = hh + eps_c2;
+  const float rc = rsqrtf(hc2);
+  const float hc = hc2 * rc;
+  const float tt = f.t1 * f.t2;
+  const float q1 = fmaf(f.t1, f.t1, hc2);
+  const float q2 = fmaf(f.t2, f.t2, hc2);
+  const float phic = fm_atan2(hc * f.L, hc2 + tt);
+  const float lg2 = fm_log(q2);
+  const float lp = fm_log1p(__fdividef(f.L * (f.t1 + f.t2), q1));
+  v.S = -(f.L * (lg2 - 2.f) + f.t1 * lp + 2.f * hc * phic) * float(kInv4Pi);
+  if (same_eps) {
+    v.Dl = -(f.h * rc) * phic * float(kInv2Pi);
+  } else {
+    const float hd2 = hh + eps_d2;
+    const float rd = rsqrtf(hd2);
+    const float phid = fm_atan2(hd2 * rd * f.L, hd2 + tt);
+    v.Dl = -(f.h * rd) * phid * float(kInv2Pi);
+  }
+  return v;
+}
+
 // Values and frame partials of both layers.
 template <typename T>
 struct LayerGrad {
@@ -183,6 +213,43 @@ __device__ __forceinline__ LayerGrad<T> layer_grad(const Frame<T>& f, T eps_c2, 
   return g;
 }
 
+template <>
+__device__ __forceinline__ LayerGrad<float> layer_grad<float>(const Frame<float>& f, float eps_c2,
+                                                             float eps_d2, bool same_eps) {
+  LayerGrad<float> g;
+  const float tt = f.t1 * f.t2;
+  const float hh = f.h * f.h;
+  const float hc2 = hh + eps_c2;
+  const float rc = rsqrtf(hc2);
+  const float hc = hc2 * rc;
+  const float q1 = fmaf(f.t1, f.t1, hc2);
+  const float q2 = fmaf(f.t2, f.t2, hc2);
+  const float phic = fm_atan2(hc * f.L, hc2 + tt);
+  const float lg2 = fm_log(q2);
+  const float lp = fm_log1p(__fdividef(f.L * (f.t1 + f.t2), q1));
+  const float lg1 = lg2 - lp;
+  g.S = -(f.L * (lg2 - 2.f) + f.t1 * lp + 2.f * hc * phic) * float(kInv4Pi);
+  g.S_t1 = lg1 * float(kInv4Pi);
+  g.S_t2 = -lg2 * float(kInv4Pi);
+  g.S_h = -(f.h * rc) * phic * float(kInv2Pi);
+  float hd2, rd, phid, r1, r2;
+  if (same_eps) {
+    hd2 = hc2; rd = rc; phid = phic; r1 = q1; r2 = q2;
+  } else {
+    hd2 = hh + eps_d2;
+    rd = rsqrtf(hd2);
+    phid = fm_atan2(hd2 * rd * f.L, hd2 + tt);
+    r1 = fmaf(f.t1, f.t1, hd2);
+    r2 = fmaf(f.t2, f.t2, hd2);
+  }
+  const float ir1 = __fdividef(1.f, r1), ir2 = __fdividef(1.f, r2);
+  g.Dl = -(f.h * rd) * phid * float(kInv2Pi);
+  g.D_t1 = f.h * ir1 * float(kInv2Pi);
+  g.D_t2 = -f.h * ir2 * float(kInv2Pi);
+  g.D_h = -(eps_d2 * phid * rd - hh * f.L * (hd2 - tt) * ir1 * ir2) * (rd * rd) * float(kInv2Pi);
+  return g;
+}
+
 // Chain rule from frame partials (F_t1, F_t2, F_h) to d/da, d/db.
 template <typename T>
 __device__ __forceinline__ void frame_to_endpoints(const Panel<T>& p, const Frame<T>& f, T Ft1,
@@ -205,6 +272,12 @@ template <typename T>
 __device__ __forceinline__ T seg_angle(T ax, T ay, T bx, T by, T x, T y) {
   T dax = ax - x, day = ay - y, dbx = bx - x, dby = by - y;
   return m_atan2(dax * dby - day * dbx, dax * dbx + day * dby);
+}
+template <>
+__device__ __forceinline__ float seg_angle<float>(float ax, float ay, float bx, float by, float x,
+                                                  float y) {
+  float dax = ax - x, day = ay - y, dbx = bx - x, dby = by - y;
+  return fm_atan2(dax * dby - day * dbx, dax * dbx + day * dby);
 }
 
 }  // namespace bem

@@ -1,0 +1,49 @@
+"""The library's float transcendentals against CUDA's accurate float functions
+(GPU only), over the ranges the pair formulas use."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def model():
+    import paper_2602_05492_gb300 as bg
+    return bg.BEM(precision=bg.BEM_MIXED)
+
+
+def _t(a):
+    return torch.tensor(np.asarray(a, np.float32), device="cuda:0")
+
+
+def test_atan2(model):
+    rng = np.random.default_rng(0)
+    ang = rng.uniform(-math.pi, math.pi, 200000)
+    r = 10.0 ** rng.uniform(-6, 1, ang.size)
+    y, x = r * np.sin(ang), r * np.cos(ang)
+    special = np.array([[1, 1], [1, -1], [-1, -1], [1e-7, -1], [-1e-7, -1], [1, 0], [0, 1],
+                        [3e-8, 2.0], [1.0, 1e-8]], np.float32)
+    y = np.concatenate([y, special[:, 0]])
+    x = np.concatenate([x, special[:, 1]])
+    fast, ref = model.fastmath(0, _t(y), _t(x))
+    err = (fast - ref).abs().max().item()
+    assert err < 3e-7, err
+
+
+def test_log(model):
+    x = 10.0 ** np.random.default_rng(1).uniform(-6, 1, 200000)
+    fast, ref = model.fastmath(1, _t(x))
+    err = ((fast - ref).abs() / torch.clamp(ref.abs(), min=1.0)).max().item()
+    assert err < 1e-6, err
+
+
+def test_log1p(model):
+    rng = np.random.default_rng(2)
+    z = np.concatenate([rng.uniform(-0.999, 10, 100000), rng.uniform(-0.3, 0.3, 100000),
+                        10.0 ** rng.uniform(-9, -1, 50000), -(10.0 ** rng.uniform(-9, -1, 50000))])
+    fast, ref = model.fastmath(2, _t(z))
+    rel = ((fast - ref).abs() / torch.clamp(ref.abs(), min=1e-30)).max().item()
+    assert rel < 2e-6, rel
