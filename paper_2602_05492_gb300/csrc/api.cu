@@ -227,7 +227,7 @@ void bem_destroy(bem_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   DevBuf* bufs[] = {&c->part, &c->part2, &c->loss, &c->gpart, &c->jrow, &c->phi, &c->Hc, &c->Mc,
                     &c->Dfc, &c->Fg, &c->lmK, &c->lmL, &c->lmLt, &c->lmW, &c->H, &c->g,
-                    &c->tcJ, &c->tcPart, &c->tcMt, &c->nearP, &c->nearS, &c->nearF};
+                    &c->tcJ, &c->tcPart, &c->tcMt, &c->nearP, &c->nearS, &c->nearF, &c->gwork};
   for (DevBuf* b : bufs) free_buf(*b);
   delete c;
 }
@@ -408,10 +408,17 @@ int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_tri
   double s0 = 0;
   if ((rc = cuda_check(c, cudaMemcpyAsync(&s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
     return rc;
-  if ((rc = adj_vjp(c, n, xy, resid, g))) return rc;
-  k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0 / double(n), c->d_scal + 1);
-  BEM_LAUNCHED(c);
-  if ((rc = jtj_build(c, n, xy, (double*)c->H.p))) return rc;
+  if (jtj_gives_gradient(c)) {
+    // g = (1/n) J^T r from the J rows that also build H (Eq. (lossjacobian))
+    if ((rc = jtj_build(c, n, xy, (double*)c->H.p, resid, g))) return rc;
+    k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0, c->d_scal + 1);
+    BEM_LAUNCHED(c);
+  } else {
+    if ((rc = adj_vjp(c, n, xy, resid, g))) return rc;
+    k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0 / double(n), c->d_scal + 1);
+    BEM_LAUNCHED(c);
+    if ((rc = jtj_build(c, n, xy, (double*)c->H.p))) return rc;
+  }
   double gn2 = 0;
   if ((rc = cuda_check(c, cudaMemcpyAsync(&gn2, c->d_scal + 1, 8, cudaMemcpyDeviceToHost, S(c)), "norm")) ||
       (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "sync")))

@@ -85,7 +85,7 @@ struct bem_ctx {
 
   // growable scratch
   bem::DevBuf part, part2, loss, gpart, jrow, phi, Hc, Mc, Dfc, Fg, lmK, lmL, lmLt, lmW, H, g,
-      tcJ, tcPart, tcMt, nearP, nearS, nearF;
+      tcJ, tcPart, tcMt, nearP, nearS, nearF, gwork;
   bool pbins_valid = false;        // panel -> cell bins match the current panels
 };
 
@@ -136,7 +136,11 @@ int near_adjoint(bem_ctx* c, int64_t n, const float* xy, const float* w, double*
 int adj_vjp(bem_ctx* c, int64_t n, const void* xy, const void* resid, double* grad);
 
 // ---- Gauss-Newton matrix (k_jtj.cu) ----------------------------------------------
-int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H);
+// H = (1/n) J^T J; with resid (sample type [n][3]) and g also g = (1/n) J^T r
+// when jtj_gives_gradient() (tensor-core modes of the mixed path)
+int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H, const void* resid = nullptr,
+              double* g = nullptr);
+bool jtj_gives_gradient(const bem_ctx* c);
 
 // ---- tensor-core contractions (k_gemm_tc.cu) ----------------------------------------
 int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const void* B, int ldb,

@@ -33,18 +33,34 @@ __global__ void k_phi_rows(const T* __restrict__ xy, int ns, const T* __restrict
 
 // F rows of ns points for one curve per blockIdx.y.  TR = false: double
 // F[c][s][nc]; TR = true: float F^T[c*nc + col][s] with row stride ldf.
+// Panel k of the curve runs from vertex k to vertex k+1 (vertex v = B(v/K)),
+// so the endpoint derivatives are first summed per vertex (panel k's start
+// plus panel k-1's end) and then spread to the control points with the
+// Bernstein weights B_j(v/K), read with the mid-parameter weights from a
+// per-block shared-memory table.
+constexpr int kFrowsTable = 256;   // panels per curve covered by the weight table
+
 template <typename T, bool SAME, bool TR>
 __global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __restrict__ pan,
                         const int* __restrict__ off, const int* __restrict__ Kc,
                         const uint8_t* __restrict__ closed, int C, T ec2, T ed2,
                         void* __restrict__ Fout, int ldf) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  int i = blockIdx.y;
+  __shared__ T wtab[kFrowsTable][8];     // B_j(k/K), B_j((k+1/2)/K)
+  const int i = blockIdx.y;
+  const int K = Kc[i];
+  for (int e = threadIdx.x; e < min(K, kFrowsTable) * 4; e += blockDim.x) {
+    const int k = e / 4, j = e % 4;
+    wtab[k][j] = bern3(j, T(k) / T(K));
+    wtab[k][4 + j] = bern3(j, (T(k) + T(0.5)) / T(K));
+  }
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ns) return;
-  int nc = 16 * C, K = Kc[i];
-  T x = xy[2 * s], y = xy[2 * s + 1];
+  const int nc = 16 * C;
+  const T x = xy[2 * s], y = xy[2 * s + 1];
   T pos[4][2][3];
   T cd[4], cs[4];
+  T carry[2][3];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     cd[j] = 0; cs[j] = 0;
@@ -53,31 +69,59 @@ __global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __rest
 #pragma unroll
       for (int c = 0; c < 3; ++c) pos[j][e][c] = 0;
   }
+#pragma unroll
+  for (int e = 0; e < 2; ++e)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) carry[e][c] = 0;
   for (int k = 0; k < K; ++k) {
     const Panel<T> p = pan[off[i] + k];
-    T t0 = T(k) / T(K), t1 = T(k + 1) / T(K), tm = (T(k) + T(0.5)) / T(K);
-    T wa[4], wb[4], wm[4];
+    T wv[4], wm[4];
+    if (k < kFrowsTable) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { wa[j] = bern3(j, t0); wb[j] = bern3(j, t1); wm[j] = bern3(j, tm); }
+      for (int j = 0; j < 4; ++j) { wv[j] = wtab[k][j]; wm[j] = wtab[k][4 + j]; }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { wv[j] = bern3(j, T(k) / T(K)); wm[j] = bern3(j, (T(k) + T(0.5)) / T(K)); }
+    }
     Frame<T> f = frame(p, x, y);
     LayerGrad<T> g = layer_grad(f, ec2, ed2, SAME);
 #pragma unroll
     for (int j = 0; j < 4; ++j) { cd[j] -= wm[j] * g.Dl; cs[j] += wm[j] * g.S; }
-    if (!(p.L > T(0))) continue;
+    T da[2][3], db[2][3];
+    if (p.L > T(0)) {
+      T Dax, Day, Dbx, Dby, Sax, Say, Sbx, Sby;
+      frame_to_endpoints(p, f, g.D_t1, g.D_t2, g.D_h, Dax, Day, Dbx, Dby);
+      frame_to_endpoints(p, f, g.S_t1, g.S_t2, g.S_h, Sax, Say, Sbx, Sby);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T Ft1 = -p.wd[c] * g.D_t1 + p.wc[c] * g.S_t1;
-      T Ft2 = -p.wd[c] * g.D_t2 + p.wc[c] * g.S_t2;
-      T Fh = -p.wd[c] * g.D_h + p.wc[c] * g.S_h;
-      T dax, day, dbx, dby;
-      frame_to_endpoints(p, f, Ft1, Ft2, Fh, dax, day, dbx, dby);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        pos[j][0][c] += wa[j] * dax + wb[j] * dbx;
-        pos[j][1][c] += wa[j] * day + wb[j] * dby;
+      for (int c = 0; c < 3; ++c) {
+        const T a = -p.wd[c], b = p.wc[c];
+        da[0][c] = a * Dax + b * Sax;
+        da[1][c] = a * Day + b * Say;
+        db[0][c] = a * Dbx + b * Sbx;
+        db[1][c] = a * Dby + b * Sby;
       }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { da[e][c] = 0; db[e][c] = 0; }
     }
+    // vertex k: start of panel k and end of panel k-1
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T v = da[e][c] + carry[e][c];
+        carry[e][c] = db[e][c];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pos[j][e][c] += wv[j] * v;
+      }
   }
+  // vertex K = B(1) = control point 3
+#pragma unroll
+  for (int e = 0; e < 2; ++e)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pos[3][e][c] += carry[e][c];
   if (closed[i]) {
 #pragma unroll
     for (int e = 0; e < 2; ++e)
@@ -157,6 +201,126 @@ __global__ void k_mt_x3(const double* __restrict__ Mc, int Nb, int nc, float* __
   float h = tf32_round((float)v);
   hi[(size_t)row * Nb + j] = h;
   lo[(size_t)row * Nb + j] = tf32_round((float)(v - (double)h));
+}
+
+// Phi rows of a chunk of samples written from the segment side: thread j
+// (boundary segment) walks the block's sample slice, writes phi_j(x_s)/(2 pi)
+// into row s (bf16, or tf32 hi/lo) and, when residuals are given, sums
+// q_j += phi_j(x_s)/(2 pi) r_s into a per-slice double partial qpart[slice][j][3].
+template <bool X3>
+__global__ void __launch_bounds__(128) k_phi_q(const float* __restrict__ xy, const float* __restrict__ r,
+                                               int m, int slice_len, const float* __restrict__ vert,
+                                               int Nb, void* __restrict__ phi0,
+                                               void* __restrict__ phi1, double* __restrict__ qpart) {
+  __shared__ float2 sx[128];
+  __shared__ float sr[3][128];
+  const int j = blockIdx.x * 128 + threadIdx.x;
+  const int s0 = blockIdx.y * slice_len, s1 = min(m, s0 + slice_len);
+  const bool live = j < Nb;
+  float ax = 0, ay = 0, bx = 0, by = 0;
+  if (live) { ax = vert[2 * j]; ay = vert[2 * j + 1]; bx = vert[2 * j + 2]; by = vert[2 * j + 3]; }
+  double q0 = 0, q1 = 0, q2 = 0;
+  for (int base = s0; base < s1; base += 128) {
+    const int cnt = min(128, s1 - base);
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      const int s = base + threadIdx.x;
+      sx[threadIdx.x] = make_float2(xy[2 * s], xy[2 * s + 1]);
+      if (r) {
+        sr[0][threadIdx.x] = r[3 * s];
+        sr[1][threadIdx.x] = r[3 * s + 1];
+        sr[2][threadIdx.x] = r[3 * s + 2];
+      }
+    }
+    __syncthreads();
+    if (!live) continue;
+    float a0 = 0, a1 = 0, a2 = 0;
+    for (int k = 0; k < cnt; ++k) {
+      const float phi = seg_angle(ax, ay, bx, by, sx[k].x, sx[k].y) * float(kInv2Pi);
+      const size_t o = (size_t)(base + k) * Nb + j;
+      if (X3) {
+        const float h = tf32_round(phi);
+        ((float*)phi0)[o] = h;
+        ((float*)phi1)[o] = tf32_round(phi - h);
+      } else {
+        ((__nv_bfloat16*)phi0)[o] = __float2bfloat16_rn(phi);
+      }
+      if (r) { a0 += phi * sr[0][k]; a1 += phi * sr[1][k]; a2 += phi * sr[2][k]; }
+    }
+    q0 += a0; q1 += a1; q2 += a2;
+  }
+  if (live && r && qpart) {
+    double* o = qpart + ((size_t)blockIdx.y * Nb + j) * 3;
+    o[0] = q0; o[1] = q1; o[2] = q2;
+  }
+}
+
+// out[t] = sum over k of part[k][t] (fixed order)
+__global__ void k_sum_rows(const double* __restrict__ part, int nparts, int m, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  double s = 0;
+  for (int k = 0; k < nparts; ++k) s += part[(size_t)k * m + t];
+  out[t] = s;
+}
+
+// gpart[row] = sum over the chunk's samples of F^T[row][s] r[s][row / nc]
+// (double accumulation); one warp per row of F^T
+__global__ void k_ft_gemv(const float* __restrict__ F, int ldf, int rows, int nc, int m,
+                          const float* __restrict__ r, double* __restrict__ gpart) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const int c = row / nc;
+  const float* f = F + (size_t)row * ldf;
+  double acc = 0;
+  for (int s0 = 0; s0 < m; s0 += 32 * 8) {
+    float a = 0;
+    for (int u = 0; u < 8; ++u) {
+      const int s = s0 + u * 32 + lane;
+      if (s < m) a += f[s] * r[3 * s + c];
+    }
+    acc += a;
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) gpart[row] = acc;
+}
+
+// g[theta] = scale * sum over channels of (handle part + boundary part) of
+// channel-local column col_c(theta); gh[c*nc + col] summed over chunks,
+// boundary part gb[c*nc + col] = sum_i Df[c][i][col] lambda[i][c]
+__global__ void k_g_boundary(const double* __restrict__ Df, int Nb, int nc,
+                             const double* __restrict__ lam, double* __restrict__ gb) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;   // c*nc + col
+  const int lane = threadIdx.x & 31;
+  if (row >= 3 * nc) return;
+  const int c = row / nc, col = row % nc;
+  double acc = 0;
+  for (int i = lane; i < Nb; i += 32) acc += Df[((size_t)c * Nb + i) * nc + col] * lam[3 * i + c];
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) gb[row] = acc;
+}
+
+__global__ void k_g_assemble(const double* __restrict__ gparts, int nparts, int stride,
+                             const double* __restrict__ gb, int C, double scale,
+                             double* __restrict__ g) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = 32 * C, nc = 16 * C;
+  if (t >= nth) return;
+  const int h = t / 8, comp = t % 8;
+  double s = 0;
+  for (int c = 0; c < 3; ++c) {
+    int col;
+    if (comp < 2) col = 2 * h + comp;
+    else if (comp < 5) col = comp - 2 == c ? 8 * C + h : -1;
+    else col = comp - 5 == c ? 12 * C + h : -1;
+    if (col < 0) continue;
+    const int row = c * nc + col;
+    double v = gb[row];
+    for (int k = 0; k < nparts; ++k) v += gparts[(size_t)k * stride + row];
+    s += v;
+  }
+  g[t] = scale * s;
 }
 
 // Mt[c*nc + col][j] = bf16(Mc[c][j][col])
@@ -317,9 +481,15 @@ static int jtj_stacked_rhs(bem_ctx* c) {
 // Mixed precision: J^T rows and the Gram blocks on the tensor cores, either
 // in bf16 (fp32 accumulate) or in the 3xtf32 split; Gram blocks accumulate
 // per K slice in fp32 and the slices are summed in double.
-static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3) {
+// With residuals r (float [n][3]) it also forms the gradient g = (1/n) J^T r
+// from the same J rows (Eq. (lossjacobian)): the handle part as a double
+// GEMV over F^T per chunk, the boundary part as q^T M_c = (A^+T q)^T Df_c
+// with q = sum_s phi_s r_s summed while the Phi rows are written.
+static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
+                  const float* resid, double* gout) {
   int rc;
   int C = c->sc.C, nc = 16 * C, Nb = c->bd.Nb, nth = c->sc.nth;
+  const bool want_g = resid && gout;
   if ((rc = jtj_stacked_rhs<float>(c))) return rc;
   const size_t es = x3 ? 2 * sizeof(float) : sizeof(__nv_bfloat16);   // bytes per element (all parts)
   // M_c^T, [3 nc][Nb]
@@ -335,14 +505,22 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3)
   BEM_LAUNCHED(c);
   // per-chunk buffers: Phi [m][Nb], F^T f32 [3nc][ld], J^T [3nc][ld]
   const int64_t chunk = std::min<int64_t>(std::max<int64_t>(n, 1), 262144);
+  const int nchunks = (int)((n + chunk - 1) / chunk);
   const int ld = (int)((chunk + 63) / 64 * 64);
   const size_t phi_part = (x3 ? 4 : 2) * (size_t)chunk * Nb;
   const size_t phi_b = (x3 ? 2 : 1) * phi_part;
   const size_t f_b = sizeof(float) * 3 * (size_t)nc * ld;
   const size_t j_part = (x3 ? 4 : 2) * 3 * (size_t)nc * ld;
   const size_t j_b = (x3 ? 2 : 1) * j_part;
+  // gradient work: per chunk handle partial [3nc], q partials per slice
+  const int qslices = (int)std::max<int64_t>(1, std::min<int64_t>(64, (chunk + 4095) / 4096));
+  const int qslice_len = (int)((chunk + qslices - 1) / qslices);
+  const size_t gh_b = sizeof(double) * (size_t)std::max(nchunks, 1) * 3 * nc;
+  const size_t q_b = sizeof(double) * (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
+  const size_t gb_b = sizeof(double) * 3 * (size_t)nc;
   if ((rc = grow(c, c->jrow, phi_b + 256 + f_b + 256))) return rc;
   if ((rc = grow(c, c->tcJ, j_b))) return rc;
+  if (want_g && (rc = grow(c, c->gwork, gh_b + q_b + gb_b + 256))) return rc;
   const int splits = tc_syrk_splits(nc, x3);
   const size_t part_b = sizeof(float) * (size_t)splits * 3 * nc * nc;
   if ((rc = grow(c, c->tcPart, part_b))) return rc;
@@ -351,22 +529,38 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3)
   float* F = (float*)((char*)c->jrow.p + (phi_b + 255) / 256 * 256);
   void* J[2] = {c->tcJ.p, (char*)c->tcJ.p + j_part};
   float* part = (float*)c->tcPart.p;
+  double* gh = (double*)c->gwork.p;
+  double* qp = gh + (size_t)std::max(nchunks, 1) * 3 * nc;
+  double* gb = qp + (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
   if ((rc = cuda_check(c, cudaMemsetAsync(part, 0, part_b, S(c)), "memset"))) return rc;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
-  for (int64_t s0 = 0; s0 < n; s0 += chunk) {
+  int ci = 0;
+  for (int64_t s0 = 0; s0 < n; s0 += chunk, ++ci) {
     const int m = (int)std::min<int64_t>(chunk, n - s0);
     {
       ProfScope _pp(c, "k_phi_rows");
-      const unsigned blocks = (unsigned)(((int64_t)m * Nb + 255) / 256);
+      const int sl = want_g ? qslices : (int)std::max<int64_t>(1, std::min<int64_t>(64, (m + 4095) / 4096));
+      const int len = (m + sl - 1) / sl;
+      dim3 grid((Nb + 127) / 128, (m + len - 1) / len);
+      double* q = want_g ? qp + (size_t)ci * qslices * Nb * 3 : nullptr;
+      const float* rr = want_g ? resid + 3 * s0 : nullptr;
+      if (want_g && (int)grid.y < qslices)      // unused slices of a short chunk hold zeros
+        cudaMemsetAsync(q, 0, sizeof(double) * qslices * Nb * 3, S(c));
       if (x3)
-        k_phi_rows_x3<<<blocks, 256, 0, S(c)>>>(xy + 2 * s0, m, c->bd.d_vert32, Nb,
-                                                (float*)phi[0], (float*)phi[1]);
+        k_phi_q<true><<<grid, 128, 0, S(c)>>>(xy + 2 * s0, rr, m, len, c->bd.d_vert32, Nb,
+                                              (void*)phi[0], (void*)phi[1], q);
       else
-        k_phi_rows_bf16<<<blocks, 256, 0, S(c)>>>(xy + 2 * s0, m, c->bd.d_vert32, Nb,
-                                                  (__nv_bfloat16*)phi[0]);
+        k_phi_q<false><<<grid, 128, 0, S(c)>>>(xy + 2 * s0, rr, m, len, c->bd.d_vert32, Nb,
+                                               (void*)phi[0], nullptr, q);
       BEM_LAUNCHED(c);
     }
     launch_frows<float, true>(c, xy + 2 * s0, m, F, ld);
+    if (want_g) {
+      ProfScope _pg(c, "k_ft_gemv");
+      k_ft_gemv<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>(F, ld, 3 * nc, nc, m, resid + 3 * s0,
+                                                    gh + (size_t)ci * 3 * nc);
+      BEM_LAUNCHED(c);
+    }
     if ((rc = tc_jrows(c, x3, 3 * nc, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld))) return rc;
     const void* Jc[2] = {J[0], J[1]};
     if ((rc = tc_syrk(c, x3, nc, m, Jc, ld, part, splits))) return rc;
@@ -376,6 +570,17 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3)
   k_h_assemble<<<dim3((nth + 127) / 128, nth), 128, 0, S(c)>>>((const double*)c->Hc.p, C,
                                                                 n > 0 ? 1.0 / double(n) : 0.0, Hout);
   c->launches += 2;
+  if (want_g) {
+    // q = sum over chunks and slices (fixed order) -> lambda = (A^+)^T q
+    const int nq = nchunks * qslices;
+    k_sum_rows<<<(3 * Nb + 255) / 256, 256, 0, S(c)>>>(qp, nq, 3 * Nb, c->d_q);
+    BEM_LAUNCHED(c);
+    if ((rc = la_apply3_refined(c, c->bd.d_WT32, c->bd.d_A, c->d_q, c->d_lb, true))) return rc;
+    k_g_boundary<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>((const double*)c->Dfc.p, Nb, nc, c->d_lb, gb);
+    k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(gh, nchunks, 3 * nc, gb, C,
+                                                       n > 0 ? 1.0 / double(n) : 0.0, gout);
+    c->launches += 2;
+  }
   if ((rc = cuda_check(c, cudaGetLastError(), "jtj tc"))) return rc;
   int st = 0;
   if ((rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost,
@@ -386,11 +591,18 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3)
   return BEM_OK;
 }
 
-int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H) {
+int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H, const void* resid, double* g) {
   if (c->opts.precision == BEM_FP64) return jtj_t<double>(c, n, (const double*)xy, H);
-  if (c->opts.jtj_mode == BEM_JTJ_BF16) return jtj_tc(c, n, (const float*)xy, H, false);
-  if (c->opts.jtj_mode == BEM_JTJ_3XTF32) return jtj_tc(c, n, (const float*)xy, H, true);
+  if (c->opts.jtj_mode == BEM_JTJ_BF16)
+    return jtj_tc(c, n, (const float*)xy, H, false, (const float*)resid, g);
+  if (c->opts.jtj_mode == BEM_JTJ_3XTF32)
+    return jtj_tc(c, n, (const float*)xy, H, true, (const float*)resid, g);
   return jtj_t<float>(c, n, (const float*)xy, H);
+}
+
+bool jtj_gives_gradient(const bem_ctx* c) {
+  return c->opts.precision == BEM_MIXED &&
+         (c->opts.jtj_mode == BEM_JTJ_BF16 || c->opts.jtj_mode == BEM_JTJ_3XTF32);
 }
 
 }  // namespace bem

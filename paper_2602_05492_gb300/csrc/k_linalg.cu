@@ -396,43 +396,45 @@ __global__ void k_constraint_cols(int n, const double* __restrict__ a, double* _
   for (int c = 0; c < 3; ++c) cons[4 * i + 1 + c] = (comp == 5 + c) ? a[h] : 0.0;
 }
 
-// Unblocked Cholesky of the nb x nb diagonal block at (k0,k0) in shared memory.
+// Cholesky of the nb x nb (nb <= 32) diagonal block at (k0,k0): one warp,
+// lane r owns row r of the block in shared memory; no block-wide barriers.
 __global__ void k_potrf_diag(double* __restrict__ Km, int n, int k0, int nb,
                              int* __restrict__ status) {
   __shared__ double T[32][33];
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    int r = e / nb, q = e % nb;
-    T[r][q] = Km[(size_t)(k0 + r) * n + k0 + q];
-  }
-  __syncthreads();
+  const int lane = threadIdx.x;
+  for (int q = 0; q < nb; ++q) T[lane][q] = lane < nb ? Km[(size_t)(k0 + lane) * n + k0 + q] : 0.0;
+  __syncwarp();
   for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) {
-      double d = T[j][j];
-      if (!(d > 0.0)) { *status = 1; d = 1.0; }
-      T[j][j] = sqrt(d);
+    double d = T[j][j];
+    if (!(d > 0.0)) {
+      if (lane == 0) *status = 1;
+      d = 1.0;
     }
-    __syncthreads();
-    for (int r = j + 1 + threadIdx.x; r < nb; r += blockDim.x) T[r][j] /= T[j][j];
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-      int r = e / nb, q = e % nb;
-      if (q > j && r >= q) T[r][q] -= T[r][j] * T[q][j];
+    const double ri = rsqrt(d);        // 1/sqrt(pivot)
+    __syncwarp();
+    if (lane == j) T[j][j] = d * ri;
+    if (lane > j && lane < nb) T[lane][j] *= ri;
+    __syncwarp();
+    if (lane > j && lane < nb) {
+      const double lrj = T[lane][j];
+      for (int q = j + 1; q <= lane; ++q) T[lane][q] -= lrj * T[q][j];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    int r = e / nb, q = e % nb;
-    Km[(size_t)(k0 + r) * n + k0 + q] = (q <= r) ? T[r][q] : 0.0;
-  }
+  if (lane < nb)
+    for (int q = 0; q < nb; ++q) Km[(size_t)(k0 + lane) * n + k0 + q] = q <= lane ? T[lane][q] : 0.0;
 }
 
 // rows i >= k0+nb of the panel: L_i = A_i L_kk^-T (forward substitution per row)
 __global__ void k_trsm_rows(double* __restrict__ Km, int n, int k0, int nb) {
   __shared__ double Lk[32][33];
+  __shared__ double inv[32];
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     int r = e / nb, q = e % nb;
     Lk[r][q] = Km[(size_t)(k0 + r) * n + k0 + q];
   }
+  __syncthreads();
+  if (threadIdx.x < nb) inv[threadIdx.x] = 1.0 / Lk[threadIdx.x][threadIdx.x];
   __syncthreads();
   int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -441,7 +443,7 @@ __global__ void k_trsm_rows(double* __restrict__ Km, int n, int k0, int nb) {
   for (int j = 0; j < nb; ++j) {
     double s = row[j];
     for (int l = 0; l < j; ++l) s -= x[l] * Lk[j][l];
-    x[j] = s / Lk[j][j];
+    x[j] = s * inv[j];
   }
   for (int j = 0; j < nb; ++j) row[j] = x[j];
 }
@@ -454,32 +456,90 @@ __global__ void k_transpose_lower(const double* __restrict__ Km, int n, double* 
   Lt[(size_t)j * n + i] = (j <= i) ? Km[(size_t)i * n + j] : 0.0;
 }
 
-// Solve L L^T X = R for R[n][4] in place (one block).  Lt rows give the
-// columns of L for the forward sweep; L rows give the columns of L^T.
-__global__ void k_chol_solve4(const double* __restrict__ L, const double* __restrict__ Lt, int n,
-                              double* __restrict__ R) {
-  __shared__ double xi[4];
-  for (int i = 0; i < n; ++i) {
-    if (threadIdx.x < 4) xi[threadIdx.x] = R[4 * i + threadIdx.x] / L[(size_t)i * n + i];
-    __syncthreads();
-    if (threadIdx.x < 4) R[4 * i + threadIdx.x] = xi[threadIdx.x];
-    const double* col = Lt + (size_t)i * n;    // L[j][i] = Lt[i][j]
-    for (int j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
-      double l = col[j];
-      for (int r = 0; r < 4; ++r) R[4 * j + r] -= l * xi[r];
+// Triangular solves with four right-hand sides R[n][4], blocked by 32 rows,
+// column oriented: a one-warp kernel solves the 32 x 32 diagonal block
+// (lane = row), then a kernel over all CTAs subtracts that block's
+// contribution from every remaining row.  Forward sweep with L (rows of L),
+// back sweep with L^T (rows of Lt).
+
+// forward: diagonal block [kb, kb+nb) of L y = R
+__global__ void k_trsv_diag_fwd(const double* __restrict__ L, int n, int kb, int nb,
+                                double* __restrict__ R) {
+  const int lane = threadIdx.x, i = kb + lane;
+  const bool in = lane < nb;
+  double r[4];
+  for (int q = 0; q < 4; ++q) r[q] = in ? R[4 * i + q] : 0.0;
+  for (int k = 0; k < nb; ++k) {
+    double y[4];
+    if (lane == k) {
+      const double inv = 1.0 / L[(size_t)i * n + i];
+      for (int q = 0; q < 4; ++q) r[q] *= inv;
     }
-    __syncthreads();
+    for (int q = 0; q < 4; ++q) y[q] = __shfl_sync(0xffffffffu, r[q], k);
+    if (in && lane > k) {
+      const double l = L[(size_t)i * n + kb + k];
+      for (int q = 0; q < 4; ++q) r[q] -= l * y[q];
+    }
   }
-  for (int i = n - 1; i >= 0; --i) {
-    if (threadIdx.x < 4) xi[threadIdx.x] = R[4 * i + threadIdx.x] / L[(size_t)i * n + i];
-    __syncthreads();
-    if (threadIdx.x < 4) R[4 * i + threadIdx.x] = xi[threadIdx.x];
-    const double* rowi = L + (size_t)i * n;    // L^T[j][i] = L[i][j]
-    for (int j = threadIdx.x; j < i; j += blockDim.x) {
-      double l = rowi[j];
-      for (int r = 0; r < 4; ++r) R[4 * j + r] -= l * xi[r];
+  if (in)
+    for (int q = 0; q < 4; ++q) R[4 * i + q] = r[q];
+}
+
+// back: diagonal block [kb, kb+nb) of L^T x = R (upper triangular rows of Lt)
+__global__ void k_trsv_diag_bwd(const double* __restrict__ Lt, int n, int kb, int nb,
+                                double* __restrict__ R) {
+  const int lane = threadIdx.x, i = kb + lane;
+  const bool in = lane < nb;
+  double r[4];
+  for (int q = 0; q < 4; ++q) r[q] = in ? R[4 * i + q] : 0.0;
+  for (int k = nb - 1; k >= 0; --k) {
+    double y[4];
+    if (lane == k) {
+      const double inv = 1.0 / Lt[(size_t)i * n + i];
+      for (int q = 0; q < 4; ++q) r[q] *= inv;
     }
-    __syncthreads();
+    for (int q = 0; q < 4; ++q) y[q] = __shfl_sync(0xffffffffu, r[q], k);
+    if (in && lane < k) {
+      const double l = Lt[(size_t)i * n + kb + k];
+      for (int q = 0; q < 4; ++q) r[q] -= l * y[q];
+    }
+  }
+  if (in)
+    for (int q = 0; q < 4; ++q) R[4 * i + q] = r[q];
+}
+
+// R[i] -= M[i][kb..kb+nb) . R[kb..kb+nb) for the rows i in [r0, r1)
+// (M = L for the forward sweep, rows below the block; M = Lt for the back
+// sweep, rows above it).  One warp per row.
+__global__ void k_trsv_update(const double* __restrict__ M, int n, int kb, int nb, int r0, int r1,
+                              double* __restrict__ R) {
+  const int row = r0 + blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= r1) return;
+  double s[4] = {0, 0, 0, 0};
+  if (lane < nb) {
+    const double m = M[(size_t)row * n + kb + lane];
+    for (int q = 0; q < 4; ++q) s[q] = m * R[4 * (kb + lane) + q];
+  }
+  for (int o = 16; o; o >>= 1)
+    for (int q = 0; q < 4; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+  if (lane == 0)
+    for (int q = 0; q < 4; ++q) R[4 * row + q] -= s[q];
+}
+
+static void chol_solve4(bem_ctx* c, const double* L, const double* Lt, int n, double* R) {
+  for (int kb = 0; kb < n; kb += 32) {
+    const int nb = min(32, n - kb);
+    k_trsv_diag_fwd<<<1, 32, 0, S(c)>>>(L, n, kb, nb, R);
+    const int r0 = kb + nb;
+    if (r0 < n) k_trsv_update<<<(n - r0 + 7) / 8, 256, 0, S(c)>>>(L, n, kb, nb, r0, n, R);
+    c->launches += 2;
+  }
+  for (int kb = (n - 1) / 32 * 32; kb >= 0; kb -= 32) {
+    const int nb = min(32, n - kb);
+    k_trsv_diag_bwd<<<1, 32, 0, S(c)>>>(Lt, n, kb, nb, R);
+    if (kb > 0) k_trsv_update<<<(kb + 7) / 8, 256, 0, S(c)>>>(Lt, n, kb, nb, 0, kb, R);
+    c->launches += 2;
   }
 }
 
@@ -559,14 +619,19 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
   double* gn = mx + 1;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
   ProfScope _ps(c, "lm_solve");
-  k_diag_max<<<1, 1024, 0, S(c)>>>(H, n, mx);
   dim3 grid((n + 127) / 128, n);
-  k_lm_build<<<grid, 128, 0, S(c)>>>(H, g, n, c->sc.C, c->sc.d_closed, c->d_compat, mx, lam, Km, R);
-  c->launches += 2;
+  {
+    ProfScope _pb(c, "lm_build");
+    k_diag_max<<<1, 1024, 0, S(c)>>>(H, n, mx);
+    k_lm_build<<<grid, 128, 0, S(c)>>>(H, g, n, c->sc.C, c->sc.d_closed, c->d_compat, mx, lam, Km, R);
+    c->launches += 2;
+  }
   const int NB = 32;
+  {
+  ProfScope _pc(c, "lm_cholesky");
   for (int k0 = 0; k0 < n; k0 += NB) {
     int nb = n - k0 < NB ? n - k0 : NB;
-    k_potrf_diag<<<1, 256, 0, S(c)>>>(Km, n, k0, nb, c->d_status);
+    k_potrf_diag<<<1, 32, 0, S(c)>>>(Km, n, k0, nb, c->d_status);
     BEM_LAUNCHED(c);
     int rest = n - k0 - nb;
     if (rest > 0) {
@@ -577,9 +642,13 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
       la_dgemm(c, false, true, rest, rest, nb, -1.0, Lp, n, Lp, n, 1.0, Ct, n);
     }
   }
-  k_transpose_lower<<<grid, 128, 0, S(c)>>>(Km, n, Lt);
-  k_chol_solve4<<<1, 1024, 0, S(c)>>>(Km, Lt, n, R);
-  c->launches += 2;
+  }
+  {
+    ProfScope _pt(c, "lm_trisolve");
+    k_transpose_lower<<<grid, 128, 0, S(c)>>>(Km, n, Lt);
+    BEM_LAUNCHED(c);
+    chol_solve4(c, Km, Lt, n, R);
+  }
   // the constraint columns are needed again for the Schur complement
   k_constraint_cols<<<(n + 255) / 256, 256, 0, S(c)>>>(n, c->d_compat, cons);
   BEM_LAUNCHED(c);

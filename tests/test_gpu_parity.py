@@ -211,6 +211,8 @@ def test_lm_step_mixed(cfg1, mode):
     if res["accepted"]:
         assert res["loss_after"] == pytest.approx(o.loss(th, sub, tsub), rel=1e-4)
     want = o.lm_step(sc.theta_init, sub, tsub, 1e-3)
+    # gradient of the step (from the same J rows as H) against the oracle's
+    assert res["grad_norm"] == pytest.approx(np.linalg.norm(want["g"]), rel=1e-4)
     assert res["accepted"] == want["accepted"]
     assert res["loss_after"] == pytest.approx(want["loss_after"], rel=2e-2 if mode == "bf16" else 1e-4)
 
