@@ -169,6 +169,29 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
   umma::fence_after();
   const int r = warp * 32 + lane;     // row of the tile owned by this thread
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  // bf16 J rows: the stage ring is free once the accumulator is complete;
+  // F's 128 x 128 tile is staged there with coalesced loads (row stride 129
+  // floats keeps the per-row reads below free of bank conflicts)
+  float* fs = reinterpret_cast<float*>(smem);
+  if (!X3 && g.mode == EPI_JROWS) {
+    for (int e = threadIdx.x; e < BM * (BN / 4); e += 128) {
+      const int rr = e / (BN / 4), cc = (e % (BN / 4)) * 4;
+      const int row = arow + rr, col = brow + cc;
+      float4 fv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row < g.M) {
+        const float* src = g.F + (size_t)row * g.ldf + col;
+        if (col + 3 < g.N) fv = *reinterpret_cast<const float4*>(src);
+        else {
+          if (col < g.N) fv.x = src[0];
+          if (col + 1 < g.N) fv.y = src[1];
+          if (col + 2 < g.N) fv.z = src[2];
+        }
+      }
+      float* d = fs + rr * 129 + cc;
+      d[0] = fv.x; d[1] = fv.y; d[2] = fv.z; d[3] = fv.w;
+    }
+    __syncthreads();
+  }
 #pragma unroll 1
   for (int cb = 0; cb < BN; cb += 32) {
     float v[32];
@@ -200,26 +223,16 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
           }
       }
     } else if (g.mode == EPI_JROWS) {
-      const int row = arow + r;
-      if (row < g.M) {
-        const float* f = g.F + (size_t)row * g.ldf + brow + cb;
-        __nv_bfloat16* o = g.J + (size_t)row * g.ldj + brow + cb;
-        if (brow + cb + 32 <= g.N) {
+      // F row r of the tile was staged in shared memory (fs, 129-float rows);
+      // this chunk's F is read before its bf16 result overwrites the front
+      // of the same row (fs bytes 64 cb .. 64 cb + 63 <= F bytes of chunk cb)
+      float* fr = fs + r * 129;
+      __nv_bfloat16* jr = reinterpret_cast<__nv_bfloat16*>(fr);
+      float f[32];
 #pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            float4 fv = *reinterpret_cast<const float4*>(f + j);
-            __nv_bfloat162 p0 = __floats2bfloat162_rn(v[j] + fv.x, v[j + 1] + fv.y);
-            __nv_bfloat162 p1 = __floats2bfloat162_rn(v[j + 2] + fv.z, v[j + 3] + fv.w);
-            uint2 w;
-            w.x = *reinterpret_cast<uint32_t*>(&p0);
-            w.y = *reinterpret_cast<uint32_t*>(&p1);
-            *reinterpret_cast<uint2*>(o + j) = w;
-          }
-        } else {
-          for (int j = 0; j < 32; ++j)
-            if (brow + cb + j < g.N) o[j] = __float2bfloat16_rn(v[j] + f[j]);
-        }
-      }
+      for (int j = 0; j < 32; ++j) f[j] = fr[cb + j];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) jr[cb + j] = __float2bfloat16_rn(v[j] + f[j]);
     } else {
       const int i = ti * BM + r;
       if (i < g.nc) {
@@ -229,6 +242,27 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
           const int col = tj * BN + cb + j;
           if (col < g.nc) d[col] += v[j];
         }
+      }
+    }
+  }
+  if (!X3 && g.mode == EPI_JROWS) {
+    __syncthreads();
+    // row rr of the bf16 tile sits at the front of fs row rr: one warp writes
+    // a 256-byte row per step, 8 bytes per lane
+    for (int rr = warp; rr < BM; rr += 4) {
+      const int row = arow + rr;
+      if (row >= g.M) continue;
+      const __nv_bfloat16* src = reinterpret_cast<const __nv_bfloat16*>(fs + rr * 129);
+      const int col = brow + lane * 4;
+      __nv_bfloat16* dst = g.J + (size_t)row * g.ldj + col;
+      if (col + 3 < g.N) {
+        uint2 w;
+        w.x = *reinterpret_cast<const uint32_t*>(src + lane * 4);
+        w.y = *reinterpret_cast<const uint32_t*>(src + lane * 4 + 2);
+        *reinterpret_cast<uint2*>(dst) = w;
+      } else {
+        for (int q = 0; q < 4; ++q)
+          if (col + q < g.N) dst[q] = src[lane * 4 + q];
       }
     }
   }

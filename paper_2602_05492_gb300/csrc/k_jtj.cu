@@ -255,6 +255,8 @@ __global__ void __launch_bounds__(128) k_phi_q(const float* __restrict__ xy, con
   }
 }
 
+constexpr int kGemvSegs = 16;   // sample segments per row in k_ft_gemv
+
 // out[t] = sum over k of part[k][t] (fixed order)
 __global__ void k_sum_rows(const double* __restrict__ part, int nparts, int m, double* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,26 +266,30 @@ __global__ void k_sum_rows(const double* __restrict__ part, int nparts, int m, d
   out[t] = s;
 }
 
-// gpart[row] = sum over the chunk's samples of F^T[row][s] r[s][row / nc]
-// (double accumulation); one warp per row of F^T
+// gpart[seg][row] = sum over segment seg of the chunk's samples of
+// F^T[row][s] r[s][row / nc] (double accumulation); one warp per (row,
+// segment), gridDim.y segments
 __global__ void k_ft_gemv(const float* __restrict__ F, int ldf, int rows, int nc, int m,
                           const float* __restrict__ r, double* __restrict__ gpart) {
   const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
   const int c = row / nc;
+  const int seg = (m + gridDim.y - 1) / gridDim.y;
+  const int sb = blockIdx.y * seg, se = min(m, sb + seg);
   const float* f = F + (size_t)row * ldf;
   double acc = 0;
-  for (int s0 = 0; s0 < m; s0 += 32 * 8) {
+  for (int s0 = sb; s0 < se; s0 += 32 * 8) {
     float a = 0;
+#pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int s = s0 + u * 32 + lane;
-      if (s < m) a += f[s] * r[3 * s + c];
+      if (s < se) a += f[s] * r[3 * s + c];
     }
     acc += a;
   }
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) gpart[row] = acc;
+  if (lane == 0) gpart[(size_t)blockIdx.y * rows + row] = acc;
 }
 
 // g[theta] = scale * sum over channels of (handle part + boundary part) of
@@ -515,7 +521,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   // gradient work: per chunk handle partial [3nc], q partials per slice
   const int qslices = (int)std::max<int64_t>(1, std::min<int64_t>(64, (chunk + 4095) / 4096));
   const int qslice_len = (int)((chunk + qslices - 1) / qslices);
-  const size_t gh_b = sizeof(double) * (size_t)std::max(nchunks, 1) * 3 * nc;
+  const size_t gh_b = sizeof(double) * (size_t)std::max(nchunks, 1) * kGemvSegs * 3 * nc;
   const size_t q_b = sizeof(double) * (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
   const size_t gb_b = sizeof(double) * 3 * (size_t)nc;
   if ((rc = grow(c, c->jrow, phi_b + 256 + f_b + 256))) return rc;
@@ -530,7 +536,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   void* J[2] = {c->tcJ.p, (char*)c->tcJ.p + j_part};
   float* part = (float*)c->tcPart.p;
   double* gh = (double*)c->gwork.p;
-  double* qp = gh + (size_t)std::max(nchunks, 1) * 3 * nc;
+  double* qp = gh + (size_t)std::max(nchunks, 1) * kGemvSegs * 3 * nc;
   double* gb = qp + (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
   if ((rc = cuda_check(c, cudaMemsetAsync(part, 0, part_b, S(c)), "memset"))) return rc;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
@@ -557,8 +563,8 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
     launch_frows<float, true>(c, xy + 2 * s0, m, F, ld);
     if (want_g) {
       ProfScope _pg(c, "k_ft_gemv");
-      k_ft_gemv<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>(F, ld, 3 * nc, nc, m, resid + 3 * s0,
-                                                    gh + (size_t)ci * 3 * nc);
+      k_ft_gemv<<<dim3((3 * nc + 7) / 8, kGemvSegs), 256, 0, S(c)>>>(
+          F, ld, 3 * nc, nc, m, resid + 3 * s0, gh + (size_t)ci * kGemvSegs * 3 * nc);
       BEM_LAUNCHED(c);
     }
     if ((rc = tc_jrows(c, x3, 3 * nc, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld))) return rc;
@@ -577,7 +583,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
     BEM_LAUNCHED(c);
     if ((rc = la_apply3_refined(c, c->bd.d_WT32, c->bd.d_A, c->d_q, c->d_lb, true))) return rc;
     k_g_boundary<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>((const double*)c->Dfc.p, Nb, nc, c->d_lb, gb);
-    k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(gh, nchunks, 3 * nc, gb, C,
+    k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(gh, nchunks * kGemvSegs, 3 * nc, gb, C,
                                                        n > 0 ? 1.0 / double(n) : 0.0, gout);
     c->launches += 2;
   }
