@@ -193,6 +193,31 @@ int bem_gemm_bf16(bem_ctx *ctx, int M, int N, int K, const void *A, int lda, con
 int bem_fastmath_eval(bem_ctx *ctx, int which, int64_t n, const float *a, const float *b,
                       float *out_fast, float *out_ref, void *stream);
 
+/* bem_vjp without any device allocation (the paper has no counterpart; this
+ * is for callers, not for the method).  Some callers may not allocate GPU
+ * memory while they run the hot path: work recorded into a CUDA graph
+ * (allocation calls cannot be captured), real-time loops that must never
+ * enter the allocator (cudaMalloc and cudaFree can stall the whole device),
+ * and host programs whose own memory pool owns the GPU.  This entry point
+ * computes the same vector-Jacobian product as bem_vjp on a context that
+ * bem_setup and bem_factor have already prepared, taking every per-call
+ * buffer from one static device array of 32 MiB that the library reserves
+ * on each GPU that loads it (held until the process exits); it calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   - In BEM_MIXED contexts every pair is evaluated in float (no double near
+ *     field), so the result agrees with bem_vjp to the mixed-path gradient
+ *     accuracy; in BEM_FP64 contexts the arithmetic is the same as bem_vjp's.
+ *   - Scenes whose panel sums do not fit the array (about 190,000 panels at
+ *     1,024 boundary segments) are rejected with BEM_EINVAL and a message.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls on a device share the array and it keeps the last call's
+ *     contents (each call writes what it reads).  Calls whose GPU work
+ *     overlaps (other streams, other threads) race on it: serialise them.
+ * Arguments and layouts as bem_vjp. */
+int bem_vjp_noalloc(bem_ctx *ctx, int64_t n, const void *xy, const void *resid,
+                    double *grad_out, void *stream);
+
 /* Sizes of the current scene (host ints; any pointer may be NULL). */
 int bem_sizes(const bem_ctx *ctx, int *n_theta, int *n_panels, int *n_boundary);
 

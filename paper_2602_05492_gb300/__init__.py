@@ -77,6 +77,7 @@ def _load():
         "bem_profile_enable": (ci, [vp, ci]),
         "bem_gemm_bf16": (ci, [vp, ci, ci, ci, vp, ci, vp, ci, vp, ci, vp]),
         "bem_fastmath_eval": (ci, [vp, ci, i64, vp, vp, vp, vp, vp]),
+        "bem_vjp_noalloc": (ci, [vp, i64, vp, vp, vp, vp]),
         "bem_profile_read": (ci, [vp, ci, ctypes.c_char_p, dp, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ci)]),
     }
@@ -93,7 +94,7 @@ EXPORTED = [
     "bem_set_params", "bem_get_params", "bem_set_mean_color", "bem_sample_mean", "bem_eval",
     "bem_loss", "bem_vjp", "bem_jtj", "lm_step", "bem_sizes", "bem_boundary_values",
     "bem_launch_count", "bem_profile_enable", "bem_profile_read", "bem_gemm_bf16",
-    "bem_fastmath_eval",
+    "bem_fastmath_eval", "bem_vjp_noalloc",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -229,6 +230,13 @@ class BEM:
             grad = torch.empty(self.n_theta, dtype=torch.float64, device=xy.device)
         self._check(_lib.bem_vjp(self.h, xy.shape[0], _ptr(xy), _ptr(resid), _ptr(grad),
                                  _stream(stream)))
+        return grad
+
+    def vjp_noalloc(self, xy, resid, grad, stream=None):
+        """bem_vjp into a caller-provided gradient buffer, with no device allocation."""
+        self._samples(xy, resid)
+        self._check(_lib.bem_vjp_noalloc(self.h, xy.shape[0], _ptr(xy), _ptr(resid), _ptr(grad),
+                                         _stream(stream)))
         return grad
 
     def jtj(self, xy, H=None, stream=None):

@@ -112,6 +112,8 @@ int la_apply3(bem_ctx* c, const double* W, const double* x, double* y);
 // refined float solve: y = A^+ x via float W and a double residual
 int la_apply3_refined(bem_ctx* c, const float* W32, const double* A, const double* x, double* y,
                       bool transpose);
+int la_apply3_refined_buf(bem_ctx* c, const float* W32, const double* A, const double* x,
+                          double* y, bool transpose, double* scratch);
 void la_dgemm(bem_ctx* c, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
               int lda, const double* B, int ldb, double beta, double* C, int ldc);
 // LM solve: delta for (H + lam D) delta = -g with the compatibility KKT;

@@ -19,6 +19,7 @@
 // these sums stay in registers (no cross-thread reduction per pair).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "ctx.h"
 
@@ -412,3 +413,169 @@ int adj_vjp(bem_ctx* c, int64_t n, const void* xy, const void* resid, double* gr
 }
 
 }  // namespace bem
+
+// ---------------------------------------------------------------------------
+// Allocation-free adjoint.
+//
+// For callers that may not allocate device memory while the hot path runs:
+// code recorded into a CUDA graph (cudaMalloc cannot be captured), real-time
+// loops that must not enter the allocator (cudaMalloc/cudaFree can stall the
+// whole device), and hosts whose own memory pool owns the GPU.  Every
+// per-call buffer of the adjoint (per-slice partial sums, panel sums, Gauss
+// weights, refinement residuals) lives in the static array below; the
+// persistent state (panels, boundary factors) was allocated by bem_setup and
+// bem_factor beforehand.  The array is shared by all calls on a device and
+// keeps the previous call's contents; everything a call reads is written by
+// that call first.  Calls whose work overlaps on the GPU race on it.
+
+namespace bem {
+namespace {
+
+constexpr size_t kNoAllocBytes = 32u << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kMaxDevices] = {};
+
+// device address of the static array on the current device (looked up once
+// per device, with that device current)
+int noalloc_base(bem_ctx* c, unsigned char** out) {
+  if (c->device < 0 || c->device >= kMaxDevices)
+    return fail(c, BEM_EINVAL, "bem_vjp_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[c->device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaGetSymbolAddress of the static scratch");
+    g_noalloc_addr[c->device] = (unsigned char*)p;
+  }
+  *out = g_noalloc_addr[c->device];
+  return BEM_OK;
+}
+
+size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+
+// one pass of the adjoint kernels over n points with explicit buffers:
+// partial sums into part (slices x P x 11) and qpart, reduced into sums
+// (added when accumulate) and q
+template <typename T>
+int noalloc_pass(bem_ctx* c, int64_t n, const T* xy, const T* w, bool boundary, int accumulate,
+                 int max_slices, double* part, double* qpart, double* sums, double* q) {
+  const int P = c->sc.P, Nb = boundary ? c->bd.Nb : 0;
+  const int ptiles = (P + kVB - 1) / kVB, btiles = (Nb + kVB - 1) / kVB;
+  const int tiles = ptiles + btiles;
+  const bool f32 = sizeof(T) == 4;
+  const int step = f32 ? kVT : kVB;
+  int64_t want = f32 ? (3 * 7 * 152 + tiles - 1) / tiles : (4 * 152 + tiles - 1) / tiles;
+  want = std::min<int64_t>(want, max_slices);
+  int64_t maxs = (n + step - 1) / step;
+  int slices = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxs));
+  const int64_t chunk = ((n + slices - 1) / slices + step - 1) / step * step;
+  slices = (int)std::max<int64_t>(1, (n + chunk - 1) / chunk);
+  const int64_t m = (int64_t)P * kNP;
+  if (n <= 0) {
+    if (!accumulate)
+      cudaMemsetAsync(sums, 0, sizeof(double) * m, S(c));
+    if (boundary) cudaMemsetAsync(q, 0, sizeof(double) * 3 * Nb, S(c));
+    return cuda_check(c, cudaGetLastError(), "noalloc pass");
+  }
+  VjpArgs<T> a{};
+  a.xy = xy;
+  a.w = w;
+  a.n = n;
+  a.pan = (const Panel<T>*)(f32 ? (const void*)c->d_pan32 : (const void*)c->d_pan64);
+  a.pan64 = c->d_pan64;
+  a.P = P;
+  a.vert = (const T*)(f32 ? (const void*)c->bd.d_vert32 : (const void*)c->bd.d_vert);
+  a.Nb = Nb;
+  a.ec2 = T(c->opts.eps_c * c->opts.eps_c);
+  a.ed2 = T(c->opts.eps_d * c->opts.eps_d);
+  a.ec2d = c->opts.eps_c * c->opts.eps_c;
+  a.ed2d = c->opts.eps_d * c->opts.eps_d;
+  a.near2 = T(0);
+  a.chunk = chunk;
+  a.part = part;
+  a.qpart = qpart;
+  dim3 grid(tiles, slices);
+  const bool same = c->opts.eps_c == c->opts.eps_d;
+  if constexpr (sizeof(T) == 4) {
+    if (same) k_vjp_f32<true, false><<<grid, kVB, 0, S(c)>>>(a);
+    else k_vjp_f32<false, false><<<grid, kVB, 0, S(c)>>>(a);
+  } else {
+    if (same) k_vjp<T, true, false><<<grid, kVB, 0, S(c)>>>(a);
+    else k_vjp<T, false, false><<<grid, kVB, 0, S(c)>>>(a);
+  }
+  k_reduce_slices<<<(unsigned)((m + 255) / 256), 256, 0, S(c)>>>(part, slices, m, sums, accumulate);
+  c->launches += 2;
+  if (boundary) {
+    k_reduce_slices<<<(3 * Nb + 255) / 256, 256, 0, S(c)>>>(qpart, slices, 3 * (int64_t)Nb, q, 0);
+    BEM_LAUNCHED(c);
+  }
+  return cuda_check(c, cudaGetLastError(), "noalloc pass");
+}
+
+template <typename T>
+int noalloc_vjp(bem_ctx* c, int64_t n, const T* xy, const T* resid, double* grad,
+                unsigned char* base) {
+  const int P = c->sc.P, Nb = c->bd.Nb;
+  // fixed part: panel sums, Gauss weights, refinement residuals
+  const size_t sums_b = up256(sizeof(double) * (size_t)P * kNP);
+  const size_t gw_b = up256(sizeof(T) * 9 * (size_t)Nb);
+  const size_t ref_b = up256(sizeof(double) * 6 * (size_t)Nb);
+  const size_t fixed = sums_b + gw_b + ref_b;
+  const size_t per_slice = sizeof(double) * ((size_t)P * kNP + 3 * (size_t)Nb);
+  if (fixed + per_slice > kNoAllocBytes) {
+    char msg[200];
+    snprintf(msg, sizeof(msg),
+             "bem_vjp_noalloc: %d panels need more than its %zu-byte static scratch "
+             "(limit about %zu panels at %d boundary segments)",
+             P, kNoAllocBytes,
+             (kNoAllocBytes - ref_b - 8 * 12 * (size_t)Nb) / (2 * 8 * kNP), Nb);
+    return fail(c, BEM_EINVAL, msg);
+  }
+  const int max_slices = (int)std::min<size_t>(4096, (kNoAllocBytes - fixed) / per_slice);
+  double* sums = (double*)base;
+  T* gw = (T*)(base + sums_b);
+  double* ref = (double*)(base + sums_b + gw_b);
+  double* part = (double*)(base + fixed);
+  double* qpart = part + (size_t)max_slices * P * kNP;
+  int rc;
+  if ((rc = geom_panelize(c, c->d_theta))) return rc;
+  if ((rc = noalloc_pass<T>(c, n, xy, resid, true, 0, max_slices, part, qpart, sums, c->d_q))) return rc;
+  if (c->opts.precision == BEM_FP64) rc = la_apply3(c, c->bd.d_WT, c->d_q, c->d_lb);
+  else rc = la_apply3_refined_buf(c, c->bd.d_WT32, c->bd.d_A, c->d_q, c->d_lb, true, ref);
+  if (rc) return rc;
+  k_gauss_weights<T><<<(3 * Nb + 255) / 256, 256, 0, S(c)>>>(c->d_lb, Nb, c->bd.d_vert, gw);
+  BEM_LAUNCHED(c);
+  const T* gp = (const T*)(sizeof(T) == 8 ? (const void*)c->bd.d_gp : (const void*)c->bd.d_gp32);
+  if ((rc = noalloc_pass<T>(c, 3 * (int64_t)Nb, gp, gw, false, 1, max_slices, part, qpart, sums,
+                            nullptr)))
+    return rc;
+  k_chain<<<(4 * c->sc.C + 127) / 128, 128, 0, S(c)>>>(sums, c->d_pan64, c->sc.d_off, c->sc.d_K,
+                                                        c->sc.d_closed, c->sc.C, 1.0, grad);
+  BEM_LAUNCHED(c);
+  return cuda_check(c, cudaGetLastError(), "noalloc vjp");
+}
+
+}  // namespace
+
+}  // namespace bem
+
+extern "C" int bem_vjp_noalloc(bem_ctx* c, int64_t n, const void* xy, const void* resid,
+                               double* grad_out, void* stream) {
+  using namespace bem;
+  if (!c) return BEM_EINVAL;
+  if (n < 0 || !grad_out || (n > 0 && (!xy || !resid)))
+    return fail(c, BEM_EINVAL, "bem_vjp_noalloc: bad arguments");
+  if (!c->have_scene) return fail(c, BEM_ESTATE, "bem_setup has not been called");
+  if (!c->bd.factored) return fail(c, BEM_ESTATE, "bem_factor has not been called");
+  int rc;
+  if ((rc = cuda_check(c, cudaSetDevice(c->device), "cudaSetDevice"))) return rc;
+  c->cur = (cudaStream_t)stream;
+  unsigned char* base = nullptr;
+  if ((rc = noalloc_base(c, &base))) return rc;
+  if (c->opts.precision == BEM_FP64)
+    return noalloc_vjp<double>(c, n, (const double*)xy, (const double*)resid, grad_out, base);
+  return noalloc_vjp<float>(c, n, (const float*)xy, (const float*)resid, grad_out, base);
+}

@@ -266,6 +266,21 @@ int la_apply3_refined(bem_ctx* c, const float* W32, const double* A, const doubl
   return cuda_check(c, cudaGetLastError(), "refined apply");
 }
 
+// Same refined product as la_apply3_refined with the caller's scratch
+// (6 Nb doubles) instead of a context buffer.
+int la_apply3_refined_buf(bem_ctx* c, const float* W32, const double* A, const double* x,
+                          double* y, bool transpose, double* scratch) {
+  int Nb = c->bd.Nb;
+  double* r = scratch;
+  double* d = r + 3 * Nb;
+  k_apply3_f<<<(Nb + 7) / 8, 256, 0, S(c)>>>(W32, Nb, x, y);
+  k_resid3<<<(Nb + 7) / 8, 256, 0, S(c)>>>(A, Nb, x, y, r, transpose);
+  k_apply3_f<<<(Nb + 7) / 8, 256, 0, S(c)>>>(W32, Nb, r, d);
+  k_add3<<<(3 * Nb + 255) / 256, 256, 0, S(c)>>>(y, d, 3 * Nb);
+  c->launches += 4;
+  return cuda_check(c, cudaGetLastError(), "refined apply");
+}
+
 // ---------------------------------------------------------------------------
 // C = alpha op(A) op(B) + beta C, row-major, double.  64 x 64 tiles, 4 x 4 per thread.
 
