@@ -35,8 +35,6 @@ UNIT = "LM iter/s"
 CFG = 2
 L2_FLUSH_BYTES = 256 << 20
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 lanes x 2 flops per FMA x SMs x max SM clock (GB300: 128, 152, 2070 MHz)
-FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12
 
 
 def workload_desc(sc):
@@ -111,27 +109,81 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per unit (counted from the source formulas)
+# algorithmic work per unit, counted from the source formulas (FP32 flops:
+# add/mul = 1, FMA = 2, one special-function op = 1; compares, selects and
+# min/max are not counted)
 
-# FP32 flops per handle pair (FMA = 2): frame 9, layer values 21, three
-# transcendentals (log, log1p, atan2) and one sqrt counted as 1 each, two
-# divisions as 1 each, 3-channel accumulation 12
-FLOP_FWD_HANDLE = 9 + 21 + 4 + 2 + 12
-# boundary pair: 4 sub, cross 3, dot 3, atan2 1, 3-channel accumulation 6
-FLOP_FWD_BOUND = 4 + 3 + 3 + 1 + 6
-# adjoint handle pair: frame 9, layer values and frame partials 45,
-# 4 transcendentals + 2 sqrt/div + 4 reciprocals, weights 10, 11 sums 26
-FLOP_ADJ_HANDLE = 9 + 45 + 10 + 10 + 26
-FLOP_ADJ_BOUND = 4 + 3 + 3 + 1 + 6
+# handle pair of the evaluation: rounded frame 9, h^2 1, h', q1, q2, t1 t2 8, atan2(h'L, h'^2 + t1 t2) 22 (octant reduction, one
+# reciprocal, degree-7 minimax polynomial), (1/2) log q2 - 1 3, z = L(t1+t2)/q1 4,
+# (1/2) log1p(z) 13 (atanh series), S 5, Dl 2, 3-channel accumulation 12
+FLOP_FWD_HANDLE = 9 + 1 + 8 + 22 + 3 + 4 + 13 + 5 + 2 + 12
+# boundary pair: vertex offset 2, cross 3, dot 3, atan2 20, 3-channel accumulation 6
+FLOP_FWD_BOUND = 2 + 3 + 3 + 20 + 6
+# F-row pair: frame 10, values and frame partials of both layers 73, chain rule
+# to both endpoints for Dl and S 43, jump columns 16, 3 channels x 2 coordinates
+# x (combine 7 + four Bernstein accumulations 8) 90
+FLOP_FROWS_PAIR = 10 + 73 + 43 + 16 + 90
+# FP32 lanes x 2 flops per FMA x SMs x max SM clock (GB300: 128, 152, 2070 MHz)
+FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12
 
 
-def kernel_work(name, n, P, Nb, nc):
-    """(flops per launch, unit) of the profiled kernels."""
-    if name == "k_field":
-        return n * (P * FLOP_FWD_HANDLE + Nb * FLOP_FWD_BOUND), "alu"
-    if name == "k_vjp":
-        return n * (P * FLOP_ADJ_HANDLE + Nb * FLOP_ADJ_BOUND), "alu"
+def step_work(name, n, P, Nb, nc):
+    """(flops of one LM step's launches of `name`, bound) for the modelled kernels."""
+    if name == "k_field":            # evaluation at the current and at the trial parameters
+        return 2.0 * n * (P * FLOP_FWD_HANDLE + Nb * FLOP_FWD_BOUND), "alu"
+    if name == "k_frows":            # all samples, plus the 3 Nb boundary Gauss points
+        return float(n + 3 * Nb) * P * FLOP_FROWS_PAIR, "alu"
+    if name == "tc_jrows":           # J^T = M_c^T Phi^T (+ F^T) for 3 channels
+        return 2.0 * 3 * nc * Nb * n, "tensor"
+    if name == "tc_syrk":            # 3 symmetric rank-n updates of order nc
+        return 3.0 * nc * (nc + 1) * n, "tensor"
     return None, None
+
+
+def read_peaks():
+    try:
+        with open(PEAKS) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def kernel_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel's source has changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            rec = json.load(f).get(name)
+        if not rec:
+            return None
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        return rec["bytes_per_launch"] if sha == rec["sha256"] else None
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def rooflines(prof, steps, n, P, Nb, nc):
+    peaks, src = read_peaks()
+    out = []
+    for name, (ms, cnt) in prof.items():
+        work, bound = step_work(name, n, P, Nb, nc)
+        if work is None or not cnt:
+            continue
+        per_launch = work * steps / cnt
+        ach = per_launch / (ms / cnt / 1e3) / 1e12
+        if bound == "alu":
+            peak, psrc = FP32_PEAK_TFLOPS, "FP32: 128 lanes x 2 x 152 SMs x 2070 MHz (derived)"
+        else:
+            peak = peaks["bf16_tflops_sustained"]
+            psrc = f"bf16 dense, sustained ({src})"
+        out.append({"bound": bound, "kernel": name, "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": kernel_traffic(name),
+                    "flops_per_launch": per_launch, "peak_source": psrc,
+                    "share_ms": ms})
+    out.sort(key=lambda r: -r.pop("share_ms"))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -258,21 +310,10 @@ def run_ours(args, rank, world, dist):
 
     if rank != 0:
         return
-    # ---- per-kernel live timing -> roofline of the dominant kernel
+    # ---- per-kernel live timing -> roofline of the dominant modelled kernel
     P, Nb, nc = sc.n_panels, 1024, 16 * sc.n_curves
-    top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else (None, (0.0, 0))
-    top_name, (top_ms, top_cnt) = top
-    work, kind = kernel_work(top_name, n, P, Nb, nc)
-    roof = None
-    if work is not None and top_cnt:
-        per_launch_s = top_ms / top_cnt / 1e3
-        ach = work / per_launch_s / 1e12
-        roof = {"bound": kind, "kernel": top_name, "achieved": ach,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "FP32 FMA lanes x max SM clock (derived)"}
-    elif top_name is not None:
-        roof = {"bound": "fp64", "kernel": top_name, "achieved": None, "peak": None,
-                "unit": "TFLOP/s", "frac": None, "traffic": None}
+    roofs = rooflines(prof, args.steps, n, P, Nb, nc)
+    roof = roofs[0] if roofs else None
     kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
                    "share": v[0] / total_ms} for k, v in sorted(prof.items())}
 
@@ -375,7 +416,7 @@ def run_ours(args, rank, world, dist):
             "pairs_per_s": {"value": pairs_per_s, "unit": "sample x panel evals/s (fwd+adjoint)",
                             "fwd_ms": fwd_ms, "adj_ms": adj_ms, "pairs_per_pass": pairs},
             "fp64_gpu": fp64, "accuracy": accuracy, "kernels": kernels,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "roofline": roof, "rooflines_other": roofs[1:], "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
 

@@ -188,8 +188,9 @@ int bem_gemm_bf16(bem_ctx *ctx, int M, int N, int K, const void *A, int lda, con
 
 /* The float approximations the mixed-precision kernels use, next to CUDA's
  * accurate float functions, for validation (no counterpart in the paper):
- * which = 0: atan2(a[i], b[i]); 1: log(a[i]); 2: log1p(a[i]).  a, b,
- * out_fast, out_ref: device float [n] (b only for which = 0). */
+ * which = 0: atan2(a[i], b[i]); 1: log(a[i]); 2: log1p(a[i]);
+ * 3: atan2(|a[i]|, b[i]) by the y >= 0 variant; 4: log1p(a[i])/2.  a, b,
+ * out_fast, out_ref: device float [n] (b only for which = 0 and 3). */
 int bem_fastmath_eval(bem_ctx *ctx, int which, int64_t n, const float *a, const float *b,
                       float *out_fast, float *out_ref, void *stream);
 

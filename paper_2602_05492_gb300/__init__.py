@@ -276,7 +276,8 @@ class BEM:
         return D
 
     def fastmath(self, which: int, a, b=None, stream=None):
-        """(library approximation, CUDA accurate) of atan2 (0), log (1), log1p (2)."""
+        """(library approximation, CUDA accurate) of atan2 (0), log (1), log1p (2),
+        atan2 for y >= 0 (3, a taken as |a|) and log1p/2 (4)."""
         import torch
         fast = torch.empty_like(a)
         ref = torch.empty_like(a)

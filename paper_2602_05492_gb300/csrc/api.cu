@@ -145,9 +145,15 @@ __global__ void k_fastmath(int which, int64_t n, const float* __restrict__ a,
   } else if (which == 1) {
     fast[i] = fm_log(x);
     ref[i] = logf(x);
-  } else {
+  } else if (which == 2) {
     fast[i] = fm_log1p(x);
     ref[i] = log1pf(x);
+  } else if (which == 3) {
+    fast[i] = fm_atan2_ypos(fabsf(x), b[i]);
+    ref[i] = atan2f(fabsf(x), b[i]);
+  } else {
+    fast[i] = fm_log1p_half(x);
+    ref[i] = 0.5f * log1pf(x);
   }
 }
 
@@ -503,7 +509,8 @@ int bem_gemm_bf16(bem_ctx* c, int M, int N, int K, const void* A, int lda, const
 int bem_fastmath_eval(bem_ctx* c, int which, int64_t n, const float* a, const float* b,
                       float* out_fast, float* out_ref, void* stream) {
   if (!c) return BEM_EINVAL;
-  if (which < 0 || which > 2 || n < 0 || (n > 0 && (!a || !out_fast || !out_ref || (which == 0 && !b))))
+  if (which < 0 || which > 4 || n < 0 ||
+      (n > 0 && (!a || !out_fast || !out_ref || ((which == 0 || which == 3) && !b))))
     return fail(c, BEM_EINVAL, "bem_fastmath_eval: bad arguments");
   int rc;
   if ((rc = set_device(c))) return rc;

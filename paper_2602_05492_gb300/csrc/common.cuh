@@ -33,9 +33,10 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kInv2Pi = 0.15915494309189533577;   // 1/(2 pi)
 constexpr double kInv4Pi = 0.07957747154594766788;   // 1/(4 pi)
 
-// One straight panel as the kernels stage it (12 words).
+// One straight panel as the kernels stage it (12 words, 16-byte aligned so
+// that a float panel is three 128-bit loads).
 template <typename T>
-struct Panel {
+struct __align__(16) Panel {
   T ax, ay;      // start point a
   T tx, ty;      // unit tangent (0,0 for a zero-length panel)
   T L;           // length
@@ -91,19 +92,102 @@ __device__ __forceinline__ Frame<T> frame(const Panel<T>& p, T x, T y) {
   return f;
 }
 
-// Near-field test of the mixed-precision path: the distance from x to the
-// panel segment is below near_factor * L (compared squared).  The frame is
-// recomputed here with explicitly rounded operations so that every kernel
-// (the float main loops that skip these pairs and the double near-field
-// kernels that take them) reaches the same decision bit for bit.
+// Near-field decision of the mixed-precision path: the distance from x to
+// the panel segment is below near_factor * L (compared squared).  Every
+// kernel that takes it (the float main loops that skip these pairs and the
+// double near-field kernels that take them) computes the frame with the same
+// explicitly rounded operations, so the decision agrees bit for bit.
+__device__ __forceinline__ Frame<float> frame_rn(float ax, float ay, float tx, float ty, float L,
+                                                 float x, float y) {
+  Frame<float> f;
+  const float dax = __fsub_rn(ax, x), day = __fsub_rn(ay, y);
+  f.t1 = __fmaf_rn(dax, tx, __fmul_rn(day, ty));
+  f.h = __fmaf_rn(dax, ty, -__fmul_rn(day, tx));
+  f.t2 = __fadd_rn(f.t1, L);
+  f.L = L;
+  return f;
+}
+
+// near_factor^2 L^2
+__device__ __forceinline__ float near_thr(float L, float near2) {
+  return __fmul_rn(near2, __fmul_rn(L, L));
+}
+
+// hh = h*h of the frame.  The along-panel offset max(t1,0) + min(t2,0) is
+// t1, t2 or 0 as x projects before, after or onto the panel (t1 <= t2).
+__device__ __forceinline__ bool near_test(const Frame<float>& f, float hh, float thr) {
+  const float dt = __fadd_rn(fmaxf(f.t1, 0.f), fminf(f.t2, 0.f));
+  return __fmaf_rn(dt, dt, hh) < thr;
+}
+
 __device__ __forceinline__ bool near_pair(const Panel<float>& p, float x, float y, float near2) {
-  const float dax = __fsub_rn(p.ax, x), day = __fsub_rn(p.ay, y);
-  const float t1 = __fmaf_rn(dax, p.tx, __fmul_rn(day, p.ty));
-  const float h = __fmaf_rn(dax, p.ty, -__fmul_rn(day, p.tx));
-  const float t2 = __fadd_rn(t1, p.L);
-  const float dt = t1 > 0.f ? t1 : (t2 < 0.f ? t2 : 0.f);
-  const float d2 = __fmaf_rn(dt, dt, __fmul_rn(h, h));
-  return d2 < __fmul_rn(near2, __fmul_rn(p.L, p.L));
+  const Frame<float> f = frame_rn(p.ax, p.ay, p.tx, p.ty, p.L, x, y);
+  return near_test(f, __fmul_rn(f.h, f.h), near_thr(p.L, near2));
+}
+
+// Axis-aligned box (xmin, ymin, xmax, ymax) around every point whose pair
+// with the panel near_test can call near: the segment grown by
+// near_factor L, plus a margin far above the rounding of the frame.  A
+// block of points whose box misses it has no near pair with the panel.
+__device__ __forceinline__ float4 near_zone(const Panel<float>& p, float nfac) {
+  const float R = fmaf(nfac * p.L, 1.001f, 1e-5f);
+  const float bx = fmaf(p.L, p.tx, p.ax), by = fmaf(p.L, p.ty, p.ay);
+  return make_float4(fminf(p.ax, bx) - R, fminf(p.ay, by) - R, fmaxf(p.ax, bx) + R,
+                     fmaxf(p.ay, by) + R);
+}
+
+__device__ __forceinline__ bool boxes_meet(float4 a, float4 b) {
+  return a.x <= b.z && b.x <= a.z && a.y <= b.w && b.y <= a.w;
+}
+
+// Bounding box of the points (x, y) held by the threads of a block of
+// blockDim.x = 32 * nw threads (dead threads pass live = false); red: 4 nw floats
+// of shared memory.  Every thread receives the box.  An empty set gives
+// (+inf, +inf, -inf, -inf), which meets no box.
+__device__ __forceinline__ float4 block_bbox(float x0, float y0, float x1, float y1, bool live,
+                                             float* red) {
+  float4 b = live ? make_float4(x0, y0, x1, y1)
+                  : make_float4(__int_as_float(0x7f800000), __int_as_float(0x7f800000),
+                                __int_as_float(0xff800000), __int_as_float(0xff800000));
+  for (int o = 16; o; o >>= 1) {
+    b.x = fminf(b.x, __shfl_xor_sync(0xffffffffu, b.x, o));
+    b.y = fminf(b.y, __shfl_xor_sync(0xffffffffu, b.y, o));
+    b.z = fmaxf(b.z, __shfl_xor_sync(0xffffffffu, b.z, o));
+    b.w = fmaxf(b.w, __shfl_xor_sync(0xffffffffu, b.w, o));
+  }
+  const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red[4 * w] = b.x; red[4 * w + 1] = b.y; red[4 * w + 2] = b.z; red[4 * w + 3] = b.w;
+  }
+  __syncthreads();
+  b = make_float4(red[0], red[1], red[2], red[3]);
+  for (int k = 1; k < nw; ++k) {
+    b.x = fminf(b.x, red[4 * k]); b.y = fminf(b.y, red[4 * k + 1]);
+    b.z = fmaxf(b.z, red[4 * k + 2]); b.w = fmaxf(b.w, red[4 * k + 3]);
+  }
+  return b;
+}
+
+// A float panel as the forward loops stage it in shared memory, with the
+// constants of the layer integrals folded into the jumps:
+//   wd' = w_d/(2 pi), wc' = -w_c/(2 pi), thr = near_thr(L, near_factor^2)
+// so that -w_d Dl + w_c S = wd' Dh + wc' Sh with Dh, Sh of pair_fwd_f.
+struct __align__(16) PanelF {
+  float ax, ay, tx, ty;
+  float L, thr, wd0, wd1;
+  float wd2, wc0, wc1, wc2;
+};
+
+__device__ __forceinline__ PanelF stage_panel(const Panel<float>& p, float near2) {
+  constexpr float k = 0.159154943f;   // 1/(2 pi)
+  PanelF s;
+  s.ax = p.ax; s.ay = p.ay; s.tx = p.tx; s.ty = p.ty;
+  s.L = p.L;
+  s.thr = near_thr(p.L, near2);
+  s.wd0 = p.wd[0] * k; s.wd1 = p.wd[1] * k; s.wd2 = p.wd[2] * k;
+  s.wc0 = -p.wc[0] * k; s.wc1 = -p.wc[1] * k; s.wc2 = -p.wc[2] * k;
+  return s;
 }
 
 // One regularised layer pair: S with eps_c, Dl with eps_d.
@@ -137,32 +221,31 @@ __device__ __forceinline__ LayerVals<T> layer_values(const Frame<T>& f, T eps_c2
   return v;
 }
 
-// Float versions: own transcendentals (fastmath.cuh), one rsqrt for both
-// h' and h/h', approximate divisions.
-template <>
-__device__ __forceinline__ LayerVals<float> layer_values<float>(const Frame<float>& f, float eps_c2,
-                                                               float eps_d2, bool same_eps) {
-  LayerVals<float> v;
-  const float hh = f.h * f.h;
+// Forward pair of the float loops, with the layer constants taken out
+// (multiplied by -2 pi) so that they fold into the staged jumps of PanelF:
+//   Dh = (h/h'_d) Phi_d                                              = -2 pi Dl
+//   Sh = (1/2) L (log q2 - 2) + (1/2) t1 log1p(L(t1+t2)/q1) + h'_c Phi_c = -2 pi S
+// hh = h*h.  Own transcendentals (fastmath.cuh), one rsqrt for both h' and
+// h/h', approximate divisions.
+__device__ __forceinline__ void pair_fwd_f(const Frame<float>& f, float hh, float eps_c2,
+                                           float eps_d2, bool same_eps, float& Dh, float& Sh) {
   const float hc2 = hh + eps_c2;
   const float rc = rsqrtf(hc2);
   const float hc = hc2 * rc;
   const float tt = f.t1 * f.t2;
   const float q1 = fmaf(f.t1, f.t1, hc2);
   const float q2 = fmaf(f.t2, f.t2, hc2);
-  const float phic = fm_atan2(hc * f.L, hc2 + tt);
-  const float lg2 = fm_log(q2);
-  const float lp = fm_log1p(__fdividef(f.L * (f.t1 + f.t2), q1));
-  v.S = -(f.L * (lg2 - 2.f) + f.t1 * lp + 2.f * hc * phic) * float(kInv4Pi);
+  const float phic = fm_atan2_ypos(hc * f.L, hc2 + tt);
+  const float a = fmaf(__log2f(q2), kLn2Halff, -1.f);          // (1/2) log q2 - 1
+  const float lph = fm_log1p_half(__fdividef(f.L * (f.t1 + f.t2), q1));
+  Sh = fmaf(hc, phic, fmaf(f.t1, lph, f.L * a));
   if (same_eps) {
-    v.Dl = -(f.h * rc) * phic * float(kInv2Pi);
+    Dh = f.h * rc * phic;
   } else {
     const float hd2 = hh + eps_d2;
     const float rd = rsqrtf(hd2);
-    const float phid = fm_atan2(hd2 * rd * f.L, hd2 + tt);
-    v.Dl = -(f.h * rd) * phid * float(kInv2Pi);
+    Dh = f.h * rd * fm_atan2_ypos(hd2 * rd * f.L, hd2 + tt);
   }
-  return v;
 }
 
 // Values and frame partials of both layers.
@@ -213,40 +296,51 @@ __device__ __forceinline__ LayerGrad<T> layer_grad(const Frame<T>& f, T eps_c2, 
   return g;
 }
 
-template <>
-__device__ __forceinline__ LayerGrad<float> layer_grad<float>(const Frame<float>& f, float eps_c2,
-                                                             float eps_d2, bool same_eps) {
-  LayerGrad<float> g;
+// Values and frame partials of the float loops, each multiplied by -2 pi
+// (the factor is applied once to the sums the loops accumulate):
+//   S   = Sh of pair_fwd_f          D   = (h/h'_d) Phi_d
+//   St1 = -(1/2) log q1             Dt1 = -h/q1
+//   St2 =  (1/2) log q2             Dt2 =  h/q2
+//   Sh_ = (h/h'_c) Phi_c            Dh_ = (1/h'^2)[eps_d^2 Phi_d/h' - h^2 L (h'^2 - t1 t2)/(q1 q2)]
+// with log q1 = log q2 - log1p(L(t1+t2)/q1) (q2 = q1 + L(t1+t2)).
+struct GradHat {
+  float S, D;
+  float St1, St2, Sh;
+  float Dt1, Dt2, Dh;
+};
+
+__device__ __forceinline__ GradHat layer_grad_hat(const Frame<float>& f, float hh, float eps_c2,
+                                                  float eps_d2, bool same_eps) {
+  GradHat g;
   const float tt = f.t1 * f.t2;
-  const float hh = f.h * f.h;
   const float hc2 = hh + eps_c2;
   const float rc = rsqrtf(hc2);
   const float hc = hc2 * rc;
   const float q1 = fmaf(f.t1, f.t1, hc2);
   const float q2 = fmaf(f.t2, f.t2, hc2);
-  const float phic = fm_atan2(hc * f.L, hc2 + tt);
-  const float lg2 = fm_log(q2);
-  const float lp = fm_log1p(__fdividef(f.L * (f.t1 + f.t2), q1));
-  const float lg1 = lg2 - lp;
-  g.S = -(f.L * (lg2 - 2.f) + f.t1 * lp + 2.f * hc * phic) * float(kInv4Pi);
-  g.S_t1 = lg1 * float(kInv4Pi);
-  g.S_t2 = -lg2 * float(kInv4Pi);
-  g.S_h = -(f.h * rc) * phic * float(kInv2Pi);
+  const float phic = fm_atan2_ypos(hc * f.L, hc2 + tt);
+  const float lq2h = __log2f(q2) * kLn2Halff;                  // (1/2) log q2
+  const float lph = fm_log1p_half(__fdividef(f.L * (f.t1 + f.t2), q1));
+  g.S = fmaf(hc, phic, fmaf(f.t1, lph, f.L * (lq2h - 1.f)));
+  g.St1 = lph - lq2h;
+  g.St2 = lq2h;
+  g.Sh = f.h * rc * phic;
   float hd2, rd, phid, r1, r2;
   if (same_eps) {
     hd2 = hc2; rd = rc; phid = phic; r1 = q1; r2 = q2;
+    g.D = g.Sh;
   } else {
     hd2 = hh + eps_d2;
     rd = rsqrtf(hd2);
-    phid = fm_atan2(hd2 * rd * f.L, hd2 + tt);
+    phid = fm_atan2_ypos(hd2 * rd * f.L, hd2 + tt);
     r1 = fmaf(f.t1, f.t1, hd2);
     r2 = fmaf(f.t2, f.t2, hd2);
+    g.D = f.h * rd * phid;
   }
   const float ir1 = __fdividef(1.f, r1), ir2 = __fdividef(1.f, r2);
-  g.Dl = -(f.h * rd) * phid * float(kInv2Pi);
-  g.D_t1 = f.h * ir1 * float(kInv2Pi);
-  g.D_t2 = -f.h * ir2 * float(kInv2Pi);
-  g.D_h = -(eps_d2 * phid * rd - hh * f.L * (hd2 - tt) * ir1 * ir2) * (rd * rd) * float(kInv2Pi);
+  g.Dt1 = -f.h * ir1;
+  g.Dt2 = f.h * ir2;
+  g.Dh = (eps_d2 * phid * rd - hh * f.L * (hd2 - tt) * ir1 * ir2) * (rd * rd);
   return g;
 }
 
@@ -263,6 +357,20 @@ __device__ __forceinline__ void frame_to_endpoints(const Panel<T>& p, const Fram
   day = Ft1 * p.ty - na * p.tx;
   dbx = Ft2 * p.tx + nb * p.ty;
   dby = Ft2 * p.ty - nb * p.tx;
+}
+
+// Float chain rule with an approximate reciprocal of L (L > 0).
+__device__ __forceinline__ void frame_to_endpoints_f(float tx, float ty, const Frame<float>& f,
+                                                     float Ft1, float Ft2, float Fh, float& dax,
+                                                     float& day, float& dbx, float& dby) {
+  const float iL = __fdividef(1.f, f.L);
+  const float s = f.h * (Ft1 + Ft2) * iL;
+  const float na = fmaf(f.t2 * iL, Fh, -s);
+  const float nb = fmaf(-f.t1 * iL, Fh, s);
+  dax = fmaf(na, ty, Ft1 * tx);
+  day = fmaf(-na, tx, Ft1 * ty);
+  dbx = fmaf(nb, ty, Ft2 * tx);
+  dby = fmaf(-nb, tx, Ft2 * ty);
 }
 
 // Signed angle subtended at (x,y) by the segment a->b:

@@ -41,6 +41,7 @@ struct VjpArgs {
   T ec2, ed2;
   double ec2d, ed2d;
   T near2;
+  float nfac;          // near_factor (float path)
   int64_t chunk;       // points per blockIdx.y
   double* part;        // [gridDim.y][P][11]
   double* qpart;       // [gridDim.y][Nb][3]
@@ -158,12 +159,37 @@ __global__ void __launch_bounds__(kVB) k_vjp(VjpArgs<T> a) {
   }
 }
 
+// Float pair of the adjoint with the -2 pi-scaled partials of
+// layer_grad_hat: the 11 sums come out multiplied by -2 pi.
+template <bool SAME>
+__device__ __forceinline__ void pair_adj_f(const Panel<float>& p, const Frame<float>& f, float hh,
+                                           float r0, float r1, float r2, float ec2, float ed2,
+                                           float* acc) {
+  const GradHat g = layer_grad_hat(f, hh, ec2, ed2, SAME);
+  const float al = -(r0 * p.wd[0] + r1 * p.wd[1] + r2 * p.wd[2]);
+  const float be = r0 * p.wc[0] + r1 * p.wc[1] + r2 * p.wc[2];
+  const float gt1 = al * g.Dt1 + be * g.St1;
+  const float gt2 = al * g.Dt2 + be * g.St2;
+  const float gh = al * g.Dh + be * g.Sh;
+  acc[0] += gt1;
+  acc[1] += gt2;
+  acc[2] += f.h * (gt1 + gt2);
+  acc[3] += f.t1 * gh;
+  acc[4] += gh;
+  acc[5] -= r0 * g.D;
+  acc[6] -= r1 * g.D;
+  acc[7] -= r2 * g.D;
+  acc[8] += r0 * g.S;
+  acc[9] += r1 * g.S;
+  acc[10] += r2 * g.S;
+}
+
 // Float adjoint of the mixed path: one thread per panel (or boundary
 // segment), the block's points staged 256 at a time as (x, y, r0, r1), r2;
 // float sums per tile are added to double totals kept in shared memory
 // (thread-owned columns), so the registers hold only the panel, the tile sums
 // and the pair's temporaries.  Near pairs are skipped (evaluated in double by
-// k_near_adjoint).
+// k_near_adjoint); the rounded frame of the near test is the pair's frame.
 constexpr int kVT = 256;
 
 template <bool SAME, bool NEAR>
@@ -171,6 +197,7 @@ __global__ void __launch_bounds__(kVB) k_vjp_f32(VjpArgs<float> a) {
   __shared__ float4 sq[kVT];
   __shared__ float sr2[kVT];
   __shared__ double stot[kNP][kVB];
+  __shared__ float bred[4 * (kVB / 32)];
   const int tid = threadIdx.x;
   const int ptiles = (a.P + kVB - 1) / kVB;
   const bool is_pan = (int)blockIdx.x < ptiles;
@@ -179,10 +206,14 @@ __global__ void __launch_bounds__(kVB) k_vjp_f32(VjpArgs<float> a) {
   const int64_t s0 = (int64_t)blockIdx.y * a.chunk;
   const int64_t s1 = min(a.n, s0 + a.chunk);
   Panel<float> p{};
+  float thr = 0.f;
+  float4 zone = make_float4(0.f, 0.f, -1.f, -1.f);
   float bax = 0, bay = 0, bbx = 0, bby = 0;
   if (live) {
     if (is_pan) {
       p = a.pan[idx];
+      thr = near_thr(p.L, a.near2);
+      zone = near_zone(p, a.nfac);
     } else {
       bax = a.vert[2 * idx]; bay = a.vert[2 * idx + 1];
       bbx = a.vert[2 * idx + 2]; bby = a.vert[2 * idx + 3];
@@ -193,10 +224,20 @@ __global__ void __launch_bounds__(kVB) k_vjp_f32(VjpArgs<float> a) {
   for (int64_t base = s0; base < s1; base += kVT) {
     const int cnt = (int)min((int64_t)kVT, s1 - base);
     __syncthreads();
+    float x0 = __int_as_float(0x7f800000), y0 = x0, x1 = -x0, y1 = -x0;
     for (int e = tid; e < cnt; e += kVB) {
       const int64_t i = base + e;
-      sq[e] = make_float4(a.xy[2 * i], a.xy[2 * i + 1], a.w[3 * i], a.w[3 * i + 1]);
+      const float x = a.xy[2 * i], y = a.xy[2 * i + 1];
+      sq[e] = make_float4(x, y, a.w[3 * i], a.w[3 * i + 1]);
       sr2[e] = a.w[3 * i + 2];
+      x0 = fminf(x0, x); y0 = fminf(y0, y); x1 = fmaxf(x1, x); y1 = fmaxf(y1, y);
+    }
+    // near pairs are possible only in warps with a panel whose near zone
+    // meets the tile's bounding box
+    bool tested = false;
+    if (NEAR && is_pan) {
+      const float4 bb = block_bbox(x0, y0, x1, y1, tid < cnt, bred);
+      tested = __any_sync(0xffffffffu, live && boxes_meet(zone, bb));
     }
     __syncthreads();
     if (!live) continue;
@@ -204,10 +245,20 @@ __global__ void __launch_bounds__(kVB) k_vjp_f32(VjpArgs<float> a) {
 #pragma unroll
     for (int k = 0; k < kNP; ++k) acc[k] = 0.f;
     if (is_pan) {
-      for (int k = 0; k < cnt; ++k) {
-        const float4 q = sq[k];
-        if (NEAR && near_pair(p, q.x, q.y, a.near2)) continue;
-        pair_adj<float, SAME>(p, q.x, q.y, q.z, q.w, sr2[k], a.ec2, a.ed2, acc);
+      if (tested) {
+        for (int k = 0; k < cnt; ++k) {
+          const float4 q = sq[k];
+          const Frame<float> f = frame_rn(p.ax, p.ay, p.tx, p.ty, p.L, q.x, q.y);
+          const float hh = __fmul_rn(f.h, f.h);
+          if (near_test(f, hh, thr)) continue;
+          pair_adj_f<SAME>(p, f, hh, q.z, q.w, sr2[k], a.ec2, a.ed2, acc);
+        }
+      } else {
+        for (int k = 0; k < cnt; ++k) {
+          const float4 q = sq[k];
+          const Frame<float> f = frame_rn(p.ax, p.ay, p.tx, p.ty, p.L, q.x, q.y);
+          pair_adj_f<SAME>(p, f, f.h * f.h, q.z, q.w, sr2[k], a.ec2, a.ed2, acc);
+        }
       }
     } else {
       for (int k = 0; k < cnt; ++k) {
@@ -225,7 +276,7 @@ __global__ void __launch_bounds__(kVB) k_vjp_f32(VjpArgs<float> a) {
   if (is_pan) {
     double* o = a.part + ((size_t)blockIdx.y * a.P + idx) * kNP;
 #pragma unroll
-    for (int k = 0; k < kNP; ++k) o[k] = stot[k][tid];
+    for (int k = 0; k < kNP; ++k) o[k] = stot[k][tid] * -kInv2Pi;
   } else {
     double* o = a.qpart + ((size_t)blockIdx.y * a.Nb + idx) * 3;
     for (int k = 0; k < 3; ++k) o[k] = stot[k][tid] * kInv2Pi;
@@ -331,6 +382,7 @@ static int vjp_pass(bem_ctx* c, int64_t n, const T* xy, const T* w, bool boundar
   a.ec2d = c->opts.eps_c * c->opts.eps_c;
   a.ed2d = c->opts.eps_d * c->opts.eps_d;
   a.near2 = T(c->opts.near_factor * c->opts.near_factor);
+  a.nfac = float(c->opts.near_factor);
   a.chunk = chunk;
   a.part = (double*)c->part.p;
   a.qpart = (double*)((char*)c->part.p + pbytes);

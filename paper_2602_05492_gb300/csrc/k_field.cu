@@ -27,6 +27,7 @@ struct FieldArgs {
   T ec2, ed2;          // eps_c^2, eps_d^2
   double ec2d, ed2d;
   T near2;             // (near_factor)^2, mixed precision only
+  float nfac;          // near_factor, mixed precision only
   const T* target;     // clamp target or null
   T* out;              // colours [n][3] or null
   T* resid;            // residual [n][3] or null
@@ -35,15 +36,12 @@ struct FieldArgs {
   const double* near_add;  // double near-field sum [n][3] or null
 };
 
-// Sum over one shared-memory tile of panels (near pairs skipped when NEAR).
-template <typename T, bool SAME, bool NEAR>
+// Sum over one shared-memory tile of panels (double path).
+template <typename T, bool SAME>
 __device__ __forceinline__ void tile_accum(const Panel<T>* tile, int cnt, T x, T y,
                                            const FieldArgs<T>& a, T& s0, T& s1, T& s2) {
   for (int k = 0; k < cnt; ++k) {
     const Panel<T>& p = tile[k];
-    if constexpr (NEAR) {
-      if (near_pair(p, x, y, a.near2)) continue;
-    }
     Frame<T> f = frame(p, x, y);
     LayerVals<T> v = layer_values(f, a.ec2, a.ed2, SAME);
     s0 += -p.wd[0] * v.Dl + p.wc[0] * v.S;
@@ -52,61 +50,12 @@ __device__ __forceinline__ void tile_accum(const Panel<T>* tile, int cnt, T x, T
   }
 }
 
-template <typename T, bool SAME, bool NEAR>
-__global__ void __launch_bounds__(kFB) k_field(FieldArgs<T> a) {
-  __shared__ Panel<T> tile[kFB];
-  __shared__ T sv[2 * (kFB + 1)];
-  __shared__ T su[3 * kFB];
-  __shared__ double red[kFB / 32];
+// Colour, residual and the block's loss partial from the handle sum s and the
+// boundary angle sum b (without its 1/(2 pi)).
+template <typename T>
+__device__ __forceinline__ void field_epilogue(const FieldArgs<T>& a, int64_t i, bool live, T s0,
+                                               T s1, T s2, T b0, T b1, T b2, double* red) {
   const int tid = threadIdx.x;
-  const int64_t i = (int64_t)blockIdx.x * kFB + tid;
-  const bool live = i < a.n;
-  T x = T(0.5), y = T(0.5);
-  if (live) { x = a.xy[2 * i]; y = a.xy[2 * i + 1]; }
-  T s0 = 0, s1 = 0, s2 = 0;
-  const int p0 = a.split_out ? blockIdx.y * a.pchunk : 0;
-  const int p1 = a.split_out ? min(a.P, p0 + a.pchunk) : a.P;
-  for (int base = p0; base < p1; base += kFB) {
-    __syncthreads();
-    if (base + tid < p1) tile[tid] = a.pan[base + tid];
-    __syncthreads();
-    tile_accum<T, SAME, NEAR>(tile, min(kFB, p1 - base), x, y, a, s0, s1, s2);
-  }
-  if (a.split_out) {
-    if (live) {
-      double* o = a.split_out + ((size_t)blockIdx.y * a.n + i) * 3;
-      o[0] = double(s0);
-      o[1] = double(s1);
-      o[2] = double(s2);
-    }
-    return;
-  }
-  // boundary double layer with the (double) boundary solution
-  T b0 = 0, b1 = 0, b2 = 0;
-  if (a.ub) {
-    for (int base = 0; base < a.Nb; base += kFB) {
-      __syncthreads();
-      int cnt = min(kFB, a.Nb - base);
-      if (tid < cnt) {
-        sv[2 * tid] = a.vert[2 * (base + tid)];
-        sv[2 * tid + 1] = a.vert[2 * (base + tid) + 1];
-        su[3 * tid] = T(a.ub[3 * (base + tid)]);
-        su[3 * tid + 1] = T(a.ub[3 * (base + tid) + 1]);
-        su[3 * tid + 2] = T(a.ub[3 * (base + tid) + 2]);
-      }
-      if (tid == 0) {
-        sv[2 * cnt] = a.vert[2 * (base + cnt)];
-        sv[2 * cnt + 1] = a.vert[2 * (base + cnt) + 1];
-      }
-      __syncthreads();
-      for (int k = 0; k < cnt; ++k) {
-        T phi = seg_angle(sv[2 * k], sv[2 * k + 1], sv[2 * k + 2], sv[2 * k + 3], x, y);
-        b0 += phi * su[3 * k];
-        b1 += phi * su[3 * k + 1];
-        b2 += phi * su[3 * k + 2];
-      }
-    }
-  }
   double u0 = a.mean0 + double(b0) * kInv2Pi + double(s0);
   double u1 = a.mean1 + double(b1) * kInv2Pi + double(s1);
   double u2 = a.mean2 + double(b2) * kInv2Pi + double(s2);
@@ -144,6 +93,182 @@ __global__ void __launch_bounds__(kFB) k_field(FieldArgs<T> a) {
       a.loss_part[blockIdx.x] = s;
     }
   }
+}
+
+template <typename T, bool SAME>
+__global__ void __launch_bounds__(kFB) k_field(FieldArgs<T> a) {
+  __shared__ Panel<T> tile[kFB];
+  __shared__ T sv[2 * (kFB + 1)];
+  __shared__ T su[3 * kFB];
+  __shared__ double red[kFB / 32];
+  const int tid = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * kFB + tid;
+  const bool live = i < a.n;
+  T x = T(0.5), y = T(0.5);
+  if (live) { x = a.xy[2 * i]; y = a.xy[2 * i + 1]; }
+  T s0 = 0, s1 = 0, s2 = 0;
+  const int p0 = a.split_out ? blockIdx.y * a.pchunk : 0;
+  const int p1 = a.split_out ? min(a.P, p0 + a.pchunk) : a.P;
+  for (int base = p0; base < p1; base += kFB) {
+    __syncthreads();
+    if (base + tid < p1) tile[tid] = a.pan[base + tid];
+    __syncthreads();
+    tile_accum<T, SAME>(tile, min(kFB, p1 - base), x, y, a, s0, s1, s2);
+  }
+  if (a.split_out) {
+    if (live) {
+      double* o = a.split_out + ((size_t)blockIdx.y * a.n + i) * 3;
+      o[0] = double(s0);
+      o[1] = double(s1);
+      o[2] = double(s2);
+    }
+    return;
+  }
+  // boundary double layer with the (double) boundary solution
+  T b0 = 0, b1 = 0, b2 = 0;
+  if (a.ub) {
+    for (int base = 0; base < a.Nb; base += kFB) {
+      __syncthreads();
+      int cnt = min(kFB, a.Nb - base);
+      if (tid < cnt) {
+        sv[2 * tid] = a.vert[2 * (base + tid)];
+        sv[2 * tid + 1] = a.vert[2 * (base + tid) + 1];
+        su[3 * tid] = T(a.ub[3 * (base + tid)]);
+        su[3 * tid + 1] = T(a.ub[3 * (base + tid) + 1]);
+        su[3 * tid + 2] = T(a.ub[3 * (base + tid) + 2]);
+      }
+      if (tid == 0) {
+        sv[2 * cnt] = a.vert[2 * (base + cnt)];
+        sv[2 * cnt + 1] = a.vert[2 * (base + cnt) + 1];
+      }
+      __syncthreads();
+      for (int k = 0; k < cnt; ++k) {
+        T phi = seg_angle(sv[2 * k], sv[2 * k + 1], sv[2 * k + 2], sv[2 * k + 3], x, y);
+        b0 += phi * su[3 * k];
+        b1 += phi * su[3 * k + 1];
+        b2 += phi * su[3 * k + 2];
+      }
+    }
+  }
+  field_epilogue<T>(a, i, live, s0, s1, s2, b0, b1, b2, red);
+}
+
+// Float kernel of the mixed path.  Panels are staged as PanelF (three
+// 128-bit shared-memory loads per panel, the layer constants folded into the
+// jumps); one rounded frame per pair serves the near-field test and the layer
+// formulas.  With NEAR, each tile puts first the panels whose near zone meets
+// the block's bounding box; only those pairs take the near test, the rest
+// cannot be near.  The boundary vertices are walked in order so that each
+// vertex offset is formed once.
+template <bool SAME>
+__device__ __forceinline__ void pair_acc_f(const float4 A, const float4 B, const float4 C,
+                                           const Frame<float>& f, float hh, float ec2, float ed2,
+                                           float& s0, float& s1, float& s2) {
+  // A = (ax, ay, tx, ty), B = (L, thr, wd0', wd1'), C = (wd2', wc0', wc1', wc2')
+  float Dh, Sh;
+  pair_fwd_f(f, hh, ec2, ed2, SAME, Dh, Sh);
+  s0 = fmaf(B.z, Dh, fmaf(C.y, Sh, s0));
+  s1 = fmaf(B.w, Dh, fmaf(C.z, Sh, s1));
+  s2 = fmaf(C.x, Dh, fmaf(C.w, Sh, s2));
+}
+
+template <bool SAME, bool NEAR>
+__global__ void __launch_bounds__(kFB) k_field_f32(FieldArgs<float> a) {
+  __shared__ float4 tile[3 * kFB];
+  __shared__ float2 sv[kFB + 1];
+  __shared__ float4 su[kFB];
+  __shared__ double red[kFB / 32];
+  __shared__ float bred[4 * (kFB / 32)];
+  __shared__ int wcnt[kFB / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kFB + tid;
+  const bool live = i < a.n;
+  float x = 0.5f, y = 0.5f;
+  if (live) { x = a.xy[2 * i]; y = a.xy[2 * i + 1]; }
+  float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
+  if constexpr (NEAR) bb = block_bbox(x, y, x, y, live, bred);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  const int p0 = a.split_out ? blockIdx.y * a.pchunk : 0;
+  const int p1 = a.split_out ? min(a.P, p0 + a.pchunk) : a.P;
+  for (int base = p0; base < p1; base += kFB) {
+    const int cnt = min(kFB, p1 - base);
+    int nf = 0;   // panels [0, nf) of the tile may have near pairs
+    __syncthreads();
+    if constexpr (NEAR) {
+      Panel<float> p{};
+      bool cand = false;
+      if (tid < cnt) {
+        p = a.pan[base + tid];
+        cand = boxes_meet(near_zone(p, a.nfac), bb);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, cand);
+      if (lane == 0) wcnt[warp] = __popc(m);
+      __syncthreads();
+      int before = 0;
+#pragma unroll
+      for (int w = 0; w < kFB / 32; ++w) {
+        before += w < warp ? wcnt[w] : 0;
+        nf += wcnt[w];
+      }
+      if (tid < cnt) {
+        const int below = __popc(m & ((1u << lane) - 1u));
+        const int slot = cand ? before + below : nf + (warp * 32 - before) + (lane - below);
+        reinterpret_cast<PanelF*>(tile)[slot] = stage_panel(p, a.near2);
+      }
+    } else {
+      if (tid < cnt) reinterpret_cast<PanelF*>(tile)[tid] = stage_panel(a.pan[base + tid], 0.f);
+    }
+    __syncthreads();
+    for (int k = 0; k < nf; ++k) {
+      const float4 A = tile[3 * k], B = tile[3 * k + 1], C = tile[3 * k + 2];
+      const Frame<float> f = frame_rn(A.x, A.y, A.z, A.w, B.x, x, y);
+      const float hh = __fmul_rn(f.h, f.h);
+      if (near_test(f, hh, B.y)) continue;
+      pair_acc_f<SAME>(A, B, C, f, hh, a.ec2, a.ed2, s0, s1, s2);
+    }
+    for (int k = nf; k < cnt; ++k) {
+      const float4 A = tile[3 * k], B = tile[3 * k + 1], C = tile[3 * k + 2];
+      const Frame<float> f = frame_rn(A.x, A.y, A.z, A.w, B.x, x, y);
+      pair_acc_f<SAME>(A, B, C, f, f.h * f.h, a.ec2, a.ed2, s0, s1, s2);
+    }
+  }
+  if (a.split_out) {
+    if (live) {
+      double* o = a.split_out + ((size_t)blockIdx.y * a.n + i) * 3;
+      o[0] = double(s0);
+      o[1] = double(s1);
+      o[2] = double(s2);
+    }
+    return;
+  }
+  float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+  if (a.ub) {
+    for (int base = 0; base < a.Nb; base += kFB) {
+      __syncthreads();
+      const int cnt = min(kFB, a.Nb - base);
+      if (tid < cnt) {
+        const int j = base + tid;
+        sv[tid] = make_float2(a.vert[2 * j], a.vert[2 * j + 1]);
+        su[tid] = make_float4(float(a.ub[3 * j]), float(a.ub[3 * j + 1]), float(a.ub[3 * j + 2]),
+                              0.f);
+      }
+      if (tid == 0) sv[cnt] = make_float2(a.vert[2 * (base + cnt)], a.vert[2 * (base + cnt) + 1]);
+      __syncthreads();
+      float dax = sv[0].x - x, day = sv[0].y - y;
+      for (int k = 0; k < cnt; ++k) {
+        const float2 w = sv[k + 1];
+        const float dbx = w.x - x, dby = w.y - y;
+        const float phi = fm_atan2(dax * dby - day * dbx, dax * dbx + day * dby);
+        const float4 u = su[k];
+        b0 = fmaf(phi, u.x, b0);
+        b1 = fmaf(phi, u.y, b1);
+        b2 = fmaf(phi, u.z, b2);
+        dax = dbx;
+        day = dby;
+      }
+    }
+  }
+  field_epilogue<float>(a, i, live, s0, s1, s2, b0, b1, b2, red);
 }
 
 // sum of per-block partials in fixed order -> out[0]
@@ -219,6 +344,7 @@ static FieldArgs<T> make_args(bem_ctx* c) {
   a.ec2d = c->opts.eps_c * c->opts.eps_c;
   a.ed2d = c->opts.eps_d * c->opts.eps_d;
   a.near2 = T(c->opts.near_factor * c->opts.near_factor);
+  a.nfac = float(c->opts.near_factor);
   return a;
 }
 
@@ -229,15 +355,15 @@ static void launch_field(bem_ctx* c, const FieldArgs<T>& a, dim3 grid) {
   if constexpr (sizeof(T) == 4) {
     const bool near = c->opts.near_factor > 0;
     if (same) {
-      if (near) k_field<T, true, true><<<grid, kFB, 0, S(c)>>>(a);
-      else k_field<T, true, false><<<grid, kFB, 0, S(c)>>>(a);
+      if (near) k_field_f32<true, true><<<grid, kFB, 0, S(c)>>>(a);
+      else k_field_f32<true, false><<<grid, kFB, 0, S(c)>>>(a);
     } else {
-      if (near) k_field<T, false, true><<<grid, kFB, 0, S(c)>>>(a);
-      else k_field<T, false, false><<<grid, kFB, 0, S(c)>>>(a);
+      if (near) k_field_f32<false, true><<<grid, kFB, 0, S(c)>>>(a);
+      else k_field_f32<false, false><<<grid, kFB, 0, S(c)>>>(a);
     }
   } else {
-    if (same) k_field<T, true, false><<<grid, kFB, 0, S(c)>>>(a);
-    else k_field<T, false, false><<<grid, kFB, 0, S(c)>>>(a);
+    if (same) k_field<T, true><<<grid, kFB, 0, S(c)>>>(a);
+    else k_field<T, false><<<grid, kFB, 0, S(c)>>>(a);
   }
   BEM_LAUNCHED(c);
 }

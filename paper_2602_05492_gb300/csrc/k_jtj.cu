@@ -40,12 +40,48 @@ __global__ void k_phi_rows(const T* __restrict__ xy, int ns, const T* __restrict
 // per-block shared-memory table.
 constexpr int kFrowsTable = 256;   // panels per curve covered by the weight table
 
+// One (point, panel) pair of the F rows: the two layer values and the
+// endpoint derivatives (a then b, x then y) of Dl and S.  The double path
+// returns them as they are; the float path returns them multiplied by -2 pi
+// (layer_grad_hat), which the kernel undoes once per output entry.
+template <typename T, bool SAME>
+__device__ __forceinline__ void frows_pair(const Panel<T>& p, T x, T y, T ec2, T ed2, T& Dl, T& S,
+                                           T (&Dd)[4], T (&Sd)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const Frame<float> f = frame_rn(p.ax, p.ay, p.tx, p.ty, p.L, x, y);
+    const GradHat g = layer_grad_hat(f, f.h * f.h, ec2, ed2, SAME);
+    Dl = g.D;
+    S = g.S;
+    if (p.L > 0.f) {
+      frame_to_endpoints_f(p.tx, p.ty, f, g.Dt1, g.Dt2, g.Dh, Dd[0], Dd[1], Dd[2], Dd[3]);
+      frame_to_endpoints_f(p.tx, p.ty, f, g.St1, g.St2, g.Sh, Sd[0], Sd[1], Sd[2], Sd[3]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { Dd[e] = 0.f; Sd[e] = 0.f; }
+    }
+  } else {
+    const Frame<T> f = frame(p, x, y);
+    const LayerGrad<T> g = layer_grad(f, ec2, ed2, SAME);
+    Dl = g.Dl;
+    S = g.S;
+    if (p.L > T(0)) {
+      frame_to_endpoints(p, f, g.D_t1, g.D_t2, g.D_h, Dd[0], Dd[1], Dd[2], Dd[3]);
+      frame_to_endpoints(p, f, g.S_t1, g.S_t2, g.S_h, Sd[0], Sd[1], Sd[2], Sd[3]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { Dd[e] = T(0); Sd[e] = T(0); }
+    }
+  }
+}
+
 template <typename T, bool SAME, bool TR>
 __global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __restrict__ pan,
                         const int* __restrict__ off, const int* __restrict__ Kc,
                         const uint8_t* __restrict__ closed, int C, T ec2, T ed2,
                         void* __restrict__ Fout, int ldf) {
-  __shared__ T wtab[kFrowsTable][8];     // B_j(k/K), B_j((k+1/2)/K)
+  __shared__ __align__(16) T wtab[kFrowsTable][8];     // B_j(k/K), B_j((k+1/2)/K)
+  // the float pair values carry a factor -2 pi (frows_pair)
+  constexpr T kOut = sizeof(T) == 4 ? T(-kInv2Pi) : T(1);
   const int i = blockIdx.y;
   const int K = Kc[i];
   for (int e = threadIdx.x; e < min(K, kFrowsTable) * 4; e += blockDim.x) {
@@ -73,8 +109,9 @@ __global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __rest
   for (int e = 0; e < 2; ++e)
 #pragma unroll
     for (int c = 0; c < 3; ++c) carry[e][c] = 0;
+  const Panel<T>* cp = pan + off[i];
   for (int k = 0; k < K; ++k) {
-    const Panel<T> p = pan[off[i] + k];
+    const Panel<T> p = cp[k];
     T wv[4], wm[4];
     if (k < kFrowsTable) {
 #pragma unroll
@@ -83,39 +120,22 @@ __global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __rest
 #pragma unroll
       for (int j = 0; j < 4; ++j) { wv[j] = bern3(j, T(k) / T(K)); wm[j] = bern3(j, (T(k) + T(0.5)) / T(K)); }
     }
-    Frame<T> f = frame(p, x, y);
-    LayerGrad<T> g = layer_grad(f, ec2, ed2, SAME);
+    T Dl, S, Dd[4], Sd[4];
+    frows_pair<T, SAME>(p, x, y, ec2, ed2, Dl, S, Dd, Sd);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { cd[j] -= wm[j] * g.Dl; cs[j] += wm[j] * g.S; }
-    T da[2][3], db[2][3];
-    if (p.L > T(0)) {
-      T Dax, Day, Dbx, Dby, Sax, Say, Sbx, Sby;
-      frame_to_endpoints(p, f, g.D_t1, g.D_t2, g.D_h, Dax, Day, Dbx, Dby);
-      frame_to_endpoints(p, f, g.S_t1, g.S_t2, g.S_h, Sax, Say, Sbx, Sby);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T a = -p.wd[c], b = p.wc[c];
-        da[0][c] = a * Dax + b * Sax;
-        da[1][c] = a * Day + b * Say;
-        db[0][c] = a * Dbx + b * Sbx;
-        db[1][c] = a * Dby + b * Sby;
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < 2; ++e)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) { da[e][c] = 0; db[e][c] = 0; }
-    }
+    for (int j = 0; j < 4; ++j) { cd[j] -= wm[j] * Dl; cs[j] += wm[j] * S; }
     // vertex k: start of panel k and end of panel k-1
 #pragma unroll
-    for (int e = 0; e < 2; ++e)
+    for (int c = 0; c < 3; ++c) {
+      const T a = -p.wd[c], b = p.wc[c];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T v = da[e][c] + carry[e][c];
-        carry[e][c] = db[e][c];
+      for (int e = 0; e < 2; ++e) {
+        const T v = a * Dd[e] + b * Sd[e] + carry[e][c];
+        carry[e][c] = a * Dd[2 + e] + b * Sd[2 + e];
 #pragma unroll
         for (int j = 0; j < 4; ++j) pos[j][e][c] += wv[j] * v;
       }
+    }
   }
   // vertex K = B(1) = control point 3
 #pragma unroll
@@ -136,10 +156,10 @@ __global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __rest
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         int h = 4 * i + j;
-        base[(size_t)(2 * h) * ldf] = float(pos[j][0][c]);
-        base[(size_t)(2 * h + 1) * ldf] = float(pos[j][1][c]);
-        base[(size_t)(8 * C + h) * ldf] = float(cd[j]);
-        base[(size_t)(12 * C + h) * ldf] = float(cs[j]);
+        base[(size_t)(2 * h) * ldf] = float(kOut * pos[j][0][c]);
+        base[(size_t)(2 * h + 1) * ldf] = float(kOut * pos[j][1][c]);
+        base[(size_t)(8 * C + h) * ldf] = float(kOut * cd[j]);
+        base[(size_t)(12 * C + h) * ldf] = float(kOut * cs[j]);
       }
     }
     return;
@@ -151,56 +171,18 @@ __global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __rest
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int h = 4 * i + j;
-      row[2 * h] = double(pos[j][0][c]);
-      row[2 * h + 1] = double(pos[j][1][c]);
-      row[8 * C + h] = double(cd[j]);
-      row[12 * C + h] = double(cs[j]);
+      row[2 * h] = double(kOut * pos[j][0][c]);
+      row[2 * h + 1] = double(kOut * pos[j][1][c]);
+      row[8 * C + h] = double(kOut * cd[j]);
+      row[12 * C + h] = double(kOut * cs[j]);
     }
   }
-}
-
-// bf16 rows phi_j(x_s)/(2 pi): Phi[s][j], row stride Nb
-__global__ void k_phi_rows_bf16(const float* __restrict__ xy, int ns, const float* __restrict__ vert,
-                                int Nb, __nv_bfloat16* __restrict__ phi) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)ns * Nb) return;
-  int s = (int)(t / Nb), j = (int)(t % Nb);
-  float a = seg_angle(vert[2 * j], vert[2 * j + 1], vert[2 * j + 2], vert[2 * j + 3], xy[2 * s],
-                      xy[2 * s + 1]);
-  phi[t] = __float2bfloat16_rn(a * float(kInv2Pi));
 }
 
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
-}
-
-// tf32 hi/lo split of phi_j(x_s)/(2 pi): hi[s][j], lo[s][j]
-__global__ void k_phi_rows_x3(const float* __restrict__ xy, int ns, const float* __restrict__ vert,
-                              int Nb, float* __restrict__ hi, float* __restrict__ lo) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)ns * Nb) return;
-  int s = (int)(t / Nb), j = (int)(t % Nb);
-  float a = seg_angle(vert[2 * j], vert[2 * j + 1], vert[2 * j + 2], vert[2 * j + 3], xy[2 * s],
-                      xy[2 * s + 1]) *
-            float(kInv2Pi);
-  float h = tf32_round(a);
-  hi[t] = h;
-  lo[t] = tf32_round(a - h);
-}
-
-// tf32 hi/lo split of Mt[c*nc + col][j] = Mc[c][j][col]
-__global__ void k_mt_x3(const double* __restrict__ Mc, int Nb, int nc, float* __restrict__ hi,
-                        float* __restrict__ lo) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int row = blockIdx.y;
-  if (j >= Nb) return;
-  int c = row / nc, col = row % nc;
-  double v = Mc[((size_t)c * Nb + j) * nc + col];
-  float h = tf32_round((float)v);
-  hi[(size_t)row * Nb + j] = h;
-  lo[(size_t)row * Nb + j] = tf32_round((float)(v - (double)h));
 }
 
 // Phi rows of a chunk of samples written from the segment side: thread j
@@ -329,16 +311,6 @@ __global__ void k_g_assemble(const double* __restrict__ gparts, int nparts, int 
   g[t] = scale * s;
 }
 
-// Mt[c*nc + col][j] = bf16(Mc[c][j][col])
-__global__ void k_mt_bf16(const double* __restrict__ Mc, int Nb, int nc,
-                          __nv_bfloat16* __restrict__ Mt) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int row = blockIdx.y;             // c*nc + col
-  if (j >= Nb) return;
-  int c = row / nc, col = row % nc;
-  Mt[(size_t)row * Nb + j] = __float2bfloat16_rn((float)Mc[((size_t)c * Nb + j) * nc + col]);
-}
-
 // Hc[c][i][j] = sum over splits of part[split][c][i][j] (upper blocks) in
 // fixed order, mirrored to the lower triangle
 __global__ void k_syrk_reduce(const float* __restrict__ part, int splits, int nc,
@@ -463,9 +435,81 @@ static int jtj_t(bem_ctx* c, int64_t n, const T* xy, double* Hout) {
   return cuda_check(c, cudaGetLastError(), "jtj");
 }
 
-// Stacked right-hand sides M_c = A^+ df_b,c/dtheta in double (shared by both paths).
+// The A operand of the tensor-core J-row contraction straight from Df:
+//   Mt[c nc + col][j] = M_c[j][col] = sum_i W[j][i] Df_c[i][col]
+// in fp32 (W = A^+ as float, Df converted on load), 64 x 64 tiles of 4 x 4
+// outputs per thread, written as bf16 or as the tf32 hi/lo pair.  The result
+// is rounded to bf16 / tf32 at once, so fp32 accumulation loses nothing the
+// J rows keep.
+template <bool X3>
+__global__ void __launch_bounds__(256) k_mt_sgemm(const float* __restrict__ W,
+                                                  const double* __restrict__ Df, int Nb, int nc,
+                                                  void* __restrict__ out0, void* __restrict__ out1) {
+  __shared__ float As[16][64 + 4];   // [k][row of Mt]
+  __shared__ float Bs[16][64 + 4];   // [k][j]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int j0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
+  const int rows = 3 * nc;
+  float acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+  for (int i0 = 0; i0 < Nb; i0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      const int kk = e >> 6, rr = e & 63;
+      const int r = r0 + rr, i = i0 + kk;
+      float v = 0.f;
+      if (r < rows && i < Nb) {
+        const int ch = r / nc, col = r - ch * nc;
+        v = (float)Df[((size_t)ch * Nb + i) * nc + col];
+      }
+      As[kk][rr] = v;
+    }
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      const int jj = e >> 4, kk = e & 15;
+      const int j = j0 + jj, i = i0 + kk;
+      Bs[kk][jj] = (j < Nb && i < Nb) ? W[(size_t)j * Nb + i] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int r = r0 + ty * 4 + p;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + tx * 4 + q;
+      if (j >= Nb) continue;
+      const size_t o = (size_t)r * Nb + j;
+      if (X3) {
+        const float hi = tf32_round(acc[p][q]);
+        ((float*)out0)[o] = hi;
+        ((float*)out1)[o] = tf32_round(acc[p][q] - hi);
+      } else {
+        ((__nv_bfloat16*)out0)[o] = __float2bfloat16_rn(acc[p][q]);
+      }
+    }
+  }
+}
+
+// Stacked right-hand sides M_c = A^+ df_b,c/dtheta (Sec. 3.2.3): the F rows
+// at the boundary Gauss points reduced to Df_c, then, when `solve` is set,
+// the double products M_c = A^+ Df_c (the tensor-core path forms its
+// rounded M_c^T itself, k_mt_sgemm).
 template <typename T>
-static int jtj_stacked_rhs(bem_ctx* c) {
+static int jtj_stacked_rhs(bem_ctx* c, bool solve = true) {
   int rc;
   int C = c->sc.C, nc = 16 * C, Nb = c->bd.Nb, n3 = 3 * Nb;
   if ((rc = grow(c, c->Fg, sizeof(double) * 3 * (size_t)n3 * nc))) return rc;
@@ -478,6 +522,8 @@ static int jtj_stacked_rhs(bem_ctx* c) {
   BEM_LAUNCHED(c);
   double* Mc = (double*)c->Mc.p;
   double* Df = (double*)c->Dfc.p;
+  if (!solve) return cuda_check(c, cudaGetLastError(), "stacked rhs");
+  if (!solve) return cuda_check(c, cudaGetLastError(), "stacked rhs");
   for (int ch = 0; ch < 3; ++ch)
     la_dgemm(c, false, false, Nb, nc, Nb, 1.0, c->bd.d_W, Nb, Df + (size_t)ch * Nb * nc, nc, 0.0,
              Mc + (size_t)ch * Nb * nc, nc);
@@ -496,19 +542,23 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   int rc;
   int C = c->sc.C, nc = 16 * C, Nb = c->bd.Nb, nth = c->sc.nth;
   const bool want_g = resid && gout;
-  if ((rc = jtj_stacked_rhs<float>(c))) return rc;
+  if ((rc = jtj_stacked_rhs<float>(c, false))) return rc;
   const size_t es = x3 ? 2 * sizeof(float) : sizeof(__nv_bfloat16);   // bytes per element (all parts)
   // M_c^T, [3 nc][Nb]
   const size_t mt_part = (x3 ? 4 : 2) * 3 * (size_t)nc * Nb;
   if ((rc = grow(c, c->tcMt, es * 3 * (size_t)nc * Nb))) return rc;
   const void* Mt[2] = {c->tcMt.p, (char*)c->tcMt.p + mt_part};
-  if (x3)
-    k_mt_x3<<<dim3((Nb + 127) / 128, 3 * nc), 128, 0, S(c)>>>((const double*)c->Mc.p, Nb, nc,
-                                                               (float*)Mt[0], (float*)Mt[1]);
-  else
-    k_mt_bf16<<<dim3((Nb + 127) / 128, 3 * nc), 128, 0, S(c)>>>((const double*)c->Mc.p, Nb, nc,
-                                                                 (__nv_bfloat16*)Mt[0]);
-  BEM_LAUNCHED(c);
+  {
+    ProfScope _pm(c, "k_mt_sgemm");
+    dim3 grid((Nb + 63) / 64, (3 * nc + 63) / 64);
+    if (x3)
+      k_mt_sgemm<true><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, (const double*)c->Dfc.p, Nb, nc,
+                                               (void*)Mt[0], (void*)Mt[1]);
+    else
+      k_mt_sgemm<false><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, (const double*)c->Dfc.p, Nb, nc,
+                                                (void*)Mt[0], nullptr);
+    BEM_LAUNCHED(c);
+  }
   // per-chunk buffers: Phi [m][Nb], F^T f32 [3nc][ld], J^T [3nc][ld]
   const int64_t chunk = std::min<int64_t>(std::max<int64_t>(n, 1), 262144);
   const int nchunks = (int)((n + chunk - 1) / chunk);
@@ -520,7 +570,6 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   const size_t j_b = (x3 ? 2 : 1) * j_part;
   // gradient work: per chunk handle partial [3nc], q partials per slice
   const int qslices = (int)std::max<int64_t>(1, std::min<int64_t>(64, (chunk + 4095) / 4096));
-  const int qslice_len = (int)((chunk + qslices - 1) / qslices);
   const size_t gh_b = sizeof(double) * (size_t)std::max(nchunks, 1) * kGemvSegs * 3 * nc;
   const size_t q_b = sizeof(double) * (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
   const size_t gb_b = sizeof(double) * 3 * (size_t)nc;

@@ -18,6 +18,8 @@
 //    constraints (one per colour channel).
 #include <cmath>
 
+#include <algorithm>
+
 #include "ctx.h"
 
 namespace bem {
@@ -411,150 +413,222 @@ __global__ void k_constraint_cols(int n, const double* __restrict__ a, double* _
   for (int c = 0; c < 3; ++c) cons[4 * i + 1 + c] = (comp == 5 + c) ? a[h] : 0.0;
 }
 
-// Cholesky of the nb x nb (nb <= 32) diagonal block at (k0,k0): one warp,
-// lane r owns row r of the block in shared memory; no block-wide barriers.
-__global__ void k_potrf_diag(double* __restrict__ Km, int n, int k0, int nb,
-                             int* __restrict__ status) {
+// Blocked right-looking Cholesky K = L L^T in double, 32-column panels.
+// FP64 throughput is low on this GPU, so the sequential parts are kept short:
+// the diagonal block is factored by a 32 x 32 thread block and inverted at
+// once (recursive doubling), the panel below it is the product with that
+// inverse, the trailing update touches the lower triangle only, and the
+// triangular solves use the stored diagonal inverses (one launch per block).
+
+// Cholesky of the nb x nb (nb <= 32) diagonal block at (k0, k0) and the
+// inverse of its factor into Linv[k0/32] (32 x 32, zero-padded).  Thread
+// (r, q) owns entry (r, q).  A pivot that is not positive sets *status.
+__global__ void __launch_bounds__(1024) k_potrf_inv(double* __restrict__ Km, int n, int k0, int nb,
+                                                    double* __restrict__ Linv,
+                                                    int* __restrict__ status) {
   __shared__ double T[32][33];
-  const int lane = threadIdx.x;
-  for (int q = 0; q < nb; ++q) T[lane][q] = lane < nb ? Km[(size_t)(k0 + lane) * n + k0 + q] : 0.0;
-  __syncwarp();
-  for (int j = 0; j < nb; ++j) {
-    double d = T[j][j];
-    if (!(d > 0.0)) {
-      if (lane == 0) *status = 1;
-      d = 1.0;
-    }
-    const double ri = rsqrt(d);        // 1/sqrt(pivot)
-    __syncwarp();
-    if (lane == j) T[j][j] = d * ri;
-    if (lane > j && lane < nb) T[lane][j] *= ri;
-    __syncwarp();
-    if (lane > j && lane < nb) {
-      const double lrj = T[lane][j];
-      for (int q = j + 1; q <= lane; ++q) T[lane][q] -= lrj * T[q][j];
-    }
-    __syncwarp();
-  }
-  if (lane < nb)
-    for (int q = 0; q < nb; ++q) Km[(size_t)(k0 + lane) * n + k0 + q] = q <= lane ? T[lane][q] : 0.0;
-}
-
-// rows i >= k0+nb of the panel: L_i = A_i L_kk^-T (forward substitution per row)
-__global__ void k_trsm_rows(double* __restrict__ Km, int n, int k0, int nb) {
-  __shared__ double Lk[32][33];
-  __shared__ double inv[32];
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    int r = e / nb, q = e % nb;
-    Lk[r][q] = Km[(size_t)(k0 + r) * n + k0 + q];
-  }
+  __shared__ double X[32][33];
+  __shared__ double Y[32][33];
+  __shared__ double piv;
+  const int q = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const bool in = r < nb && q < nb;
+  T[r][q] = (in && q <= r) ? Km[(size_t)(k0 + r) * n + k0 + q] : 0.0;
+  X[r][q] = 0.0;
   __syncthreads();
-  if (threadIdx.x < nb) inv[threadIdx.x] = 1.0 / Lk[threadIdx.x][threadIdx.x];
-  __syncthreads();
-  int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double x[32];
-  double* row = Km + (size_t)i * n + k0;
   for (int j = 0; j < nb; ++j) {
-    double s = row[j];
-    for (int l = 0; l < j; ++l) s -= x[l] * Lk[j][l];
-    x[j] = s * inv[j];
+    if (r == j && q == j) {
+      double d = T[j][j];
+      if (!(d > 0.0)) {
+        atomicExch(status, 1);
+        d = 1.0;
+      }
+      const double sd = sqrt(d);
+      T[j][j] = sd;
+      piv = 1.0 / sd;
+    }
+    __syncthreads();
+    if (q == j && r > j && r < nb) T[r][j] *= piv;
+    __syncthreads();
+    if (q > j && q <= r && r < nb) T[r][q] -= T[r][j] * T[q][j];
+    __syncthreads();
   }
-  for (int j = 0; j < nb; ++j) row[j] = x[j];
-}
-
-// Lt = L^T (lower triangle of Km)
-__global__ void k_transpose_lower(const double* __restrict__ Km, int n, double* __restrict__ Lt) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int i = blockIdx.y;
-  if (j >= n) return;
-  Lt[(size_t)j * n + i] = (j <= i) ? Km[(size_t)i * n + j] : 0.0;
-}
-
-// Triangular solves with four right-hand sides R[n][4], blocked by 32 rows,
-// column oriented: a one-warp kernel solves the 32 x 32 diagonal block
-// (lane = row), then a kernel over all CTAs subtracts that block's
-// contribution from every remaining row.  Forward sweep with L (rows of L),
-// back sweep with L^T (rows of Lt).
-
-// forward: diagonal block [kb, kb+nb) of L y = R
-__global__ void k_trsv_diag_fwd(const double* __restrict__ L, int n, int kb, int nb,
-                                double* __restrict__ R) {
-  const int lane = threadIdx.x, i = kb + lane;
-  const bool in = lane < nb;
-  double r[4];
-  for (int q = 0; q < 4; ++q) r[q] = in ? R[4 * i + q] : 0.0;
-  for (int k = 0; k < nb; ++k) {
-    double y[4];
-    if (lane == k) {
-      const double inv = 1.0 / L[(size_t)i * n + i];
-      for (int q = 0; q < 4; ++q) r[q] *= inv;
+  // inverse of the lower-triangular T: diagonal reciprocals, then for block
+  // sizes s = 1, 2, 4, 8, 16 the off-diagonal block of every 2s x 2s diagonal
+  // block, X_BA = -X_BB T_BA X_AA
+  if (r == q && r < nb) X[r][r] = 1.0 / T[r][r];
+  __syncthreads();
+  for (int sz = 1; sz < 32; sz *= 2) {
+    const int base = r / (2 * sz) * (2 * sz);         // start of r's 2s block
+    const bool off = (r - base) >= sz && (q - base) >= 0 && (q - base) < sz && r < nb && q < nb;
+    if (off) {            // Y = T_BA X_AA  (k over the A block, X_AA lower)
+      double y = 0.0;
+      for (int k = q; k < base + sz; ++k) y += T[r][k] * X[k][q];
+      Y[r][q] = y;
     }
-    for (int q = 0; q < 4; ++q) y[q] = __shfl_sync(0xffffffffu, r[q], k);
-    if (in && lane > k) {
-      const double l = L[(size_t)i * n + kb + k];
-      for (int q = 0; q < 4; ++q) r[q] -= l * y[q];
+    __syncthreads();
+    if (off) {            // X_BA = -X_BB Y  (k over the B block, X_BB lower)
+      double x = 0.0;
+      for (int k = base + sz; k <= r; ++k) x -= X[r][k] * Y[k][q];
+      X[r][q] = x;
     }
+    __syncthreads();
   }
-  if (in)
-    for (int q = 0; q < 4; ++q) R[4 * i + q] = r[q];
+  if (in) Km[(size_t)(k0 + r) * n + k0 + q] = q <= r ? T[r][q] : 0.0;
+  Linv[(size_t)(k0 / 32) * 1024 + r * 32 + q] = (in && q <= r) ? X[r][q] : 0.0;
 }
 
-// back: diagonal block [kb, kb+nb) of L^T x = R (upper triangular rows of Lt)
-__global__ void k_trsv_diag_bwd(const double* __restrict__ Lt, int n, int kb, int nb,
-                                double* __restrict__ R) {
-  const int lane = threadIdx.x, i = kb + lane;
-  const bool in = lane < nb;
-  double r[4];
-  for (int q = 0; q < 4; ++q) r[q] = in ? R[4 * i + q] : 0.0;
-  for (int k = nb - 1; k >= 0; --k) {
-    double y[4];
-    if (lane == k) {
-      const double inv = 1.0 / Lt[(size_t)i * n + i];
-      for (int q = 0; q < 4; ++q) r[q] *= inv;
-    }
-    for (int q = 0; q < 4; ++q) y[q] = __shfl_sync(0xffffffffu, r[q], k);
-    if (in && lane < k) {
-      const double l = Lt[(size_t)i * n + kb + k];
-      for (int q = 0; q < 4; ++q) r[q] -= l * y[q];
-    }
-  }
-  if (in)
-    for (int q = 0; q < 4; ++q) R[4 * i + q] = r[q];
-}
-
-// R[i] -= M[i][kb..kb+nb) . R[kb..kb+nb) for the rows i in [r0, r1)
-// (M = L for the forward sweep, rows below the block; M = Lt for the back
-// sweep, rows above it).  One warp per row.
-__global__ void k_trsv_update(const double* __restrict__ M, int n, int kb, int nb, int r0, int r1,
-                              double* __restrict__ R) {
-  const int row = r0 + blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+// Panel below the diagonal block: L[i][k0 + q] = sum_{l <= q} K[i][k0 + l] Linv[q][l]
+// for the rows i >= k0 + nb; one warp per row, lane q computes column q.
+__global__ void __launch_bounds__(256) k_trsm_panel(double* __restrict__ Km, int n, int k0, int nb,
+                                                    const double* __restrict__ Linv) {
+  __shared__ double Li[32][33];
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x)
+    Li[e >> 5][e & 31] = Linv[(size_t)(k0 / 32) * 1024 + e];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
-  if (row >= r1) return;
-  double s[4] = {0, 0, 0, 0};
-  if (lane < nb) {
-    const double m = M[(size_t)row * n + kb + lane];
-    for (int q = 0; q < 4; ++q) s[q] = m * R[4 * (kb + lane) + q];
+  const int i = k0 + nb + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  double* row = Km + (size_t)i * n + k0;
+  const double a = lane < nb ? row[lane] : 0.0;
+  double x = 0.0;
+  for (int l = 0; l < nb; ++l) {
+    const double al = __shfl_sync(0xffffffffu, a, l);
+    if (l <= lane) x += al * Li[lane][l];
   }
-  for (int o = 16; o; o >>= 1)
-    for (int q = 0; q < 4; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
-  if (lane == 0)
-    for (int q = 0; q < 4; ++q) R[4 * row + q] -= s[q];
+  if (lane < nb) row[lane] = x;
 }
 
-static void chol_solve4(bem_ctx* c, const double* L, const double* Lt, int n, double* R) {
+// Trailing update on the lower triangle: K[i][j] -= sum_l P[i][l] P[j][l]
+// over 64 x 64 tiles (bi, bj), bj <= bi, of the rows/columns >= r0, with the
+// panel P = K[:, k0 .. k0+nb).  Diagonal tiles are computed whole; the strict
+// upper triangle of K is never read.
+__global__ void __launch_bounds__(256) k_syrk_lower(double* __restrict__ Km, int n, int k0, int nb,
+                                                    int r0) {
+  __shared__ double Pa[32][65];
+  __shared__ double Pb[32][65];
+  int t = blockIdx.x, bi = 0;
+  while (t > bi) { t -= bi + 1; ++bi; }
+  const int bj = t;
+  const int i0 = r0 + bi * 64, j0 = r0 + bj * 64;
+  for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+    const int rr = e >> 5, l = e & 31;
+    const int gi = i0 + rr, gj = j0 + rr;
+    Pa[l][rr] = (gi < n && l < nb) ? Km[(size_t)gi * n + k0 + l] : 0.0;
+    Pb[l][rr] = (gj < n && l < nb) ? Km[(size_t)gj * n + k0 + l] : 0.0;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int l = 0; l < nb; ++l) {
+    double pa[4], pb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) pa[a] = Pa[l][ty + 16 * a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) pb[b] = Pb[l][tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += pa[a] * pb[b];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int gi = i0 + ty + 16 * a;
+    if (gi >= n) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gj = j0 + tx + 16 * b;
+      if (gj < n) Km[(size_t)gi * n + gj] -= acc[a][b];
+    }
+  }
+}
+
+// One block step of the forward solve L y = b with four right-hand sides
+// R[n][4]: every CTA forms y_k = Linv_k b_k for block k (CTA 0 stores it in
+// Y), then subtracts L[i][block k] y_k from the rows i below the block that
+// it owns (one warp per row).  b_k is final when step k starts.
+__global__ void __launch_bounds__(256) k_trsv_fwd_step(const double* __restrict__ L, int n, int kb,
+                                                       int nb, const double* __restrict__ Linv,
+                                                       double* __restrict__ R, double* __restrict__ Y) {
+  __shared__ double bk[32][4];
+  __shared__ double yk[32][4];
+  const int tid = threadIdx.x;
+  if (tid < 128) bk[tid >> 2][tid & 3] = (tid >> 2) < nb ? R[4 * (kb + (tid >> 2)) + (tid & 3)] : 0.0;
+  __syncthreads();
+  if (tid < 128) {
+    const int rr = tid >> 2, qq = tid & 3;
+    const double* li = Linv + (size_t)(kb / 32) * 1024 + rr * 32;
+    double y = 0.0;
+    for (int l = 0; l <= rr; ++l) y += li[l] * bk[l][qq];
+    yk[rr][qq] = y;
+    if (blockIdx.x == 0 && rr < nb) Y[4 * (kb + rr) + qq] = y;
+  }
+  __syncthreads();
+  const int lane = tid & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int row = kb + nb + (int)((blockIdx.x * blockDim.x + tid) >> 5); row < n; row += nw) {
+    const double m = lane < nb ? L[(size_t)row * n + kb + lane] : 0.0;
+    double s[4];
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) s[qq] = m * yk[lane][qq];
+    for (int o = 16; o; o >>= 1)
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) s[qq] += __shfl_xor_sync(0xffffffffu, s[qq], o);
+    if (lane == 0)
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) R[4 * row + qq] -= s[qq];
+  }
+}
+
+// One block step of the back solve L^T x = y: every CTA forms
+// x_k = Linv_k^T y_k (CTA 0 stores it in X), then subtracts
+// sum_r L[kb + r][i] x_r from the rows i < kb that it owns (one thread per row).
+__global__ void __launch_bounds__(256) k_trsv_bwd_step(const double* __restrict__ L, int n, int kb,
+                                                       int nb, const double* __restrict__ Linv,
+                                                       double* __restrict__ Yv, double* __restrict__ X) {
+  __shared__ double yk[32][4];
+  __shared__ double xk[32][4];
+  const int tid = threadIdx.x;
+  if (tid < 128) yk[tid >> 2][tid & 3] = (tid >> 2) < nb ? Yv[4 * (kb + (tid >> 2)) + (tid & 3)] : 0.0;
+  __syncthreads();
+  if (tid < 128) {
+    const int rr = tid >> 2, qq = tid & 3;
+    const double* li = Linv + (size_t)(kb / 32) * 1024;
+    double x = 0.0;
+    for (int l = rr; l < 32; ++l) x += li[l * 32 + rr] * yk[l][qq];
+    xk[rr][qq] = x;
+    if (blockIdx.x == 0 && rr < nb) X[4 * (kb + rr) + qq] = x;
+  }
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + tid; i < kb; i += gridDim.x * blockDim.x) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int rr = 0; rr < nb; ++rr) {
+      const double m = L[(size_t)(kb + rr) * n + i];
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) s[qq] += m * xk[rr][qq];
+    }
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) Yv[4 * i + qq] -= s[qq];
+  }
+}
+
+// Solve K X = R (four right-hand sides) with the factor in the lower
+// triangle of L and the diagonal inverses in Linv; the solution replaces R.
+// Y: scratch [n][4].
+static void chol_solve4(bem_ctx* c, const double* L, const double* Linv, int n, double* R,
+                        double* Y) {
+  const int grid = std::max(1, std::min(152, (n + 255) / 256));
   for (int kb = 0; kb < n; kb += 32) {
-    const int nb = min(32, n - kb);
-    k_trsv_diag_fwd<<<1, 32, 0, S(c)>>>(L, n, kb, nb, R);
-    const int r0 = kb + nb;
-    if (r0 < n) k_trsv_update<<<(n - r0 + 7) / 8, 256, 0, S(c)>>>(L, n, kb, nb, r0, n, R);
-    c->launches += 2;
+    k_trsv_fwd_step<<<std::max(1, std::min(152, (n - kb + 7) / 8)), 256, 0, S(c)>>>(
+        L, n, kb, std::min(32, n - kb), Linv, R, Y);
+    BEM_LAUNCHED(c);
   }
   for (int kb = (n - 1) / 32 * 32; kb >= 0; kb -= 32) {
-    const int nb = min(32, n - kb);
-    k_trsv_diag_bwd<<<1, 32, 0, S(c)>>>(Lt, n, kb, nb, R);
-    if (kb > 0) k_trsv_update<<<(kb + 7) / 8, 256, 0, S(c)>>>(Lt, n, kb, nb, 0, kb, R);
-    c->launches += 2;
+    k_trsv_bwd_step<<<grid, 256, 0, S(c)>>>(L, n, kb, std::min(32, n - kb), Linv, Y, R);
+    BEM_LAUNCHED(c);
   }
 }
 
@@ -623,14 +697,16 @@ __global__ void k_kkt_finish(const double* __restrict__ X, const double* __restr
 int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double* delta) {
   int n = c->sc.nth, rc;
   size_t nn = (size_t)n * n * sizeof(double);
+  const size_t nblk = ((size_t)n + 31) / 32;
   if ((rc = grow(c, c->lmK, nn))) return rc;
-  if ((rc = grow(c, c->lmLt, nn))) return rc;
-  if ((rc = grow(c, c->lmL, sizeof(double) * (8 * (size_t)n + 8)))) return rc;
+  if ((rc = grow(c, c->lmLt, sizeof(double) * 1024 * nblk))) return rc;
+  if ((rc = grow(c, c->lmL, sizeof(double) * (12 * (size_t)n + 8)))) return rc;
   double* Km = (double*)c->lmK.p;
-  double* Lt = (double*)c->lmLt.p;
+  double* Linv = (double*)c->lmLt.p;      // [n/32][32][32] inverses of the diagonal blocks
   double* R = (double*)c->lmL.p;          // [n][4] right-hand sides, then solutions
   double* cons = R + 4 * (size_t)n;       // [n][4] constraint columns
-  double* mx = cons + 4 * (size_t)n;
+  double* Ytmp = cons + 4 * (size_t)n;    // [n][4] forward-solve result
+  double* mx = Ytmp + 4 * (size_t)n;
   double* gn = mx + 1;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
   ProfScope _ps(c, "lm_solve");
@@ -641,28 +717,24 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
     k_lm_build<<<grid, 128, 0, S(c)>>>(H, g, n, c->sc.C, c->sc.d_closed, c->d_compat, mx, lam, Km, R);
     c->launches += 2;
   }
-  const int NB = 32;
   {
-  ProfScope _pc(c, "lm_cholesky");
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    int nb = n - k0 < NB ? n - k0 : NB;
-    k_potrf_diag<<<1, 32, 0, S(c)>>>(Km, n, k0, nb, c->d_status);
-    BEM_LAUNCHED(c);
-    int rest = n - k0 - nb;
-    if (rest > 0) {
-      k_trsm_rows<<<(rest + 127) / 128, 128, 0, S(c)>>>(Km, n, k0, nb);
+    ProfScope _pc(c, "lm_cholesky");
+    for (int k0 = 0; k0 < n; k0 += 32) {
+      const int nb = std::min(32, n - k0);
+      k_potrf_inv<<<1, 1024, 0, S(c)>>>(Km, n, k0, nb, Linv, c->d_status);
       BEM_LAUNCHED(c);
-      double* Lp = Km + (size_t)(k0 + nb) * n + k0;
-      double* Ct = Km + (size_t)(k0 + nb) * n + k0 + nb;
-      la_dgemm(c, false, true, rest, rest, nb, -1.0, Lp, n, Lp, n, 1.0, Ct, n);
+      const int r0 = k0 + nb, rest = n - r0;
+      if (rest > 0) {
+        k_trsm_panel<<<(rest + 7) / 8, 256, 0, S(c)>>>(Km, n, k0, nb, Linv);
+        const int tiles = (rest + 63) / 64;
+        k_syrk_lower<<<tiles * (tiles + 1) / 2, 256, 0, S(c)>>>(Km, n, k0, nb, r0);
+        c->launches += 2;
+      }
     }
-  }
   }
   {
     ProfScope _pt(c, "lm_trisolve");
-    k_transpose_lower<<<grid, 128, 0, S(c)>>>(Km, n, Lt);
-    BEM_LAUNCHED(c);
-    chol_solve4(c, Km, Lt, n, R);
+    chol_solve4(c, Km, Linv, n, R, Ytmp);
   }
   // the constraint columns are needed again for the Schur complement
   k_constraint_cols<<<(n + 255) / 256, 256, 0, S(c)>>>(n, c->d_compat, cons);

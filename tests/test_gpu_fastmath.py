@@ -47,3 +47,26 @@ def test_log1p(model):
     fast, ref = model.fastmath(2, _t(z))
     rel = ((fast - ref).abs() / torch.clamp(ref.abs(), min=1e-30)).max().item()
     assert rel < 2e-6, rel
+
+
+def test_atan2_ypos(model):
+    rng = np.random.default_rng(3)
+    ang = rng.uniform(0, math.pi, 200000)
+    r = 10.0 ** rng.uniform(-6, 1, ang.size)
+    y, x = r * np.sin(ang), r * np.cos(ang)
+    special = np.array([[1, 1], [1, -1], [0, -1], [0, 1], [1, 0], [0, 0], [3e-8, 2.0],
+                        [3e-8, -2.0], [1.0, 1e-8]], np.float32)
+    y = np.concatenate([y, special[:, 0]])
+    x = np.concatenate([x, special[:, 1]])
+    fast, ref = model.fastmath(3, _t(y), _t(x))
+    err = (fast - ref).abs().max().item()
+    assert err < 3e-7, err
+
+
+def test_log1p_half(model):
+    rng = np.random.default_rng(4)
+    z = np.concatenate([rng.uniform(-0.999, 10, 100000), rng.uniform(-0.3, 0.3, 100000),
+                        10.0 ** rng.uniform(-9, -1, 50000), -(10.0 ** rng.uniform(-9, -1, 50000))])
+    fast, ref = model.fastmath(4, _t(z))
+    rel = ((fast - ref).abs() / torch.clamp(ref.abs(), min=1e-30)).max().item()
+    assert rel < 2e-6, rel

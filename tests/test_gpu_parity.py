@@ -283,6 +283,24 @@ def test_vjp_mixed_cfg2_linear_in_residual(cfg2):
     assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-4
 
 
+def test_mixed_sample_order_cfg2(cfg2):
+    """The float kernels cull near-field tests by the bounding box of a block's
+    points; a random order (boxes spanning the image, every panel tested)
+    must give the colours and gradient of the pixel order, up to the float
+    summation order."""
+    sc, xy, target, mean, o, idx = cfg2
+    m = _ctx(sc, mean, _bg().BEM_MIXED)
+    perm = np.random.default_rng(11).permutation(xy.shape[0])
+    inv = np.argsort(perm)
+    u0 = m.eval(_t(xy, torch.float32)).double().cpu().numpy()
+    u1 = m.eval(_t(xy[perm], torch.float32)).double().cpu().numpy()[inv]
+    assert np.abs(u0 - u1).max() < 2e-6
+    r = np.random.default_rng(12).normal(size=(xy.shape[0], 3)).astype(np.float32)
+    g0 = m.vjp(_t(xy, torch.float32), _t(r, torch.float32)).cpu().numpy()
+    g1 = m.vjp(_t(xy[perm], torch.float32), _t(r[perm], torch.float32)).cpu().numpy()
+    assert np.linalg.norm(g0 - g1) / np.linalg.norm(g0) < 1e-5
+
+
 # ---- errors ------------------------------------------------------------------------
 
 def test_state_and_argument_errors(cfg1):
