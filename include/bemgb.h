@@ -54,6 +54,12 @@ typedef enum {
 
 enum { BEM_FP64 = 0, BEM_MIXED = 1 };                         /* bem_opts.precision */
 enum { BEM_JTJ_FP64 = 0, BEM_JTJ_BF16 = 1, BEM_JTJ_3XTF32 = 2 }; /* bem_opts.jtj_mode */
+/* bem_opts.lm_solver: how the damped KKT system of lm_step is solved.
+ * AUTO: Cholesky of the equilibrated matrix in float, iterative refinement
+ * against the double residual until the normwise backward error is below
+ * 1e-14, double Cholesky if the float factor fails or the refinement stalls.
+ * FP64: double Cholesky only. */
+enum { BEM_LM_AUTO = 0, BEM_LM_FP64 = 1 };
 
 typedef struct {
     int precision;        /* BEM_FP64: every step in double.  BEM_MIXED: float
@@ -64,9 +70,10 @@ typedef struct {
     double eps_c;         /* regularisation of the w_c (single-layer) term; default 1e-2 */
     int segs_per_side;    /* boundary segments per side of the square, Sec. 3.1.3; default 256 */
     double near_factor;   /* BEM_MIXED: pairs closer than near_factor panel
-                             lengths are evaluated in double; default 2; 0 = never */
+                             lengths are evaluated in double; default 0.5; 0 = never */
     int jtj_mode;         /* arithmetic of the J^T J contraction (BEM_JTJ_*) */
-    int reserved[8];
+    int lm_solver;        /* BEM_LM_AUTO (default) or BEM_LM_FP64 */
+    int reserved[7];
 } bem_opts;
 
 typedef struct {

@@ -23,6 +23,7 @@ BEM_OK, BEM_EINVAL, BEM_ESTATE, BEM_ESINGULAR, BEM_ENOTSPD, BEM_ECUDA, BEM_ETIME
     0, -1, -2, -3, -4, -5, -6, -7
 BEM_FP64, BEM_MIXED = 0, 1
 BEM_JTJ_FP64, BEM_JTJ_BF16, BEM_JTJ_3XTF32 = 0, 1, 2
+BEM_LM_AUTO, BEM_LM_FP64 = 0, 1
 
 _STATUS = {0: "BEM_OK", -1: "BEM_EINVAL", -2: "BEM_ESTATE", -3: "BEM_ESINGULAR",
            -4: "BEM_ENOTSPD", -5: "BEM_ECUDA", -6: "BEM_ETIMEDOUT", -7: "BEM_ENOMEM"}
@@ -32,7 +33,7 @@ class bem_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eps_d", ctypes.c_double),
                 ("eps_c", ctypes.c_double), ("segs_per_side", ctypes.c_int),
                 ("near_factor", ctypes.c_double), ("jtj_mode", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("lm_solver", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class lm_result(ctypes.Structure):
@@ -121,7 +122,7 @@ class BEM:
     """One library context (scene + factored boundary) on one CUDA device."""
 
     def __init__(self, precision=BEM_FP64, eps_d=1e-2, eps_c=1e-2, segs_per_side=256,
-                 near_factor=2.0, jtj_mode=None, device=0):
+                 near_factor=0.5, jtj_mode=None, lm_solver=0, device=0):
         o = bem_opts()
         _lib.bem_default_opts(ctypes.byref(o))
         o.precision = precision
@@ -130,6 +131,7 @@ class BEM:
         o.near_factor = near_factor
         o.jtj_mode = (BEM_JTJ_FP64 if precision == BEM_FP64 else BEM_JTJ_BF16) \
             if jtj_mode is None else jtj_mode
+        o.lm_solver = lm_solver
         self.opts = o
         self.device = device
         h = ctypes.c_void_p()

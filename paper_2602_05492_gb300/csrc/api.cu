@@ -170,8 +170,9 @@ int bem_default_opts(bem_opts* o) {
   o->eps_d = 1e-2;
   o->eps_c = 1e-2;
   o->segs_per_side = 256;
-  o->near_factor = 2.0;
+  o->near_factor = 0.5;
   o->jtj_mode = BEM_JTJ_FP64;
+  o->lm_solver = BEM_LM_AUTO;
   return BEM_OK;
 }
 
@@ -190,6 +191,8 @@ int bem_create(bem_ctx** out, const bem_opts* opts, int device) {
   if (!(o.near_factor >= 0)) return fail(nullptr, BEM_EINVAL, "near_factor must be >= 0");
   if (o.jtj_mode < BEM_JTJ_FP64 || o.jtj_mode > BEM_JTJ_3XTF32)
     return fail(nullptr, BEM_EINVAL, "unknown jtj_mode");
+  if (o.lm_solver != BEM_LM_AUTO && o.lm_solver != BEM_LM_FP64)
+    return fail(nullptr, BEM_EINVAL, "unknown lm_solver");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
     return fail(nullptr, BEM_ECUDA, "no such CUDA device");

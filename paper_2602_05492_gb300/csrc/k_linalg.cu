@@ -423,28 +423,29 @@ __global__ void k_constraint_cols(int n, const double* __restrict__ a, double* _
 // Cholesky of the nb x nb (nb <= 32) diagonal block at (k0, k0) and the
 // inverse of its factor into Linv[k0/32] (32 x 32, zero-padded).  Thread
 // (r, q) owns entry (r, q).  A pivot that is not positive sets *status.
-__global__ void __launch_bounds__(1024) k_potrf_inv(double* __restrict__ Km, int n, int k0, int nb,
-                                                    double* __restrict__ Linv,
+template <typename T_>
+__global__ void __launch_bounds__(1024) k_potrf_inv(T_* __restrict__ Km, int n, int k0, int nb,
+                                                    T_* __restrict__ Linv,
                                                     int* __restrict__ status) {
-  __shared__ double T[32][33];
-  __shared__ double X[32][33];
-  __shared__ double Y[32][33];
-  __shared__ double piv;
+  __shared__ T_ T[32][33];
+  __shared__ T_ X[32][33];
+  __shared__ T_ Y[32][33];
+  __shared__ T_ piv;
   const int q = threadIdx.x & 31, r = threadIdx.x >> 5;
   const bool in = r < nb && q < nb;
-  T[r][q] = (in && q <= r) ? Km[(size_t)(k0 + r) * n + k0 + q] : 0.0;
-  X[r][q] = 0.0;
+  T[r][q] = (in && q <= r) ? Km[(size_t)(k0 + r) * n + k0 + q] : T_(0);
+  X[r][q] = T_(0);
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
     if (r == j && q == j) {
-      double d = T[j][j];
-      if (!(d > 0.0)) {
+      T_ d = T[j][j];
+      if (!(d > T_(0))) {
         atomicExch(status, 1);
-        d = 1.0;
+        d = T_(1);
       }
-      const double sd = sqrt(d);
+      const T_ sd = sqrt(d);
       T[j][j] = sd;
-      piv = 1.0 / sd;
+      piv = T_(1) / sd;
     }
     __syncthreads();
     if (q == j && r > j && r < nb) T[r][j] *= piv;
@@ -455,44 +456,45 @@ __global__ void __launch_bounds__(1024) k_potrf_inv(double* __restrict__ Km, int
   // inverse of the lower-triangular T: diagonal reciprocals, then for block
   // sizes s = 1, 2, 4, 8, 16 the off-diagonal block of every 2s x 2s diagonal
   // block, X_BA = -X_BB T_BA X_AA
-  if (r == q && r < nb) X[r][r] = 1.0 / T[r][r];
+  if (r == q && r < nb) X[r][r] = T_(1) / T[r][r];
   __syncthreads();
   for (int sz = 1; sz < 32; sz *= 2) {
     const int base = r / (2 * sz) * (2 * sz);         // start of r's 2s block
     const bool off = (r - base) >= sz && (q - base) >= 0 && (q - base) < sz && r < nb && q < nb;
     if (off) {            // Y = T_BA X_AA  (k over the A block, X_AA lower)
-      double y = 0.0;
+      T_ y = T_(0);
       for (int k = q; k < base + sz; ++k) y += T[r][k] * X[k][q];
       Y[r][q] = y;
     }
     __syncthreads();
     if (off) {            // X_BA = -X_BB Y  (k over the B block, X_BB lower)
-      double x = 0.0;
+      T_ x = T_(0);
       for (int k = base + sz; k <= r; ++k) x -= X[r][k] * Y[k][q];
       X[r][q] = x;
     }
     __syncthreads();
   }
-  if (in) Km[(size_t)(k0 + r) * n + k0 + q] = q <= r ? T[r][q] : 0.0;
-  Linv[(size_t)(k0 / 32) * 1024 + r * 32 + q] = (in && q <= r) ? X[r][q] : 0.0;
+  if (in) Km[(size_t)(k0 + r) * n + k0 + q] = q <= r ? T[r][q] : T_(0);
+  Linv[(size_t)(k0 / 32) * 1024 + r * 32 + q] = (in && q <= r) ? X[r][q] : T_(0);
 }
 
 // Panel below the diagonal block: L[i][k0 + q] = sum_{l <= q} K[i][k0 + l] Linv[q][l]
 // for the rows i >= k0 + nb; one warp per row, lane q computes column q.
-__global__ void __launch_bounds__(256) k_trsm_panel(double* __restrict__ Km, int n, int k0, int nb,
-                                                    const double* __restrict__ Linv) {
-  __shared__ double Li[32][33];
+template <typename T>
+__global__ void __launch_bounds__(256) k_trsm_panel(T* __restrict__ Km, int n, int k0, int nb,
+                                                    const T* __restrict__ Linv) {
+  __shared__ T Li[32][33];
   for (int e = threadIdx.x; e < 1024; e += blockDim.x)
     Li[e >> 5][e & 31] = Linv[(size_t)(k0 / 32) * 1024 + e];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int i = k0 + nb + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
-  double* row = Km + (size_t)i * n + k0;
-  const double a = lane < nb ? row[lane] : 0.0;
-  double x = 0.0;
+  T* row = Km + (size_t)i * n + k0;
+  const T a = lane < nb ? row[lane] : T(0);
+  T x = T(0);
   for (int l = 0; l < nb; ++l) {
-    const double al = __shfl_sync(0xffffffffu, a, l);
+    const T al = __shfl_sync(0xffffffffu, a, l);
     if (l <= lane) x += al * Li[lane][l];
   }
   if (lane < nb) row[lane] = x;
@@ -502,10 +504,11 @@ __global__ void __launch_bounds__(256) k_trsm_panel(double* __restrict__ Km, int
 // over 64 x 64 tiles (bi, bj), bj <= bi, of the rows/columns >= r0, with the
 // panel P = K[:, k0 .. k0+nb).  Diagonal tiles are computed whole; the strict
 // upper triangle of K is never read.
-__global__ void __launch_bounds__(256) k_syrk_lower(double* __restrict__ Km, int n, int k0, int nb,
+template <typename T>
+__global__ void __launch_bounds__(256) k_syrk_lower(T* __restrict__ Km, int n, int k0, int nb,
                                                     int r0) {
-  __shared__ double Pa[32][65];
-  __shared__ double Pb[32][65];
+  __shared__ T Pa[32][65];
+  __shared__ T Pb[32][65];
   int t = blockIdx.x, bi = 0;
   while (t > bi) { t -= bi + 1; ++bi; }
   const int bj = t;
@@ -513,18 +516,18 @@ __global__ void __launch_bounds__(256) k_syrk_lower(double* __restrict__ Km, int
   for (int e = threadIdx.x; e < 64 * 32; e += 256) {
     const int rr = e >> 5, l = e & 31;
     const int gi = i0 + rr, gj = j0 + rr;
-    Pa[l][rr] = (gi < n && l < nb) ? Km[(size_t)gi * n + k0 + l] : 0.0;
-    Pb[l][rr] = (gj < n && l < nb) ? Km[(size_t)gj * n + k0 + l] : 0.0;
+    Pa[l][rr] = (gi < n && l < nb) ? Km[(size_t)gi * n + k0 + l] : T(0);
+    Pb[l][rr] = (gj < n && l < nb) ? Km[(size_t)gj * n + k0 + l] : T(0);
   }
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
   for (int l = 0; l < nb; ++l) {
-    double pa[4], pb[4];
+    T pa[4], pb[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) pa[a] = Pa[l][ty + 16 * a];
 #pragma unroll
@@ -615,6 +618,361 @@ __global__ void __launch_bounds__(256) k_trsv_bwd_step(const double* __restrict_
   }
 }
 
+// Blocked Cholesky of the n x n matrix in the lower triangle of Km (in place)
+// with the diagonal-block inverses in Linv.
+template <typename T>
+static void chol_factor(bem_ctx* c, T* Km, int n, T* Linv, int* status) {
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int nb = std::min(32, n - k0);
+    k_potrf_inv<T><<<1, 1024, 0, S(c)>>>(Km, n, k0, nb, Linv, status);
+    BEM_LAUNCHED(c);
+    const int r0 = k0 + nb, rest = n - r0;
+    if (rest > 0) {
+      k_trsm_panel<T><<<(rest + 7) / 8, 256, 0, S(c)>>>(Km, n, k0, nb, Linv);
+      const int tiles = (rest + 63) / 64;
+      k_syrk_lower<T><<<tiles * (tiles + 1) / 2, 256, 0, S(c)>>>(Km, n, k0, nb, r0);
+      c->launches += 2;
+    }
+  }
+}
+
+// One 32-column step of the float Cholesky in a single launch.  Every CTA
+// factors the 32 x 32 diagonal block of the working matrix Kf in one warp
+// (the same arithmetic in every CTA, so the same bits).  The last CTA also
+// inverts the factor and stores L_kk and its inverse; CTA (bi, bj), bj <= bi, forms the
+// panel rows of its two 64-row blocks by forward substitution,
+// P = A_panel L_kk^-T, and subtracts P_I P_J^T from its tile of the trailing
+// matrix.  The factor goes to Lf (the panel rows of block bi by CTA (bi, 0))
+// so that no CTA writes what another reads; Kf keeps the trailing updates.
+__global__ void __launch_bounds__(256) k_chol_step_f32(float* __restrict__ Kf, float* __restrict__ Lf,
+                                                       int n, int k0, float* __restrict__ Linv,
+                                                       int* __restrict__ status) {
+  __shared__ float T[32][33], X[32][33];
+  __shared__ float Araw[2][64][33];
+  __shared__ float P[2][32][65];
+  __shared__ float rdg[32];
+  const int tid = threadIdx.x;
+  const int nb = min(32, n - k0), r0 = k0 + nb, rest = n - r0;
+  const bool diag_cta = blockIdx.x == gridDim.x - 1;
+  int bi = 0, bj = 0, i0 = 0, j0 = 0, nsides = 0;
+  if (!diag_cta) {
+    int t = blockIdx.x;
+    while (t > bi) { t -= bi + 1; ++bi; }
+    bj = t;
+    i0 = r0 + 64 * bi;
+    j0 = r0 + 64 * bj;
+    nsides = bi == bj ? 1 : 2;
+  }
+  // loads: the diagonal block and (tile CTAs) the raw panel rows of I and J
+  for (int e = tid; e < 1024; e += 256) {
+    const int r = e >> 5, q = e & 31;
+    T[r][q] = (r < nb && q <= r) ? Kf[(size_t)(k0 + r) * n + k0 + q] : 0.f;
+  }
+  if (!diag_cta)
+    for (int e = tid; e < 2 * 64 * 32; e += 256) {
+      const int sd = e >> 11, rr = (e >> 5) & 63, l = e & 31;
+      const int g = (sd == 0 ? i0 : j0) + rr;
+      Araw[sd][rr][l] = (sd < nsides && g < n && l < nb) ? Kf[(size_t)g * n + k0 + l] : 0.f;
+    }
+  __syncthreads();
+  // ---- factor the diagonal block in warp 0: lane r holds row r in
+  // registers; column j: pivot from lane j, l_rj = a_rj / sqrt(pivot) for
+  // r > j, then a_rq -= l_rj l_qj with l_qj shuffled from lane q (entries
+  // above the diagonal are left as garbage and never used)
+  if (tid < 32) {
+    const int r = tid;
+    float a[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) a[q] = T[r][q];
+    float rd = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j < nb) {
+        float d = __shfl_sync(0xffffffffu, a[j], j);
+        if (!(d > 0.f)) {
+          if (r == 0) atomicExch(status, 1);
+          d = 1.f;
+        }
+        const float rs = rsqrtf(d);
+        const float l = r > j ? a[j] * rs : 0.f;
+        if (r == j) { a[j] = d * rs; rd = rs; }
+        if (r > j) a[j] = l;
+#pragma unroll
+        for (int q = j + 1; q < 32; ++q) a[q] = fmaf(-l, __shfl_sync(0xffffffffu, l, q), a[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) T[r][q] = (q <= r && r < nb) ? a[q] : 0.f;
+    rdg[r] = r < nb ? rd : 0.f;
+    if (diag_cta) {
+      // inverse, lane c computes column c: X_rc = (delta_rc - sum_{k=c}^{r-1} L_rk X_kc) / L_rr
+      // with L_rk shuffled from lane r (row r of the factor)
+      float x[32];
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) {
+        float sacc = rr == r ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < rr; ++k) sacc = fmaf(-__shfl_sync(0xffffffffu, a[k], rr), x[k], sacc);
+        const float rdr = __shfl_sync(0xffffffffu, rd, rr);
+        x[rr] = (rr >= r && rr < nb) ? sacc * rdr : 0.f;
+      }
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) X[rr][r] = x[rr];
+    }
+  }
+  __syncthreads();
+  if (diag_cta) {
+    for (int e = tid; e < 1024; e += 256) {
+      const int r = e >> 5, q = e & 31;
+      if (r < nb && q < nb) Lf[(size_t)(k0 + r) * n + k0 + q] = q <= r ? T[r][q] : 0.f;
+      Linv[(size_t)(k0 / 32) * 1024 + e] = (r < nb && q <= r) ? X[r][q] : 0.f;
+    }
+    return;
+  }
+  // ---- panel rows by forward substitution: x_q = (a_q - sum_{l<q} x_l L_ql) / L_qq
+  if (tid < 128) {
+    const int sd = tid >> 6, rr = tid & 63;
+    if (sd < nsides) {
+      float x[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        float v = Araw[sd][rr][q];
+#pragma unroll
+        for (int l = 0; l < q; ++l) v = fmaf(-x[l], T[q][l], v);
+        x[q] = q < nb ? v * rdg[q] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 32; ++q) P[sd][q][rr] = x[q];
+    }
+  }
+  __syncthreads();
+  if (bj == 0) {
+    for (int e = tid; e < 64 * 32; e += 256) {
+      const int rr = e >> 5, q = e & 31;
+      const int g = i0 + rr;
+      if (g < n && q < nb) Lf[(size_t)g * n + k0 + q] = P[0][q][rr];
+    }
+  }
+  const float (*PJ)[65] = P[nsides - 1];
+  const int tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int l = 0; l < nb; ++l) {
+    float pa[4], pb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) pa[a] = P[0][l][ty + 16 * a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) pb[b] = PJ[l][tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int gi = i0 + ty + 16 * a;
+    if (gi >= n) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gj = j0 + tx + 16 * b;
+      if (gj < n) Kf[(size_t)gi * n + gj] -= acc[a][b];
+    }
+  }
+}
+
+// Mixed-precision solve of the LM system (iterative refinement, e.g. Carson
+// and Higham 2018): the equilibrated matrix d_i K_ij d_j (d_i = K_ii^-1/2) is
+// factored in float; each refinement step solves with that factor and
+// updates X in double against the double residual R - K X.
+
+// Kf[i][j] = float(d_i K[i][j] d_j) on the lower triangle, d_i = 1/sqrt(K_ii)
+__global__ void k_equilibrate(const double* __restrict__ K, int n, float* __restrict__ Kf,
+                              double* __restrict__ d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j > i || j >= n) return;
+  const double di = rsqrt(K[(size_t)i * n + i]), dj = rsqrt(K[(size_t)j * n + j]);
+  Kf[(size_t)i * n + j] = float(di * K[(size_t)i * n + j] * dj);
+  if (j == 0) d[i] = di;
+}
+
+// 128-bit shared-memory load kept inside the loop that issues it (the
+// compiler would otherwise hoist all 128 block values into registers).
+__device__ __forceinline__ float4 lds4(const float4* p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return v;
+}
+
+// One float solve of (D K D) z = D r with the factor L (lower triangle of Lf)
+// and the diagonal-block inverses, by one CTA of 1024 threads: forward and
+// back substitution over 32-row blocks, the right-hand sides (n x 4) in
+// shared memory.  X += D z in double.  Rres: the double residual R - K X.
+__global__ void __launch_bounds__(1024) k_trsv_f32_single(const float* __restrict__ Lf,
+                                                          const float* __restrict__ Linv, int n,
+                                                          const double* __restrict__ d,
+                                                          const double* __restrict__ Rres,
+                                                          double* __restrict__ X) {
+  extern __shared__ float sb[];    // [n][4]
+  __shared__ float4 yk4[32];
+  __shared__ float Li[32][33];
+  float (*yk)[4] = reinterpret_cast<float (*)[4]>(yk4);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 4 * n; e += blockDim.x) sb[e] = float(d[e >> 2] * Rres[e]);
+  __syncthreads();
+  // forward: L y = b
+  for (int kb = 0; kb < n; kb += 32) {
+    const int nb = min(32, n - kb);
+    Li[tid >> 5][tid & 31] = Linv[(size_t)(kb / 32) * 1024 + tid];
+    __syncthreads();
+    if (tid < 128) {
+      const int rr = tid >> 2, qq = tid & 3;
+      float y = 0.f;
+      for (int l = 0; l <= rr && l < nb; ++l) y = fmaf(Li[rr][l], sb[4 * (kb + l) + qq], y);
+      yk[rr][qq] = y;
+    }
+    __syncthreads();
+    if (tid < 128 && (tid >> 2) < nb) sb[4 * kb + tid] = yk[tid >> 2][tid & 3];
+    for (int i = kb + nb + tid; i < n; i += blockDim.x) {
+      const float* row = Lf + (size_t)i * n + kb;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      if (nb == 32 && (n & 3) == 0) {      // whole block: eight 128-bit loads in flight
+        float4 m4[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) m4[v] = reinterpret_cast<const float4*>(row)[v];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          const float mv[4] = {m4[v].x, m4[v].y, m4[v].z, m4[v].w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 y = lds4(&yk4[4 * v + u]);
+            s0 = fmaf(mv[u], y.x, s0); s1 = fmaf(mv[u], y.y, s1);
+            s2 = fmaf(mv[u], y.z, s2); s3 = fmaf(mv[u], y.w, s3);
+          }
+        }
+      } else {
+        for (int l = 0; l < nb; ++l) {
+          const float m = row[l];
+          s0 = fmaf(m, yk[l][0], s0); s1 = fmaf(m, yk[l][1], s1);
+          s2 = fmaf(m, yk[l][2], s2); s3 = fmaf(m, yk[l][3], s3);
+        }
+      }
+      sb[4 * i] -= s0; sb[4 * i + 1] -= s1; sb[4 * i + 2] -= s2; sb[4 * i + 3] -= s3;
+    }
+    __syncthreads();
+  }
+  // back: L^T z = y
+  for (int kb = (n - 1) / 32 * 32; kb >= 0; kb -= 32) {
+    const int nb = min(32, n - kb);
+    Li[tid >> 5][tid & 31] = Linv[(size_t)(kb / 32) * 1024 + tid];
+    __syncthreads();
+    if (tid < 128) {
+      const int rr = tid >> 2, qq = tid & 3;
+      float x = 0.f;
+      for (int l = rr; l < nb; ++l) x = fmaf(Li[l][rr], sb[4 * (kb + l) + qq], x);
+      yk[rr][qq] = x;
+    }
+    __syncthreads();
+    if (tid < 128 && (tid >> 2) < nb) sb[4 * kb + tid] = yk[tid >> 2][tid & 3];
+    for (int i = tid; i < kb; i += blockDim.x) {
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      if (nb == 32) {                      // whole block: 16 loads in flight at a time
+#pragma unroll
+        for (int h = 0; h < 32; h += 16) {
+          float m[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) m[u] = Lf[(size_t)(kb + h + u) * n + i];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const float4 y = lds4(&yk4[h + u]);
+            s0 = fmaf(m[u], y.x, s0); s1 = fmaf(m[u], y.y, s1);
+            s2 = fmaf(m[u], y.z, s2); s3 = fmaf(m[u], y.w, s3);
+          }
+        }
+      } else {
+        for (int rr = 0; rr < nb; ++rr) {
+          const float m = Lf[(size_t)(kb + rr) * n + i];
+          s0 = fmaf(m, yk[rr][0], s0); s1 = fmaf(m, yk[rr][1], s1);
+          s2 = fmaf(m, yk[rr][2], s2); s3 = fmaf(m, yk[rr][3], s3);
+        }
+      }
+      sb[4 * i] -= s0; sb[4 * i + 1] -= s1; sb[4 * i + 2] -= s2; sb[4 * i + 3] -= s3;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < 4 * n; e += blockDim.x) X[e] += d[e >> 2] * double(sb[e]);
+}
+
+// Rres = R - K X (double, one warp per row, K full) and per-block sums for
+// the normwise backward error: part[block] = (max_q |Rres|, max |R|, max row
+// sum |K|, max |X|) over the block's rows.
+__global__ void __launch_bounds__(256) k_resid4(const double* __restrict__ K, int n,
+                                                const double* __restrict__ R,
+                                                const double* __restrict__ X,
+                                                double* __restrict__ Rres, double* __restrict__ part) {
+  __shared__ double red[8][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 8 + w;
+  double m[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, a = 0.0;
+    const double* row = K + (size_t)i * n;
+    for (int j = lane; j < n; j += 32) {
+      const double k = row[j];
+      s0 += k * X[4 * j]; s1 += k * X[4 * j + 1]; s2 += k * X[4 * j + 2]; s3 += k * X[4 * j + 3];
+      a += fabs(k);
+    }
+    for (int o = 16; o; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+    }
+    const double r0 = R[4 * i] - s0, r1 = R[4 * i + 1] - s1, r2 = R[4 * i + 2] - s2,
+                 r3 = R[4 * i + 3] - s3;
+    if (lane == 0) {
+      Rres[4 * i] = r0; Rres[4 * i + 1] = r1; Rres[4 * i + 2] = r2; Rres[4 * i + 3] = r3;
+    }
+    m[0] = fmax(fmax(fabs(r0), fabs(r1)), fmax(fabs(r2), fabs(r3)));
+    m[1] = fmax(fmax(fabs(R[4 * i]), fabs(R[4 * i + 1])), fmax(fabs(R[4 * i + 2]), fabs(R[4 * i + 3])));
+    m[2] = a;
+    m[3] = fmax(fmax(fabs(X[4 * i]), fabs(X[4 * i + 1])), fmax(fabs(X[4 * i + 2]), fabs(X[4 * i + 3])));
+  }
+  if (lane == 0)
+    for (int q = 0; q < 4; ++q) red[w][q] = m[q];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0.0;
+    for (int k = 0; k < 8; ++k) v = fmax(v, red[k][threadIdx.x]);
+    part[4 * blockIdx.x + threadIdx.x] = v;
+  }
+}
+
+// eta = |R - K X|_max / (|K|_inf |X|_max + |R|_max) from the block partials
+__global__ void k_backward_error(const double* __restrict__ part, int nblk,
+                                 double* __restrict__ eta) {
+  __shared__ double red[4][32];
+  double m[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+    for (int q = 0; q < 4; ++q) m[q] = fmax(m[q], part[4 * b + q]);
+  for (int o = 16; o; o >>= 1)
+    for (int q = 0; q < 4; ++q) m[q] = fmax(m[q], __shfl_xor_sync(0xffffffffu, m[q], o));
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 4; ++q) red[q][threadIdx.x >> 5] = m[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 4; ++q)
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) red[q][0] = fmax(red[q][0], red[q][w]);
+    const double den = red[2][0] * red[3][0] + red[1][0];
+    *eta = den > 0.0 ? red[0][0] / den : 0.0;
+  }
+}
+
 // Solve K X = R (four right-hand sides) with the factor in the lower
 // triangle of L and the diagonal inverses in Linv; the solution replaces R.
 // Y: scratch [n][4].
@@ -694,19 +1052,37 @@ __global__ void k_kkt_finish(const double* __restrict__ X, const double* __restr
     delta[i] = X[4 * i] - (X[4 * i + 1] * mu[0] + X[4 * i + 2] * mu[1] + X[4 * i + 3] * mu[2]);
 }
 
+// Refinement: checked from step kRefineCheck on, at most kRefineMax steps,
+// converged when the normwise backward error is below kRefineTol; the
+// single-CTA float solve keeps n x 4 floats in shared memory.
+constexpr int kRefineCheck = 2, kRefineMax = 10;
+constexpr double kRefineTol = 1e-14;
+constexpr int kMaxSingleCtaSolve = 12288;
+
 int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double* delta) {
   int n = c->sc.nth, rc;
   size_t nn = (size_t)n * n * sizeof(double);
   const size_t nblk = ((size_t)n + 31) / 32;
+  const size_t rblk = ((size_t)n + 7) / 8;
   if ((rc = grow(c, c->lmK, nn))) return rc;
   if ((rc = grow(c, c->lmLt, sizeof(double) * 1024 * nblk))) return rc;
-  if ((rc = grow(c, c->lmL, sizeof(double) * (12 * (size_t)n + 8)))) return rc;
+  if ((rc = grow(c, c->lmW, nn + sizeof(float) * 1024 * nblk + 256))) return rc;
+  if ((rc = grow(c, c->lmL, sizeof(double) * (25 * (size_t)n + 4 * rblk + 16)))) return rc;
   double* Km = (double*)c->lmK.p;
   double* Linv = (double*)c->lmLt.p;      // [n/32][32][32] inverses of the diagonal blocks
+  float* Kf = (float*)c->lmW.p;           // equilibrated matrix in float (trailing updates)
+  float* Lf = Kf + (size_t)n * n;         // its float Cholesky factor (lower triangle)
+  float* Linvf = Lf + (size_t)n * n;      // the factor's diagonal-block inverses
   double* R = (double*)c->lmL.p;          // [n][4] right-hand sides, then solutions
   double* cons = R + 4 * (size_t)n;       // [n][4] constraint columns
-  double* Ytmp = cons + 4 * (size_t)n;    // [n][4] forward-solve result
-  double* mx = Ytmp + 4 * (size_t)n;
+  double* Ytmp = cons + 4 * (size_t)n;    // [n][4] forward-solve result (double path)
+  double* Rres = Ytmp + 4 * (size_t)n;    // [n][4] refinement residual
+  double* Xs = Rres + 4 * (size_t)n;      // [n][4] refined solution
+  double* dsc = Xs + 4 * (size_t)n;       // [n] equilibration
+  double* epart = dsc + (size_t)n;        // [rblk][4] backward-error partials
+  double* eta_d = epart + 4 * rblk;
+  int* fstat = (int*)(eta_d + 1);
+  double* mx = eta_d + 2;
   double* gn = mx + 1;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
   ProfScope _ps(c, "lm_solve");
@@ -717,23 +1093,57 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
     k_lm_build<<<grid, 128, 0, S(c)>>>(H, g, n, c->sc.C, c->sc.d_closed, c->d_compat, mx, lam, Km, R);
     c->launches += 2;
   }
-  {
-    ProfScope _pc(c, "lm_cholesky");
-    for (int k0 = 0; k0 < n; k0 += 32) {
-      const int nb = std::min(32, n - k0);
-      k_potrf_inv<<<1, 1024, 0, S(c)>>>(Km, n, k0, nb, Linv, c->d_status);
+  // float factor of the equilibrated matrix, refined in double; the double
+  // factorization is the fallback when the float one fails or stalls
+  bool done = false;
+  if (c->opts.lm_solver == BEM_LM_AUTO && n <= kMaxSingleCtaSolve) {
+    int fst = 0;
+    {
+      ProfScope _pc(c, "lm_cholesky");
+      k_equilibrate<<<dim3((n + 127) / 128, n), 128, 0, S(c)>>>(Km, n, Kf, dsc);
       BEM_LAUNCHED(c);
-      const int r0 = k0 + nb, rest = n - r0;
-      if (rest > 0) {
-        k_trsm_panel<<<(rest + 7) / 8, 256, 0, S(c)>>>(Km, n, k0, nb, Linv);
-        const int tiles = (rest + 63) / 64;
-        k_syrk_lower<<<tiles * (tiles + 1) / 2, 256, 0, S(c)>>>(Km, n, k0, nb, r0);
-        c->launches += 2;
+      if ((rc = cuda_check(c, cudaMemsetAsync(fstat, 0, sizeof(int), S(c)), "memset"))) return rc;
+      for (int k0 = 0; k0 < n; k0 += 32) {
+        const int tiles = (n - std::min(n, k0 + 32) + 63) / 64;
+        k_chol_step_f32<<<tiles * (tiles + 1) / 2 + 1, 256, 0, S(c)>>>(Kf, Lf, n, k0, Linvf,
+                                                                         fstat);
+        BEM_LAUNCHED(c);
       }
     }
-  }
-  {
     ProfScope _pt(c, "lm_trisolve");
+    if ((rc = cuda_check(c, cudaMemcpyAsync(Rres, R, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, S(c)), "copy")) ||
+        (rc = cuda_check(c, cudaMemsetAsync(Xs, 0, sizeof(double) * 4 * n, S(c)), "memset")))
+      return rc;
+    const int rblk = (n + 7) / 8;
+    const size_t smem = sizeof(float) * 4 * (size_t)n;
+    if (smem > 48 * 1024 &&
+        (rc = cuda_check(c, cudaFuncSetAttribute(k_trsv_f32_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attribute")))
+      return rc;
+    double eta = 1.0, eta_prev = 2.0;
+    for (int it = 0; it < kRefineMax; ++it) {
+      k_trsv_f32_single<<<1, 1024, smem, S(c)>>>(Lf, Linvf, n, dsc, Rres, Xs);
+      k_resid4<<<rblk, 256, 0, S(c)>>>(Km, n, R, Xs, Rres, epart);
+      k_backward_error<<<1, 256, 0, S(c)>>>(epart, rblk, eta_d);
+      c->launches += 3;
+      if (it + 1 < kRefineCheck) continue;
+      double h[1];
+      if ((rc = cuda_check(c, cudaMemcpyAsync(h, eta_d, sizeof(double), cudaMemcpyDeviceToHost, S(c)), "eta")) ||
+          (rc = cuda_check(c, cudaMemcpyAsync(&fst, fstat, sizeof(int), cudaMemcpyDeviceToHost, S(c)), "status")) ||
+          (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "refine sync")))
+        return rc;
+      if (fst) break;                      // the float factor hit a non-positive pivot
+      eta_prev = it + 1 == kRefineCheck ? 2.0 : eta;
+      eta = h[0];
+      if (eta < kRefineTol) { done = true; break; }
+      if (!(eta < 0.5 * eta_prev)) break;  // stalled
+    }
+    if (done &&
+        (rc = cuda_check(c, cudaMemcpyAsync(R, Xs, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, S(c)), "copy")))
+      return rc;
+  }
+  if (!done) {
+    ProfScope _pc(c, "lm_cholesky_fp64");
+    chol_factor<double>(c, Km, n, Linv, c->d_status);
     chol_solve4(c, Km, Linv, n, R, Ytmp);
   }
   // the constraint columns are needed again for the Schur complement
