@@ -170,26 +170,27 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
   const int r = warp * 32 + lane;     // row of the tile owned by this thread
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
   // bf16 J rows: the stage ring is free once the accumulator is complete;
-  // F's 128 x 128 tile is staged there with coalesced loads (row stride 129
-  // floats keeps the per-row reads below free of bank conflicts)
+  // F's 128 x 128 fp32 tile is copied there with cp.async, all 16-byte
+  // chunks in flight at once.  Row rr holds 32 chunks of 16 bytes; logical
+  // chunk cc sits at position cc ^ (rr & 7), so that the per-row reads below
+  // (lane = row) and the in-place bf16 writes are free of bank conflicts.
   float* fs = reinterpret_cast<float*>(smem);
   if (!X3 && g.mode == EPI_JROWS) {
     for (int e = threadIdx.x; e < BM * (BN / 4); e += 128) {
-      const int rr = e / (BN / 4), cc = (e % (BN / 4)) * 4;
-      const int row = arow + rr, col = brow + cc;
-      float4 fv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (row < g.M) {
+      const int rr = e / (BN / 4), cc = e % (BN / 4);
+      const int row = arow + rr, col = brow + cc * 4;
+      float* d = fs + rr * BN + ((cc ^ (rr & 7)) << 2);
+      if (row < g.M && col + 3 < g.N) {
+        umma::cp_async16(d, g.F + (size_t)row * g.ldf + col);
+      } else {
         const float* src = g.F + (size_t)row * g.ldf + col;
-        if (col + 3 < g.N) fv = *reinterpret_cast<const float4*>(src);
-        else {
-          if (col < g.N) fv.x = src[0];
-          if (col + 1 < g.N) fv.y = src[1];
-          if (col + 2 < g.N) fv.z = src[2];
-        }
+        d[0] = (row < g.M && col < g.N) ? src[0] : 0.f;
+        d[1] = (row < g.M && col + 1 < g.N) ? src[1] : 0.f;
+        d[2] = (row < g.M && col + 2 < g.N) ? src[2] : 0.f;
+        d[3] = 0.f;
       }
-      float* d = fs + rr * 129 + cc;
-      d[0] = fv.x; d[1] = fv.y; d[2] = fv.z; d[3] = fv.w;
     }
+    umma::cp_async_wait_all();
     __syncthreads();
   }
 #pragma unroll 1
@@ -223,16 +224,31 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
           }
       }
     } else if (g.mode == EPI_JROWS) {
-      // F row r of the tile was staged in shared memory (fs, 129-float rows);
-      // this chunk's F is read before its bf16 result overwrites the front
-      // of the same row (fs bytes 64 cb .. 64 cb + 63 <= F bytes of chunk cb)
-      float* fr = fs + r * 129;
-      __nv_bfloat16* jr = reinterpret_cast<__nv_bfloat16*>(fr);
+      // F row r of the tile was staged in shared memory (fs, swizzled
+      // 16-byte chunks); this chunk's bf16 result goes to the front of the
+      // same row, bf16 chunk k (8 values) at position k ^ (r & 7): those
+      // positions hold F chunks of this or an earlier 32-column block only,
+      // already read
+      float* fr = fs + r * BN;
+      const int sw = r & 7;
       float f[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) f[j] = fr[cb + j];
+      for (int k = 0; k < 8; ++k) {
+        const float4 q = *reinterpret_cast<const float4*>(fr + ((((cb >> 2) + k) ^ sw) << 2));
+        f[4 * k] = q.x; f[4 * k + 1] = q.y; f[4 * k + 2] = q.z; f[4 * k + 3] = q.w;
+      }
 #pragma unroll
-      for (int j = 0; j < 32; ++j) jr[cb + j] = __float2bfloat16_rn(v[j] + f[j]);
+      for (int k = 0; k < 4; ++k) {
+        uint4 w;
+        uint32_t* wp = &w.x;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * k + 2 * h] + f[8 * k + 2 * h],
+                                                          v[8 * k + 2 * h + 1] + f[8 * k + 2 * h + 1]);
+          wp[h] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        *reinterpret_cast<uint4*>(fr + ((((cb >> 3) + k) ^ sw) << 2)) = w;
+      }
     } else {
       const int i = ti * BM + r;
       if (i < g.nc) {
@@ -247,22 +263,22 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
   }
   if (!X3 && g.mode == EPI_JROWS) {
     __syncthreads();
-    // row rr of the bf16 tile sits at the front of fs row rr: one warp writes
-    // a 256-byte row per step, 8 bytes per lane
+    // row rr of the bf16 tile sits at the front of fs row rr (bf16 chunk k
+    // at position k ^ (rr & 7)): one warp writes a 256-byte row per step,
+    // 8 bytes per lane
     for (int rr = warp; rr < BM; rr += 4) {
       const int row = arow + rr;
       if (row >= g.M) continue;
-      const __nv_bfloat16* src = reinterpret_cast<const __nv_bfloat16*>(fs + rr * 129);
       const int col = brow + lane * 4;
+      const char* src = reinterpret_cast<const char*>(fs + rr * BN) +
+                        ((((lane >> 1) ^ (rr & 7)) << 4) | ((lane & 1) << 3));
       __nv_bfloat16* dst = g.J + (size_t)row * g.ldj + col;
       if (col + 3 < g.N) {
-        uint2 w;
-        w.x = *reinterpret_cast<const uint32_t*>(src + lane * 4);
-        w.y = *reinterpret_cast<const uint32_t*>(src + lane * 4 + 2);
-        *reinterpret_cast<uint2*>(dst) = w;
+        *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
       } else {
+        const __nv_bfloat16* sb = reinterpret_cast<const __nv_bfloat16*>(src);
         for (int q = 0; q < 4; ++q)
-          if (col + q < g.N) dst[q] = src[lane * 4 + q];
+          if (col + q < g.N) dst[q] = sb[q];
       }
     }
   }
