@@ -150,16 +150,18 @@ def read_peaks():
 
 def kernel_traffic(name):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel's source has changed since the counters were taken."""
+    kernel's sources have changed since the counters were taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
             rec = json.load(f).get(name)
         if not rec:
             return None
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-        return rec["bytes_per_launch"] if sha == rec["sha256"] else None
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return rec["bytes_per_launch"] if h.hexdigest() == rec["sha256"] else None
     except (OSError, ValueError, KeyError):
         return None
 
