@@ -32,19 +32,21 @@ import gen  # noqa: E402
 METRIC = ("LM iters/s & sample×panel evals/s (fwd+adjoint), mixed vs FP64 GPU at "
           "≤1e-4 RMSE")
 UNIT = "LM iter/s"
-CFG = 2
+CFG = 2            # the configuration the metric is quoted on
 L2_FLUSH_BYTES = 256 << 20
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
-def workload_desc(sc):
-    return (f"cfg{CFG}: {sc.n_curves} cubic Bezier curves x {int(sc.panels_per_curve[0])} panels "
+def workload_desc(sc, cfg=CFG):
+    noise = ("lognormal noise with 1% fireflies" if sc.noise.get("noise") == "lognormal"
+             else "Gaussian noise")
+    return (f"cfg{cfg}: {sc.n_curves} cubic Bezier curves x {int(sc.panels_per_curve[0])} panels "
             f"({sc.n_panels} panels), {sc.W}x{sc.W} px x {sc.spp} spp ({sc.n_samples} samples), "
-            f"1024 boundary segments, lognormal noise with 1% fireflies")
+            f"1024 boundary segments, {noise}")
 
 
-def make_inputs(rank: int):
-    sc = gen.make_scene(CFG)
+def make_inputs(rank: int, cfg: int = CFG):
+    sc = gen.make_scene(cfg)
     seed = sc.seed + 7919 * rank        # independent sample set per replica
     xy = gen.make_samples(sc.W, sc.spp, seed, dtype=np.float32)
     truth = gen.analytic_truth(xy, sc.seed)
@@ -148,14 +150,15 @@ def read_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def kernel_traffic(name):
+def kernel_traffic(name, cfg=CFG):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel's sources have changed since the counters were taken."""
+    kernel's sources have changed since the counters were taken or the
+    counters were taken on another configuration."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
             rec = json.load(f).get(name)
-        if not rec:
+        if not rec or rec.get("config") != cfg:
             return None
         h = hashlib.sha256()
         for src in rec["sources"]:
@@ -166,7 +169,7 @@ def kernel_traffic(name):
         return None
 
 
-def rooflines(prof, steps, n, P, Nb, nc):
+def rooflines(prof, steps, n, P, Nb, nc, cfg=CFG):
     peaks, src = read_peaks()
     out = []
     for name, (ms, cnt) in prof.items():
@@ -181,7 +184,7 @@ def rooflines(prof, steps, n, P, Nb, nc):
             peak = peaks["bf16_tflops_sustained"]
             psrc = f"bf16 dense, sustained ({src})"
         out.append({"bound": bound, "kernel": name, "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": kernel_traffic(name),
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": kernel_traffic(name, cfg),
                     "flops_per_launch": per_launch, "peak_source": psrc,
                     "share_ms": ms})
     out.sort(key=lambda r: -r.pop("share_ms"))
@@ -256,12 +259,15 @@ def run_ours(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc, xy, target = make_inputs(rank)
+    cfg = args.config
+    sc, xy, target = make_inputs(rank, cfg)
     if args.samples:                     # profiling aid: leading part of the workload
         xy, target = xy[:args.samples].copy(), target[:args.samples].copy()
     n = xy.shape[0]
     jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32}[args.jtj]
-    m = bg.BEM(precision=bg.BEM_MIXED, device=local, jtj_mode=jm)
+    # config 4 states its FP64 near field: sample-panel distance < 2 panel lengths
+    nf = 2.0 if cfg == 4 else 0.5
+    m = bg.BEM(precision=bg.BEM_MIXED, device=local, jtj_mode=jm, near_factor=nf)
     xt = torch.from_numpy(xy).to(dev)
     tt = torch.from_numpy(target).to(dev)
     m.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, np.zeros(3))
@@ -314,7 +320,7 @@ def run_ours(args, rank, world, dist):
         return
     # ---- per-kernel live timing -> roofline of the dominant modelled kernel
     P, Nb, nc = sc.n_panels, 1024, 16 * sc.n_curves
-    roofs = rooflines(prof, args.steps, n, P, Nb, nc)
+    roofs = rooflines(prof, args.steps, n, P, Nb, nc, cfg)
     roof = roofs[0] if roofs else None
     kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
                    "share": v[0] / total_ms} for k, v in sorted(prof.items())}
@@ -342,44 +348,58 @@ def run_ours(args, rank, world, dist):
     pairs = n * (P + Nb)
     pairs_per_s = 2 * pairs / ((fwd_ms + adj_ms) / 1e3)
 
-    # ---- FP64 GPU path: one LM iteration (after one warm-up iteration)
+    # ---- FP64 GPU path: one LM iteration (after one warm-up iteration); at
+    # config 4 its cost a + b S is fitted from steps on two sample subsets
     fp64 = None
+    accuracy = None
     if args.fp64_steps > 0:
+        n64 = n if (cfg != 4 or args.fp64_samples <= 0) else min(n, args.fp64_samples)
         m64 = bg.BEM(precision=bg.BEM_FP64, device=local)
-        x64, t64 = xt.double(), tt.double()
+        x64, t64 = xt[:n64].double(), tt[:n64].double()
         m64.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, mean)
         m64.factor()
         u64 = m64.eval(x64)
         m.set_params(sc.theta_init)
-        u32 = m.eval(xt, out).double()
+        u32 = m.eval(xt[:n64]).double()
         rmse = float(torch.sqrt(torch.mean((u32 - u64) ** 2)).item())
-        r64 = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        r64 = torch.empty((n64, 3), dtype=torch.float64, device=dev)
         m64.loss(x64, t64, r64)
         g64 = m64.vjp(x64, r64)
-        m.loss(xt, tt, res)
-        g32 = m.vjp(xt, res)
+        r32 = torch.empty((n64, 3), dtype=torch.float32, device=dev)
+        m.loss(xt[:n64], tt[:n64], r32)
+        g32 = m.vjp(xt[:n64], r32)
         gerr = float((torch.linalg.norm(g32 - g64) / torch.linalg.norm(g64)).item())
-        lam64 = [1e-3]
-        m64.lm_step(x64, t64, lam64)
+        del u64, u32, r64, r32
+        m64.lm_step(x64, t64, [1e-3])
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t64_ms = 0.0
-        for _ in range(args.fp64_steps):
-            m64.set_params(sc.theta_init)
-            flush.zero_()
-            e0.record(stream)
-            m64.lm_step(x64, t64, [1e-3])
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t64_ms += e0.elapsed_time(e1) / args.fp64_steps
+
+        def t64_step(k):
+            tot = 0.0
+            for _ in range(args.fp64_steps):
+                m64.set_params(sc.theta_init)
+                flush.zero_()
+                e0.record(stream)
+                m64.lm_step(x64[:k], t64[:k], [1e-3])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1) / args.fp64_steps
+            return tot
+
+        if n64 == n:
+            t64_ms = t64_step(n64)
+            timed = f"{args.fp64_steps} full FP64 LM iteration(s) after one warm-up"
+        else:
+            th, tf = t64_step(n64 // 2), t64_step(n64)
+            b = (tf - th) / (n64 - n64 // 2)
+            t64_ms = tf + b * (n - n64)
+            timed = (f"FP64 LM iterations on {n64 // 2} and {n64} of {n} samples "
+                     f"({th:.0f} ms, {tf:.0f} ms), extrapolated linearly in samples")
         fp64 = {"lm_iters_per_s": 1e3 / t64_ms, "ms_per_iter": t64_ms,
-                "mixed_over_fp64": (value / world) / (1e3 / t64_ms),
-                "timed": f"{args.fp64_steps} full FP64 LM iteration(s) after one warm-up"}
+                "mixed_over_fp64": (value / world) / (1e3 / t64_ms), "timed": timed}
         accuracy = {"colour_rmse_mixed_vs_fp64_gpu": rmse, "grad_rel_err_mixed_vs_fp64_gpu": gerr,
-                    "at": "theta_init, all samples"}
+                    "at": f"theta_init, {'all' if n64 == n else n64} samples"}
         m64.close()
-    else:
-        accuracy = None
 
     # ---- end to end through the public API with host buffers
     xy_h = torch.from_numpy(xy).pin_memory()
@@ -403,7 +423,7 @@ def run_ours(args, rank, world, dist):
            "d2h_bytes_per_step": 8 * 3}
 
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and cfg == CFG:
         cpu = cpu_baseline(sc, xy, target, n_sub=args.cpu_samples)
         cpu.pop("seconds_per_sample_step", None)
 
@@ -411,8 +431,8 @@ def run_ours(args, rank, world, dist):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": workload_desc(sc), "precision": "mixed (f32 pairs, f64 near "
-                       "field and refined solves)", "jtj": args.jtj, "lm_trials_per_step": 1,
+            "config": {"workload": workload_desc(sc, cfg), "near_factor": nf,
+                       "precision": "mixed (f32 pairs, f64 near field and refined solves)", "jtj": args.jtj, "lm_trials_per_step": 1,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "wall_s_timed_region": t_wall},
             "pairs_per_s": {"value": pairs_per_s, "unit": "sample x panel evals/s (fwd+adjoint)",
@@ -434,6 +454,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jtj", default="bf16", choices=["bf16", "3xtf32"],
                     help="tensor-core scheme of the J^T J contraction")
+    ap.add_argument("--config", type=int, default=CFG, choices=[2, 4],
+                    help="2: the metric's configuration (default); 4: 67M samples, 8,192 panels")
+    ap.add_argument("--fp64-samples", type=int, default=1 << 20,
+                    help="config 4: samples of the FP64 GPU comparison (0 = all)")
     ap.add_argument("--samples", type=int, default=0,
                     help="profiling aid: time only the first N samples of the workload")
     args = ap.parse_args()
