@@ -443,6 +443,97 @@ def run_ours(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world):
+    """Config 5: uneven scenes with 4 damping trials each, stepped by one
+    bem_batch_lm call per LM iteration, against stepping the same scenes one
+    at a time with lm_step (same trials).  Unit: scene LM iterations/s."""
+    import torch
+    import paper_2602_05492_gb300 as bg
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    lams = [1e-3, 1e-2, 1e-1, 1.0]
+    scenes = gen.batch_scenes(args.scenes)
+    data = []
+    for k, sc in enumerate(scenes):
+        xy = gen.make_samples(sc.W, sc.spp, sc.seed, dtype=np.float32)
+        tgt = gen.add_noise(gen.analytic_truth(xy, sc.seed), sc.noise, sc.seed).astype(np.float32)
+        data.append((torch.from_numpy(xy).to(dev), torch.from_numpy(tgt).to(dev),
+                     np.minimum(tgt, 1.0).mean(0).astype(np.float64)))
+
+    def contexts():
+        ms = []
+        for sc, (x, t, mean) in zip(scenes, data):
+            m = bg.BEM(precision=bg.BEM_MIXED)
+            m.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, mean)
+            m.factor()
+            ms.append(m)
+        return ms
+
+    xs = [d[0] for d in data]
+    ts = [d[1] for d in data]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    # batched
+    mb = contexts()
+    b = bg.BEMBatch(mb)
+    for _ in range(max(args.warmup, 0)):
+        b.lm_step(xs, ts, lams)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    tb = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        b.lm_step(xs, ts, lams)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    shape = b.tile_shape()
+    b.close()
+    for m in mb:
+        m.close()
+    # one scene at a time
+    ms = contexts()
+    for _ in range(max(args.warmup, 0)):
+        for m, x, t in zip(ms, xs, ts):
+            m.lm_step(x, t, lams)
+    torch.cuda.synchronize()
+    tsq = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        for m, x, t in zip(ms, xs, ts):
+            m.lm_step(x, t, lams)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tsq += e0.elapsed_time(e1)
+    for m in ms:
+        m.close()
+    S = len(scenes)
+    nsamp = int(sum(x.shape[0] for x in xs))
+    npan = int(sum(sc.n_panels for sc in scenes))
+    value = S * args.steps / (tb / 1e3)
+    seq = S * args.steps / (tsq / 1e3)
+    line = {"metric": "scene LM iterations/s, 4 damping trials per scene (batched)",
+            "value": value, "unit": "scene LM iter/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tb / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"cfg5: {S} scenes, panels log-uniform in [256, 4096] "
+                                   f"(64 per curve, {npan} in all), 128^2..512^2 px at "
+                                   f"4..32 spp ({nsamp} samples in all), lambda in {lams}",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "tile_shape": {"points_per_tile": shape[0], "ctas_per_sm": shape[1]}},
+            "one_at_a_time": {"value": seq, "unit": "scene LM iter/s",
+                              "ms_per_step": tsq / args.steps},
+            "batched_over_one_at_a_time": value / seq, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,8 +545,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jtj", default="bf16", choices=["bf16", "3xtf32"],
                     help="tensor-core scheme of the J^T J contraction")
-    ap.add_argument("--config", type=int, default=CFG, choices=[2, 4],
-                    help="2: the metric's configuration (default); 4: 67M samples, 8,192 panels")
+    ap.add_argument("--config", type=int, default=CFG, choices=[2, 4, 5],
+                    help="2: the metric's configuration (default); 4: 67M samples, 8,192 "
+                         "panels; 5: batched uneven scenes against one at a time")
+    ap.add_argument("--scenes", type=int, default=64, help="config 5: number of scenes")
     ap.add_argument("--fp64-samples", type=int, default=1 << 20,
                     help="config 4: samples of the FP64 GPU comparison (0 = all)")
     ap.add_argument("--samples", type=int, default=0,
@@ -472,6 +565,8 @@ def main():
         dist = tdist
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == 5:
+        run_batch(args, rank, world)
     else:
         run_ours(args, rank, world, dist)
     if dist is not None:

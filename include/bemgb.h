@@ -226,6 +226,39 @@ int bem_fastmath_eval(bem_ctx *ctx, int which, int64_t n, const float *a, const 
 int bem_vjp_noalloc(bem_ctx *ctx, int64_t n, const void *xy, const void *resid,
                     double *grad_out, void *stream);
 
+/* ---- batches of scenes ------------------------------------------------
+ * Many independent scenes of uneven size stepped together.  The paper fits
+ * one scene at a time, so it has no counterpart; each scene's step is the
+ * one lm_step computes (Sec. 4.3).  The bulk sample x panel work of all
+ * scenes (the evaluation at theta and the evaluation of every damping
+ * trial) runs in one persistent launch each, replayed from a captured CUDA
+ * graph; its tile shape is chosen by timing the candidates on the first call. */
+typedef struct bem_batch bem_batch;
+
+/* Borrow n_scenes contexts (they must outlive the batch).  Each must be a
+ * BEM_MIXED context that is set up and factored; all must share the device,
+ * eps_c, eps_d and whether the near field is used.  The batch shares scene
+ * 0's Gauss-Newton chunk buffers with the others until it is destroyed.
+ * *out receives the batch.  Errors: BEM_EINVAL (message on scenes[0]). */
+int bem_batch_create(bem_batch **out, bem_ctx *const *scenes, int n_scenes);
+void bem_batch_destroy(bem_batch *b);
+
+/* One LM iteration of every scene, each with the same n_trials (1..16)
+ * damping values; out[s] is scene s's result as lm_step reports it, and
+ * each scene's theta is updated when its best trial lowers its loss.
+ *   n[s]: samples of scene s (> 0); xy[s], target[s]: device float
+ *   pointers ([n][2], [n][3]); lambdas, out: host arrays.
+ * The batch works on its own stream, ordered after `stream` and before any
+ * later work on it; the call synchronises.  Errors: as lm_step, reported on
+ * scenes[0] with the failing scene's index. */
+int bem_batch_lm(bem_batch *b, const int64_t *n, const void *const *xy,
+                 const void *const *target, int n_trials, const double *lambdas,
+                 lm_result *out, void *stream);
+
+/* The tile shape the batch uses: points per tile and CTAs per SM (0 before
+ * the first bem_batch_lm). */
+int bem_batch_tile_shape(const bem_batch *b, int *points_per_tile, int *ctas_per_sm);
+
 /* Sizes of the current scene (host ints; any pointer may be NULL). */
 int bem_sizes(const bem_ctx *ctx, int *n_theta, int *n_panels, int *n_boundary);
 

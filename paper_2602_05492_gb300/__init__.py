@@ -81,6 +81,11 @@ def _load():
         "bem_vjp_noalloc": (ci, [vp, i64, vp, vp, vp, vp]),
         "bem_profile_read": (ci, [vp, ci, ctypes.c_char_p, dp, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ci)]),
+        "bem_batch_create": (ci, [ctypes.POINTER(vp), ctypes.POINTER(vp), ci]),
+        "bem_batch_destroy": (None, [vp]),
+        "bem_batch_lm": (ci, [vp, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(vp), ci,
+                              dp, ctypes.POINTER(lm_result), vp]),
+        "bem_batch_tile_shape": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -95,7 +100,8 @@ EXPORTED = [
     "bem_set_params", "bem_get_params", "bem_set_mean_color", "bem_sample_mean", "bem_eval",
     "bem_loss", "bem_vjp", "bem_jtj", "lm_step", "bem_sizes", "bem_boundary_values",
     "bem_launch_count", "bem_profile_enable", "bem_profile_read", "bem_gemm_bf16",
-    "bem_fastmath_eval", "bem_vjp_noalloc",
+    "bem_fastmath_eval", "bem_vjp_noalloc", "bem_batch_create", "bem_batch_destroy",
+    "bem_batch_lm", "bem_batch_tile_shape",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -306,3 +312,52 @@ class BEM:
             nm = names.raw[32 * k:32 * k + 32].split(b"\0", 1)[0].decode()
             out[nm] = (float(ms[k]), int(cnt[k]))
         return out
+
+
+class BEMBatch:
+    """Scenes (BEM_MIXED contexts, set up and factored) stepped together by
+    bem_batch_lm.  The contexts must outlive the batch."""
+
+    def __init__(self, scenes):
+        self.scenes = list(scenes)
+        arr = (ctypes.c_void_p * len(self.scenes))(*[m.h.value for m in self.scenes])
+        self.h = ctypes.c_void_p()
+        rc = _lib.bem_batch_create(ctypes.byref(self.h), arr, len(self.scenes))
+        if rc:
+            raise BemError(rc, _lib.bem_last_error(self.scenes[0].h).decode())
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            _lib.bem_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lm_step(self, xys, targets, lambdas, stream=None) -> list:
+        """One LM iteration of every scene; xys[s] float [n_s, 2], targets[s]
+        float [n_s, 3] CUDA tensors.  Returns one lm_step dict per scene."""
+        S = len(self.scenes)
+        assert len(xys) == S and len(targets) == S
+        for m, x, t in zip(self.scenes, xys, targets):
+            m._samples(x, t)
+        n = (ctypes.c_int64 * S)(*[x.shape[0] for x in xys])
+        px = (ctypes.c_void_p * S)(*[x.data_ptr() for x in xys])
+        pt = (ctypes.c_void_p * S)(*[t.data_ptr() for t in targets])
+        lam = np.ascontiguousarray(np.atleast_1d(lambdas), np.float64)
+        res = (lm_result * S)()
+        rc = _lib.bem_batch_lm(self.h, n, px, pt, len(lam), _dp(lam), res, _stream(stream))
+        if rc:
+            raise BemError(rc, _lib.bem_last_error(self.scenes[0].h).decode())
+        return [dict(loss_before=r.loss_before, loss_after=r.loss_after, accepted=bool(r.accepted),
+                     best_trial=r.best_trial, lambda_next=r.lambda_next, grad_norm=r.grad_norm)
+                for r in res]
+
+    def tile_shape(self) -> tuple:
+        """(points per tile, CTAs per SM) chosen by the batch's autotuner."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _lib.bem_batch_tile_shape(self.h, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value

@@ -53,6 +53,7 @@ static void free_buf(DevBuf& b) {
 }
 
 static int set_device(bem_ctx* c) { return cuda_check(c, cudaSetDevice(c->device), "cudaSetDevice"); }
+int ctx_set_device(bem_ctx* c) { return set_device(c); }
 
 // panels, compatibility weights and boundary solution of the current theta
 static int refresh(bem_ctx* c, const double* theta) {
@@ -61,12 +62,14 @@ static int refresh(bem_ctx* c, const double* theta) {
   if ((rc = field_rhs(c))) return rc;
   return field_solve(c);
 }
+int ctx_refresh(bem_ctx* c, const double* theta) { return refresh(c, theta); }
 
 static int need_ready(bem_ctx* c) {
   if (!c->have_scene) return fail(c, BEM_ESTATE, "bem_setup has not been called");
   if (!c->bd.factored) return fail(c, BEM_ESTATE, "bem_factor has not been called");
   return BEM_OK;
 }
+int ctx_ready(bem_ctx* c) { return need_ready(c); }
 
 static cudaEvent_t prof_event(bem_ctx* c) {
   if (!c->prof_pool.empty()) {
@@ -129,6 +132,16 @@ __global__ void k_scale_norm(double* __restrict__ v, int n, double s, double* __
     for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
     *norm2 = t;
   }
+}
+
+void ctx_axpy(bem_ctx* c, const double* a, const double* b, int n, double* out) {
+  k_axpy<<<(n + 255) / 256, 256, 0, S(c)>>>(a, b, n, out);
+  BEM_LAUNCHED(c);
+}
+
+void ctx_scale_norm(bem_ctx* c, double* v, int n, double s, double* norm2) {
+  k_scale_norm<<<1, 1024, 0, S(c)>>>(v, n, s, norm2);
+  BEM_LAUNCHED(c);
 }
 
 // which = 0: atan2(a, b); 1: log(a); 2: log1p(a).  Library approximation and

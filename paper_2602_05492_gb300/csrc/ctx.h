@@ -9,6 +9,7 @@
 
 #include "bemgb.h"
 #include "common.cuh"
+#include "field_args.cuh"
 
 namespace bem {
 
@@ -87,6 +88,10 @@ struct bem_ctx {
   bem::DevBuf part, part2, loss, gpart, jrow, phi, Hc, Mc, Dfc, Fg, lmK, lmL, lmLt, lmW, H, g,
       tcJ, tcPart, tcMt, nearP, nearS, nearF, gwork;
   bool pbins_valid = false;        // panel -> cell bins match the current panels
+  // When set, the Gauss-Newton chunk buffers (jrow, tcJ, tcPart, gwork) are
+  // taken from this context: a batch of scenes processed one after another
+  // on one stream shares them.
+  bem_ctx* scratch = nullptr;
 };
 
 namespace bem {
@@ -96,6 +101,13 @@ int fail(bem_ctx* c, int code, const std::string& msg);
 int cuda_check(bem_ctx* c, cudaError_t e, const char* what);
 int grow(bem_ctx* c, DevBuf& b, size_t bytes);
 inline cudaStream_t S(bem_ctx* c) { return c->cur; }
+
+// ---- context helpers (api.cu) --------------------------------------------------
+int ctx_set_device(bem_ctx* c);
+int ctx_ready(bem_ctx* c);                              // set up and factored
+int ctx_refresh(bem_ctx* c, const double* theta);       // panels, RHS, boundary solution
+void ctx_axpy(bem_ctx* c, const double* a, const double* b, int n, double* out);
+void ctx_scale_norm(bem_ctx* c, double* v, int n, double s, double* norm2);
 
 // ---- geometry (k_geom.cu) -----------------------------------------------------
 int geom_panelize(bem_ctx* c, const double* d_theta);
@@ -127,6 +139,14 @@ int field_eval(bem_ctx* c, int64_t n, const void* xy, void* out, const void* tar
 int field_rhs(bem_ctx* c);           // d_fb from the current panels
 int field_solve(bem_ctx* c);         // d_ub = A^+ d_fb
 int field_sample_mean(bem_ctx* c, int64_t n, const void* target, double* host_mean);
+// base float arguments of a mixed context (panels, boundary, eps, near field)
+FieldArgs<float> field_args_f32(bem_ctx* c);
+// one persistent launch over the tiles of all jobs (128 * spt points per
+// tile, blocks_per_sm CTAs per SM); total_tiles and counter: device words
+// (the counter is reset here), so that a captured graph can be replayed
+// with new job contents
+int field_batch_launch(bem_ctx* c, const BatchJob* jobs, int njobs, const int64_t* total_tiles,
+                       unsigned long long* counter, int spt, int blocks_per_sm);
 
 // ---- near field of the mixed path (k_near.cu) ------------------------------------
 // out[n][3] = double sum over the near panels of each point

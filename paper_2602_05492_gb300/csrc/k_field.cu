@@ -4,37 +4,15 @@
 // in shared memory and broadcast to every warp.  In mixed precision the
 // pair terms are float; pairs closer than near_factor panel lengths are
 // skipped here and their double sum (k_near.cu) is added per point.
+#include <algorithm>
 #include <cmath>
 
 #include "ctx.h"
+#include "field_args.cuh"
 
 namespace bem {
 
 constexpr int kFB = 128;   // threads per block = panels per shared-memory tile
-
-template <typename T>
-struct FieldArgs {
-  const T* xy;
-  int64_t n;
-  const Panel<T>* pan;
-  const Panel<double>* pan64;
-  int P;
-  int pchunk;          // panels per blockIdx.y slice (split mode)
-  const T* vert;       // boundary vertices [(Nb+1)][2] or null
-  const double* ub;    // boundary solution [Nb][3] or null
-  int Nb;
-  double mean0, mean1, mean2;
-  T ec2, ed2;          // eps_c^2, eps_d^2
-  double ec2d, ed2d;
-  T near2;             // (near_factor)^2, mixed precision only
-  float nfac;          // near_factor, mixed precision only
-  const T* target;     // clamp target or null
-  T* out;              // colours [n][3] or null
-  T* resid;            // residual [n][3] or null
-  double* loss_part;   // per-block sum of |r|^2 or null
-  double* split_out;   // split mode: [gridDim.y][n][3] handle-term partials
-  const double* near_add;  // double near-field sum [n][3] or null
-};
 
 // Sum over one shared-memory tile of panels (double path).
 template <typename T, bool SAME>
@@ -172,23 +150,48 @@ __device__ __forceinline__ void pair_acc_f(const float4 A, const float4 B, const
   s2 = fmaf(C.x, Dh, fmaf(C.w, Sh, s2));
 }
 
-template <bool SAME, bool NEAR>
-__global__ void __launch_bounds__(kFB) k_field_f32(FieldArgs<float> a) {
-  __shared__ float4 tile[3 * kFB];
-  __shared__ float2 sv[kFB + 1];
-  __shared__ float4 su[kFB];
-  __shared__ double red[kFB / 32];
-  __shared__ float bred[4 * (kFB / 32)];
-  __shared__ int wcnt[kFB / 32];
+// Shared memory of one CTA of the float field kernels.
+struct FieldSmemF {
+  float4 tile[3 * kFB];
+  float2 sv[kFB + 1];
+  float4 su[kFB];
+  double red[kFB / 32];
+  float bred[4 * (kFB / 32)];
+  int wcnt[kFB / 32];
+};
+
+// One tile of kFB * SPT points, thread t owning points t, t + kFB, ...:
+// handle sums with near-zone culling, the boundary term and the epilogue
+// (colour, residual, the tile's loss partial in loss_part[tile]).  `ys` is
+// the panel slice in split mode.  Every CTA-wide barrier is reached by all
+// threads.
+template <bool SAME, bool NEAR, int SPT>
+__device__ __forceinline__ void field_tile_f32(const FieldArgs<float>& a, int64_t tile, int ys,
+                                               FieldSmemF& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t i = (int64_t)blockIdx.x * kFB + tid;
-  const bool live = i < a.n;
-  float x = 0.5f, y = 0.5f;
-  if (live) { x = a.xy[2 * i]; y = a.xy[2 * i + 1]; }
+  int64_t i[SPT];
+  bool live[SPT];
+  float x[SPT], y[SPT];
+  float x0 = __int_as_float(0x7f800000), y0 = x0, x1 = -x0, y1 = -x0;
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    i[k] = tile * (kFB * SPT) + k * kFB + tid;
+    live[k] = i[k] < a.n;
+    x[k] = 0.5f; y[k] = 0.5f;
+    if (live[k]) {
+      x[k] = a.xy[2 * i[k]];
+      y[k] = a.xy[2 * i[k] + 1];
+      x0 = fminf(x0, x[k]); y0 = fminf(y0, y[k]); x1 = fmaxf(x1, x[k]); y1 = fmaxf(y1, y[k]);
+      any = true;
+    }
+  }
   float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
-  if constexpr (NEAR) bb = block_bbox(x, y, x, y, live, bred);
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  const int p0 = a.split_out ? blockIdx.y * a.pchunk : 0;
+  if constexpr (NEAR) bb = block_bbox(x0, y0, x1, y1, any, sm.bred);
+  float s[SPT][3];
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) s[k][0] = s[k][1] = s[k][2] = 0.f;
+  const int p0 = a.split_out ? ys * a.pchunk : 0;
   const int p1 = a.split_out ? min(a.P, p0 + a.pchunk) : a.P;
   for (int base = p0; base < p1; base += kFB) {
     const int cnt = min(kFB, p1 - base);
@@ -202,73 +205,164 @@ __global__ void __launch_bounds__(kFB) k_field_f32(FieldArgs<float> a) {
         cand = boxes_meet(near_zone(p, a.nfac), bb);
       }
       const unsigned m = __ballot_sync(0xffffffffu, cand);
-      if (lane == 0) wcnt[warp] = __popc(m);
+      if (lane == 0) sm.wcnt[warp] = __popc(m);
       __syncthreads();
       int before = 0;
 #pragma unroll
       for (int w = 0; w < kFB / 32; ++w) {
-        before += w < warp ? wcnt[w] : 0;
-        nf += wcnt[w];
+        before += w < warp ? sm.wcnt[w] : 0;
+        nf += sm.wcnt[w];
       }
       if (tid < cnt) {
         const int below = __popc(m & ((1u << lane) - 1u));
         const int slot = cand ? before + below : nf + (warp * 32 - before) + (lane - below);
-        reinterpret_cast<PanelF*>(tile)[slot] = stage_panel(p, a.near2);
+        reinterpret_cast<PanelF*>(sm.tile)[slot] = stage_panel(p, a.near2);
       }
     } else {
-      if (tid < cnt) reinterpret_cast<PanelF*>(tile)[tid] = stage_panel(a.pan[base + tid], 0.f);
+      if (tid < cnt) reinterpret_cast<PanelF*>(sm.tile)[tid] = stage_panel(a.pan[base + tid], 0.f);
     }
     __syncthreads();
     for (int k = 0; k < nf; ++k) {
-      const float4 A = tile[3 * k], B = tile[3 * k + 1], C = tile[3 * k + 2];
-      const Frame<float> f = frame_rn(A.x, A.y, A.z, A.w, B.x, x, y);
-      const float hh = __fmul_rn(f.h, f.h);
-      if (near_test(f, hh, B.y)) continue;
-      pair_acc_f<SAME>(A, B, C, f, hh, a.ec2, a.ed2, s0, s1, s2);
+      const float4 A = sm.tile[3 * k], B = sm.tile[3 * k + 1], C = sm.tile[3 * k + 2];
+#pragma unroll
+      for (int q = 0; q < SPT; ++q) {
+        const Frame<float> f = frame_rn(A.x, A.y, A.z, A.w, B.x, x[q], y[q]);
+        const float hh = __fmul_rn(f.h, f.h);
+        if (!near_test(f, hh, B.y))
+          pair_acc_f<SAME>(A, B, C, f, hh, a.ec2, a.ed2, s[q][0], s[q][1], s[q][2]);
+      }
     }
     for (int k = nf; k < cnt; ++k) {
-      const float4 A = tile[3 * k], B = tile[3 * k + 1], C = tile[3 * k + 2];
-      const Frame<float> f = frame_rn(A.x, A.y, A.z, A.w, B.x, x, y);
-      pair_acc_f<SAME>(A, B, C, f, f.h * f.h, a.ec2, a.ed2, s0, s1, s2);
+      const float4 A = sm.tile[3 * k], B = sm.tile[3 * k + 1], C = sm.tile[3 * k + 2];
+#pragma unroll
+      for (int q = 0; q < SPT; ++q) {
+        const Frame<float> f = frame_rn(A.x, A.y, A.z, A.w, B.x, x[q], y[q]);
+        pair_acc_f<SAME>(A, B, C, f, f.h * f.h, a.ec2, a.ed2, s[q][0], s[q][1], s[q][2]);
+      }
     }
   }
   if (a.split_out) {
-    if (live) {
-      double* o = a.split_out + ((size_t)blockIdx.y * a.n + i) * 3;
-      o[0] = double(s0);
-      o[1] = double(s1);
-      o[2] = double(s2);
-    }
+#pragma unroll
+    for (int q = 0; q < SPT; ++q)
+      if (live[q]) {
+        double* o = a.split_out + ((size_t)ys * a.n + i[q]) * 3;
+        o[0] = double(s[q][0]);
+        o[1] = double(s[q][1]);
+        o[2] = double(s[q][2]);
+      }
     return;
   }
-  float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+  float b[SPT][3];
+#pragma unroll
+  for (int q = 0; q < SPT; ++q) b[q][0] = b[q][1] = b[q][2] = 0.f;
   if (a.ub) {
     for (int base = 0; base < a.Nb; base += kFB) {
       __syncthreads();
       const int cnt = min(kFB, a.Nb - base);
       if (tid < cnt) {
         const int j = base + tid;
-        sv[tid] = make_float2(a.vert[2 * j], a.vert[2 * j + 1]);
-        su[tid] = make_float4(float(a.ub[3 * j]), float(a.ub[3 * j + 1]), float(a.ub[3 * j + 2]),
-                              0.f);
+        sm.sv[tid] = make_float2(a.vert[2 * j], a.vert[2 * j + 1]);
+        sm.su[tid] = make_float4(float(a.ub[3 * j]), float(a.ub[3 * j + 1]),
+                                 float(a.ub[3 * j + 2]), 0.f);
       }
-      if (tid == 0) sv[cnt] = make_float2(a.vert[2 * (base + cnt)], a.vert[2 * (base + cnt) + 1]);
+      if (tid == 0)
+        sm.sv[cnt] = make_float2(a.vert[2 * (base + cnt)], a.vert[2 * (base + cnt) + 1]);
       __syncthreads();
-      float dax = sv[0].x - x, day = sv[0].y - y;
+      float dax[SPT], day[SPT];
+#pragma unroll
+      for (int q = 0; q < SPT; ++q) { dax[q] = sm.sv[0].x - x[q]; day[q] = sm.sv[0].y - y[q]; }
       for (int k = 0; k < cnt; ++k) {
-        const float2 w = sv[k + 1];
-        const float dbx = w.x - x, dby = w.y - y;
-        const float phi = fm_atan2(dax * dby - day * dbx, dax * dbx + day * dby);
-        const float4 u = su[k];
-        b0 = fmaf(phi, u.x, b0);
-        b1 = fmaf(phi, u.y, b1);
-        b2 = fmaf(phi, u.z, b2);
-        dax = dbx;
-        day = dby;
+        const float2 w = sm.sv[k + 1];
+        const float4 u = sm.su[k];
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+          const float dbx = w.x - x[q], dby = w.y - y[q];
+          const float phi = fm_atan2(dax[q] * dby - day[q] * dbx, dax[q] * dbx + day[q] * dby);
+          b[q][0] = fmaf(phi, u.x, b[q][0]);
+          b[q][1] = fmaf(phi, u.y, b[q][1]);
+          b[q][2] = fmaf(phi, u.z, b[q][2]);
+          dax[q] = dbx;
+          day[q] = dby;
+        }
       }
     }
   }
-  field_epilogue<float>(a, i, live, s0, s1, s2, b0, b1, b2, red);
+  // colour, residual and the tile's loss partial
+  double r2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < SPT; ++q) {
+    double u0 = a.mean0 + double(b[q][0]) * kInv2Pi + double(s[q][0]);
+    double u1 = a.mean1 + double(b[q][1]) * kInv2Pi + double(s[q][1]);
+    double u2 = a.mean2 + double(b[q][2]) * kInv2Pi + double(s[q][2]);
+    if (!live[q]) continue;
+    const int64_t ii = i[q];
+    if (a.near_add) {
+      u0 += a.near_add[3 * ii];
+      u1 += a.near_add[3 * ii + 1];
+      u2 += a.near_add[3 * ii + 2];
+    }
+    if (a.out) {
+      a.out[3 * ii] = float(u0);
+      a.out[3 * ii + 1] = float(u1);
+      a.out[3 * ii + 2] = float(u2);
+    }
+    if (a.target) {
+      const double r0 = u0 - fmin(double(a.target[3 * ii]), 1.0);
+      const double r1 = u1 - fmin(double(a.target[3 * ii + 1]), 1.0);
+      const double rr = u2 - fmin(double(a.target[3 * ii + 2]), 1.0);
+      if (a.resid) {
+        a.resid[3 * ii] = float(r0);
+        a.resid[3 * ii + 1] = float(r1);
+        a.resid[3 * ii + 2] = float(rr);
+      }
+      r2 += r0 * r0 + r1 * r1 + rr * rr;
+    }
+  }
+  if (a.loss_part) {
+    for (int o = 16; o; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
+    __syncthreads();
+    if (lane == 0) sm.red[warp] = r2;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0;
+      for (int w = 0; w < kFB / 32; ++w) t += sm.red[w];
+      a.loss_part[tile] = t;
+    }
+  }
+}
+
+template <bool SAME, bool NEAR>
+__global__ void __launch_bounds__(kFB) k_field_f32(const __grid_constant__ FieldArgs<float> a) {
+  __shared__ FieldSmemF sm;
+  field_tile_f32<SAME, NEAR, 1>(a, blockIdx.x, blockIdx.y, sm);
+}
+
+// Batched evaluation: one persistent launch over the 128 * SPT-point tiles
+// of every job (a job = one scene at one parameter vector).  CTAs take tiles
+// from a global counter; a tile's job is found by binary search over the
+// jobs' first-tile offsets.  Each tile runs the same code as k_field_f32, so
+// with SPT = 1 a scene's colours, residuals and loss partials are those of a
+// single-scene evaluation bit for bit.
+template <bool SAME, bool NEAR, int SPT>
+__global__ void __launch_bounds__(kFB) k_field_batch_f32(const BatchJob* __restrict__ jobs, int njobs,
+                                                         const int64_t* __restrict__ total_p,
+                                                         unsigned long long* __restrict__ counter) {
+  __shared__ FieldSmemF sm;
+  __shared__ int64_t item_s;
+  const int64_t total = *total_p;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) item_s = (int64_t)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t item = item_s;
+    if (item >= total) return;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].tile0 <= item) lo = mid; else hi = mid - 1;
+    }
+    field_tile_f32<SAME, NEAR, SPT>(jobs[lo].a, item - jobs[lo].tile0, 0, sm);
+  }
 }
 
 // sum of per-block partials in fixed order -> out[0]
@@ -400,6 +494,31 @@ static int field_eval_t(bem_ctx* c, int64_t n, const void* xy, void* out, const 
     }
   }
   return cuda_check(c, cudaGetLastError(), "k_field");
+}
+
+FieldArgs<float> field_args_f32(bem_ctx* c) { return make_args<float>(c); }
+
+int field_batch_launch(bem_ctx* c, const BatchJob* jobs, int njobs, const int64_t* total_tiles,
+                       unsigned long long* counter, int spt, int blocks_per_sm) {
+  int rc;
+  if ((rc = cuda_check(c, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), S(c)), "memset")))
+    return rc;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const unsigned grid = (unsigned)std::max(1, sms * blocks_per_sm);
+  const bool same = c->opts.eps_c == c->opts.eps_d, near = c->opts.near_factor > 0;
+#define BEM_BATCH_LAUNCH(SM_, NR_, SPT_) \
+  k_field_batch_f32<SM_, NR_, SPT_><<<grid, kFB, 0, S(c)>>>(jobs, njobs, total_tiles, counter)
+  if (spt == 2) {
+    if (same) { if (near) BEM_BATCH_LAUNCH(true, true, 2); else BEM_BATCH_LAUNCH(true, false, 2); }
+    else { if (near) BEM_BATCH_LAUNCH(false, true, 2); else BEM_BATCH_LAUNCH(false, false, 2); }
+  } else {
+    if (same) { if (near) BEM_BATCH_LAUNCH(true, true, 1); else BEM_BATCH_LAUNCH(true, false, 1); }
+    else { if (near) BEM_BATCH_LAUNCH(false, true, 1); else BEM_BATCH_LAUNCH(false, false, 1); }
+  }
+#undef BEM_BATCH_LAUNCH
+  BEM_LAUNCHED(c);
+  return cuda_check(c, cudaGetLastError(), "k_field_batch_f32");
 }
 
 int field_eval(bem_ctx* c, int64_t n, const void* xy, void* out, const void* target, void* resid,

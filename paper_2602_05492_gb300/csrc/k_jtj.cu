@@ -404,8 +404,9 @@ static int jtj_t(bem_ctx* c, int64_t n, const T* xy, double* Hout) {
   size_t per = sizeof(double) * ((size_t)Nb + 3 * (size_t)nc);
   int64_t ns = std::max<int64_t>(128, std::min<int64_t>(n, (int64_t)((512u << 20) / per)));
   ns = std::min<int64_t>(ns, 32768);
-  if ((rc = grow(c, c->jrow, per * (size_t)ns))) return rc;
-  double* phi = (double*)c->jrow.p;
+  bem_ctx* w = c->scratch ? c->scratch : c;   // owner of the chunk buffers
+  if ((rc = grow(c, w->jrow, per * (size_t)ns))) return rc;
+  double* phi = (double*)w->jrow.p;
   double* F = phi + (size_t)ns * Nb;
   double* Hc = (double*)c->Hc.p;
   const T* vert = (const T*)(sizeof(T) == 8 ? (const void*)c->bd.d_vert : (const void*)c->bd.d_vert32);
@@ -573,18 +574,19 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   const size_t gh_b = sizeof(double) * (size_t)std::max(nchunks, 1) * kGemvSegs * 3 * nc;
   const size_t q_b = sizeof(double) * (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
   const size_t gb_b = sizeof(double) * 3 * (size_t)nc;
-  if ((rc = grow(c, c->jrow, phi_b + 256 + f_b + 256))) return rc;
-  if ((rc = grow(c, c->tcJ, j_b))) return rc;
-  if (want_g && (rc = grow(c, c->gwork, gh_b + q_b + gb_b + 256))) return rc;
+  bem_ctx* w = c->scratch ? c->scratch : c;   // owner of the chunk buffers
+  if ((rc = grow(c, w->jrow, phi_b + 256 + f_b + 256))) return rc;
+  if ((rc = grow(c, w->tcJ, j_b))) return rc;
+  if (want_g && (rc = grow(c, w->gwork, gh_b + q_b + gb_b + 256))) return rc;
   const int splits = tc_syrk_splits(nc, x3);
   const size_t part_b = sizeof(float) * (size_t)splits * 3 * nc * nc;
-  if ((rc = grow(c, c->tcPart, part_b))) return rc;
+  if ((rc = grow(c, w->tcPart, part_b))) return rc;
   if ((rc = grow(c, c->Hc, sizeof(double) * 3 * (size_t)nc * nc))) return rc;
-  const void* phi[2] = {c->jrow.p, (char*)c->jrow.p + phi_part};
-  float* F = (float*)((char*)c->jrow.p + (phi_b + 255) / 256 * 256);
-  void* J[2] = {c->tcJ.p, (char*)c->tcJ.p + j_part};
-  float* part = (float*)c->tcPart.p;
-  double* gh = (double*)c->gwork.p;
+  const void* phi[2] = {w->jrow.p, (char*)w->jrow.p + phi_part};
+  float* F = (float*)((char*)w->jrow.p + (phi_b + 255) / 256 * 256);
+  void* J[2] = {w->tcJ.p, (char*)w->tcJ.p + j_part};
+  float* part = (float*)w->tcPart.p;
+  double* gh = (double*)w->gwork.p;
   double* qp = gh + (size_t)std::max(nchunks, 1) * kGemvSegs * 3 * nc;
   double* gb = qp + (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
   if ((rc = cuda_check(c, cudaMemsetAsync(part, 0, part_b, S(c)), "memset"))) return rc;

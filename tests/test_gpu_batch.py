@@ -1,0 +1,113 @@
+"""bem_batch_lm: many scenes of uneven size, four damping trials each, in
+one call (GPU only).
+
+Each scene's result must be the one lm_step gives for that scene alone with
+the same trials: the batched evaluation runs the single-scene evaluation's
+code per tile (with the autotuner's tile shape, so only the float summation
+order can differ), and H, g and the solves are the single-scene ones.  The
+loss at theta is also checked against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+LAMBDAS = [1e-3, 1e-2, 1e-1, 1.0]
+SPECS = [dict(C=4, K=16, W=48, spp=4), dict(C=6, K=32, W=64, spp=8),
+         dict(C=8, K=16, W=32, spp=16), dict(C=2, K=64, W=40, spp=6)]
+
+
+def _bg():
+    import paper_2602_05492_gb300 as bg
+    return bg
+
+
+@pytest.fixture(scope="module")
+def scenes():
+    out = []
+    for k, sp in enumerate(SPECS):
+        spec = dict(sp, layout="random", cross=0.2, noise="gauss", sigma=0.05)
+        sc = gen.make_scene(spec, seed=3100 + k)
+        xy = gen.make_samples(sc.W, sc.spp, sc.seed, dtype=np.float32)
+        tgt = gen.add_noise(gen.analytic_truth(xy, sc.seed), sc.noise, sc.seed).astype(np.float32)
+        mean = np.minimum(tgt, 1.0).mean(0).astype(np.float64)
+        out.append((sc, xy, tgt, mean))
+    return out
+
+
+def _contexts(scenes):
+    bg = _bg()
+    ms = []
+    for sc, xy, tgt, mean in scenes:
+        m = bg.BEM(precision=bg.BEM_MIXED)
+        m.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, mean)
+        m.factor()
+        ms.append(m)
+    return ms
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda:0")
+
+
+def test_batch_matches_single_scene_steps(scenes):
+    bg = _bg()
+    single = _contexts(scenes)
+    batched = _contexts(scenes)
+    b = bg.BEMBatch(batched)
+    xs = [_t(xy) for _, xy, _, _ in scenes]
+    ts = [_t(tg) for _, _, tg, _ in scenes]
+    for it in range(2):
+        rb = b.lm_step(xs, ts, LAMBDAS)
+        for s, m in enumerate(single):
+            r = m.lm_step(xs[s], ts[s], LAMBDAS)
+            assert rb[s]["loss_before"] == pytest.approx(r["loss_before"], rel=1e-6)
+            assert rb[s]["accepted"] == r["accepted"]
+            assert rb[s]["best_trial"] == r["best_trial"]
+            assert rb[s]["loss_after"] == pytest.approx(r["loss_after"], rel=1e-5)
+            assert rb[s]["grad_norm"] == pytest.approx(r["grad_norm"], rel=1e-5)
+            assert rb[s]["lambda_next"] == pytest.approx(r["lambda_next"], rel=1e-12)
+            th_b, th_s = batched[s].get_params(), m.get_params()
+            assert np.abs(th_b - th_s).max() <= 1e-5 * max(1.0, np.abs(th_s).max())
+    pts, ctas = b.tile_shape()
+    assert pts in (128, 256) and ctas in (4, 8, 12)
+    b.close()
+
+
+def test_batch_loss_against_oracle(scenes):
+    bg = _bg()
+    ms = _contexts(scenes)
+    b = bg.BEMBatch(ms)
+    xs = [_t(xy) for _, xy, _, _ in scenes]
+    ts = [_t(tg) for _, _, tg, _ in scenes]
+    rb = b.lm_step(xs, ts, LAMBDAS)
+    for s, (sc, xy, tg, mean) in enumerate(scenes):
+        o = oracle.Oracle.from_scene(sc, mean_color=mean)
+        want = o.loss(sc.theta_init, xy.astype(np.float64), tg.astype(np.float64))
+        assert rb[s]["loss_before"] == pytest.approx(want, rel=1e-5)
+    b.close()
+
+
+def test_batch_arguments(scenes):
+    bg = _bg()
+    ms = _contexts(scenes[:2])
+    m64 = bg.BEM(precision=bg.BEM_FP64)
+    sc = scenes[0][0]
+    m64.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, scenes[0][3])
+    m64.factor()
+    with pytest.raises(bg.BemError):
+        bg.BEMBatch([ms[0], m64])
+    with pytest.raises(bg.BemError):
+        bg.BEMBatch([ms[0], ms[0]])
+    b = bg.BEMBatch(ms)
+    xs = [_t(xy) for _, xy, _, _ in scenes[:2]]
+    ts = [_t(tg) for _, _, tg, _ in scenes[:2]]
+    with pytest.raises(bg.BemError):
+        b.lm_step(xs, ts, [1e-3] * 17)
+    with pytest.raises(bg.BemError):
+        b.lm_step(xs, ts, [float("nan")])
+    b.close()
