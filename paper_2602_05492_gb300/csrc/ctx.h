@@ -168,7 +168,9 @@ bool jtj_gives_gradient(const bem_ctx* c);
 int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                   float* D, int ldd);
 int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt, int ldm,
-             const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj);
+             const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj,
+             const float* resid = nullptr, int nc = 0, double* gpart = nullptr,
+             int64_t gstride = 0);
 int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, float* part,
             int splits);
 int tc_syrk_splits(int nc, bool x3);

@@ -331,11 +331,14 @@ __device__ __forceinline__ void field_tile_f32(const FieldArgs<float>& a, int64_
   }
 }
 
-template <bool SAME, bool NEAR>
+template <bool SAME, bool NEAR, int SPT>
 __global__ void __launch_bounds__(kFB) k_field_f32(const __grid_constant__ FieldArgs<float> a) {
   __shared__ FieldSmemF sm;
-  field_tile_f32<SAME, NEAR, 1>(a, blockIdx.x, blockIdx.y, sm);
+  field_tile_f32<SAME, NEAR, SPT>(a, blockIdx.x, blockIdx.y, sm);
 }
+
+// points per thread of the float evaluation (split mode: 1)
+constexpr int kSptEval = 2;
 
 // Batched evaluation: one persistent launch over the 128 * SPT-point tiles
 // of every job (a job = one scene at one parameter vector).  CTAs take tiles
@@ -448,13 +451,19 @@ static void launch_field(bem_ctx* c, const FieldArgs<T>& a, dim3 grid) {
   const bool same = c->opts.eps_c == c->opts.eps_d;
   if constexpr (sizeof(T) == 4) {
     const bool near = c->opts.near_factor > 0;
-    if (same) {
-      if (near) k_field_f32<true, true><<<grid, kFB, 0, S(c)>>>(a);
-      else k_field_f32<true, false><<<grid, kFB, 0, S(c)>>>(a);
-    } else {
-      if (near) k_field_f32<false, true><<<grid, kFB, 0, S(c)>>>(a);
-      else k_field_f32<false, false><<<grid, kFB, 0, S(c)>>>(a);
-    }
+#define BEM_FIELD_F32(SPT_)                                                  \
+  do {                                                                       \
+    if (same) {                                                              \
+      if (near) k_field_f32<true, true, SPT_><<<grid, kFB, 0, S(c)>>>(a);    \
+      else k_field_f32<true, false, SPT_><<<grid, kFB, 0, S(c)>>>(a);        \
+    } else {                                                                 \
+      if (near) k_field_f32<false, true, SPT_><<<grid, kFB, 0, S(c)>>>(a);   \
+      else k_field_f32<false, false, SPT_><<<grid, kFB, 0, S(c)>>>(a);       \
+    }                                                                        \
+  } while (0)
+    if (a.split_out) BEM_FIELD_F32(1);
+    else BEM_FIELD_F32(kSptEval);
+#undef BEM_FIELD_F32
   } else {
     if (same) k_field<T, true><<<grid, kFB, 0, S(c)>>>(a);
     else k_field<T, false><<<grid, kFB, 0, S(c)>>>(a);
@@ -474,7 +483,8 @@ static int field_eval_t(bem_ctx* c, int64_t n, const void* xy, void* out, const 
   a.target = (const T*)target;
   a.out = (T*)out;
   a.resid = (T*)resid;
-  int64_t nblk = (n + kFB - 1) / kFB;
+  const int64_t per_block = sizeof(T) == 4 ? (int64_t)kFB * kSptEval : kFB;
+  int64_t nblk = (n + per_block - 1) / per_block;
   if (sizeof(T) == 4 && c->opts.near_factor > 0 && n > 0) {
     if ((rc = grow(c, c->nearF, sizeof(double) * 3 * (size_t)n))) return rc;
     if ((rc = near_forward(c, n, (const float*)xy, (double*)c->nearF.p))) return rc;

@@ -65,6 +65,12 @@ struct TcArgs {
   int k_per_split;
   float* part;              // [splits][3][nc][nc]
   int* err;
+  // EPI_JROWS (bf16) with residuals: gpart[row * gstride + blockIdx.y] =
+  // sum over the tile's samples s of F[row][s] resid[s][row / gnc]
+  const float* resid;
+  int gnc;
+  double* gpart;
+  int64_t gstride;
 };
 
 template <bool X3>
@@ -175,6 +181,8 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
   // chunk cc sits at position cc ^ (rr & 7), so that the per-row reads below
   // (lane = row) and the in-place bf16 writes are free of bank conflicts.
   float* fs = reinterpret_cast<float*>(smem);
+  // residuals of the tile's samples (when the gradient is formed here)
+  float* rs = fs + BM * BN;
   if (!X3 && g.mode == EPI_JROWS) {
     for (int e = threadIdx.x; e < BM * (BN / 4); e += 128) {
       const int rr = e / (BN / 4), cc = e % (BN / 4);
@@ -190,9 +198,16 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
         d[3] = 0.f;
       }
     }
+    if (g.gpart)
+      for (int e = threadIdx.x; e < 3 * BN; e += 128) {
+        const int col = brow + e / 3;
+        rs[e] = col < g.N ? g.resid[3 * (size_t)col + e % 3] : 0.f;
+      }
     umma::cp_async_wait_all();
     __syncthreads();
   }
+  const int gch = (g.gpart && arow + r < g.M) ? (arow + r) / g.gnc : 0;
+  float gacc = 0.f;
 #pragma unroll 1
   for (int cb = 0; cb < BN; cb += 32) {
     float v[32];
@@ -237,6 +252,10 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
         const float4 q = *reinterpret_cast<const float4*>(fr + ((((cb >> 2) + k) ^ sw) << 2));
         f[4 * k] = q.x; f[4 * k + 1] = q.y; f[4 * k + 2] = q.z; f[4 * k + 3] = q.w;
       }
+      if (g.gpart) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rs[3 * (cb + j) + gch], gacc);
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         uint4 w;
@@ -261,6 +280,8 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
       }
     }
   }
+  if (!X3 && g.mode == EPI_JROWS && g.gpart && arow + r < g.M)
+    g.gpart[(size_t)(arow + r) * g.gstride + blockIdx.y] = (double)gacc;
   if (!X3 && g.mode == EPI_JROWS) {
     __syncthreads();
     // row rr of the bf16 tile sits at the front of fs row rr (bf16 chunk k
@@ -350,10 +371,12 @@ int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const
 }
 
 // J^T rows: J[rows][m] = Mt[rows][Nb] Phi[m][Nb]^T + F[rows][m].
-//   bf16:   Mt, Phi bf16; J bf16 (Jout[0])
+//   bf16:   Mt, Phi bf16; J bf16 (Jout[0]); with gpart, also the handle part
+//           of the gradient per 128-sample tile (see TcArgs)
 //   3xtf32: Mt = (Mt[0] hi, Mt[1] lo), Phi likewise, fp32; J hi/lo fp32 (Jout[0], Jout[1])
 int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt, int ldm,
-             const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj) {
+             const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj,
+             const float* resid, int nc, double* gpart, int64_t gstride) {
   int rc;
   CUtensorMap ta, tb, ta2, tb2;
   if ((rc = make_map(c, &ta, Mt[0], Nb, rows, ldm, x3)) ||
@@ -368,6 +391,12 @@ int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt
   g.err = c->d_status;
   if (x3) { g.Jhi = (float*)Jout[0]; g.Jlo = (float*)Jout[1]; }
   else g.J = (__nv_bfloat16*)Jout[0];
+  if (!x3 && gpart) {
+    g.resid = resid;
+    g.gnc = nc;
+    g.gpart = gpart;
+    g.gstride = gstride;
+  }
   ProfScope _ps(c, "tc_jrows");
   dim3 grid((rows + BM - 1) / BM, (m + BN - 1) / BN);
   return x3 ? launch<true>(c, ta, tb, ta2, tb2, g, grid) : launch<false>(c, ta, tb, ta, tb, g, grid);

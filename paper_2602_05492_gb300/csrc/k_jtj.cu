@@ -75,7 +75,7 @@ __device__ __forceinline__ void frows_pair(const Panel<T>& p, T x, T y, T ec2, T
 }
 
 template <typename T, bool SAME, bool TR>
-__global__ void k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __restrict__ pan,
+__global__ void __launch_bounds__(128, 6) k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __restrict__ pan,
                         const int* __restrict__ off, const int* __restrict__ Kc,
                         const uint8_t* __restrict__ closed, int C, T ec2, T ed2,
                         void* __restrict__ Fout, int ldf) {
@@ -246,6 +246,19 @@ __global__ void k_sum_rows(const double* __restrict__ part, int nparts, int m, d
   double s = 0;
   for (int k = 0; k < nparts; ++k) s += part[(size_t)k * m + t];
   out[t] = s;
+}
+
+// out[row] = sum over k of part[row][k] (fixed order; one warp per row)
+__global__ void k_row_sums(const double* __restrict__ part, int rows, int64_t nparts,
+                           double* __restrict__ out) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const double* p = part + (size_t)row * nparts;
+  double s = 0;
+  for (int64_t k = lane; k < nparts; k += 32) s += p[k];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[row] = s;
 }
 
 // gpart[seg][row] = sum over segment seg of the chunk's samples of
@@ -571,7 +584,12 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   const size_t j_b = (x3 ? 2 : 1) * j_part;
   // gradient work: per chunk handle partial [3nc], q partials per slice
   const int qslices = (int)std::max<int64_t>(1, std::min<int64_t>(64, (chunk + 4095) / 4096));
-  const size_t gh_b = sizeof(double) * (size_t)std::max(nchunks, 1) * kGemvSegs * 3 * nc;
+  // handle part of the gradient: bf16 J rows form it per 128-sample tile in
+  // their epilogue ([3nc][tiles]); 3xtf32 runs a GEMV per chunk ([chunks x segs][3nc])
+  const bool fused_g = want_g && !x3;
+  const int64_t tiles_all = (n + 127) / 128 + nchunks;   // tile columns, a little slack per chunk
+  const size_t gh_b = sizeof(double) * (fused_g ? (size_t)tiles_all * 3 * nc + 3 * (size_t)nc
+                                                : (size_t)std::max(nchunks, 1) * kGemvSegs * 3 * nc);
   const size_t q_b = sizeof(double) * (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
   const size_t gb_b = sizeof(double) * 3 * (size_t)nc;
   bem_ctx* w = c->scratch ? c->scratch : c;   // owner of the chunk buffers
@@ -587,11 +605,15 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   void* J[2] = {w->tcJ.p, (char*)w->tcJ.p + j_part};
   float* part = (float*)w->tcPart.p;
   double* gh = (double*)w->gwork.p;
-  double* qp = gh + (size_t)std::max(nchunks, 1) * kGemvSegs * 3 * nc;
+  double* qp = gh + gh_b / sizeof(double);
   double* gb = qp + (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
   if ((rc = cuda_check(c, cudaMemsetAsync(part, 0, part_b, S(c)), "memset"))) return rc;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
   int ci = 0;
+  int64_t tile_col = 0;
+  if (fused_g &&
+      (rc = cuda_check(c, cudaMemsetAsync(gh, 0, sizeof(double) * (size_t)tiles_all * 3 * nc, S(c)), "memset")))
+    return rc;
   for (int64_t s0 = 0; s0 < n; s0 += chunk, ++ci) {
     const int m = (int)std::min<int64_t>(chunk, n - s0);
     {
@@ -612,13 +634,17 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
       BEM_LAUNCHED(c);
     }
     launch_frows<float, true>(c, xy + 2 * s0, m, F, ld);
-    if (want_g) {
+    if (want_g && !fused_g) {
       ProfScope _pg(c, "k_ft_gemv");
       k_ft_gemv<<<dim3((3 * nc + 7) / 8, kGemvSegs), 256, 0, S(c)>>>(
           F, ld, 3 * nc, nc, m, resid + 3 * s0, gh + (size_t)ci * kGemvSegs * 3 * nc);
       BEM_LAUNCHED(c);
     }
-    if ((rc = tc_jrows(c, x3, 3 * nc, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld))) return rc;
+    if ((rc = tc_jrows(c, x3, 3 * nc, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld,
+                       fused_g ? resid + 3 * s0 : nullptr, nc,
+                       fused_g ? gh + tile_col : nullptr, tiles_all)))
+      return rc;
+    tile_col += (m + 127) / 128;
     const void* Jc[2] = {J[0], J[1]};
     if ((rc = tc_syrk(c, x3, nc, m, Jc, ld, part, splits))) return rc;
   }
@@ -634,9 +660,17 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
     BEM_LAUNCHED(c);
     if ((rc = la_apply3_refined(c, c->bd.d_WT32, c->bd.d_A, c->d_q, c->d_lb, true))) return rc;
     k_g_boundary<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>((const double*)c->Dfc.p, Nb, nc, c->d_lb, gb);
-    k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(gh, nchunks * kGemvSegs, 3 * nc, gb, C,
-                                                       n > 0 ? 1.0 / double(n) : 0.0, gout);
-    c->launches += 2;
+    if (fused_g) {
+      double* ghr = gh + (size_t)tiles_all * 3 * nc;
+      k_row_sums<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>(gh, 3 * nc, tiles_all, ghr);
+      k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(ghr, 1, 3 * nc, gb, C,
+                                                         n > 0 ? 1.0 / double(n) : 0.0, gout);
+      c->launches += 3;
+    } else {
+      k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(gh, nchunks * kGemvSegs, 3 * nc, gb, C,
+                                                         n > 0 ? 1.0 / double(n) : 0.0, gout);
+      c->launches += 2;
+    }
   }
   if ((rc = cuda_check(c, cudaGetLastError(), "jtj tc"))) return rc;
   int st = 0;

@@ -17,6 +17,7 @@
 //    triangular solves, and a 3 x 3 Schur complement for the compatibility
 //    constraints (one per colour channel).
 #include <cmath>
+#include <cstring>
 
 #include <algorithm>
 
@@ -646,13 +647,14 @@ static void chol_factor(bem_ctx* c, T* Km, int n, T* Linv, int* status) {
 // so that no CTA writes what another reads; Kf keeps the trailing updates.
 __global__ void __launch_bounds__(256) k_chol_step_f32(float* __restrict__ Kf, float* __restrict__ Lf,
                                                        int n, int k0, float* __restrict__ Linv,
-                                                       int* __restrict__ status) {
+                                                       int* __restrict__ status,
+                                                       float* __restrict__ bad_pivot) {
   __shared__ float T[32][33], X[32][33];
   __shared__ float Araw[2][64][33];
   __shared__ float P[2][32][65];
   __shared__ float rdg[32];
   const int tid = threadIdx.x;
-  const int nb = min(32, n - k0), r0 = k0 + nb, rest = n - r0;
+  const int nb = min(32, n - k0), r0 = k0 + nb;
   const bool diag_cta = blockIdx.x == gridDim.x - 1;
   int bi = 0, bj = 0, i0 = 0, j0 = 0, nsides = 0;
   if (!diag_cta) {
@@ -690,7 +692,8 @@ __global__ void __launch_bounds__(256) k_chol_step_f32(float* __restrict__ Kf, f
       if (j < nb) {
         float d = __shfl_sync(0xffffffffu, a[j], j);
         if (!(d > 0.f)) {
-          if (r == 0) atomicExch(status, 1);
+          // the first failing pivot (all CTAs compute the same one)
+          if (r == 0 && atomicCAS(status, 0, 1) == 0) *bad_pivot = d;
           d = 1.f;
         }
         const float rs = rsqrtf(d);
@@ -1058,6 +1061,7 @@ __global__ void k_kkt_finish(const double* __restrict__ X, const double* __restr
 constexpr int kRefineCheck = 2, kRefineMax = 10;
 constexpr double kRefineTol = 1e-14;
 constexpr int kMaxSingleCtaSolve = 12288;
+constexpr float kIndefinitePivot = -1e-2f;
 
 int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double* delta) {
   int n = c->sc.nth, rc;
@@ -1082,6 +1086,7 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
   double* epart = dsc + (size_t)n;        // [rblk][4] backward-error partials
   double* eta_d = epart + 4 * rblk;
   int* fstat = (int*)(eta_d + 1);
+  float* fpiv = (float*)(eta_d + 1) + 1;
   double* mx = eta_d + 2;
   double* gn = mx + 1;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
@@ -1102,11 +1107,11 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
       ProfScope _pc(c, "lm_cholesky");
       k_equilibrate<<<dim3((n + 127) / 128, n), 128, 0, S(c)>>>(Km, n, Kf, dsc);
       BEM_LAUNCHED(c);
-      if ((rc = cuda_check(c, cudaMemsetAsync(fstat, 0, sizeof(int), S(c)), "memset"))) return rc;
+      if ((rc = cuda_check(c, cudaMemsetAsync(fstat, 0, 2 * sizeof(int), S(c)), "memset"))) return rc;
       for (int k0 = 0; k0 < n; k0 += 32) {
         const int tiles = (n - std::min(n, k0 + 32) + 63) / 64;
         k_chol_step_f32<<<tiles * (tiles + 1) / 2 + 1, 256, 0, S(c)>>>(Kf, Lf, n, k0, Linvf,
-                                                                         fstat);
+                                                                         fstat, fpiv);
         BEM_LAUNCHED(c);
       }
     }
@@ -1126,12 +1131,21 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
       k_backward_error<<<1, 256, 0, S(c)>>>(epart, rblk, eta_d);
       c->launches += 3;
       if (it + 1 < kRefineCheck) continue;
-      double h[1];
-      if ((rc = cuda_check(c, cudaMemcpyAsync(h, eta_d, sizeof(double), cudaMemcpyDeviceToHost, S(c)), "eta")) ||
-          (rc = cuda_check(c, cudaMemcpyAsync(&fst, fstat, sizeof(int), cudaMemcpyDeviceToHost, S(c)), "status")) ||
+      double h[2];
+      if ((rc = cuda_check(c, cudaMemcpyAsync(h, eta_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, S(c)), "eta")) ||
           (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "refine sync")))
         return rc;
-      if (fst) break;                      // the float factor hit a non-positive pivot
+      std::memcpy(&fst, &h[1], sizeof(int));
+      if (fst) {
+        // the float factor hit a non-positive pivot.  The equilibrated
+        // matrix has a unit diagonal, so float rounding moves a pivot by
+        // about n * 6e-8; a pivot far below zero means the matrix itself is
+        // not positive definite, which the double factor would only confirm
+        float pv;
+        std::memcpy(&pv, reinterpret_cast<const char*>(&h[1]) + sizeof(int), sizeof(float));
+        if (pv < kIndefinitePivot) return fail(c, BEM_ENOTSPD, "LM matrix is not positive definite");
+        break;
+      }
       eta_prev = it + 1 == kRefineCheck ? 2.0 : eta;
       eta = h[0];
       if (eta < kRefineTol) { done = true; break; }

@@ -62,6 +62,7 @@ def test_batch_matches_single_scene_steps(scenes):
     xs = [_t(xy) for _, xy, _, _ in scenes]
     ts = [_t(tg) for _, _, tg, _ in scenes]
     for it in range(2):
+        before = [m.get_params() for m in single]
         rb = b.lm_step(xs, ts, LAMBDAS)
         for s, m in enumerate(single):
             r = m.lm_step(xs[s], ts[s], LAMBDAS)
@@ -71,8 +72,12 @@ def test_batch_matches_single_scene_steps(scenes):
             assert rb[s]["loss_after"] == pytest.approx(r["loss_after"], rel=1e-5)
             assert rb[s]["grad_norm"] == pytest.approx(r["grad_norm"], rel=1e-5)
             assert rb[s]["lambda_next"] == pytest.approx(r["lambda_next"], rel=1e-12)
+            # the tile shape may differ from the single-scene evaluation's, so
+            # the residuals agree to float rounding only; the damped solve
+            # amplifies that by its conditioning: compare against the step
             th_b, th_s = batched[s].get_params(), m.get_params()
-            assert np.abs(th_b - th_s).max() <= 1e-5 * max(1.0, np.abs(th_s).max())
+            step = np.abs(th_s - before[s]).max()
+            assert np.abs(th_b - th_s).max() <= 1e-3 * step + 1e-7
     pts, ctas = b.tile_shape()
     assert pts in (128, 256) and ctas in (4, 8, 12)
     b.close()
