@@ -240,18 +240,38 @@ def boundary_field(xy, seg, ub):
 # ---------------------------------------------------------------------------
 # Galerkin system and its pseudo-inverse
 
-def assemble_A(seg: np.ndarray) -> np.ndarray:
+def assemble_A(seg: np.ndarray, mode: int = 0) -> np.ndarray:
     """Galerkin matrix of Eq. (bie_galerkin).
 
-    A_ii = |G_i| / 2 (coincident double-layer term is zero for a straight
-    segment); A_ij = int_{G_i} int_{G_j} dG/dn_y dy dx with the inner
-    integral exact (-phi_j(x)/2pi) and the outer by 3-point Gauss.
+    A_ii = |G_i| / 2 (the coincident double-layer term is zero for a straight
+    segment); A_ij = int_{G_i} int_{G_j} dG/dn_y dy dx with the outer
+    integral by 3-point Gauss and the inner one
+      mode 0: exact, -phi_j(x)/2pi (the signed angle segment j subtends);
+      mode 1: 3-point Gauss as well (the paper's 3 x 3 rule), with
+              dG/dn_y = -(1/2pi) n_y.(y - x)/|y - x|^2, n_y the right normal.
     """
     Nb = seg.shape[0]
     ell = np.hypot(seg[:, 2] - seg[:, 0], seg[:, 3] - seg[:, 1])
     gp = gauss_points(seg).reshape(-1, 2)                 # [3 Nb, 2]
-    phi = angles(gp, seg).reshape(Nb, 3, Nb)              # phi_j at x_iq
-    A = -(ell[:, None] / (2.0 * math.pi)) * np.einsum("q,iqj->ij", GAUSS_WEIGHTS, phi)
+    if mode == 0:
+        inner = -angles(gp, seg) / (2.0 * math.pi)        # [3 Nb, Nb]
+    elif mode == 1:
+        a, b = seg[:, 0:2], seg[:, 2:4]
+        tau = (b - a) / ell[:, None]
+        nrm = np.stack([tau[:, 1], -tau[:, 0]], 1)        # right normal
+        y = gauss_points(seg)                             # [Nb, 3, 2]
+        inner = np.empty((gp.shape[0], Nb))
+        for r0 in range(0, gp.shape[0], 256):
+            x = gp[r0:r0 + 256]
+            d = y[None, :, :, :] - x[:, None, None, :]    # [r, Nb, 3, 2]
+            r2 = np.sum(d * d, axis=-1)
+            num = np.sum(d * nrm[None, :, None, :], axis=-1)
+            with np.errstate(invalid="ignore", divide="ignore"):
+                k = np.where(r2 > 0, num / r2, 0.0)
+            inner[r0:r0 + 256] = -(ell[None, :] / (2.0 * math.pi)) * (k @ GAUSS_WEIGHTS)
+    else:
+        raise ValueError(f"galerkin mode {mode}")
+    A = ell[:, None] * np.einsum("q,iqj->ij", GAUSS_WEIGHTS, inner.reshape(Nb, 3, Nb))
     A[np.arange(Nb), np.arange(Nb)] = 0.5 * ell
     return A
 
@@ -269,7 +289,8 @@ class Oracle:
     """FP64 reference of one scene: fixed boundary, varying handle parameters."""
 
     def __init__(self, n_curves, panels_per_curve, closed, mean_color,
-                 segs_per_side: int = 256, eps_d: float = 1e-2, eps_c: float = 1e-2):
+                 segs_per_side: int = 256, eps_d: float = 1e-2, eps_c: float = 1e-2,
+                 galerkin_mode: int = 0):
         self.geo = Geometry.build(n_curves, panels_per_curve, closed)
         self.mean = np.asarray(mean_color, np.float64).reshape(3)
         self.eps_d = float(eps_d)
@@ -278,7 +299,7 @@ class Oracle:
         self.Nb = self.seg.shape[0]
         self.ell = np.hypot(self.seg[:, 2] - self.seg[:, 0], self.seg[:, 3] - self.seg[:, 1])
         self.gp = gauss_points(self.seg)                 # [Nb, 3, 2]
-        self.A = assemble_A(self.seg)
+        self.A = assemble_A(self.seg, galerkin_mode)
         self.Apinv = pinv_svd(self.A)
 
     @staticmethod

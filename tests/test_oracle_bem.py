@@ -187,3 +187,44 @@ def test_quarter_turn_symmetry():
     u1 = o.eval(sc.theta_true, pts)
     u2 = o.eval(th2.reshape(-1), rot(pts))
     np.testing.assert_allclose(u1, u2, atol=1e-11)
+
+
+# ---- paper-literal 3 x 3 Galerkin rule (galerkin_mode = 1) ----------------------
+
+def test_galerkin_3x3_gauss_order():
+    """The 3-point Gauss inner integral of a smooth kernel converges to the
+    exact (mode 0) entry with the rule's order: the relative error of the
+    pair (centre of the bottom side, centre of the top side) falls by 2^6 per
+    halving of the segment length."""
+    from oracle.bem import assemble_A, square_boundary
+    errs = []
+    for M in (16, 32, 64):
+        seg = square_boundary(M)
+        A0, A1 = assemble_A(seg, 0), assemble_A(seg, 1)
+        i, j = M // 2, 2 * M + M // 2          # bottom centre, top centre (opposite)
+        errs.append(abs(A1[i, j] - A0[i, j]) / abs(A0[i, j]))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 40 < r1 < 90 and 40 < r2 < 90, (errs, r1, r2)
+
+
+def test_galerkin_3x3_structure():
+    """Quarter-turn invariance of the square (side s -> side s+1), zero
+    entries for collinear segments of one side, and the diagonal."""
+    from oracle.bem import assemble_A, square_boundary
+    M = 12
+    seg = square_boundary(M)
+    A1 = assemble_A(seg, 1)
+    Nb = 4 * M
+    idx = (np.arange(Nb) + M) % Nb
+    assert np.allclose(A1[np.ix_(idx, idx)], A1, rtol=0, atol=1e-15)
+    for i in range(M):
+        for j in range(M):
+            if i != j:
+                assert A1[i, j] == 0.0
+    ell = 1.0 / M
+    assert np.allclose(np.diag(A1), 0.5 * ell, rtol=0, atol=1e-16)
+    # not exactly singular any more: the constants are no null vector, but
+    # the smallest singular value stays well separated (the truncation of
+    # Sec. 3.1.3 remains well defined)
+    s = np.linalg.svd(A1, compute_uv=False)
+    assert s[-1] < 1e-3 * s[-2]
