@@ -73,7 +73,12 @@ typedef struct {
                              lengths are evaluated in double; default 0.5; 0 = never */
     int jtj_mode;         /* arithmetic of the J^T J contraction (BEM_JTJ_*) */
     int lm_solver;        /* BEM_LM_AUTO (default) or BEM_LM_FP64 */
-    int reserved[7];
+    int galerkin_mode;    /* boundary matrix, Sec. 3.1.3: 0 (default) inner integral of
+                             each entry exact, outer by 3-point Gauss; 1 both by 3-point
+                             Gauss (the paper's rule).  Mode 1 leaves the constants only
+                             nearly in the null space; its pseudo-inverse drops the
+                             smallest singular value exactly, as in mode 0 */
+    int reserved[6];
 } bem_opts;
 
 typedef struct {

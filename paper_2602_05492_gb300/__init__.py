@@ -33,7 +33,8 @@ class bem_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("eps_d", ctypes.c_double),
                 ("eps_c", ctypes.c_double), ("segs_per_side", ctypes.c_int),
                 ("near_factor", ctypes.c_double), ("jtj_mode", ctypes.c_int),
-                ("lm_solver", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("lm_solver", ctypes.c_int), ("galerkin_mode", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class lm_result(ctypes.Structure):
@@ -128,7 +129,7 @@ class BEM:
     """One library context (scene + factored boundary) on one CUDA device."""
 
     def __init__(self, precision=BEM_FP64, eps_d=1e-2, eps_c=1e-2, segs_per_side=256,
-                 near_factor=0.5, jtj_mode=None, lm_solver=0, device=0):
+                 near_factor=0.5, jtj_mode=None, lm_solver=0, galerkin_mode=0, device=0):
         o = bem_opts()
         _lib.bem_default_opts(ctypes.byref(o))
         o.precision = precision
@@ -138,6 +139,7 @@ class BEM:
         o.jtj_mode = (BEM_JTJ_FP64 if precision == BEM_FP64 else BEM_JTJ_BF16) \
             if jtj_mode is None else jtj_mode
         o.lm_solver = lm_solver
+        o.galerkin_mode = galerkin_mode
         self.opts = o
         self.device = device
         h = ctypes.c_void_p()

@@ -186,6 +186,7 @@ int bem_default_opts(bem_opts* o) {
   o->near_factor = 0.5;
   o->jtj_mode = BEM_JTJ_FP64;
   o->lm_solver = BEM_LM_AUTO;
+  o->galerkin_mode = 0;
   return BEM_OK;
 }
 
@@ -206,6 +207,8 @@ int bem_create(bem_ctx** out, const bem_opts* opts, int device) {
     return fail(nullptr, BEM_EINVAL, "unknown jtj_mode");
   if (o.lm_solver != BEM_LM_AUTO && o.lm_solver != BEM_LM_FP64)
     return fail(nullptr, BEM_EINVAL, "unknown lm_solver");
+  if (o.galerkin_mode != 0 && o.galerkin_mode != 1)
+    return fail(nullptr, BEM_EINVAL, "unknown galerkin_mode");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
     return fail(nullptr, BEM_ECUDA, "no such CUDA device");

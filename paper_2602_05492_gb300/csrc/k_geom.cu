@@ -92,11 +92,14 @@ __global__ void k_compat(double* __restrict__ theta, const Panel<double>* __rest
     for (int c = 0; c < 3; ++c) theta[h * 8 + 5 + c] -= a[h] * tot[1 + c] / tot[0];
 }
 
-// A_ij = -|G_i| sum_q w_q phi_j(x_iq) / (2 pi) (exact inner integral, 3-point
-// Gauss outer rule), A_ii = |G_i| / 2 (the coincident double-layer term of a
-// straight segment vanishes), Eq. (bie_galerkin).
+// A_ij = |G_i| sum_q w_q I_j(x_iq), A_ii = |G_i| / 2 (the coincident
+// double-layer term of a straight segment vanishes), Eq. (bie_galerkin), with
+// the inner integral I_j(x) of dG/dn_y over segment j
+//   mode 0: exact, -phi_j(x)/(2 pi) (the signed angle of the segment at x);
+//   mode 1: 3-point Gauss, -(|G_j|/2pi) sum_q' w_q' n_j.(y_jq' - x)/|y_jq' - x|^2
+//           with n_j the right normal (the paper's 3 x 3 rule).
 __global__ void k_assemble(const double* __restrict__ vert, const double* __restrict__ gp, int Nb,
-                           double* __restrict__ A) {
+                           int mode, double* __restrict__ A) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y;
   if (j >= Nb) return;
@@ -108,9 +111,26 @@ __global__ void k_assemble(const double* __restrict__ vert, const double* __rest
   }
   double ax = vert[2 * j], ay = vert[2 * j + 1], bx = vert[2 * (j + 1)], by = vert[2 * (j + 1) + 1];
   double s = 0;
-  for (int q = 0; q < 3; ++q)
-    s += gauss_weight(q) * seg_angle(ax, ay, bx, by, gp[2 * (3 * i + q)], gp[2 * (3 * i + q) + 1]);
-  A[(size_t)i * Nb + j] = -ell * s * kInv2Pi;
+  if (mode == 0) {
+    for (int q = 0; q < 3; ++q)
+      s += gauss_weight(q) * seg_angle(ax, ay, bx, by, gp[2 * (3 * i + q)], gp[2 * (3 * i + q) + 1]);
+    A[(size_t)i * Nb + j] = -ell * s * kInv2Pi;
+    return;
+  }
+  const double lj = sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+  const double nx = (by - ay) / lj, ny = -(bx - ax) / lj;     // right normal
+  for (int q = 0; q < 3; ++q) {
+    const double x = gp[2 * (3 * i + q)], y = gp[2 * (3 * i + q) + 1];
+    double in = 0;
+    for (int p = 0; p < 3; ++p) {
+      const double t = gauss_node(p);
+      const double dx = ax + t * (bx - ax) - x, dy = ay + t * (by - ay) - y;
+      const double r2 = dx * dx + dy * dy;
+      if (r2 > 0) in += gauss_weight(p) * (nx * dx + ny * dy) / r2;
+    }
+    s += gauss_weight(q) * in;
+  }
+  A[(size_t)i * Nb + j] = -ell * lj * s * kInv2Pi;
 }
 
 int geom_panelize(bem_ctx* c, const double* d_theta) {
@@ -169,7 +189,8 @@ int geom_boundary_tables(bem_ctx* c) {
 int geom_assemble(bem_ctx* c) {
   int Nb = c->bd.Nb;
   dim3 grid((Nb + 127) / 128, Nb);
-  k_assemble<<<grid, 128, 0, S(c)>>>(c->bd.d_vert, c->bd.d_gp, Nb, c->bd.d_A);
+  k_assemble<<<grid, 128, 0, S(c)>>>(c->bd.d_vert, c->bd.d_gp, Nb, c->opts.galerkin_mode,
+                                     c->bd.d_A);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_assemble");
 }

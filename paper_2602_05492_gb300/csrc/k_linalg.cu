@@ -20,6 +20,7 @@
 #include <cstring>
 
 #include <algorithm>
+#include <vector>
 
 #include "ctx.h"
 
@@ -28,8 +29,12 @@ namespace bem {
 // ---------------------------------------------------------------------------
 // Gauss-Jordan on the augmented matrix G = [B | I], N rows, 2N columns.
 
-__global__ void k_gj_init(const double* __restrict__ A, int Nb, double* __restrict__ G) {
-  int N = Nb + 1, W = 2 * N;
+// G = [B | I] with B = A (bordered = 0, N = Nb) or B = [[A, c],[r^T, 0]]
+// (bordered = 1, N = Nb + 1; c, r default to the constants).
+__global__ void k_gj_init(const double* __restrict__ A, int Nb, int bordered,
+                          const double* __restrict__ bcol, const double* __restrict__ brow,
+                          double* __restrict__ G) {
+  int N = Nb + bordered, W = 2 * N;
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)N * W) return;
   int i = idx / W, j = idx % W;
@@ -37,7 +42,8 @@ __global__ void k_gj_init(const double* __restrict__ A, int Nb, double* __restri
   if (j < N) {
     if (i < Nb && j < Nb) v = A[(size_t)i * Nb + j];
     else if (i == Nb && j == Nb) v = 0.0;
-    else v = 1.0;
+    else if (j == Nb) v = bcol ? bcol[i] : 1.0;
+    else v = brow ? brow[j] : 1.0;
   } else {
     v = (j - N == i) ? 1.0 : 0.0;
   }
@@ -136,7 +142,125 @@ __global__ void k_pinv_form(const double* __restrict__ G, int Nb, const double* 
   WT32[(size_t)j * Nb + i] = float(w);
 }
 
+// y = M x (trans = 0, one warp per row) or M^T x (trans = 1, one thread per
+// entry); M is n x n with row stride ld.
+__global__ void k_mv(const double* __restrict__ M, int ld, int n, int trans,
+                     const double* __restrict__ x, double* __restrict__ y) {
+  if (trans) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0;
+    for (int j = 0; j < n; ++j) s += M[(size_t)j * ld + i] * x[j];
+    y[i] = s;
+    return;
+  }
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, l = threadIdx.x & 31;
+  if (row >= n) return;
+  double s = 0;
+  for (int j = l; j < n; j += 32) s += M[(size_t)row * ld + j] * x[j];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (l == 0) y[row] = s;
+}
+
+// x /= |x| (one block)
+__global__ void k_normalize(double* __restrict__ x, int n) {
+  __shared__ double red[32];
+  __shared__ double nrm;
+  double s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i] * x[i];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    nrm = sqrt(t);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] /= nrm;
+}
+
+// W = leading Nb x Nb block of the bordered inverse, plus W^T and float copies
+__global__ void k_pinv_copy(const double* __restrict__ G, int Nb, double* __restrict__ Wm,
+                            double* __restrict__ WT, float* __restrict__ W32,
+                            float* __restrict__ WT32) {
+  int N = Nb + 1, Wd = 2 * N;
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y;
+  if (j >= Nb) return;
+  double w = G[(size_t)i * Wd + N + j];
+  Wm[(size_t)i * Nb + j] = w;
+  WT[(size_t)j * Nb + i] = w;
+  W32[(size_t)i * Nb + j] = float(w);
+  WT32[(size_t)j * Nb + i] = float(w);
+}
+
+static void gj_run(bem_ctx* c, double* G, int N, double* col) {
+  for (int k = 0; k < N; ++k) {
+    k_gj_pivot<<<1, 1024, 0, S(c)>>>(G, N, k, col, c->d_status);
+    dim3 grid((2 * N + 255) / 256, N);
+    k_gj_elim<<<grid, 256, 0, S(c)>>>(G, N, k, col);
+    c->launches += 2;
+  }
+}
+
+// Pseudo-inverse that drops the smallest singular value (Sec. 3.1.3) of a
+// matrix that is only nearly singular (galerkin_mode 1): with (s, u, v) the
+// smallest singular triple of A, the bordered system [[A, u],[v^T, 0]] is
+// well conditioned and [x; m] = its inverse times [f; 0] gives A x + m u = f,
+// v.x = 0, i.e. x = sum over the other singular triples of v_k (u_k.f)/s_k.
+// v comes from inverse iteration with A^-1 A^-T (Gauss-Jordan inverse of A;
+// the gap to the next singular value makes two steps exact to rounding),
+// u = A v / |A v|.
+static int la_pinv_truncated(bem_ctx* c) {
+  int Nb = c->bd.Nb, N = Nb + 1, rc;
+  const size_t gsz = (size_t)N * 2 * N;
+  if ((rc = grow(c, c->lmW, sizeof(double) * (gsz + N + 3 * (size_t)Nb)))) return rc;
+  double* G = (double*)c->lmW.p;
+  double* col = G + gsz;
+  double* v = col + N;
+  double* u = v + Nb;
+  double* t = u + Nb;
+  if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
+  // A^-1
+  size_t tot = (size_t)Nb * 2 * Nb;
+  k_gj_init<<<(tot + 255) / 256, 256, 0, S(c)>>>(c->bd.d_A, Nb, 0, nullptr, nullptr, G);
+  BEM_LAUNCHED(c);
+  gj_run(c, G, Nb, col);
+  const double* Ainv = G + Nb;   // right half, row stride 2 Nb
+  std::vector<double> ones(Nb, 1.0);
+  if ((rc = cuda_check(c, cudaMemcpyAsync(v, ones.data(), sizeof(double) * Nb,
+                                          cudaMemcpyHostToDevice, S(c)), "copy")))
+    return rc;
+  for (int it = 0; it < 3; ++it) {
+    k_mv<<<(Nb + 255) / 256, 256, 0, S(c)>>>(Ainv, 2 * Nb, Nb, 1, v, t);   // t = A^-T v
+    k_mv<<<(Nb + 7) / 8, 256, 0, S(c)>>>(Ainv, 2 * Nb, Nb, 0, t, v);       // v = A^-1 t
+    k_normalize<<<1, 1024, 0, S(c)>>>(v, Nb);
+    c->launches += 3;
+  }
+  k_mv<<<(Nb + 7) / 8, 256, 0, S(c)>>>(c->bd.d_A, Nb, Nb, 0, v, u);
+  k_normalize<<<1, 1024, 0, S(c)>>>(u, Nb);
+  c->launches += 2;
+  // bordered inverse with (u, v)
+  tot = (size_t)N * 2 * N;
+  k_gj_init<<<(tot + 255) / 256, 256, 0, S(c)>>>(c->bd.d_A, Nb, 1, u, v, G);
+  BEM_LAUNCHED(c);
+  gj_run(c, G, N, col);
+  dim3 g2((Nb + 127) / 128, Nb);
+  k_pinv_copy<<<g2, 128, 0, S(c)>>>(G, Nb, c->bd.d_W, c->bd.d_WT, c->bd.d_W32, c->bd.d_WT32);
+  BEM_LAUNCHED(c);
+  if ((rc = cuda_check(c, cudaGetLastError(), "pinv"))) return rc;
+  int st = 0;
+  if ((rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                                          S(c)), "status")) ||
+      (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "pinv sync")))
+    return rc;
+  if (st) return fail(c, BEM_ESINGULAR, "boundary matrix: zero pivot in Gauss-Jordan");
+  return BEM_OK;
+}
+
 int la_pinv(bem_ctx* c) {
+  if (c->opts.galerkin_mode == 1) return la_pinv_truncated(c);
   int Nb = c->bd.Nb, N = Nb + 1;
   size_t gsz = (size_t)N * 2 * N * sizeof(double);
   int rc;
@@ -147,7 +271,7 @@ int la_pinv(bem_ctx* c) {
   double* vv = tv + Nb;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
   size_t tot = (size_t)N * 2 * N;
-  k_gj_init<<<(tot + 255) / 256, 256, 0, S(c)>>>(c->bd.d_A, Nb, G);
+  k_gj_init<<<(tot + 255) / 256, 256, 0, S(c)>>>(c->bd.d_A, Nb, 1, nullptr, nullptr, G);
   BEM_LAUNCHED(c);
   for (int k = 0; k < N; ++k) {
     k_gj_pivot<<<1, 1024, 0, S(c)>>>(G, N, k, col, c->d_status);

@@ -50,6 +50,7 @@ def test_default_opts(lib):
     assert o.precision == bg.BEM_FP64 and o.eps_d == 1e-2 and o.eps_c == 1e-2
     assert o.segs_per_side == 256 and o.near_factor == 0.5
     assert o.jtj_mode == bg.BEM_JTJ_FP64 and o.lm_solver == bg.BEM_LM_AUTO
+    assert o.galerkin_mode == 0
     assert bg.bem_default_opts(None) == bg.BEM_EINVAL
 
 
@@ -60,7 +61,7 @@ def test_struct_layout_matches_header():
     import paper_2602_05492_gb300 as bg
     src = ('#include "bemgb.h"\n#include <stdio.h>\n#include <stddef.h>\n'
            'int main(void){printf("%zu %zu %zu\\n", sizeof(bem_opts), sizeof(lm_result),'
-           ' offsetof(bem_opts, lm_solver));return 0;}\n')
+           ' offsetof(bem_opts, galerkin_mode));return 0;}\n')
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
         open(c, "w").write(src)
@@ -69,4 +70,4 @@ def test_struct_layout_matches_header():
         a, b, off = map(int, subprocess.run([exe], capture_output=True, text=True,
                                             check=True).stdout.split())
     assert a == ctypes.sizeof(bg.bem_opts) and b == ctypes.sizeof(bg.lm_result)
-    assert off == bg.bem_opts.lm_solver.offset
+    assert off == bg.bem_opts.galerkin_mode.offset

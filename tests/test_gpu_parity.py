@@ -173,6 +173,33 @@ def test_ragged_sizes_fp64(cfg1, n):
     assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-10
 
 
+def test_galerkin_3x3_fp64(cfg1):
+    """galerkin_mode 1 (the paper's 3 x 3 Gauss rule): the boundary solution
+    and the colours against the oracle's mode-1 matrix and SVD truncation."""
+    bg = _bg()
+    sc, xy, target, mean, o = cfg1
+    o1 = oracle.Oracle.from_scene(sc, mean_color=mean, galerkin_mode=1)
+    m = _ctx(sc, mean, bg.BEM_FP64, galerkin_mode=1)
+    ub = m.boundary_values()
+    want_ub = o1.boundary_values(sc.theta_init)
+    assert _rel(ub, want_ub) < 1e-10
+    sub = xy[::4]
+    u = m.eval(_t(sub, torch.float64)).cpu().numpy()
+    assert _rel(u, o1.eval(sc.theta_init, sub)) < 1e-10
+    # and the modes differ by the quadrature error only
+    assert _rel(u, o.eval(sc.theta_init, sub)) < 1e-3
+
+
+def test_galerkin_3x3_mixed(cfg1):
+    bg = _bg()
+    sc, xy, target, mean, o = cfg1
+    o1 = oracle.Oracle.from_scene(sc, mean_color=mean, galerkin_mode=1)
+    m = _ctx(sc, mean, bg.BEM_MIXED, galerkin_mode=1)
+    u = m.eval(_t(xy, torch.float32)).double().cpu().numpy()
+    rmse = np.sqrt(np.mean((u - o1.eval(sc.theta_init, xy)) ** 2))
+    assert rmse < 1e-4, rmse
+
+
 # ---- mixed path -----------------------------------------------------------------
 
 def test_eval_mixed_cfg1_full(cfg1):
