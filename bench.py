@@ -348,6 +348,20 @@ def run_ours(args, rank, world, dist):
     pairs = n * (P + Nb)
     pairs_per_s = 2 * pairs / ((fwd_ms + adj_ms) / 1e3)
 
+    # ---- output rendering: the colour field on a 1024 x 1024 pixel grid
+    img = torch.empty((1024, 1024, 3), dtype=torch.float32, device=dev)
+    m.render(1024, 1024, img)
+    e0r, e1r = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0r.record(stream)
+    for _ in range(3):
+        m.render(1024, 1024, img)
+    e1r.record(stream)
+    torch.cuda.synchronize()
+    rms = e0r.elapsed_time(e1r) / 3
+    render = {"pixels": 1024 * 1024, "ms": rms, "mpix_per_s": 1024 * 1024 / rms / 1e3}
+    del img
+
     # ---- FP64 GPU path: one LM iteration (after one warm-up iteration); at
     # config 4 its cost a + b S is fitted from steps on two sample subsets
     fp64 = None
@@ -437,7 +451,8 @@ def run_ours(args, rank, world, dist):
                        "wall_s_timed_region": t_wall},
             "pairs_per_s": {"value": pairs_per_s, "unit": "sample x panel evals/s (fwd+adjoint)",
                             "fwd_ms": fwd_ms, "adj_ms": adj_ms, "pairs_per_pass": pairs},
-            "fp64_gpu": fp64, "accuracy": accuracy, "kernels": kernels,
+            "fp64_gpu": fp64, "accuracy": accuracy, "render_1024x1024": render,
+            "kernels": kernels,
             "roofline": roof, "rooflines_other": roofs[1:], "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)

@@ -141,6 +141,20 @@ int bem_set_mean_color(bem_ctx *ctx, const double *mean_color);
  * paragraph) into host double[3].  target: device [n][3] sample type. */
 int bem_sample_mean(bem_ctx *ctx, int64_t n, const void *target, double *mean_out, void *stream);
 
+/* The image of the current theta on a width x height pixel grid: the colour
+ * of Eq. (bie) at every pixel centre ((i + 1/2)/width, (j + 1/2)/height),
+ * row-major with row j = y index; no rasterisation of the curves.
+ *   rgb_out: device [height][width][3] (sample type).  Errors: BEM_EINVAL. */
+int bem_render(bem_ctx *ctx, int width, int height, void *rgb_out, void *stream);
+
+/* Two-sided colours of every panel (Sec. 3.1.3, recovering double-sided
+ * colours): the colour u at the panel midpoint is the average c_avg across
+ * the handle, and the two sides are c_avg +- w_d/2.
+ *   out: host double [n_panels][2][3]: [p][0] = c_avg + w_d/2, the side to
+ *   the left of a -> b (the one the right normal points away from);
+ *   [p][1] = c_avg - w_d/2.  Synchronises `stream`. */
+int bem_handle_colors(bem_ctx *ctx, double *out, void *stream);
+
 /* Colours u(x) = mean + sum_j phi_j(x)/(2 pi) u_b,j + f(x; theta) at n
  * interior sample points (Eq. (bie) with alpha = 1, Sec. 3.1.3 last
  * paragraph; f from Eq. (handleterm) regularised as in Sec. 3.1.3).

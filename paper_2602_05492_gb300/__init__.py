@@ -87,6 +87,8 @@ def _load():
         "bem_batch_lm": (ci, [vp, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(vp), ci,
                               dp, ctypes.POINTER(lm_result), vp]),
         "bem_batch_tile_shape": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]),
+        "bem_render": (ci, [vp, ci, ci, vp, vp]),
+        "bem_handle_colors": (ci, [vp, dp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -102,7 +104,7 @@ EXPORTED = [
     "bem_loss", "bem_vjp", "bem_jtj", "lm_step", "bem_sizes", "bem_boundary_values",
     "bem_launch_count", "bem_profile_enable", "bem_profile_read", "bem_gemm_bf16",
     "bem_fastmath_eval", "bem_vjp_noalloc", "bem_batch_create", "bem_batch_destroy",
-    "bem_batch_lm", "bem_batch_tile_shape",
+    "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -123,6 +125,12 @@ def _stream(stream=None):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _lib_sizes(m):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    m._check(_lib.bem_sizes(m.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 class BEM:
@@ -265,6 +273,22 @@ class BEM:
                                  ctypes.byref(r), _stream(stream)))
         return dict(loss_before=r.loss_before, loss_after=r.loss_after, accepted=bool(r.accepted),
                     best_trial=r.best_trial, lambda_next=r.lambda_next, grad_norm=r.grad_norm)
+
+    def render(self, width, height, out=None, stream=None):
+        """Colours at the pixel centres of a width x height grid, [height, width, 3]."""
+        import torch
+        if out is None:
+            out = torch.empty((height, width, 3), dtype=self.dtype, device=f"cuda:{self.device}")
+        self._samples(out)
+        self._check(_lib.bem_render(self.h, width, height, _ptr(out), _stream(stream)))
+        return out
+
+    def handle_colors(self, stream=None) -> np.ndarray:
+        """[n_panels, 2, 3]: colour on the left / right of each panel (c_avg +- w_d/2)."""
+        P = _lib_sizes(self)[1]
+        out = np.empty((P, 2, 3))
+        self._check(_lib.bem_handle_colors(self.h, _dp(out), _stream(stream)))
+        return out
 
     def boundary_values(self, stream=None) -> np.ndarray:
         out = np.empty((self.Nb, 3))

@@ -1,4 +1,5 @@
 // C ABI of libbemgb: context lifecycle and the hot-path entry points.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -170,6 +171,40 @@ __global__ void k_fastmath(int which, int64_t n, const float* __restrict__ a,
   }
 }
 
+// pixel centres ((i + 1/2)/W, (j + 1/2)/H) of pixels p0 .. p0 + cnt - 1 (row-major)
+template <typename T>
+__global__ void k_pixel_centres(int W, int H, int64_t p0, int64_t cnt, T* __restrict__ xy) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  const int64_t p = p0 + k;
+  const int i = (int)(p % W), j = (int)(p / W);
+  xy[2 * k] = T((i + 0.5) / W);
+  xy[2 * k + 1] = T((j + 0.5) / H);
+}
+
+// panel midpoints a + (L/2) tau
+template <typename T>
+__global__ void k_panel_mids(const Panel<double>* __restrict__ pan, int P, T* __restrict__ xy) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const Panel<double> q = pan[p];
+  xy[2 * p] = T(q.ax + 0.5 * q.L * q.tx);
+  xy[2 * p + 1] = T(q.ay + 0.5 * q.L * q.ty);
+}
+
+// out[p][0] = u(mid) + w_d/2 (left of a->b), out[p][1] = u(mid) - w_d/2 (right)
+template <typename T>
+__global__ void k_two_sided(const T* __restrict__ u, const Panel<double>* __restrict__ pan, int P,
+                            double* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  for (int ch = 0; ch < 3; ++ch) {
+    const double avg = double(u[3 * p + ch]), h = 0.5 * pan[p].wd[ch];
+    out[6 * p + ch] = avg + h;
+    out[6 * p + 3 + ch] = avg - h;
+  }
+}
+
 }  // namespace bem
 
 using namespace bem;
@@ -251,7 +286,7 @@ void bem_destroy(bem_ctx* c) {
   prof_resolve(c);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   DevBuf* bufs[] = {&c->part, &c->part2, &c->loss, &c->gpart, &c->jrow, &c->phi, &c->Hc, &c->Mc,
-                    &c->Dfc, &c->Fg, &c->lmK, &c->lmL, &c->lmLt, &c->lmW, &c->H, &c->g,
+                    &c->Dfc, &c->Fg, &c->lmK, &c->lmL, &c->lmLt, &c->lmW, &c->H, &c->g, &c->rend,
                     &c->tcJ, &c->tcPart, &c->tcMt, &c->nearP, &c->nearS, &c->nearF, &c->gwork};
   for (DevBuf* b : bufs) free_buf(*b);
   delete c;
@@ -360,6 +395,58 @@ int bem_eval(bem_ctx* c, int64_t n, const void* xy, void* rgb, void* stream) {
   c->cur = (cudaStream_t)stream;
   if ((rc = refresh(c, c->d_theta))) return rc;
   return field_eval(c, n, xy, rgb, nullptr, nullptr, false);
+}
+
+int bem_render(bem_ctx* c, int width, int height, void* rgb, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (width < 1 || height < 1 || !rgb) return fail(c, BEM_EINVAL, "bem_render: bad arguments");
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  if ((rc = refresh(c, c->d_theta))) return rc;
+  const bool f64 = c->opts.precision == BEM_FP64;
+  const size_t es = f64 ? 8 : 4;
+  const int64_t total = (int64_t)width * height, chunk = std::min<int64_t>(total, 1 << 22);
+  if ((rc = grow(c, c->rend, 2 * es * (size_t)chunk))) return rc;
+  for (int64_t p0 = 0; p0 < total; p0 += chunk) {
+    const int64_t cnt = std::min(chunk, total - p0);
+    if (f64) k_pixel_centres<double><<<(unsigned)((cnt + 255) / 256), 256, 0, S(c)>>>(width, height, p0, cnt, (double*)c->rend.p);
+    else k_pixel_centres<float><<<(unsigned)((cnt + 255) / 256), 256, 0, S(c)>>>(width, height, p0, cnt, (float*)c->rend.p);
+    BEM_LAUNCHED(c);
+    if ((rc = field_eval(c, cnt, c->rend.p, (char*)rgb + 3 * es * (size_t)p0, nullptr, nullptr, false)))
+      return rc;
+  }
+  return cuda_check(c, cudaGetLastError(), "bem_render");
+}
+
+int bem_handle_colors(bem_ctx* c, double* out, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (!out) return fail(c, BEM_EINVAL, "bem_handle_colors: out is NULL");
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  if ((rc = refresh(c, c->d_theta))) return rc;
+  const bool f64 = c->opts.precision == BEM_FP64;
+  const size_t es = f64 ? 8 : 4;
+  const int P = c->sc.P;
+  // scratch: midpoints [P][2], colours [P][3] (sample type), result [P][2][3] double
+  const size_t xyb = ((2 * es * (size_t)P + 255) / 256) * 256;
+  const size_t ub = ((3 * es * (size_t)P + 255) / 256) * 256;
+  if ((rc = grow(c, c->rend, xyb + ub + sizeof(double) * 6 * (size_t)P))) return rc;
+  void* xy = c->rend.p;
+  void* u = (char*)c->rend.p + xyb;
+  double* o = (double*)((char*)u + ub);
+  if (f64) k_panel_mids<double><<<(P + 127) / 128, 128, 0, S(c)>>>(c->d_pan64, P, (double*)xy);
+  else k_panel_mids<float><<<(P + 127) / 128, 128, 0, S(c)>>>(c->d_pan64, P, (float*)xy);
+  BEM_LAUNCHED(c);
+  if ((rc = field_eval(c, P, xy, u, nullptr, nullptr, false))) return rc;
+  if (f64) k_two_sided<double><<<(P + 127) / 128, 128, 0, S(c)>>>((const double*)u, c->d_pan64, P, o);
+  else k_two_sided<float><<<(P + 127) / 128, 128, 0, S(c)>>>((const float*)u, c->d_pan64, P, o);
+  BEM_LAUNCHED(c);
+  if ((rc = cuda_check(c, cudaMemcpyAsync(out, o, sizeof(double) * 6 * (size_t)P,
+                                          cudaMemcpyDeviceToHost, S(c)), "colors")))
+    return rc;
+  return cuda_check(c, cudaStreamSynchronize(S(c)), "sync");
 }
 
 int bem_loss(bem_ctx* c, int64_t n, const void* xy, const void* target, void* resid, double* loss,

@@ -86,7 +86,7 @@ struct bem_ctx {
 
   // growable scratch
   bem::DevBuf part, part2, loss, gpart, jrow, phi, Hc, Mc, Dfc, Fg, lmK, lmL, lmLt, lmW, H, g,
-      tcJ, tcPart, tcMt, nearP, nearS, nearF, gwork;
+      tcJ, tcPart, tcMt, nearP, nearS, nearF, gwork, rend;
   bool pbins_valid = false;        // panel -> cell bins match the current panels
   // When set, the Gauss-Newton chunk buffers (jrow, tcJ, tcPart, gwork) are
   // taken from this context: a batch of scenes processed one after another

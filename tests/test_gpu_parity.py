@@ -200,6 +200,43 @@ def test_galerkin_3x3_mixed(cfg1):
     assert rmse < 1e-4, rmse
 
 
+def _pixel_centres(W, H):
+    j, i = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    return np.stack([(i.ravel() + 0.5) / W, (j.ravel() + 0.5) / H], 1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_render(cfg1, prec):
+    """The image on a 40 x 30 pixel grid against the oracle at the pixel centres."""
+    bg = _bg()
+    sc, xy, target, mean, o = cfg1
+    m = _ctx(sc, mean, bg.BEM_FP64 if prec == "fp64" else bg.BEM_MIXED)
+    img = m.render(40, 30).double().cpu().numpy()
+    assert img.shape == (30, 40, 3)
+    want = o.eval(sc.theta_init, _pixel_centres(40, 30)).reshape(30, 40, 3)
+    if prec == "fp64":
+        assert _rel(img, want) < 1e-10
+    else:
+        assert np.sqrt(np.mean((img - want) ** 2)) < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_handle_colors(cfg1, prec):
+    """Two-sided colours: the colour at each panel midpoint +- w_d/2, and the
+    jump between the sides is w_d exactly."""
+    bg = _bg()
+    sc, xy, target, mean, o = cfg1
+    m = _ctx(sc, mean, bg.BEM_FP64 if prec == "fp64" else bg.BEM_MIXED)
+    hc = m.handle_colors()
+    ab, wd, _ = o.panels(sc.theta_init)
+    mid = 0.5 * (ab[:, 0:2] + ab[:, 2:4])
+    avg = o.eval(sc.theta_init, mid)
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    assert np.abs(hc[:, 0] - (avg + 0.5 * wd)).max() < tol * max(1.0, np.abs(avg).max())
+    assert np.abs(hc[:, 1] - (avg - 0.5 * wd)).max() < tol * max(1.0, np.abs(avg).max())
+    assert np.abs((hc[:, 0] - hc[:, 1]) - wd).max() < 1e-12
+
+
 # ---- mixed path -----------------------------------------------------------------
 
 def test_eval_mixed_cfg1_full(cfg1):
