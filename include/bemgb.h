@@ -202,6 +202,16 @@ int bem_jtj(bem_ctx *ctx, int64_t n, const void *xy, double *H_out, void *stream
 int lm_step(bem_ctx *ctx, int64_t n, const void *xy, const void *target,
             int n_trials, const double *lambdas, lm_result *out, void *stream);
 
+/* lm_step with a separate Hessian sample set (Sec. 4.3, Monte Carlo
+ * integration: Eq. (losshessian) with M_H points, Eq. (lossjacobian) and the
+ * trial losses with M_J points): H = (1/n_h) sum over xy_h of J^T J; g and
+ * the losses from the n points (xy, target), g by the adjoint.  Passing
+ * fewer Hessian points cuts the cost of J^T J.
+ *   xy_h: device [n_h][2] (sample type), n_h > 0.  Otherwise as lm_step. */
+int lm_step_split(bem_ctx *ctx, int64_t n, const void *xy, const void *target, int64_t n_h,
+                  const void *xy_h, int n_trials, const double *lambdas, lm_result *out,
+                  void *stream);
+
 /* D[M][N] = A[M][K] B[N][K]^T on the tensor cores (tcgen05, fp32
  * accumulate): the contraction behind bem_jtj in BEM_MIXED contexts with
  * BEM_JTJ_BF16, exposed for validation.  A, B: device bf16, row-major, row

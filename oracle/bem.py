@@ -441,9 +441,23 @@ class Oracle:
         delta[act] = da
         return delta
 
-    def lm_step(self, theta, xy, target, lam):
-        """One LM iteration (Eq. optimstep) with the paper's two-stage projection."""
+    def hessian(self, theta, xy, chunk: int = 512) -> np.ndarray:
+        """H = (1/M_H) sum over the M_H points of J^T J (Eq. losshessian, p = 1)."""
+        Mb = self.boundary_jac(theta)
+        nt = self.geo.n_theta
+        H = np.zeros((nt, nt))
+        for s0 in range(0, xy.shape[0], chunk):
+            Jf = self.jac(theta, xy[s0:s0 + chunk], Mb).reshape(-1, nt)
+            H += Jf.T @ Jf
+        return H / xy.shape[0]
+
+    def lm_step(self, theta, xy, target, lam, xy_h=None):
+        """One LM iteration (Eq. optimstep) with the paper's two-stage projection.
+        With xy_h, the Hessian integral uses those M_H points and the gradient
+        and the losses the M_J points xy (Sec. 4.3, Monte Carlo integration)."""
         L0, g, H = self.gauss_newton(theta, xy, target)
+        if xy_h is not None:
+            H = self.hessian(theta, xy_h)
         delta = self.solve_step(theta, H, g, lam)
         lam = self.last_lambda
         th_new = project_compat(self.geo, theta + delta)

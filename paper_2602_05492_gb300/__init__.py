@@ -73,6 +73,7 @@ def _load():
         "bem_vjp": (ci, [vp, i64, vp, vp, vp, vp]),
         "bem_jtj": (ci, [vp, i64, vp, vp, vp]),
         "lm_step": (ci, [vp, i64, vp, vp, ci, dp, ctypes.POINTER(lm_result), vp]),
+        "lm_step_split": (ci, [vp, i64, vp, vp, i64, vp, ci, dp, ctypes.POINTER(lm_result), vp]),
         "bem_sizes": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]),
         "bem_boundary_values": (ci, [vp, dp, vp]),
         "bem_launch_count": (i64, [vp]),
@@ -104,7 +105,7 @@ EXPORTED = [
     "bem_loss", "bem_vjp", "bem_jtj", "lm_step", "bem_sizes", "bem_boundary_values",
     "bem_launch_count", "bem_profile_enable", "bem_profile_read", "bem_gemm_bf16",
     "bem_fastmath_eval", "bem_vjp_noalloc", "bem_batch_create", "bem_batch_destroy",
-    "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors",
+    "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors", "lm_step_split",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -289,6 +290,17 @@ class BEM:
         out = np.empty((P, 2, 3))
         self._check(_lib.bem_handle_colors(self.h, _dp(out), _stream(stream)))
         return out
+
+    def lm_step_split(self, xy, target, xy_h, lambdas, stream=None) -> dict:
+        """LM iteration with H from the points xy_h and g, losses from (xy, target)."""
+        self._samples(xy, target, xy_h)
+        lam = np.ascontiguousarray(np.atleast_1d(lambdas), np.float64)
+        r = lm_result()
+        self._check(_lib.lm_step_split(self.h, xy.shape[0], _ptr(xy), _ptr(target), xy_h.shape[0],
+                                       _ptr(xy_h), len(lam), _dp(lam), ctypes.byref(r),
+                                       _stream(stream)))
+        return dict(loss_before=r.loss_before, loss_after=r.loss_after, accepted=bool(r.accepted),
+                    best_trial=r.best_trial, lambda_next=r.lambda_next, grad_norm=r.grad_norm)
 
     def boundary_values(self, stream=None) -> np.ndarray:
         out = np.empty((self.Nb, 3))

@@ -491,10 +491,18 @@ int bem_jtj(bem_ctx* c, int64_t n, const void* xy, double* H, void* stream) {
   return BEM_OK;
 }
 
-int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_trials,
-            const double* lambdas, lm_result* out, void* stream) {
+}  // extern "C"
+
+namespace bem {
+
+// One LM iteration; with xy_h the Hessian integral uses those n_h points and
+// the gradient comes from the adjoint over (xy, target).
+static int lm_step_impl(bem_ctx* c, int64_t n, const void* xy, const void* target, int64_t n_h,
+                        const void* xy_h, int n_trials, const double* lambdas, lm_result* out,
+                        void* stream) {
   if (!c) return BEM_EINVAL;
-  if (n <= 0 || !xy || !target || n_trials < 1 || n_trials > 64 || !lambdas || !out)
+  if (n <= 0 || !xy || !target || n_trials < 1 || n_trials > 64 || !lambdas || !out ||
+      (xy_h && n_h <= 0))
     return fail(c, BEM_EINVAL, "lm_step: bad arguments");
   for (int t = 0; t < n_trials; ++t)
     if (!(lambdas[t] >= 0) || !std::isfinite(lambdas[t]))
@@ -520,7 +528,7 @@ int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_tri
   double s0 = 0;
   if ((rc = cuda_check(c, cudaMemcpyAsync(&s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
     return rc;
-  if (jtj_gives_gradient(c)) {
+  if (!xy_h && jtj_gives_gradient(c)) {
     // g = (1/n) J^T r from the J rows that also build H (Eq. (lossjacobian))
     if ((rc = jtj_build(c, n, xy, (double*)c->H.p, resid, g))) return rc;
     k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0, c->d_scal + 1);
@@ -529,7 +537,7 @@ int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_tri
     if ((rc = adj_vjp(c, n, xy, resid, g))) return rc;
     k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0 / double(n), c->d_scal + 1);
     BEM_LAUNCHED(c);
-    if ((rc = jtj_build(c, n, xy, (double*)c->H.p))) return rc;
+    if ((rc = jtj_build(c, xy_h ? n_h : n, xy_h ? xy_h : xy, (double*)c->H.p))) return rc;
   }
   double gn2 = 0;
   if ((rc = cuda_check(c, cudaMemcpyAsync(&gn2, c->d_scal + 1, 8, cudaMemcpyDeviceToHost, S(c)), "norm")) ||
@@ -591,6 +599,22 @@ int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_tri
   }
   // panels and boundary solution are rebuilt from theta by the next call
   return cuda_check(c, cudaStreamSynchronize(S(c)), "sync");
+}
+
+}  // namespace bem
+
+extern "C" {
+
+int lm_step(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_trials,
+            const double* lambdas, lm_result* out, void* stream) {
+  return lm_step_impl(c, n, xy, target, 0, nullptr, n_trials, lambdas, out, stream);
+}
+
+int lm_step_split(bem_ctx* c, int64_t n, const void* xy, const void* target, int64_t n_h,
+                  const void* xy_h, int n_trials, const double* lambdas, lm_result* out,
+                  void* stream) {
+  if (c && !xy_h) return fail(c, BEM_EINVAL, "lm_step_split: xy_h is NULL");
+  return lm_step_impl(c, n, xy, target, n_h, xy_h, n_trials, lambdas, out, stream);
 }
 
 int bem_gemm_bf16(bem_ctx* c, int M, int N, int K, const void* A, int lda, const void* B, int ldb,

@@ -237,6 +237,26 @@ def test_handle_colors(cfg1, prec):
     assert np.abs((hc[:, 0] - hc[:, 1]) - wd).max() < 1e-12
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_lm_step_split_hessian(cfg1, prec):
+    """H from a separate (smaller) point set, g and losses from the samples,
+    against the oracle's step with the same two sets."""
+    bg = _bg()
+    sc, xy, target, mean, o = cfg1
+    sub, tsub, hsub = xy[::16], target[::16], xy[5::64]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    m = _ctx(sc, mean, bg.BEM_FP64 if prec == "fp64" else bg.BEM_MIXED)
+    res = m.lm_step_split(_t(sub, dt), _t(tsub, dt), _t(hsub, dt), [1e-3])
+    want = o.lm_step(sc.theta_init, sub, tsub, 1e-3, xy_h=hsub)
+    tol = 1e-9 if prec == "fp64" else 2e-2
+    assert res["loss_before"] == pytest.approx(want["loss_before"], rel=1e-11 if prec == "fp64" else 1e-5)
+    assert res["grad_norm"] == pytest.approx(np.linalg.norm(want["g"]), rel=1e-9 if prec == "fp64" else 1e-4)
+    assert res["accepted"] == want["accepted"]
+    assert res["loss_after"] == pytest.approx(want["loss_after"], rel=tol)
+    if prec == "fp64":
+        assert _rel(m.get_params(), want["theta"]) < 1e-9
+
+
 # ---- mixed path -----------------------------------------------------------------
 
 def test_eval_mixed_cfg1_full(cfg1):

@@ -133,3 +133,21 @@ def test_noiseless_recovery():
         res = o.lm_step(th, xy, target, lam)
         th, lam = res["theta"], res["lambda_next"]
     assert o.loss(th, xy, target) < 1e-6 * L0
+
+
+def test_split_hessian_sets():
+    """lm_step with a separate Hessian set: the same set gives the plain step,
+    and H of the union of two sets is the sample-weighted mean of their Hs."""
+    import gen
+    import oracle
+    sc = gen.make_scene(1)
+    xy = gen.make_samples(sc.W, sc.spp, sc.seed)[::64]
+    o = oracle.Oracle.from_scene(sc, segs_per_side=16)
+    t = o.eval(sc.theta_true, xy)
+    a = o.lm_step(sc.theta_init, xy, t, 1e-3)
+    b = o.lm_step(sc.theta_init, xy, t, 1e-3, xy_h=xy)
+    assert np.array_equal(a["theta"], b["theta"]) and a["loss_after"] == b["loss_after"]
+    h1, h2 = xy[:200], xy[200:]
+    H = o.hessian(sc.theta_init, xy)
+    Hm = (200 * o.hessian(sc.theta_init, h1) + (len(xy) - 200) * o.hessian(sc.theta_init, h2)) / len(xy)
+    assert np.abs(H - Hm).max() <= 1e-12 * np.abs(H).max()
