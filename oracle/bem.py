@@ -40,7 +40,8 @@ import scipy.sparse
 from . import lib as _lib_loader
 
 __all__ = [
-    "GAUSS_NODES", "GAUSS_WEIGHTS", "square_boundary", "gauss_points", "bernstein",
+    "GAUSS_NODES", "GAUSS_WEIGHTS", "square_boundary", "polygon_boundary", "gauss_points",
+    "bernstein",
     "Geometry", "panelize", "compat_vectors", "project_compat", "pair_terms",
     "handle_field", "angles", "boundary_field", "assemble_A", "pinv_svd", "Oracle",
     "set_threads", "num_threads",
@@ -82,6 +83,20 @@ def square_boundary(M: int) -> np.ndarray:
         b = corners[s] + dirs[s] * ((m + 1) / M)[:, None]
         seg[s * M:(s + 1) * M, 0:2] = a
         seg[s * M:(s + 1) * M, 2:4] = b
+    return seg
+
+
+def polygon_boundary(verts, M: int) -> np.ndarray:
+    """Segments of a closed counter-clockwise polygon (a subdomain boundary,
+    Sec. 4.2): each edge v_e -> v_{e+1} cut into M equal segments, [V M, 4]."""
+    v = np.asarray(verts, np.float64).reshape(-1, 2)
+    V = v.shape[0]
+    seg = np.empty((V * M, 4))
+    m = np.arange(M)
+    for e in range(V):
+        a, b = v[e], v[(e + 1) % V]
+        seg[e * M:(e + 1) * M, 0:2] = a + (b - a) * (m / M)[:, None]
+        seg[e * M:(e + 1) * M, 2:4] = a + (b - a) * ((m + 1) / M)[:, None]
     return seg
 
 
@@ -290,12 +305,15 @@ class Oracle:
 
     def __init__(self, n_curves, panels_per_curve, closed, mean_color,
                  segs_per_side: int = 256, eps_d: float = 1e-2, eps_c: float = 1e-2,
-                 galerkin_mode: int = 0):
+                 galerkin_mode: int = 0, polygon=None):
         self.geo = Geometry.build(n_curves, panels_per_curve, closed)
         self.mean = np.asarray(mean_color, np.float64).reshape(3)
         self.eps_d = float(eps_d)
         self.eps_c = float(eps_c)
-        self.seg = square_boundary(segs_per_side)
+        # the unit square, or a counter-clockwise polygon with segs_per_side
+        # segments per edge (one subdomain)
+        self.seg = (square_boundary(segs_per_side) if polygon is None
+                    else polygon_boundary(polygon, segs_per_side))
         self.Nb = self.seg.shape[0]
         self.ell = np.hypot(self.seg[:, 2] - self.seg[:, 0], self.seg[:, 3] - self.seg[:, 1])
         self.gp = gauss_points(self.seg)                 # [Nb, 3, 2]

@@ -228,3 +228,51 @@ def test_galerkin_3x3_structure():
     # Sec. 3.1.3 remains well defined)
     s = np.linalg.svd(A1, compute_uv=False)
     assert s[-1] < 1e-3 * s[-2]
+
+
+# ---- polygon subdomains -----------------------------------------------------------
+
+L_SHAPE = [(0.0, 0.0), (1.0, 0.0), (1.0, 0.5), (0.5, 0.5), (0.5, 1.0), (0.0, 1.0)]
+
+
+def test_polygon_boundary_identities():
+    """On a non-convex (L-shaped) polygon: the square's segmentation is the
+    4-vertex case, the angles of all segments sum to 2 pi inside, 0 outside,
+    and the exact-inner Galerkin rows sum to zero."""
+    from oracle.bem import polygon_boundary, square_boundary
+    sq = polygon_boundary([(0, 0), (1, 0), (1, 1), (0, 1)], 8)
+    assert np.array_equal(sq, square_boundary(8))
+    seg = polygon_boundary(L_SHAPE, 8)
+    inside = np.array([[0.25, 0.25], [0.75, 0.25], [0.25, 0.75], [0.45, 0.45]])
+    outside = np.array([[0.75, 0.75], [0.6, 0.9], [1.2, 0.2]])
+    assert np.allclose(oracle.angles(inside, seg).sum(1), 2 * np.pi, atol=1e-13)
+    assert np.allclose(oracle.angles(outside, seg).sum(1), 0.0, atol=1e-13)
+    A = oracle.assemble_A(seg)
+    assert np.abs(A.sum(1)).max() < 1e-15
+
+
+def test_handle_splitting_l_shape():
+    """A straight handle at y = 1/4 across the L-shaped subdomain with constant
+    w_d and w_c = 0: the Neumann solution is piecewise constant, the top part
+    w_d above the bottom part, and the zero-mean boundary solution fixes the
+    constants by the segment counts on each side: c_bot = -w_d n_top/(n_top +
+    n_bot), c_top = w_d n_bot/(n_top + n_bot)."""
+    mean = np.array([0.3, 0.4, 0.5])
+    wd = np.array([1.0, -0.5, 0.25])
+    pts_bot = np.array([[0.2, 0.1], [0.8, 0.2], [0.5, 0.05]])
+    pts_top = np.array([[0.2, 0.4], [0.8, 0.4], [0.25, 0.9], [0.4, 0.6]])
+    for M in (8, 16, 32):
+        o = oracle.Oracle(1, [64], [0], mean, segs_per_side=M, eps_d=1e-9, eps_c=1e-9,
+                          polygon=L_SHAPE)
+        th = np.zeros(32)
+        for j in range(4):
+            th[j * 8:j * 8 + 2] = (j / 3.0, 0.25)
+            th[j * 8 + 2:j * 8 + 5] = wd
+        # segments below the line: bottom edge M, lower half of the right edge
+        # M/2, lowest quarter of the left edge M/4
+        n_bot = M + M // 2 + M // 4
+        n_top = 6 * M - n_bot
+        c_bot = -wd * n_top / (n_top + n_bot)
+        c_top = wd * n_bot / (n_top + n_bot)
+        assert np.abs(o.eval(th, pts_bot) - (mean + c_bot)).max() < 1e-12
+        assert np.abs(o.eval(th, pts_top) - (mean + c_top)).max() < 1e-12
