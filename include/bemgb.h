@@ -118,6 +118,16 @@ const char *bem_last_error(const bem_ctx *ctx);
 int bem_setup(bem_ctx *ctx, int n_curves, const int32_t *panels_per_curve,
               const uint8_t *closed, const double *theta, const double *mean_color);
 
+/* Replace the image boundary by a closed polygon, one subdomain of the
+ * domain decomposition (Sec. 4.2): n_vertices >= 3 vertices, counter-
+ * clockwise, inside the unit square; each edge is cut into segs_per_edge
+ * equal segments (at most 8192 in all).  Invalidates the factorisation: call
+ * bem_factor next.  Samples of this context must lie inside the polygon; a
+ * multi-domain image is one context per subdomain (stepped together with
+ * bem_batch_lm), each with its own mean colour.
+ *   vertices: host double [n_vertices][2].  Errors: BEM_EINVAL. */
+int bem_set_boundary(bem_ctx *ctx, int n_vertices, const double *vertices, int segs_per_edge);
+
 /* Assemble the Galerkin matrix of the image boundary (Eq. (bie_galerkin),
  * 3-point Gauss outer rule, exact inner integral, zero coincident term) and
  * factor it once in double (Sec. 3.1.3): LU with partial pivoting of the

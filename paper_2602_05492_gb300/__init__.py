@@ -64,6 +64,7 @@ def _load():
         "bem_setup": (ci, [vp, ci, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint8),
                            dp, dp]),
         "bem_factor": (ci, [vp, vp]),
+        "bem_set_boundary": (ci, [vp, ci, dp, ci]),
         "bem_set_params": (ci, [vp, vp, ci, vp]),
         "bem_get_params": (ci, [vp, dp, vp]),
         "bem_set_mean_color": (ci, [vp, dp]),
@@ -106,6 +107,7 @@ EXPORTED = [
     "bem_launch_count", "bem_profile_enable", "bem_profile_read", "bem_gemm_bf16",
     "bem_fastmath_eval", "bem_vjp_noalloc", "bem_batch_create", "bem_batch_destroy",
     "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors", "lm_step_split",
+    "bem_set_boundary",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -301,6 +303,13 @@ class BEM:
                                        _stream(stream)))
         return dict(loss_before=r.loss_before, loss_after=r.loss_after, accepted=bool(r.accepted),
                     best_trial=r.best_trial, lambda_next=r.lambda_next, grad_norm=r.grad_norm)
+
+    def set_boundary(self, vertices, segs_per_edge):
+        """Use a counter-clockwise polygon (one subdomain) as the image boundary;
+        call factor() afterwards."""
+        v = np.ascontiguousarray(np.asarray(vertices, np.float64).reshape(-1, 2))
+        self._check(_lib.bem_set_boundary(self.h, v.shape[0], _dp(v), int(segs_per_edge)))
+        self.Nb = v.shape[0] * int(segs_per_edge)
 
     def boundary_values(self, stream=None) -> np.ndarray:
         out = np.empty((self.Nb, 3))

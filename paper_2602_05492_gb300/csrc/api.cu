@@ -54,6 +54,23 @@ static void free_buf(DevBuf& b) {
 }
 
 static int set_device(bem_ctx* c) { return cuda_check(c, cudaSetDevice(c->device), "cudaSetDevice"); }
+
+// device tables and solutions sized by the number of boundary segments
+static int alloc_boundary(bem_ctx* c) {
+  const size_t Nb = (size_t)c->bd.Nb;
+  int rc;
+  if ((rc = alloc(c, c->bd.d_vert, 2 * (Nb + 1))) || (rc = alloc(c, c->bd.d_vert32, 2 * (Nb + 1))) ||
+      (rc = alloc(c, c->bd.d_gp, 6 * Nb)) || (rc = alloc(c, c->bd.d_gp32, 6 * Nb)) ||
+      (rc = alloc(c, c->bd.d_A, Nb * Nb)) || (rc = alloc(c, c->bd.d_W, Nb * Nb)) ||
+      (rc = alloc(c, c->bd.d_WT, Nb * Nb)) || (rc = alloc(c, c->bd.d_W32, Nb * Nb)) ||
+      (rc = alloc(c, c->bd.d_WT32, Nb * Nb)) || (rc = alloc(c, c->d_ub, 3 * Nb)) ||
+      (rc = alloc(c, c->d_fb, 3 * Nb)) || (rc = alloc(c, c->d_q, 3 * Nb)) ||
+      (rc = alloc(c, c->d_lb, 3 * Nb)))
+    return rc;
+  return BEM_OK;
+}
+
+
 int ctx_set_device(bem_ctx* c) { return set_device(c); }
 
 // panels, compatibility weights and boundary solution of the current theta
@@ -255,15 +272,7 @@ int bem_create(bem_ctx** out, const bem_opts* opts, int device) {
   if ((rc = set_device(c))) { g_create_err = c->err; delete c; return rc; }
   c->bd.M = o.segs_per_side;
   c->bd.Nb = 4 * o.segs_per_side;
-  int Nb = c->bd.Nb;
-  if ((rc = alloc(c, c->bd.d_vert, 2 * (size_t)(Nb + 1))) || (rc = alloc(c, c->bd.d_vert32, 2 * (size_t)(Nb + 1))) ||
-      (rc = alloc(c, c->bd.d_gp, 6 * (size_t)Nb)) || (rc = alloc(c, c->bd.d_gp32, 6 * (size_t)Nb)) ||
-      (rc = alloc(c, c->bd.d_A, (size_t)Nb * Nb)) || (rc = alloc(c, c->bd.d_W, (size_t)Nb * Nb)) ||
-      (rc = alloc(c, c->bd.d_WT, (size_t)Nb * Nb)) || (rc = alloc(c, c->bd.d_W32, (size_t)Nb * Nb)) ||
-      (rc = alloc(c, c->bd.d_WT32, (size_t)Nb * Nb)) || (rc = alloc(c, c->d_ub, 3 * (size_t)Nb)) ||
-      (rc = alloc(c, c->d_fb, 3 * (size_t)Nb)) || (rc = alloc(c, c->d_q, 3 * (size_t)Nb)) ||
-      (rc = alloc(c, c->d_lb, 3 * (size_t)Nb)) || (rc = alloc(c, c->d_scal, 64)) ||
-      (rc = alloc(c, c->d_status, 4))) {
+  if ((rc = alloc_boundary(c)) || (rc = alloc(c, c->d_scal, 64)) || (rc = alloc(c, c->d_status, 4))) {
     g_create_err = c->err;
     bem_destroy(c);
     return rc;
@@ -337,6 +346,33 @@ int bem_setup(bem_ctx* c, int n_curves, const int32_t* ppc, const uint8_t* close
   memcpy(c->mean, mean_color, sizeof(c->mean));
   c->have_scene = true;
   return BEM_OK;
+}
+
+int bem_set_boundary(bem_ctx* c, int n_vertices, const double* vertices, int segs_per_edge) {
+  if (!c) return BEM_EINVAL;
+  if (n_vertices < 3 || !vertices || segs_per_edge < 1)
+    return fail(c, BEM_EINVAL, "bem_set_boundary: bad arguments");
+  const int64_t Nb = (int64_t)n_vertices * segs_per_edge;
+  if (Nb > 8192) return fail(c, BEM_EINVAL, "bem_set_boundary: more than 8192 boundary segments");
+  double area2 = 0;
+  for (int e = 0; e < n_vertices; ++e) {
+    const double ax = vertices[2 * e], ay = vertices[2 * e + 1];
+    const double bx = vertices[2 * ((e + 1) % n_vertices)], by = vertices[2 * ((e + 1) % n_vertices) + 1];
+    if (!(ax >= 0 && ax <= 1 && ay >= 0 && ay <= 1))
+      return fail(c, BEM_EINVAL, "bem_set_boundary: vertices must lie in the unit square");
+    if (ax == bx && ay == by) return fail(c, BEM_EINVAL, "bem_set_boundary: zero-length edge");
+    area2 += ax * by - bx * ay;
+  }
+  if (!(area2 > 0)) return fail(c, BEM_EINVAL, "bem_set_boundary: polygon must be counter-clockwise");
+  int rc;
+  if ((rc = set_device(c))) return rc;
+  c->bd.poly.assign(vertices, vertices + 2 * n_vertices);
+  c->bd.M = segs_per_edge;
+  c->bd.Nb = (int)Nb;
+  c->bd.factored = false;
+  if ((rc = cuda_check(c, cudaDeviceSynchronize(), "sync")) || (rc = alloc_boundary(c)))
+    return rc;
+  return geom_boundary_tables(c);
 }
 
 int bem_factor(bem_ctx* c, void* stream) {

@@ -35,8 +35,9 @@ struct Scene {
 };
 
 struct Boundary {
-  int M = 0;      // segments per side
-  int Nb = 0;     // 4 M
+  int M = 0;      // segments per side (per polygon edge)
+  int Nb = 0;     // M times the number of edges
+  std::vector<double> poly;    // counter-clockwise polygon [V][2]; empty = the unit square
   double* d_vert = nullptr;    // [(Nb+1)][2] CCW vertices, vert[Nb] = vert[0]
   float* d_vert32 = nullptr;
   double* d_gp = nullptr;      // [3 Nb][2] Gauss points

@@ -153,16 +153,21 @@ int geom_compat(bem_ctx* c, double* d_theta, bool project) {
 }
 
 int geom_boundary_tables(bem_ctx* c) {
-  int M = c->bd.M, Nb = 4 * M;
+  // the unit square, or the context's polygon; each edge cut into M equal segments
+  static const double sq[8] = {0, 0, 1, 0, 1, 1, 0, 1};
+  const std::vector<double> poly =
+      c->bd.poly.empty() ? std::vector<double>(sq, sq + 8) : c->bd.poly;
+  const int V = (int)poly.size() / 2, M = c->bd.M, Nb = V * M;
   std::vector<double> v(2 * (Nb + 1)), g(2 * 3 * Nb);
-  const double cx[4] = {0, 1, 1, 0}, cy[4] = {0, 0, 1, 1};
-  const double dx[4] = {1, 0, -1, 0}, dy[4] = {0, 1, 0, -1};
-  for (int s = 0; s < 4; ++s)
+  for (int e = 0; e < V; ++e) {
+    const double ax = poly[2 * e], ay = poly[2 * e + 1];
+    const double bx = poly[2 * ((e + 1) % V)], by = poly[2 * ((e + 1) % V) + 1];
     for (int m = 0; m < M; ++m) {
-      double t = double(m) / M;
-      v[2 * (s * M + m)] = cx[s] + dx[s] * t;
-      v[2 * (s * M + m) + 1] = cy[s] + dy[s] * t;
+      const double t = double(m) / M;
+      v[2 * (e * M + m)] = ax + (bx - ax) * t;
+      v[2 * (e * M + m) + 1] = ay + (by - ay) * t;
     }
+  }
   v[2 * Nb] = v[0];
   v[2 * Nb + 1] = v[1];
   for (int i = 0; i < Nb; ++i)
