@@ -121,18 +121,44 @@ def bernstein(t) -> np.ndarray:
 
 @dataclasses.dataclass
 class Geometry:
-    """Discretisation of a set of Bezier curves into straight panels."""
+    """Discretisation of the handles into straight panels.
+
+    Two parametrisations share one layout: colour owners of pp position
+    parameters followed by w_d (RGB) and w_c (RGB), stride pp + 6.
+      Bezier curves (pp = 2): 4 control handles per curve (x, y, w_d, w_c)
+      segments (pp = 4):      the paper's handles, endpoints a, b and jumps
+                              constant over the handle (Sec. 4.2), one panel each
+    """
     n_curves: int
     K: np.ndarray          # panels per curve
     closed: np.ndarray     # bool per curve
     curve: np.ndarray      # curve index of each panel
     k: np.ndarray          # panel index within its curve
     Tgeo: scipy.sparse.csr_matrix   # [4P, n_theta] d(ax, ay, bx, by)/d theta
-    Tmid: np.ndarray                # [P, 4C] Bernstein weights at panel mid-parameters
+    Tmid: np.ndarray                # [P, n_owner] colour weights of the panels
+    pp: int = 2                     # position parameters per colour owner
+
+    @property
+    def stride(self):
+        return self.pp + 6
+
+    @property
+    def n_owner(self):
+        return 4 * self.n_curves if self.pp == 2 else self.n_curves
 
     @property
     def n_theta(self):
-        return 32 * self.n_curves
+        return self.stride * self.n_owner
+
+    @staticmethod
+    def build_segments(n_handles: int) -> "Geometry":
+        """H independent straight handles: panel h = handle h."""
+        H = int(n_handles)
+        rows = np.arange(4 * H)
+        cols = (rows // 4) * 10 + rows % 4
+        Tgeo = scipy.sparse.csr_matrix((np.ones(4 * H), (rows, cols)), shape=(4 * H, 10 * H))
+        return Geometry(H, np.ones(H, np.int64), np.zeros(H, bool), np.arange(H),
+                        np.zeros(H, np.int64), Tgeo, np.eye(H), pp=4)
 
     @property
     def P(self):
@@ -168,6 +194,8 @@ class Geometry:
     def active(self) -> np.ndarray:
         """Free parameters: all but the duplicated end point of closed loops."""
         m = np.ones(self.n_theta, bool)
+        if self.pp != 2:
+            return m
         for i in np.nonzero(self.closed)[0]:
             m[(i * 4 + 3) * 8 + 0] = False
             m[(i * 4 + 3) * 8 + 1] = False
@@ -177,9 +205,9 @@ class Geometry:
 def panelize(geo: Geometry, theta: np.ndarray):
     """Panel endpoints ab [P, 4] and jumps wd, wc [P, 3] of a parameter vector."""
     ab = (geo.Tgeo @ theta).reshape(-1, 4)
-    th = theta.reshape(-1, 8)            # per control handle
-    wd = geo.Tmid @ th[:, 2:5]
-    wc = geo.Tmid @ th[:, 5:8]
+    th = theta.reshape(-1, geo.stride)   # per colour owner
+    wd = geo.Tmid @ th[:, geo.pp:geo.pp + 3]
+    wc = geo.Tmid @ th[:, geo.pp + 3:geo.pp + 6]
     return ab, wd, wc
 
 
@@ -197,12 +225,12 @@ def compat_vectors(geo: Geometry, theta: np.ndarray) -> np.ndarray:
 def project_compat(geo: Geometry, theta: np.ndarray) -> np.ndarray:
     """Orthogonal projection of w_c onto the compatibility hyperplane (Sec. 4.3)."""
     a = compat_vectors(geo, theta)
-    th = theta.reshape(-1, 8).copy()
+    th = theta.reshape(-1, geo.stride).copy()
     aa = float(a @ a)
     if aa > 0.0:
         for c in range(3):
-            w = th[:, 5 + c]
-            th[:, 5 + c] = w - a * (a @ w) / aa
+            w = th[:, geo.pp + 3 + c]
+            th[:, geo.pp + 3 + c] = w - a * (a @ w) / aa
     return th.reshape(-1)
 
 
@@ -306,7 +334,8 @@ class Oracle:
     def __init__(self, n_curves, panels_per_curve, closed, mean_color,
                  segs_per_side: int = 256, eps_d: float = 1e-2, eps_c: float = 1e-2,
                  galerkin_mode: int = 0, polygon=None):
-        self.geo = Geometry.build(n_curves, panels_per_curve, closed)
+        self.geo = (Geometry.build_segments(n_curves) if panels_per_curve is None
+                    else Geometry.build(n_curves, panels_per_curve, closed))
         self.mean = np.asarray(mean_color, np.float64).reshape(3)
         self.eps_d = float(eps_d)
         self.eps_c = float(eps_c)
@@ -319,6 +348,12 @@ class Oracle:
         self.gp = gauss_points(self.seg)                 # [Nb, 3, 2]
         self.A = assemble_A(self.seg, galerkin_mode)
         self.Apinv = pinv_svd(self.A)
+
+    @staticmethod
+    def segments(n_handles, mean_color, **kw) -> "Oracle":
+        """The paper's parametrisation: n_handles straight handles of 10
+        parameters (a, b, w_d RGB, w_c RGB)."""
+        return Oracle(n_handles, None, None, mean_color, **kw)
 
     @staticmethod
     def from_scene(scene, mean_color=None, **kw) -> "Oracle":
@@ -360,15 +395,14 @@ class Oracle:
         S, Dl, dS, dD = pair_terms(xy, ab, self.eps_d, self.eps_c, grad=True)
         n = xy.shape[0]
         F = np.zeros((n, 3, geo.n_theta))
-        nh = 4 * geo.n_curves
-        hidx = np.arange(nh) * 8
-        colD = -Dl @ geo.Tmid            # [n, 4C] d f_c / d w_d,c of each control handle
-        colS = S @ geo.Tmid              # [n, 4C] d f_c / d w_c,c
+        hidx = np.arange(geo.n_owner) * geo.stride
+        colD = -Dl @ geo.Tmid            # [n, n_owner] d f_c / d w_d,c of each colour owner
+        colS = S @ geo.Tmid              # [n, n_owner] d f_c / d w_c,c
         for c in range(3):
             G = -wd[None, :, c, None] * dD + wc[None, :, c, None] * dS   # [n, P, 4]
             F[:, c, :] = (geo.Tgeo.T @ G.reshape(n, -1).T).T
-            F[:, c, hidx + 2 + c] += colD
-            F[:, c, hidx + 5 + c] += colS
+            F[:, c, hidx + geo.pp + c] += colD
+            F[:, c, hidx + geo.pp + 3 + c] += colS
         return F
 
     def boundary_jac(self, theta) -> np.ndarray:
@@ -421,9 +455,9 @@ class Oracle:
         """Columns = compatibility constraint of each channel on theta, [n_theta, 3]."""
         a = compat_vectors(self.geo, theta)
         Ac = np.zeros((self.geo.n_theta, 3))
-        idx = np.arange(4 * self.geo.n_curves) * 8
+        idx = np.arange(self.geo.n_owner) * self.geo.stride
         for c in range(3):
-            Ac[idx + 5 + c, c] = a
+            Ac[idx + self.geo.pp + 3 + c, c] = a
         return Ac
 
     def solve_step(self, theta, H, g, lam, free=None) -> np.ndarray:
