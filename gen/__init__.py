@@ -15,4 +15,7 @@ from .scenes import (  # noqa: F401
     perturb,
     batch_scenes,
     crossing_fraction,
+    SEGMENT_CONFIGS,
+    SegmentScene,
+    make_segment_scene,
 )

@@ -336,3 +336,65 @@ def batch_scenes(n_scenes: int = 64, seed: int = 1005) -> list[Scene]:
         spec = dict(C=C, K=64, W=W, spp=spp, layout="random", cross=0.2, **nz)
         out.append(make_scene(spec, seed=seed * 1000 + s))
     return out
+
+
+# ---------------------------------------------------------------------------
+# segment handles (the paper's own parametrisation, Sec. 4.2)
+
+@dataclasses.dataclass
+class SegmentScene:
+    """Independent straight handles, theta[h][10] = (a, b, w_d RGB, w_c RGB)."""
+    n_handles: int
+    theta_true: np.ndarray         # float64 [H*10]
+    theta_init: np.ndarray         # float64 [H*10]
+    mean_true: np.ndarray          # float64 [3]
+    W: int
+    spp: int
+    noise: dict
+    seed: int
+
+    @property
+    def n_theta(self) -> int:
+        return 10 * self.n_handles
+
+    @property
+    def n_samples(self) -> int:
+        return self.W * self.W * self.spp
+
+
+SEGMENT_CONFIGS = {
+    # the paper's optimiser state: 500 handles on a 256^2 image at 16 spp
+    "seg500": dict(H=500, W=256, spp=16, noise="lognormal", sigma=0.3, firefly=0.01,
+                   firefly_gain=20.0, seed=1006),
+}
+
+
+def make_segment_scene(cfg="seg500", seed: int | None = None, **over) -> SegmentScene:
+    """Random segment handles: endpoint a uniform in [0.05, 0.95]^2, direction
+    uniform, length uniform in [0.025, 0.1] (around the paper's initial 1/20 of
+    the image width), b clipped to [0.02, 0.98]^2; jumps as for curves
+    (w_d = c+ - c- with colours U[0,1]^3, w_c ~ U[-0.5, 0.5]^3).  theta_init
+    moves endpoints by N(0, 0.01^2) and jumps by N(0, 0.1^2)."""
+    spec = dict(SEGMENT_CONFIGS[cfg]) if isinstance(cfg, str) else dict(cfg)
+    spec.update(over)
+    seed = spec.get("seed", 0) if seed is None else seed
+    rs = _streams(seed)
+    H = int(spec["H"])
+    g = rs[_GEOM]
+    a = g.uniform(0.05, 0.95, size=(H, 2))
+    ang = g.uniform(0.0, 2.0 * math.pi, size=H)
+    ln = g.uniform(0.025, 0.1, size=H)
+    b = np.clip(a + ln[:, None] * np.stack([np.cos(ang), np.sin(ang)], 1), 0.02, 0.98)
+    c_plus = rs[_COLOR].uniform(0.0, 1.0, size=(H, 3))
+    c_minus = rs[_COLOR].uniform(0.0, 1.0, size=(H, 3))
+    wc = rs[_COLOR].uniform(-0.5, 0.5, size=(H, 3))
+    th = np.concatenate([a, b, c_plus - c_minus, wc], 1)
+    mean_true = rs[_MEAN].uniform(0.25, 0.75, size=3)
+    p = rs[_PERTURB]
+    init = th.copy()
+    init[:, 0:4] += p.normal(0.0, spec.get("pos_sigma", 0.01), size=(H, 4))
+    init[:, 4:10] += p.normal(0.0, spec.get("color_sigma", 0.1), size=(H, 6))
+    noise = {k: spec[k] for k in ("noise", "sigma", "firefly", "firefly_gain") if k in spec}
+    return SegmentScene(n_handles=H, theta_true=th.reshape(-1), theta_init=init.reshape(-1),
+                        mean_true=mean_true, W=int(spec["W"]), spp=int(spec["spp"]),
+                        noise=noise, seed=seed)

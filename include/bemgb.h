@@ -118,6 +118,16 @@ const char *bem_last_error(const bem_ctx *ctx);
 int bem_setup(bem_ctx *ctx, int n_curves, const int32_t *panels_per_curve,
               const uint8_t *closed, const double *theta, const double *mean_color);
 
+/* The paper's handle parametrisation (Sec. 4.2): n_handles independent
+ * straight handles, each one panel, with 10 parameters
+ *   theta[10 h ..] = (a_x, a_y, b_x, b_y, w_d RGB, w_c RGB)
+ * (the jumps constant over the handle).  Every other call works as for
+ * Bezier curves; n_theta = 10 n_handles, the compatibility condition uses
+ * the handle lengths.  theta: host double [10 n_handles]; mean_color: host
+ * double[3].  Errors: BEM_EINVAL. */
+int bem_setup_segments(bem_ctx *ctx, int n_handles, const double *theta,
+                       const double *mean_color);
+
 /* Replace the image boundary by a closed polygon, one subdomain of the
  * domain decomposition (Sec. 4.2): n_vertices >= 3 vertices, counter-
  * clockwise, inside the unit square; each edge is cut into segs_per_edge

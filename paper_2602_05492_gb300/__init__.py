@@ -64,6 +64,7 @@ def _load():
         "bem_setup": (ci, [vp, ci, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint8),
                            dp, dp]),
         "bem_factor": (ci, [vp, vp]),
+        "bem_setup_segments": (ci, [vp, ci, dp, dp]),
         "bem_set_boundary": (ci, [vp, ci, dp, ci]),
         "bem_set_params": (ci, [vp, vp, ci, vp]),
         "bem_get_params": (ci, [vp, dp, vp]),
@@ -107,7 +108,7 @@ EXPORTED = [
     "bem_launch_count", "bem_profile_enable", "bem_profile_read", "bem_gemm_bf16",
     "bem_fastmath_eval", "bem_vjp_noalloc", "bem_batch_create", "bem_batch_destroy",
     "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors", "lm_step_split",
-    "bem_set_boundary",
+    "bem_set_boundary", "bem_setup_segments",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -192,6 +193,14 @@ class BEM:
                                    cl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                                    _dp(th), _dp(m)))
         self.n_theta = 32 * int(n_curves)
+
+    def setup_segments(self, n_handles, theta, mean_color):
+        """Independent straight handles, 10 parameters each (Sec. 4.2)."""
+        th = np.ascontiguousarray(theta, np.float64)
+        m = np.ascontiguousarray(mean_color, np.float64)
+        assert th.size == 10 * int(n_handles)
+        self._check(_lib.bem_setup_segments(self.h, int(n_handles), _dp(th), _dp(m)))
+        self.n_theta = 10 * int(n_handles)
 
     def factor(self, stream=None):
         self._check(_lib.bem_factor(self.h, _stream(stream)))

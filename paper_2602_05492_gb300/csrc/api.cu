@@ -303,11 +303,15 @@ void bem_destroy(bem_ctx* c) {
 
 const char* bem_last_error(const bem_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
 
-int bem_setup(bem_ctx* c, int n_curves, const int32_t* ppc, const uint8_t* closed,
-              const double* theta, const double* mean_color) {
-  if (!c) return BEM_EINVAL;
-  if (n_curves < 1 || !ppc || !closed || !theta || !mean_color)
-    return fail(c, BEM_EINVAL, "bem_setup: n_curves >= 1 and non-NULL arrays required");
+}  // extern "C"
+
+namespace bem {
+
+// Scene of n_curves handles with the given panels per handle; pp = 2: cubic
+// Bezier curves (4 control handles of 8 parameters), pp = 4: segment
+// handles (10 parameters, one panel each).
+static int setup_scene(bem_ctx* c, int n_curves, const int32_t* ppc, const uint8_t* closed,
+                       const double* theta, const double* mean_color, int pp) {
   int rc;
   if ((rc = set_device(c))) return rc;
   Scene& s = c->sc;
@@ -319,13 +323,15 @@ int bem_setup(bem_ctx* c, int n_curves, const int32_t* ppc, const uint8_t* close
     if (s.K[i] < 1 || s.K[i] > (1 << 20)) return fail(c, BEM_EINVAL, "panels_per_curve out of range");
     s.off[i + 1] = s.off[i] + s.K[i];
   }
-  for (int i = 0; i < 32 * n_curves; ++i)
+  s.pp = pp;
+  s.NH = pp == 4 ? n_curves : 4 * n_curves;
+  s.nth = (pp + 6) * s.NH;
+  s.nc = (pp + 2) * s.NH;
+  for (int i = 0; i < s.nth; ++i)
     if (!std::isfinite(theta[i])) return fail(c, BEM_EINVAL, "theta has a non-finite entry");
   for (int k = 0; k < 3; ++k)
     if (!std::isfinite(mean_color[k])) return fail(c, BEM_EINVAL, "mean colour not finite");
   s.P = s.off[n_curves];
-  s.nth = 32 * n_curves;
-  s.nc = 16 * n_curves;
   std::vector<int> pc(s.P), pk(s.P);
   for (int i = 0; i < n_curves; ++i)
     for (int k = 0; k < s.K[i]; ++k) { pc[s.off[i] + k] = i; pk[s.off[i] + k] = k; }
@@ -334,7 +340,7 @@ int bem_setup(bem_ctx* c, int n_curves, const int32_t* ppc, const uint8_t* close
       (rc = alloc(c, s.d_closed, n_curves)) || (rc = alloc(c, c->d_theta, s.nth)) ||
       (rc = alloc(c, c->d_trial, s.nth)) || (rc = alloc(c, c->d_delta, s.nth)) ||
       (rc = alloc(c, c->d_pan64, s.P)) || (rc = alloc(c, c->d_pan32, s.P)) ||
-      (rc = alloc(c, c->d_compat, 4 * (size_t)n_curves)))
+      (rc = alloc(c, c->d_compat, (size_t)s.NH)))
     return rc;
   if ((rc = cuda_check(c, cudaMemcpy(s.d_pcurve, pc.data(), 4 * s.P, cudaMemcpyHostToDevice), "copy")) ||
       (rc = cuda_check(c, cudaMemcpy(s.d_pk, pk.data(), 4 * s.P, cudaMemcpyHostToDevice), "copy")) ||
@@ -346,6 +352,27 @@ int bem_setup(bem_ctx* c, int n_curves, const int32_t* ppc, const uint8_t* close
   memcpy(c->mean, mean_color, sizeof(c->mean));
   c->have_scene = true;
   return BEM_OK;
+}
+
+}  // namespace bem
+
+extern "C" {
+
+int bem_setup(bem_ctx* c, int n_curves, const int32_t* ppc, const uint8_t* closed,
+              const double* theta, const double* mean_color) {
+  if (!c) return BEM_EINVAL;
+  if (n_curves < 1 || !ppc || !closed || !theta || !mean_color)
+    return fail(c, BEM_EINVAL, "bem_setup: n_curves >= 1 and non-NULL arrays required");
+  return setup_scene(c, n_curves, ppc, closed, theta, mean_color, 2);
+}
+
+int bem_setup_segments(bem_ctx* c, int n_handles, const double* theta, const double* mean_color) {
+  if (!c) return BEM_EINVAL;
+  if (n_handles < 1 || n_handles > (1 << 20) || !theta || !mean_color)
+    return fail(c, BEM_EINVAL, "bem_setup_segments: n_handles >= 1 and non-NULL arrays required");
+  std::vector<int32_t> one(n_handles, 1);
+  std::vector<uint8_t> open(n_handles, 0);
+  return setup_scene(c, n_handles, one.data(), open.data(), theta, mean_color, 4);
 }
 
 int bem_set_boundary(bem_ctx* c, int n_vertices, const double* vertices, int segs_per_edge) {

@@ -23,7 +23,12 @@ struct Scene {
   int C = 0;          // curves
   int P = 0;          // panels
   int nth = 0;        // parameters, 32 C
-  int nc = 0;         // active parameters per colour channel, 16 C
+  int nc = 0;         // parameters per colour channel: pp NH + 2 NH
+  // colour owners: the 4 control handles of each Bezier curve (pp = 2
+  // position parameters each, 8 parameters) or the paper's segment handles
+  // (pp = 4: endpoints a and b, 10 parameters, one panel each)
+  int pp = 2;
+  int NH = 0;
   std::vector<int> K, off;        // panels per curve, panel offset of each curve
   std::vector<uint8_t> closed;
   // device metadata

@@ -347,6 +347,40 @@ __global__ void k_chain(const double* __restrict__ ps, const Panel<double>* __re
   }
 }
 
+// Panel sums -> parameter gradient of segment handles (panel h = handle h):
+// a, b from the frame chain rule, the jumps directly.
+__global__ void k_chain_seg(const double* __restrict__ ps, const Panel<double>* __restrict__ pan,
+                            int H, double scale, double* __restrict__ grad) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  const double* q = ps + (size_t)h * kNP;
+  double* g = grad + (size_t)h * 10;
+  const double L = pan[h].L;
+  double dax = 0, day = 0, dbx = 0, dby = 0;
+  if (L > 0) {
+    const double tx = pan[h].tx, ty = pan[h].ty, iL = 1.0 / L;
+    const double na = (-q[2] + q[3] + L * q[4]) * iL;
+    const double nb = (q[2] - q[3]) * iL;
+    dax = q[0] * tx + na * ty; day = q[0] * ty - na * tx;
+    dbx = q[1] * tx + nb * ty; dby = q[1] * ty - nb * tx;
+  }
+  g[0] = scale * dax; g[1] = scale * day; g[2] = scale * dbx; g[3] = scale * dby;
+  for (int c = 0; c < 3; ++c) {
+    g[4 + c] = scale * q[5 + c];
+    g[7 + c] = scale * q[8 + c];
+  }
+}
+
+// gradient from the panel sums for either parametrisation
+static void launch_chain(bem_ctx* c, const double* sums, double* grad) {
+  if (c->sc.pp == 4)
+    k_chain_seg<<<(c->sc.NH + 127) / 128, 128, 0, S(c)>>>(sums, c->d_pan64, c->sc.NH, 1.0, grad);
+  else
+    k_chain<<<(4 * c->sc.C + 127) / 128, 128, 0, S(c)>>>(sums, c->d_pan64, c->sc.d_off, c->sc.d_K,
+                                                        c->sc.d_closed, c->sc.C, 1.0, grad);
+  BEM_LAUNCHED(c);
+}
+
 template <typename T>
 static int vjp_pass(bem_ctx* c, int64_t n, const T* xy, const T* w, bool boundary, int accumulate) {
   int rc;
@@ -451,10 +485,7 @@ static int adj_vjp_t(bem_ctx* c, int64_t n, const T* xy, const T* resid, double*
   BEM_LAUNCHED(c);
   const T* gp = (const T*)(sizeof(T) == 8 ? (const void*)c->bd.d_gp : (const void*)c->bd.d_gp32);
   if ((rc = vjp_pass<T>(c, 3 * (int64_t)Nb, gp, gw, false, 1))) return rc;
-  k_chain<<<(4 * c->sc.C + 127) / 128, 128, 0, S(c)>>>((const double*)c->part2.p, c->d_pan64,
-                                                        c->sc.d_off, c->sc.d_K, c->sc.d_closed,
-                                                        c->sc.C, 1.0, grad);
-  BEM_LAUNCHED(c);
+  launch_chain(c, (const double*)c->part2.p, grad);
   return cuda_check(c, cudaGetLastError(), "vjp chain");
 }
 
@@ -604,9 +635,7 @@ int noalloc_vjp(bem_ctx* c, int64_t n, const T* xy, const T* resid, double* grad
   if ((rc = noalloc_pass<T>(c, 3 * (int64_t)Nb, gp, gw, false, 1, max_slices, part, qpart, sums,
                             nullptr)))
     return rc;
-  k_chain<<<(4 * c->sc.C + 127) / 128, 128, 0, S(c)>>>(sums, c->d_pan64, c->sc.d_off, c->sc.d_K,
-                                                        c->sc.d_closed, c->sc.C, 1.0, grad);
-  BEM_LAUNCHED(c);
+  launch_chain(c, sums, grad);
   return cuda_check(c, cudaGetLastError(), "noalloc vjp");
 }
 

@@ -10,26 +10,33 @@ namespace bem {
 // cubic Bezier through the curve's four control points (a closed curve uses
 // its first point as its last) and jumps interpolated with the Bernstein
 // weights at the mid-parameter (k+1/2)/K.
+// Segment handles (pp = 4): panel p is handle p, (a, b, w_d, w_c) directly.
 __global__ void k_panelize(const double* __restrict__ theta, const int* __restrict__ pcurve,
                            const int* __restrict__ pk, const int* __restrict__ Kc,
-                           const uint8_t* __restrict__ closed, int P, Panel<double>* out64,
-                           Panel<float>* out32) {
+                           const uint8_t* __restrict__ closed, int P, int pp,
+                           Panel<double>* out64, Panel<float>* out32) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  int i = pcurve[p], k = pk[p], K = Kc[i];
-  const double* th = theta + (size_t)i * 32;
-  double t0 = double(k) / K, t1 = double(k + 1) / K, tm = (k + 0.5) / K;
   double ax = 0, ay = 0, bx = 0, by = 0;
   double wd[3] = {0, 0, 0}, wc[3] = {0, 0, 0};
-  for (int j = 0; j < 4; ++j) {
-    int jg = (closed[i] && j == 3) ? 0 : j;
-    double px = th[jg * 8 + 0], py = th[jg * 8 + 1];
-    double w0 = bern3(j, t0), w1 = bern3(j, t1), wm = bern3(j, tm);
-    ax += w0 * px; ay += w0 * py;
-    bx += w1 * px; by += w1 * py;
-    for (int c = 0; c < 3; ++c) {
-      wd[c] += wm * th[j * 8 + 2 + c];
-      wc[c] += wm * th[j * 8 + 5 + c];
+  if (pp == 4) {
+    const double* th = theta + (size_t)p * 10;
+    ax = th[0]; ay = th[1]; bx = th[2]; by = th[3];
+    for (int c = 0; c < 3; ++c) { wd[c] = th[4 + c]; wc[c] = th[7 + c]; }
+  } else {
+    int i = pcurve[p], k = pk[p], K = Kc[i];
+    const double* th = theta + (size_t)i * 32;
+    double t0 = double(k) / K, t1 = double(k + 1) / K, tm = (k + 0.5) / K;
+    for (int j = 0; j < 4; ++j) {
+      int jg = (closed[i] && j == 3) ? 0 : j;
+      double px = th[jg * 8 + 0], py = th[jg * 8 + 1];
+      double w0 = bern3(j, t0), w1 = bern3(j, t1), wm = bern3(j, tm);
+      ax += w0 * px; ay += w0 * py;
+      bx += w1 * px; by += w1 * py;
+      for (int c = 0; c < 3; ++c) {
+        wd[c] += wm * th[j * 8 + 2 + c];
+        wc[c] += wm * th[j * 8 + 5 + c];
+      }
     }
   }
   double ex = bx - ax, ey = by - ay;
@@ -50,19 +57,24 @@ __global__ void k_panelize(const double* __restrict__ theta, const int* __restri
   out32[p] = r;
 }
 
-// a_h = sum_k length_k B_j((k+1/2)/K) over the panels of h's curve, then
-// w_c <- w_c - a (a.w_c)/(a.a) per channel (compatibility, Sec. 3.1.2 and
-// the re-projection of Sec. 4.3).  One block.
+// a_h = sum_k length_k B_j((k+1/2)/K) over the panels of h's curve (a
+// segment handle: its length), then w_c <- w_c - a (a.w_c)/(a.a) per
+// channel (compatibility, Sec. 3.1.2 and the re-projection of Sec. 4.3).
+// One block; colour owner h has its w_c at theta[h (pp + 6) + pp + 3 + c].
 __global__ void k_compat(double* __restrict__ theta, const Panel<double>* __restrict__ pan,
-                         const int* __restrict__ off, const int* __restrict__ Kc, int C,
+                         const int* __restrict__ off, const int* __restrict__ Kc, int C, int pp,
                          double* __restrict__ a_out, int project) {
-  extern __shared__ double sh[];   // [4C] a, then 4 partial sums per warp
-  int H = 4 * C;
+  extern __shared__ double sh[];   // [owners] a
+  const int H = pp == 4 ? C : 4 * C, stride = pp + 6, wco = pp + 3;
   double* a = sh;
   for (int h = threadIdx.x; h < H; h += blockDim.x) {
-    int i = h / 4, j = h % 4, K = Kc[i];
     double s = 0;
-    for (int k = 0; k < K; ++k) s += pan[off[i] + k].L * bern3(j, (k + 0.5) / K);
+    if (pp == 4) {
+      s = pan[h].L;
+    } else {
+      int i = h / 4, j = h % 4, K = Kc[i];
+      for (int k = 0; k < K; ++k) s += pan[off[i] + k].L * bern3(j, (k + 0.5) / K);
+    }
     a[h] = s;
     a_out[h] = s;
   }
@@ -72,7 +84,7 @@ __global__ void k_compat(double* __restrict__ theta, const Panel<double>* __rest
   double v[4] = {0, 0, 0, 0};
   for (int h = threadIdx.x; h < H; h += blockDim.x) {
     v[0] += a[h] * a[h];
-    for (int c = 0; c < 3; ++c) v[1 + c] += a[h] * theta[h * 8 + 5 + c];
+    for (int c = 0; c < 3; ++c) v[1 + c] += a[h] * theta[h * stride + wco + c];
   }
   for (int o = 16; o; o >>= 1)
     for (int q = 0; q < 4; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
@@ -89,7 +101,7 @@ __global__ void k_compat(double* __restrict__ theta, const Panel<double>* __rest
   __syncthreads();
   if (tot[0] <= 0) return;
   for (int h = threadIdx.x; h < H; h += blockDim.x)
-    for (int c = 0; c < 3; ++c) theta[h * 8 + 5 + c] -= a[h] * tot[1 + c] / tot[0];
+    for (int c = 0; c < 3; ++c) theta[h * stride + wco + c] -= a[h] * tot[1 + c] / tot[0];
 }
 
 // A_ij = |G_i| sum_q w_q I_j(x_iq), A_ii = |G_i| / 2 (the coincident
@@ -137,17 +149,18 @@ int geom_panelize(bem_ctx* c, const double* d_theta) {
   int P = c->sc.P;
   c->pbins_valid = false;
   k_panelize<<<(P + 127) / 128, 128, 0, S(c)>>>(d_theta, c->sc.d_pcurve, c->sc.d_pk, c->sc.d_K,
-                                                c->sc.d_closed, P, c->d_pan64, c->d_pan32);
+                                                c->sc.d_closed, P, c->sc.pp, c->d_pan64,
+                                                c->d_pan32);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_panelize");
 }
 
 int geom_compat(bem_ctx* c, double* d_theta, bool project) {
   int C = c->sc.C;
-  size_t shm = sizeof(double) * 4 * C;
-  if (shm > 48 * 1024) return fail(c, BEM_EINVAL, "too many curves for the compatibility kernel");
-  k_compat<<<1, 256, shm, S(c)>>>(d_theta, c->d_pan64, c->sc.d_off, c->sc.d_K, C, c->d_compat,
-                                  project ? 1 : 0);
+  size_t shm = sizeof(double) * c->sc.NH;
+  if (shm > 48 * 1024) return fail(c, BEM_EINVAL, "too many handles for the compatibility kernel");
+  k_compat<<<1, 256, shm, S(c)>>>(d_theta, c->d_pan64, c->sc.d_off, c->sc.d_K, C, c->sc.pp,
+                                  c->d_compat, project ? 1 : 0);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_compat");
 }

@@ -302,19 +302,25 @@ __global__ void k_g_boundary(const double* __restrict__ Df, int Nb, int nc,
   if (lane == 0) gb[row] = acc;
 }
 
+// Column of parameter t in channel c's block of J (or -1): colour owner
+// h = t / (pp + 6) has its pp position entries at pp h + comp (every channel),
+// w_d,c at pp NH + h and w_c,c at (pp + 1) NH + h.
+__device__ __forceinline__ int param_col(int t, int c, int pp, int NH) {
+  const int stride = pp + 6, h = t / stride, comp = t % stride;
+  if (comp < pp) return pp * h + comp;
+  if (comp < pp + 3) return comp - pp == c ? pp * NH + h : -1;
+  return comp - pp - 3 == c ? (pp + 1) * NH + h : -1;
+}
+
 __global__ void k_g_assemble(const double* __restrict__ gparts, int nparts, int stride,
-                             const double* __restrict__ gb, int C, double scale,
+                             const double* __restrict__ gb, int pp, int NH, double scale,
                              double* __restrict__ g) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nth = 32 * C, nc = 16 * C;
+  const int nth = (pp + 6) * NH, nc = (pp + 2) * NH;
   if (t >= nth) return;
-  const int h = t / 8, comp = t % 8;
   double s = 0;
   for (int c = 0; c < 3; ++c) {
-    int col;
-    if (comp < 2) col = 2 * h + comp;
-    else if (comp < 5) col = comp - 2 == c ? 8 * C + h : -1;
-    else col = comp - 5 == c ? 12 * C + h : -1;
+    const int col = param_col(t, c, pp, NH);
     if (col < 0) continue;
     const int row = c * nc + col;
     double v = gb[row];
@@ -356,24 +362,59 @@ __global__ void k_df_reduce(const double* __restrict__ Fg, int Nb, int nc,
 }
 
 // H[a][b] = scale * sum_c Hc[c][col_c(a)][col_c(b)] over channels where both are active
-__global__ void k_h_assemble(const double* __restrict__ Hc, int C, double scale,
+__global__ void k_h_assemble(const double* __restrict__ Hc, int pp, int NH, double scale,
                              double* __restrict__ H) {
-  int nth = 32 * C, nc = 16 * C;
+  const int nth = (pp + 6) * NH, nc = (pp + 2) * NH;
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   int a = blockIdx.y;
   if (b >= nth) return;
-  auto col = [&](int t, int c) {
-    int h = t / 8, comp = t % 8;
-    if (comp < 2) return 2 * h + comp;
-    if (comp < 5) return comp - 2 == c ? 8 * C + h : -1;
-    return comp - 5 == c ? 12 * C + h : -1;
-  };
   double s = 0;
   for (int c = 0; c < 3; ++c) {
-    int ca = col(a, c), cb = col(b, c);
+    const int ca = param_col(a, c, pp, NH), cb = param_col(b, c, pp, NH);
     if (ca >= 0 && cb >= 0) s += Hc[((size_t)c * nc + ca) * nc + cb];
   }
   H[(size_t)a * nth + b] = scale * s;
+}
+
+// F rows of segment handles (the paper's parametrisation, one panel per
+// handle): thread = point, blockIdx.y = a run of kSegRun handles.  Columns of
+// channel c: a, b of handle h at 4h .. 4h+3, w_d,c at 4H + h, w_c,c at 5H + h.
+constexpr int kSegRun = 8;
+
+template <typename T, bool SAME, bool TR>
+__global__ void __launch_bounds__(128) k_frows_seg(const T* __restrict__ xy, int ns,
+                                                   const Panel<T>* __restrict__ pan, int H, T ec2,
+                                                   T ed2, void* __restrict__ Fout, int ldf) {
+  constexpr T kOut = sizeof(T) == 4 ? T(-kInv2Pi) : T(1);
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const int nc = 6 * H;
+  const T x = xy[2 * s], y = xy[2 * s + 1];
+  const int h0 = blockIdx.y * kSegRun, h1 = min(H, h0 + kSegRun);
+  for (int h = h0; h < h1; ++h) {
+    const Panel<T> p = pan[h];
+    T Dl, S, Dd[4], Sd[4];
+    frows_pair<T, SAME>(p, x, y, ec2, ed2, Dl, S, Dd, Sd);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T a = -p.wd[c], b = p.wc[c];
+      T v[6];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = kOut * (a * Dd[e] + b * Sd[e]);
+      v[4] = -kOut * Dl;
+      v[5] = kOut * S;
+      const int cols[6] = {4 * h, 4 * h + 1, 4 * h + 2, 4 * h + 3, 4 * H + h, 5 * H + h};
+      if (TR) {
+        float* F = (float*)Fout + (size_t)c * nc * ldf + s;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) F[(size_t)cols[e] * ldf] = float(v[e]);
+      } else {
+        double* row = (double*)Fout + ((size_t)c * ns + s) * nc;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) row[cols[e]] = double(v[e]);
+      }
+    }
+  }
 }
 
 template <typename T, bool TR = false>
@@ -384,6 +425,16 @@ static void launch_frows(bem_ctx* c, const T* xy, int ns, void* F, int ldf = 0) 
       (const Panel<T>*)(sizeof(T) == 8 ? (const void*)c->d_pan64 : (const void*)c->d_pan32);
   T ec2 = T(c->opts.eps_c * c->opts.eps_c), ed2 = T(c->opts.eps_d * c->opts.eps_d);
   ProfScope _ps(c, "k_frows");
+  if (c->sc.pp == 4) {
+    const int H = c->sc.NH;
+    dim3 gs((ns + 127) / 128, (H + kSegRun - 1) / kSegRun);
+    if (c->opts.eps_c == c->opts.eps_d)
+      k_frows_seg<T, true, TR><<<gs, 128, 0, S(c)>>>(xy, ns, pan, H, ec2, ed2, F, ldf);
+    else
+      k_frows_seg<T, false, TR><<<gs, 128, 0, S(c)>>>(xy, ns, pan, H, ec2, ed2, F, ldf);
+    BEM_LAUNCHED(c);
+    return;
+  }
   if (c->opts.eps_c == c->opts.eps_d)
     k_frows<T, true, TR><<<grid, 128, 0, S(c)>>>(xy, ns, pan, c->sc.d_off, c->sc.d_K,
                                                  c->sc.d_closed, C, ec2, ed2, F, ldf);
@@ -396,7 +447,7 @@ static void launch_frows(bem_ctx* c, const T* xy, int ns, void* F, int ldf = 0) 
 template <typename T>
 static int jtj_t(bem_ctx* c, int64_t n, const T* xy, double* Hout) {
   int rc;
-  int C = c->sc.C, nc = 16 * C, Nb = c->bd.Nb, nth = c->sc.nth;
+  int C = c->sc.C, nc = c->sc.nc, Nb = c->bd.Nb, nth = c->sc.nth;
   // stacked right-hand sides: F at the boundary Gauss points -> Df -> M_c = A^+ Df_c
   int n3 = 3 * Nb;
   if ((rc = grow(c, c->Fg, sizeof(double) * 3 * (size_t)n3 * nc))) return rc;
@@ -443,7 +494,7 @@ static int jtj_t(bem_ctx* c, int64_t n, const T* xy, double* Hout) {
       la_dgemm(c, true, false, nc, nc, m, 1.0, Fc, nc, Fc, nc, 1.0, Hc + (size_t)ch * nc * nc, nc);
     }
   }
-  k_h_assemble<<<dim3((nth + 127) / 128, nth), 128, 0, S(c)>>>(Hc, C, n > 0 ? 1.0 / double(n) : 0.0,
+  k_h_assemble<<<dim3((nth + 127) / 128, nth), 128, 0, S(c)>>>(Hc, c->sc.pp, c->sc.NH, n > 0 ? 1.0 / double(n) : 0.0,
                                                                 Hout);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "jtj");
@@ -525,7 +576,7 @@ __global__ void __launch_bounds__(256) k_mt_sgemm(const float* __restrict__ W,
 template <typename T>
 static int jtj_stacked_rhs(bem_ctx* c, bool solve = true) {
   int rc;
-  int C = c->sc.C, nc = 16 * C, Nb = c->bd.Nb, n3 = 3 * Nb;
+  int C = c->sc.C, nc = c->sc.nc, Nb = c->bd.Nb, n3 = 3 * Nb;
   if ((rc = grow(c, c->Fg, sizeof(double) * 3 * (size_t)n3 * nc))) return rc;
   if ((rc = grow(c, c->Dfc, sizeof(double) * 3 * (size_t)Nb * nc))) return rc;
   if ((rc = grow(c, c->Mc, sizeof(double) * 3 * (size_t)Nb * nc))) return rc;
@@ -554,7 +605,7 @@ static int jtj_stacked_rhs(bem_ctx* c, bool solve = true) {
 static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
                   const float* resid, double* gout) {
   int rc;
-  int C = c->sc.C, nc = 16 * C, Nb = c->bd.Nb, nth = c->sc.nth;
+  int C = c->sc.C, nc = c->sc.nc, Nb = c->bd.Nb, nth = c->sc.nth;
   const bool want_g = resid && gout;
   if ((rc = jtj_stacked_rhs<float>(c, false))) return rc;
   const size_t es = x3 ? 2 * sizeof(float) : sizeof(__nv_bfloat16);   // bytes per element (all parts)
@@ -650,7 +701,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   }
   k_syrk_reduce<<<dim3((nc + 127) / 128, nc, 3), 128, 0, S(c)>>>(part, splits, nc,
                                                                   (double*)c->Hc.p);
-  k_h_assemble<<<dim3((nth + 127) / 128, nth), 128, 0, S(c)>>>((const double*)c->Hc.p, C,
+  k_h_assemble<<<dim3((nth + 127) / 128, nth), 128, 0, S(c)>>>((const double*)c->Hc.p, c->sc.pp, c->sc.NH,
                                                                 n > 0 ? 1.0 / double(n) : 0.0, Hout);
   c->launches += 2;
   if (want_g) {
@@ -663,11 +714,11 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
     if (fused_g) {
       double* ghr = gh + (size_t)tiles_all * 3 * nc;
       k_row_sums<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>(gh, 3 * nc, tiles_all, ghr);
-      k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(ghr, 1, 3 * nc, gb, C,
+      k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(ghr, 1, 3 * nc, gb, c->sc.pp, c->sc.NH,
                                                          n > 0 ? 1.0 / double(n) : 0.0, gout);
       c->launches += 3;
     } else {
-      k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(gh, nchunks * kGemvSegs, 3 * nc, gb, C,
+      k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(gh, nchunks * kGemvSegs, 3 * nc, gb, c->sc.pp, c->sc.NH,
                                                          n > 0 ? 1.0 / double(n) : 0.0, gout);
       c->launches += 2;
     }

@@ -502,18 +502,23 @@ __global__ void k_diag_max(const double* __restrict__ H, int n, double* __restri
 
 // K = H + lam diag(max(H_ii, 1e-12 max)) on active parameters; inactive
 // rows/columns become identity rows.  rhs[n][4] = (-g, a-columns).
+// Parameter t of colour owner h = t / (pp + 6), component t % (pp + 6):
+// pp position entries, then w_d (RGB), then w_c (RGB).  Inactive: the
+// duplicated end point of a closed Bezier curve (pp = 2).
+__device__ __forceinline__ bool param_active(int t, int pp, const uint8_t* closed) {
+  if (pp != 2) return true;
+  const int h = t / 8, comp = t % 8;
+  return !(comp < 2 && (h % 4) == 3 && closed[h / 4]);
+}
+
 __global__ void k_lm_build(const double* __restrict__ H, const double* __restrict__ g, int n,
-                           int C, const uint8_t* __restrict__ closed, const double* __restrict__ a,
+                           int pp, const uint8_t* __restrict__ closed, const double* __restrict__ a,
                            const double* __restrict__ mx, double lam, double* __restrict__ Kmat,
                            double* __restrict__ rhs) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y;
   if (j >= n) return;
-  auto active = [&](int t) {
-    int h = t / 8, comp = t % 8;
-    return !(comp < 2 && (h % 4) == 3 && closed[h / 4]);
-  };
-  bool ai = active(i), aj = active(j);
+  bool ai = param_active(i, pp, closed), aj = param_active(j, pp, closed);
   double v;
   if (!ai || !aj) v = (i == j) ? 1.0 : 0.0;
   else {
@@ -522,20 +527,21 @@ __global__ void k_lm_build(const double* __restrict__ H, const double* __restric
   }
   Kmat[(size_t)i * n + j] = v;
   if (j == 0) {
-    int h = i / 8, comp = i % 8;
+    const int stride = pp + 6, h = i / stride, comp = i % stride;
     rhs[4 * i] = ai ? -g[i] : 0.0;
-    for (int c = 0; c < 3; ++c) rhs[4 * i + 1 + c] = (comp == 5 + c) ? a[h] : 0.0;
+    for (int c = 0; c < 3; ++c) rhs[4 * i + 1 + c] = (comp == pp + 3 + c) ? a[h] : 0.0;
   }
 }
 
 // cons[n][4]: columns 1..3 = compatibility constraint of channel 0..2
-// (a_h at the w_c entry of control handle h), column 0 unused.
-__global__ void k_constraint_cols(int n, const double* __restrict__ a, double* __restrict__ cons) {
+// (a_h at the w_c entry of colour owner h), column 0 unused.
+__global__ void k_constraint_cols(int n, int pp, const double* __restrict__ a,
+                                  double* __restrict__ cons) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int h = i / 8, comp = i % 8;
+  const int stride = pp + 6, h = i / stride, comp = i % stride;
   cons[4 * i] = 0.0;
-  for (int c = 0; c < 3; ++c) cons[4 * i + 1 + c] = (comp == 5 + c) ? a[h] : 0.0;
+  for (int c = 0; c < 3; ++c) cons[4 * i + 1 + c] = (comp == pp + 3 + c) ? a[h] : 0.0;
 }
 
 // Blocked right-looking Cholesky K = L L^T in double, 32-column panels.
@@ -1219,7 +1225,7 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
   {
     ProfScope _pb(c, "lm_build");
     k_diag_max<<<1, 1024, 0, S(c)>>>(H, n, mx);
-    k_lm_build<<<grid, 128, 0, S(c)>>>(H, g, n, c->sc.C, c->sc.d_closed, c->d_compat, mx, lam, Km, R);
+    k_lm_build<<<grid, 128, 0, S(c)>>>(H, g, n, c->sc.pp, c->sc.d_closed, c->d_compat, mx, lam, Km, R);
     c->launches += 2;
   }
   // float factor of the equilibrated matrix, refined in double; the double
@@ -1285,7 +1291,7 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
     chol_solve4(c, Km, Linv, n, R, Ytmp);
   }
   // the constraint columns are needed again for the Schur complement
-  k_constraint_cols<<<(n + 255) / 256, 256, 0, S(c)>>>(n, c->d_compat, cons);
+  k_constraint_cols<<<(n + 255) / 256, 256, 0, S(c)>>>(n, c->sc.pp, c->d_compat, cons);
   BEM_LAUNCHED(c);
   k_kkt_finish<<<1, 1024, 0, S(c)>>>(R, cons, n, delta, gn, g);
   BEM_LAUNCHED(c);
