@@ -62,3 +62,4 @@ def lib():
 
 
 from .bem import *  # noqa: E402,F401,F403
+from . import regularize  # noqa: E402,F401

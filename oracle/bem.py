@@ -503,17 +503,29 @@ class Oracle:
             H += Jf.T @ Jf
         return H / xy.shape[0]
 
-    def lm_step(self, theta, xy, target, lam, xy_h=None):
+    def lm_step(self, theta, xy, target, lam, xy_h=None, reg=None):
         """One LM iteration (Eq. optimstep) with the paper's two-stage projection.
         With xy_h, the Hessian integral uses those M_H points and the gradient
-        and the losses the M_J points xy (Sec. 4.3, Monte Carlo integration)."""
+        and the losses the M_J points xy (Sec. 4.3, Monte Carlo integration).
+        With reg (segment handles, a regularize.RegParams), the Sec. 4.4
+        losses add their analytic gradient and Hessian to g and H and their
+        values to both losses; the snapping pairs are chosen once, at theta."""
         L0, g, H = self.gauss_newton(theta, xy, target)
         if xy_h is not None:
             H = self.hessian(theta, xy_h)
+        pairs = None
+        if reg is not None:
+            from . import regularize
+            pairs = regularize.snap_pairs(theta, reg)
+            gr, Hr = regularize.reg_grad_hess(theta, reg, pairs)
+            g, H = g + gr, H + Hr
+            L0 += regularize.reg_loss(theta, reg, pairs)
         delta = self.solve_step(theta, H, g, lam)
         lam = self.last_lambda
         th_new = project_compat(self.geo, theta + delta)
         L1 = self.loss(th_new, xy, target)
+        if reg is not None:
+            L1 += regularize.reg_loss(th_new, reg, pairs)
         accept = L1 < L0
         return dict(loss_before=L0, loss_after=L1, accepted=bool(accept),
                     lambda_next=lam / 3.0 if accept else lam * 2.0,
