@@ -90,6 +90,26 @@ typedef struct {
     double grad_norm;     /* |g|_2 of the gradient at theta */
 } lm_result;
 
+/* Regularisers of segment handles (Sec. 4.4); a zero weight turns a term
+ * off, all off by default.  Each adds its loss to the LM objective and its
+ * analytic gradient and Hessian to g and H of Eq. (optimstep):
+ *   length    len_weight (|b - a| - len_max)^2 where |b - a| > len_max
+ *   snapping  snap_weight |p - q|^2 for endpoints p, q of two handles closer
+ *             than snap_radius that choose each other by the lowest score
+ *             snap_alpha |p - q| / snap_radius + (1 - snap_alpha)(1 - |u_p.u_q|)
+ *             (u = unit handle directions; ties to the lower endpoint index
+ *             2h + s, s = 0 for a, 1 for b); pairs chosen once per LM step
+ *   sparsity  lam t tanh(sqrt(w.w + eps^2) / t) per handle for w = w_d
+ *             (lam = sparse_wd) and w = w_c (lam = sparse_wc), t = sparse_t,
+ *             eps = sparse_eps; H receives its Hessian with the factor
+ *             sech^2(rho/t) held fixed (positive semidefinite), without the
+ *             negative curvature of the saturation. */
+typedef struct {
+    double len_weight, len_max;
+    double snap_weight, snap_radius, snap_alpha;
+    double sparse_wd, sparse_wc, sparse_eps, sparse_t;
+} bem_reg;
+
 typedef struct bem_ctx bem_ctx;
 
 /* Fill *opts with the defaults above.  Never fails for a non-NULL opts. */
@@ -127,6 +147,38 @@ int bem_setup(bem_ctx *ctx, int n_curves, const int32_t *panels_per_curve,
  * double[3].  Errors: BEM_EINVAL. */
 int bem_setup_segments(bem_ctx *ctx, int n_handles, const double *theta,
                        const double *mean_color);
+
+/* Set (reg non-NULL) or clear (reg NULL) the Sec. 4.4 regularisers of a
+ * segment-handle context; lm_step and lm_step_split then report the losses
+ * with the regulariser values included.  Errors: BEM_EINVAL for negative or
+ * non-finite weights, snap_radius <= 0, snap_alpha outside [0, 1],
+ * sparse_eps or sparse_t <= 0 while their term is on, BEM_ESTATE unless the
+ * scene was set up with bem_setup_segments. */
+int bem_set_regularizers(bem_ctx *ctx, const bem_reg *reg);
+
+/* Pruning (Sec. 4.4, Sparsity): remove every handle with |w_d| < threshold
+ * and |w_c| < threshold (2-norms over RGB), keep the others in order, and
+ * re-project w_c onto the compatibility hyperplane of the kept handles
+ * (Sec. 4.3).  *n_kept receives their number and kept_index (host int32
+ * [old n_handles], may be NULL) their former indices.  If no handle would
+ * remain the scene is left as it is and *n_kept = 0.  The boundary
+ * factorisation stays valid.  Synchronises `stream`.  Errors: BEM_EINVAL,
+ * BEM_ESTATE unless the scene has segment handles and is factored. */
+int bem_prune(bem_ctx *ctx, double threshold, int *n_kept, int32_t *kept_index, void *stream);
+
+/* Initial segment handles (Sec. 4.2), host only (no context, no GPU): for
+ * the sequence indices k = first_index .. first_index + n_points - 1, the
+ * first endpoint a is point k of the two-dimensional Sobol sequence (Gray-
+ * code order, unscrambled); handles are made only where a lies inside the
+ * polygon (even-odd rule; vertices NULL = the unit square).  The second
+ * endpoint is a + length (cos phi, sin phi) with phi = 2 pi times the base-3
+ * radical inverse of k (a stand-in for a third Sobol coordinate), pulled
+ * back along the handle to its first crossing with the polygon.  Jumps are
+ * zero.  theta_out: host double [10 n_points] (the first 10 *n_handles
+ * entries are written); vertices: host double [n_vertices][2].
+ * Errors: BEM_EINVAL. */
+int bem_init_segments(int n_points, double length, int64_t first_index, int n_vertices,
+                      const double *vertices, double *theta_out, int *n_handles);
 
 /* Replace the image boundary by a closed polygon, one subdomain of the
  * domain decomposition (Sec. 4.2): n_vertices >= 3 vertices, counter-

@@ -18,6 +18,14 @@ the Gauss-Newton gradient and matrix of the LM step (Eq. optimstep):
   sparsity       lam_w t tanh(sqrt(w.w + eps^2) / t) for w = w_d (lam_d) and
                  w = w_c (lam_c) of every handle.
 
+Reading of the sparsity Hessian: the exact Hessian of the saturated term is
+lam s (I / rho - w w^T / rho^3) - lam s (2 tanh(rho/t) / (t rho^2)) w w^T
+with s = sech^2(rho / t); the second part is the negative curvature of the
+saturation and can turn diagonal entries of H negative, and then H + lam D
+with D = diag(H) (floored) does not factor for any damping.  H receives the
+first, positive semidefinite part only (the saturation factor s held fixed
+at the current w); the gradient and the loss are exact.
+
 Pruning (Sec. 4.4, Sparsity): a handle whose |w_d| and |w_c| are both below a
 threshold is removed; w_c is then re-projected onto the compatibility
 hyperplane of the remaining handles (Sec. 4.3).
@@ -130,7 +138,8 @@ def reg_loss(theta, rp: RegParams, pairs=None) -> float:
 
 
 def reg_grad_hess(theta, rp: RegParams, pairs=None):
-    """Analytic gradient [10H] and Hessian [10H, 10H] of reg_loss (Sec. 4.4)."""
+    """Analytic gradient [10H] and Hessian [10H, 10H] of reg_loss (Sec. 4.4);
+    the sparsity part of the Hessian without its saturation curvature."""
     a, b, wd, wc = _handles(theta)
     H = a.shape[0]
     n = 10 * H
@@ -181,8 +190,7 @@ def reg_grad_hess(theta, rp: RegParams, pairs=None):
             s = 1.0 - th_ * th_                  # sech^2(rho / t)
             i = 10 * h + off
             g[i:i + 3] += lam * s * v / rho
-            Hm[i:i + 3, i:i + 3] += lam * s * (I3 / rho - np.outer(v, v) / rho ** 3
-                                               - (2.0 * th_ / t) * np.outer(v, v) / rho ** 2)
+            Hm[i:i + 3, i:i + 3] += lam * s * (I3 / rho - np.outer(v, v) / rho ** 3)
     return g, Hm
 
 

@@ -43,6 +43,12 @@ class lm_result(ctypes.Structure):
                 ("lambda_next", ctypes.c_double), ("grad_norm", ctypes.c_double)]
 
 
+class bem_reg(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "len_weight", "len_max", "snap_weight", "snap_radius", "snap_alpha",
+        "sparse_wd", "sparse_wc", "sparse_eps", "sparse_t")]
+
+
 class BemError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{_STATUS.get(code, code)}: {msg}")
@@ -92,6 +98,10 @@ def _load():
         "bem_batch_tile_shape": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]),
         "bem_render": (ci, [vp, ci, ci, vp, vp]),
         "bem_handle_colors": (ci, [vp, dp, vp]),
+        "bem_set_regularizers": (ci, [vp, ctypes.POINTER(bem_reg)]),
+        "bem_prune": (ci, [vp, ctypes.c_double, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_int32),
+                           vp]),
+        "bem_init_segments": (ci, [ci, ctypes.c_double, i64, ci, dp, dp, ctypes.POINTER(ci)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -108,7 +118,8 @@ EXPORTED = [
     "bem_launch_count", "bem_profile_enable", "bem_profile_read", "bem_gemm_bf16",
     "bem_fastmath_eval", "bem_vjp_noalloc", "bem_batch_create", "bem_batch_destroy",
     "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors", "lm_step_split",
-    "bem_set_boundary", "bem_setup_segments",
+    "bem_set_boundary", "bem_setup_segments", "bem_set_regularizers", "bem_prune",
+    "bem_init_segments",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -201,6 +212,34 @@ class BEM:
         assert th.size == 10 * int(n_handles)
         self._check(_lib.bem_setup_segments(self.h, int(n_handles), _dp(th), _dp(m)))
         self.n_theta = 10 * int(n_handles)
+
+    def set_regularizers(self, **kw):
+        """Sec. 4.4 regularisers of a segment-handle scene (bem_reg field
+        names as keywords; none given clears them)."""
+        if not kw:
+            self._check(_lib.bem_set_regularizers(self.h, None))
+            return
+        r = bem_reg(len_max=0.1, snap_radius=0.02, snap_alpha=0.5, sparse_eps=1e-3,
+                    sparse_t=0.05)
+        for k, v in kw.items():
+            if k not in dict(bem_reg._fields_):
+                raise TypeError(f"unknown regulariser setting {k}")
+            setattr(r, k, float(v))
+        self._check(_lib.bem_set_regularizers(self.h, ctypes.byref(r)))
+
+    def prune(self, threshold, stream=None) -> np.ndarray:
+        """Remove handles whose |w_d| and |w_c| are below threshold; returns
+        the former indices of the kept handles (empty: nothing removed
+        because nothing would remain)."""
+        H = self.n_theta // 10
+        kept = np.zeros(H, np.int32)
+        n = ctypes.c_int(0)
+        self._check(_lib.bem_prune(self.h, float(threshold), ctypes.byref(n),
+                                   kept.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   _stream(stream)))
+        if n.value:
+            self.n_theta = 10 * n.value
+        return kept[:n.value].copy()
 
     def factor(self, stream=None):
         self._check(_lib.bem_factor(self.h, _stream(stream)))
@@ -417,3 +456,21 @@ class BEMBatch:
         a, b = ctypes.c_int(), ctypes.c_int()
         _lib.bem_batch_tile_shape(self.h, ctypes.byref(a), ctypes.byref(b))
         return a.value, b.value
+
+
+def init_segments(n_points, length, first_index=1, polygon=None) -> np.ndarray:
+    """Initial segment handles of Sec. 4.2 (host computation in the library):
+    theta [10 * n_handles] for the Sobol points first_index .. + n_points - 1
+    that fall inside the polygon (default: the unit square)."""
+    out = np.zeros(10 * max(int(n_points), 1))
+    n = ctypes.c_int(0)
+    if polygon is None:
+        rc = _lib.bem_init_segments(int(n_points), float(length), int(first_index), 0, None,
+                                    _dp(out), ctypes.byref(n))
+    else:
+        v = np.ascontiguousarray(polygon, np.float64).reshape(-1, 2)
+        rc = _lib.bem_init_segments(int(n_points), float(length), int(first_index), v.shape[0],
+                                    _dp(v), _dp(out), ctypes.byref(n))
+    if rc != BEM_OK:
+        raise BemError(rc, "bem_init_segments: bad arguments")
+    return out[:10 * n.value].copy()

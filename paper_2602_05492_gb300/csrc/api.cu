@@ -375,6 +375,53 @@ int bem_setup_segments(bem_ctx* c, int n_handles, const double* theta, const dou
   return setup_scene(c, n_handles, one.data(), open.data(), theta, mean_color, 4);
 }
 
+int bem_set_regularizers(bem_ctx* c, const bem_reg* r) {
+  if (!c) return BEM_EINVAL;
+  if (!r) {
+    c->reg = bem_reg{};
+    return BEM_OK;
+  }
+  const double v[9] = {r->len_weight, r->len_max, r->snap_weight, r->snap_radius, r->snap_alpha,
+                       r->sparse_wd, r->sparse_wc, r->sparse_eps, r->sparse_t};
+  for (double x : v)
+    if (!std::isfinite(x) || x < 0) return fail(c, BEM_EINVAL, "regulariser settings must be finite and >= 0");
+  if (r->snap_weight > 0 && (!(r->snap_radius > 0) || r->snap_alpha > 1))
+    return fail(c, BEM_EINVAL, "snapping needs snap_radius > 0 and snap_alpha in [0, 1]");
+  if ((r->sparse_wd > 0 || r->sparse_wc > 0) && (!(r->sparse_eps > 0) || !(r->sparse_t > 0)))
+    return fail(c, BEM_EINVAL, "sparsity needs sparse_eps > 0 and sparse_t > 0");
+  if (!c->have_scene || c->sc.pp != 4)
+    return fail(c, BEM_ESTATE, "regularisers need a scene of segment handles (bem_setup_segments)");
+  c->reg = *r;
+  return BEM_OK;
+}
+
+int bem_prune(bem_ctx* c, double threshold, int* n_kept, int32_t* kept_index, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (!n_kept || !(threshold >= 0) || !std::isfinite(threshold))
+    return fail(c, BEM_EINVAL, "bem_prune: finite threshold >= 0 and n_kept required");
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  if (c->sc.pp != 4) return fail(c, BEM_ESTATE, "bem_prune needs segment handles (bem_setup_segments)");
+  c->cur = (cudaStream_t)stream;
+  const int H = c->sc.NH;
+  std::vector<double> th;
+  std::vector<int> idx;
+  if ((rc = reg_prune(c, threshold, th, idx))) return rc;
+  const int n = (int)idx.size();
+  *n_kept = n;
+  if (n == 0) return BEM_OK;
+  if (kept_index)
+    for (int i = 0; i < n; ++i) kept_index[i] = idx[i];
+  if (n == H) return BEM_OK;
+  const double mean[3] = {c->mean[0], c->mean[1], c->mean[2]};
+  std::vector<int32_t> one(n, 1);
+  std::vector<uint8_t> open(n, 0);
+  if ((rc = setup_scene(c, n, one.data(), open.data(), th.data(), mean, 4))) return rc;
+  // w_c re-projected with the lengths of the kept handles (Sec. 4.3)
+  if ((rc = geom_panelize(c, c->d_theta)) || (rc = geom_compat(c, c->d_theta, true))) return rc;
+  return cuda_check(c, cudaStreamSynchronize(S(c)), "sync");
+}
+
 int bem_set_boundary(bem_ctx* c, int n_vertices, const double* vertices, int segs_per_edge) {
   if (!c) return BEM_EINVAL;
   if (n_vertices < 3 || !vertices || segs_per_edge < 1)
@@ -602,11 +649,24 @@ static int lm_step_impl(bem_ctx* c, int64_t n, const void* xy, const void* targe
     BEM_LAUNCHED(c);
     if ((rc = jtj_build(c, xy_h ? n_h : n, xy_h ? xy_h : xy, (double*)c->H.p))) return rc;
   }
+  // Sec. 4.4 regularisers: analytic gradient and Hessian added to g and H,
+  // snapping pairs chosen here and kept for the trial losses
+  const bool reg = reg_active(c);
+  double R[2] = {0, 0};
+  if (reg) {
+    if ((rc = reg_pairs(c, c->d_theta)) || (rc = reg_add(c, c->d_theta, (double*)c->H.p, g)) ||
+        (rc = reg_loss(c, c->d_theta, c->d_scal + 2)))
+      return rc;
+    k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0, c->d_scal + 1);
+    BEM_LAUNCHED(c);
+    if ((rc = cuda_check(c, cudaMemcpyAsync(R, c->d_scal + 2, 8, cudaMemcpyDeviceToHost, S(c)), "reg")))
+      return rc;
+  }
   double gn2 = 0;
   if ((rc = cuda_check(c, cudaMemcpyAsync(&gn2, c->d_scal + 1, 8, cudaMemcpyDeviceToHost, S(c)), "norm")) ||
       (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "sync")))
     return rc;
-  const double L0 = 0.5 * s0 / double(n);
+  const double L0 = 0.5 * s0 / double(n) + R[0];
   out->grad_norm = std::sqrt(gn2);
   double best = INFINITY;
   int best_t = -1;
@@ -632,11 +692,14 @@ static int lm_step_impl(bem_ctx* c, int64_t n, const void* xy, const void* targe
     if ((rc = geom_compat(c, c->d_trial, true))) return rc;
     if ((rc = refresh(c, c->d_trial))) return rc;
     if ((rc = field_eval(c, n, xy, nullptr, target, nullptr, true))) return rc;
+    if (reg && (rc = reg_loss(c, c->d_trial, c->d_scal + 3))) return rc;
     double s1 = 0;
     if ((rc = cuda_check(c, cudaMemcpyAsync(&s1, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")) ||
+        (reg && (rc = cuda_check(c, cudaMemcpyAsync(R + 1, c->d_scal + 3, 8, cudaMemcpyDeviceToHost,
+                                                     S(c)), "reg"))) ||
         (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "sync")))
       return rc;
-    const double L1 = 0.5 * s1 / double(n);
+    const double L1 = 0.5 * s1 / double(n) + R[1];
     if (L1 < best) {
       best = L1;
       best_t = t;

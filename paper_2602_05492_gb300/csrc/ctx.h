@@ -75,7 +75,7 @@ struct bem_ctx {
   double* d_delta = nullptr;       // [nth]
   bem::Panel<double>* d_pan64 = nullptr;   // [P]
   bem::Panel<float>* d_pan32 = nullptr;    // [P]
-  double* d_compat = nullptr;      // [4C] compatibility weights a_h
+  double* d_compat = nullptr;      // [NH] compatibility weights a_h of the colour owners
   double* d_ub = nullptr;          // [Nb][3] boundary solution of the current panels
   double* d_fb = nullptr;          // [Nb][3] right-hand side
   double* d_q = nullptr;           // [Nb][3] adjoint boundary source
@@ -92,7 +92,8 @@ struct bem_ctx {
 
   // growable scratch
   bem::DevBuf part, part2, loss, gpart, jrow, phi, Hc, Mc, Dfc, Fg, lmK, lmL, lmLt, lmW, H, g,
-      tcJ, tcPart, tcMt, nearP, nearS, nearF, gwork, rend;
+      tcJ, tcPart, tcMt, nearP, nearS, nearF, gwork, rend, regw;
+  bem_reg reg{};                   // Sec. 4.4 regularisers (segment handles)
   bool pbins_valid = false;        // panel -> cell bins match the current panels
   // When set, the Gauss-Newton chunk buffers (jrow, tcJ, tcPart, gwork) are
   // taken from this context: a batch of scenes processed one after another
@@ -122,6 +123,13 @@ int geom_panelize(bem_ctx* c, const double* d_theta);
 int geom_compat(bem_ctx* c, double* d_theta, bool project);
 int geom_boundary_tables(bem_ctx* c);                  // vertices, Gauss points
 int geom_assemble(bem_ctx* c);                         // d_A
+
+// ---- regularisers and pruning of segment handles (k_reg.cu) ------------------
+bool reg_active(const bem_ctx* c);
+int reg_pairs(bem_ctx* c, const double* theta);                 // snapping pairs at theta
+int reg_add(bem_ctx* c, const double* theta, double* H, double* g);
+int reg_loss(bem_ctx* c, const double* theta, double* d_out);  // with the chosen pairs
+int reg_prune(bem_ctx* c, double thr, std::vector<double>& kept_theta, std::vector<int>& kept_idx);
 
 // ---- linear algebra (k_linalg.cu) -------------------------------------------
 int la_pinv(bem_ctx* c);   // factor bordered system, W = A^+ (double, float copies)

@@ -472,9 +472,12 @@ int bem_batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const vo
   for (int t = 0; t < n_trials; ++t)
     if (!(lambdas[t] >= 0) || !std::isfinite(lambdas[t]))
       return fail(c0, BEM_EINVAL, "bem_batch_lm: lambda must be finite and >= 0");
-  for (int s = 0; s < S; ++s)
+  for (int s = 0; s < S; ++s) {
     if (n[s] <= 0 || !xy[s] || !target[s])
       return fail(c0, BEM_EINVAL, "bem_batch_lm: every scene needs samples and targets");
+    if (reg_active(b->sc[s]))
+      return fail(c0, BEM_EINVAL, "bem_batch_lm: regularisers are applied by lm_step only");
+  }
   int rc;
   if ((rc = ctx_set_device(c0))) return rc;
   // order after the caller's stream

@@ -130,14 +130,18 @@ def test_seg_jtj_mixed(seg, mode, tol):
 
 @pytest.mark.parametrize("mode", ["bf16", "3xtf32"])
 def test_seg_lm_step_mixed(seg, mode):
-    """Mixed LM step (tensor-core J^T J with the fused gradient)."""
+    """Mixed LM step (tensor-core J^T J with the fused gradient) at a damping
+    where the step is accepted; at 1e-3 the oracle's own step raises the
+    loss more than tenfold and its size amplifies rounding by the
+    conditioning of the damped matrix."""
     bg = _bg()
     jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32}[mode]
     sc, xy, target, mean, o = seg
     sub, tsub = xy[::8], target[::8]
     m = _ctx(sc, mean, bg.BEM_MIXED, jtj_mode=jm)
-    res = m.lm_step(_t(sub, torch.float32), _t(tsub, torch.float32), [1e-3])
-    want = o.lm_step(sc.theta_init, sub, tsub, 1e-3)
+    res = m.lm_step(_t(sub, torch.float32), _t(tsub, torch.float32), [1e-1])
+    want = o.lm_step(sc.theta_init, sub, tsub, 1e-1)
+    assert want["accepted"]
     assert res["loss_before"] == pytest.approx(want["loss_before"], rel=1e-5)
     assert res["grad_norm"] == pytest.approx(np.linalg.norm(want["g"]), rel=1e-4)
     assert res["accepted"] == want["accepted"]

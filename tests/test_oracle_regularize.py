@@ -20,8 +20,30 @@ def _rand_handles(H, seed, long_frac=0.5):
     return th.reshape(-1)
 
 
+def _saturation_curvature(th, rp):
+    """The dropped part of the exact sparsity Hessian,
+    -lam s (2 tanh(rho/t) / (t rho^2)) w w^T per weight vector."""
+    n = th.size
+    D = np.zeros((n, n))
+    t = rp.sparse_t
+    for lam, off in ((rp.sparse_wd, 4), (rp.sparse_wc, 7)):
+        if not lam > 0:
+            continue
+        for h in range(n // 10):
+            w = th[10 * h + off:10 * h + off + 3]
+            rho = math.sqrt(float(w @ w) + rp.sparse_eps ** 2)
+            tn = math.tanh(rho / t)
+            i = 10 * h + off
+            D[i:i + 3, i:i + 3] -= lam * (1 - tn * tn) * (2 * tn / (t * rho * rho)) * np.outer(w, w)
+    return D
+
+
 def _fd_check(th, rp, pairs, h=1e-6):
     g, Hm = R.reg_grad_hess(th, rp, pairs)
+    # the kept Hessian is PSD; with the dropped saturation curvature added
+    # back it must be the exact Hessian of the loss
+    assert np.linalg.eigvalsh(Hm).min() >= -1e-10 * max(1.0, np.abs(Hm).max())
+    Hm = Hm + _saturation_curvature(th, rp)
     n = th.size
     gfd = np.zeros(n)
     Hfd = np.zeros((n, n))
