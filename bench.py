@@ -428,6 +428,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     e0g, e1g = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     gms = 0.0
+    ms_.profile(True)
     for _ in range(3):
         flush.zero_()
         e0g.record(stream)
@@ -436,9 +437,13 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         lseg[0] = r_["lambda_next"]
         gms += e0g.elapsed_time(e1g) / 3
+    gprof = ms_.profile_read()
+    ms_.profile(False)
     segments = {"handles": ss.n_handles, "n_theta": 10 * ss.n_handles,
                 "samples": int(xs.shape[0]), "regularisers": SEG_REG, "ms_per_step": gms,
                 "lm_iters_per_s": 1e3 / gms,
+                "kernel_share": {k: round(v[0] / (3 * gms), 4) for k, v in sorted(gprof.items())
+                                 if v[0] / (3 * gms) >= 0.005},
                 "workload": "500 random segment handles (length 0.025-0.1), 256^2 px x 16 spp, "
                             "lognormal noise with 1% fireflies"}
     ms_.close()
