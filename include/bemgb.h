@@ -304,10 +304,10 @@ int bem_fastmath_eval(bem_ctx *ctx, int which, int64_t n, const float *a, const 
 
 /* bem_vjp without any device allocation (the paper has no counterpart; this
  * is for callers, not for the method).  Some callers may not allocate GPU
- * memory while they run the hot path: work recorded into a CUDA graph
- * (allocation calls cannot be captured), real-time loops that must never
- * enter the allocator (cudaMalloc and cudaFree can stall the whole device),
- * and host programs whose own memory pool owns the GPU.  This entry point
+ * memory while they run the hot path: real-time loops that must never enter
+ * the allocator (cudaMalloc and cudaFree can stall the whole device), and
+ * host programs whose own memory pool owns the GPU and hands out no more
+ * device memory once it is set up.  This entry point
  * computes the same vector-Jacobian product as bem_vjp on a context that
  * bem_setup and bem_factor have already prepared, taking every per-call
  * buffer from one static device array of 32 MiB that the library reserves

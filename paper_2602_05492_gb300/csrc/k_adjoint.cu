@@ -501,9 +501,9 @@ int adj_vjp(bem_ctx* c, int64_t n, const void* xy, const void* resid, double* gr
 // Allocation-free adjoint.
 //
 // For callers that may not allocate device memory while the hot path runs:
-// code recorded into a CUDA graph (cudaMalloc cannot be captured), real-time
-// loops that must not enter the allocator (cudaMalloc/cudaFree can stall the
-// whole device), and hosts whose own memory pool owns the GPU.  Every
+// real-time loops that must not enter the allocator (cudaMalloc/cudaFree can
+// stall the whole device), and hosts whose own memory pool owns the GPU and
+// hands out no more device memory once it is set up.  Every
 // per-call buffer of the adjoint (per-slice partial sums, panel sums, Gauss
 // weights, refinement residuals) lives in the static array below; the
 // persistent state (panels, boundary factors) was allocated by bem_setup and

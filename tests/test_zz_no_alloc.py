@@ -1,13 +1,13 @@
 """The allocation-free adjoint (bem_vjp_noalloc) against bem_vjp, through the C ABI.
 
 This entry point serves callers that cannot allocate GPU memory while they
-run: work captured into a CUDA graph, real-time loops that must stay out of
-the allocator, and hosts whose own pool owns the GPU.  It takes its scratch
-from one static device array instead.  The test calls it twice in a row
-(the second call reuses the array the first one left behind) and compares
-both results with bem_vjp at the tolerances of the other gradient tests:
-1e-10 relative in FP64 contexts, 1e-4 relative in mixed ones.  The file is
-named to be collected last.
+run: real-time loops that must stay out of the allocator (an allocation can
+stall the whole device), and hosts whose own memory pool owns the GPU.  It
+takes its scratch from one static device array instead.  The test calls it
+twice in a row (the second call reuses the array the first one left behind)
+and compares both results with bem_vjp at the tolerances of the other
+gradient tests: 1e-10 relative in FP64 contexts, 1e-4 relative in mixed
+ones.  The file is named to be collected last.
 """
 import ctypes
 
