@@ -258,6 +258,28 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_quadrants(bg, quads, flush, stream, n):
+    """Four quadrant subdomains stepped together by one bem_batch_lm call."""
+    import torch
+    bq = bg.BEMBatch([q[0] for q in quads])
+    lq = [1e-3, 1e-2, 1e-1, 1.0]
+    bq.lm_step([q[1] for q in quads], [q[2] for q in quads], lq)
+    torch.cuda.synchronize()
+    e0q, e1q = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    qms = 0.0
+    for _ in range(2):
+        flush.zero_()
+        e0q.record(stream)
+        bq.lm_step([q[1] for q in quads], [q[2] for q in quads], lq)
+        e1q.record(stream)
+        torch.cuda.synchronize()
+        qms += e0q.elapsed_time(e1q) / 2
+    bq.close()
+    return {"subdomains": 4, "boundary": "each quadrant a square subdomain, 128 segments "
+            "per edge", "curves_per_subdomain": 8, "samples": n, "lm_trials": 4,
+            "ms_per_step": qms}
+
+
 def run_ours(args, rank, world, dist):
     import torch
     import paper_2602_05492_gb300 as bg
@@ -375,9 +397,10 @@ def run_ours(args, rank, world, dist):
     del xh
 
     # ---- four subdomains (the quadrants, Sec. 4.2), 8 curves and the samples
-    # of each quadrant, stepped together by one bem_batch_lm call
+    # of each quadrant, stepped together by one bem_batch_lm call (left out
+    # with --samples, whose leading samples do not reach every quadrant)
     quads = []
-    for qi in range(4):
+    for qi in range(4 if not args.samples else 0):
         x0, y0 = 0.5 * (qi % 2), 0.5 * (qi // 2)
         poly = [(x0, y0), (x0 + 0.5, y0), (x0 + 0.5, y0 + 0.5), (x0, y0 + 0.5)]
         sel = ((xy[:, 0] >= x0) & (xy[:, 0] < x0 + 0.5) & (xy[:, 1] >= y0) & (xy[:, 1] < y0 + 0.5))
@@ -390,23 +413,7 @@ def run_ours(args, rank, world, dist):
         mq.set_boundary(poly, 128)
         mq.factor()
         quads.append((mq, torch.from_numpy(np.ascontiguousarray(xy[sel])).to(dev), tq))
-    bq = bg.BEMBatch([q[0] for q in quads])
-    lq = [1e-3, 1e-2, 1e-1, 1.0]
-    bq.lm_step([q[1] for q in quads], [q[2] for q in quads], lq)
-    torch.cuda.synchronize()
-    e0q, e1q = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    qms = 0.0
-    for _ in range(2):
-        flush.zero_()
-        e0q.record(stream)
-        bq.lm_step([q[1] for q in quads], [q[2] for q in quads], lq)
-        e1q.record(stream)
-        torch.cuda.synchronize()
-        qms += e0q.elapsed_time(e1q) / 2
-    subdomains = {"subdomains": 4, "boundary": "each quadrant a square subdomain, 128 segments "
-                  "per edge", "curves_per_subdomain": 8, "samples": n, "lm_trials": 4,
-                  "ms_per_step": qms}
-    bq.close()
+    subdomains = run_quadrants(bg, quads, flush, stream, n) if quads else None
     for q in quads:
         q[0].close()
     del quads
