@@ -131,6 +131,16 @@ int reg_add(bem_ctx* c, const double* theta, double* H, double* g);
 int reg_loss(bem_ctx* c, const double* theta, double* d_out);  // with the chosen pairs
 int reg_prune(bem_ctx* c, double thr, std::vector<double>& kept_theta, std::vector<int>& kept_idx);
 
+// ---- float Cholesky and cluster triangular solve for large LM systems (k_chol.cu)
+// factor of the equilibrated matrix Kf (lower triangle, updated in place) into
+// Lf, diagonal-block inverses into Linv64 [ceil(n/64)][64][64]
+void chol_blocked_f32(bem_ctx* c, float* Kf, float* Lf, int n, float* Linv64, int* status,
+                      float* bad_pivot);
+int trsv_cluster_prepare(bem_ctx* c, int n);     // shared-memory size attribute
+// X += D z with (D K D) z = D Rres solved with the factor (four right-hand sides)
+void trsv_cluster_f32(bem_ctx* c, const float* Lf, const float* Linv64, int n, const double* d,
+                      const double* Rres, double* X);
+
 // ---- linear algebra (k_linalg.cu) -------------------------------------------
 int la_pinv(bem_ctx* c);   // factor bordered system, W = A^+ (double, float copies)
 // y[Nb][3] = W x[Nb][3] (transpose: W^T)

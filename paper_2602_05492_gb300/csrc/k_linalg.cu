@@ -1190,7 +1190,7 @@ __global__ void k_kkt_finish(const double* __restrict__ X, const double* __restr
 // single-CTA float solve keeps n x 4 floats in shared memory.
 constexpr int kRefineCheck = 2, kRefineMax = 10;
 constexpr double kRefineTol = 1e-14;
-constexpr int kMaxSingleCtaSolve = 12288;
+constexpr int kBlockedMinN = 2048, kMaxBlockedSolve = 32768;
 constexpr float kIndefinitePivot = -1e-2f;
 
 int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double* delta) {
@@ -1200,13 +1200,16 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
   const size_t rblk = ((size_t)n + 7) / 8;
   if ((rc = grow(c, c->lmK, nn))) return rc;
   if ((rc = grow(c, c->lmLt, sizeof(double) * 1024 * nblk))) return rc;
-  if ((rc = grow(c, c->lmW, nn + sizeof(float) * 1024 * nblk + 256))) return rc;
+  const size_t nb64 = ((size_t)n + 63) / 64;
+  if ((rc = grow(c, c->lmW, nn + sizeof(float) * std::max<size_t>(1024 * nblk, 4096 * nb64) + 256)))
+    return rc;
   if ((rc = grow(c, c->lmL, sizeof(double) * (25 * (size_t)n + 4 * rblk + 16)))) return rc;
   double* Km = (double*)c->lmK.p;
   double* Linv = (double*)c->lmLt.p;      // [n/32][32][32] inverses of the diagonal blocks
   float* Kf = (float*)c->lmW.p;           // equilibrated matrix in float (trailing updates)
   float* Lf = Kf + (size_t)n * n;         // its float Cholesky factor (lower triangle)
   float* Linvf = Lf + (size_t)n * n;      // the factor's diagonal-block inverses
+                                          // (32 x 32 blocks; 64 x 64 when blocked)
   double* R = (double*)c->lmL.p;          // [n][4] right-hand sides, then solutions
   double* cons = R + 4 * (size_t)n;       // [n][4] constraint columns
   double* Ytmp = cons + 4 * (size_t)n;    // [n][4] forward-solve result (double path)
@@ -1231,18 +1234,25 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
   // float factor of the equilibrated matrix, refined in double; the double
   // factorization is the fallback when the float one fails or stalls
   bool done = false;
-  if (c->opts.lm_solver == BEM_LM_AUTO && n <= kMaxSingleCtaSolve) {
+  // large systems: 64-column blocked factor and the cluster solve; below
+  // kBlockedMinN the 32-column step kernel and the single-CTA solve
+  const bool blocked = n >= kBlockedMinN;
+  if (c->opts.lm_solver == BEM_LM_AUTO && (blocked ? n <= kMaxBlockedSolve : true)) {
     int fst = 0;
     {
       ProfScope _pc(c, "lm_cholesky");
       k_equilibrate<<<dim3((n + 127) / 128, n), 128, 0, S(c)>>>(Km, n, Kf, dsc);
       BEM_LAUNCHED(c);
       if ((rc = cuda_check(c, cudaMemsetAsync(fstat, 0, 2 * sizeof(int), S(c)), "memset"))) return rc;
-      for (int k0 = 0; k0 < n; k0 += 32) {
-        const int tiles = (n - std::min(n, k0 + 32) + 63) / 64;
-        k_chol_step_f32<<<tiles * (tiles + 1) / 2 + 1, 256, 0, S(c)>>>(Kf, Lf, n, k0, Linvf,
-                                                                         fstat, fpiv);
-        BEM_LAUNCHED(c);
+      if (blocked) {
+        chol_blocked_f32(c, Kf, Lf, n, Linvf, fstat, fpiv);
+      } else {
+        for (int k0 = 0; k0 < n; k0 += 32) {
+          const int tiles = (n - std::min(n, k0 + 32) + 63) / 64;
+          k_chol_step_f32<<<tiles * (tiles + 1) / 2 + 1, 256, 0, S(c)>>>(Kf, Lf, n, k0, Linvf,
+                                                                           fstat, fpiv);
+          BEM_LAUNCHED(c);
+        }
       }
     }
     ProfScope _pt(c, "lm_trisolve");
@@ -1251,15 +1261,23 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
       return rc;
     const int rblk = (n + 7) / 8;
     const size_t smem = sizeof(float) * 4 * (size_t)n;
-    if (smem > 48 * 1024 &&
-        (rc = cuda_check(c, cudaFuncSetAttribute(k_trsv_f32_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attribute")))
+    if (blocked) {
+      if ((rc = trsv_cluster_prepare(c, n))) return rc;
+    } else if (smem > 48 * 1024 &&
+               (rc = cuda_check(c, cudaFuncSetAttribute(k_trsv_f32_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attribute"))) {
       return rc;
+    }
     double eta = 1.0, eta_prev = 2.0;
     for (int it = 0; it < kRefineMax; ++it) {
-      k_trsv_f32_single<<<1, 1024, smem, S(c)>>>(Lf, Linvf, n, dsc, Rres, Xs);
+      if (blocked) {
+        trsv_cluster_f32(c, Lf, Linvf, n, dsc, Rres, Xs);
+      } else {
+        k_trsv_f32_single<<<1, 1024, smem, S(c)>>>(Lf, Linvf, n, dsc, Rres, Xs);
+        BEM_LAUNCHED(c);
+      }
       k_resid4<<<rblk, 256, 0, S(c)>>>(Km, n, R, Xs, Rres, epart);
       k_backward_error<<<1, 256, 0, S(c)>>>(epart, rblk, eta_d);
-      c->launches += 3;
+      c->launches += 2;
       if (it + 1 < kRefineCheck) continue;
       double h[2];
       if ((rc = cuda_check(c, cudaMemcpyAsync(h, eta_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, S(c)), "eta")) ||

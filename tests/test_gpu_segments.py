@@ -184,3 +184,37 @@ def test_seg_argument_errors():
     th[5] = np.nan
     with pytest.raises(bg.BemError):
         m.setup_segments(1, th, np.zeros(3))
+
+
+@pytest.mark.parametrize("Hn", [205, 211])
+def test_seg_blocked_factor_large_system(Hn):
+    """n_theta = 2,050 and 2,110 use the 64-column blocked float Cholesky and
+    the cluster triangular solve (ragged last blocks of 2 and 62 rows).  At
+    this damping the refinement converges on its own (no double factor
+    runs) and the step matches the oracle's and the double solver's."""
+    bg = _bg()
+    sc = gen.make_segment_scene("seg500", H=Hn, W=32, spp=4, seed=5 + Hn)
+    xy = gen.make_samples(sc.W, sc.spp, sc.seed)
+    o = oracle.Oracle.segments(Hn, sc.mean_true, segs_per_side=64)
+    target = gen.add_noise(o.eval(oracle.project_compat(o.geo, sc.theta_true), xy), sc.noise,
+                           sc.seed)
+    mean = np.minimum(target, 1.0).mean(0)
+    o.mean = mean
+    lam = 1e-1
+    want = o.lm_step(sc.theta_init, xy, target, lam)
+    got = {}
+    for solver in (bg.BEM_LM_AUTO, bg.BEM_LM_FP64):
+        m = bg.BEM(precision=bg.BEM_FP64, segs_per_side=64, lm_solver=solver)
+        m.setup_segments(Hn, sc.theta_init, mean)
+        m.factor()
+        m.profile(True)
+        res = m.lm_step(_t(xy, torch.float64), _t(target, torch.float64), [lam])
+        prof = m.profile_read()
+        m.profile(False)
+        if solver == bg.BEM_LM_AUTO:
+            assert "lm_cholesky" in prof and "lm_cholesky_fp64" not in prof
+        assert res["accepted"] == want["accepted"]
+        assert res["loss_after"] == pytest.approx(want["loss_after"], rel=1e-9)
+        got[solver] = m.get_params()
+        assert _rel(got[solver], want["theta"]) < 1e-9
+    assert _rel(got[bg.BEM_LM_AUTO], got[bg.BEM_LM_FP64]) < 1e-9
