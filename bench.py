@@ -135,9 +135,13 @@ FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12
 
 
 def step_work(name, n, P, Nb, nc):
-    """(flops of one LM step's launches of `name`, bound) for the modelled kernels."""
-    if name == "k_field":            # evaluation at the current and at the trial parameters
-        return 2.0 * n * (P * FLOP_FWD_HANDLE + Nb * FLOP_FWD_BOUND), "alu"
+    """(flops of one LM step's launches of `name`, bound) for the modelled
+    kernels; for k_field the flops of one launch (every launch evaluates all
+    samples, and the step has one or two of them)."""
+    if name == "k_field":            # one evaluation of every sample (per launch)
+        return n * (P * FLOP_FWD_HANDLE + Nb * FLOP_FWD_BOUND), "alu_per_launch"
+    if name == "k_field_bnd":        # boundary term of every sample, in chunks
+        return float(n) * Nb * FLOP_FWD_BOUND, "alu"
     if name == "k_frows":            # all samples, plus the 3 Nb boundary Gauss points
         return float(n + 3 * Nb) * P * FLOP_FROWS_PAIR, "alu"
     if name == "tc_jrows":           # J^T = M_c^T Phi^T (+ F^T) for 3 channels
@@ -181,7 +185,10 @@ def rooflines(prof, steps, n, P, Nb, nc, cfg=CFG):
         work, bound = step_work(name, n, P, Nb, nc)
         if work is None or not cnt:
             continue
-        per_launch = work * steps / cnt
+        if bound == "alu_per_launch":
+            per_launch, bound = work, "alu"
+        else:
+            per_launch = work * steps / cnt
         ach = per_launch / (ms / cnt / 1e3) / 1e12
         if bound == "alu":
             peak, psrc = FP32_PEAK_TFLOPS, "FP32: 128 lanes x 2 x 152 SMs x 2070 MHz (derived)"

@@ -634,16 +634,28 @@ static int lm_step_impl(bem_ctx* c, int64_t n, const void* xy, const void* targe
   // current lengths (the fixed-endpoint constraint of the step)
   if ((rc = refresh(c, c->d_theta))) return rc;
   if ((rc = geom_compat(c, c->d_theta, false))) return rc;
-  if ((rc = field_eval(c, n, xy, nullptr, target, resid, true))) return rc;
   double s0 = 0;
-  if ((rc = cuda_check(c, cudaMemcpyAsync(&s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
-    return rc;
-  if (!xy_h && jtj_gives_gradient(c)) {
+  if (!xy_h && jtj_fuses_eval(c)) {
+    // one pass over the samples: the residual at theta (handle term as F w,
+    // near-field correction, boundary term), g = (1/n) J^T r (Eq.
+    // (lossjacobian)) and H from the same J rows
+    if ((rc = jtj_build(c, n, xy, (double*)c->H.p, resid, g, target))) return rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(&s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
+      return rc;
+    k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0, c->d_scal + 1);
+    BEM_LAUNCHED(c);
+  } else if (!xy_h && jtj_gives_gradient(c)) {
+    if ((rc = field_eval(c, n, xy, nullptr, target, resid, true))) return rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(&s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
+      return rc;
     // g = (1/n) J^T r from the J rows that also build H (Eq. (lossjacobian))
     if ((rc = jtj_build(c, n, xy, (double*)c->H.p, resid, g))) return rc;
     k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0, c->d_scal + 1);
     BEM_LAUNCHED(c);
   } else {
+    if ((rc = field_eval(c, n, xy, nullptr, target, resid, true))) return rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(&s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
+      return rc;
     if ((rc = adj_vjp(c, n, xy, resid, g))) return rc;
     k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0 / double(n), c->d_scal + 1);
     BEM_LAUNCHED(c);

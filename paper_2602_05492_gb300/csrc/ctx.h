@@ -158,6 +158,13 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
 
 // ---- forward field (k_field.cu) --------------------------------------------------
 // u at n points into out (sample type), optional residual/loss; loss sum -> d_scal[0]
+// residual and loss partials of m points whose handle term (with its near-field
+// correction) is given in hand [m][3]: the boundary term, the mean colour and
+// the clamp are added here.  loss_part receives field_blocks(m) block sums.
+int field_finish_hand(bem_ctx* c, int64_t m, const float* xy, const double* hand,
+                      const float* target, float* resid, double* loss_part);
+int64_t field_blocks(int64_t m);
+int field_sum_loss(bem_ctx* c, const double* loss_part, int64_t nblk);   // -> d_scal[0]
 int field_eval(bem_ctx* c, int64_t n, const void* xy, void* out, const void* target,
                void* resid, bool want_loss);
 int field_rhs(bem_ctx* c);           // d_fb from the current panels
@@ -175,6 +182,8 @@ int field_batch_launch(bem_ctx* c, const BatchJob* jobs, int njobs, const int64_
 // ---- near field of the mixed path (k_near.cu) ------------------------------------
 // out[n][3] = double sum over the near panels of each point
 int near_forward(bem_ctx* c, int64_t n, const float* xy, double* out);
+// per point, sum over its near pairs of (double value - the F rows' float value)
+int near_forward_minus_float(bem_ctx* c, int64_t n, const float* xy, double* out);
 // out[P][11] = double adjoint sums of each panel over its near points
 int near_adjoint(bem_ctx* c, int64_t n, const float* xy, const float* w, double* out);
 
@@ -184,9 +193,13 @@ int adj_vjp(bem_ctx* c, int64_t n, const void* xy, const void* resid, double* gr
 // ---- Gauss-Newton matrix (k_jtj.cu) ----------------------------------------------
 // H = (1/n) J^T J; with resid (sample type [n][3]) and g also g = (1/n) J^T r
 // when jtj_gives_gradient() (tensor-core modes of the mixed path)
+// With target (tensor-core modes only), the residual at the current theta is
+// formed inside the pass instead of read: resid is written, the loss sum
+// sum |r|^2 lands in d_scal[0] (the handle term as F w, see jtj_tc).
 int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H, const void* resid = nullptr,
-              double* g = nullptr);
+              double* g = nullptr, const void* target = nullptr);
 bool jtj_gives_gradient(const bem_ctx* c);
+bool jtj_fuses_eval(const bem_ctx* c);   // jtj_build accepts a target
 
 // ---- tensor-core contractions (k_gemm_tc.cu) ----------------------------------------
 int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const void* B, int ldb,

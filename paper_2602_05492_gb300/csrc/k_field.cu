@@ -446,8 +446,8 @@ static FieldArgs<T> make_args(bem_ctx* c) {
 }
 
 template <typename T>
-static void launch_field(bem_ctx* c, const FieldArgs<T>& a, dim3 grid) {
-  ProfScope _ps(c, a.split_out ? "k_field_rhs" : "k_field");
+static void launch_field(bem_ctx* c, const FieldArgs<T>& a, dim3 grid, const char* name = nullptr) {
+  ProfScope _ps(c, name ? name : a.split_out ? "k_field_rhs" : "k_field");
   const bool same = c->opts.eps_c == c->opts.eps_d;
   if constexpr (sizeof(T) == 4) {
     const bool near = c->opts.near_factor > 0;
@@ -507,6 +507,32 @@ static int field_eval_t(bem_ctx* c, int64_t n, const void* xy, void* out, const 
 }
 
 FieldArgs<float> field_args_f32(bem_ctx* c) { return make_args<float>(c); }
+
+int64_t field_blocks(int64_t m) { return (m + (int64_t)kFB * kSptEval - 1) / ((int64_t)kFB * kSptEval); }
+
+int field_finish_hand(bem_ctx* c, int64_t m, const float* xy, const double* hand,
+                      const float* target, float* resid, double* loss_part) {
+  FieldArgs<float> a = make_args<float>(c);
+  a.P = 0;                 // no panel loop: the handle term comes in as hand
+  a.xy = xy;
+  a.n = m;
+  a.ub = c->d_ub;
+  a.mean0 = c->mean[0]; a.mean1 = c->mean[1]; a.mean2 = c->mean[2];
+  a.target = target;
+  a.resid = resid;
+  a.near_add = hand;
+  a.loss_part = loss_part;
+  const int64_t nblk = field_blocks(m);
+  if (nblk > 0) launch_field<float>(c, a, dim3((unsigned)nblk), "k_field_bnd");
+  return cuda_check(c, cudaGetLastError(), "k_field boundary");
+}
+
+int field_sum_loss(bem_ctx* c, const double* loss_part, int64_t nblk) {
+  if (nblk <= 0) return cuda_check(c, cudaMemsetAsync(c->d_scal, 0, 8, S(c)), "memset");
+  k_sum_fixed<<<1, 1024, 0, S(c)>>>(loss_part, nblk, c->d_scal);
+  BEM_LAUNCHED(c);
+  return cuda_check(c, cudaGetLastError(), "loss sum");
+}
 
 int field_batch_launch(bem_ctx* c, const BatchJob* jobs, int njobs, const int64_t* total_tiles,
                        unsigned long long* counter, int spt, int blocks_per_sm) {

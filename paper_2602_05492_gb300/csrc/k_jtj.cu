@@ -602,11 +602,62 @@ static int jtj_stacked_rhs(bem_ctx* c, bool solve = true) {
 // from the same J rows (Eq. (lossjacobian)): the handle part as a double
 // GEMV over F^T per chunk, the boundary part as q^T M_c = (A^+T q)^T Df_c
 // with q = sum_s phi_s r_s summed while the Phi rows are written.
+// Handle term of the colour at theta from the F rows.  The colour is linear
+// in the jumps, so f_c(x_s) = sum over colour owners h of F_c[s][w_d col h]
+// w_d,hc + F_c[s][w_c col h] w_c,hc: the colour columns of F_c times the
+// current jumps (F^T rows pp NH .. (pp + 2) NH - 1 of channel c).  hand[s][c]
+// += that (it already holds the near-field correction).  Thread = point; the
+// jumps staged as float in shared memory, [c][2 NH].
+__global__ void __launch_bounds__(256) k_hand_fw(const float* __restrict__ Ft, int ldf, int nc,
+                                                 int pp, int NH, const double* __restrict__ theta,
+                                                 int m, double* __restrict__ hand) {
+  extern __shared__ float wsh[];
+  const int stride = pp + 6, nw = 2 * NH;
+  for (int e = threadIdx.x; e < 3 * nw; e += blockDim.x) {
+    const int c = e / nw, k = e % nw, h = k % NH, isc = k / NH;
+    wsh[e] = float(theta[(size_t)h * stride + pp + 3 * isc + c]);
+  }
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= m) return;
+  for (int c = 0; c < 3; ++c) {
+    const float* f = Ft + ((size_t)c * nc + (size_t)pp * NH) * ldf + s;
+    const float* w = wsh + c * nw;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int k = 0;
+    for (; k + 8 <= nw; k += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = f[(size_t)(k + u) * ldf];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = fmaf(v[u], w[k + u], acc[u]);
+    }
+    for (; k < nw; ++k) acc[0] = fmaf(f[(size_t)k * ldf], w[k], acc[0]);
+    const float t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    hand[3 * (size_t)s + c] += double(t);
+  }
+}
+
+// The residual comes out of the J-row pass when reading the colour rows of F
+// (24 n_owner bytes per point) is cheaper than evaluating every pair again
+// (about 79 flops per panel): with more than six panels per colour owner,
+// i.e. Bezier curves of more than 24 panels, not for one-panel segment
+// handles.
+bool jtj_fuses_eval(const bem_ctx* c) {
+  return jtj_gives_gradient(c) && 6 * (size_t)c->sc.NH * sizeof(float) <= 48 * 1024 &&
+         c->sc.P > 6 * c->sc.NH;
+}
+
 static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
-                  const float* resid, double* gout) {
+                  const float* resid, double* gout, const float* target) {
   int rc;
   int C = c->sc.C, nc = c->sc.nc, Nb = c->bd.Nb, nth = c->sc.nth;
   const bool want_g = resid && gout;
+  // with target the residual at theta is formed here, chunk by chunk, from
+  // the F rows (handle term F w), the near-field correction and the
+  // boundary term, before the chunk's Phi rows and J rows need it
+  const bool fuse_r = want_g && target;
+  if (target && !want_g) return fail(c, BEM_EINVAL, "jtj: a target needs the residual and gradient outputs");
   if ((rc = jtj_stacked_rhs<float>(c, false))) return rc;
   const size_t es = x3 ? 2 * sizeof(float) : sizeof(__nv_bfloat16);   // bytes per element (all parts)
   // M_c^T, [3 nc][Nb]
@@ -658,6 +709,15 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   double* gh = (double*)w->gwork.p;
   double* qp = gh + gh_b / sizeof(double);
   double* gb = qp + (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
+  double* hand = nullptr;
+  double* lossp = nullptr;
+  int64_t lblk = 0;
+  if (fuse_r) {
+    if ((rc = grow(c, c->nearF, sizeof(double) * 3 * (size_t)chunk))) return rc;
+    if ((rc = grow(c, c->loss, sizeof(double) * (size_t)(field_blocks(n) + nchunks + 1)))) return rc;
+    hand = (double*)c->nearF.p;
+    lossp = (double*)c->loss.p;
+  }
   if ((rc = cuda_check(c, cudaMemsetAsync(part, 0, part_b, S(c)), "memset"))) return rc;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
   int ci = 0;
@@ -667,6 +727,25 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
     return rc;
   for (int64_t s0 = 0; s0 < n; s0 += chunk, ++ci) {
     const int m = (int)std::min<int64_t>(chunk, n - s0);
+    launch_frows<float, true>(c, xy + 2 * s0, m, F, ld);
+    if (fuse_r) {
+      if (c->opts.near_factor > 0) {
+        if ((rc = near_forward_minus_float(c, m, xy + 2 * s0, hand))) return rc;
+      } else if ((rc = cuda_check(c, cudaMemsetAsync(hand, 0, sizeof(double) * 3 * (size_t)m, S(c)),
+                                  "memset"))) {
+        return rc;
+      }
+      {
+        ProfScope _ph(c, "k_hand_fw");
+        k_hand_fw<<<(m + 255) / 256, 256, sizeof(float) * 6 * (size_t)c->sc.NH, S(c)>>>(
+            F, ld, nc, c->sc.pp, c->sc.NH, c->d_theta, m, hand);
+        BEM_LAUNCHED(c);
+      }
+      if ((rc = field_finish_hand(c, m, xy + 2 * s0, hand, target + 3 * s0,
+                                  const_cast<float*>(resid) + 3 * s0, lossp + lblk)))
+        return rc;
+      lblk += field_blocks(m);
+    }
     {
       ProfScope _pp(c, "k_phi_rows");
       const int sl = want_g ? qslices : (int)std::max<int64_t>(1, std::min<int64_t>(64, (m + 4095) / 4096));
@@ -684,7 +763,6 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
                                                (void*)phi[0], nullptr, q);
       BEM_LAUNCHED(c);
     }
-    launch_frows<float, true>(c, xy + 2 * s0, m, F, ld);
     if (want_g && !fused_g) {
       ProfScope _pg(c, "k_ft_gemv");
       k_ft_gemv<<<dim3((3 * nc + 7) / 8, kGemvSegs), 256, 0, S(c)>>>(
@@ -699,6 +777,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
     const void* Jc[2] = {J[0], J[1]};
     if ((rc = tc_syrk(c, x3, nc, m, Jc, ld, part, splits))) return rc;
   }
+  if (fuse_r && (rc = field_sum_loss(c, lossp, lblk))) return rc;
   k_syrk_reduce<<<dim3((nc + 127) / 128, nc, 3), 128, 0, S(c)>>>(part, splits, nc,
                                                                   (double*)c->Hc.p);
   k_h_assemble<<<dim3((nth + 127) / 128, nth), 128, 0, S(c)>>>((const double*)c->Hc.p, c->sc.pp, c->sc.NH,
@@ -733,12 +812,15 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   return BEM_OK;
 }
 
-int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H, const void* resid, double* g) {
+int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H, const void* resid, double* g,
+              const void* target) {
+  if (target && !jtj_fuses_eval(c))
+    return fail(c, BEM_EINVAL, "jtj: residual formed in the pass only in the tensor-core modes");
   if (c->opts.precision == BEM_FP64) return jtj_t<double>(c, n, (const double*)xy, H);
   if (c->opts.jtj_mode == BEM_JTJ_BF16)
-    return jtj_tc(c, n, (const float*)xy, H, false, (const float*)resid, g);
+    return jtj_tc(c, n, (const float*)xy, H, false, (const float*)resid, g, (const float*)target);
   if (c->opts.jtj_mode == BEM_JTJ_3XTF32)
-    return jtj_tc(c, n, (const float*)xy, H, true, (const float*)resid, g);
+    return jtj_tc(c, n, (const float*)xy, H, true, (const float*)resid, g, (const float*)target);
   return jtj_t<float>(c, n, (const float*)xy, H);
 }
 

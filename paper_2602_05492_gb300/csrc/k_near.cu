@@ -216,7 +216,11 @@ static int build_bins(bem_ctx* c, DevBuf& buf, bool panels, int64_t n, const flo
 // ---------------------------------------------------------------------------
 // double evaluation of the near pairs
 
-template <bool SAME>
+// SUBF: the sum of (double - float) pair values instead, the float value
+// being the one the F rows hold (frame_rn, layer_grad_hat); added to the
+// float handle term F w it gives the same near-field treatment as the
+// evaluation kernel's skip-and-add.
+template <bool SAME, bool SUBF>
 __global__ void k_near_forward(const float* __restrict__ xy, int64_t n,
                                const Panel<float>* __restrict__ pan32,
                                const Panel<double>* __restrict__ pan64, Bins b, float near2,
@@ -235,6 +239,15 @@ __global__ void k_near_forward(const float* __restrict__ xy, int64_t n,
     s0 += -q.wd[0] * v.Dl + q.wc[0] * v.S;
     s1 += -q.wd[1] * v.Dl + q.wc[1] * v.S;
     s2 += -q.wd[2] * v.Dl + q.wc[2] * v.S;
+    if constexpr (SUBF) {
+      const Panel<float>& pf = pan32[p];
+      const Frame<float> ff = frame_rn(pf.ax, pf.ay, pf.tx, pf.ty, pf.L, x, y);
+      const GradHat g = layer_grad_hat(ff, ff.h * ff.h, float(ec2), float(ed2), SAME);
+      constexpr float kOut = float(-kInv2Pi);   // the hat values carry -2 pi
+      s0 -= double(kOut * (-pf.wd[0] * g.D + pf.wc[0] * g.S));
+      s1 -= double(kOut * (-pf.wd[1] * g.D + pf.wc[1] * g.S));
+      s2 -= double(kOut * (-pf.wd[2] * g.D + pf.wc[2] * g.S));
+    }
   }
   out[3 * i] = s0;
   out[3 * i + 1] = s1;
@@ -330,7 +343,7 @@ __global__ void __launch_bounds__(32 * kNearWarps)
     for (int k = 0; k < 11; ++k) out[(size_t)p * 11 + k] = acc[k];
 }
 
-int near_forward(bem_ctx* c, int64_t n, const float* xy, double* out) {
+static int near_forward_t(bem_ctx* c, int64_t n, const float* xy, double* out, bool subf) {
   int rc;
   Bins b;
   if (!c->pbins_valid) {
@@ -348,15 +361,23 @@ int near_forward(bem_ctx* c, int64_t n, const float* xy, double* out) {
   const float near2 = (float)(c->opts.near_factor * c->opts.near_factor);
   const double ec2 = c->opts.eps_c * c->opts.eps_c, ed2 = c->opts.eps_d * c->opts.eps_d;
   ProfScope _ps(c, "k_near_forward");
-  if (c->opts.eps_c == c->opts.eps_d)
-    k_near_forward<true><<<(unsigned)((n + 127) / 128), 128, 0, S(c)>>>(xy, n, c->d_pan32, c->d_pan64,
-                                                                       b, near2, ec2, ed2, out);
-  else
-    k_near_forward<false><<<(unsigned)((n + 127) / 128), 128, 0, S(c)>>>(xy, n, c->d_pan32,
-                                                                        c->d_pan64, b, near2, ec2,
-                                                                        ed2, out);
+  const unsigned grid = (unsigned)((n + 127) / 128);
+  const bool same = c->opts.eps_c == c->opts.eps_d;
+#define BEM_NEAR_FW(SM_, SUB_) \
+  k_near_forward<SM_, SUB_><<<grid, 128, 0, S(c)>>>(xy, n, c->d_pan32, c->d_pan64, b, near2, ec2, ed2, out)
+  if (same) { if (subf) BEM_NEAR_FW(true, true); else BEM_NEAR_FW(true, false); }
+  else { if (subf) BEM_NEAR_FW(false, true); else BEM_NEAR_FW(false, false); }
+#undef BEM_NEAR_FW
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "near forward");
+}
+
+int near_forward(bem_ctx* c, int64_t n, const float* xy, double* out) {
+  return near_forward_t(c, n, xy, out, false);
+}
+
+int near_forward_minus_float(bem_ctx* c, int64_t n, const float* xy, double* out) {
+  return near_forward_t(c, n, xy, out, true);
 }
 
 int near_adjoint(bem_ctx* c, int64_t n, const float* xy, const float* w, double* out) {

@@ -311,6 +311,26 @@ def test_lm_step_mixed(cfg1, mode):
     assert res["loss_after"] == pytest.approx(want["loss_after"], rel=2e-2 if mode == "bf16" else 1e-4)
 
 
+@pytest.mark.parametrize("nf", [0.0, 0.5, 1000.0])
+@pytest.mark.parametrize("mode", ["bf16", "3xtf32"])
+def test_lm_step_residual_from_jrow_pass(cfg1, mode, nf):
+    """In the tensor-core modes the LM step forms the residual at theta inside
+    the J-row pass: the handle term as F w (the colour is linear in the
+    jumps), the near pairs corrected to their double values, the boundary
+    term added.  Its loss matches the evaluation kernel's (bem_loss) to float
+    rounding and the oracle's, with no near field, the default one and every
+    pair near."""
+    bg = _bg()
+    jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32}[mode]
+    sc, xy, target, mean, o = cfg1
+    m = _ctx(sc, mean, bg.BEM_MIXED, jtj_mode=jm, near_factor=nf)
+    x32, t32 = _t(xy, torch.float32), _t(target, torch.float32)
+    L = m.loss(x32, t32)
+    res = m.lm_step(x32, t32, [1e-3])
+    assert res["loss_before"] == pytest.approx(L, rel=2e-6)
+    assert res["loss_before"] == pytest.approx(o.loss(sc.theta_init, xy, target), rel=1e-5)
+
+
 def test_mixed_all_pairs_near(cfg1):
     """near_factor = 1000 sends every handle pair through the double near-field
     kernels: colours and gradient then match the oracle to float rounding of
