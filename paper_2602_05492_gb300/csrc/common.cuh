@@ -223,10 +223,14 @@ __device__ __forceinline__ LayerVals<T> layer_values(const Frame<T>& f, T eps_c2
 
 // Forward pair of the float loops, with the layer constants taken out
 // (multiplied by -2 pi) so that they fold into the staged jumps of PanelF:
-//   Dh = (h/h'_d) Phi_d                                              = -2 pi Dl
-//   Sh = (1/2) L (log q2 - 2) + (1/2) t1 log1p(L(t1+t2)/q1) + h'_c Phi_c = -2 pi S
-// hh = h*h.  Own transcendentals (fastmath.cuh), one rsqrt for both h' and
-// h/h', approximate divisions.
+//   Dh = (h/h'_d) Phi_d                                        = -2 pi Dl
+//   Sh = (1/2)(t2 log q2 - t1 log q1) - L + h'_c Phi_c          = -2 pi S
+// hh = h*h.  Own arctangent (fastmath.cuh), both logarithms by the MUFU
+// base-2 logarithm, one rsqrt for both h' and h/h'.  The difference of the
+// two log terms loses to cancellation when t1 and t2 are far larger than L,
+// but only about one float ulp of |t log q| (q <= 2 on the unit square)
+// in absolute terms; pairs close to the panel, where it would matter
+// relative to the value, are the near pairs evaluated in double.
 __device__ __forceinline__ void pair_fwd_f(const Frame<float>& f, float hh, float eps_c2,
                                            float eps_d2, bool same_eps, float& Dh, float& Sh) {
   const float hc2 = hh + eps_c2;
@@ -236,9 +240,8 @@ __device__ __forceinline__ void pair_fwd_f(const Frame<float>& f, float hh, floa
   const float q1 = fmaf(f.t1, f.t1, hc2);
   const float q2 = fmaf(f.t2, f.t2, hc2);
   const float phic = fm_atan2_ypos(hc * f.L, hc2 + tt);
-  const float a = fmaf(__log2f(q2), kLn2Halff, -1.f);          // (1/2) log q2 - 1
-  const float lph = fm_log1p_half(__fdividef(f.L * (f.t1 + f.t2), q1));
-  Sh = fmaf(hc, phic, fmaf(f.t1, lph, f.L * a));
+  const float d = fmaf(f.t2, __log2f(q2), -f.t1 * __log2f(q1));   // t2 lg q2 - t1 lg q1
+  Sh = fmaf(hc, phic, fmaf(d, kLn2Halff, -f.L));
   if (same_eps) {
     Dh = f.h * rc * phic;
   } else {
