@@ -305,7 +305,7 @@ __device__ __forceinline__ LayerGrad<T> layer_grad(const Frame<T>& f, T eps_c2, 
 //   St1 = -(1/2) log q1             Dt1 = -h/q1
 //   St2 =  (1/2) log q2             Dt2 =  h/q2
 //   Sh_ = (h/h'_c) Phi_c            Dh_ = (1/h'^2)[eps_d^2 Phi_d/h' - h^2 L (h'^2 - t1 t2)/(q1 q2)]
-// with log q1 = log q2 - log1p(L(t1+t2)/q1) (q2 = q1 + L(t1+t2)).
+// with both logarithms from the MUFU base-2 logarithm.
 struct GradHat {
   float S, D;
   float St1, St2, Sh;
@@ -322,10 +322,10 @@ __device__ __forceinline__ GradHat layer_grad_hat(const Frame<float>& f, float h
   const float q1 = fmaf(f.t1, f.t1, hc2);
   const float q2 = fmaf(f.t2, f.t2, hc2);
   const float phic = fm_atan2_ypos(hc * f.L, hc2 + tt);
+  const float lq1h = __log2f(q1) * kLn2Halff;                  // (1/2) log q1
   const float lq2h = __log2f(q2) * kLn2Halff;                  // (1/2) log q2
-  const float lph = fm_log1p_half(__fdividef(f.L * (f.t1 + f.t2), q1));
-  g.S = fmaf(hc, phic, fmaf(f.t1, lph, f.L * (lq2h - 1.f)));
-  g.St1 = lph - lq2h;
+  g.S = fmaf(hc, phic, fmaf(f.t2, lq2h, fmaf(-f.t1, lq1h, -f.L)));
+  g.St1 = -lq1h;
   g.St2 = lq2h;
   g.Sh = f.h * rc * phic;
   float hd2, rd, phid, r1, r2;
