@@ -124,20 +124,23 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
   umma::fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // a diagonal Gram tile multiplies a tile of J^T by itself: one load serves
+  // as both operands
+  const bool same_ab = g.mode == EPI_SYRK && ti == tj;
   if (warp == 0 && lane == 0) {
     // TMA producer
     for (int it = 0; it < nk; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
       if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err)) break;
-      umma::mbar_expect_tx(&full[s], PARTS * TILE_BYTES);
+      umma::mbar_expect_tx(&full[s], (same_ab ? PARTS / 2 : PARTS) * TILE_BYTES);
       const int kc = kb + it * BK;
       uint8_t* st = smem + (size_t)s * PARTS * TILE_BYTES;
       umma::tma_load_2d(st, &tA, &full[s], kc, arow);
-      umma::tma_load_2d(st + TILE_BYTES, &tB, &full[s], kc, brow);
+      if (!same_ab) umma::tma_load_2d(st + TILE_BYTES, &tB, &full[s], kc, brow);
       if (X3) {
         umma::tma_load_2d(st + 2 * TILE_BYTES, &tA2, &full[s], kc, arow);
-        umma::tma_load_2d(st + 3 * TILE_BYTES, &tB2, &full[s], kc, brow);
+        if (!same_ab) umma::tma_load_2d(st + 3 * TILE_BYTES, &tB2, &full[s], kc, brow);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
       if (!umma::mbar_wait(&full[s], ph, g.err)) break;
       umma::fence_after();
       const uint32_t a0 = umma::smem_u32(smem + (size_t)s * PARTS * TILE_BYTES);
-      const uint32_t b0 = a0 + TILE_BYTES;
+      const uint32_t b0 = same_ab ? a0 : a0 + TILE_BYTES;
       // each instruction consumes 32 bytes of every row (16 bf16 or 8 tf32)
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
