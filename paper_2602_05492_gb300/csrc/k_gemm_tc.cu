@@ -19,6 +19,10 @@
 //              tf32 hi/lo pair of D + F in the 3xtf32 scheme
 //   EPI_SYRK   one upper-triangular 128 x 128 block of J_c^T J_c over a K
 //              slice of samples, added to that slice's fp32 partial sum
+// The bf16 J rows run in a persistent, warp-specialised variant
+// (k_tc_jrows_pers): one CTA per SM, a producer warp, an MMA warp and eight
+// epilogue warps, with two TMEM accumulators so that a tile's epilogue
+// overlaps the next tile's MMAs.
 // Every wait is bounded (about one second); a timeout sets *err and the CTA
 // drains and frees its TMEM before returning.
 #include <cuda_bf16.h>
@@ -311,6 +315,224 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
   if (warp == 0) umma::tmem_dealloc(tmem, 128);
 }
 
+// ---- bf16 J rows, persistent ----------------------------------------------
+// One CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (t = row tile + col tile * row tiles, so consecutive tiles share their Phi
+// tile).  Warp 0 lane 0 streams A/B slabs through a PSTAGES ring (TMA), warp 1
+// lane 0 issues the MMAs into one of two 128-column TMEM accumulators, and
+// warps 2..9 drain the other: warp w owns TMEM lanes 32 (w % 4) .. +31 and
+// the columns 64 ((w - 2) / 4) .. +63 of them.  So the epilogue of a tile
+// (F rows added, bf16 packing, the handle part of the gradient, coalesced
+// stores) overlaps the MMAs of the next.  Per tile the F rows are copied by
+// cp.async into fs (issued while the previous tile's rows are stored), the
+// bf16 result goes to jb (16-byte chunk k of row r at k ^ (r & 7)).
+constexpr int PSTAGES = 3;
+constexpr int kPersThreads = 320;           // 2 control warps + 8 epilogue warps
+constexpr int kPersSmem = 1024 + PSTAGES * 2 * TILE_BYTES + BM * BN * 4 + BM * BN * 2 +
+                          3 * BN * 4 + 2 * BM * 4 + 256;
+
+__device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kPersThreads, 1)
+    k_tc_jrows_pers(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+                    TcArgs g) {
+  constexpr int BK = Scheme<false>::BK;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* fs = reinterpret_cast<float*>(smem + PSTAGES * 2 * TILE_BYTES);      // [BM][BN] F rows
+  uint8_t* jb = reinterpret_cast<uint8_t*>(fs + BM * BN);                    // [BM][256 B] bf16
+  float* rs = reinterpret_cast<float*>(jb + BM * BN * 2);                    // [BN][3] residuals
+  float* gsum = rs + 3 * BN;                                                 // [2][BM]
+  uint64_t* full = reinterpret_cast<uint64_t*>(gsum + 2 * BM);
+  uint64_t* empty = full + PSTAGES;
+  uint64_t* tfull = empty + PSTAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  int* fail_flag = reinterpret_cast<int*>(tmem_slot + 1);   // set when an epilogue wait gave up
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rtiles = (g.M + BM - 1) / BM, ctiles = (g.N + BN - 1) / BN;
+  const int ntiles = rtiles * ctiles;
+  const int nk = (g.K + BK - 1) / BK;
+  if (threadIdx.x == 0) {
+    *fail_flag = 0;
+    for (int s = 0; s < PSTAGES; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      umma::mbar_init(&tfull[b], 1);
+      umma::mbar_init(&tempty[b], 8);
+    }
+    umma::fence_barrier_init();
+  }
+  if (warp == 0) umma::tmem_alloc(tmem_slot, 256);
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer over all of this CTA's tiles
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int arow = (t % rtiles) * BM, brow = (t / rtiles) * BN;
+        for (int kk = 0; kk < nk; ++kk, ++it) {
+          const int s = it % PSTAGES;
+          const uint32_t ph = (it / PSTAGES) & 1;
+          if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err)) { ok = false; break; }
+          umma::mbar_expect_tx(&full[s], 2 * TILE_BYTES);
+          uint8_t* st = smem + (size_t)s * 2 * TILE_BYTES;
+          umma::tma_load_2d(st, &tA, &full[s], kk * BK, arow);
+          umma::tma_load_2d(st + TILE_BYTES, &tB, &full[s], kk * BK, brow);
+        }
+      }
+      // the last loads of every slot have landed before the CTA can leave
+      for (int j = it > PSTAGES ? it - PSTAGES : 0; j < it; ++j)
+        umma::mbar_wait(&full[j % PSTAGES], (j / PSTAGES) & 1, g.err);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: tile i of this CTA accumulates into TMEM buffer i & 1
+      const uint32_t id = umma::idesc(1, BM, BN);
+      int it = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        const int b = i & 1;
+        if (!umma::mbar_wait(&tempty[b], ((i >> 1) & 1) ^ 1, g.err)) break;
+        umma::fence_after();
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        for (int kk = 0; kk < nk; ++kk, ++it) {
+          const int s = it % PSTAGES;
+          const uint32_t ph = (it / PSTAGES) & 1;
+          if (!umma::mbar_wait(&full[s], ph, g.err)) { ok = false; break; }
+          umma::fence_after();
+          const uint32_t a0 = umma::smem_u32(smem + (size_t)s * 2 * TILE_BYTES);
+          const uint32_t b0 = a0 + TILE_BYTES;
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4)
+            umma::mma_bf16(acc, umma::sdesc_sw128(a0 + k4 * 32), umma::sdesc_sw128(b0 + k4 * 32), id,
+                           (kk | k4) != 0);
+          umma::mma_commit(&empty[s]);
+        }
+        umma::mma_commit(&tfull[b]);
+      }
+    }
+  } else {
+    // epilogue, 256 threads
+    const int et = threadIdx.x - 64;                 // 0 .. 255
+    const int q = warp & 3, half = (warp - 2) >> 2;  // TMEM lane quarter, column half
+    const int r = 32 * q + lane;                     // tile row of this thread
+    auto stage = [&](int t) {
+      const int arow = (t % rtiles) * BM, brow = (t / rtiles) * BN;
+      for (int e = et; e < BM * (BN / 4); e += 256) {
+        const int rr = e / (BN / 4), cc = e % (BN / 4);
+        const int row = arow + rr, col = brow + cc * 4;
+        float* d = fs + rr * BN + ((cc ^ (rr & 7)) << 2);
+        if (row < g.M && col + 3 < g.N) {
+          umma::cp_async16(d, g.F + (size_t)row * g.ldf + col);
+        } else {
+          const float* src = g.F + (size_t)row * g.ldf + col;
+          d[0] = (row < g.M && col < g.N) ? src[0] : 0.f;
+          d[1] = (row < g.M && col + 1 < g.N) ? src[1] : 0.f;
+          d[2] = (row < g.M && col + 2 < g.N) ? src[2] : 0.f;
+          d[3] = 0.f;
+        }
+      }
+      if (g.gpart)
+        for (int e = et; e < 3 * BN; e += 256) {
+          const int col = brow + e / 3;
+          rs[e] = col < g.N ? g.resid[3 * (size_t)col + e % 3] : 0.f;
+        }
+    };
+    if (blockIdx.x < ntiles) stage(blockIdx.x);
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int b = i & 1;
+      const int arow = (t % rtiles) * BM, brow = (t / rtiles) * BN, ct = t / rtiles;
+      if (!umma::mbar_wait(&tfull[b], (i >> 1) & 1, g.err)) atomicOr(fail_flag, 1);
+      umma::fence_after();
+      umma::cp_async_wait_all();
+      bar_epi();
+      const bool ok = *(volatile int*)fail_flag == 0;   // the same for all epilogue threads
+      const int gch = (g.gpart && arow + r < g.M) ? (arow + r) / g.gnc : 0;
+      float gacc = 0.f;
+      const float* fr = fs + r * BN;
+      const int sw = r & 7;
+#pragma unroll 1
+      for (int cb = 64 * half; cb < 64 * half + 64; cb += 32) {
+        float v[32];
+        umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cb), v);
+        if (!ok) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        }
+        float f[32];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float4 w4 = *reinterpret_cast<const float4*>(fr + ((((cb >> 2) + k) ^ sw) << 2));
+          f[4 * k] = w4.x; f[4 * k + 1] = w4.y; f[4 * k + 2] = w4.z; f[4 * k + 3] = w4.w;
+        }
+        if (g.gpart) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rs[3 * (cb + j) + gch], gacc);
+        }
+        uint8_t* jr = jb + r * 256;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          uint4 w;
+          uint32_t* wp = &w.x;
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * k + 2 * h] + f[8 * k + 2 * h],
+                                                            v[8 * k + 2 * h + 1] + f[8 * k + 2 * h + 1]);
+            wp[h] = *reinterpret_cast<const uint32_t*>(&b2);
+          }
+          *reinterpret_cast<uint4*>(jr + ((((cb >> 3) + k) ^ sw) << 4)) = w;
+        }
+      }
+      gsum[half * BM + r] = gacc;
+      // this warp's TMEM reads are complete: release the buffer
+      umma::fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+      bar_epi();
+      // fs, rs and gsum are read; the next tile's F rows come in meanwhile
+      if (t + (int)gridDim.x < ntiles) stage(t + gridDim.x);
+      if (g.gpart && et < BM && arow + et < g.M)
+        g.gpart[(size_t)(arow + et) * g.gstride + ct] = (double)(gsum[et] + gsum[BM + et]);
+      // bf16 rows: one warp writes a 256-byte row per step, 8 bytes per lane
+      for (int rr = warp - 2; rr < BM; rr += 8) {
+        const int row = arow + rr;
+        if (row >= g.M) continue;
+        const int col = brow + lane * 4;
+        const uint8_t* src = jb + rr * 256 + ((((lane >> 1) ^ (rr & 7)) << 4) | ((lane & 1) << 3));
+        __nv_bfloat16* dst = g.J + (size_t)row * g.ldj + col;
+        if (col + 3 < g.N) {
+          *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
+        } else {
+          const __nv_bfloat16* sb = reinterpret_cast<const __nv_bfloat16*>(src);
+          for (int u = 0; u < 4; ++u)
+            if (col + u < g.N) dst[u] = sb[u];
+        }
+      }
+      bar_epi();
+      if (!ok) break;
+    }
+    umma::cp_async_wait_all();
+  }
+  __syncwarp();
+  umma::fence_before();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, 256);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -401,8 +623,24 @@ int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt
     g.gstride = gstride;
   }
   ProfScope _ps(c, "tc_jrows");
+  if (!x3) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_tc_jrows_pers, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kPersSmem);
+      if (e != cudaSuccess) return cuda_check(c, e, "persistent J rows smem attribute");
+      attr = true;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const int ntiles = ((rows + BM - 1) / BM) * ((m + BN - 1) / BN);
+    const int grid = std::max(1, std::min(ntiles, sms));
+    k_tc_jrows_pers<<<grid, kPersThreads, kPersSmem, S(c)>>>(ta, tb, g);
+    BEM_LAUNCHED(c);
+    return cuda_check(c, cudaGetLastError(), "k_tc_jrows_pers");
+  }
   dim3 grid((rows + BM - 1) / BM, (m + BN - 1) / BN);
-  return x3 ? launch<true>(c, ta, tb, ta2, tb2, g, grid) : launch<false>(c, ta, tb, ta, tb, g, grid);
+  return launch<true>(c, ta, tb, ta2, tb2, g, grid);
 }
 
 // part[split][ch][nc][nc] += upper blocks of J_ch^T J_ch over the m samples of J
