@@ -324,12 +324,15 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
 // the columns 64 ((w - 2) / 4) .. +63 of them.  So the epilogue of a tile
 // (F rows added, bf16 packing, the handle part of the gradient, coalesced
 // stores) overlaps the MMAs of the next.  Per tile the F rows are copied by
-// cp.async into fs (issued while the previous tile's rows are stored), the
-// bf16 result goes to jb (16-byte chunk k of row r at k ^ (r & 7)).
-constexpr int PSTAGES = 3;
+// cp.async into fs (issued once the previous tile's rows are stored); row r
+// holds 32 chunks of 16 bytes, logical chunk c at position c ^ (r & 7).  The
+// bf16 result is written back in place: output chunk o of column half h goes
+// to position (16 h + o) ^ (r & 7), which held an F chunk of the same half
+// that has already been read, so the two warps of a row never overlap.
+constexpr int PSTAGES = 4;
 constexpr int kPersThreads = 320;           // 2 control warps + 8 epilogue warps
-constexpr int kPersSmem = 1024 + PSTAGES * 2 * TILE_BYTES + BM * BN * 4 + BM * BN * 2 +
-                          3 * BN * 4 + 2 * BM * 4 + 256;
+constexpr int kPersSmem = 1024 + PSTAGES * 2 * TILE_BYTES + BM * BN * 4 + 3 * BN * 4 +
+                          2 * BM * 4 + 256;
 
 __device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
@@ -344,8 +347,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* fs = reinterpret_cast<float*>(smem + PSTAGES * 2 * TILE_BYTES);      // [BM][BN] F rows
-  uint8_t* jb = reinterpret_cast<uint8_t*>(fs + BM * BN);                    // [BM][256 B] bf16
-  float* rs = reinterpret_cast<float*>(jb + BM * BN * 2);                    // [BN][3] residuals
+  float* rs = fs + BM * BN;                                                  // [BN][3] residuals
   float* gsum = rs + 3 * BN;                                                 // [2][BM]
   uint64_t* full = reinterpret_cast<uint64_t*>(gsum + 2 * BM);
   uint64_t* empty = full + PSTAGES;
@@ -483,7 +485,9 @@ __global__ void __launch_bounds__(kPersThreads, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rs[3 * (cb + j) + gch], gacc);
         }
-        uint8_t* jr = jb + r * 256;
+        // output chunks of this 32-column block: o = ((cb - 64 half) >> 3) + k
+        uint8_t* jr = reinterpret_cast<uint8_t*>(fs + r * BN);
+        const int o0 = 16 * half + ((cb - 64 * half) >> 3);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           uint4 w;
@@ -494,7 +498,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
                                                             v[8 * k + 2 * h + 1] + f[8 * k + 2 * h + 1]);
             wp[h] = *reinterpret_cast<const uint32_t*>(&b2);
           }
-          *reinterpret_cast<uint4*>(jr + ((((cb >> 3) + k) ^ sw) << 4)) = w;
+          *reinterpret_cast<uint4*>(jr + (((o0 + k) ^ sw) << 4)) = w;
         }
       }
       gsum[half * BM + r] = gacc;
@@ -503,8 +507,6 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[b]);
       bar_epi();
-      // fs, rs and gsum are read; the next tile's F rows come in meanwhile
-      if (t + (int)gridDim.x < ntiles) stage(t + gridDim.x);
       if (g.gpart && et < BM && arow + et < g.M)
         g.gpart[(size_t)(arow + et) * g.gstride + ct] = (double)(gsum[et] + gsum[BM + et]);
       // bf16 rows: one warp writes a 256-byte row per step, 8 bytes per lane
@@ -512,7 +514,9 @@ __global__ void __launch_bounds__(kPersThreads, 1)
         const int row = arow + rr;
         if (row >= g.M) continue;
         const int col = brow + lane * 4;
-        const uint8_t* src = jb + rr * 256 + ((((lane >> 1) ^ (rr & 7)) << 4) | ((lane & 1) << 3));
+        const int oc = lane >> 1;                      // output chunk 0..15 of the row
+        const int pos = (oc < 8 ? oc : oc + 8) ^ (rr & 7);
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(fs + rr * BN) + ((pos << 4) | ((lane & 1) << 3));
         __nv_bfloat16* dst = g.J + (size_t)row * g.ldj + col;
         if (col + 3 < g.N) {
           *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
@@ -524,6 +528,8 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       }
       bar_epi();
       if (!ok) break;
+      // fs now free: the next tile's F rows come in while its MMAs run
+      if (t + (int)gridDim.x < ntiles) stage(t + gridDim.x);
     }
     umma::cp_async_wait_all();
   }
@@ -665,11 +671,14 @@ int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, f
   return x3 ? launch<true>(c, tj, tj, tj2, tj2, g, grid) : launch<false>(c, tj, tj, tj, tj, g, grid);
 }
 
+// K slices per block pair: as many as fill the resident CTA slots in one
+// wave without starting a second, nearly empty one (rounding up would leave
+// a short tail wave that costs as long as the first)
 int tc_syrk_splits(int nc, bool x3) {
   int tiles = (nc + BM - 1) / BM;
   int ctas = 3 * tiles * (tiles + 1) / 2;
   int slots = (x3 ? 1 : 2) * 152;
-  return std::max(1, std::min(64, (slots + ctas - 1) / ctas));
+  return std::max(1, std::min(64, slots / ctas));
 }
 
 }  // namespace bem
