@@ -1288,10 +1288,15 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
         // the float factor hit a non-positive pivot.  The equilibrated
         // matrix has a unit diagonal, so float rounding moves a pivot by
         // about n * 6e-8; a pivot far below zero means the matrix itself is
-        // not positive definite, which the double factor would only confirm
+        // not positive definite, which the double factor would only confirm.
+        // In a mixed context H is a bf16 Gram matrix, accurate to about 1e-2
+        // of its largest entries: a damped matrix that float cannot factor
+        // counts as not positive definite there, and the step raises the
+        // damping instead of factoring it in double.
         float pv;
         std::memcpy(&pv, reinterpret_cast<const char*>(&h[1]) + sizeof(int), sizeof(float));
-        if (pv < kIndefinitePivot) return fail(c, BEM_ENOTSPD, "LM matrix is not positive definite");
+        if (pv < kIndefinitePivot || c->opts.precision == BEM_MIXED)
+          return fail(c, BEM_ENOTSPD, "LM matrix is not positive definite");
         break;
       }
       eta_prev = it + 1 == kRefineCheck ? 2.0 : eta;
