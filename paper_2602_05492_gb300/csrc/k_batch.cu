@@ -265,23 +265,29 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
   bem_ctx* c0 = b->c0;
   int rc;
   if ((rc = size_buffers(b, n, T))) return rc;
-  // ---- A: state at theta, near sums at the samples
+  // ---- A: state at theta, near sums at the samples.  A scene whose
+  // residual comes out of its J-row pass (jtj_fuses_eval) gets no tiles here.
   b->hjobs[0].resize(S);
+  bool any_eval = false;
   for (int s = 0; s < S; ++s) {
     bem_ctx* c = b->sc[s];
     if ((rc = ctx_refresh(c, c->d_theta)) || (rc = geom_compat(c, c->d_theta, false))) return rc;
+    const bool fused = jtj_fuses_eval(c);
     double* nb = nullptr;
-    if (c->opts.near_factor > 0) {
+    if (!fused && c->opts.near_factor > 0) {
       nb = (double*)b->nearb[(size_t)s * (T + 1)].p;
       if ((rc = near_forward(c, n[s], (const float*)xy[s], nb))) return rc;
     }
     BatchJob j = scene_job(c, n[s], xy[s], target[s]);
     j.a.near_add = nb;
     j.a.resid = (float*)b->resid[s].p;
+    if (fused) j.a.n = 0;
+    any_eval = any_eval || !fused;
     b->hjobs[0][s] = j;
   }
-  // ---- A': one persistent launch over all scenes (tile shape tuned once)
-  if (!b->tuned && (rc = autotune(b, 0))) return rc;
+  // ---- A': one persistent launch over the scenes evaluated here (the tile
+  // shape is tuned once, on the first job table with work)
+  if (any_eval && !b->tuned && (rc = autotune(b, 0))) return rc;
   number_tiles(b, 0, b->spt);
   bind_partials(b, 0);
   if ((rc = upload(b, 0)) || (rc = eval_graph(b, 0))) return rc;
@@ -291,7 +297,14 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
     const int nth = c->sc.nth;
     double* g = (double*)b->gvec[s].p;
     if ((rc = grow(c, c->H, sizeof(double) * (size_t)nth * nth))) return rc;
-    if (jtj_gives_gradient(c)) {
+    if (jtj_fuses_eval(c)) {
+      // residual, loss sum, g and H from one pass; the loss sum joins the others
+      if ((rc = jtj_build(c, n[s], xy[s], (double*)c->H.p, b->resid[s].p, g, target[s])) ||
+          (rc = cuda_check(c, cudaMemcpyAsync((double*)b->sums[0].p + s, c->d_scal, sizeof(double),
+                                              cudaMemcpyDeviceToDevice, b->st), "loss")))
+        return rc;
+      ctx_scale_norm(c, g, nth, 1.0, (double*)b->gn2.p + s);
+    } else if (jtj_gives_gradient(c)) {
       if ((rc = jtj_build(c, n[s], xy[s], (double*)c->H.p, b->resid[s].p, g))) return rc;
       ctx_scale_norm(c, g, nth, 1.0, (double*)b->gn2.p + s);
     } else {
@@ -355,6 +368,7 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
     }
   }
   // ---- D: one persistent launch over all (scene, trial) pairs
+  if (!b->tuned && (rc = autotune(b, 1))) return rc;
   number_tiles(b, 1, b->spt);
   bind_partials(b, 1);
   if ((rc = upload(b, 1)) || (rc = eval_graph(b, 1))) return rc;

@@ -1255,9 +1255,27 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
         }
       }
     }
+    // a failed float factor is known before any solve with it (the pivot
+    // status and value sit in the word after eta_d)
+    bool factored = true;
+    {
+      double h1 = 0;
+      if ((rc = cuda_check(c, cudaMemcpyAsync(&h1, eta_d + 1, sizeof(double), cudaMemcpyDeviceToHost, S(c)), "pivot")) ||
+          (rc = cuda_check(c, cudaStreamSynchronize(S(c)), "factor sync")))
+        return rc;
+      std::memcpy(&fst, &h1, sizeof(int));
+      if (fst) {
+        float pv;
+        std::memcpy(&pv, reinterpret_cast<const char*>(&h1) + sizeof(int), sizeof(float));
+        if (pv < kIndefinitePivot || c->opts.precision == BEM_MIXED)
+          return fail(c, BEM_ENOTSPD, "LM matrix is not positive definite");
+        factored = false;     // the double factor decides
+      }
+    }
     ProfScope _pt(c, "lm_trisolve");
-    if ((rc = cuda_check(c, cudaMemcpyAsync(Rres, R, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, S(c)), "copy")) ||
-        (rc = cuda_check(c, cudaMemsetAsync(Xs, 0, sizeof(double) * 4 * n, S(c)), "memset")))
+    if (factored &&
+        ((rc = cuda_check(c, cudaMemcpyAsync(Rres, R, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, S(c)), "copy")) ||
+         (rc = cuda_check(c, cudaMemsetAsync(Xs, 0, sizeof(double) * 4 * n, S(c)), "memset"))))
       return rc;
     const int rblk = (n + 7) / 8;
     const size_t smem = sizeof(float) * 4 * (size_t)n;
@@ -1268,7 +1286,7 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
       return rc;
     }
     double eta = 1.0, eta_prev = 2.0;
-    for (int it = 0; it < kRefineMax; ++it) {
+    for (int it = 0; factored && it < kRefineMax; ++it) {
       if (blocked) {
         trsv_cluster_f32(c, Lf, Linvf, n, dsc, Rres, Xs);
       } else {
