@@ -121,15 +121,16 @@ class ClockSampler:
 # min/max are not counted)
 
 # handle pair of the evaluation: rounded frame 9, h^2 1, h', q1, q2, t1 t2 8, atan2(h'L, h'^2 + t1 t2) 22 (octant reduction, one
-# reciprocal, degree-7 minimax polynomial), (1/2) log q2 - 1 3, z = L(t1+t2)/q1 4,
-# (1/2) log1p(z) 13 (atanh series), S 5, Dl 2, 3-channel accumulation 12
-FLOP_FWD_HANDLE = 9 + 1 + 8 + 22 + 3 + 4 + 13 + 5 + 2 + 12
+# reciprocal, degree-7 minimax polynomial), S from t2 log q2 - t1 log q1 9 (two
+# logarithms, one product, three multiply-adds), Dl 2, 3-channel accumulation 12
+FLOP_FWD_HANDLE = 9 + 1 + 8 + 22 + 9 + 2 + 12
 # boundary pair: vertex offset 2, cross 3, dot 3, atan2 20, 3-channel accumulation 6
 FLOP_FWD_BOUND = 2 + 3 + 3 + 20 + 6
-# F-row pair: frame 10, values and frame partials of both layers 73, chain rule
-# to both endpoints for Dl and S 43, jump columns 16, 3 channels x 2 coordinates
-# x (combine 7 + four Bernstein accumulations 8) 90
-FLOP_FROWS_PAIR = 10 + 73 + 43 + 16 + 90
+# F-row pair: frame 10, values and frame partials of both layers 57 (both
+# logarithms taken directly), chain rule to both endpoints for Dl and S 43,
+# jump columns 16, 3 channels x 2 coordinates x (combine 7 + four Bernstein
+# accumulations 8) 90
+FLOP_FROWS_PAIR = 10 + 57 + 43 + 16 + 90
 # FP32 lanes x 2 flops per FMA x SMs x max SM clock (GB300: 128, 152, 2070 MHz)
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12
 
