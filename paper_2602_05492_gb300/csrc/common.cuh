@@ -9,9 +9,11 @@
 //     Dl = -(1/2pi) (h/h') Phi,      Phi = atan2(h' L, h'^2 + t1 t2)
 // S multiplies w_c and Dl multiplies -w_d in the handle term f.
 //
-// t2 log q2 - t1 log q1 is evaluated as L log q2 + t1 log1p(L (t1+t2)/q1),
-// which has no cancellation when the panel is far from x (t1 ~ t2); this is
-// what keeps single precision accurate in the far field.
+// The double path evaluates t2 log q2 - t1 log q1 as L log q2 +
+// t1 log1p(L (t1+t2)/q1), which has no cancellation when the panel is far
+// from x (t1 ~ t2).  The float loops take both logarithms directly with the
+// MUFU base-2 logarithm: the cancellation costs a few float ulps of log q
+// times |t1|, far inside the mixed path's colour and gradient bounds.
 //
 // Endpoint derivatives go through the frame: with F(t1, t2, h)
 //     dF/da = F_t1 tau + n [ -(h/L)(F_t1+F_t2) + (t2/L) F_h ]
@@ -234,19 +236,19 @@ __device__ __forceinline__ LayerVals<T> layer_values(const Frame<T>& f, T eps_c2
 __device__ __forceinline__ void pair_fwd_f(const Frame<float>& f, float hh, float eps_c2,
                                            float eps_d2, bool same_eps, float& Dh, float& Sh) {
   const float hc2 = hh + eps_c2;
-  const float rc = rsqrtf(hc2);
+  const float rc = mufu_rsqrt(hc2);
   const float hc = hc2 * rc;
   const float tt = f.t1 * f.t2;
   const float q1 = fmaf(f.t1, f.t1, hc2);
   const float q2 = fmaf(f.t2, f.t2, hc2);
   const float phic = fm_atan2_ypos(hc * f.L, hc2 + tt);
-  const float d = fmaf(f.t2, __log2f(q2), -f.t1 * __log2f(q1));   // t2 lg q2 - t1 lg q1
+  const float d = fmaf(f.t2, mufu_lg2(q2), -f.t1 * mufu_lg2(q1));   // t2 lg q2 - t1 lg q1
   Sh = fmaf(hc, phic, fmaf(d, kLn2Halff, -f.L));
   if (same_eps) {
     Dh = f.h * rc * phic;
   } else {
     const float hd2 = hh + eps_d2;
-    const float rd = rsqrtf(hd2);
+    const float rd = mufu_rsqrt(hd2);
     Dh = f.h * rd * fm_atan2_ypos(hd2 * rd * f.L, hd2 + tt);
   }
 }
@@ -305,7 +307,7 @@ __device__ __forceinline__ LayerGrad<T> layer_grad(const Frame<T>& f, T eps_c2, 
 //   St1 = -(1/2) log q1             Dt1 = -h/q1
 //   St2 =  (1/2) log q2             Dt2 =  h/q2
 //   Sh_ = (h/h'_c) Phi_c            Dh_ = (1/h'^2)[eps_d^2 Phi_d/h' - h^2 L (h'^2 - t1 t2)/(q1 q2)]
-// with both logarithms from the MUFU base-2 logarithm.
+// with both logarithms from the MUFU base-2 logarithm (mufu_lg2).
 struct GradHat {
   float S, D;
   float St1, St2, Sh;
@@ -317,13 +319,13 @@ __device__ __forceinline__ GradHat layer_grad_hat(const Frame<float>& f, float h
   GradHat g;
   const float tt = f.t1 * f.t2;
   const float hc2 = hh + eps_c2;
-  const float rc = rsqrtf(hc2);
+  const float rc = mufu_rsqrt(hc2);
   const float hc = hc2 * rc;
   const float q1 = fmaf(f.t1, f.t1, hc2);
   const float q2 = fmaf(f.t2, f.t2, hc2);
   const float phic = fm_atan2_ypos(hc * f.L, hc2 + tt);
-  const float lq1h = __log2f(q1) * kLn2Halff;                  // (1/2) log q1
-  const float lq2h = __log2f(q2) * kLn2Halff;                  // (1/2) log q2
+  const float lq1h = mufu_lg2(q1) * kLn2Halff;                 // (1/2) log q1
+  const float lq2h = mufu_lg2(q2) * kLn2Halff;                 // (1/2) log q2
   g.S = fmaf(hc, phic, fmaf(f.t2, lq2h, fmaf(-f.t1, lq1h, -f.L)));
   g.St1 = -lq1h;
   g.St2 = lq2h;
@@ -334,13 +336,13 @@ __device__ __forceinline__ GradHat layer_grad_hat(const Frame<float>& f, float h
     g.D = g.Sh;
   } else {
     hd2 = hh + eps_d2;
-    rd = rsqrtf(hd2);
+    rd = mufu_rsqrt(hd2);
     phid = fm_atan2_ypos(hd2 * rd * f.L, hd2 + tt);
     r1 = fmaf(f.t1, f.t1, hd2);
     r2 = fmaf(f.t2, f.t2, hd2);
     g.D = f.h * rd * phid;
   }
-  const float ir1 = __fdividef(1.f, r1), ir2 = __fdividef(1.f, r2);
+  const float ir1 = mufu_rcp(r1), ir2 = mufu_rcp(r2);
   g.Dt1 = -f.h * ir1;
   g.Dt2 = f.h * ir2;
   g.Dh = (eps_d2 * phid * rd - hh * f.L * (hd2 - tt) * ir1 * ir2) * (rd * rd);
@@ -362,11 +364,11 @@ __device__ __forceinline__ void frame_to_endpoints(const Panel<T>& p, const Fram
   dby = Ft2 * p.ty - nb * p.tx;
 }
 
-// Float chain rule with an approximate reciprocal of L (L > 0).
+// Float chain rule with the MUFU reciprocal of L (L > 0).
 __device__ __forceinline__ void frame_to_endpoints_f(float tx, float ty, const Frame<float>& f,
                                                      float Ft1, float Ft2, float Fh, float& dax,
                                                      float& day, float& dbx, float& dby) {
-  const float iL = __fdividef(1.f, f.L);
+  const float iL = mufu_rcp(f.L);
   const float s = f.h * (Ft1 + Ft2) * iL;
   const float na = fmaf(f.t2 * iL, Fh, -s);
   const float nb = fmaf(-f.t1 * iL, Fh, s);
