@@ -795,17 +795,44 @@ __global__ void __launch_bounds__(256) k_chol_step_f32(float* __restrict__ Kf, f
     j0 = r0 + 64 * bj;
     nsides = bi == bj ? 1 : 2;
   }
-  // loads: the diagonal block and (tile CTAs) the raw panel rows of I and J
-  for (int e = tid; e < 1024; e += 256) {
-    const int r = e >> 5, q = e & 31;
-    T[r][q] = (r < nb && q <= r) ? Kf[(size_t)(k0 + r) * n + k0 + q] : 0.f;
-  }
-  if (!diag_cta)
-    for (int e = tid; e < 2 * 64 * 32; e += 256) {
-      const int sd = e >> 11, rr = (e >> 5) & 63, l = e & 31;
-      const int g = (sd == 0 ? i0 : j0) + rr;
-      Araw[sd][rr][l] = (sd < nsides && g < n && l < nb) ? Kf[(size_t)g * n + k0 + l] : 0.f;
+  // loads, all issued before the first use so that one round trip covers
+  // them: the diagonal block, (tile CTAs) the raw panel rows of I and J and
+  // the CTA's tile of the trailing matrix (no other CTA of the launch writes
+  // the panel columns or this tile)
+  const int tx = tid & 15, ty = tid >> 4;
+  float old[4][4];
+  {
+    float tv[4], av[16];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u, r = e >> 5, q = e & 31;
+      tv[u] = (r < nb && q <= r) ? Kf[(size_t)(k0 + r) * n + k0 + q] : 0.f;
     }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + 256 * u, sd = e >> 11, rr = (e >> 5) & 63, l = e & 31;
+      const int g = (sd == 0 ? i0 : j0) + rr;
+      av[u] = (!diag_cta && sd < nsides && g < n && l < nb) ? Kf[(size_t)g * n + k0 + l] : 0.f;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
+        old[a][b] = (!diag_cta && gi < n && gj < n) ? Kf[(size_t)gi * n + gj] : 0.f;
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u;
+      T[e >> 5][e & 31] = tv[u];
+    }
+    if (!diag_cta)
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * u;
+        Araw[e >> 11][(e >> 5) & 63][e & 31] = av[u];
+      }
+  }
   __syncthreads();
   // ---- factor the diagonal block in warp 0: lane r holds row r in
   // registers; column j: pivot from lane j, l_rj = a_rj / sqrt(pivot) for
@@ -887,7 +914,6 @@ __global__ void __launch_bounds__(256) k_chol_step_f32(float* __restrict__ Kf, f
     }
   }
   const float (*PJ)[65] = P[nsides - 1];
-  const int tx = tid & 15, ty = tid >> 4;
   float acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -911,7 +937,7 @@ __global__ void __launch_bounds__(256) k_chol_step_f32(float* __restrict__ Kf, f
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int gj = j0 + tx + 16 * b;
-      if (gj < n) Kf[(size_t)gi * n + gj] -= acc[a][b];
+      if (gj < n) Kf[(size_t)gi * n + gj] = old[a][b] - acc[a][b];
     }
   }
 }
@@ -931,113 +957,182 @@ __global__ void k_equilibrate(const double* __restrict__ K, int n, float* __rest
   if (j == 0) d[i] = di;
 }
 
-// 128-bit shared-memory load kept inside the loop that issues it (the
-// compiler would otherwise hoist all 128 block values into registers).
-__device__ __forceinline__ float4 lds4(const float4* p) {
-  float4 v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"((unsigned)__cvta_generic_to_shared(p)));
-  return v;
+// ---- explicit inverse of the float factor (systems below the blocked size)
+//
+// W = L^-1 by recursive doubling over the 32-row blocks: on a pair of s-row
+// ranges, L = [[A, 0], [B, C]] has the inverse [[A^-1, 0], [-C^-1 B A^-1,
+// C^-1]].  Level s takes every pair (a0 = 2 p s, c0 = a0 + s) at once:
+// first T = B W_A, then W_CA = -W_C T; the 32 x 32 diagonal blocks are the
+// factor's block inverses.  W lives in the lower triangle of an n x n float
+// matrix.  T is kept transposed in the strictly upper triangle (rows
+// [a0, c0), columns [c0, c0 + s)), which no later level reads; a last pass
+// mirrors the lower triangle into the upper one, so that row k holds column
+// k of W from the diagonal on.  Each refinement solve is then two parallel
+// matrix-vector products, z = W^T (W b), where a substitution would take
+// 2 n / 32 block steps one after another.
+
+// W's diagonal blocks from the factor's block inverses (zeros above the
+// diagonal included)
+__global__ void __launch_bounds__(1024) k_inv_init(const float* __restrict__ Linv, int n,
+                                                   float* __restrict__ W) {
+  const int b = blockIdx.x, i = 32 * b + (threadIdx.x >> 5), j = 32 * b + (threadIdx.x & 31);
+  if (i < n && j < n) W[(size_t)i * n + j] = Linv[(size_t)b * 1024 + threadIdx.x];
 }
 
-// One float solve of (D K D) z = D r with the factor L (lower triangle of Lf)
-// and the diagonal-block inverses, by one CTA of 1024 threads: forward and
-// back substitution over 32-row blocks, the right-hand sides (n x 4) in
-// shared memory.  X += D z in double.  Rres: the double residual R - K X.
-__global__ void __launch_bounds__(1024) k_trsv_f32_single(const float* __restrict__ Lf,
-                                                          const float* __restrict__ Linv, int n,
-                                                          const double* __restrict__ d,
-                                                          const double* __restrict__ Rres,
-                                                          double* __restrict__ X) {
-  extern __shared__ float sb[];    // [n][4]
-  __shared__ float4 yk4[32];
-  __shared__ float Li[32][33];
-  float (*yk)[4] = reinterpret_cast<float (*)[4]>(yk4);
-  const int tid = threadIdx.x;
-  for (int e = tid; e < 4 * n; e += blockDim.x) sb[e] = float(d[e >> 2] * Rres[e]);
+// T = B W_A for every pair of level s (blockIdx.z = pair), one 32 x 32 tile
+// per CTA: T[i][j] = sum_k L[c0+i][a0+k] W[a0+k][a0+j], k from the tile's
+// first column on (W_A is lower triangular), stored at W[a0+j][c0+i].  The
+// next 32-column chunk is loaded into registers while the current one is used.
+__global__ void __launch_bounds__(256) k_inv_level_t(const float* __restrict__ Lf,
+                                                     float* __restrict__ W, int n, int s) {
+  __shared__ float As[32][33], Bs[32][33];
+  const int a0 = 2 * s * blockIdx.z, c0 = a0 + s, sC = min(s, n - c0);
+  const int i0 = 32 * blockIdx.y, j0 = 32 * blockIdx.x;
+  if (i0 >= sC) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float av[4], bv[4], acc[4] = {0.f, 0.f, 0.f, 0.f};
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = ty + 8 * u;
+      av[u] = i0 + r < sC ? Lf[(size_t)(c0 + i0 + r) * n + a0 + k0 + tx] : 0.f;
+      bv[u] = W[(size_t)(a0 + k0 + r) * n + a0 + j0 + tx];
+    }
+  };
+  load(j0);
+  for (int k0 = j0; k0 < s; k0 += 32) {
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { As[ty + 8 * u][tx] = av[u]; Bs[ty + 8 * u][tx] = bv[u]; }
+    __syncthreads();
+    if (k0 + 32 < s) load(k0 + 32);
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const float b = Bs[kk][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fmaf(As[ty + 8 * u][kk], b, acc[u]);
+    }
+  }
+  // transposed store through shared memory: As[j][i] = T[i][j]
   __syncthreads();
-  // forward: L y = b
-  for (int kb = 0; kb < n; kb += 32) {
-    const int nb = min(32, n - kb);
-    Li[tid >> 5][tid & 31] = Linv[(size_t)(kb / 32) * 1024 + tid];
-    __syncthreads();
-    if (tid < 128) {
-      const int rr = tid >> 2, qq = tid & 3;
-      float y = 0.f;
-      for (int l = 0; l <= rr && l < nb; ++l) y = fmaf(Li[rr][l], sb[4 * (kb + l) + qq], y);
-      yk[rr][qq] = y;
-    }
-    __syncthreads();
-    if (tid < 128 && (tid >> 2) < nb) sb[4 * kb + tid] = yk[tid >> 2][tid & 3];
-    for (int i = kb + nb + tid; i < n; i += blockDim.x) {
-      const float* row = Lf + (size_t)i * n + kb;
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      if (nb == 32 && (n & 3) == 0) {      // whole block: eight 128-bit loads in flight
-        float4 m4[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) m4[v] = reinterpret_cast<const float4*>(row)[v];
+  for (int u = 0; u < 4; ++u) As[tx][ty + 8 * u] = acc[u];
+  __syncthreads();
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const float mv[4] = {m4[v].x, m4[v].y, m4[v].z, m4[v].w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 y = lds4(&yk4[4 * v + u]);
-            s0 = fmaf(mv[u], y.x, s0); s1 = fmaf(mv[u], y.y, s1);
-            s2 = fmaf(mv[u], y.z, s2); s3 = fmaf(mv[u], y.w, s3);
-          }
-        }
-      } else {
-        for (int l = 0; l < nb; ++l) {
-          const float m = row[l];
-          s0 = fmaf(m, yk[l][0], s0); s1 = fmaf(m, yk[l][1], s1);
-          s2 = fmaf(m, yk[l][2], s2); s3 = fmaf(m, yk[l][3], s3);
-        }
-      }
-      sb[4 * i] -= s0; sb[4 * i + 1] -= s1; sb[4 * i + 2] -= s2; sb[4 * i + 3] -= s3;
-    }
-    __syncthreads();
+  for (int u = 0; u < 4; ++u) {
+    const int jj = ty + 8 * u;
+    if (i0 + tx < sC) W[(size_t)(a0 + j0 + jj) * n + c0 + i0 + tx] = As[jj][tx];
   }
-  // back: L^T z = y
-  for (int kb = (n - 1) / 32 * 32; kb >= 0; kb -= 32) {
-    const int nb = min(32, n - kb);
-    Li[tid >> 5][tid & 31] = Linv[(size_t)(kb / 32) * 1024 + tid];
-    __syncthreads();
-    if (tid < 128) {
-      const int rr = tid >> 2, qq = tid & 3;
-      float x = 0.f;
-      for (int l = rr; l < nb; ++l) x = fmaf(Li[l][rr], sb[4 * (kb + l) + qq], x);
-      yk[rr][qq] = x;
+}
+
+// W_CA = -W_C T for every pair of level s: W[c0+i][a0+j] = -sum_k
+// W[c0+i][c0+k] T[k][j] with T[k][j] read from W[a0+j][c0+k]; k ends with
+// the tile's last row (W_C is lower triangular).
+__global__ void __launch_bounds__(256) k_inv_level_w(float* __restrict__ W, int n, int s) {
+  __shared__ float As[32][33], Bt[32][33];
+  const int a0 = 2 * s * blockIdx.z, c0 = a0 + s, sC = min(s, n - c0);
+  const int i0 = 32 * blockIdx.y, j0 = 32 * blockIdx.x;
+  if (i0 >= sC) return;
+  const int kend = min(i0 + 32, sC);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float av[4], bv[4], acc[4] = {0.f, 0.f, 0.f, 0.f};
+  auto load = [&](int k0) {
+    const bool kin = k0 + tx < sC;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = ty + 8 * u;
+      av[u] = (i0 + r < sC && kin) ? W[(size_t)(c0 + i0 + r) * n + c0 + k0 + tx] : 0.f;
+      bv[u] = kin ? W[(size_t)(a0 + j0 + r) * n + c0 + k0 + tx] : 0.f;
     }
+  };
+  load(0);
+  for (int k0 = 0; k0 < kend; k0 += 32) {
     __syncthreads();
-    if (tid < 128 && (tid >> 2) < nb) sb[4 * kb + tid] = yk[tid >> 2][tid & 3];
-    for (int i = tid; i < kb; i += blockDim.x) {
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      if (nb == 32) {                      // whole block: 16 loads in flight at a time
 #pragma unroll
-        for (int h = 0; h < 32; h += 16) {
-          float m[16];
+    for (int u = 0; u < 4; ++u) { As[ty + 8 * u][tx] = av[u]; Bt[ty + 8 * u][tx] = bv[u]; }
+    __syncthreads();
+    if (k0 + 32 < kend) load(k0 + 32);
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const float b = Bt[tx][kk];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) m[u] = Lf[(size_t)(kb + h + u) * n + i];
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const float4 y = lds4(&yk4[h + u]);
-            s0 = fmaf(m[u], y.x, s0); s1 = fmaf(m[u], y.y, s1);
-            s2 = fmaf(m[u], y.z, s2); s3 = fmaf(m[u], y.w, s3);
-          }
-        }
-      } else {
-        for (int rr = 0; rr < nb; ++rr) {
-          const float m = Lf[(size_t)(kb + rr) * n + i];
-          s0 = fmaf(m, yk[rr][0], s0); s1 = fmaf(m, yk[rr][1], s1);
-          s2 = fmaf(m, yk[rr][2], s2); s3 = fmaf(m, yk[rr][3], s3);
-        }
-      }
-      sb[4 * i] -= s0; sb[4 * i + 1] -= s1; sb[4 * i + 2] -= s2; sb[4 * i + 3] -= s3;
+      for (int u = 0; u < 4; ++u) acc[u] = fmaf(As[ty + 8 * u][kk], b, acc[u]);
     }
-    __syncthreads();
   }
-  for (int e = tid; e < 4 * n; e += blockDim.x) X[e] += d[e >> 2] * double(sb[e]);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = ty + 8 * u;
+    if (i0 + r < sC) W[(size_t)(c0 + i0 + r) * n + a0 + j0 + tx] = -acc[u];
+  }
+}
+
+// W[j][i] = W[i][j] for i > j, one 32 x 32 tile pair (ib >= jb) per CTA.
+// Reads touch only the strictly lower triangle, writes only the strictly
+// upper one.
+__global__ void __launch_bounds__(256) k_inv_mirror(float* __restrict__ W, int n) {
+  __shared__ float t[32][33];
+  int tt = blockIdx.x, ib = 0;
+  while (tt > ib) { tt -= ib + 1; ++ib; }
+  const int jb = tt, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = ty + 8 * u, i = 32 * ib + r, j = 32 * jb + tx;
+    t[r][tx] = (i < n && i > j) ? W[(size_t)i * n + j] : 0.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = ty + 8 * u, orow = 32 * jb + r, ocol = 32 * ib + tx;
+    if (ocol < n && ocol > orow) W[(size_t)orow * n + ocol] = t[tx][r];
+  }
+}
+
+// One float solve of (D K D) z = D r with the explicit inverse: FWD forms
+// y = W (D r); !FWD adds D W^T y to X (double).  One warp per row, the
+// n x 4 vector staged in shared memory.  Rres: the double residual R - K X.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_inv_apply(const float* __restrict__ W, int n,
+                                                   const double* __restrict__ d,
+                                                   const double* __restrict__ Rres,
+                                                   float* __restrict__ y, double* __restrict__ X) {
+  extern __shared__ float4 v4[];   // [n]
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    if constexpr (FWD) {
+      const double dk = d[k];
+      v4[k] = make_float4(float(dk * Rres[4 * k]), float(dk * Rres[4 * k + 1]),
+                          float(dk * Rres[4 * k + 2]), float(dk * Rres[4 * k + 3]));
+    } else {
+      v4[k] = reinterpret_cast<const float4*>(y)[k];
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const float* row = W + (size_t)i * n;
+  const int ke = FWD ? i + 1 : n;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 4
+  for (int k = (FWD ? 0 : i) + lane; k < ke; k += 32) {
+    const float m = row[k];
+    const float4 v = v4[k];
+    s0 = fmaf(m, v.x, s0); s1 = fmaf(m, v.y, s1); s2 = fmaf(m, v.z, s2); s3 = fmaf(m, v.w, s3);
+  }
+  for (int o = 16; o; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+  }
+  if (lane != 0) return;
+  if constexpr (FWD) {
+    reinterpret_cast<float4*>(y)[i] = make_float4(s0, s1, s2, s3);
+  } else {
+    const double di = d[i];
+    X[4 * i] += di * double(s0);
+    X[4 * i + 1] += di * double(s1);
+    X[4 * i + 2] += di * double(s2);
+    X[4 * i + 3] += di * double(s3);
+  }
 }
 
 // Rres = R - K X (double, one warp per row, K full) and per-block sums for
@@ -1186,8 +1281,7 @@ __global__ void k_kkt_finish(const double* __restrict__ X, const double* __restr
 }
 
 // Refinement: checked from step kRefineCheck on, at most kRefineMax steps,
-// converged when the normwise backward error is below kRefineTol; the
-// single-CTA float solve keeps n x 4 floats in shared memory.
+// converged when the normwise backward error is below kRefineTol.
 constexpr int kRefineCheck = 2, kRefineMax = 10;
 constexpr double kRefineTol = 1e-14;
 constexpr int kBlockedMinN = 2048, kMaxBlockedSolve = 32768;
@@ -1212,7 +1306,8 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
                                           // (32 x 32 blocks; 64 x 64 when blocked)
   double* R = (double*)c->lmL.p;          // [n][4] right-hand sides, then solutions
   double* cons = R + 4 * (size_t)n;       // [n][4] constraint columns
-  double* Ytmp = cons + 4 * (size_t)n;    // [n][4] forward-solve result (double path)
+  double* Ytmp = cons + 4 * (size_t)n;    // [n][4] forward-solve result (double path;
+                                          // float y of the inverse solves)
   double* Rres = Ytmp + 4 * (size_t)n;    // [n][4] refinement residual
   double* Xs = Rres + 4 * (size_t)n;      // [n][4] refined solution
   double* dsc = Xs + 4 * (size_t)n;       // [n] equilibration
@@ -1235,7 +1330,9 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
   // factorization is the fallback when the float one fails or stalls
   bool done = false;
   // large systems: 64-column blocked factor and the cluster solve; below
-  // kBlockedMinN the 32-column step kernel and the single-CTA solve
+  // kBlockedMinN the 32-column step kernel, the explicit inverse of the
+  // factor (written over Kf, which the factor no longer needs) and two
+  // matrix-vector products per solve
   const bool blocked = n >= kBlockedMinN;
   if (c->opts.lm_solver == BEM_LM_AUTO && (blocked ? n <= kMaxBlockedSolve : true)) {
     int fst = 0;
@@ -1272,27 +1369,42 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
         factored = false;     // the double factor decides
       }
     }
+    if (factored && !blocked) {
+      ProfScope _pi(c, "lm_inverse");
+      const int nblk32 = (n + 31) / 32;
+      k_inv_init<<<nblk32, 1024, 0, S(c)>>>(Linvf, n, Kf);
+      BEM_LAUNCHED(c);
+      for (int s = 32; s < n; s *= 2) {
+        const dim3 g(s / 32, s / 32, (n - s + 2 * s - 1) / (2 * s));   // pairs with c0 < n
+        k_inv_level_t<<<g, 256, 0, S(c)>>>(Lf, Kf, n, s);
+        k_inv_level_w<<<g, 256, 0, S(c)>>>(Kf, n, s);
+        c->launches += 2;
+      }
+      k_inv_mirror<<<nblk32 * (nblk32 + 1) / 2, 256, 0, S(c)>>>(Kf, n);
+      BEM_LAUNCHED(c);
+    }
     ProfScope _pt(c, "lm_trisolve");
     if (factored &&
         ((rc = cuda_check(c, cudaMemcpyAsync(Rres, R, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, S(c)), "copy")) ||
          (rc = cuda_check(c, cudaMemsetAsync(Xs, 0, sizeof(double) * 4 * n, S(c)), "memset"))))
       return rc;
     const int rblk = (n + 7) / 8;
-    const size_t smem = sizeof(float) * 4 * (size_t)n;
-    if (blocked) {
-      if ((rc = trsv_cluster_prepare(c, n))) return rc;
-    } else if (smem > 48 * 1024 &&
-               (rc = cuda_check(c, cudaFuncSetAttribute(k_trsv_f32_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attribute"))) {
-      return rc;
-    }
-    double eta = 1.0, eta_prev = 2.0;
-    for (int it = 0; factored && it < kRefineMax; ++it) {
+    const size_t vsmem = sizeof(float) * 4 * (size_t)n;   // below 48 KB for n < kBlockedMinN
+    float* yf = reinterpret_cast<float*>(Ytmp);
+    if (blocked && (rc = trsv_cluster_prepare(c, n))) return rc;
+    // X += float solve of the residual Rres
+    auto correct = [&]() {
       if (blocked) {
         trsv_cluster_f32(c, Lf, Linvf, n, dsc, Rres, Xs);
       } else {
-        k_trsv_f32_single<<<1, 1024, smem, S(c)>>>(Lf, Linvf, n, dsc, Rres, Xs);
-        BEM_LAUNCHED(c);
+        k_inv_apply<true><<<rblk, 256, vsmem, S(c)>>>(Kf, n, dsc, Rres, yf, nullptr);
+        k_inv_apply<false><<<rblk, 256, vsmem, S(c)>>>(Kf, n, dsc, nullptr, yf, Xs);
+        c->launches += 2;
       }
+    };
+    double eta = 1.0, eta_prev = 2.0;
+    for (int it = 0; factored && it < kRefineMax; ++it) {
+      correct();
       k_resid4<<<rblk, 256, 0, S(c)>>>(Km, n, R, Xs, Rres, epart);
       k_backward_error<<<1, 256, 0, S(c)>>>(epart, rblk, eta_d);
       c->launches += 2;
@@ -1319,7 +1431,16 @@ int la_lm_solve(bem_ctx* c, const double* H, const double* g, double lam, double
       }
       eta_prev = it + 1 == kRefineCheck ? 2.0 : eta;
       eta = h[0];
-      if (eta < kRefineTol) { done = true; break; }
+      if (eta < kRefineTol) {
+        // one more correction with the residual just formed: the test
+        // bounds the residual normwise, which on a badly scaled K still
+        // leaves an error of up to cond(K) times it in X, and each
+        // correction shrinks the error by about cond(D K D) times the float
+        // rounding unit
+        correct();
+        done = true;
+        break;
+      }
       if (!(eta < 0.5 * eta_prev)) break;  // stalled
     }
     if (done &&
