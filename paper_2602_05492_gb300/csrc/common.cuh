@@ -349,33 +349,29 @@ __device__ __forceinline__ GradHat layer_grad_hat(const Frame<float>& f, float h
   return g;
 }
 
-// Chain rule from frame partials (F_t1, F_t2, F_h) to d/da, d/db.
+// Chain rule from frame partials (F_t1, F_t2, F_h) to d/da, d/db, out =
+// (dF/dax, dF/day, dF/dbx, dF/dby).  iL = 1/L, or 0 for a zero-length panel
+// (whose tangent is 0 too), which makes all four vanish without a branch.
 template <typename T>
-__device__ __forceinline__ void frame_to_endpoints(const Panel<T>& p, const Frame<T>& f, T Ft1,
-                                                   T Ft2, T Fh, T& dax, T& day, T& dbx, T& dby) {
-  T iL = T(1) / f.L;
-  T s = f.h * (Ft1 + Ft2) * iL;
-  T na = -s + f.t2 * iL * Fh;
-  T nb = s - f.t1 * iL * Fh;
-  // n = (ty, -tx)
-  dax = Ft1 * p.tx + na * p.ty;
-  day = Ft1 * p.ty - na * p.tx;
-  dbx = Ft2 * p.tx + nb * p.ty;
-  dby = Ft2 * p.ty - nb * p.tx;
+__device__ __forceinline__ void chain_endpoints(T tx, T ty, T iL, const Frame<T>& f, T Ft1, T Ft2,
+                                                T Fh, T (&out)[4]) {
+  const T s = f.h * (Ft1 + Ft2) * iL;
+  const T na = fma(f.t2 * iL, Fh, -s);
+  const T nb = fma(-f.t1 * iL, Fh, s);
+  out[0] = fma(na, ty, Ft1 * tx);
+  out[1] = fma(-na, tx, Ft1 * ty);
+  out[2] = fma(nb, ty, Ft2 * tx);
+  out[3] = fma(-nb, tx, Ft2 * ty);
 }
 
-// Float chain rule with the MUFU reciprocal of L (L > 0).
-__device__ __forceinline__ void frame_to_endpoints_f(float tx, float ty, const Frame<float>& f,
-                                                     float Ft1, float Ft2, float Fh, float& dax,
-                                                     float& day, float& dbx, float& dby) {
-  const float iL = mufu_rcp(f.L);
-  const float s = f.h * (Ft1 + Ft2) * iL;
-  const float na = fmaf(f.t2 * iL, Fh, -s);
-  const float nb = fmaf(-f.t1 * iL, Fh, s);
-  dax = fmaf(na, ty, Ft1 * tx);
-  day = fmaf(-na, tx, Ft1 * ty);
-  dbx = fmaf(nb, ty, Ft2 * tx);
-  dby = fmaf(-nb, tx, Ft2 * ty);
+// 1/L of a panel, 0 for a zero-length one (the float path with the MUFU reciprocal)
+template <typename T>
+__device__ __forceinline__ T inv_len(T L) {
+  if constexpr (sizeof(T) == 4) {
+    return L > 0.f ? mufu_rcp(L) : 0.f;
+  } else {
+    return L > T(0) ? T(1) / L : T(0);
+  }
 }
 
 // Signed angle subtended at (x,y) by the segment a->b:

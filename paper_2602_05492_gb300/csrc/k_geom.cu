@@ -60,23 +60,30 @@ __global__ void k_panelize(const double* __restrict__ theta, const int* __restri
 // a_h = sum_k length_k B_j((k+1/2)/K) over the panels of h's curve (a
 // segment handle: its length), then w_c <- w_c - a (a.w_c)/(a.a) per
 // channel (compatibility, Sec. 3.1.2 and the re-projection of Sec. 4.3).
-// One block; colour owner h has its w_c at theta[h (pp + 6) + pp + 3 + c].
+// One block of up to 1,024 threads (a warp per owner for the panel sums);
+// colour owner h has its w_c at theta[h (pp + 6) + pp + 3 + c].
 __global__ void k_compat(double* __restrict__ theta, const Panel<double>* __restrict__ pan,
                          const int* __restrict__ off, const int* __restrict__ Kc, int C, int pp,
                          double* __restrict__ a_out, int project) {
   extern __shared__ double sh[];   // [owners] a
   const int H = pp == 4 ? C : 4 * C, stride = pp + 6, wco = pp + 3;
   double* a = sh;
-  for (int h = threadIdx.x; h < H; h += blockDim.x) {
-    double s = 0;
-    if (pp == 4) {
-      s = pan[h].L;
-    } else {
-      int i = h / 4, j = h % 4, K = Kc[i];
-      for (int k = 0; k < K; ++k) s += pan[off[i] + k].L * bern3(j, (k + 0.5) / K);
+  {
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int h = threadIdx.x >> 5; h < H; h += nwarp) {
+      double s = 0;
+      if (pp == 4) {
+        s = lane == 0 ? pan[h].L : 0.0;
+      } else {
+        const int i = h / 4, j = h % 4, K = Kc[i];
+        for (int k = lane; k < K; k += 32) s += pan[off[i] + k].L * bern3(j, (k + 0.5) / K);
+      }
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        a[h] = s;
+        a_out[h] = s;
+      }
     }
-    a[h] = s;
-    a_out[h] = s;
   }
   __syncthreads();
   if (!project) return;
@@ -159,8 +166,8 @@ int geom_compat(bem_ctx* c, double* d_theta, bool project) {
   int C = c->sc.C;
   size_t shm = sizeof(double) * c->sc.NH;
   if (shm > 48 * 1024) return fail(c, BEM_EINVAL, "too many handles for the compatibility kernel");
-  k_compat<<<1, 256, shm, S(c)>>>(d_theta, c->d_pan64, c->sc.d_off, c->sc.d_K, C, c->sc.pp,
-                                  c->d_compat, project ? 1 : 0);
+  k_compat<<<1, 1024, shm, S(c)>>>(d_theta, c->d_pan64, c->sc.d_off, c->sc.d_K, C, c->sc.pp,
+                                   c->d_compat, project ? 1 : 0);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_compat");
 }

@@ -36,64 +36,66 @@ __global__ void k_phi_rows(const T* __restrict__ xy, int ns, const T* __restrict
 // Panel k of the curve runs from vertex k to vertex k+1 (vertex v = B(v/K)),
 // so the endpoint derivatives are first summed per vertex (panel k's start
 // plus panel k-1's end) and then spread to the control points with the
-// Bernstein weights B_j(v/K), read with the mid-parameter weights from a
-// per-block shared-memory table.
-constexpr int kFrowsTable = 256;   // panels per curve covered by the weight table
+// Bernstein weights B_j(v/K).  Each block stages its curve's panels, with
+// these weights and the mid-parameter ones, in shared memory, kFrowsTable
+// panels at a time.
+constexpr int kFrowsTable = 128;
 
 // One (point, panel) pair of the F rows: the two layer values and the
-// endpoint derivatives (a then b, x then y) of Dl and S.  The double path
-// returns them as they are; the float path returns them multiplied by -2 pi
-// (layer_grad_hat), which the kernel undoes once per output entry.
+// endpoint derivatives (a then b, x then y) of Dl and S.  iL as in
+// chain_endpoints.  The double path returns them as they are; the float
+// path returns them multiplied by -2 pi (layer_grad_hat), which the kernels
+// undo once per output entry.
 template <typename T, bool SAME>
-__device__ __forceinline__ void frows_pair(const Panel<T>& p, T x, T y, T ec2, T ed2, T& Dl, T& S,
-                                           T (&Dd)[4], T (&Sd)[4]) {
+__device__ __forceinline__ void frows_pair(T ax, T ay, T tx, T ty, T L, T iL, T x, T y, T ec2,
+                                           T ed2, T& Dl, T& S, T (&Dd)[4], T (&Sd)[4]) {
   if constexpr (sizeof(T) == 4) {
-    const Frame<float> f = frame_rn(p.ax, p.ay, p.tx, p.ty, p.L, x, y);
+    const Frame<float> f = frame_rn(ax, ay, tx, ty, L, x, y);
     const GradHat g = layer_grad_hat(f, f.h * f.h, ec2, ed2, SAME);
     Dl = g.D;
     S = g.S;
-    if (p.L > 0.f) {
-      frame_to_endpoints_f(p.tx, p.ty, f, g.Dt1, g.Dt2, g.Dh, Dd[0], Dd[1], Dd[2], Dd[3]);
-      frame_to_endpoints_f(p.tx, p.ty, f, g.St1, g.St2, g.Sh, Sd[0], Sd[1], Sd[2], Sd[3]);
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) { Dd[e] = 0.f; Sd[e] = 0.f; }
-    }
+    chain_endpoints(tx, ty, iL, f, g.Dt1, g.Dt2, g.Dh, Dd);
+    chain_endpoints(tx, ty, iL, f, g.St1, g.St2, g.Sh, Sd);
   } else {
-    const Frame<T> f = frame(p, x, y);
+    Frame<T> f;
+    const T dax = ax - x, day = ay - y;
+    f.t1 = dax * tx + day * ty;
+    f.h = dax * ty - day * tx;
+    f.L = L;
+    f.t2 = f.t1 + L;
     const LayerGrad<T> g = layer_grad(f, ec2, ed2, SAME);
     Dl = g.Dl;
     S = g.S;
-    if (p.L > T(0)) {
-      frame_to_endpoints(p, f, g.D_t1, g.D_t2, g.D_h, Dd[0], Dd[1], Dd[2], Dd[3]);
-      frame_to_endpoints(p, f, g.S_t1, g.S_t2, g.S_h, Sd[0], Sd[1], Sd[2], Sd[3]);
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) { Dd[e] = T(0); Sd[e] = T(0); }
-    }
+    chain_endpoints(tx, ty, iL, f, g.D_t1, g.D_t2, g.D_h, Dd);
+    chain_endpoints(tx, ty, iL, f, g.S_t1, g.S_t2, g.S_h, Sd);
   }
 }
+
+// A panel of the block's curve as k_frows stages it in shared memory: the
+// frame data, iL, the jumps with the handle term's signs folded in
+// (a = -w_d, b = w_c) and the Bernstein weights of the panel's start vertex
+// (wv) and midpoint (wm).
+template <typename T>
+struct __align__(16) FrowsPanel {
+  T ax, ay, tx, ty;
+  T L, iL, a[3], b[3];
+  T wv[4], wm[4];
+};
 
 template <typename T, bool SAME, bool TR>
 __global__ void __launch_bounds__(128, 6) k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __restrict__ pan,
                         const int* __restrict__ off, const int* __restrict__ Kc,
                         const uint8_t* __restrict__ closed, int C, T ec2, T ed2,
                         void* __restrict__ Fout, int ldf) {
-  __shared__ __align__(16) T wtab[kFrowsTable][8];     // B_j(k/K), B_j((k+1/2)/K)
+  __shared__ FrowsPanel<T> tab[kFrowsTable];
   // the float pair values carry a factor -2 pi (frows_pair)
   constexpr T kOut = sizeof(T) == 4 ? T(-kInv2Pi) : T(1);
   const int i = blockIdx.y;
   const int K = Kc[i];
-  for (int e = threadIdx.x; e < min(K, kFrowsTable) * 4; e += blockDim.x) {
-    const int k = e / 4, j = e % 4;
-    wtab[k][j] = bern3(j, T(k) / T(K));
-    wtab[k][4 + j] = bern3(j, (T(k) + T(0.5)) / T(K));
-  }
-  __syncthreads();
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= ns) return;
+  const bool live = s < ns;
   const int nc = 16 * C;
-  const T x = xy[2 * s], y = xy[2 * s + 1];
+  const T x = live ? xy[2 * s] : T(0), y = live ? xy[2 * s + 1] : T(0);
   T pos[4][2][3];
   T cd[4], cs[4];
   T carry[2][3];
@@ -110,33 +112,48 @@ __global__ void __launch_bounds__(128, 6) k_frows(const T* __restrict__ xy, int 
 #pragma unroll
     for (int c = 0; c < 3; ++c) carry[e][c] = 0;
   const Panel<T>* cp = pan + off[i];
-  for (int k = 0; k < K; ++k) {
-    const Panel<T> p = cp[k];
-    T wv[4], wm[4];
-    if (k < kFrowsTable) {
+  for (int k0 = 0; k0 < K; k0 += kFrowsTable) {
+    const int cnt = min(K - k0, kFrowsTable);
+    __syncthreads();   // every thread is done with the previous table
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const Panel<T> p = cp[k0 + e];
+      const int k = k0 + e;
+      FrowsPanel<T> r;
+      r.ax = p.ax; r.ay = p.ay; r.tx = p.tx; r.ty = p.ty;
+      r.L = p.L;
+      r.iL = inv_len(p.L);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { wv[j] = wtab[k][j]; wm[j] = wtab[k][4 + j]; }
-    } else {
+      for (int c = 0; c < 3; ++c) { r.a[c] = -p.wd[c]; r.b[c] = p.wc[c]; }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { wv[j] = bern3(j, T(k) / T(K)); wm[j] = bern3(j, (T(k) + T(0.5)) / T(K)); }
+      for (int j = 0; j < 4; ++j) {
+        r.wv[j] = bern3(j, T(k) / T(K));
+        r.wm[j] = bern3(j, (T(k) + T(0.5)) / T(K));
+      }
+      tab[e] = r;
     }
-    T Dl, S, Dd[4], Sd[4];
-    frows_pair<T, SAME>(p, x, y, ec2, ed2, Dl, S, Dd, Sd);
+    __syncthreads();
+    if (!live) continue;
+#pragma unroll (sizeof(T) == 4 ? 2 : 1)
+    for (int e = 0; e < cnt; ++e) {
+      const FrowsPanel<T>& r = tab[e];
+      T Dl, S, Dd[4], Sd[4];
+      frows_pair<T, SAME>(r.ax, r.ay, r.tx, r.ty, r.L, r.iL, x, y, ec2, ed2, Dl, S, Dd, Sd);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { cd[j] -= wm[j] * Dl; cs[j] += wm[j] * S; }
-    // vertex k: start of panel k and end of panel k-1
+      for (int j = 0; j < 4; ++j) { cd[j] = fma(-r.wm[j], Dl, cd[j]); cs[j] = fma(r.wm[j], S, cs[j]); }
+      // vertex k: start of panel k and end of panel k-1
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T a = -p.wd[c], b = p.wc[c];
+      for (int c = 0; c < 3; ++c) {
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const T v = a * Dd[e] + b * Sd[e] + carry[e][c];
-        carry[e][c] = a * Dd[2 + e] + b * Sd[2 + e];
+        for (int e2 = 0; e2 < 2; ++e2) {
+          const T v = fma(r.a[c], Dd[e2], fma(r.b[c], Sd[e2], carry[e2][c]));
+          carry[e2][c] = fma(r.a[c], Dd[2 + e2], r.b[c] * Sd[2 + e2]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) pos[j][e][c] += wv[j] * v;
+          for (int j = 0; j < 4; ++j) pos[j][e2][c] = fma(r.wv[j], v, pos[j][e2][c]);
+        }
       }
     }
   }
+  if (!live) return;
   // vertex K = B(1) = control point 3
 #pragma unroll
   for (int e = 0; e < 2; ++e)
@@ -194,8 +211,8 @@ __global__ void __launch_bounds__(128) k_phi_q(const float* __restrict__ xy, con
                                                int m, int slice_len, const float* __restrict__ vert,
                                                int Nb, void* __restrict__ phi0,
                                                void* __restrict__ phi1, double* __restrict__ qpart) {
-  __shared__ float2 sx[128];
-  __shared__ float sr[3][128];
+  __shared__ float4 sxr[128];   // x, y, r0, r1 of the slice's samples
+  __shared__ float sr2[128];     // r2
   const int j = blockIdx.x * 128 + threadIdx.x;
   const int s0 = blockIdx.y * slice_len, s1 = min(m, s0 + slice_len);
   const bool live = j < Nb;
@@ -207,18 +224,17 @@ __global__ void __launch_bounds__(128) k_phi_q(const float* __restrict__ xy, con
     __syncthreads();
     if ((int)threadIdx.x < cnt) {
       const int s = base + threadIdx.x;
-      sx[threadIdx.x] = make_float2(xy[2 * s], xy[2 * s + 1]);
-      if (r) {
-        sr[0][threadIdx.x] = r[3 * s];
-        sr[1][threadIdx.x] = r[3 * s + 1];
-        sr[2][threadIdx.x] = r[3 * s + 2];
-      }
+      sxr[threadIdx.x] = make_float4(xy[2 * s], xy[2 * s + 1], r ? r[3 * s] : 0.f,
+                                     r ? r[3 * s + 1] : 0.f);
+      sr2[threadIdx.x] = r ? r[3 * s + 2] : 0.f;
     }
     __syncthreads();
     if (!live) continue;
     float a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 4
     for (int k = 0; k < cnt; ++k) {
-      const float phi = seg_angle(ax, ay, bx, by, sx[k].x, sx[k].y) * float(kInv2Pi);
+      const float4 p = sxr[k];
+      const float phi = seg_angle(ax, ay, bx, by, p.x, p.y) * float(kInv2Pi);
       const size_t o = (size_t)(base + k) * Nb + j;
       if (X3) {
         const float h = tf32_round(phi);
@@ -227,7 +243,7 @@ __global__ void __launch_bounds__(128) k_phi_q(const float* __restrict__ xy, con
       } else {
         ((__nv_bfloat16*)phi0)[o] = __float2bfloat16_rn(phi);
       }
-      if (r) { a0 += phi * sr[0][k]; a1 += phi * sr[1][k]; a2 += phi * sr[2][k]; }
+      if (r) { a0 = fmaf(phi, p.z, a0); a1 = fmaf(phi, p.w, a1); a2 = fmaf(phi, sr2[k], a2); }
     }
     q0 += a0; q1 += a1; q2 += a2;
   }
@@ -394,7 +410,7 @@ __global__ void __launch_bounds__(128) k_frows_seg(const T* __restrict__ xy, int
   for (int h = h0; h < h1; ++h) {
     const Panel<T> p = pan[h];
     T Dl, S, Dd[4], Sd[4];
-    frows_pair<T, SAME>(p, x, y, ec2, ed2, Dl, S, Dd, Sd);
+    frows_pair<T, SAME>(p.ax, p.ay, p.tx, p.ty, p.L, inv_len(p.L), x, y, ec2, ed2, Dl, S, Dd, Sd);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const T a = -p.wd[c], b = p.wc[c];
