@@ -82,11 +82,18 @@ struct __align__(16) FrowsPanel {
   T wv[4], wm[4];
 };
 
+// With hw (float path only) the block also writes its curve's share of the
+// handle term at theta, hw[(c C + i) ldh + s] = sum over the curve's four
+// colour owners of F_c[s][w_d col] w_d,c + F_c[s][w_c col] w_c,c, from the
+// float values it stores in F^T and the jumps of theta (owner h at
+// theta[8 h + 2 .. 8 h + 7]).  The colour is linear in the jumps, so these
+// shares summed over the curves are the handle term of the colour.
 template <typename T, bool SAME, bool TR>
 __global__ void __launch_bounds__(128, 6) k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __restrict__ pan,
                         const int* __restrict__ off, const int* __restrict__ Kc,
                         const uint8_t* __restrict__ closed, int C, T ec2, T ed2,
-                        void* __restrict__ Fout, int ldf) {
+                        void* __restrict__ Fout, int ldf, const double* __restrict__ theta,
+                        float* __restrict__ hw, int ldh) {
   __shared__ FrowsPanel<T> tab[kFrowsTable];
   // the float pair values carry a factor -2 pi (frows_pair)
   constexpr T kOut = sizeof(T) == 4 ? T(-kInv2Pi) : T(1);
@@ -170,14 +177,21 @@ __global__ void __launch_bounds__(128, 6) k_frows(const T* __restrict__ xy, int 
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       float* base = F + (size_t)c * nc * ldf + s;
+      float t = 0.f;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         int h = 4 * i + j;
+        const float fd = float(kOut * cd[j]), fs = float(kOut * cs[j]);
         base[(size_t)(2 * h) * ldf] = float(kOut * pos[j][0][c]);
         base[(size_t)(2 * h + 1) * ldf] = float(kOut * pos[j][1][c]);
-        base[(size_t)(8 * C + h) * ldf] = float(kOut * cd[j]);
-        base[(size_t)(12 * C + h) * ldf] = float(kOut * cs[j]);
+        base[(size_t)(8 * C + h) * ldf] = fd;
+        base[(size_t)(12 * C + h) * ldf] = fs;
+        if (hw) {
+          t = fmaf(fd, float(theta[8 * h + 2 + c]), t);
+          t = fmaf(fs, float(theta[8 * h + 5 + c]), t);
+        }
       }
+      if (hw) hw[((size_t)c * C + i) * ldh + s] = t;
     }
     return;
   }
@@ -434,7 +448,8 @@ __global__ void __launch_bounds__(128) k_frows_seg(const T* __restrict__ xy, int
 }
 
 template <typename T, bool TR = false>
-static void launch_frows(bem_ctx* c, const T* xy, int ns, void* F, int ldf = 0) {
+static void launch_frows(bem_ctx* c, const T* xy, int ns, void* F, int ldf = 0,
+                         float* hw = nullptr, int ldh = 0) {
   int C = c->sc.C;
   dim3 grid((ns + 127) / 128, C);
   const Panel<T>* pan =
@@ -453,10 +468,12 @@ static void launch_frows(bem_ctx* c, const T* xy, int ns, void* F, int ldf = 0) 
   }
   if (c->opts.eps_c == c->opts.eps_d)
     k_frows<T, true, TR><<<grid, 128, 0, S(c)>>>(xy, ns, pan, c->sc.d_off, c->sc.d_K,
-                                                 c->sc.d_closed, C, ec2, ed2, F, ldf);
+                                                 c->sc.d_closed, C, ec2, ed2, F, ldf, c->d_theta,
+                                                 hw, ldh);
   else
     k_frows<T, false, TR><<<grid, 128, 0, S(c)>>>(xy, ns, pan, c->sc.d_off, c->sc.d_K,
-                                                  c->sc.d_closed, C, ec2, ed2, F, ldf);
+                                                  c->sc.d_closed, C, ec2, ed2, F, ldf, c->d_theta,
+                                                  hw, ldh);
   BEM_LAUNCHED(c);
 }
 
@@ -618,50 +635,37 @@ static int jtj_stacked_rhs(bem_ctx* c, bool solve = true) {
 // from the same J rows (Eq. (lossjacobian)): the handle part as a double
 // GEMV over F^T per chunk, the boundary part as q^T M_c = (A^+T q)^T Df_c
 // with q = sum_s phi_s r_s summed while the Phi rows are written.
-// Handle term of the colour at theta from the F rows.  The colour is linear
-// in the jumps, so f_c(x_s) = sum over colour owners h of F_c[s][w_d col h]
-// w_d,hc + F_c[s][w_c col h] w_c,hc: the colour columns of F_c times the
-// current jumps (F^T rows pp NH .. (pp + 2) NH - 1 of channel c).  hand[s][c]
-// += that (it already holds the near-field correction).  Thread = point; the
-// jumps staged as float in shared memory, [c][2 NH].
-__global__ void __launch_bounds__(256) k_hand_fw(const float* __restrict__ Ft, int ldf, int nc,
-                                                 int pp, int NH, const double* __restrict__ theta,
-                                                 int m, double* __restrict__ hand) {
-  extern __shared__ float wsh[];
-  const int stride = pp + 6, nw = 2 * NH;
-  for (int e = threadIdx.x; e < 3 * nw; e += blockDim.x) {
-    const int c = e / nw, k = e % nw, h = k % NH, isc = k / NH;
-    wsh[e] = float(theta[(size_t)h * stride + pp + 3 * isc + c]);
-  }
-  __syncthreads();
+// hand[s][c] += sum over the curves i (fixed order) of hw[(c C + i) ldh + s],
+// the curves' shares of the handle term at theta that k_frows wrote (hand
+// already holds the near-field correction).  Thread = point.
+__global__ void __launch_bounds__(256) k_hand_sum(const float* __restrict__ hw, int ldh, int C,
+                                                  int m, double* __restrict__ hand) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= m) return;
   for (int c = 0; c < 3; ++c) {
-    const float* f = Ft + ((size_t)c * nc + (size_t)pp * NH) * ldf + s;
-    const float* w = wsh + c * nw;
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int k = 0;
-    for (; k + 8 <= nw; k += 8) {
+    const float* p = hw + (size_t)c * C * ldh + s;
+    // eight independent partial sums keep eight loads in flight
+    double t[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int i = 0;
+    for (; i + 8 <= C; i += 8) {
       float v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = f[(size_t)(k + u) * ldf];
+      for (int u = 0; u < 8; ++u) v[u] = p[(size_t)(i + u) * ldh];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] = fmaf(v[u], w[k + u], acc[u]);
+      for (int u = 0; u < 8; ++u) t[u] += double(v[u]);
     }
-    for (; k < nw; ++k) acc[0] = fmaf(f[(size_t)k * ldf], w[k], acc[0]);
-    const float t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-    hand[3 * (size_t)s + c] += double(t);
+    for (; i < C; ++i) t[0] += double(p[(size_t)i * ldh]);
+    hand[3 * (size_t)s + c] += ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
   }
 }
 
-// The residual comes out of the J-row pass when reading the colour rows of F
-// (24 n_owner bytes per point) is cheaper than evaluating every pair again
-// (about 79 flops per panel): with more than six panels per colour owner,
-// i.e. Bezier curves of more than 24 panels, not for one-panel segment
-// handles.
+// The residual comes out of the J-row pass when forming the handle term from
+// the colour columns of the F rows (a few flops per colour owner and point)
+// is cheaper than evaluating every pair again (about 63 flops per panel):
+// with more than six panels per colour owner, i.e. Bezier curves of more
+// than 24 panels, not for one-panel segment handles.
 bool jtj_fuses_eval(const bem_ctx* c) {
-  return jtj_gives_gradient(c) && 6 * (size_t)c->sc.NH * sizeof(float) <= 48 * 1024 &&
-         c->sc.P > 6 * c->sc.NH;
+  return jtj_gives_gradient(c) && c->sc.P > 6 * c->sc.NH;
 }
 
 static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
@@ -711,7 +715,9 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   const size_t q_b = sizeof(double) * (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
   const size_t gb_b = sizeof(double) * 3 * (size_t)nc;
   bem_ctx* w = c->scratch ? c->scratch : c;   // owner of the chunk buffers
-  if ((rc = grow(c, w->jrow, phi_b + 256 + f_b + 256))) return rc;
+  // the curves' shares of the handle term at theta, [3][C][ld]
+  const size_t hw_b = fuse_r ? sizeof(float) * 3 * (size_t)C * ld : 0;
+  if ((rc = grow(c, w->jrow, phi_b + 256 + f_b + 256 + hw_b + 256))) return rc;
   if ((rc = grow(c, w->tcJ, j_b))) return rc;
   if (want_g && (rc = grow(c, w->gwork, gh_b + q_b + gb_b + 256))) return rc;
   const int splits = tc_syrk_splits(nc, x3);
@@ -720,6 +726,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   if ((rc = grow(c, c->Hc, sizeof(double) * 3 * (size_t)nc * nc))) return rc;
   const void* phi[2] = {w->jrow.p, (char*)w->jrow.p + phi_part};
   float* F = (float*)((char*)w->jrow.p + (phi_b + 255) / 256 * 256);
+  float* hw = fuse_r ? (float*)((char*)F + (f_b + 255) / 256 * 256) : nullptr;
   void* J[2] = {w->tcJ.p, (char*)w->tcJ.p + j_part};
   float* part = (float*)w->tcPart.p;
   double* gh = (double*)w->gwork.p;
@@ -743,7 +750,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
     return rc;
   for (int64_t s0 = 0; s0 < n; s0 += chunk, ++ci) {
     const int m = (int)std::min<int64_t>(chunk, n - s0);
-    launch_frows<float, true>(c, xy + 2 * s0, m, F, ld);
+    launch_frows<float, true>(c, xy + 2 * s0, m, F, ld, hw, ld);
     if (fuse_r) {
       if (c->opts.near_factor > 0) {
         if ((rc = near_forward_minus_float(c, m, xy + 2 * s0, hand))) return rc;
@@ -752,9 +759,8 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
         return rc;
       }
       {
-        ProfScope _ph(c, "k_hand_fw");
-        k_hand_fw<<<(m + 255) / 256, 256, sizeof(float) * 6 * (size_t)c->sc.NH, S(c)>>>(
-            F, ld, nc, c->sc.pp, c->sc.NH, c->d_theta, m, hand);
+        ProfScope _ph(c, "k_hand_sum");
+        k_hand_sum<<<(m + 255) / 256, 256, 0, S(c)>>>(hw, ld, C, m, hand);
         BEM_LAUNCHED(c);
       }
       if ((rc = field_finish_hand(c, m, xy + 2 * s0, hand, target + 3 * s0,
