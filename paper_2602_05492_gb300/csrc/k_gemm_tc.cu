@@ -21,8 +21,9 @@
 //              slice of samples, added to that slice's fp32 partial sum
 // The bf16 J rows run in a persistent, warp-specialised variant
 // (k_tc_jrows_pers): one CTA per SM, a producer warp, an MMA warp and eight
-// epilogue warps, with two TMEM accumulators so that a tile's epilogue
-// overlaps the next tile's MMAs.
+// epilogue warps, 128 x 256 tiles (M = 128, N = 256 MMAs), with two
+// 256-column TMEM accumulators so that a tile's epilogue overlaps the next
+// tile's MMAs.
 // Every wait is bounded (about one second); a timeout sets *err and the CTA
 // drains and frees its TMEM before returning.
 #include <cuda_bf16.h>
@@ -317,22 +318,30 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
 
 // ---- bf16 J rows, persistent ----------------------------------------------
 // One CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// (t = row tile + col tile * row tiles, so consecutive tiles share their Phi
-// tile).  Warp 0 lane 0 streams A/B slabs through a PSTAGES ring (TMA), warp 1
-// lane 0 issues the MMAs into one of two 128-column TMEM accumulators, and
-// warps 2..9 drain the other: warp w owns TMEM lanes 32 (w % 4) .. +31 and
-// the columns 64 ((w - 2) / 4) .. +63 of them.  So the epilogue of a tile
-// (F rows added, bf16 packing, the handle part of the gradient, coalesced
-// stores) overlaps the MMAs of the next.  Per tile the F rows are copied by
-// cp.async into fs (issued once the previous tile's rows are stored); row r
-// holds 32 chunks of 16 bytes, logical chunk c at position c ^ (r & 7).  The
-// bf16 result is written back in place: output chunk o of column half h goes
-// to position (16 h + o) ^ (r & 7), which held an F chunk of the same half
-// that has already been read, so the two warps of a row never overlap.
-constexpr int PSTAGES = 4;
+// of 128 rows x 256 samples (t = row tile + col tile * row tiles, so
+// consecutive tiles share their Phi tile).  Warp 0 lane 0 streams A/B slabs
+// (A 128 rows, B 256 rows as two 128-row boxes) through a PSTAGES ring (TMA),
+// warp 1 lane 0 issues M = 128, N = 256 MMAs into one of two 256-column TMEM
+// accumulators, and warps 2..9 drain the other in two passes of 128 columns:
+// warp w owns TMEM lanes 32 (w % 4) .. +31 and the columns 64 ((w - 2) / 4)
+// .. +63 of the pass.  The epilogue of a tile (F rows added, bf16 packing,
+// the handle part of the gradient, coalesced stores) overlaps the MMAs of
+// the next.  One 256-sample tile per MMA halves the operand bytes per output
+// of the A slabs against 128-sample tiles, the share of the L2 traffic that
+// bounds this contraction.  Per pass the F rows are copied by cp.async into
+// fs (the first pass's once the previous tile's rows are stored); row r holds
+// 32 chunks of 16 bytes, logical chunk c at position c ^ (r & 7).  The bf16
+// result is written back in place: output chunk o of column half h goes to
+// position (16 h + o) ^ (r & 7), which held an F chunk of the same half that
+// has already been read, so the two warps of a row never overlap.
+constexpr int PSTAGES = 3;
+constexpr int kPersBN = 256;                          // samples per tile
+constexpr int kPersPass = kPersBN / BN;               // epilogue passes of BN columns
+constexpr int kPersStage = TILE_BYTES * (1 + kPersPass);   // A slab + B slab (48 KB)
 constexpr int kPersThreads = 320;           // 2 control warps + 8 epilogue warps
-constexpr int kPersSmem = 1024 + PSTAGES * 2 * TILE_BYTES + BM * BN * 4 + 3 * BN * 4 +
-                          2 * BM * 4 + 256;
+constexpr int kPersSmem = 1024 + PSTAGES * kPersStage + BM * BN * 4 + 3 * BN * 4 + 2 * BM * 4 +
+                          256;
+static_assert(kPersSmem <= 227 * 1024, "persistent J-row kernel exceeds shared memory");
 
 __device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   constexpr int BK = Scheme<false>::BK;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* fs = reinterpret_cast<float*>(smem + PSTAGES * 2 * TILE_BYTES);      // [BM][BN] F rows
+  float* fs = reinterpret_cast<float*>(smem + PSTAGES * kPersStage);        // [BM][BN] F rows
   float* rs = fs + BM * BN;                                                  // [BN][3] residuals
   float* gsum = rs + 3 * BN;                                                 // [2][BM]
   uint64_t* full = reinterpret_cast<uint64_t*>(gsum + 2 * BM);
@@ -357,7 +366,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   int* fail_flag = reinterpret_cast<int*>(tmem_slot + 1);   // set when an epilogue wait gave up
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rtiles = (g.M + BM - 1) / BM, ctiles = (g.N + BN - 1) / BN;
+  const int rtiles = (g.M + BM - 1) / BM, ctiles = (g.N + kPersBN - 1) / kPersBN;
   const int ntiles = rtiles * ctiles;
   const int nk = (g.K + BK - 1) / BK;
   if (threadIdx.x == 0) {
@@ -372,7 +381,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
     }
     umma::fence_barrier_init();
   }
-  if (warp == 0) umma::tmem_alloc(tmem_slot, 256);
+  if (warp == 0) umma::tmem_alloc(tmem_slot, 2 * kPersBN);
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
@@ -384,15 +393,17 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       int it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int arow = (t % rtiles) * BM, brow = (t / rtiles) * BN;
+        const int arow = (t % rtiles) * BM, brow = (t / rtiles) * kPersBN;
         for (int kk = 0; kk < nk; ++kk, ++it) {
           const int s = it % PSTAGES;
           const uint32_t ph = (it / PSTAGES) & 1;
           if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err)) { ok = false; break; }
-          umma::mbar_expect_tx(&full[s], 2 * TILE_BYTES);
-          uint8_t* st = smem + (size_t)s * 2 * TILE_BYTES;
+          umma::mbar_expect_tx(&full[s], kPersStage);
+          uint8_t* st = smem + (size_t)s * kPersStage;
           umma::tma_load_2d(st, &tA, &full[s], kk * BK, arow);
-          umma::tma_load_2d(st + TILE_BYTES, &tB, &full[s], kk * BK, brow);
+#pragma unroll
+          for (int p = 0; p < kPersPass; ++p)
+            umma::tma_load_2d(st + (1 + p) * TILE_BYTES, &tB, &full[s], kk * BK, brow + p * BN);
         }
       }
       // the last loads of every slot have landed before the CTA can leave
@@ -402,21 +413,21 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer: tile i of this CTA accumulates into TMEM buffer i & 1
-      const uint32_t id = umma::idesc(1, BM, BN);
+      const uint32_t id = umma::idesc(1, BM, kPersBN);
       int it = 0, i = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
         const int b = i & 1;
         if (!umma::mbar_wait(&tempty[b], ((i >> 1) & 1) ^ 1, g.err)) break;
         umma::fence_after();
-        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        const uint32_t acc = tmem + (uint32_t)(b * kPersBN);
         for (int kk = 0; kk < nk; ++kk, ++it) {
           const int s = it % PSTAGES;
           const uint32_t ph = (it / PSTAGES) & 1;
           if (!umma::mbar_wait(&full[s], ph, g.err)) { ok = false; break; }
           umma::fence_after();
-          const uint32_t a0 = umma::smem_u32(smem + (size_t)s * 2 * TILE_BYTES);
-          const uint32_t b0 = a0 + TILE_BYTES;
+          const uint32_t a0 = umma::smem_u32(smem + (size_t)s * kPersStage);
+          const uint32_t b0 = a0 + TILE_BYTES;   // 256 rows: two 128-row boxes back to back
 #pragma unroll
           for (int k4 = 0; k4 < 4; ++k4)
             umma::mma_bf16(acc, umma::sdesc_sw128(a0 + k4 * 32), umma::sdesc_sw128(b0 + k4 * 32), id,
@@ -431,11 +442,12 @@ __global__ void __launch_bounds__(kPersThreads, 1)
     const int et = threadIdx.x - 64;                 // 0 .. 255
     const int q = warp & 3, half = (warp - 2) >> 2;  // TMEM lane quarter, column half
     const int r = 32 * q + lane;                     // tile row of this thread
-    auto stage = [&](int t) {
-      const int arow = (t % rtiles) * BM, brow = (t / rtiles) * BN;
+    // F rows and residuals of pass p of tile t (columns col0 .. col0 + BN - 1)
+    auto stage = [&](int t, int p) {
+      const int arow = (t % rtiles) * BM, col0 = (t / rtiles) * kPersBN + p * BN;
       for (int e = et; e < BM * (BN / 4); e += 256) {
         const int rr = e / (BN / 4), cc = e % (BN / 4);
-        const int row = arow + rr, col = brow + cc * 4;
+        const int row = arow + rr, col = col0 + cc * 4;
         float* d = fs + rr * BN + ((cc ^ (rr & 7)) << 2);
         if (row < g.M && col + 3 < g.N) {
           umma::cp_async16(d, g.F + (size_t)row * g.ldf + col);
@@ -449,94 +461,106 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       }
       if (g.gpart)
         for (int e = et; e < 3 * BN; e += 256) {
-          const int col = brow + e / 3;
+          const int col = col0 + e / 3;
           rs[e] = col < g.N ? g.resid[3 * (size_t)col + e % 3] : 0.f;
         }
     };
-    if (blockIdx.x < ntiles) stage(blockIdx.x);
+    if (blockIdx.x < ntiles) stage(blockIdx.x, 0);
     int i = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
       const int b = i & 1;
-      const int arow = (t % rtiles) * BM, brow = (t / rtiles) * BN, ct = t / rtiles;
+      const int arow = (t % rtiles) * BM, ct = t / rtiles;
       if (!umma::mbar_wait(&tfull[b], (i >> 1) & 1, g.err)) atomicOr(fail_flag, 1);
       umma::fence_after();
-      umma::cp_async_wait_all();
-      bar_epi();
-      const bool ok = *(volatile int*)fail_flag == 0;   // the same for all epilogue threads
-      const int gch = (g.gpart && arow + r < g.M) ? (arow + r) / g.gnc : 0;
-      float gacc = 0.f;
-      const float* fr = fs + r * BN;
-      const int sw = r & 7;
+      for (int p = 0; p < kPersPass; ++p) {
+        const int col0 = ct * kPersBN + p * BN;
+        // fs holds pass 0's rows already (staged after the previous tile's stores)
+        if (p > 0) stage(t, p);
+        umma::cp_async_wait_all();
+        bar_epi();
+        ok = *(volatile int*)fail_flag == 0;   // the same for all epilogue threads
+        const int gch = (g.gpart && arow + r < g.M) ? (arow + r) / g.gnc : 0;
+        float gacc = 0.f;
+        const float* fr = fs + r * BN;
+        const int sw = r & 7;
 #pragma unroll 1
-      for (int cb = 64 * half; cb < 64 * half + 64; cb += 32) {
-        float v[32];
-        umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cb), v);
-        if (!ok) {
+        for (int cb = 64 * half; cb < 64 * half + 64; cb += 32) {
+          float v[32];
+          umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kPersBN + p * BN + cb), v);
+          if (!ok) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = 0.f;
-        }
-        float f[32];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float4 w4 = *reinterpret_cast<const float4*>(fr + ((((cb >> 2) + k) ^ sw) << 2));
-          f[4 * k] = w4.x; f[4 * k + 1] = w4.y; f[4 * k + 2] = w4.z; f[4 * k + 3] = w4.w;
-        }
-        if (g.gpart) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rs[3 * (cb + j) + gch], gacc);
-        }
-        // output chunks of this 32-column block: o = ((cb - 64 half) >> 3) + k
-        uint8_t* jr = reinterpret_cast<uint8_t*>(fs + r * BN);
-        const int o0 = 16 * half + ((cb - 64 * half) >> 3);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          uint4 w;
-          uint32_t* wp = &w.x;
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * k + 2 * h] + f[8 * k + 2 * h],
-                                                            v[8 * k + 2 * h + 1] + f[8 * k + 2 * h + 1]);
-            wp[h] = *reinterpret_cast<const uint32_t*>(&b2);
+            for (int j = 0; j < 32; ++j) v[j] = 0.f;
           }
-          *reinterpret_cast<uint4*>(jr + (((o0 + k) ^ sw) << 4)) = w;
+          float f[32];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float4 w4 = *reinterpret_cast<const float4*>(fr + ((((cb >> 2) + k) ^ sw) << 2));
+            f[4 * k] = w4.x; f[4 * k + 1] = w4.y; f[4 * k + 2] = w4.z; f[4 * k + 3] = w4.w;
+          }
+          if (g.gpart) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rs[3 * (cb + j) + gch], gacc);
+          }
+          // output chunks of this 32-column block: o = ((cb - 64 half) >> 3) + k
+          uint8_t* jr = reinterpret_cast<uint8_t*>(fs + r * BN);
+          const int o0 = 16 * half + ((cb - 64 * half) >> 3);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            uint4 w;
+            uint32_t* wp = &w.x;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * k + 2 * h] + f[8 * k + 2 * h],
+                                                              v[8 * k + 2 * h + 1] + f[8 * k + 2 * h + 1]);
+              wp[h] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
+            *reinterpret_cast<uint4*>(jr + (((o0 + k) ^ sw) << 4)) = w;
+          }
         }
-      }
-      gsum[half * BM + r] = gacc;
-      // this warp's TMEM reads are complete: release the buffer
-      umma::fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[b]);
-      bar_epi();
-      if (g.gpart && et < BM && arow + et < g.M)
-        g.gpart[(size_t)(arow + et) * g.gstride + ct] = (double)(gsum[et] + gsum[BM + et]);
-      // bf16 rows: one warp writes a 256-byte row per step, 8 bytes per lane
-      for (int rr = warp - 2; rr < BM; rr += 8) {
-        const int row = arow + rr;
-        if (row >= g.M) continue;
-        const int col = brow + lane * 4;
-        const int oc = lane >> 1;                      // output chunk 0..15 of the row
-        const int pos = (oc < 8 ? oc : oc + 8) ^ (rr & 7);
-        const uint8_t* src = reinterpret_cast<const uint8_t*>(fs + rr * BN) + ((pos << 4) | ((lane & 1) << 3));
-        __nv_bfloat16* dst = g.J + (size_t)row * g.ldj + col;
-        if (col + 3 < g.N) {
-          *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
-        } else {
-          const __nv_bfloat16* sb = reinterpret_cast<const __nv_bfloat16*>(src);
-          for (int u = 0; u < 4; ++u)
-            if (col + u < g.N) dst[u] = sb[u];
+        gsum[half * BM + r] = gacc;
+        if (p == kPersPass - 1 || !ok) {
+          // this warp's TMEM reads of the tile are complete (or given up, and
+          // the loop ends after this pass): release the buffer
+          umma::fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[b]);
         }
+        bar_epi();
+        // the gradient partial of each 128-sample column block (a block past
+        // the chunk's end holds nothing and is not written)
+        if (g.gpart && et < BM && arow + et < g.M && col0 < g.N)
+          g.gpart[(size_t)(arow + et) * g.gstride + (kPersPass * ct + p)] =
+              (double)(gsum[et] + gsum[BM + et]);
+        // bf16 rows: one warp writes a 256-byte row per step, 8 bytes per lane
+        for (int rr = warp - 2; rr < BM; rr += 8) {
+          const int row = arow + rr;
+          if (row >= g.M) continue;
+          const int col = col0 + lane * 4;
+          const int oc = lane >> 1;                      // output chunk 0..15 of the row
+          const int pos = (oc < 8 ? oc : oc + 8) ^ (rr & 7);
+          const uint8_t* src = reinterpret_cast<const uint8_t*>(fs + rr * BN) + ((pos << 4) | ((lane & 1) << 3));
+          __nv_bfloat16* dst = g.J + (size_t)row * g.ldj + col;
+          if (col + 3 < g.N) {
+            *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
+          } else {
+            const __nv_bfloat16* sb = reinterpret_cast<const __nv_bfloat16*>(src);
+            for (int u = 0; u < 4; ++u)
+              if (col + u < g.N) dst[u] = sb[u];
+          }
+        }
+        bar_epi();
+        if (!ok) break;
       }
-      bar_epi();
-      if (!ok) break;
-      // fs now free: the next tile's F rows come in while its MMAs run
-      if (t + (int)gridDim.x < ntiles) stage(t + gridDim.x);
+      // fs now free: the next tile's first F rows come in while its MMAs run
+      if (ok && t + (int)gridDim.x < ntiles) stage(t + gridDim.x, 0);
     }
     umma::cp_async_wait_all();
   }
   __syncwarp();
   umma::fence_before();
   __syncthreads();
-  if (warp == 0) umma::tmem_dealloc(tmem, 256);
+  if (warp == 0) umma::tmem_dealloc(tmem, 2 * kPersBN);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
@@ -639,7 +663,7 @@ int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const int ntiles = ((rows + BM - 1) / BM) * ((m + BN - 1) / BN);
+    const int ntiles = ((rows + BM - 1) / BM) * ((m + kPersBN - 1) / kPersBN);
     const int grid = std::max(1, std::min(ntiles, sms));
     k_tc_jrows_pers<<<grid, kPersThreads, kPersSmem, S(c)>>>(ta, tb, g);
     BEM_LAUNCHED(c);
