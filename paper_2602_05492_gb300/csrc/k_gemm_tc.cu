@@ -563,6 +563,169 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   if (warp == 0) umma::tmem_dealloc(tmem, 2 * kPersBN);
 }
 
+// ---- bf16 Gram blocks on paired tiles ----------------------------------------
+// The upper 128 x 128 blocks (ti <= tj) of each channel's J_c^T J_c are
+// grouped into units of two blocks that share an operand slab:
+//   kind 1  (ti, tj), (ti, tj + 1): one M = 128, N = 256 MMA on B rows of
+//           tiles tj, tj + 1 (the pairs along each block row, from the
+//           diagonal on)
+//   kind 2  (ti, T - 1), (ti + 2, T - 1): two M = 128, N = 128 MMAs on the
+//           same B slab (the last blocks of the rows with an odd count)
+//   kind 0  (T - 1, T - 1) when one such block is left over
+// A unit streams two or three 16 KB slabs per K step (one fewer where an A
+// tile is also the B tile) for two blocks, against two slabs per block
+// for single blocks: about a quarter fewer L2 bytes per MMA.
+struct SyrkUnit {
+  int kind, a0, a1, b;
+};
+
+// unit u of the T x T upper block triangle, in the order above
+__device__ __forceinline__ SyrkUnit syrk_unit(int T, int u) {
+  int np = 0;
+  for (int r = 0; r < T; ++r) np += (T - r) / 2;
+  SyrkUnit un;
+  if (u < np) {
+    int r = 0;
+    while (u >= (T - r) / 2) { u -= (T - r) / 2; ++r; }
+    un.kind = 1; un.a0 = r; un.a1 = r; un.b = r + 2 * u;
+  } else {
+    u -= np;
+    const int r0 = (T - 1) & 1, L = (T + 1) / 2;   // rows with an odd block count: r0, r0 + 2, ..
+    if (2 * u + 1 < L) {
+      un.kind = 2; un.a0 = r0 + 4 * u; un.a1 = un.a0 + 2; un.b = T - 1;
+    } else {
+      un.kind = 0; un.a0 = T - 1; un.a1 = T - 1; un.b = T - 1;
+    }
+  }
+  return un;
+}
+
+int syrk_units(int T) {
+  int np = 0;
+  for (int r = 0; r < T; ++r) np += (T - r) / 2;
+  return np + ((T + 1) / 2 + 1) / 2;
+}
+
+constexpr int SY_STAGES = 4;
+constexpr int kSyStage = 3 * TILE_BYTES;     // up to three 128-row slabs (48 KB)
+constexpr int kSySmem = 1024 + SY_STAGES * kSyStage + 256;
+
+// part[split][ch][i][j] += the unit's two blocks over its K slice;
+// blockIdx.x = ch * units + unit, blockIdx.y = K slice.  g.tiles = T,
+// g.npairs = units per channel.
+__global__ void __launch_bounds__(128, 1)
+    k_tc_syrk_pair(const __grid_constant__ CUtensorMap tJ, TcArgs g) {
+  constexpr int BK = Scheme<false>::BK;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + SY_STAGES * kSyStage);
+  uint64_t* empty = full + SY_STAGES;
+  uint64_t* done = empty + SY_STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ch = blockIdx.x / g.npairs;
+  const SyrkUnit un = syrk_unit(g.tiles, blockIdx.x % g.npairs);
+  const int rbase = ch * g.nc;
+  const int kb = blockIdx.y * g.k_per_split, ke = min(g.K, kb + g.k_per_split);
+  const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;
+  // slab 0: A (a0), slab 1: A (a1, kind 2) or B, slab 2: B (kind 2) or B's second tile (kind 1)
+  const bool loadA0 = un.kind == 2 || un.a0 != un.b;
+  const bool loadA1 = un.kind == 2 && un.a1 != un.b;
+  const int nslab = (loadA0 ? 1 : 0) + (loadA1 ? 1 : 0) + (un.kind == 0 ? 1 : 2) - (un.kind == 2 ? 1 : 0);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SY_STAGES; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    umma::mbar_init(done, 1);
+    umma::fence_barrier_init();
+  }
+  if (warp == 0) umma::tmem_alloc(tmem_slot, 256);
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % SY_STAGES;
+      const uint32_t ph = (it / SY_STAGES) & 1;
+      if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err)) break;
+      umma::mbar_expect_tx(&full[s], nslab * TILE_BYTES);
+      const int kc = kb + it * BK;
+      uint8_t* st = smem + (size_t)s * kSyStage;
+      if (loadA0) umma::tma_load_2d(st, &tJ, &full[s], kc, rbase + un.a0 * BM);
+      if (un.kind == 2) {
+        if (loadA1) umma::tma_load_2d(st + TILE_BYTES, &tJ, &full[s], kc, rbase + un.a1 * BM);
+        umma::tma_load_2d(st + 2 * TILE_BYTES, &tJ, &full[s], kc, rbase + un.b * BM);
+      } else {
+        umma::tma_load_2d(st + TILE_BYTES, &tJ, &full[s], kc, rbase + un.b * BM);
+        if (un.kind == 1)
+          umma::tma_load_2d(st + 2 * TILE_BYTES, &tJ, &full[s], kc, rbase + (un.b + 1) * BM);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t id128 = umma::idesc(1, BM, BN), id256 = umma::idesc(1, BM, 2 * BN);
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % SY_STAGES;
+      const uint32_t ph = (it / SY_STAGES) & 1;
+      if (!umma::mbar_wait(&full[s], ph, g.err)) break;
+      umma::fence_after();
+      const uint32_t s0 = umma::smem_u32(smem + (size_t)s * kSyStage);
+      const uint32_t s1 = s0 + TILE_BYTES, s2 = s0 + 2 * TILE_BYTES;
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4) {
+        const uint32_t acc = (it | k4) != 0;
+        if (un.kind == 2) {
+          const uint64_t db = umma::sdesc_sw128(s2 + k4 * 32);
+          umma::mma_bf16(tmem, umma::sdesc_sw128(s0 + k4 * 32), db, id128, acc);
+          umma::mma_bf16(tmem + BN, umma::sdesc_sw128((loadA1 ? s1 : s2) + k4 * 32), db, id128,
+                         acc);
+        } else {
+          const uint64_t da = umma::sdesc_sw128((loadA0 ? s0 : s1) + k4 * 32);
+          umma::mma_bf16(tmem, da, umma::sdesc_sw128(s1 + k4 * 32), un.kind == 1 ? id256 : id128,
+                         acc);
+        }
+      }
+      umma::mma_commit(&empty[s]);
+    }
+    umma::mma_commit(done);
+  }
+  __syncwarp();
+  // ---- epilogue: all four warps, thread r = row of the unit's row tile(s)
+  const bool ok = umma::mbar_wait(done, 0, g.err);
+  umma::fence_after();
+  const int r = warp * 32 + lane;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  const int nout = un.kind == 0 ? 1 : 2;
+  for (int o = 0; o < nout; ++o) {
+    const int ti = (un.kind == 2 && o == 1) ? un.a1 : un.a0;
+    const int tj = un.kind == 1 ? un.b + o : un.b;
+    const int i = ti * BM + r;
+#pragma unroll 1
+    for (int cb = 0; cb < BN; cb += 32) {
+      float v[32];
+      umma::tmem_ld32(trow + o * BN + cb, v);
+      if (!ok || nk == 0) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+      }
+      if (i < g.nc) {
+        float* d = g.part + (((size_t)blockIdx.y * 3 + ch) * g.nc + i) * g.nc;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = tj * BN + cb + j;
+          if (col < g.nc) d[col] += v[j];
+        }
+      }
+    }
+  }
+  umma::fence_before();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, 256);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -691,8 +854,21 @@ int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, f
   g.part = part; g.err = c->d_status;
   int sp = (m + g.k_per_split - 1) / g.k_per_split;
   ProfScope _ps(c, "tc_syrk");
+  if (!x3) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_tc_syrk_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kSySmem);
+      if (e != cudaSuccess) return cuda_check(c, e, "paired Gram smem attribute");
+      attr = true;
+    }
+    g.npairs = syrk_units(g.tiles);
+    k_tc_syrk_pair<<<dim3(3 * g.npairs, sp), 128, kSySmem, S(c)>>>(tj, g);
+    BEM_LAUNCHED(c);
+    return cuda_check(c, cudaGetLastError(), "k_tc_syrk_pair");
+  }
   dim3 grid(3 * g.npairs, sp);
-  return x3 ? launch<true>(c, tj, tj, tj2, tj2, g, grid) : launch<false>(c, tj, tj, tj, tj, g, grid);
+  return launch<true>(c, tj, tj, tj2, tj2, g, grid);
 }
 
 // K slices per block pair: as many as fill the resident CTA slots in one
@@ -700,8 +876,9 @@ int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, f
 // a short tail wave that costs as long as the first)
 int tc_syrk_splits(int nc, bool x3) {
   int tiles = (nc + BM - 1) / BM;
-  int ctas = 3 * tiles * (tiles + 1) / 2;
-  int slots = (x3 ? 1 : 2) * 152;
+  // bf16: one CTA per SM on paired blocks; 3xtf32: one CTA per SM per block
+  int ctas = 3 * (x3 ? tiles * (tiles + 1) / 2 : syrk_units(tiles));
+  int slots = 152;
   return std::max(1, std::min(64, slots / ctas));
 }
 
