@@ -878,8 +878,18 @@ int tc_syrk_splits(int nc, bool x3) {
   int tiles = (nc + BM - 1) / BM;
   // bf16: one CTA per SM on paired blocks; 3xtf32: one CTA per SM per block
   int ctas = 3 * (x3 ? tiles * (tiles + 1) / 2 : syrk_units(tiles));
-  int slots = 152;
-  return std::max(1, std::min(64, slots / ctas));
+  const int slots = 152;
+  // the fewest slices whose CTAs fill their waves to 95 %, else the best fill up to 8 slices
+  // (204 units at n_c = 2,048: one slice leaves the second wave a third full, three fill four)
+  int best = 1;
+  double best_fill = 0.0;
+  for (int sp = 1; sp <= 64; ++sp) {
+    const int n = ctas * sp;
+    const double fill = double(n) / (double((n + slots - 1) / slots) * slots);
+    if (fill >= 0.95) return sp;
+    if (sp <= 8 && fill > best_fill) { best_fill = fill; best = sp; }
+  }
+  return best;
 }
 
 }  // namespace bem
