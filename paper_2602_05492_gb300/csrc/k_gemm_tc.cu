@@ -19,6 +19,8 @@
 //              tf32 hi/lo pair of D + F in the 3xtf32 scheme
 //   EPI_SYRK   one upper-triangular 128 x 128 block of J_c^T J_c over a K
 //              slice of samples, added to that slice's fp32 partial sum
+//              (3xtf32; the bf16 Gram blocks run in k_tc_syrk_pair, two
+//              blocks per CTA that share an operand slab)
 // The bf16 J rows run in a persistent, warp-specialised variant
 // (k_tc_jrows_pers): one CTA per SM, a producer warp, an MMA warp and eight
 // epilogue warps, 128 x 256 tiles (M = 128, N = 256 MMAs), with two
