@@ -90,28 +90,31 @@ __device__ __forceinline__ void panel_cells(const Panel<float>& p, float nf, int
   y1 = cell_of(fmaxf(p.ay, by) + r, G);
 }
 
+// One warp per panel: the lanes take the cells of the panel's box in turn
+// (a box spans tens of cells; one thread per panel would wait for each
+// cell's atomic in sequence).
 __global__ void k_pbin_count(const Panel<float>* __restrict__ pan, int P, float nf, int G,
                              int* __restrict__ cnt) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (p >= P) return;
   int x0, x1, y0, y1;
   panel_cells(pan[p], nf, G, x0, x1, y0, y1);
-  for (int cy = y0; cy <= y1; ++cy)
-    for (int cx = x0; cx <= x1; ++cx) atomicAdd(&cnt[cy * G + cx], 1);
+  const int w = x1 - x0 + 1, ncell = w * (y1 - y0 + 1);
+  for (int k = lane; k < ncell; k += 32) atomicAdd(&cnt[(y0 + k / w) * G + x0 + k % w], 1);
 }
 
 __global__ void k_pbin_fill(const Panel<float>* __restrict__ pan, int P, float nf, int G,
                             const int* __restrict__ start, int* __restrict__ fill,
                             int* __restrict__ items) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (p >= P) return;
   int x0, x1, y0, y1;
   panel_cells(pan[p], nf, G, x0, x1, y0, y1);
-  for (int cy = y0; cy <= y1; ++cy)
-    for (int cx = x0; cx <= x1; ++cx) {
-      int cell = cy * G + cx;
-      items[start[cell] + atomicAdd(&fill[cell], 1)] = p;
-    }
+  const int w = x1 - x0 + 1, ncell = w * (y1 - y0 + 1);
+  for (int k = lane; k < ncell; k += 32) {
+    const int cell = (y0 + k / w) * G + x0 + k % w;
+    items[start[cell] + atomicAdd(&fill[cell], 1)] = p;
+  }
 }
 
 __global__ void k_sbin_count(const float* __restrict__ xy, int64_t n, int G, int* __restrict__ cnt) {
@@ -175,8 +178,8 @@ static int build_bins(bem_ctx* c, DevBuf& buf, bool panels, int64_t n, const flo
                        "memset")))
     return rc;
   if (panels)
-    k_pbin_count<<<(P + 127) / 128, 128, 0, S(c)>>>(c->d_pan32, P, (float)c->opts.near_factor, G,
-                                                    start);
+    k_pbin_count<<<(P + 7) / 8, 256, 0, S(c)>>>(c->d_pan32, P, (float)c->opts.near_factor, G,
+                                                start);
   else
     k_sbin_count<<<(unsigned)((n + 255) / 256), 256, 0, S(c)>>>(xy, n, G, start);
   BEM_LAUNCHED(c);
@@ -201,8 +204,8 @@ static int build_bins(bem_ctx* c, DevBuf& buf, bool panels, int64_t n, const flo
   }
   int* items = (int*)((char*)buf.p + head);
   if (panels)
-    k_pbin_fill<<<(P + 127) / 128, 128, 0, S(c)>>>(c->d_pan32, P, (float)c->opts.near_factor, G,
-                                                   start, fill, items);
+    k_pbin_fill<<<(P + 7) / 8, 256, 0, S(c)>>>(c->d_pan32, P, (float)c->opts.near_factor, G,
+                                               start, fill, items);
   else
     k_sbin_fill<<<(unsigned)((n + 255) / 256), 256, 0, S(c)>>>(xy, n, G, start, fill, items);
   k_bin_sort<<<(ncell + 255) / 256, 256, 0, S(c)>>>(start, ncell, items);
