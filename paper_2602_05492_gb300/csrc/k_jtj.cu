@@ -705,7 +705,10 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   const size_t j_part = (x3 ? 4 : 2) * 3 * (size_t)nc * ld;
   const size_t j_b = (x3 ? 2 : 1) * j_part;
   // gradient work: per chunk handle partial [3nc], q partials per slice
-  const int qslices = (int)std::max<int64_t>(1, std::min<int64_t>(64, (chunk + 4095) / 4096));
+  // sample slices of the Phi-row pass: 1,024 samples each, up to 256 (a
+  // 262,144-sample chunk gives 8 x 256 CTAs, enough to fill the SMs to the
+  // kernel's register limit of 12 CTAs)
+  const int qslices = (int)std::max<int64_t>(1, std::min<int64_t>(256, (chunk + 1023) / 1024));
   // handle part of the gradient: bf16 J rows form it per 128-sample tile in
   // their epilogue ([3nc][tiles]); 3xtf32 runs a GEMV per chunk ([chunks x segs][3nc])
   const bool fused_g = want_g && !x3;
@@ -770,7 +773,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
     }
     {
       ProfScope _pp(c, "k_phi_rows");
-      const int sl = want_g ? qslices : (int)std::max<int64_t>(1, std::min<int64_t>(64, (m + 4095) / 4096));
+      const int sl = want_g ? qslices : (int)std::max<int64_t>(1, std::min<int64_t>(256, (m + 1023) / 1024));
       const int len = (m + sl - 1) / sl;
       dim3 grid((Nb + 127) / 128, (m + len - 1) / len);
       double* q = want_g ? qp + (size_t)ci * qslices * Nb * 3 : nullptr;
