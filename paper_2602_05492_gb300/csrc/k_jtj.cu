@@ -644,18 +644,24 @@ __global__ void __launch_bounds__(256) k_hand_sum(const float* __restrict__ hw, 
   if (s >= m) return;
   for (int c = 0; c < 3; ++c) {
     const float* p = hw + (size_t)c * C * ldh + s;
-    // eight independent partial sums keep eight loads in flight
-    double t[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    // eight independent float partial sums keep eight loads in flight (a
+    // partial adds C / 8 shares, a few float roundings of a colour), and
+    // only the eight partials are added in double: double adds run at a
+    // small fraction of the float rate here
+    float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int i = 0;
     for (; i + 8 <= C; i += 8) {
       float v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = p[(size_t)(i + u) * ldh];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) t[u] += double(v[u]);
+      for (int u = 0; u < 8; ++u) t[u] += v[u];
     }
-    for (; i < C; ++i) t[0] += double(p[(size_t)i * ldh]);
-    hand[3 * (size_t)s + c] += ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+    for (; i < C; ++i) t[0] += p[(size_t)i * ldh];
+    double d = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) d += double(t[u]);
+    hand[3 * (size_t)s + c] += d;
   }
 }
 
