@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
   const bool same_ab = g.mode == EPI_SYRK && ti == tj;
   if (warp == 0 && lane == 0) {
     // TMA producer
-    for (int it = 0; it < nk; ++it) {
+    int issued = 0;
+    for (int it = 0; it < nk; ++it, issued = it) {
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
       if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err)) break;
@@ -150,6 +151,9 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
         if (!same_ab) umma::tma_load_2d(st + 3 * TILE_BYTES, &tB2, &full[s], kc, brow);
       }
     }
+    // the loads still in flight (after a timeout) land before the CTA can leave
+    for (int j = issued > STAGES ? issued - STAGES : 0; j < issued; ++j)
+      umma::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, g.err);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     const uint32_t id = umma::idesc(X3 ? 2 : 1, BM, BN);
@@ -649,7 +653,8 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem = *tmem_slot;
   if (warp == 0 && lane == 0) {
     // TMA producer
-    for (int it = 0; it < nk; ++it) {
+    int issued = 0;
+    for (int it = 0; it < nk; ++it, issued = it) {
       const int s = it % SY_STAGES;
       const uint32_t ph = (it / SY_STAGES) & 1;
       if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err)) break;
@@ -666,6 +671,9 @@ __global__ void __launch_bounds__(128, 1)
           umma::tma_load_2d(st + 2 * TILE_BYTES, &tJ, &full[s], kc, rbase + (un.b + 1) * BM);
       }
     }
+    // the loads still in flight (after a timeout) land before the CTA can leave
+    for (int j = issued > SY_STAGES ? issued - SY_STAGES : 0; j < issued; ++j)
+      umma::mbar_wait(&full[j % SY_STAGES], (j / SY_STAGES) & 1, g.err);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     const uint32_t id128 = umma::idesc(1, BM, BN), id256 = umma::idesc(1, BM, 2 * BN);
