@@ -9,9 +9,9 @@ The flat parameter vector is therefore theta[curve][handle][8], n_theta =
 
 The paper fits line-segment handles to Monte Carlo colour samples (Sec. 4);
 Bezier curves with interpolated jumps are its suggested extension (Sec. 6,
-"Post-processing").  The workloads below follow the five benchmark
-configurations of this project (sizes, noise models, perturbations); the
-readings taken where they are loose are listed in the design doc.
+"Post-processing").  The workloads below follow five benchmark
+configurations (sizes, noise models, perturbations); where those leave a
+detail open, the choice is stated with the function that makes it.
 
 Random streams are independent children of one SeedSequence per config, in a
 fixed order (geometry, colours, mean colour, initial perturbation, sample
