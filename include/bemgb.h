@@ -302,6 +302,18 @@ int bem_gemm_bf16(bem_ctx *ctx, int M, int N, int K, const void *A, int lda, con
 int bem_fastmath_eval(bem_ctx *ctx, int which, int64_t n, const float *a, const float *b,
                       float *out_fast, float *out_ref, void *stream);
 
+/* The pairing of the bf16 Gram kernel, exposed for validation (host only, no
+ * context, no GPU).  The upper 128 x 128 blocks (i <= j) of each channel's
+ * n_c x n_c Gram matrix, tiles = ceil(n_c / 128) block rows, are computed in
+ * units of two blocks that share an operand slab.  out[0..3] = {kind, a0,
+ * a1, b} of unit `unit`:
+ *   kind 1: blocks (a0, b) and (a0, b + 1), one N = 256 product;
+ *   kind 2: blocks (a0, b) and (a1, b), two products on one B slab;
+ *   kind 0: block (a0, b) alone.
+ * Every upper block belongs to exactly one unit.  Errors: BEM_EINVAL for
+ * tiles < 1, unit outside [0, number of units) or out == NULL. */
+int bem_gram_unit(int tiles, int unit, int32_t *out);
+
 /* bem_vjp without any device allocation (the paper has no counterpart; this
  * is for callers, not for the method).  Some callers may not allocate GPU
  * memory while they run the hot path: real-time loops that must never enter

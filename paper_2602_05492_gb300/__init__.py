@@ -102,6 +102,7 @@ def _load():
         "bem_prune": (ci, [vp, ctypes.c_double, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_int32),
                            vp]),
         "bem_init_segments": (ci, [ci, ctypes.c_double, i64, ci, dp, dp, ctypes.POINTER(ci)]),
+        "bem_gram_unit": (ci, [ci, ci, ctypes.POINTER(ctypes.c_int32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -119,7 +120,7 @@ EXPORTED = [
     "bem_fastmath_eval", "bem_vjp_noalloc", "bem_batch_create", "bem_batch_destroy",
     "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors", "lm_step_split",
     "bem_set_boundary", "bem_setup_segments", "bem_set_regularizers", "bem_prune",
-    "bem_init_segments",
+    "bem_init_segments", "bem_gram_unit",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -474,3 +475,17 @@ def init_segments(n_points, length, first_index=1, polygon=None) -> np.ndarray:
     if rc != BEM_OK:
         raise BemError(rc, "bem_init_segments: bad arguments")
     return out[:10 * n.value].copy()
+
+
+def gram_units(tiles: int) -> list:
+    """The bf16 Gram kernel's units over `tiles` block rows, as (kind, a0,
+    a1, b) tuples in launch order (bem_gram_unit; host only)."""
+    units = []
+    out = (ctypes.c_int32 * 4)()
+    while True:
+        rc = _lib.bem_gram_unit(int(tiles), len(units), out)
+        if rc == BEM_EINVAL:
+            return units
+        if rc != BEM_OK:
+            raise BemError(rc, "bem_gram_unit failed")
+        units.append(tuple(int(v) for v in out))

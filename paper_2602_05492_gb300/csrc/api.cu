@@ -790,6 +790,15 @@ int bem_fastmath_eval(bem_ctx* c, int which, int64_t n, const float* a, const fl
   return cuda_check(c, cudaGetLastError(), "k_fastmath");
 }
 
+int bem_gram_unit(int tiles, int unit, int32_t* out) {
+  if (!out) return BEM_EINVAL;
+  int v[4];
+  const int rc = tc_gram_unit(tiles, unit, v);
+  if (rc) return rc;
+  for (int k = 0; k < 4; ++k) out[k] = v[k];
+  return BEM_OK;
+}
+
 int bem_sizes(const bem_ctx* c, int* n_theta, int* n_panels, int* n_boundary) {
   if (!c) return BEM_EINVAL;
   if (n_theta) *n_theta = c->sc.nth;

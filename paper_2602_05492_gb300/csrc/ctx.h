@@ -211,6 +211,9 @@ int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt
 int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, float* part,
             int splits);
 int tc_syrk_splits(int nc, bool x3);
+// {kind, a0, a1, b} of the bf16 Gram kernel's unit u over T block rows;
+// BEM_EINVAL when T < 1 or u is not a unit of T
+int tc_gram_unit(int T, int u, int* out);
 
 // Brackets the kernel launches of its lifetime with events when profiling.
 struct ProfScope {

@@ -585,8 +585,9 @@ struct SyrkUnit {
   int kind, a0, a1, b;
 };
 
-// unit u of the T x T upper block triangle, in the order above
-__device__ __forceinline__ SyrkUnit syrk_unit(int T, int u) {
+// unit u of the T x T upper block triangle, in the order above (also
+// compiled for the host, where bem_gram_unit exposes it to the tests)
+__host__ __device__ __forceinline__ SyrkUnit syrk_unit(int T, int u) {
   int np = 0;
   for (int r = 0; r < T; ++r) np += (T - r) / 2;
   SyrkUnit un;
@@ -884,6 +885,17 @@ int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, f
 // K slices per block pair: as many as fill the resident CTA slots in one
 // wave without starting a second, nearly empty one (rounding up would leave
 // a short tail wave that costs as long as the first)
+// out = {kind, a0, a1, b} of Gram unit u of a T x T block triangle
+int tc_gram_unit(int T, int u, int* out) {
+  if (T < 1 || u < 0 || u >= syrk_units(T)) return BEM_EINVAL;
+  const SyrkUnit un = syrk_unit(T, u);
+  out[0] = un.kind;
+  out[1] = un.a0;
+  out[2] = un.a1;
+  out[3] = un.b;
+  return BEM_OK;
+}
+
 int tc_syrk_splits(int nc, bool x3) {
   int tiles = (nc + BM - 1) / BM;
   // bf16: one CTA per SM on paired blocks; 3xtf32: one CTA per SM per block
