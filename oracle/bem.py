@@ -466,6 +466,12 @@ class Oracle:
         (H + lam D) delta + Ac mu = -g,  Ac^T delta = 0,  D = diag(H) floored
         at 1e-12 max diag(H); Cholesky of H + lam D and a 3x3 Schur complement.
         `free` (optional bool mask) freezes the parameters it leaves out.
+
+        H is positive semi-definite only up to rounding.  When H + lam D does
+        not factor, lam is raised tenfold (a zero lam becomes 1e-9) and the
+        factorisation tried again, 13 attempts in all; the lam that factored
+        (or the last one tried, when every attempt failed and LinAlgError is
+        raised) is left in self.last_lambda.
         """
         act = self.geo.active()
         if free is not None:
@@ -474,8 +480,8 @@ class Oracle:
         ga = g[act]
         dg = np.diag(Ha).copy()
         D = np.maximum(dg, 1e-12 * dg.max())
-        # H is PSD only up to rounding: raise lambda tenfold until H + lam D factors
         for attempt in range(13):
+            self.last_lambda = lam
             try:
                 cf = scipy.linalg.cho_factor(Ha + lam * np.diag(D), lower=True)
                 break
@@ -483,7 +489,6 @@ class Oracle:
                 if attempt == 12:
                     raise
                 lam = 10.0 * lam if lam > 0 else 1e-9
-        self.last_lambda = lam
         Ac = self.constraint_matrix(theta)[act]
         y = scipy.linalg.cho_solve(cf, -ga)
         Z = scipy.linalg.cho_solve(cf, Ac)
@@ -509,7 +514,20 @@ class Oracle:
         and the losses the M_J points xy (Sec. 4.3, Monte Carlo integration).
         With reg (segment handles, a regularize.RegParams), the Sec. 4.4
         losses add their analytic gradient and Hessian to g and H and their
-        values to both losses; the snapping pairs are chosen once, at theta."""
+        values to both losses; the snapping pairs are chosen once, at theta.
+
+        lam is one damping value or a sequence of trial values.  Every trial
+        solves the damped system (raising its lam tenfold while H + lam D
+        does not factor, see solve_step) and evaluates the loss at its
+        re-projected theta on the same samples.  The trial with the lowest
+        loss (the first of equal ones) is taken if its loss is below the
+        current one.  The damping schedule after Transtrum & Sethna, whose
+        constants the paper does not give: the taken trial's lam / 3 after
+        an accepted step; after a rejected one 2 lam with a single trial and
+        10 times the largest lam tried with several.  A trial whose matrix
+        never factors is skipped (its last lam still counts in that maximum);
+        LinAlgError if no trial factors."""
+        lams = [float(v) for v in np.atleast_1d(np.asarray(lam, np.float64))]
         L0, g, H = self.gauss_newton(theta, xy, target)
         if xy_h is not None:
             H = self.hessian(theta, xy_h)
@@ -520,14 +538,34 @@ class Oracle:
             gr, Hr = regularize.reg_grad_hess(theta, reg, pairs)
             g, H = g + gr, H + Hr
             L0 += regularize.reg_loss(theta, reg, pairs)
-        delta = self.solve_step(theta, H, g, lam)
-        lam = self.last_lambda
-        th_new = project_compat(self.geo, theta + delta)
-        L1 = self.loss(th_new, xy, target)
-        if reg is not None:
-            L1 += regularize.reg_loss(th_new, reg, pairs)
-        accept = L1 < L0
-        return dict(loss_before=L0, loss_after=L1, accepted=bool(accept),
-                    lambda_next=lam / 3.0 if accept else lam * 2.0,
-                    theta=th_new if accept else theta.copy(), theta_trial=th_new,
-                    delta=delta, g=g, H=H)
+        used, losses, trials, deltas = [], [], [], []
+        for lt in lams:
+            try:
+                delta = self.solve_step(theta, H, g, lt)
+            except np.linalg.LinAlgError:
+                used.append(self.last_lambda)
+                losses.append(math.inf)
+                trials.append(None)
+                deltas.append(None)
+                continue
+            used.append(self.last_lambda)
+            th_new = project_compat(self.geo, theta + delta)
+            L1 = self.loss(th_new, xy, target)
+            if reg is not None:
+                L1 += regularize.reg_loss(th_new, reg, pairs)
+            losses.append(L1)
+            trials.append(th_new)
+            deltas.append(delta)
+        if all(t is None for t in trials):
+            raise np.linalg.LinAlgError("no trial's damped matrix factors")
+        best = int(np.argmin(losses))          # first of equal minima
+        accept = losses[best] < L0
+        if accept:
+            lam_next = used[best] / 3.0
+        else:
+            lam_next = 2.0 * used[0] if len(lams) == 1 else 10.0 * max(used)
+        return dict(loss_before=L0, loss_after=losses[best], accepted=bool(accept),
+                    best_trial=best if accept else -1, lambda_next=lam_next,
+                    lambdas_used=used, trial_losses=losses,
+                    theta=trials[best] if accept else theta.copy(), theta_trial=trials[best],
+                    delta=deltas[best], g=g, H=H)
