@@ -2,10 +2,12 @@
 """Throughput of the differential-BEM Levenberg-Marquardt hot path on GB300.
 
 One step = one LM iteration of the mixed-precision path (panelize, boundary
-right-hand side and solve, evaluation + residual + loss at every sample,
-adjoint gradient, Gauss-Newton matrix, damped KKT solve, trial evaluation)
-on the 32-curve / 2,048-panel / 1,048,576-sample workload.  Prints one JSON
-line.  `--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+right-hand side and solve, residual + loss at every sample, gradient,
+Gauss-Newton matrix, damped KKT solve, trial evaluation) on the workload the
+throughput target is stated on: 128 cubic Bezier curves x 64 panels (8,192
+panels), 1024 x 1024 px x 64 spp (67,108,864 samples), FP64 near field within
+2 panel lengths.  Prints one JSON line.  `--impl reference` times the FP64
+CPU oracle on the same workload instead (rank 0 only).
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
 torch.distributed.run, one independent replica per GPU (weak scaling).
@@ -16,9 +18,11 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -32,7 +36,7 @@ import gen  # noqa: E402
 METRIC = ("LM iters/s & sample×panel evals/s (fwd+adjoint), mixed vs FP64 GPU at "
           "≤1e-4 RMSE")
 UNIT = "LM iter/s"
-CFG = 2            # the configuration the metric is quoted on
+CFG = 4            # 1024^2 px x 64 spp, 8,192 panels: the configuration of the throughput target
 L2_FLUSH_BYTES = 256 << 20
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -40,6 +44,11 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # regularisers of the 500-handle segment workload: length above twice the
 # initial 1/20 of the width, snapping within 1% of the width, no sparsity
 SEG_REG = dict(len_weight=1.0, len_max=0.1, snap_weight=1.0, snap_radius=0.01, snap_alpha=0.5)
+
+
+def near_factor(cfg):
+    # config 4 states its FP64 near field: sample-panel distance < 2 panel lengths
+    return 2.0 if cfg == 4 else 0.5
 
 
 def workload_desc(sc, cfg=CFG):
@@ -50,6 +59,14 @@ def workload_desc(sc, cfg=CFG):
             f"1024 boundary segments, {noise}")
 
 
+def bench_config(sc, cfg, jtj="bf16"):
+    """The `config` object of both arms' JSON lines (identical for the same workload)."""
+    return {"workload": workload_desc(sc, cfg), "near_factor": near_factor(cfg),
+            "precision": "mixed (f32 pairs, f64 near field and refined solves)", "jtj": jtj,
+            "lm_trials_per_step": 1,
+            "l2": "flushed between timed steps (256 MiB write); inputs larger than L2"}
+
+
 def make_inputs(rank: int, cfg: int = CFG):
     sc = gen.make_scene(cfg)
     seed = sc.seed + 7919 * rank        # independent sample set per replica
@@ -57,6 +74,23 @@ def make_inputs(rank: int, cfg: int = CFG):
     truth = gen.analytic_truth(xy, sc.seed)
     target = gen.add_noise(truth, sc.noise, seed).astype(np.float32)
     return sc, xy, target
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
 
 # ---------------------------------------------------------------------------
@@ -116,39 +150,48 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per unit, counted from the source formulas (FP32 flops:
-# add/mul = 1, FMA = 2, one special-function op = 1; compares, selects and
-# min/max are not counted)
+# algorithmic work per unit, counted from the source formulas.  FP32 flops:
+# add/mul = 1, FMA = 2 (compares, selects, min/max not counted).  Each
+# transcendental of the method (log, atan2, sqrt or rsqrt, rcp) is one
+# special-function op, whatever its implementation costs (atan2 has no
+# hardware instruction and runs as a polynomial).
 
-# handle pair of the evaluation: rounded frame 9, h^2 1, h', q1, q2, t1 t2 8, atan2(h'L, h'^2 + t1 t2) 22 (octant reduction, one
-# reciprocal, degree-7 minimax polynomial), S from t2 log q2 - t1 log q1 9 (two
-# logarithms, one product, three multiply-adds), Dl 2, 3-channel accumulation 12
-FLOP_FWD_HANDLE = 9 + 1 + 8 + 22 + 9 + 2 + 12
-# boundary pair: vertex offset 2, cross 3, dot 3, atan2 20, 3-channel accumulation 6
-FLOP_FWD_BOUND = 2 + 3 + 3 + 20 + 6
-# F-row pair: frame 10, values and frame partials of both layers 57 (both
-# logarithms taken directly), chain rule to both endpoints for Dl and S 43,
-# jump columns 16, 3 channels x 2 coordinates x (combine 7 + four Bernstein
-# accumulations 8) 90
-FLOP_FROWS_PAIR = 10 + 57 + 43 + 16 + 90
-# FP32 lanes x 2 flops per FMA x SMs x max SM clock (GB300: 128, 152, 2070 MHz)
-FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12
+# handle pair of the evaluation: rounded frame 9, h^2 1, h'^2, h', t1 t2, q1, q2 7,
+# atan2 arguments 2, t2 log q2 - t1 log q1 3, Sh 4, Dh 2, 3-channel
+# accumulation 12; special ops as the method states them: 2 logs, atan2, the
+# square root h' and the reciprocal in h/h' (the kernels form h' and 1/h'
+# from one reciprocal square root)
+FWD_HANDLE = (9 + 1 + 7 + 2 + 3 + 4 + 2 + 12, 5)        # (flops, special ops)
+# boundary pair: vertex offset 2, cross 3, dot 3, 3-channel accumulation 6 (+ atan2)
+FWD_BOUND = (2 + 3 + 3 + 6, 1)
+# F-row pair: frame 9, h^2 1, values and frame partials of both layers 31 (+
+# sqrt and reciprocal of h', atan2, 2 logs, 2 rcp), chain rule to both
+# endpoints for Dl and S 42, jump columns 16, 3 channels x 2 coordinates x
+# (combine 7 + four Bernstein accumulations 8) 90
+FROWS_PAIR = (9 + 1 + 31 + 42 + 16 + 90, 7)
 
 
 def step_work(name, n, P, Nb, nc):
-    """(flops of one LM step's launches of `name`, bound) for the modelled
-    kernels; for k_field the flops of one launch (every launch evaluates all
-    samples, and the step has one or two of them)."""
+    """((flops, special ops) of one LM step's launches of `name`, bound) for
+    the modelled kernels; for k_field the work of one launch (every launch
+    evaluates all samples)."""
     if name == "k_field":            # one evaluation of every sample (per launch)
-        return n * (P * FLOP_FWD_HANDLE + Nb * FLOP_FWD_BOUND), "alu_per_launch"
+        return (n * (P * FWD_HANDLE[0] + Nb * FWD_BOUND[0]),
+                n * (P * FWD_HANDLE[1] + Nb * FWD_BOUND[1])), "alu_per_launch"
     if name == "k_field_bnd":        # boundary term of every sample, in chunks
-        return float(n) * Nb * FLOP_FWD_BOUND, "alu"
+        return (float(n) * Nb * FWD_BOUND[0], float(n) * Nb * FWD_BOUND[1]), "alu"
     if name == "k_frows":            # all samples, plus the 3 Nb boundary Gauss points
-        return float(n + 3 * Nb) * P * FLOP_FROWS_PAIR, "alu"
-    if name == "tc_jrows":           # J^T = M_c^T Phi^T (+ F^T) for 3 channels
-        return 2.0 * 3 * nc * Nb * n, "tensor"
-    if name == "tc_syrk":            # 3 symmetric rank-n updates of order nc
-        return 3.0 * nc * (nc + 1) * n, "tensor"
+        u = float(n + 3 * Nb) * P
+        return (u * FROWS_PAIR[0], u * FROWS_PAIR[1]), "alu"
+    # J rows: the position columns of each channel and the jump columns once
+    # (they are the same in every channel): 3 (nc/2) + nc/2 = 2 nc rows for
+    # Bezier curves (nc = 16 C: 8 C position, 8 C jump columns per channel)
+    rows, jump = 3 * (nc // 2) + nc // 2, nc // 2
+    if name == "tc_jrows":           # J^T = M^T Phi^T (+ F^T) over those rows
+        return 2.0 * rows * Nb * n, "tensor"
+    if name == "tc_syrk":            # 3 symmetric rank-n updates of order nc, the
+        # jump-jump block (the same in every channel) once
+        return (3.0 * nc * (nc + 1) - 2.0 * jump * (jump + 1)) * n, "tensor"
     return None, None
 
 
@@ -179,89 +222,208 @@ def kernel_traffic(name, cfg=CFG):
         return None
 
 
-def rooflines(prof, steps, n, P, Nb, nc, cfg=CFG):
+def measure_pipes(m):
+    """Measured pipe peaks of this GPU (bem_pipe_peak) with the clocks seen
+    while the probes ran: FP32 FMA (TFLOP/s, 2 flops per FMA) and the MUFU
+    rate of the slowest of lg2 / rcp / rsqrt (special ops per second)."""
+    clk = ClockSampler(m.device)
+    clk.start()
+    fma = m.pipe_peak(0, 20) * 2.0
+    mufu = {nm: m.pipe_peak(k, 20) for k, nm in ((1, "lg2"), (2, "rcp"), (3, "rsqrt"))}
+    c = clk.stop()
+    return {"fp32_tflops": fma / 1e12, "mufu_gops": {k: v / 1e9 for k, v in mufu.items()},
+            "sfu_gops": min(mufu.values()) / 1e9, "clocks": c,
+            "how": "bem_pipe_peak: 4 CTAs x 256 threads per SM, 8 independent chains per "
+                   "thread, median of 20 launches of about 30 ms"}
+
+
+def rooflines(prof, steps, n, P, Nb, nc, pipes, cfg=CFG):
+    """One entry per modelled kernel.  ALU kernels: the FP32/SFU roofline of
+    two pipes that run side by side, t_roof = max(flops / FP32 peak, special
+    ops / SFU peak), peaks measured by bem_pipe_peak; `bound` names the
+    binding pipe and `frac` = t_roof / measured time.  `fp32_only` gives the
+    FP32-peak fraction with each special op counted as one flop.  Tensor
+    kernels: flops against the measured sustained bf16 rate."""
     peaks, src = read_peaks()
     out = []
+    fp32 = pipes["fp32_tflops"] * 1e12
+    sfu = pipes["sfu_gops"] * 1e9
     for name, (ms, cnt) in prof.items():
         work, bound = step_work(name, n, P, Nb, nc)
         if work is None or not cnt:
             continue
-        if bound == "alu_per_launch":
-            per_launch, bound = work, "alu"
+        t = ms / cnt / 1e3                      # seconds per launch
+        if bound in ("alu", "alu_per_launch"):
+            F, T = work if bound == "alu_per_launch" else (w * steps / cnt for w in work)
+            t_fp, t_sf = F / fp32, T / sfu
+            if t_sf > t_fp:
+                rec = {"bound": "sfu", "achieved": T / t / 1e9, "peak": pipes["sfu_gops"],
+                       "unit": "Gop/s (special functions)"}
+            else:
+                rec = {"bound": "fp32", "achieved": F / t / 1e12, "peak": pipes["fp32_tflops"],
+                       "unit": "TFLOP/s"}
+            rec.update({"kernel": name, "frac": max(t_fp, t_sf) / t,
+                        "traffic": kernel_traffic(name, cfg), "flops_per_launch": F,
+                        "special_ops_per_launch": T,
+                        "fp32_pipe_frac": t_fp / t, "sfu_pipe_frac": t_sf / t,
+                        "fp32_only": {"achieved": (F + T) / t / 1e12, "peak": pipes["fp32_tflops"],
+                                      "frac": (F + T) / t / fp32},
+                        "peak_source": "measured by bem_pipe_peak in this run"})
         else:
             per_launch = work * steps / cnt
-        ach = per_launch / (ms / cnt / 1e3) / 1e12
-        if bound == "alu":
-            peak, psrc = FP32_PEAK_TFLOPS, "FP32: 128 lanes x 2 x 152 SMs x 2070 MHz (derived)"
-        else:
+            ach = per_launch / t / 1e12
             peak = peaks["bf16_tflops_sustained"]
-            psrc = f"bf16 dense, sustained ({src})"
-        out.append({"bound": bound, "kernel": name, "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": kernel_traffic(name, cfg),
-                    "flops_per_launch": per_launch, "peak_source": psrc,
-                    "share_ms": ms})
+            rec = {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak,
+                   "unit": "TFLOP/s", "frac": ach / peak, "traffic": kernel_traffic(name, cfg),
+                   "flops_per_launch": per_launch,
+                   "peak_source": f"bf16 dense, sustained ({src}, MEASURED_PEAKS.json)"}
+        rec["share_ms"] = ms
+        out.append(rec)
     out.sort(key=lambda r: -r.pop("share_ms"))
     return out
 
 
 # ---------------------------------------------------------------------------
+# the oracle, timed as it stands on the host cores
 
-def oracle_rate(sc, xy, target, n_sub: int, steps: int, warmup: int = 0) -> dict:
-    """The oracle as it stands, timed on bounded samples of the same workload.
+def _oracle_fixed(o, th, x0, t0):
+    """The part of the oracle's LM iteration (Oracle.lm_step) that does not
+    depend on the number of samples: boundary values and boundary Jacobian
+    (the stacked right-hand sides) at theta, the damped KKT solve of order
+    n_theta, and the trial's boundary values.  Returns its seconds and the
+    state the per-sample part needs."""
+    import oracle
+    c0 = time.perf_counter()
+    ub = o.boundary_values(th)
+    Mb = o.boundary_jac(th)
+    t_bnd = time.perf_counter() - c0
+    # H and g of a small sample set stand in for the full sums (same size;
+    # their cost belongs to the per-sample part and is not counted here)
+    r = o.eval(th, x0, ub) - np.minimum(t0, 1.0)
+    J = o.jac(th, x0, Mb)
+    g = np.einsum("sct,sc->t", J, r) / x0.shape[0]
+    Jf = J.reshape(-1, o.geo.n_theta)
+    H = Jf.T @ Jf / x0.shape[0]
+    c1 = time.perf_counter()
+    delta = o.solve_step(th, H, g, 1e-3)
+    th1 = oracle.project_compat(o.geo, th + delta)
+    ub1 = o.boundary_values(th1)
+    t_solve = time.perf_counter() - c1
+    return t_bnd + t_solve, dict(th=th, ub=ub, Mb=Mb, th1=th1, ub1=ub1)
 
-    One LM step costs a + b n on n samples (a: boundary Jacobian and other
-    per-iteration work, b: per-sample evaluation and Jacobian rows).  One step
-    on n_sub/2 samples and `steps` steps on n_sub samples fit a and b; the full
-    workload's time per iteration is a + b S.
-    """
+
+def _oracle_per_sample(o, st, x, t):
+    """The oracle's per-sample work of one LM iteration on the points x:
+    colour and residual at theta, J rows (handle part + boundary part), their
+    contributions to g and H, and the colour at the trial theta (its loss).
+    Returns seconds."""
+    c0 = time.perf_counter()
+    nt = o.geo.n_theta
+    r = o.eval(st["th"], x, st["ub"]) - np.minimum(t, 1.0)
+    J = o.jac(st["th"], x, st["Mb"])
+    g = np.einsum("sct,sc->t", J, r)
+    Jf = J.reshape(-1, nt)
+    H = Jf.T @ Jf
+    u1 = o.eval(st["th1"], x, st["ub1"])
+    L1 = 0.5 * float(np.sum((u1 - np.minimum(t, 1.0)) ** 2))
+    assert np.isfinite(L1) and np.isfinite(g).all() and np.isfinite(H).all()
+    return time.perf_counter() - c0
+
+
+def oracle_rate(sc, xy, target, steps: int, warmup: int, n_step: int = 64, one_thread=True) -> dict:
+    """The oracle's LM iteration timed in its two parts on the host cores:
+    the fixed part once (after the warm-up of the per-sample part), the
+    per-sample part on `steps` seeded subsets of n_step samples after
+    `warmup` untimed ones.  One iteration on the S samples of the workload
+    costs a + b S (extrapolated).  With one_thread, the per-sample part is
+    also timed in a child process limited to one thread."""
     import oracle
     mean = np.minimum(target, 1.0).mean(0)
     o = oracle.Oracle.from_scene(sc, mean_color=mean)
     rng = np.random.default_rng(0)
-    idx = np.sort(rng.choice(xy.shape[0], n_sub, replace=False))
-    x, t = xy[idx].astype(np.float64), target[idx].astype(np.float64)
-    th, lam = sc.theta_init.copy(), 1e-3
-    for _ in range(warmup):
-        res = o.lm_step(th, x, t, lam)
-        th, lam = res["theta"], res["lambda_next"]
-    h = n_sub // 2
-    t0 = time.perf_counter()
-    o.lm_step(th, x[:h], t[:h], lam)
-    t_half = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for _ in range(max(steps, 1)):
-        res = o.lm_step(th, x, t, lam)
-        th, lam = res["theta"], res["lambda_next"]
-    t_full = (time.perf_counter() - t0) / max(steps, 1)
-    b = max((t_full - t_half) / (n_sub - h), t_full / n_sub * 0.5)
-    a = max(t_full - b * n_sub, 0.0)
-    per_iter = a + b * xy.shape[0]
-    return {"value": 1.0 / per_iter, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"FP64 oracle LM steps on {h} and {n_sub} of {xy.shape[0]} samples "
-                       f"({t_half:.2f} s, {t_full:.2f} s); per-iteration time a + b S with "
-                       f"a = {a:.2f} s, b = {b * 1e3:.3f} ms/sample"),
-            "ms_per_step": per_iter * 1e3}
+    S = xy.shape[0]
+
+    def subset():
+        idx = np.sort(rng.choice(S, n_step, replace=False))
+        return xy[idx].astype(np.float64), target[idx].astype(np.float64)
+
+    x0, t0 = subset()
+    a, st = _oracle_fixed(o, sc.theta_init, x0, t0)
+    for _ in range(max(warmup, 0)):
+        _oracle_per_sample(o, st, *subset())
+    per = [_oracle_per_sample(o, st, *subset()) / n_step for _ in range(max(steps, 1))]
+    b = statistics.mean(per)
+    per_iter = a + b * S
+    out = {"value": 1.0 / per_iter, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "cpu_model": cpu_model(),
+           "sample": (f"FP64 oracle LM iteration in two parts: the fixed part (boundary values, "
+                      f"boundary Jacobian, damped solve of order {o.geo.n_theta}, trial boundary "
+                      f"values) once, {a:.1f} s; the per-sample part (colour, J rows, g and H "
+                      f"sums, trial colour) on {max(steps, 1)} seeded subsets of {n_step} of "
+                      f"the {S} samples, b = {b * 1e3:.3f} ms/sample; one iteration a + b S "
+                      f"= {per_iter:.4g} s (extrapolated)"),
+           "fixed_s": a, "per_sample_s": b, "ms_per_step": per_iter * 1e3}
+    if one_thread:
+        out["one_thread"] = oracle_one_thread(o, st, sc, xy, target, S)
+    return out
 
 
-def cpu_baseline(sc, xy, target, n_sub: int) -> dict:
-    r = oracle_rate(sc, xy, target, n_sub, steps=1)
-    r.pop("ms_per_step")
-    return r
+def oracle_one_thread(o, st, sc, xy, target, S, n_step=16):
+    """Per-sample part of the oracle's iteration in a child process with one
+    thread (OpenMP and BLAS); the fixed part is not repeated there (at
+    millions of samples it is a negligible share of a + b S)."""
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "state.npz")
+        rng = np.random.default_rng(1)
+        idx = np.sort(rng.choice(xy.shape[0], 3 * n_step, replace=False))
+        np.savez(path, x=xy[idx].astype(np.float64), t=target[idx].astype(np.float64),
+                 mean=o.mean, **st)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+                   MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-probe", path,
+                            "--config", str(_cfg_of(sc))], env=env, capture_output=True,
+                           text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    b1 = json.loads(r.stdout.strip().splitlines()[-1])["per_sample_s"]
+    return {"cores": 1, "per_sample_s": b1, "iters_per_s": 1.0 / (b1 * S),
+            "sample": f"per-sample part on {2 * n_step} samples after {n_step} untimed, one "
+                      f"thread; iterations/s = 1 / (b S), the fixed part left out"}
+
+
+def _cfg_of(sc):
+    from gen import scenes
+    return next(k for k, v in scenes.CONFIGS.items() if v["seed"] == sc.seed)
+
+
+def oracle_probe(path, cfg):
+    """Child process of oracle_one_thread: the per-sample part with the
+    threads the environment allows."""
+    import oracle
+    z = np.load(path)
+    sc = gen.make_scene(cfg)
+    o = oracle.Oracle.from_scene(sc, mean_color=z["mean"])
+    st = {k: z[k] for k in ("th", "ub", "Mb", "th1", "ub1")}
+    x, t = z["x"], z["t"]
+    n = x.shape[0] // 3
+    _oracle_per_sample(o, st, x[:n], t[:n])
+    dt = _oracle_per_sample(o, st, x[n:], t[n:])
+    print(json.dumps({"per_sample_s": dt / (x.shape[0] - n), "threads": oracle.num_threads()}))
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    sc, xy, target = make_inputs(0)
-    r = oracle_rate(sc, xy, target, args.cpu_samples, steps=args.steps, warmup=args.warmup)
+    sc, xy, target = make_inputs(0, args.config)
+    r = oracle_rate(sc, xy, target, steps=args.steps, warmup=args.warmup, one_thread=False)
     v = r["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_desc(sc)},
+            "config": bench_config(sc, args.config, args.jtj),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+                             "cpu_model": r["cpu_model"], "sample": r["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -288,6 +450,137 @@ def run_quadrants(bg, quads, flush, stream, n):
             "ms_per_step": qms}
 
 
+def _timed(step, K, flush, stream):
+    """K steps, each after an L2 flush, bracketed by CUDA events on the
+    launching stream; per-step milliseconds."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for k in range(K):
+        flush.zero_()                              # evict L2 between steps
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def config2_extras(bg, dev, flush, stream, local, jm, rank):
+    """Secondary measurements on the 1,048,576-sample / 2,048-panel workload:
+    its full LM step, H from every fourth sample, four quadrant subdomains,
+    the paper's 500 segment handles, and a 1024 x 1024 rendering."""
+    import torch
+    sc2, xy2, tg2 = make_inputs(rank, 2)
+    n2 = xy2.shape[0]
+    x2, t2 = torch.from_numpy(xy2).to(dev), torch.from_numpy(tg2).to(dev)
+    m2 = bg.BEM(precision=bg.BEM_MIXED, device=local, jtj_mode=jm, near_factor=near_factor(2))
+    m2.setup(sc2.n_curves, sc2.panels_per_curve, sc2.closed, sc2.theta_init, np.zeros(3))
+    m2.set_mean_color(m2.sample_mean(t2))
+    m2.factor()
+    out = {"workload": workload_desc(sc2, 2)}
+    lam = [1e-3]
+
+    def step2():
+        r = m2.lm_step(x2, t2, lam)
+        lam[0] = r["lambda_next"]
+
+    for _ in range(3):
+        step2()
+    torch.cuda.synchronize()
+    ms = _timed(step2, 10, flush, stream)
+    out["lm_step"] = {"ms_per_step": sum(ms) / len(ms), "lm_iters_per_s": 1e3 * len(ms) / sum(ms)}
+
+    # M_H = M_J / 4: H from every fourth sample (lm_step_split)
+    xh = x2[::4].contiguous()
+    m2.set_params(sc2.theta_init)
+    lam_s = [1e-3]
+
+    def split_step():
+        r = m2.lm_step_split(x2, t2, xh, lam_s)
+        lam_s[0] = r["lambda_next"]
+
+    split_step()
+    torch.cuda.synchronize()
+    ms = _timed(split_step, 2, flush, stream)
+    out["lm_step_split_hessian"] = {
+        "hessian_samples": int(xh.shape[0]), "gradient_samples": n2,
+        "ms_per_step": sum(ms) / 2, "lm_iters_per_s": 2e3 / sum(ms),
+        "note": "H from every fourth sample, g by the adjoint"}
+    del xh
+
+    # four subdomains (the quadrants, Sec. 4.2), 8 curves and the samples of
+    # each quadrant, stepped together by one bem_batch_lm call
+    quads = []
+    for qi in range(4):
+        x0, y0 = 0.5 * (qi % 2), 0.5 * (qi // 2)
+        poly = [(x0, y0), (x0 + 0.5, y0), (x0 + 0.5, y0 + 0.5), (x0, y0 + 0.5)]
+        sel = ((xy2[:, 0] >= x0) & (xy2[:, 0] < x0 + 0.5) & (xy2[:, 1] >= y0) &
+               (xy2[:, 1] < y0 + 0.5))
+        th = sc2.theta_init.reshape(sc2.n_curves, 4, 8)[8 * qi:8 * qi + 8].copy()
+        th[:, :, 0:2] = np.array([x0, y0]) + 0.05 + 0.4 * th[:, :, 0:2]
+        mq = bg.BEM(precision=bg.BEM_MIXED, device=local, segs_per_side=128)
+        tq = torch.from_numpy(np.ascontiguousarray(tg2[sel])).to(dev)
+        qmean = np.minimum(tg2[sel], 1.0).mean(0)
+        mq.setup(8, sc2.panels_per_curve[:8], sc2.closed[8 * qi:8 * qi + 8], th.reshape(-1), qmean)
+        mq.set_boundary(poly, 128)
+        mq.factor()
+        quads.append((mq, torch.from_numpy(np.ascontiguousarray(xy2[sel])).to(dev), tq))
+    out["subdomains_batched"] = run_quadrants(bg, quads, flush, stream, n2)
+    for q in quads:
+        q[0].close()
+    del quads
+
+    # output rendering: the colour field on a 1024 x 1024 pixel grid
+    img = torch.empty((1024, 1024, 3), dtype=torch.float32, device=dev)
+    m2.render(1024, 1024, img)
+    e0r, e1r = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0r.record(stream)
+    for _ in range(3):
+        m2.render(1024, 1024, img)
+    e1r.record(stream)
+    torch.cuda.synchronize()
+    rms = e0r.elapsed_time(e1r) / 3
+    out["render_1024x1024"] = {"pixels": 1024 * 1024, "ms": rms, "mpix_per_s": 1024 * 1024 / rms / 1e3}
+    del img
+    m2.close()
+    del x2, t2
+
+    # the paper's own parametrisation: 500 segment handles (Sec. 4.2) on the
+    # same sample count, with the length and snapping regularisers on and
+    # sparsity off (the paper's default, Sec. 4.4)
+    ss = gen.make_segment_scene("seg500")
+    xs = gen.make_samples(ss.W, ss.spp, ss.seed, dtype=np.float32)
+    ts = gen.add_noise(gen.analytic_truth(xs, ss.seed), ss.noise, ss.seed).astype(np.float32)
+    xst, tst = torch.from_numpy(xs).to(dev), torch.from_numpy(ts).to(dev)
+    ms_ = bg.BEM(precision=bg.BEM_MIXED, device=local, jtj_mode=jm, near_factor=near_factor(2))
+    ms_.setup_segments(ss.n_handles, ss.theta_init, np.minimum(ts, 1.0).mean(0))
+    ms_.factor()
+    ms_.set_regularizers(**SEG_REG)
+    lseg = [1e-3]
+
+    def seg_step():
+        r = ms_.lm_step(xst, tst, lseg)
+        lseg[0] = r["lambda_next"]
+
+    seg_step()
+    torch.cuda.synchronize()
+    ms_.profile(True)
+    ms = _timed(seg_step, 3, flush, stream)
+    gprof = ms_.profile_read()
+    ms_.profile(False)
+    gms = sum(ms) / 3
+    out["segments_500"] = {
+        "handles": ss.n_handles, "n_theta": 10 * ss.n_handles, "samples": int(xs.shape[0]),
+        "regularisers": SEG_REG, "ms_per_step": gms, "lm_iters_per_s": 1e3 / gms,
+        "kernel_share": {k: round(v[0] / (3 * gms), 4) for k, v in sorted(gprof.items())
+                         if v[0] / (3 * gms) >= 0.005},
+        "workload": "500 random segment handles (length 0.025-0.1), 256^2 px x 16 spp, "
+                    "lognormal noise with 1% fireflies"}
+    ms_.close()
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import torch
     import paper_2602_05492_gb300 as bg
@@ -300,8 +593,7 @@ def run_ours(args, rank, world, dist):
         xy, target = xy[:args.samples].copy(), target[:args.samples].copy()
     n = xy.shape[0]
     jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32}[args.jtj]
-    # config 4 states its FP64 near field: sample-panel distance < 2 panel lengths
-    nf = 2.0 if cfg == 4 else 0.5
+    nf = near_factor(cfg)
     m = bg.BEM(precision=bg.BEM_MIXED, device=local, jtj_mode=jm, near_factor=nf)
     xt = torch.from_numpy(xy).to(dev)
     tt = torch.from_numpy(target).to(dev)
@@ -310,6 +602,8 @@ def run_ours(args, rank, world, dist):
     m.set_mean_color(mean)
     m.factor()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    pipes = measure_pipes(m)
     lam = [1e-3]
 
     def step():
@@ -320,9 +614,6 @@ def run_ours(args, rank, world, dist):
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     if dist is not None:
         dist.barrier()
@@ -331,18 +622,11 @@ def run_ours(args, rank, world, dist):
     m.profile(True)
     clocks.start()
     t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()                              # evict L2 between steps
-        starts[k].record(stream)
-        step()
-        ends[k].record(stream)
-    torch.cuda.synchronize()
+    step_ms = _timed(step, args.steps, flush, stream)
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     prof = m.profile_read()
-    m.profile(False)
     launches = m.launch_count() - launches0
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     if dist is not None:
         tt_ = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -351,20 +635,56 @@ def run_ours(args, rank, world, dist):
         dist.barrier()
     value = world * args.steps / (total_ms / 1e3)
 
+    # ---- end to end through the public API with host buffers: the same
+    # start (theta_init, lambda 1e-3), warm-up, steps, L2 flush and event
+    # profiler as the device-timed run; every step copies its inputs from
+    # pinned host memory and reads the losses back (lm_step returns them)
+    xy_h = torch.from_numpy(xy).pin_memory()
+    t_h = torch.from_numpy(target).pin_memory()
+    xe = torch.empty_like(xt)
+    te = torch.empty_like(tt)
+    m.set_params(sc.theta_init)
+    lam_e = [1e-3]
+
+    def e2e_step():
+        xe.copy_(xy_h, non_blocking=True)
+        te.copy_(t_h, non_blocking=True)
+        r = m.lm_step(xe, te, lam_e)
+        lam_e[0] = r["lambda_next"]
+
+    for _ in range(max(args.warmup, 0)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - c0
+    m.profile(False)
+    e2e = {"value": world * args.steps / e2e_s if dist is None else args.steps / e2e_s * world,
+           "unit": UNIT, "h2d_bytes_per_step": int(xy.nbytes + target.nbytes),
+           "d2h_bytes_per_step": 8 * 3, "steps": args.steps, "warmup": args.warmup,
+           "timer": "host clock around each step (copies, lm_step, its host read-back)"}
+    del xy_h, t_h, xe, te
+
     if rank != 0:
         return
     # ---- per-kernel live timing -> roofline of the dominant modelled kernel
     P, Nb, nc = sc.n_panels, 1024, 16 * sc.n_curves
-    roofs = rooflines(prof, args.steps, n, P, Nb, nc, cfg)
+    roofs = rooflines(prof, args.steps, n, P, Nb, nc, pipes, cfg)
     roof = roofs[0] if roofs else None
     kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
                    "share": v[0] / total_ms} for k, v in sorted(prof.items())}
 
     # ---- sample x panel throughput, forward and adjoint, measured separately
+    m.set_params(sc.theta_init)
     out = torch.empty((n, 3), dtype=torch.float32, device=dev)
     res = torch.empty((n, 3), dtype=torch.float32, device=dev)
     m.loss(xt, tt, res)
-    reps = 3
+    reps = 1 if n > (1 << 22) else 3
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * reps)]
     fwd_ms = adj_ms = 0.0
     for r in range(reps):
@@ -374,7 +694,7 @@ def run_ours(args, rank, world, dist):
         ev[4 * r + 1].record(stream)
         flush.zero_()
         ev[4 * r + 2].record(stream)
-        g = m.vjp(xt, res)
+        m.vjp(xt, res)
         ev[4 * r + 3].record(stream)
     torch.cuda.synchronize()
     for r in range(reps):
@@ -382,114 +702,20 @@ def run_ours(args, rank, world, dist):
         adj_ms += ev[4 * r + 2].elapsed_time(ev[4 * r + 3]) / reps
     pairs = n * (P + Nb)
     pairs_per_s = 2 * pairs / ((fwd_ms + adj_ms) / 1e3)
+    del out, res
 
-    # ---- M_H = M_J / 4: H from every fourth sample (lm_step_split)
-    xh = xt[::4].contiguous()
-    m.set_params(sc.theta_init)
-    lam_s = [1e-3]
-    r_ = m.lm_step_split(xt, tt, xh, lam_s)
-    lam_s[0] = r_["lambda_next"]
-    torch.cuda.synchronize()
-    e0s, e1s = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sms = 0.0
-    for _ in range(2):
-        flush.zero_()
-        e0s.record(stream)
-        r_ = m.lm_step_split(xt, tt, xh, lam_s)
-        e1s.record(stream)
-        torch.cuda.synchronize()
-        lam_s[0] = r_["lambda_next"]
-        sms += e0s.elapsed_time(e1s) / 2
-    split_h = {"hessian_samples": int(xh.shape[0]), "gradient_samples": n, "ms_per_step": sms,
-               "lm_iters_per_s": 1e3 / sms, "note": "H from every fourth sample, g by the adjoint"}
-    del xh
-
-    # ---- four subdomains (the quadrants, Sec. 4.2), 8 curves and the samples
-    # of each quadrant, stepped together by one bem_batch_lm call (left out
-    # with --samples, whose leading samples do not reach every quadrant)
-    quads = []
-    for qi in range(4 if not args.samples else 0):
-        x0, y0 = 0.5 * (qi % 2), 0.5 * (qi // 2)
-        poly = [(x0, y0), (x0 + 0.5, y0), (x0 + 0.5, y0 + 0.5), (x0, y0 + 0.5)]
-        sel = ((xy[:, 0] >= x0) & (xy[:, 0] < x0 + 0.5) & (xy[:, 1] >= y0) & (xy[:, 1] < y0 + 0.5))
-        th = sc.theta_init.reshape(sc.n_curves, 4, 8)[8 * qi:8 * qi + 8].copy()
-        th[:, :, 0:2] = np.array([x0, y0]) + 0.05 + 0.4 * th[:, :, 0:2]
-        mq = bg.BEM(precision=bg.BEM_MIXED, device=local, segs_per_side=128)
-        tq = torch.from_numpy(np.ascontiguousarray(target[sel])).to(dev)
-        qmean = np.minimum(target[sel], 1.0).mean(0)
-        mq.setup(8, sc.panels_per_curve[:8], sc.closed[8 * qi:8 * qi + 8], th.reshape(-1), qmean)
-        mq.set_boundary(poly, 128)
-        mq.factor()
-        quads.append((mq, torch.from_numpy(np.ascontiguousarray(xy[sel])).to(dev), tq))
-    subdomains = run_quadrants(bg, quads, flush, stream, n) if quads else None
-    for q in quads:
-        q[0].close()
-    del quads
-
-    # ---- the paper's own parametrisation: 500 segment handles (Sec. 4.2) on
-    # the same sample count, with the length and snapping regularisers on and
-    # sparsity off (the paper's default, Sec. 4.4)
-    ss = gen.make_segment_scene("seg500")
-    xs = gen.make_samples(ss.W, ss.spp, ss.seed, dtype=np.float32)
-    ts = gen.add_noise(gen.analytic_truth(xs, ss.seed), ss.noise, ss.seed).astype(np.float32)
-    xst, tst = torch.from_numpy(xs).to(dev), torch.from_numpy(ts).to(dev)
-    ms_ = bg.BEM(precision=bg.BEM_MIXED, device=local, jtj_mode=jm, near_factor=nf)
-    ms_.setup_segments(ss.n_handles, ss.theta_init, np.minimum(ts, 1.0).mean(0))
-    ms_.factor()
-    ms_.set_regularizers(**SEG_REG)
-    lseg = [1e-3]
-    r_ = ms_.lm_step(xst, tst, lseg)
-    lseg[0] = r_["lambda_next"]
-    torch.cuda.synchronize()
-    e0g, e1g = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    gms = 0.0
-    ms_.profile(True)
-    for _ in range(3):
-        flush.zero_()
-        e0g.record(stream)
-        r_ = ms_.lm_step(xst, tst, lseg)
-        e1g.record(stream)
-        torch.cuda.synchronize()
-        lseg[0] = r_["lambda_next"]
-        gms += e0g.elapsed_time(e1g) / 3
-    gprof = ms_.profile_read()
-    ms_.profile(False)
-    segments = {"handles": ss.n_handles, "n_theta": 10 * ss.n_handles,
-                "samples": int(xs.shape[0]), "regularisers": SEG_REG, "ms_per_step": gms,
-                "lm_iters_per_s": 1e3 / gms,
-                "kernel_share": {k: round(v[0] / (3 * gms), 4) for k, v in sorted(gprof.items())
-                                 if v[0] / (3 * gms) >= 0.005},
-                "workload": "500 random segment handles (length 0.025-0.1), 256^2 px x 16 spp, "
-                            "lognormal noise with 1% fireflies"}
-    ms_.close()
-    del xst, tst
-
-    # ---- output rendering: the colour field on a 1024 x 1024 pixel grid
-    img = torch.empty((1024, 1024, 3), dtype=torch.float32, device=dev)
-    m.render(1024, 1024, img)
-    e0r, e1r = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0r.record(stream)
-    for _ in range(3):
-        m.render(1024, 1024, img)
-    e1r.record(stream)
-    torch.cuda.synchronize()
-    rms = e0r.elapsed_time(e1r) / 3
-    render = {"pixels": 1024 * 1024, "ms": rms, "mpix_per_s": 1024 * 1024 / rms / 1e3}
-    del img
-
-    # ---- FP64 GPU path: one LM iteration (after one warm-up iteration); at
-    # config 4 its cost a + b S is fitted from steps on two sample subsets
+    # ---- FP64 GPU path: LM iterations on two leading sample sets (fitted
+    # a + b S when they are smaller than the workload), colour and gradient
+    # error of the mixed path against it
     fp64 = None
     accuracy = None
     if args.fp64_steps > 0:
-        n64 = n if (cfg != 4 or args.fp64_samples <= 0) else min(n, args.fp64_samples)
+        n64 = n if args.fp64_samples <= 0 else min(n, args.fp64_samples)
         m64 = bg.BEM(precision=bg.BEM_FP64, device=local)
         x64, t64 = xt[:n64].double(), tt[:n64].double()
         m64.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, mean)
         m64.factor()
         u64 = m64.eval(x64)
-        m.set_params(sc.theta_init)
         u32 = m.eval(xt[:n64]).double()
         rmse = float(torch.sqrt(torch.mean((u32 - u64) ** 2)).item())
         r64 = torch.empty((n64, 3), dtype=torch.float64, device=dev)
@@ -500,7 +726,7 @@ def run_ours(args, rank, world, dist):
         g32 = m.vjp(xt[:n64], r32)
         gerr = float((torch.linalg.norm(g32 - g64) / torch.linalg.norm(g64)).item())
         del u64, u32, r64, r32
-        m64.lm_step(x64, t64, [1e-3])
+        m64.lm_step(x64[:n64 // 2], t64[:n64 // 2], [1e-3])
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -520,59 +746,43 @@ def run_ours(args, rank, world, dist):
             t64_ms = t64_step(n64)
             timed = f"{args.fp64_steps} full FP64 LM iteration(s) after one warm-up"
         else:
-            th, tf = t64_step(n64 // 2), t64_step(n64)
-            b = (tf - th) / (n64 - n64 // 2)
+            th_, tf = t64_step(n64 // 2), t64_step(n64)
+            b = (tf - th_) / (n64 - n64 // 2)
             t64_ms = tf + b * (n - n64)
             timed = (f"FP64 LM iterations on {n64 // 2} and {n64} of {n} samples "
-                     f"({th:.0f} ms, {tf:.0f} ms), extrapolated linearly in samples")
+                     f"({th_:.0f} ms, {tf:.0f} ms), extrapolated linearly in samples")
         fp64 = {"lm_iters_per_s": 1e3 / t64_ms, "ms_per_iter": t64_ms,
                 "mixed_over_fp64": (value / world) / (1e3 / t64_ms), "timed": timed}
         accuracy = {"colour_rmse_mixed_vs_fp64_gpu": rmse, "grad_rel_err_mixed_vs_fp64_gpu": gerr,
                     "at": f"theta_init, {'all' if n64 == n else n64} samples"}
         m64.close()
+        del x64, t64
+    m.close()
+    del xt, tt
 
-    # ---- end to end through the public API with host buffers
-    xy_h = torch.from_numpy(xy).pin_memory()
-    t_h = torch.from_numpy(target).pin_memory()
-    xe = torch.empty_like(xt)
-    te = torch.empty_like(tt)
-    m.set_params(sc.theta_init)
-    lam_e = [1e-3]
-    torch.cuda.synchronize()
-    e_steps = max(1, min(args.steps, 3))
-    t0 = time.perf_counter()
-    for _ in range(e_steps):
-        xe.copy_(xy_h, non_blocking=True)
-        te.copy_(t_h, non_blocking=True)
-        r = m.lm_step(xe, te, lam_e)          # returns losses to the host
-        lam_e[0] = r["lambda_next"]
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e_steps
-    e2e = {"value": 1.0 / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(xy.nbytes + target.nbytes),
-           "d2h_bytes_per_step": 8 * 3}
+    extras = None
+    if cfg == 4 and not args.samples and not args.no_extras:
+        extras = config2_extras(bg, dev, flush, stream, local, jm, rank)
 
     cpu = None
-    if world == 1 and not args.no_cpu_baseline and cfg == CFG:
-        cpu = cpu_baseline(sc, xy, target, n_sub=args.cpu_samples)
-        cpu.pop("seconds_per_sample_step", None)
+    if world == 1 and not args.no_cpu_baseline:
+        r = oracle_rate(sc, xy, target, steps=args.cpu_steps, warmup=1)
+        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "cpu_model", "sample",
+                                 "one_thread")}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": workload_desc(sc, cfg), "near_factor": nf,
-                       "precision": "mixed (f32 pairs, f64 near field and refined solves)", "jtj": args.jtj, "lm_trials_per_step": 1,
-                       "l2": "flushed between timed steps (256 MiB write)",
-                       "wall_s_timed_region": t_wall},
+            "config": bench_config(sc, cfg, args.jtj),
+            "wall_s_timed_region": t_wall,
             "pairs_per_s": {"value": pairs_per_s, "unit": "sample x panel evals/s (fwd+adjoint)",
                             "fwd_ms": fwd_ms, "adj_ms": adj_ms, "pairs_per_pass": pairs},
-            "fp64_gpu": fp64, "accuracy": accuracy, "render_1024x1024": render,
-            "lm_step_split_hessian": split_h, "subdomains_batched": subdomains,
-            "segments_500": segments,
+            "fp64_gpu": fp64, "accuracy": accuracy, "config2": extras,
+            "pipe_peaks": pipes,
             "kernels": kernels,
-            "roofline": roof, "rooflines_other": roofs[1:], "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": int(launches)}
+            "roofline": roof, "rooflines_other": roofs[1:], "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk, "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
 
 
@@ -609,6 +819,19 @@ def run_batch(args, rank, world):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    def kernel_totals(ms, steps, total_ms):
+        tot = {}
+        for m in ms:
+            for k, (t, c) in m.profile_read().items():
+                a = tot.setdefault(k, [0.0, 0])
+                a[0] += t
+                a[1] += c
+            m.profile(False)
+        out = {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps}
+               for k, v in sorted(tot.items(), key=lambda kv: -kv[1][0])}
+        out["_outside_kernels_ms_per_step"] = (total_ms - sum(v[0] for v in tot.values())) / steps
+        return out
+
     # batched
     mb = contexts()
     b = bg.BEMBatch(mb)
@@ -618,6 +841,8 @@ def run_batch(args, rank, world):
     clocks = ClockSampler(0)
     clocks.start()
     tb = 0.0
+    for m in mb:
+        m.profile(True)
     for _ in range(args.steps):
         flush.zero_()
         e0.record(stream)
@@ -626,6 +851,7 @@ def run_batch(args, rank, world):
         torch.cuda.synchronize()
         tb += e0.elapsed_time(e1)
     clk = clocks.stop()
+    kb = kernel_totals(mb, args.steps, tb)
     shape = b.tile_shape()
     b.close()
     for m in mb:
@@ -637,6 +863,8 @@ def run_batch(args, rank, world):
             m.lm_step(x, t, lams)
     torch.cuda.synchronize()
     tsq = 0.0
+    for m in ms:
+        m.profile(True)
     for _ in range(args.steps):
         flush.zero_()
         e0.record(stream)
@@ -645,6 +873,7 @@ def run_batch(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         tsq += e0.elapsed_time(e1)
+    ks = kernel_totals(ms, args.steps, tsq)
     for m in ms:
         m.close()
     S = len(scenes)
@@ -663,7 +892,8 @@ def run_batch(args, rank, world):
                        "tile_shape": {"points_per_tile": shape[0], "ctas_per_sm": shape[1]}},
             "one_at_a_time": {"value": seq, "unit": "scene LM iter/s",
                               "ms_per_step": tsq / args.steps},
-            "batched_over_one_at_a_time": value / seq, "clocks": clk}
+            "batched_over_one_at_a_time": value / seq, "clocks": clk,
+            "kernels_batched": kb, "kernels_one_at_a_time": ks}
     print(json.dumps(line), flush=True)
 
 
@@ -674,12 +904,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--cpu-samples", type=int, default=4096)
+    ap.add_argument("--cpu-steps", type=int, default=8,
+                    help="seeded 64-sample subsets of the oracle's per-sample part")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the secondary measurements on the 1M-sample workload")
+    ap.add_argument("--oracle-probe", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--jtj", default="bf16", choices=["bf16", "3xtf32"],
                     help="tensor-core scheme of the J^T J contraction")
     ap.add_argument("--config", type=int, default=CFG, choices=[2, 4, 5],
-                    help="2: the metric's configuration (default); 4: 67M samples, 8,192 "
+                    help="4: 67M samples, 8,192 panels (default); 2: 1M samples, 2,048 "
                          "panels; 5: batched uneven scenes against one at a time")
     ap.add_argument("--scenes", type=int, default=64, help="config 5: number of scenes")
     ap.add_argument("--fp64-samples", type=int, default=1 << 20,
@@ -687,6 +921,9 @@ def main():
     ap.add_argument("--samples", type=int, default=0,
                     help="profiling aid: time only the first N samples of the workload")
     args = ap.parse_args()
+    if args.oracle_probe:
+        oracle_probe(args.oracle_probe, args.config)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

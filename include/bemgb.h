@@ -78,7 +78,13 @@ typedef struct {
                              Gauss (the paper's rule).  Mode 1 leaves the constants only
                              nearly in the null space; its pseudo-inverse drops the
                              smallest singular value exactly, as in mode 0 */
-    int reserved[6];
+    int gn_chunk;         /* samples per chunk of the Gauss-Newton pass (Eq. (losshessian),
+                             (lossjacobian)): J rows exist for one chunk at a time and the
+                             chunks' sums are added in double.  0 (default): 262,144 in the
+                             tensor-core J^T J modes, 32,768 otherwise; else a multiple of
+                             128 in [128, 4,194,304].  The result does not depend on it
+                             beyond the order of the chunk sums */
+    int reserved[5];
 } bem_opts;
 
 typedef struct {
@@ -303,16 +309,20 @@ int bem_fastmath_eval(bem_ctx *ctx, int which, int64_t n, const float *a, const 
                       float *out_fast, float *out_ref, void *stream);
 
 /* The pairing of the bf16 Gram kernel, exposed for validation (host only, no
- * context, no GPU).  The upper 128 x 128 blocks (i <= j) of each channel's
- * n_c x n_c Gram matrix, tiles = ceil(n_c / 128) block rows, are computed in
- * units of two blocks that share an operand slab.  out[0..3] = {kind, a0,
- * a1, b} of unit `unit`:
+ * context, no GPU).  The upper 128 x 128 blocks (i <= j) of a channel's Gram
+ * matrix in its J-row order, tiles block rows, are computed in units of two
+ * blocks that share an operand slab; channel 0 takes the block rows
+ * 0 .. tiles-1, channels 1 and 2 only the rows of their position range (the
+ * blocks of the jump columns with each other are the same for all channels).
+ * out[0..3] = {kind, a0, a1, b} of unit `unit` over the block rows
+ * 0 .. rows-1:
  *   kind 1: blocks (a0, b) and (a0, b + 1), one N = 256 product;
  *   kind 2: blocks (a0, b) and (a1, b), two products on one B slab;
  *   kind 0: block (a0, b) alone.
- * Every upper block belongs to exactly one unit.  Errors: BEM_EINVAL for
- * tiles < 1, unit outside [0, number of units) or out == NULL. */
-int bem_gram_unit(int tiles, int unit, int32_t *out);
+ * Every upper block of those rows belongs to exactly one unit.  Errors:
+ * BEM_EINVAL for tiles < 1, rows outside [1, tiles], unit outside
+ * [0, number of units) or out == NULL. */
+int bem_gram_unit(int tiles, int rows, int unit, int32_t *out);
 
 /* bem_vjp without any device allocation (the paper has no counterpart; this
  * is for callers, not for the method).  Some callers may not allocate GPU
@@ -381,6 +391,46 @@ int bem_boundary_values(bem_ctx *ctx, double *ub_out, void *stream);
 
 /* Number of this library's kernels launched by the context so far. */
 int64_t bem_launch_count(const bem_ctx *ctx);
+
+/* Throughput of one SM pipe the float pair kernels issue to, measured on
+ * the context's device: the denominators of those kernels' roofline (no
+ * counterpart in the paper).  which = 0: FP32 fused multiply-add; 1: MUFU
+ * base-2 logarithm; 2: MUFU reciprocal; 3: MUFU reciprocal square root.  One
+ * warm-up launch, then `launches` (1..1000) timed launches of about 30 ms
+ * each, every thread with eight independent chains of the operation;
+ * *ops_per_s receives the median launch's operations per second (one fused
+ * multiply-add counts as one operation).  Synchronises `stream`.  Errors:
+ * BEM_EINVAL. */
+int bem_pipe_peak(bem_ctx *ctx, int which, int launches, double *ops_per_s, void *stream);
+
+/* Number of device allocations (cudaMalloc calls) the context has made so
+ * far: its buffers grow on demand and never shrink, so a call that needs no
+ * new buffer leaves the count as it is (no counterpart in the paper). */
+int64_t bem_alloc_count(const bem_ctx *ctx);
+
+/* Limit of the bounded waits inside the tensor-core kernels (bem_jtj,
+ * lm_step and bem_gemm_bf16 in the tensor-core J^T J modes): a wait for a
+ * pipeline slot that is not free after `seconds` of device time gives up,
+ * the kernel records the failure in the context's device status word, lets
+ * the copies and MMAs it has already issued finish (their own waits keep a
+ * one-second limit), frees its tensor memory and returns; the call then
+ * reports BEM_ETIMEDOUT and the context stays usable.  Default 1.0; 0 gives
+ * up at the first wait that is not already complete (to exercise the
+ * failure path).  No counterpart in the paper.  Errors: BEM_EINVAL for a
+ * negative or non-finite value or more than 60 seconds. */
+int bem_set_wait_limit(bem_ctx *ctx, double seconds);
+
+/* The Gauss-Newton products of one LM iteration at the current theta, as
+ * lm_step forms them before its solve (Eq. (losshessian), (lossjacobian),
+ * uniform density, the same n samples for both):
+ *   loss_out  host double: L = (1/2n) sum |u - min(t,1)|^2
+ *   g_out     device double [n_theta]: g = (1/n) J^T r
+ *   H_out     device double [n_theta][n_theta]: H = (1/n) J^T J
+ * (any of the three may be NULL); the data term only, without the Sec. 4.4
+ * regularisers lm_step adds.  xy, target: device (sample type).
+ * Synchronises `stream`.  Errors: as lm_step. */
+int bem_gn_products(bem_ctx *ctx, int64_t n, const void *xy, const void *target,
+                    double *loss_out, double *g_out, double *H_out, void *stream);
 
 /* Per-kernel timing (tracing support; no counterpart in the paper).  While
  * enabled, every hot kernel launch (field evaluation, adjoint, J rows, J^T J

@@ -34,7 +34,7 @@ class bem_opts(ctypes.Structure):
                 ("eps_c", ctypes.c_double), ("segs_per_side", ctypes.c_int),
                 ("near_factor", ctypes.c_double), ("jtj_mode", ctypes.c_int),
                 ("lm_solver", ctypes.c_int), ("galerkin_mode", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("gn_chunk", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class lm_result(ctypes.Structure):
@@ -85,6 +85,10 @@ def _load():
         "bem_sizes": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]),
         "bem_boundary_values": (ci, [vp, dp, vp]),
         "bem_launch_count": (i64, [vp]),
+        "bem_alloc_count": (i64, [vp]),
+        "bem_pipe_peak": (ci, [vp, ci, ci, dp, vp]),
+        "bem_set_wait_limit": (ci, [vp, ctypes.c_double]),
+        "bem_gn_products": (ci, [vp, i64, vp, vp, dp, vp, vp, vp]),
         "bem_profile_enable": (ci, [vp, ci]),
         "bem_gemm_bf16": (ci, [vp, ci, ci, ci, vp, ci, vp, ci, vp, ci, vp]),
         "bem_fastmath_eval": (ci, [vp, ci, i64, vp, vp, vp, vp, vp]),
@@ -102,7 +106,7 @@ def _load():
         "bem_prune": (ci, [vp, ctypes.c_double, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_int32),
                            vp]),
         "bem_init_segments": (ci, [ci, ctypes.c_double, i64, ci, dp, dp, ctypes.POINTER(ci)]),
-        "bem_gram_unit": (ci, [ci, ci, ctypes.POINTER(ctypes.c_int32)]),
+        "bem_gram_unit": (ci, [ci, ci, ci, ctypes.POINTER(ctypes.c_int32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -120,7 +124,8 @@ EXPORTED = [
     "bem_fastmath_eval", "bem_vjp_noalloc", "bem_batch_create", "bem_batch_destroy",
     "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors", "lm_step_split",
     "bem_set_boundary", "bem_setup_segments", "bem_set_regularizers", "bem_prune",
-    "bem_init_segments", "bem_gram_unit",
+    "bem_init_segments", "bem_gram_unit", "bem_alloc_count", "bem_set_wait_limit",
+    "bem_gn_products", "bem_pipe_peak",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -153,7 +158,8 @@ class BEM:
     """One library context (scene + factored boundary) on one CUDA device."""
 
     def __init__(self, precision=BEM_FP64, eps_d=1e-2, eps_c=1e-2, segs_per_side=256,
-                 near_factor=0.5, jtj_mode=None, lm_solver=0, galerkin_mode=0, device=0):
+                 near_factor=0.5, jtj_mode=None, lm_solver=0, galerkin_mode=0, device=0,
+                 gn_chunk=0):
         o = bem_opts()
         _lib.bem_default_opts(ctypes.byref(o))
         o.precision = precision
@@ -164,6 +170,7 @@ class BEM:
             if jtj_mode is None else jtj_mode
         o.lm_solver = lm_solver
         o.galerkin_mode = galerkin_mode
+        o.gn_chunk = gn_chunk
         self.opts = o
         self.device = device
         h = ctypes.c_void_p()
@@ -293,11 +300,19 @@ class BEM:
                                   ctypes.byref(v), _stream(stream)))
         return v.value
 
+    def _grad_buffer(self, grad, xy):
+        import torch
+        assert (isinstance(grad, torch.Tensor) and grad.is_cuda and grad.dtype == torch.float64
+                and grad.is_contiguous() and grad.numel() == self.n_theta
+                and grad.device == xy.device), \
+            f"grad must be a contiguous CUDA float64 tensor of {self.n_theta} entries on {xy.device}"
+
     def vjp(self, xy, resid, grad=None, stream=None):
         import torch
         self._samples(xy, resid)
         if grad is None:
             grad = torch.empty(self.n_theta, dtype=torch.float64, device=xy.device)
+        self._grad_buffer(grad, xy)
         self._check(_lib.bem_vjp(self.h, xy.shape[0], _ptr(xy), _ptr(resid), _ptr(grad),
                                  _stream(stream)))
         return grad
@@ -305,6 +320,7 @@ class BEM:
     def vjp_noalloc(self, xy, resid, grad, stream=None):
         """bem_vjp into a caller-provided gradient buffer, with no device allocation."""
         self._samples(xy, resid)
+        self._grad_buffer(grad, xy)
         self._check(_lib.bem_vjp_noalloc(self.h, xy.shape[0], _ptr(xy), _ptr(resid), _ptr(grad),
                                          _stream(stream)))
         return grad
@@ -367,6 +383,33 @@ class BEM:
 
     def launch_count(self) -> int:
         return int(_lib.bem_launch_count(self.h))
+
+    def pipe_peak(self, which: int, launches: int = 5, stream=None) -> float:
+        """Operations per second of one SM pipe (bem_pipe_peak): 0 FP32 FMA,
+        1 MUFU lg2, 2 MUFU rcp, 3 MUFU rsqrt."""
+        v = ctypes.c_double()
+        self._check(_lib.bem_pipe_peak(self.h, int(which), int(launches), ctypes.byref(v),
+                                       _stream(stream)))
+        return v.value
+
+    def alloc_count(self) -> int:
+        """Device allocations the context has made so far (bem_alloc_count)."""
+        return int(_lib.bem_alloc_count(self.h))
+
+    def set_wait_limit(self, seconds: float):
+        """Limit of the tensor-core kernels' pipeline waits (bem_set_wait_limit)."""
+        self._check(_lib.bem_set_wait_limit(self.h, float(seconds)))
+
+    def gn_products(self, xy, target, stream=None):
+        """(loss, g, H) at the current theta as lm_step forms them (bem_gn_products)."""
+        import torch
+        self._samples(xy, target)
+        g = torch.empty(self.n_theta, dtype=torch.float64, device=xy.device)
+        H = torch.empty((self.n_theta, self.n_theta), dtype=torch.float64, device=xy.device)
+        L = ctypes.c_double()
+        self._check(_lib.bem_gn_products(self.h, xy.shape[0], _ptr(xy), _ptr(target),
+                                         ctypes.byref(L), _ptr(g), _ptr(H), _stream(stream)))
+        return L.value, g, H
 
     def gemm_bf16(self, A, B, stream=None):
         """D = A B^T on the tensor cores (A [M][K], B [N][K] bf16 CUDA tensors)."""
@@ -477,13 +520,15 @@ def init_segments(n_points, length, first_index=1, polygon=None) -> np.ndarray:
     return out[:10 * n.value].copy()
 
 
-def gram_units(tiles: int) -> list:
-    """The bf16 Gram kernel's units over `tiles` block rows, as (kind, a0,
-    a1, b) tuples in launch order (bem_gram_unit; host only)."""
+def gram_units(tiles: int, rows: int | None = None) -> list:
+    """The bf16 Gram kernel's units over the block rows 0 .. rows-1 (default
+    all) of a `tiles` x `tiles` block triangle, as (kind, a0, a1, b) tuples in
+    launch order (bem_gram_unit; host only)."""
     units = []
     out = (ctypes.c_int32 * 4)()
+    rows = tiles if rows is None else rows
     while True:
-        rc = _lib.bem_gram_unit(int(tiles), len(units), out)
+        rc = _lib.bem_gram_unit(int(tiles), int(rows), len(units), out)
         if rc == BEM_EINVAL:
             return units
         if rc != BEM_OK:

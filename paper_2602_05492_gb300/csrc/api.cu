@@ -30,6 +30,7 @@ int grow(bem_ctx* c, DevBuf& b, size_t bytes) {
   b.p = nullptr;
   b.cap = 0;
   size_t want = bytes + bytes / 8;
+  ++c->allocs;
   cudaError_t e = cudaMalloc(&b.p, want);
   if (e != cudaSuccess) {
     b.p = nullptr;
@@ -44,6 +45,7 @@ static int alloc(bem_ctx* c, T*& p, size_t count) {
   if (p) cudaFree(p);
   p = nullptr;
   if (count == 0) count = 1;
+  ++c->allocs;
   return cuda_check(c, cudaMalloc((void**)&p, sizeof(T) * count), "device allocation");
 }
 
@@ -261,6 +263,8 @@ int bem_create(bem_ctx** out, const bem_opts* opts, int device) {
     return fail(nullptr, BEM_EINVAL, "unknown lm_solver");
   if (o.galerkin_mode != 0 && o.galerkin_mode != 1)
     return fail(nullptr, BEM_EINVAL, "unknown galerkin_mode");
+  if (o.gn_chunk != 0 && (o.gn_chunk < 128 || o.gn_chunk > (1 << 22) || o.gn_chunk % 128))
+    return fail(nullptr, BEM_EINVAL, "gn_chunk must be 0 or a multiple of 128 in [128, 4194304]");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
     return fail(nullptr, BEM_ECUDA, "no such CUDA device");
@@ -270,6 +274,12 @@ int bem_create(bem_ctx** out, const bem_opts* opts, int device) {
   c->opts = o;
   int rc;
   if ((rc = set_device(c))) { g_create_err = c->err; delete c; return rc; }
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      c->sms < 1) {
+    g_create_err = "cannot read the multiprocessor count";
+    delete c;
+    return BEM_ECUDA;
+  }
   c->bd.M = o.segs_per_side;
   c->bd.Nb = 4 * o.segs_per_side;
   if ((rc = alloc_boundary(c)) || (rc = alloc(c, c->d_scal, 64)) || (rc = alloc(c, c->d_status, 4))) {
@@ -605,6 +615,44 @@ int bem_jtj(bem_ctx* c, int64_t n, const void* xy, double* H, void* stream) {
 
 namespace bem {
 
+// Loss sum, residual, g = (1/n) J^T r and H of one LM iteration at the
+// context's theta, whose panels and boundary solution are current; with xy_h
+// the Hessian integral uses those n_h points and the gradient comes from the
+// adjoint over (xy, target).  *s0 receives sum |r|^2 (host) once the stream
+// reaches it; |g|^2 lands in d_scal[1].
+static int gn_at_theta(bem_ctx* c, int64_t n, const void* xy, const void* target, int64_t n_h,
+                       const void* xy_h, void* resid, double* g, double* H, double* s0) {
+  int rc;
+  const int nth = c->sc.nth;
+  if (!xy_h && jtj_fuses_eval(c)) {
+    // one pass over the samples: the residual at theta (handle term as F w,
+    // near-field correction, boundary term), g = (1/n) J^T r (Eq.
+    // (lossjacobian)) and H from the same J rows
+    if ((rc = jtj_build(c, n, xy, H, resid, g, target))) return rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
+      return rc;
+    k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0, c->d_scal + 1);
+    BEM_LAUNCHED(c);
+  } else if (!xy_h && jtj_gives_gradient(c)) {
+    if ((rc = field_eval(c, n, xy, nullptr, target, resid, true))) return rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
+      return rc;
+    // g = (1/n) J^T r from the J rows that also build H (Eq. (lossjacobian))
+    if ((rc = jtj_build(c, n, xy, H, resid, g))) return rc;
+    k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0, c->d_scal + 1);
+    BEM_LAUNCHED(c);
+  } else {
+    if ((rc = field_eval(c, n, xy, nullptr, target, resid, true))) return rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
+      return rc;
+    if ((rc = adj_vjp(c, n, xy, resid, g))) return rc;
+    k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0 / double(n), c->d_scal + 1);
+    BEM_LAUNCHED(c);
+    if ((rc = jtj_build(c, xy_h ? n_h : n, xy_h ? xy_h : xy, H))) return rc;
+  }
+  return BEM_OK;
+}
+
 // One LM iteration; with xy_h the Hessian integral uses those n_h points and
 // the gradient comes from the adjoint over (xy, target).
 static int lm_step_impl(bem_ctx* c, int64_t n, const void* xy, const void* target, int64_t n_h,
@@ -635,32 +683,7 @@ static int lm_step_impl(bem_ctx* c, int64_t n, const void* xy, const void* targe
   if ((rc = refresh(c, c->d_theta))) return rc;
   if ((rc = geom_compat(c, c->d_theta, false))) return rc;
   double s0 = 0;
-  if (!xy_h && jtj_fuses_eval(c)) {
-    // one pass over the samples: the residual at theta (handle term as F w,
-    // near-field correction, boundary term), g = (1/n) J^T r (Eq.
-    // (lossjacobian)) and H from the same J rows
-    if ((rc = jtj_build(c, n, xy, (double*)c->H.p, resid, g, target))) return rc;
-    if ((rc = cuda_check(c, cudaMemcpyAsync(&s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
-      return rc;
-    k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0, c->d_scal + 1);
-    BEM_LAUNCHED(c);
-  } else if (!xy_h && jtj_gives_gradient(c)) {
-    if ((rc = field_eval(c, n, xy, nullptr, target, resid, true))) return rc;
-    if ((rc = cuda_check(c, cudaMemcpyAsync(&s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
-      return rc;
-    // g = (1/n) J^T r from the J rows that also build H (Eq. (lossjacobian))
-    if ((rc = jtj_build(c, n, xy, (double*)c->H.p, resid, g))) return rc;
-    k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0, c->d_scal + 1);
-    BEM_LAUNCHED(c);
-  } else {
-    if ((rc = field_eval(c, n, xy, nullptr, target, resid, true))) return rc;
-    if ((rc = cuda_check(c, cudaMemcpyAsync(&s0, c->d_scal, 8, cudaMemcpyDeviceToHost, S(c)), "loss")))
-      return rc;
-    if ((rc = adj_vjp(c, n, xy, resid, g))) return rc;
-    k_scale_norm<<<1, 1024, 0, S(c)>>>(g, nth, 1.0 / double(n), c->d_scal + 1);
-    BEM_LAUNCHED(c);
-    if ((rc = jtj_build(c, xy_h ? n_h : n, xy_h ? xy_h : xy, (double*)c->H.p))) return rc;
-  }
+  if ((rc = gn_at_theta(c, n, xy, target, n_h, xy_h, resid, g, (double*)c->H.p, &s0))) return rc;
   // Sec. 4.4 regularisers: analytic gradient and Hessian added to g and H,
   // snapping pairs chosen here and kept for the trial losses
   const bool reg = reg_active(c);
@@ -790,10 +813,10 @@ int bem_fastmath_eval(bem_ctx* c, int which, int64_t n, const float* a, const fl
   return cuda_check(c, cudaGetLastError(), "k_fastmath");
 }
 
-int bem_gram_unit(int tiles, int unit, int32_t* out) {
+int bem_gram_unit(int tiles, int rows, int unit, int32_t* out) {
   if (!out) return BEM_EINVAL;
   int v[4];
-  const int rc = tc_gram_unit(tiles, unit, v);
+  const int rc = tc_gram_unit(tiles, rows, unit, v);
   if (rc) return rc;
   for (int k = 0; k < 4; ++k) out[k] = v[k];
   return BEM_OK;
@@ -819,6 +842,43 @@ int bem_boundary_values(bem_ctx* c, double* ub, void* stream) {
 }
 
 int64_t bem_launch_count(const bem_ctx* c) { return c ? c->launches : 0; }
+
+int64_t bem_alloc_count(const bem_ctx* c) { return c ? c->allocs : 0; }
+
+int bem_set_wait_limit(bem_ctx* c, double seconds) {
+  if (!c) return BEM_EINVAL;
+  if (!(seconds >= 0) || !(seconds <= 60))
+    return fail(c, BEM_EINVAL, "bem_set_wait_limit: seconds must be in [0, 60]");
+  c->wait_ns = (uint64_t)std::llround(seconds * 1e9);
+  return BEM_OK;
+}
+
+int bem_gn_products(bem_ctx* c, int64_t n, const void* xy, const void* target, double* loss_out,
+                    double* g_out, double* H_out, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (n <= 0 || !xy || !target) return fail(c, BEM_EINVAL, "bem_gn_products: bad arguments");
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  const int nth = c->sc.nth;
+  const size_t es = c->opts.precision == BEM_FP64 ? 8 : 4;
+  const size_t nn = sizeof(double) * (size_t)nth * nth;
+  if ((rc = grow(c, c->H, nn))) return rc;
+  const size_t roff = ((es * 3 * (size_t)n + 255) / 256) * 256;
+  if ((rc = grow(c, c->phi, roff + 8 * (size_t)nth * 2 + 64))) return rc;
+  double* g = (double*)((char*)c->phi.p + roff);
+  if ((rc = refresh(c, c->d_theta))) return rc;
+  double s0 = 0;
+  if ((rc = gn_at_theta(c, n, xy, target, 0, nullptr, c->phi.p, g, (double*)c->H.p, &s0))) return rc;
+  if (g_out &&
+      (rc = cuda_check(c, cudaMemcpyAsync(g_out, g, 8 * (size_t)nth, cudaMemcpyDeviceToDevice, S(c)), "g")))
+    return rc;
+  if (H_out && (rc = cuda_check(c, cudaMemcpyAsync(H_out, c->H.p, nn, cudaMemcpyDeviceToDevice, S(c)), "H")))
+    return rc;
+  if ((rc = cuda_check(c, cudaStreamSynchronize(S(c)), "sync"))) return rc;
+  if (loss_out) *loss_out = 0.5 * s0 / double(n);
+  return BEM_OK;
+}
 
 int bem_profile_enable(bem_ctx* c, int on) {
   if (!c) return BEM_EINVAL;

@@ -63,6 +63,10 @@ struct bem_ctx {
   std::string err;
   cudaStream_t cur = nullptr;
   int64_t launches = 0;
+  int64_t allocs = 0;              // device allocations made by the context (cudaMalloc calls)
+  int sms = 0;                     // multiprocessors of the device
+  // limit of the tensor-core kernels' pipeline waits (bem_set_wait_limit)
+  uint64_t wait_ns = 1000000000ull;
 
   bem::Scene sc;
   bem::Boundary bd;
@@ -103,6 +107,43 @@ struct bem_ctx {
 
 namespace bem {
 
+// Row layout of the J^T rows of the tensor-core Gauss-Newton pass.  Colour
+// channel c's J_c has the position columns of every colour owner (pp per
+// owner) and the two jump columns w_d,c and w_c,c of each owner.  The jump
+// columns do not depend on the channel (the colour is linear in the jumps
+// with the same layer values in every channel, and so are their boundary
+// parts), so the rows hold them once:
+//   rows [c Pp, c Pp + npos)     position columns of channel c (c = 0, 1, 2)
+//   rows [3 Pp, 3 Pp + 2 NH)     jump columns: w_d of owner h at 3 Pp + h,
+//                                w_c of owner h at 3 Pp + NH + h
+// with npos = pp NH, Pp = npos and Pw = 2 NH rounded up to 128 rows (the
+// padding rows are zero).  Channel c's rows, in "channel order", are its
+// position range followed by the jump range: channel index i < Pp is
+// position column i, i >= Pp is jump column i - Pp, which is column
+// npos + i - Pp of the per-channel column order (w_d at npos + h, w_c at
+// npos + NH + h).  The Gram blocks of the jump range with itself are the
+// same for every channel and are formed once, for channel 0.
+struct JLayout {
+  int npos = 0, nh = 0, Pp = 0, Pw = 0;
+  __host__ __device__ int rows() const { return 3 * Pp + Pw; }
+  __host__ __device__ int cdim() const { return Pp + Pw; }
+  __host__ __device__ int tiles() const { return (Pp + Pw) / 128; }    // channel-order 128-row tiles
+  __host__ __device__ int ptiles() const { return Pp / 128; }          // of them in the position range
+  // J^T row of the first row of channel-order tile t of channel ch
+  __host__ __device__ int tile_row(int ch, int t) const {
+    return 128 * t < Pp ? ch * Pp + 128 * t : 3 * Pp + (128 * t - Pp);
+  }
+};
+
+inline JLayout jlayout(int pp, int NH) {
+  JLayout L;
+  L.npos = pp * NH;
+  L.nh = NH;
+  L.Pp = (L.npos + 127) / 128 * 128;
+  L.Pw = (2 * NH + 127) / 128 * 128;
+  return L;
+}
+
 // ---- error plumbing (api.cu) ------------------------------------------------
 int fail(bem_ctx* c, int code, const std::string& msg);
 int cuda_check(bem_ctx* c, cudaError_t e, const char* what);
@@ -118,8 +159,9 @@ void ctx_scale_norm(bem_ctx* c, double* v, int n, double s, double* norm2);
 
 // ---- geometry (k_geom.cu) -----------------------------------------------------
 int geom_panelize(bem_ctx* c, const double* d_theta);
-// compatibility weights a_h of the current panels; with project, w_c of
-// theta is projected onto the compatibility hyperplane in place
+// compatibility weights a_h of the current panels into d_compat; with
+// project, w_c of theta is instead projected onto the compatibility
+// hyperplane of the current panels in place, and d_compat is left as it is
 int geom_compat(bem_ctx* c, double* d_theta, bool project);
 int geom_boundary_tables(bem_ctx* c);                  // vertices, Gauss points
 int geom_assemble(bem_ctx* c);                         // d_A
@@ -204,16 +246,16 @@ bool jtj_fuses_eval(const bem_ctx* c);   // jtj_build accepts a target
 // ---- tensor-core contractions (k_gemm_tc.cu) ----------------------------------------
 int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                   float* D, int ldd);
-int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt, int ldm,
+int tc_jrows(bem_ctx* c, bool x3, const JLayout& L, int m, int Nb, const void* const* Mt, int ldm,
              const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj,
              const float* resid = nullptr, int nc = 0, double* gpart = nullptr,
              int64_t gstride = 0);
-int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, float* part,
-            int splits);
-int tc_syrk_splits(int nc, bool x3);
-// {kind, a0, a1, b} of the bf16 Gram kernel's unit u over T block rows;
-// BEM_EINVAL when T < 1 or u is not a unit of T
-int tc_gram_unit(int T, int u, int* out);
+int tc_syrk(bem_ctx* c, bool x3, const JLayout& L, int m, const void* const* J, int ldj,
+            float* part, int splits);
+int tc_syrk_splits(const JLayout& L, bool x3, int sms);
+// {kind, a0, a1, b} of the bf16 Gram kernel's unit u over the block rows
+// 0 .. R-1 of T; BEM_EINVAL when T < 1, R outside [1, T] or u is not a unit
+int tc_gram_unit(int T, int R, int u, int* out);
 
 // Brackets the kernel launches of its lifetime with events when profiling.
 struct ProfScope {

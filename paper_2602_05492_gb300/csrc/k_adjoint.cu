@@ -19,7 +19,6 @@
 // these sums stay in registers (no cross-thread reduction per pair).
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 
 #include "ctx.h"
 
@@ -392,7 +391,8 @@ static int vjp_pass(bem_ctx* c, int64_t n, const T* xy, const T* w, bool boundar
   // double kernel: about four resident blocks per SM; float kernel: about
   // three waves of seven resident blocks per SM
   const int step = f32 ? kVT : kVB;
-  int64_t want = f32 ? (3 * 7 * 152 + tiles - 1) / tiles : (4 * 152 + tiles - 1) / tiles;
+  const int64_t sms = c->sms;
+  int64_t want = f32 ? (3 * 7 * sms + tiles - 1) / tiles : (4 * sms + tiles - 1) / tiles;
   int64_t maxs = (n + step - 1) / step;
   int slices = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxs));
   int64_t chunk = ((n + slices - 1) / slices + step - 1) / step * step;
@@ -517,23 +517,16 @@ namespace {
 constexpr size_t kNoAllocBytes = 32u << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-unsigned char* g_noalloc_addr[kMaxDevices] = {};
-
-// device address of the static array on the current device (looked up once
-// per device, with that device current)
+// Device address of the static array on the current device.  It is looked
+// up on every call (a host-side table lookup, no device work): a cached
+// address would outlive a device reset or a released and re-created primary
+// context.  The first lookup on a device loads the library's device code
+// there, which must not happen inside a stream capture.
 int noalloc_base(bem_ctx* c, unsigned char** out) {
-  if (c->device < 0 || c->device >= kMaxDevices)
-    return fail(c, BEM_EINVAL, "bem_vjp_noalloc: device index out of range");
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[c->device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_check(c, e, "cudaGetSymbolAddress of the static scratch");
-    g_noalloc_addr[c->device] = (unsigned char*)p;
-  }
-  *out = g_noalloc_addr[c->device];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_check(c, e, "cudaGetSymbolAddress of the static scratch");
+  *out = (unsigned char*)p;
   return BEM_OK;
 }
 
@@ -550,7 +543,8 @@ int noalloc_pass(bem_ctx* c, int64_t n, const T* xy, const T* w, bool boundary, 
   const int tiles = ptiles + btiles;
   const bool f32 = sizeof(T) == 4;
   const int step = f32 ? kVT : kVB;
-  int64_t want = f32 ? (3 * 7 * 152 + tiles - 1) / tiles : (4 * 152 + tiles - 1) / tiles;
+  const int64_t sms = c->sms;
+  int64_t want = f32 ? (3 * 7 * sms + tiles - 1) / tiles : (4 * sms + tiles - 1) / tiles;
   want = std::min<int64_t>(want, max_slices);
   int64_t maxs = (n + step - 1) / step;
   int slices = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxs));

@@ -539,9 +539,7 @@ int field_batch_launch(bem_ctx* c, const BatchJob* jobs, int njobs, const int64_
   int rc;
   if ((rc = cuda_check(c, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), S(c)), "memset")))
     return rc;
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const unsigned grid = (unsigned)std::max(1, sms * blocks_per_sm);
+  const unsigned grid = (unsigned)std::max(1, c->sms * blocks_per_sm);
   const bool same = c->opts.eps_c == c->opts.eps_d, near = c->opts.near_factor > 0;
 #define BEM_BATCH_LAUNCH(SM_, NR_, SPT_) \
   k_field_batch_f32<SM_, NR_, SPT_><<<grid, kFB, 0, S(c)>>>(jobs, njobs, total_tiles, counter)

@@ -26,8 +26,12 @@
 // epilogue warps, 128 x 256 tiles (M = 128, N = 256 MMAs), with two
 // 256-column TMEM accumulators so that a tile's epilogue overlaps the next
 // tile's MMAs.
-// Every wait is bounded (about one second); a timeout sets *err and the CTA
-// drains and frees its TMEM before returning.
+// Every wait is bounded.  The pipeline waits (a ring slot, a TMEM buffer)
+// give up after the context's limit (bem_set_wait_limit, one second by
+// default); the waits that guard work already in flight (copies landing in
+// shared memory, MMAs writing TMEM) after one second whatever that limit.  A
+// timeout sets *err, and the CTA lets its copies and MMAs finish and frees
+// its TMEM before returning.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -72,8 +76,12 @@ struct TcArgs {
   int k_per_split;
   float* part;              // [splits][3][nc][nc]
   int* err;
-  // EPI_JROWS (bf16) with residuals: gpart[row * gstride + blockIdx.y] =
-  // sum over the tile's samples s of F[row][s] resid[s][row / gnc]
+  uint64_t wait_ns;         // limit of the pipeline waits (ring slots, TMEM buffers)
+  JLayout L;                // J^T row layout (EPI_JROWS gradient, EPI_SYRK tiles)
+  // bf16 J rows (k_tc_jrows_pers) with residuals: for each J^T row and each
+  // channel c whose column col it holds (JLayout), gpart[(c gnc + col) *
+  // gstride + column block] = sum over the block's samples s of F[row][s]
+  // resid[s][c]
   const float* resid;
   int gnc;
   double* gpart;
@@ -94,19 +102,29 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  int* gave_up = (int*)(tmem_slot + 1);   // set when the MMA warp stopped early
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // ---- tile coordinates
   int arow, brow, kb, ke, ch = 0, ti = 0, tj = 0;
   if (g.mode == EPI_SYRK) {
-    ch = blockIdx.x / g.npairs;
-    int p = blockIdx.x % g.npairs;
+    // channel 0 takes every upper block of its channel-order tiles (npairs
+    // of them), channels 1 and 2 the npairs1 blocks whose row tile lies in
+    // the position range; the jump-jump blocks are channel 0's for all three
+    const int npairs1 = g.tiles * g.L.ptiles() - g.L.ptiles() * (g.L.ptiles() - 1) / 2;
+    int p = blockIdx.x;
+    ch = 0;
+    if (p >= g.npairs) {
+      p -= g.npairs;
+      ch = 1 + p / npairs1;
+      p %= npairs1;
+    }
     // p -> (ti, tj), ti <= tj, row-major over the upper triangle
     ti = 0;
     while (p >= g.tiles - ti) { p -= g.tiles - ti; ++ti; }
     tj = ti + p;
-    arow = ch * g.nc + ti * BM;
-    brow = ch * g.nc + tj * BN;
+    arow = g.L.tile_row(ch, ti);
+    brow = g.L.tile_row(ch, tj);
     kb = blockIdx.y * g.k_per_split;
     ke = min(g.K, kb + g.k_per_split);
   } else {
@@ -118,6 +136,7 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
   const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;   // BK of the scheme
 
   if (threadIdx.x == 0) {
+    *gave_up = 0;
     for (int s = 0; s < STAGES; ++s) {
       umma::mbar_init(&full[s], 1);
       umma::mbar_init(&empty[s], 1);
@@ -140,7 +159,7 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
     for (int it = 0; it < nk; ++it, issued = it) {
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
-      if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err)) break;
+      if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err, g.wait_ns)) break;
       umma::mbar_expect_tx(&full[s], (same_ab ? PARTS / 2 : PARTS) * TILE_BYTES);
       const int kc = kb + it * BK;
       uint8_t* st = smem + (size_t)s * PARTS * TILE_BYTES;
@@ -160,7 +179,10 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
     for (int it = 0; it < nk; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
-      if (!umma::mbar_wait(&full[s], ph, g.err)) break;
+      if (!umma::mbar_wait(&full[s], ph, g.err, g.wait_ns)) {
+        *(volatile int*)gave_up = 1;
+        break;
+      }
       umma::fence_after();
       const uint32_t a0 = umma::smem_u32(smem + (size_t)s * PARTS * TILE_BYTES);
       const uint32_t b0 = same_ab ? a0 : a0 + TILE_BYTES;
@@ -184,8 +206,8 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
     umma::mma_commit(done);
   }
   __syncwarp();
-  // ---- epilogue: all four warps
-  const bool ok = umma::mbar_wait(done, 0, g.err);
+  // ---- epilogue: all four warps (the guard limit: MMAs may be in flight)
+  const bool ok = umma::mbar_wait(done, 0, g.err) && *(volatile int*)gave_up == 0;
   umma::fence_after();
   const int r = warp * 32 + lane;     // row of the tile owned by this thread
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -195,8 +217,6 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
   // chunk cc sits at position cc ^ (rr & 7), so that the per-row reads below
   // (lane = row) and the in-place bf16 writes are free of bank conflicts.
   float* fs = reinterpret_cast<float*>(smem);
-  // residuals of the tile's samples (when the gradient is formed here)
-  float* rs = fs + BM * BN;
   if (!X3 && g.mode == EPI_JROWS) {
     for (int e = threadIdx.x; e < BM * (BN / 4); e += 128) {
       const int rr = e / (BN / 4), cc = e % (BN / 4);
@@ -212,16 +232,9 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
         d[3] = 0.f;
       }
     }
-    if (g.gpart)
-      for (int e = threadIdx.x; e < 3 * BN; e += 128) {
-        const int col = brow + e / 3;
-        rs[e] = col < g.N ? g.resid[3 * (size_t)col + e % 3] : 0.f;
-      }
     umma::cp_async_wait_all();
     __syncthreads();
   }
-  const int gch = (g.gpart && arow + r < g.M) ? (arow + r) / g.gnc : 0;
-  float gacc = 0.f;
 #pragma unroll 1
   for (int cb = 0; cb < BN; cb += 32) {
     float v[32];
@@ -266,10 +279,6 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
         const float4 q = *reinterpret_cast<const float4*>(fr + ((((cb >> 2) + k) ^ sw) << 2));
         f[4 * k] = q.x; f[4 * k + 1] = q.y; f[4 * k + 2] = q.z; f[4 * k + 3] = q.w;
       }
-      if (g.gpart) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rs[3 * (cb + j) + gch], gacc);
-      }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         uint4 w;
@@ -284,18 +293,12 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
       }
     } else {
       const int i = ti * BM + r;
-      if (i < g.nc) {
-        float* d = g.part + (((size_t)blockIdx.y * 3 + ch) * g.nc + i) * g.nc;
+      const int D = g.L.cdim();
+      float* d = g.part + (((size_t)blockIdx.y * 3 + ch) * D + i) * D;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = tj * BN + cb + j;
-          if (col < g.nc) d[col] += v[j];
-        }
-      }
+      for (int j = 0; j < 32; ++j) d[tj * BN + cb + j] += v[j];
     }
   }
-  if (!X3 && g.mode == EPI_JROWS && g.gpart && arow + r < g.M)
-    g.gpart[(size_t)(arow + r) * g.gstride + blockIdx.y] = (double)gacc;
   if (!X3 && g.mode == EPI_JROWS) {
     __syncthreads();
     // row rr of the bf16 tile sits at the front of fs row rr (bf16 chunk k
@@ -345,7 +348,7 @@ constexpr int kPersBN = 256;                          // samples per tile
 constexpr int kPersPass = kPersBN / BN;               // epilogue passes of BN columns
 constexpr int kPersStage = TILE_BYTES * (1 + kPersPass);   // A slab + B slab (48 KB)
 constexpr int kPersThreads = 320;           // 2 control warps + 8 epilogue warps
-constexpr int kPersSmem = 1024 + PSTAGES * kPersStage + BM * BN * 4 + 3 * BN * 4 + 2 * BM * 4 +
+constexpr int kPersSmem = 1024 + PSTAGES * kPersStage + BM * BN * 4 + 3 * BN * 4 + 6 * BM * 4 +
                           256;
 static_assert(kPersSmem <= 227 * 1024, "persistent J-row kernel exceeds shared memory");
 
@@ -363,13 +366,14 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* fs = reinterpret_cast<float*>(smem + PSTAGES * kPersStage);        // [BM][BN] F rows
   float* rs = fs + BM * BN;                                                  // [BN][3] residuals
-  float* gsum = rs + 3 * BN;                                                 // [2][BM]
-  uint64_t* full = reinterpret_cast<uint64_t*>(gsum + 2 * BM);
+  float* gsum = rs + 3 * BN;                                                 // [3][2][BM]
+  uint64_t* full = reinterpret_cast<uint64_t*>(gsum + 6 * BM);
   uint64_t* empty = full + PSTAGES;
   uint64_t* tfull = empty + PSTAGES;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   int* fail_flag = reinterpret_cast<int*>(tmem_slot + 1);   // set when an epilogue wait gave up
+  int* stop_flag = fail_flag + 1;                           // set when the MMA warp gave up
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rtiles = (g.M + BM - 1) / BM, ctiles = (g.N + kPersBN - 1) / kPersBN;
@@ -377,6 +381,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   const int nk = (g.K + BK - 1) / BK;
   if (threadIdx.x == 0) {
     *fail_flag = 0;
+    *stop_flag = 0;
     for (int s = 0; s < PSTAGES; ++s) {
       umma::mbar_init(&full[s], 1);
       umma::mbar_init(&empty[s], 1);
@@ -403,7 +408,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
         for (int kk = 0; kk < nk; ++kk, ++it) {
           const int s = it % PSTAGES;
           const uint32_t ph = (it / PSTAGES) & 1;
-          if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err)) { ok = false; break; }
+          if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err, g.wait_ns)) { ok = false; break; }
           umma::mbar_expect_tx(&full[s], kPersStage);
           uint8_t* st = smem + (size_t)s * kPersStage;
           umma::tma_load_2d(st, &tA, &full[s], kk * BK, arow);
@@ -424,13 +429,22 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
         const int b = i & 1;
-        if (!umma::mbar_wait(&tempty[b], ((i >> 1) & 1) ^ 1, g.err)) break;
+        if (!umma::mbar_wait(&tempty[b], ((i >> 1) & 1) ^ 1, g.err, g.wait_ns)) {
+          *(volatile int*)stop_flag = 1;
+          break;
+        }
         umma::fence_after();
         const uint32_t acc = tmem + (uint32_t)(b * kPersBN);
         for (int kk = 0; kk < nk; ++kk, ++it) {
           const int s = it % PSTAGES;
           const uint32_t ph = (it / PSTAGES) & 1;
-          if (!umma::mbar_wait(&full[s], ph, g.err)) { ok = false; break; }
+          if (!umma::mbar_wait(&full[s], ph, g.err, g.wait_ns)) {
+            // the epilogue learns from stop_flag, after this tile's commit,
+            // that no further tile follows
+            *(volatile int*)stop_flag = 1;
+            ok = false;
+            break;
+          }
           umma::fence_after();
           const uint32_t a0 = umma::smem_u32(smem + (size_t)s * kPersStage);
           const uint32_t b0 = a0 + TILE_BYTES;   // 256 rows: two 128-row boxes back to back
@@ -477,8 +491,10 @@ __global__ void __launch_bounds__(kPersThreads, 1)
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
       const int b = i & 1;
       const int arow = (t % rtiles) * BM, ct = t / rtiles;
+      // (the guard limit: MMAs of this buffer may still be in flight)
       if (!umma::mbar_wait(&tfull[b], (i >> 1) & 1, g.err)) atomicOr(fail_flag, 1);
       umma::fence_after();
+      if (*(volatile int*)stop_flag) atomicOr(fail_flag, 1);
       for (int p = 0; p < kPersPass; ++p) {
         const int col0 = ct * kPersBN + p * BN;
         // fs holds pass 0's rows already (staged after the previous tile's stores)
@@ -486,8 +502,13 @@ __global__ void __launch_bounds__(kPersThreads, 1)
         umma::cp_async_wait_all();
         bar_epi();
         ok = *(volatile int*)fail_flag == 0;   // the same for all epilogue threads
-        const int gch = (g.gpart && arow + r < g.M) ? (arow + r) / g.gnc : 0;
-        float gacc = 0.f;
+        // gradient rows: a position row sums against its channel's
+        // residual; a jump row (the whole tile, since the jump range starts
+        // on a tile) against all three
+        const bool jump = arow >= 3 * g.L.Pp;
+        int gch = 0;
+        if (g.gpart && !jump) gch = (arow + r) / g.L.Pp;
+        float gacc = 0.f, gacc1 = 0.f, gacc2 = 0.f;
         const float* fr = fs + r * BN;
         const int sw = r & 7;
 #pragma unroll 1
@@ -504,9 +525,16 @@ __global__ void __launch_bounds__(kPersThreads, 1)
             const float4 w4 = *reinterpret_cast<const float4*>(fr + ((((cb >> 2) + k) ^ sw) << 2));
             f[4 * k] = w4.x; f[4 * k + 1] = w4.y; f[4 * k + 2] = w4.z; f[4 * k + 3] = w4.w;
           }
-          if (g.gpart) {
+          if (g.gpart && !jump) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rs[3 * (cb + j) + gch], gacc);
+          } else if (g.gpart) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              gacc = fmaf(f[j], rs[3 * (cb + j)], gacc);
+              gacc1 = fmaf(f[j], rs[3 * (cb + j) + 1], gacc1);
+              gacc2 = fmaf(f[j], rs[3 * (cb + j) + 2], gacc2);
+            }
           }
           // output chunks of this 32-column block: o = ((cb - 64 half) >> 3) + k
           uint8_t* jr = reinterpret_cast<uint8_t*>(fs + r * BN);
@@ -525,6 +553,8 @@ __global__ void __launch_bounds__(kPersThreads, 1)
           }
         }
         gsum[half * BM + r] = gacc;
+        gsum[(2 + half) * BM + r] = gacc1;
+        gsum[(4 + half) * BM + r] = gacc2;
         if (p == kPersPass - 1 || !ok) {
           // this warp's TMEM reads of the tile are complete (or given up, and
           // the loop ends after this pass): release the buffer
@@ -535,9 +565,21 @@ __global__ void __launch_bounds__(kPersThreads, 1)
         bar_epi();
         // the gradient partial of each 128-sample column block (a block past
         // the chunk's end holds nothing and is not written)
-        if (g.gpart && et < BM && arow + et < g.M && col0 < g.N)
-          g.gpart[(size_t)(arow + et) * g.gstride + (kPersPass * ct + p)] =
-              (double)(gsum[et] + gsum[BM + et]);
+        if (g.gpart && et < BM && arow + et < g.M && col0 < g.N) {
+          const int row = arow + et;
+          const int64_t cb = kPersPass * ct + p;
+          if (!jump) {
+            const int c0 = row / g.L.Pp, col = row - c0 * g.L.Pp;
+            if (col < g.L.npos)
+              g.gpart[((size_t)c0 * g.gnc + col) * g.gstride + cb] = (double)(gsum[et] + gsum[BM + et]);
+          } else {
+            const int w = row - 3 * g.L.Pp;
+            if (w < 2 * g.L.nh)
+              for (int k = 0; k < 3; ++k)
+                g.gpart[((size_t)k * g.gnc + g.L.npos + w) * g.gstride + cb] =
+                    (double)(gsum[2 * k * BM + et] + gsum[(2 * k + 1) * BM + et]);
+          }
+        }
         // bf16 rows: one warp writes a 256-byte row per step, 8 bytes per lane
         for (int rr = warp - 2; rr < BM; rr += 8) {
           const int row = arow + rr;
@@ -585,11 +627,18 @@ struct SyrkUnit {
   int kind, a0, a1, b;
 };
 
-// unit u of the T x T upper block triangle, in the order above (also
-// compiled for the host, where bem_gram_unit exposes it to the tests)
-__host__ __device__ __forceinline__ SyrkUnit syrk_unit(int T, int u) {
+// Odd-count block rows r0, r0 + 2, .. below R of a T x T triangle: their number.
+__host__ __device__ __forceinline__ int syrk_odd_rows(int T, int R) {
+  const int r0 = (T - 1) & 1;
+  return R > r0 ? (R - r0 + 1) / 2 : 0;
+}
+
+// unit u of the block rows 0 .. R-1 of the T x T upper block triangle, in the
+// order above (also compiled for the host, where bem_gram_unit exposes it to
+// the tests for R = T)
+__host__ __device__ __forceinline__ SyrkUnit syrk_unit(int T, int R, int u) {
   int np = 0;
-  for (int r = 0; r < T; ++r) np += (T - r) / 2;
+  for (int r = 0; r < R; ++r) np += (T - r) / 2;
   SyrkUnit un;
   if (u < np) {
     int r = 0;
@@ -597,29 +646,31 @@ __host__ __device__ __forceinline__ SyrkUnit syrk_unit(int T, int u) {
     un.kind = 1; un.a0 = r; un.a1 = r; un.b = r + 2 * u;
   } else {
     u -= np;
-    const int r0 = (T - 1) & 1, L = (T + 1) / 2;   // rows with an odd block count: r0, r0 + 2, ..
+    const int r0 = (T - 1) & 1, L = syrk_odd_rows(T, R);   // rows with an odd block count
     if (2 * u + 1 < L) {
       un.kind = 2; un.a0 = r0 + 4 * u; un.a1 = un.a0 + 2; un.b = T - 1;
     } else {
-      un.kind = 0; un.a0 = T - 1; un.a1 = T - 1; un.b = T - 1;
+      un.kind = 0; un.a0 = r0 + 4 * u; un.a1 = un.a0; un.b = T - 1;
     }
   }
   return un;
 }
 
-int syrk_units(int T) {
+__host__ __device__ __forceinline__ int syrk_units(int T, int R) {
   int np = 0;
-  for (int r = 0; r < T; ++r) np += (T - r) / 2;
-  return np + ((T + 1) / 2 + 1) / 2;
+  for (int r = 0; r < R; ++r) np += (T - r) / 2;
+  return np + (syrk_odd_rows(T, R) + 1) / 2;
 }
 
 constexpr int SY_STAGES = 4;
 constexpr int kSyStage = 3 * TILE_BYTES;     // up to three 128-row slabs (48 KB)
 constexpr int kSySmem = 1024 + SY_STAGES * kSyStage + 256;
 
-// part[split][ch][i][j] += the unit's two blocks over its K slice;
-// blockIdx.x = ch * units + unit, blockIdx.y = K slice.  g.tiles = T,
-// g.npairs = units per channel.
+// part[split][ch][i][j] += the unit's two blocks over its K slice (channel-
+// order indices i, j); blockIdx.x = channel 0's units (its whole triangle,
+// g.npairs of them), then those of channels 1 and 2 (the rows of their
+// position range only: the jump-jump blocks are channel 0's), blockIdx.y =
+// K slice.  g.tiles = T channel-order tiles.
 __global__ void __launch_bounds__(128, 1)
     k_tc_syrk_pair(const __grid_constant__ CUtensorMap tJ, TcArgs g) {
   constexpr int BK = Scheme<false>::BK;
@@ -629,10 +680,17 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* empty = full + SY_STAGES;
   uint64_t* done = empty + SY_STAGES;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  int* gave_up = (int*)(tmem_slot + 1);   // set when the MMA warp stopped early
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ch = blockIdx.x / g.npairs;
-  const SyrkUnit un = syrk_unit(g.tiles, blockIdx.x % g.npairs);
-  const int rbase = ch * g.nc;
+  int ch = 0, u = blockIdx.x;
+  const int Tp = g.L.ptiles();
+  if (u >= g.npairs) {
+    const int n1 = syrk_units(g.tiles, Tp);
+    u -= g.npairs;
+    ch = 1 + u / n1;
+    u %= n1;
+  }
+  const SyrkUnit un = syrk_unit(g.tiles, ch == 0 ? g.tiles : Tp, u);
   const int kb = blockIdx.y * g.k_per_split, ke = min(g.K, kb + g.k_per_split);
   const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;
   // slab 0: A (a0), slab 1: A (a1, kind 2) or B, slab 2: B (kind 2) or B's second tile (kind 1)
@@ -640,6 +698,7 @@ __global__ void __launch_bounds__(128, 1)
   const bool loadA1 = un.kind == 2 && un.a1 != un.b;
   const int nslab = (loadA0 ? 1 : 0) + (loadA1 ? 1 : 0) + (un.kind == 0 ? 1 : 2) - (un.kind == 2 ? 1 : 0);
   if (threadIdx.x == 0) {
+    *gave_up = 0;
     for (int s = 0; s < SY_STAGES; ++s) {
       umma::mbar_init(&full[s], 1);
       umma::mbar_init(&empty[s], 1);
@@ -658,18 +717,18 @@ __global__ void __launch_bounds__(128, 1)
     for (int it = 0; it < nk; ++it, issued = it) {
       const int s = it % SY_STAGES;
       const uint32_t ph = (it / SY_STAGES) & 1;
-      if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err)) break;
+      if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err, g.wait_ns)) break;
       umma::mbar_expect_tx(&full[s], nslab * TILE_BYTES);
       const int kc = kb + it * BK;
       uint8_t* st = smem + (size_t)s * kSyStage;
-      if (loadA0) umma::tma_load_2d(st, &tJ, &full[s], kc, rbase + un.a0 * BM);
+      if (loadA0) umma::tma_load_2d(st, &tJ, &full[s], kc, g.L.tile_row(ch, un.a0));
       if (un.kind == 2) {
-        if (loadA1) umma::tma_load_2d(st + TILE_BYTES, &tJ, &full[s], kc, rbase + un.a1 * BM);
-        umma::tma_load_2d(st + 2 * TILE_BYTES, &tJ, &full[s], kc, rbase + un.b * BM);
+        if (loadA1) umma::tma_load_2d(st + TILE_BYTES, &tJ, &full[s], kc, g.L.tile_row(ch, un.a1));
+        umma::tma_load_2d(st + 2 * TILE_BYTES, &tJ, &full[s], kc, g.L.tile_row(ch, un.b));
       } else {
-        umma::tma_load_2d(st + TILE_BYTES, &tJ, &full[s], kc, rbase + un.b * BM);
+        umma::tma_load_2d(st + TILE_BYTES, &tJ, &full[s], kc, g.L.tile_row(ch, un.b));
         if (un.kind == 1)
-          umma::tma_load_2d(st + 2 * TILE_BYTES, &tJ, &full[s], kc, rbase + (un.b + 1) * BM);
+          umma::tma_load_2d(st + 2 * TILE_BYTES, &tJ, &full[s], kc, g.L.tile_row(ch, un.b + 1));
       }
     }
     // the loads still in flight (after a timeout) land before the CTA can leave
@@ -681,7 +740,10 @@ __global__ void __launch_bounds__(128, 1)
     for (int it = 0; it < nk; ++it) {
       const int s = it % SY_STAGES;
       const uint32_t ph = (it / SY_STAGES) & 1;
-      if (!umma::mbar_wait(&full[s], ph, g.err)) break;
+      if (!umma::mbar_wait(&full[s], ph, g.err, g.wait_ns)) {
+        *(volatile int*)gave_up = 1;
+        break;
+      }
       umma::fence_after();
       const uint32_t s0 = umma::smem_u32(smem + (size_t)s * kSyStage);
       const uint32_t s1 = s0 + TILE_BYTES, s2 = s0 + 2 * TILE_BYTES;
@@ -705,7 +767,8 @@ __global__ void __launch_bounds__(128, 1)
   }
   __syncwarp();
   // ---- epilogue: all four warps, thread r = row of the unit's row tile(s)
-  const bool ok = umma::mbar_wait(done, 0, g.err);
+  // (the guard limit: MMAs may be in flight)
+  const bool ok = umma::mbar_wait(done, 0, g.err) && *(volatile int*)gave_up == 0;
   umma::fence_after();
   const int r = warp * 32 + lane;
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -714,6 +777,7 @@ __global__ void __launch_bounds__(128, 1)
     const int ti = (un.kind == 2 && o == 1) ? un.a1 : un.a0;
     const int tj = un.kind == 1 ? un.b + o : un.b;
     const int i = ti * BM + r;
+    const int D = g.L.cdim();
 #pragma unroll 1
     for (int cb = 0; cb < BN; cb += 32) {
       float v[32];
@@ -722,14 +786,9 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = 0.f;
       }
-      if (i < g.nc) {
-        float* d = g.part + (((size_t)blockIdx.y * 3 + ch) * g.nc + i) * g.nc;
+      float* d = g.part + (((size_t)blockIdx.y * 3 + ch) * D + i) * D;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = tj * BN + cb + j;
-          if (col < g.nc) d[col] += v[j];
-        }
-      }
+      for (int j = 0; j < 32; ++j) d[tj * BN + cb + j] += v[j];
     }
   }
   umma::fence_before();
@@ -796,6 +855,7 @@ int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const
     return rc;
   TcArgs g{};
   g.M = M; g.N = N; g.K = K; g.mode = EPI_STORE; g.D = D; g.ldd = ldd; g.err = c->d_status;
+  g.wait_ns = c->wait_ns;
   return launch<false>(c, ta, tb, ta, tb, g, dim3((M + BM - 1) / BM, (N + BN - 1) / BN));
 }
 
@@ -803,9 +863,10 @@ int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const
 //   bf16:   Mt, Phi bf16; J bf16 (Jout[0]); with gpart, also the handle part
 //           of the gradient per 128-sample tile (see TcArgs)
 //   3xtf32: Mt = (Mt[0] hi, Mt[1] lo), Phi likewise, fp32; J hi/lo fp32 (Jout[0], Jout[1])
-int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt, int ldm,
+int tc_jrows(bem_ctx* c, bool x3, const JLayout& L, int m, int Nb, const void* const* Mt, int ldm,
              const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj,
              const float* resid, int nc, double* gpart, int64_t gstride) {
+  const int rows = L.rows();
   int rc;
   CUtensorMap ta, tb, ta2, tb2;
   if ((rc = make_map(c, &ta, Mt[0], Nb, rows, ldm, x3)) ||
@@ -818,6 +879,8 @@ int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt
   TcArgs g{};
   g.M = rows; g.N = m; g.K = Nb; g.mode = EPI_JROWS; g.F = F; g.ldf = ldf; g.ldj = ldj;
   g.err = c->d_status;
+  g.wait_ns = c->wait_ns;
+  g.L = L;
   if (x3) { g.Jhi = (float*)Jout[0]; g.Jlo = (float*)Jout[1]; }
   else g.J = (__nv_bfloat16*)Jout[0];
   if (!x3 && gpart) {
@@ -835,10 +898,8 @@ int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt
       if (e != cudaSuccess) return cuda_check(c, e, "persistent J rows smem attribute");
       attr = true;
     }
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     const int ntiles = ((rows + BM - 1) / BM) * ((m + kPersBN - 1) / kPersBN);
-    const int grid = std::max(1, std::min(ntiles, sms));
+    const int grid = std::max(1, std::min(ntiles, c->sms));
     k_tc_jrows_pers<<<grid, kPersThreads, kPersSmem, S(c)>>>(ta, tb, g);
     BEM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "k_tc_jrows_pers");
@@ -847,22 +908,32 @@ int tc_jrows(bem_ctx* c, bool x3, int rows, int m, int Nb, const void* const* Mt
   return launch<true>(c, ta, tb, ta2, tb2, g, grid);
 }
 
-// part[split][ch][nc][nc] += upper blocks of J_ch^T J_ch over the m samples of J
-// (J rows ch*nc .. ch*nc+nc-1 hold channel ch), K split into `splits` slices.
+// CTAs of one K slice of the Gram kernels: bf16 paired units, 3xtf32 single
+// blocks; channel 0 over its whole channel-order triangle, channels 1 and 2
+// without the jump-jump blocks
+static int gram_ctas(const JLayout& L, bool x3) {
+  const int T = L.tiles(), Tp = L.ptiles();
+  if (x3) return T * (T + 1) / 2 + 2 * (T * Tp - Tp * (Tp - 1) / 2);
+  return syrk_units(T, T) + 2 * syrk_units(T, Tp);
+}
+
+// part[split][ch][cdim][cdim] += upper blocks of J_ch^T J_ch (channel order,
+// JLayout) over the m samples of J, K split into `splits` slices.
 // bf16: J[0] bf16.  3xtf32: J[0] hi, J[1] lo, fp32.
-int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, float* part,
-            int splits) {
+int tc_syrk(bem_ctx* c, bool x3, const JLayout& L, int m, const void* const* J, int ldj,
+            float* part, int splits) {
   int rc;
   CUtensorMap tj, tj2;
-  if ((rc = make_map(c, &tj, J[0], m, 3 * nc, ldj, x3))) return rc;
-  if (x3 && (rc = make_map(c, &tj2, J[1], m, 3 * nc, ldj, true))) return rc;
+  if ((rc = make_map(c, &tj, J[0], m, L.rows(), ldj, x3))) return rc;
+  if (x3 && (rc = make_map(c, &tj2, J[1], m, L.rows(), ldj, true))) return rc;
   TcArgs g{};
-  g.M = g.N = nc; g.K = m; g.mode = EPI_SYRK; g.nc = nc;
-  g.tiles = (nc + BM - 1) / BM;
+  g.M = g.N = L.cdim(); g.K = m; g.mode = EPI_SYRK; g.nc = L.cdim(); g.L = L;
+  g.tiles = L.tiles();
   g.npairs = g.tiles * (g.tiles + 1) / 2;
   const int bk = x3 ? Scheme<true>::BK : Scheme<false>::BK;
   g.k_per_split = ((m + splits - 1) / splits + bk - 1) / bk * bk;
   g.part = part; g.err = c->d_status;
+  g.wait_ns = c->wait_ns;
   int sp = (m + g.k_per_split - 1) / g.k_per_split;
   ProfScope _ps(c, "tc_syrk");
   if (!x3) {
@@ -873,12 +944,12 @@ int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, f
       if (e != cudaSuccess) return cuda_check(c, e, "paired Gram smem attribute");
       attr = true;
     }
-    g.npairs = syrk_units(g.tiles);
-    k_tc_syrk_pair<<<dim3(3 * g.npairs, sp), 128, kSySmem, S(c)>>>(tj, g);
+    g.npairs = syrk_units(g.tiles, g.tiles);
+    k_tc_syrk_pair<<<dim3(gram_ctas(L, false), sp), 128, kSySmem, S(c)>>>(tj, g);
     BEM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "k_tc_syrk_pair");
   }
-  dim3 grid(3 * g.npairs, sp);
+  dim3 grid(gram_ctas(L, true), sp);
   return launch<true>(c, tj, tj, tj2, tj2, g, grid);
 }
 
@@ -886,9 +957,9 @@ int tc_syrk(bem_ctx* c, bool x3, int nc, int m, const void* const* J, int ldj, f
 // wave without starting a second, nearly empty one (rounding up would leave
 // a short tail wave that costs as long as the first)
 // out = {kind, a0, a1, b} of Gram unit u of a T x T block triangle
-int tc_gram_unit(int T, int u, int* out) {
-  if (T < 1 || u < 0 || u >= syrk_units(T)) return BEM_EINVAL;
-  const SyrkUnit un = syrk_unit(T, u);
+int tc_gram_unit(int T, int R, int u, int* out) {
+  if (T < 1 || R < 1 || R > T || u < 0 || u >= syrk_units(T, R)) return BEM_EINVAL;
+  const SyrkUnit un = syrk_unit(T, R, u);
   out[0] = un.kind;
   out[1] = un.a0;
   out[2] = un.a1;
@@ -896,11 +967,10 @@ int tc_gram_unit(int T, int u, int* out) {
   return BEM_OK;
 }
 
-int tc_syrk_splits(int nc, bool x3) {
-  int tiles = (nc + BM - 1) / BM;
+int tc_syrk_splits(const JLayout& L, bool x3, int sms) {
   // bf16: one CTA per SM on paired blocks; 3xtf32: one CTA per SM per block
-  int ctas = 3 * (x3 ? tiles * (tiles + 1) / 2 : syrk_units(tiles));
-  const int slots = 152;
+  const int ctas = gram_ctas(L, x3);
+  const int slots = std::max(1, sms);
   // the fewest slices whose CTAs fill their waves to 95 %, else the best fill up to 8 slices
   // (204 units at n_c = 2,048: one slice leaves the second wave a third full, three fill four)
   int best = 1;

@@ -81,7 +81,7 @@ __global__ void k_compat(double* __restrict__ theta, const Panel<double>* __rest
       for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) {
         a[h] = s;
-        a_out[h] = s;
+        if (a_out) a_out[h] = s;
       }
     }
   }
@@ -166,8 +166,10 @@ int geom_compat(bem_ctx* c, double* d_theta, bool project) {
   int C = c->sc.C;
   size_t shm = sizeof(double) * c->sc.NH;
   if (shm > 48 * 1024) return fail(c, BEM_EINVAL, "too many handles for the compatibility kernel");
+  // a re-projection leaves the step's weights (those of theta, which every
+  // trial's constrained solve uses) as they are
   k_compat<<<1, 1024, shm, S(c)>>>(d_theta, c->d_pan64, c->sc.d_off, c->sc.d_K, C, c->sc.pp,
-                                   c->d_compat, project ? 1 : 0);
+                                   project ? nullptr : c->d_compat, project ? 1 : 0);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_compat");
 }

@@ -20,6 +20,20 @@
 
 namespace bem {
 
+// Channel and per-channel column of J^T row r of the J-row layout, or -1 for
+// a padding row: position rows belong to their channel, the jump rows (the
+// same in every channel) are taken from channel 0.
+__device__ __forceinline__ int jrow_col(const JLayout& L, int r, int& ch) {
+  if (r < 3 * L.Pp) {
+    ch = r / L.Pp;
+    const int col = r - ch * L.Pp;
+    return col < L.npos ? col : -1;
+  }
+  ch = 0;
+  const int w = r - 3 * L.Pp;
+  return w < 2 * L.nh ? L.npos + w : -1;
+}
+
 template <typename T>
 __global__ void k_phi_rows(const T* __restrict__ xy, int ns, const T* __restrict__ vert, int Nb,
                            double* __restrict__ phi) {
@@ -32,7 +46,9 @@ __global__ void k_phi_rows(const T* __restrict__ xy, int ns, const T* __restrict
 }
 
 // F rows of ns points for one curve per blockIdx.y.  TR = false: double
-// F[c][s][nc]; TR = true: float F^T[c*nc + col][s] with row stride ldf.
+// F[c][s][nc]; TR = true: float F^T rows in the J-row layout (JLayout: the
+// position columns per channel at rows c Pp + col, the jump columns once, at
+// rows 3 Pp + h and 3 Pp + NH + h), row stride ldf.
 // Panel k of the curve runs from vertex k to vertex k+1 (vertex v = B(v/K)),
 // so the endpoint derivatives are first summed per vertex (panel k's start
 // plus panel k-1's end) and then spread to the control points with the
@@ -92,7 +108,7 @@ template <typename T, bool SAME, bool TR>
 __global__ void __launch_bounds__(128, 6) k_frows(const T* __restrict__ xy, int ns, const Panel<T>* __restrict__ pan,
                         const int* __restrict__ off, const int* __restrict__ Kc,
                         const uint8_t* __restrict__ closed, int C, T ec2, T ed2,
-                        void* __restrict__ Fout, int ldf, const double* __restrict__ theta,
+                        void* __restrict__ Fout, int ldf, int Pp, const double* __restrict__ theta,
                         float* __restrict__ hw, int ldh) {
   __shared__ FrowsPanel<T> tab[kFrowsTable];
   // the float pair values carry a factor -2 pi (frows_pair)
@@ -173,22 +189,28 @@ __global__ void __launch_bounds__(128, 6) k_frows(const T* __restrict__ xy, int 
       for (int c = 0; c < 3; ++c) { pos[0][e][c] += pos[3][e][c]; pos[3][e][c] = 0; }
   }
   if (TR) {
-    float* F = (float*)Fout;
+    float* F = (float*)Fout + s;
+    float fd[4], fs[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int h = 4 * i + j;
+      fd[j] = float(kOut * cd[j]);
+      fs[j] = float(kOut * cs[j]);
+      F[(size_t)(3 * Pp + h) * ldf] = fd[j];            // jump columns, once for all channels
+      F[(size_t)(3 * Pp + 4 * C + h) * ldf] = fs[j];
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float* base = F + (size_t)c * nc * ldf + s;
+      float* base = F + (size_t)c * Pp * ldf;
       float t = 0.f;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         int h = 4 * i + j;
-        const float fd = float(kOut * cd[j]), fs = float(kOut * cs[j]);
         base[(size_t)(2 * h) * ldf] = float(kOut * pos[j][0][c]);
         base[(size_t)(2 * h + 1) * ldf] = float(kOut * pos[j][1][c]);
-        base[(size_t)(8 * C + h) * ldf] = fd;
-        base[(size_t)(12 * C + h) * ldf] = fs;
         if (hw) {
-          t = fmaf(fd, float(theta[8 * h + 2 + c]), t);
-          t = fmaf(fs, float(theta[8 * h + 5 + c]), t);
+          t = fmaf(fd[j], float(theta[8 * h + 2 + c]), t);
+          t = fmaf(fs[j], float(theta[8 * h + 5 + c]), t);
         }
       }
       if (hw) hw[((size_t)c * C + i) * ldh + s] = t;
@@ -291,30 +313,49 @@ __global__ void k_row_sums(const double* __restrict__ part, int rows, int64_t np
   if (lane == 0) out[row] = s;
 }
 
-// gpart[seg][row] = sum over segment seg of the chunk's samples of
-// F^T[row][s] r[s][row / nc] (double accumulation); one warp per (row,
-// segment), gridDim.y segments
-__global__ void k_ft_gemv(const float* __restrict__ F, int ldf, int rows, int nc, int m,
+// The handle part of the gradient over segment seg of the chunk's samples:
+// gpart[seg][c nc + col] = sum_s F^T[row][s] r[s][c] for every J^T row of
+// the J-row layout and each channel c whose column col it holds (position
+// rows: their channel; jump rows: all three), double accumulation; one warp
+// per (row, segment), gridDim.y segments.
+__global__ void k_ft_gemv(const float* __restrict__ F, int ldf, JLayout L, int nc, int m,
                           const float* __restrict__ r, double* __restrict__ gpart) {
   const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
-  if (row >= rows) return;
-  const int c = row / nc;
+  if (row >= L.rows()) return;
+  int c0 = 0;
+  const int col = jrow_col(L, row, c0);
+  if (col < 0) return;
+  const bool jump = row >= 3 * L.Pp;
   const int seg = (m + gridDim.y - 1) / gridDim.y;
   const int sb = blockIdx.y * seg, se = min(m, sb + seg);
   const float* f = F + (size_t)row * ldf;
-  double acc = 0;
+  double acc[3] = {0, 0, 0};
   for (int s0 = sb; s0 < se; s0 += 32 * 8) {
-    float a = 0;
+    float a[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int s = s0 + u * 32 + lane;
-      if (s < se) a += f[s] * r[3 * s + c];
+      if (s < se) {
+        const float v = f[s];
+        if (jump) {
+          a[0] += v * r[3 * s]; a[1] += v * r[3 * s + 1]; a[2] += v * r[3 * s + 2];
+        } else {
+          a[0] += v * r[3 * s + c0];
+        }
+      }
     }
-    acc += a;
+    for (int k = 0; k < 3; ++k) acc[k] += a[k];
   }
-  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) gpart[(size_t)blockIdx.y * rows + row] = acc;
+  for (int k = 0; k < 3; ++k)
+    for (int o = 16; o; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  if (lane) return;
+  double* out = gpart + (size_t)blockIdx.y * 3 * nc;
+  if (jump) {
+    for (int k = 0; k < 3; ++k) out[(size_t)k * nc + col] = acc[k];
+  } else {
+    out[(size_t)c0 * nc + col] = acc[0];
+  }
 }
 
 // g[theta] = scale * sum over channels of (handle part + boundary part) of
@@ -360,19 +401,23 @@ __global__ void k_g_assemble(const double* __restrict__ gparts, int nparts, int 
   g[t] = scale * s;
 }
 
-// Hc[c][i][j] = sum over splits of part[split][c][i][j] (upper blocks) in
-// fixed order, mirrored to the lower triangle
-__global__ void k_syrk_reduce(const float* __restrict__ part, int splits, int nc,
+// Hc[c][i][j] (per-channel column order, nc x nc) = sum over splits of the
+// Gram entry of channel-order indices (i', j') of channel c (upper blocks,
+// part[split][c][cdim][cdim]) in fixed order, mirrored to the lower
+// triangle; the jump-jump entries of every channel are channel 0's.
+__global__ void k_syrk_reduce(const float* __restrict__ part, int splits, int nc, JLayout L,
                               double* __restrict__ Hc) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y, c = blockIdx.z;
   if (j >= nc) return;
-  int a = min(i, j), b = max(i, j);
-  // a block (ti, tj) with ti <= tj holds entry (a, b) when a's tile <= b's tile
-  size_t off = ((size_t)c * nc + a) * nc + b;
-  if ((a / 128) > (b / 128)) off = ((size_t)c * nc + b) * nc + a;
+  const int ci = i < L.npos ? i : L.Pp + (i - L.npos);
+  const int cj = j < L.npos ? j : L.Pp + (j - L.npos);
+  const int a = min(ci, cj), b = max(ci, cj);
+  const int D = L.cdim();
+  const int src = (a >= L.Pp) ? 0 : c;       // jump-jump blocks: channel 0
+  const size_t off = ((size_t)src * D + a) * D + b;
   double s = 0;
-  size_t stride = (size_t)3 * nc * nc;
+  const size_t stride = (size_t)3 * D * D;
   for (int k = 0; k < splits; ++k) s += (double)part[k * stride + off];
   Hc[((size_t)c * nc + i) * nc + j] = s;
 }
@@ -414,7 +459,7 @@ constexpr int kSegRun = 8;
 template <typename T, bool SAME, bool TR>
 __global__ void __launch_bounds__(128) k_frows_seg(const T* __restrict__ xy, int ns,
                                                    const Panel<T>* __restrict__ pan, int H, T ec2,
-                                                   T ed2, void* __restrict__ Fout, int ldf) {
+                                                   T ed2, void* __restrict__ Fout, int ldf, int Pp) {
   constexpr T kOut = sizeof(T) == 4 ? T(-kInv2Pi) : T(1);
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ns) return;
@@ -435,9 +480,14 @@ __global__ void __launch_bounds__(128) k_frows_seg(const T* __restrict__ xy, int
       v[5] = kOut * S;
       const int cols[6] = {4 * h, 4 * h + 1, 4 * h + 2, 4 * h + 3, 4 * H + h, 5 * H + h};
       if (TR) {
-        float* F = (float*)Fout + (size_t)c * nc * ldf + s;
+        // J-row layout: positions per channel, the jump columns once
+        float* F = (float*)Fout + s;
 #pragma unroll
-        for (int e = 0; e < 6; ++e) F[(size_t)cols[e] * ldf] = float(v[e]);
+        for (int e = 0; e < 4; ++e) F[(size_t)(c * Pp + cols[e]) * ldf] = float(v[e]);
+        if (c == 0) {
+          F[(size_t)(3 * Pp + h) * ldf] = float(v[4]);
+          F[(size_t)(3 * Pp + H + h) * ldf] = float(v[5]);
+        }
       } else {
         double* row = (double*)Fout + ((size_t)c * ns + s) * nc;
 #pragma unroll
@@ -450,6 +500,7 @@ __global__ void __launch_bounds__(128) k_frows_seg(const T* __restrict__ xy, int
 template <typename T, bool TR = false>
 static void launch_frows(bem_ctx* c, const T* xy, int ns, void* F, int ldf = 0,
                          float* hw = nullptr, int ldh = 0) {
+  const int Pp = jlayout(c->sc.pp, c->sc.NH).Pp;
   int C = c->sc.C;
   dim3 grid((ns + 127) / 128, C);
   const Panel<T>* pan =
@@ -460,20 +511,20 @@ static void launch_frows(bem_ctx* c, const T* xy, int ns, void* F, int ldf = 0,
     const int H = c->sc.NH;
     dim3 gs((ns + 127) / 128, (H + kSegRun - 1) / kSegRun);
     if (c->opts.eps_c == c->opts.eps_d)
-      k_frows_seg<T, true, TR><<<gs, 128, 0, S(c)>>>(xy, ns, pan, H, ec2, ed2, F, ldf);
+      k_frows_seg<T, true, TR><<<gs, 128, 0, S(c)>>>(xy, ns, pan, H, ec2, ed2, F, ldf, Pp);
     else
-      k_frows_seg<T, false, TR><<<gs, 128, 0, S(c)>>>(xy, ns, pan, H, ec2, ed2, F, ldf);
+      k_frows_seg<T, false, TR><<<gs, 128, 0, S(c)>>>(xy, ns, pan, H, ec2, ed2, F, ldf, Pp);
     BEM_LAUNCHED(c);
     return;
   }
   if (c->opts.eps_c == c->opts.eps_d)
     k_frows<T, true, TR><<<grid, 128, 0, S(c)>>>(xy, ns, pan, c->sc.d_off, c->sc.d_K,
-                                                 c->sc.d_closed, C, ec2, ed2, F, ldf, c->d_theta,
-                                                 hw, ldh);
+                                                 c->sc.d_closed, C, ec2, ed2, F, ldf, Pp,
+                                                 c->d_theta, hw, ldh);
   else
     k_frows<T, false, TR><<<grid, 128, 0, S(c)>>>(xy, ns, pan, c->sc.d_off, c->sc.d_K,
-                                                  c->sc.d_closed, C, ec2, ed2, F, ldf, c->d_theta,
-                                                  hw, ldh);
+                                                  c->sc.d_closed, C, ec2, ed2, F, ldf, Pp,
+                                                  c->d_theta, hw, ldh);
   BEM_LAUNCHED(c);
 }
 
@@ -500,7 +551,7 @@ static int jtj_t(bem_ctx* c, int64_t n, const T* xy, double* Hout) {
   // chunks of samples
   size_t per = sizeof(double) * ((size_t)Nb + 3 * (size_t)nc);
   int64_t ns = std::max<int64_t>(128, std::min<int64_t>(n, (int64_t)((512u << 20) / per)));
-  ns = std::min<int64_t>(ns, 32768);
+  ns = std::min<int64_t>(ns, c->opts.gn_chunk > 0 ? c->opts.gn_chunk : 32768);
   bem_ctx* w = c->scratch ? c->scratch : c;   // owner of the chunk buffers
   if ((rc = grow(c, w->jrow, per * (size_t)ns))) return rc;
   double* phi = (double*)w->jrow.p;
@@ -534,20 +585,22 @@ static int jtj_t(bem_ctx* c, int64_t n, const T* xy, double* Hout) {
 }
 
 // The A operand of the tensor-core J-row contraction straight from Df:
-//   Mt[c nc + col][j] = M_c[j][col] = sum_i W[j][i] Df_c[i][col]
-// in fp32 (W = A^+ as float, Df converted on load), 64 x 64 tiles of 4 x 4
+//   Mt[row][j] = M_c[j][col] = sum_i W[j][i] Df_c[i][col]
+// for the channel and column of each J^T row (jrow_col; padding rows 0), in
+// fp32 (W = A^+ as float, Df converted on load), 64 x 64 tiles of 4 x 4
 // outputs per thread, written as bf16 or as the tf32 hi/lo pair.  The result
 // is rounded to bf16 / tf32 at once, so fp32 accumulation loses nothing the
 // J rows keep.
 template <bool X3>
 __global__ void __launch_bounds__(256) k_mt_sgemm(const float* __restrict__ W,
                                                   const double* __restrict__ Df, int Nb, int nc,
-                                                  void* __restrict__ out0, void* __restrict__ out1) {
+                                                  JLayout L, void* __restrict__ out0,
+                                                  void* __restrict__ out1) {
   __shared__ float As[16][64 + 4];   // [k][row of Mt]
   __shared__ float Bs[16][64 + 4];   // [k][j]
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int j0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
-  const int rows = 3 * nc;
+  const int rows = L.rows();
   float acc[4][4];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
@@ -558,10 +611,9 @@ __global__ void __launch_bounds__(256) k_mt_sgemm(const float* __restrict__ W,
       const int kk = e >> 6, rr = e & 63;
       const int r = r0 + rr, i = i0 + kk;
       float v = 0.f;
-      if (r < rows && i < Nb) {
-        const int ch = r / nc, col = r - ch * nc;
-        v = (float)Df[((size_t)ch * Nb + i) * nc + col];
-      }
+      int ch = 0;
+      const int col = r < rows ? jrow_col(L, r, ch) : -1;
+      if (col >= 0 && i < Nb) v = (float)Df[((size_t)ch * Nb + i) * nc + col];
       As[kk][rr] = v;
     }
     for (int e = threadIdx.x; e < 1024; e += 256) {
@@ -685,30 +737,34 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   const bool fuse_r = want_g && target;
   if (target && !want_g) return fail(c, BEM_EINVAL, "jtj: a target needs the residual and gradient outputs");
   if ((rc = jtj_stacked_rhs<float>(c, false))) return rc;
+  // J^T rows: the position columns per channel, the jump columns once (JLayout)
+  const JLayout L = jlayout(c->sc.pp, c->sc.NH);
+  const int rows = L.rows();
   const size_t es = x3 ? 2 * sizeof(float) : sizeof(__nv_bfloat16);   // bytes per element (all parts)
-  // M_c^T, [3 nc][Nb]
-  const size_t mt_part = (x3 ? 4 : 2) * 3 * (size_t)nc * Nb;
-  if ((rc = grow(c, c->tcMt, es * 3 * (size_t)nc * Nb))) return rc;
+  // M^T in the J-row layout, [rows][Nb]
+  const size_t mt_part = (x3 ? 4 : 2) * (size_t)rows * Nb;
+  if ((rc = grow(c, c->tcMt, es * (size_t)rows * Nb))) return rc;
   const void* Mt[2] = {c->tcMt.p, (char*)c->tcMt.p + mt_part};
   {
     ProfScope _pm(c, "k_mt_sgemm");
-    dim3 grid((Nb + 63) / 64, (3 * nc + 63) / 64);
+    dim3 grid((Nb + 63) / 64, (rows + 63) / 64);
     if (x3)
-      k_mt_sgemm<true><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, (const double*)c->Dfc.p, Nb, nc,
+      k_mt_sgemm<true><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, (const double*)c->Dfc.p, Nb, nc, L,
                                                (void*)Mt[0], (void*)Mt[1]);
     else
-      k_mt_sgemm<false><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, (const double*)c->Dfc.p, Nb, nc,
+      k_mt_sgemm<false><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, (const double*)c->Dfc.p, Nb, nc, L,
                                                 (void*)Mt[0], nullptr);
     BEM_LAUNCHED(c);
   }
-  // per-chunk buffers: Phi [m][Nb], F^T f32 [3nc][ld], J^T [3nc][ld]
-  const int64_t chunk = std::min<int64_t>(std::max<int64_t>(n, 1), 262144);
+  // per-chunk buffers: Phi [m][Nb], F^T f32 [rows][ld], J^T [rows][ld]
+  const int64_t chunk = std::min<int64_t>(std::max<int64_t>(n, 1),
+                                          c->opts.gn_chunk > 0 ? c->opts.gn_chunk : 262144);
   const int nchunks = (int)((n + chunk - 1) / chunk);
   const int ld = (int)((chunk + 63) / 64 * 64);
   const size_t phi_part = (x3 ? 4 : 2) * (size_t)chunk * Nb;
   const size_t phi_b = (x3 ? 2 : 1) * phi_part;
-  const size_t f_b = sizeof(float) * 3 * (size_t)nc * ld;
-  const size_t j_part = (x3 ? 4 : 2) * 3 * (size_t)nc * ld;
+  const size_t f_b = sizeof(float) * (size_t)rows * ld;
+  const size_t j_part = (x3 ? 4 : 2) * (size_t)rows * ld;
   const size_t j_b = (x3 ? 2 : 1) * j_part;
   // gradient work: per chunk handle partial [3nc], q partials per slice
   // sample slices of the Phi-row pass: 1,024 samples each, up to 256 (a
@@ -729,8 +785,8 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   if ((rc = grow(c, w->jrow, phi_b + 256 + f_b + 256 + hw_b + 256))) return rc;
   if ((rc = grow(c, w->tcJ, j_b))) return rc;
   if (want_g && (rc = grow(c, w->gwork, gh_b + q_b + gb_b + 256))) return rc;
-  const int splits = tc_syrk_splits(nc, x3);
-  const size_t part_b = sizeof(float) * (size_t)splits * 3 * nc * nc;
+  const int splits = tc_syrk_splits(L, x3, c->sms);
+  const size_t part_b = sizeof(float) * (size_t)splits * 3 * L.cdim() * L.cdim();
   if ((rc = grow(c, w->tcPart, part_b))) return rc;
   if ((rc = grow(c, c->Hc, sizeof(double) * 3 * (size_t)nc * nc))) return rc;
   const void* phi[2] = {w->jrow.p, (char*)w->jrow.p + phi_part};
@@ -752,6 +808,16 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   }
   if ((rc = cuda_check(c, cudaMemsetAsync(part, 0, part_b, S(c)), "memset"))) return rc;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
+  // the padding rows of F^T (never written by the F rows) hold zeros, so
+  // that the J rows of the padding are zero
+  for (int k = 0; k < 4; ++k) {
+    const int r0 = k < 3 ? k * L.Pp + L.npos : 3 * L.Pp + 2 * L.nh;
+    const int r1 = k < 3 ? (k + 1) * L.Pp : rows;
+    if (r1 > r0 &&
+        (rc = cuda_check(c, cudaMemsetAsync(F + (size_t)r0 * ld, 0, sizeof(float) * (size_t)(r1 - r0) * ld,
+                                            S(c)), "memset")))
+      return rc;
+  }
   int ci = 0;
   int64_t tile_col = 0;
   if (fused_g &&
@@ -796,20 +862,20 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
     }
     if (want_g && !fused_g) {
       ProfScope _pg(c, "k_ft_gemv");
-      k_ft_gemv<<<dim3((3 * nc + 7) / 8, kGemvSegs), 256, 0, S(c)>>>(
-          F, ld, 3 * nc, nc, m, resid + 3 * s0, gh + (size_t)ci * kGemvSegs * 3 * nc);
+      k_ft_gemv<<<dim3((rows + 7) / 8, kGemvSegs), 256, 0, S(c)>>>(
+          F, ld, L, nc, m, resid + 3 * s0, gh + (size_t)ci * kGemvSegs * 3 * nc);
       BEM_LAUNCHED(c);
     }
-    if ((rc = tc_jrows(c, x3, 3 * nc, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld,
+    if ((rc = tc_jrows(c, x3, L, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld,
                        fused_g ? resid + 3 * s0 : nullptr, nc,
                        fused_g ? gh + tile_col : nullptr, tiles_all)))
       return rc;
     tile_col += (m + 127) / 128;
     const void* Jc[2] = {J[0], J[1]};
-    if ((rc = tc_syrk(c, x3, nc, m, Jc, ld, part, splits))) return rc;
+    if ((rc = tc_syrk(c, x3, L, m, Jc, ld, part, splits))) return rc;
   }
   if (fuse_r && (rc = field_sum_loss(c, lossp, lblk))) return rc;
-  k_syrk_reduce<<<dim3((nc + 127) / 128, nc, 3), 128, 0, S(c)>>>(part, splits, nc,
+  k_syrk_reduce<<<dim3((nc + 127) / 128, nc, 3), 128, 0, S(c)>>>(part, splits, nc, L,
                                                                   (double*)c->Hc.p);
   k_h_assemble<<<dim3((nth + 127) / 128, nth), 128, 0, S(c)>>>((const double*)c->Hc.p, c->sc.pp, c->sc.NH,
                                                                 n > 0 ? 1.0 / double(n) : 0.0, Hout);

@@ -378,11 +378,12 @@ __global__ void k_add3(double* __restrict__ y, const double* __restrict__ d, int
   if (i < n3) y[i] += d[i];
 }
 
-int la_apply3_refined(bem_ctx* c, const float* W32, const double* A, const double* x, double* y,
-                      bool transpose) {
-  int Nb = c->bd.Nb, rc;
-  if ((rc = grow(c, c->gpart, sizeof(double) * 6 * Nb))) return rc;
-  double* r = (double*)c->gpart.p;
+// Refined product with the caller's scratch (6 Nb doubles): y = A^+ x by the
+// float A^+, then one correction A^+ (x - A y) with the residual in double.
+int la_apply3_refined_buf(bem_ctx* c, const float* W32, const double* A, const double* x,
+                          double* y, bool transpose, double* scratch) {
+  int Nb = c->bd.Nb;
+  double* r = scratch;
   double* d = r + 3 * Nb;
   k_apply3_f<<<(Nb + 7) / 8, 256, 0, S(c)>>>(W32, Nb, x, y);
   // A^+ (x - A u): for u = A^+ x exactly this is A^+ P x - A^+ A A^+ x = 0
@@ -393,19 +394,12 @@ int la_apply3_refined(bem_ctx* c, const float* W32, const double* A, const doubl
   return cuda_check(c, cudaGetLastError(), "refined apply");
 }
 
-// Same refined product as la_apply3_refined with the caller's scratch
-// (6 Nb doubles) instead of a context buffer.
-int la_apply3_refined_buf(bem_ctx* c, const float* W32, const double* A, const double* x,
-                          double* y, bool transpose, double* scratch) {
-  int Nb = c->bd.Nb;
-  double* r = scratch;
-  double* d = r + 3 * Nb;
-  k_apply3_f<<<(Nb + 7) / 8, 256, 0, S(c)>>>(W32, Nb, x, y);
-  k_resid3<<<(Nb + 7) / 8, 256, 0, S(c)>>>(A, Nb, x, y, r, transpose);
-  k_apply3_f<<<(Nb + 7) / 8, 256, 0, S(c)>>>(W32, Nb, r, d);
-  k_add3<<<(3 * Nb + 255) / 256, 256, 0, S(c)>>>(y, d, 3 * Nb);
-  c->launches += 4;
-  return cuda_check(c, cudaGetLastError(), "refined apply");
+// The same with the context's scratch buffer.
+int la_apply3_refined(bem_ctx* c, const float* W32, const double* A, const double* x, double* y,
+                      bool transpose) {
+  int rc;
+  if ((rc = grow(c, c->gpart, sizeof(double) * 6 * c->bd.Nb))) return rc;
+  return la_apply3_refined_buf(c, W32, A, x, y, transpose, (double*)c->gpart.p);
 }
 
 // ---------------------------------------------------------------------------
@@ -1206,9 +1200,9 @@ __global__ void k_backward_error(const double* __restrict__ part, int nblk,
 // Y: scratch [n][4].
 static void chol_solve4(bem_ctx* c, const double* L, const double* Linv, int n, double* R,
                         double* Y) {
-  const int grid = std::max(1, std::min(152, (n + 255) / 256));
+  const int grid = std::max(1, std::min(c->sms, (n + 255) / 256));
   for (int kb = 0; kb < n; kb += 32) {
-    k_trsv_fwd_step<<<std::max(1, std::min(152, (n - kb + 7) / 8)), 256, 0, S(c)>>>(
+    k_trsv_fwd_step<<<std::max(1, std::min(c->sms, (n - kb + 7) / 8)), 256, 0, S(c)>>>(
         L, n, kb, std::min(32, n - kb), Linv, R, Y);
     BEM_LAUNCHED(c);
   }

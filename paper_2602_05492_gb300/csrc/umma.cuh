@@ -44,15 +44,26 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t addr, uint32_t parity) {
   return done;
 }
 
-// Wait for the phase of `parity` to complete.  Gives up after about one
-// second of device time: sets *err and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// Limit of the waits that guard asynchronous work already issued (copies in
+// flight into shared memory, MMAs in flight into TMEM) before a CTA reads
+// the result, frees TMEM or exits: one second, whatever the caller's limit.
+constexpr uint64_t kGuardNs = 1000000000ull;
+
+// Wait for the phase of `parity` to complete.  Gives up after limit_ns of
+// device time (limit_ns = 0: as soon as one poll finds the phase incomplete):
+// sets *err and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          uint64_t limit_ns = kGuardNs) {
   const uint32_t addr = smem_u32(bar);
   if (mbar_try(addr, parity)) return true;
+  if (limit_ns == 0) {
+    atomicExch(err, 1);
+    return false;
+  }
   const uint64_t t0 = gtimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(addr, parity)) return true;
-    if ((it & 255u) == 0 && gtimer() - t0 > 1000000000ull) {
+    if ((it & 255u) == 0 && gtimer() - t0 > limit_ns) {
       atomicExch(err, 1);
       return false;
     }

@@ -29,6 +29,11 @@ def _ctx(bg, sc, prec):
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
 def test_vjp_noalloc_matches_vjp_twice(prec, tol):
+    """On a fresh context (set up and factored, no adjoint run yet, so none
+    of bem_vjp's buffers exists) two bem_vjp_noalloc calls in a row: the
+    context's allocation count stays where it was, the device's free memory
+    does not move across the calls, and both results match bem_vjp on a
+    second context."""
     import paper_2602_05492_gb300 as bg
     p = {"fp64": bg.BEM_FP64, "mixed": bg.BEM_MIXED}[prec]
     dt = torch.float64 if prec == "fp64" else torch.float32
@@ -38,21 +43,32 @@ def test_vjp_noalloc_matches_vjp_twice(prec, tol):
     xt = torch.tensor(xy, dtype=dt, device="cuda:0")
     r = torch.tensor(np.random.default_rng(4).normal(size=(xy.shape[0], 3)), dtype=dt,
                      device="cuda:0")
-    want = m.vjp(xt, r).cpu().numpy()
+    gs = [torch.full((m.n_theta,), float("nan"), dtype=torch.float64, device="cuda:0")
+          for _ in range(2)]
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    outs = []
-    for _ in range(2):
-        g = torch.full((m.n_theta,), float("nan"), dtype=torch.float64, device="cuda:0")
+    torch.cuda.synchronize()
+    allocs0 = m.alloc_count()
+    for k, g in enumerate(gs):
+        free0 = torch.cuda.mem_get_info()[0]
         rc = bg.bem_vjp_noalloc(m.h, xt.shape[0], ctypes.c_void_p(xt.data_ptr()),
                                 ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(g.data_ptr()),
                                 stream)
         assert rc == 0, bg.bem_last_error(m.h).decode()
         torch.cuda.synchronize()
-        outs.append(g.cpu().numpy())
-    for g in outs:
+        # the first call on a device may load the library's device code (and
+        # with it the static array) there; from the second call on nothing
+        # may change the device's free memory
+        if k == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
+        assert m.alloc_count() == allocs0
+    ref = _ctx(bg, sc, p)
+    want = ref.vjp(xt, r).cpu().numpy()
+    for g in gs:
+        g = g.cpu().numpy()
         assert np.isfinite(g).all()
         assert np.linalg.norm(g - want) / np.linalg.norm(want) < tol
     m.close()
+    ref.close()
 
 
 def test_vjp_noalloc_rejects_oversized_scene():
