@@ -490,6 +490,25 @@ def config2_extras(bg, dev, flush, stream, local, jm, rank):
     ms = _timed(step2, 10, flush, stream)
     out["lm_step"] = {"ms_per_step": sum(ms) / len(ms), "lm_iters_per_s": 1e3 * len(ms) / sum(ms)}
 
+    # the same step with the Gauss-Newton matrix in the two compensated schemes
+    for name, mode in (("lm_step_bf16x3", bg.BEM_JTJ_BF16X3), ("lm_step_3xtf32", bg.BEM_JTJ_3XTF32)):
+        mj = bg.BEM(precision=bg.BEM_MIXED, device=local, jtj_mode=mode, near_factor=near_factor(2))
+        mj.setup(sc2.n_curves, sc2.panels_per_curve, sc2.closed, sc2.theta_init, np.zeros(3))
+        mj.set_mean_color(mj.sample_mean(t2))
+        mj.factor()
+        lam_j = [1e-3]
+
+        def step_j():
+            r = mj.lm_step(x2, t2, lam_j)
+            lam_j[0] = r["lambda_next"]
+
+        for _ in range(2):
+            step_j()
+        torch.cuda.synchronize()
+        ms = _timed(step_j, 5, flush, stream)
+        out[name] = {"ms_per_step": sum(ms) / len(ms), "lm_iters_per_s": 1e3 * len(ms) / sum(ms)}
+        mj.close()
+
     # M_H = M_J / 4: H from every fourth sample (lm_step_split)
     xh = x2[::4].contiguous()
     m2.set_params(sc2.theta_init)
@@ -592,7 +611,7 @@ def run_ours(args, rank, world, dist):
     if args.samples:                     # profiling aid: leading part of the workload
         xy, target = xy[:args.samples].copy(), target[:args.samples].copy()
     n = xy.shape[0]
-    jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32}[args.jtj]
+    jm = {"bf16": bg.BEM_JTJ_BF16, "bf16x3": bg.BEM_JTJ_BF16X3, "3xtf32": bg.BEM_JTJ_3XTF32}[args.jtj]
     nf = near_factor(cfg)
     m = bg.BEM(precision=bg.BEM_MIXED, device=local, jtj_mode=jm, near_factor=nf)
     xt = torch.from_numpy(xy).to(dev)
@@ -893,7 +912,11 @@ def run_batch(args, rank, world):
             "one_at_a_time": {"value": seq, "unit": "scene LM iter/s",
                               "ms_per_step": tsq / args.steps},
             "batched_over_one_at_a_time": value / seq, "clocks": clk,
-            "kernels_batched": kb, "kernels_one_at_a_time": ks}
+            "kernels_batched": kb, "kernels_one_at_a_time": ks,
+            "kernels_note": "event times per kernel name; in the batched call the per-scene "
+                            "trial setup (damped solves, trial geometry) runs on one stream per "
+                            "scene at once, so those kernels' times overlap and their sum "
+                            "exceeds the wall time they take"}
     print(json.dumps(line), flush=True)
 
 
@@ -910,7 +933,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="leave out the secondary measurements on the 1M-sample workload")
     ap.add_argument("--oracle-probe", default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--jtj", default="bf16", choices=["bf16", "3xtf32"],
+    ap.add_argument("--jtj", default="bf16", choices=["bf16", "bf16x3", "3xtf32"],
                     help="tensor-core scheme of the J^T J contraction")
     ap.add_argument("--config", type=int, default=CFG, choices=[2, 4, 5],
                     help="4: 67M samples, 8,192 panels (default); 2: 1M samples, 2,048 "

@@ -53,7 +53,17 @@ typedef enum {
 } bem_status;
 
 enum { BEM_FP64 = 0, BEM_MIXED = 1 };                         /* bem_opts.precision */
-enum { BEM_JTJ_FP64 = 0, BEM_JTJ_BF16 = 1, BEM_JTJ_3XTF32 = 2 }; /* bem_opts.jtj_mode */
+/* bem_opts.jtj_mode, the arithmetic of H = J^T J in BEM_MIXED contexts:
+ *   FP64     double products of the float J rows (SIMT)
+ *   BF16     J rows rounded to bf16, one tensor-core product, fp32 accumulation
+ *   3XTF32   every operand split into two tf32 parts (x = hi + lo), the three
+ *            products hi.hi + hi.lo + lo.hi accumulated in fp32
+ *   BF16X3   the same split with two bf16 parts (compensated bf16: about 16
+ *            mantissa bits per operand, at half the operand bytes and twice
+ *            the product rate of 3XTF32)
+ * In every tensor-core mode the fp32 sums of slices of samples are added in
+ * double. */
+enum { BEM_JTJ_FP64 = 0, BEM_JTJ_BF16 = 1, BEM_JTJ_3XTF32 = 2, BEM_JTJ_BF16X3 = 3 };
 /* bem_opts.lm_solver: how the damped KKT system of lm_step is solved.
  * AUTO: Cholesky of the equilibrated matrix in float, iterative refinement
  * against the double residual until the normwise backward error is below

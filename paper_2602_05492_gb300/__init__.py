@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbemgb.so")
 BEM_OK, BEM_EINVAL, BEM_ESTATE, BEM_ESINGULAR, BEM_ENOTSPD, BEM_ECUDA, BEM_ETIMEDOUT, BEM_ENOMEM = \
     0, -1, -2, -3, -4, -5, -6, -7
 BEM_FP64, BEM_MIXED = 0, 1
-BEM_JTJ_FP64, BEM_JTJ_BF16, BEM_JTJ_3XTF32 = 0, 1, 2
+BEM_JTJ_FP64, BEM_JTJ_BF16, BEM_JTJ_3XTF32, BEM_JTJ_BF16X3 = 0, 1, 2, 3
 BEM_LM_AUTO, BEM_LM_FP64 = 0, 1
 
 _STATUS = {0: "BEM_OK", -1: "BEM_EINVAL", -2: "BEM_ESTATE", -3: "BEM_ESINGULAR",

@@ -257,7 +257,7 @@ int bem_create(bem_ctx** out, const bem_opts* opts, int device) {
   if (o.segs_per_side < 1 || o.segs_per_side > 4096)
     return fail(nullptr, BEM_EINVAL, "segs_per_side must be in [1, 4096]");
   if (!(o.near_factor >= 0)) return fail(nullptr, BEM_EINVAL, "near_factor must be >= 0");
-  if (o.jtj_mode < BEM_JTJ_FP64 || o.jtj_mode > BEM_JTJ_3XTF32)
+  if (o.jtj_mode < BEM_JTJ_FP64 || o.jtj_mode > BEM_JTJ_BF16X3)
     return fail(nullptr, BEM_EINVAL, "unknown jtj_mode");
   if (o.lm_solver != BEM_LM_AUTO && o.lm_solver != BEM_LM_FP64)
     return fail(nullptr, BEM_EINVAL, "unknown lm_solver");

@@ -218,8 +218,10 @@ FieldArgs<float> field_args_f32(bem_ctx* c);
 // tile, blocks_per_sm CTAs per SM); total_tiles and counter: device words
 // (the counter is reset here), so that a captured graph can be replayed
 // with new job contents
+// nt > 1: every job evaluates its nt trials (BatchJob.tpan ..), sharing the
+// boundary angles of its points
 int field_batch_launch(bem_ctx* c, const BatchJob* jobs, int njobs, const int64_t* total_tiles,
-                       unsigned long long* counter, int spt, int blocks_per_sm);
+                       unsigned long long* counter, int spt, int blocks_per_sm, int nt = 1);
 
 // ---- near field of the mixed path (k_near.cu) ------------------------------------
 // out[n][3] = double sum over the near panels of each point
@@ -244,13 +246,18 @@ bool jtj_gives_gradient(const bem_ctx* c);
 bool jtj_fuses_eval(const bem_ctx* c);   // jtj_build accepts a target
 
 // ---- tensor-core contractions (k_gemm_tc.cu) ----------------------------------------
+// Operand schemes of the J^T J contraction: one bf16 product, or each value
+// split into a high and a low part (x = hi + lo) with the three products
+// hi.hi + hi.lo + lo.hi accumulated in fp32, the parts tf32 (stored as fp32)
+// or bf16.
+enum { SCH_BF16 = 0, SCH_TF32X3 = 1, SCH_BF16X3 = 2 };
 int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                   float* D, int ldd);
-int tc_jrows(bem_ctx* c, bool x3, const JLayout& L, int m, int Nb, const void* const* Mt, int ldm,
+int tc_jrows(bem_ctx* c, int sch, const JLayout& L, int m, int Nb, const void* const* Mt, int ldm,
              const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj,
              const float* resid = nullptr, int nc = 0, double* gpart = nullptr,
              int64_t gstride = 0);
-int tc_syrk(bem_ctx* c, bool x3, const JLayout& L, int m, const void* const* J, int ldj,
+int tc_syrk(bem_ctx* c, int sch, const JLayout& L, int m, const void* const* J, int ldj,
             float* part, int splits);
 int tc_syrk_splits(const JLayout& L, bool x3, int sms);
 // {kind, a0, a1, b} of the bf16 Gram kernel's unit u over the block rows

@@ -31,11 +31,22 @@ struct FieldArgs {
   const double* near_add;  // double near-field sum [n][3] or null
 };
 
-// One job of the batched evaluation: a scene at one parameter vector, its
-// tiles numbered from tile0 in the batch's tile list.
+// Most damping trials one job of the batched evaluation takes at once.
+constexpr int kJobTrials = 4;
+
+// One job of the batched evaluation, its tiles numbered from tile0 in the
+// batch's tile list: a scene at one parameter vector (a), or, in the trial
+// launch, a scene at nt trial parameter vectors, their panels, boundary
+// solutions, double near-field sums and loss partials (per tile) given per
+// trial.
 struct BatchJob {
   FieldArgs<float> a;
   int64_t tile0;
+  int nt;
+  const Panel<float>* tpan[kJobTrials];
+  const double* tub[kJobTrials];
+  const double* tnear[kJobTrials];
+  double* tloss[kJobTrials];
 };
 
 }  // namespace bem

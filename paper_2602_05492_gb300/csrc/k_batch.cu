@@ -9,9 +9,15 @@
 //      residuals and loss partials (k_field_batch_f32);
 //   B  per scene: H and g = (1/n) J^T r from the J rows (tensor cores);
 //   C  per scene and trial: the damped KKT solve, theta_t = theta + delta,
-//      projection, panels, boundary solution and near sums of theta_t;
-//   D  one persistent launch over the sample tiles of all (scene, trial)
-//      pairs: the trial losses;
+//      projection, panels, boundary solution and near sums of theta_t.  The
+//      scenes are independent here and their work is chains of small,
+//      latency-bound kernels with host checks (the solves' refinement), so
+//      each scene runs on its own stream, driven by one of several host
+//      threads, and the chains of different scenes overlap on the GPU;
+//   D  one persistent launch over the sample tiles of all scenes: the trial
+//      losses, the (up to four) trials of a scene on the same tile so that
+//      they share the boundary angles of its points, which do not depend on
+//      the handles;
 //   E  per scene: the best trial is kept if it lowers the loss.
 // The two persistent launches (with their counter reset and loss sums) are
 // captured once into CUDA graphs and replayed: the job tables they read live
@@ -23,19 +29,23 @@
 // and before its next work; the Gauss-Newton chunk buffers of scene 0 serve
 // every scene.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ctx.h"
 
 namespace bem {
 
-// sums[j] = sum over the tiles of job j of part[tile] (fixed order, one block per job)
+// sums[j nt + t] = sum over the tiles of job j of part[t total + tile] (fixed
+// order, one block per job and trial, blockIdx.y = trial)
 __global__ void k_job_sums(const double* __restrict__ part, const BatchJob* __restrict__ jobs,
                            int njobs, const int64_t* __restrict__ total, double* __restrict__ sums) {
   __shared__ double red[32];
-  const int j = blockIdx.x;
+  const int j = blockIdx.x, t = blockIdx.y;
+  part += (size_t)t * *total;
   const int64_t b = jobs[j].tile0, e = j + 1 < njobs ? jobs[j + 1].tile0 : *total;
   double s = 0.0;
   const int64_t m = e - b;
@@ -46,9 +56,9 @@ __global__ void k_job_sums(const double* __restrict__ part, const BatchJob* __re
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    sums[j] = t;
+    double acc = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w];
+    sums[(size_t)j * gridDim.y + t] = acc;
   }
 }
 
@@ -61,6 +71,9 @@ struct bem_batch {
   bem_ctx* c0 = nullptr;                 // errors, device, shared chunk buffers
   cudaStream_t st = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<cudaStream_t> sst;         // [S] the scenes' streams of phase C
+  std::vector<cudaEvent_t> sev;          // [S] their ends
+  cudaEvent_t ev_b = nullptr;            // end of phase B
   int T = 0;                             // trials the buffers are sized for
   std::vector<int64_t> n;                // samples the buffers are sized for
   std::vector<DevBuf> resid;             // [S] float [n][3]
@@ -71,6 +84,7 @@ struct bem_batch {
   std::vector<BatchJob> hjobs[2];
   std::vector<int64_t> htotal;
   int spt = 1, bps = 8;
+  int nt[2] = {1, 1};                    // trials per job of each job table
   bool tuned = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_njobs[2] = {-1, -1};
@@ -103,9 +117,14 @@ void number_tiles(bem_batch* b, int k, int spt) {
   b->htotal[k] = t;
 }
 
-// point every job's loss partials at its tiles
+// point every job's loss partials at its tiles (trial t of a multi-trial
+// job: the t-th block of htotal partials)
 void bind_partials(bem_batch* b, int k) {
-  for (auto& j : b->hjobs[k]) j.a.loss_part = (double*)b->part[k].p + j.tile0;
+  double* part = (double*)b->part[k].p;
+  for (auto& j : b->hjobs[k]) {
+    j.a.loss_part = part + j.tile0;
+    for (int t = 0; t < j.nt && j.nt > 1; ++t) j.tloss[t] = part + (size_t)t * b->htotal[k] + j.tile0;
+  }
 }
 
 int upload(bem_batch* b, int k) {
@@ -126,10 +145,12 @@ int run_eval(bem_batch* b, int k) {
   const int nj = (int)b->hjobs[k].size();
   int rc;
   if ((rc = field_batch_launch(c, (const BatchJob*)b->jobs[k].p, nj, (const int64_t*)b->total[k].p,
-                               (unsigned long long*)b->counter[k].p, b->spt, b->bps)))
+                               (unsigned long long*)b->counter[k].p, b->spt, b->bps, b->nt[k])))
     return rc;
-  k_job_sums<<<nj, 256, 0, b->st>>>((const double*)b->part[k].p, (const BatchJob*)b->jobs[k].p, nj,
-                                    (const int64_t*)b->total[k].p, (double*)b->sums[k].p);
+  k_job_sums<<<dim3(nj, b->nt[k]), 256, 0, b->st>>>((const double*)b->part[k].p,
+                                                    (const BatchJob*)b->jobs[k].p, nj,
+                                                    (const int64_t*)b->total[k].p,
+                                                    (double*)b->sums[k].p);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_job_sums");
 }
@@ -157,6 +178,7 @@ int eval_graph(bem_batch* b, int k) {
     if ((rc = cuda_check(c, e, "graph instantiate"))) return rc;
     b->graph_njobs[k] = nj;
   }
+  ProfScope _ps(c, "k_field_batch");   // c->cur is b->st outside the per-scene phase
   return cuda_check(c, cudaGraphLaunch(b->graph[k], b->st), "graph launch");
 }
 
@@ -248,6 +270,7 @@ int size_buffers(bem_batch* b, const int64_t* n, int T) {
 // the evaluation job of scene s with its current device state
 BatchJob scene_job(bem_ctx* cs, int64_t n, const void* xy, const void* target) {
   BatchJob j{};
+  j.nt = 1;
   j.a = field_args_f32(cs);
   j.a.xy = (const float*)xy;
   j.a.n = n;
@@ -320,12 +343,19 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
                                            cudaMemcpyDeviceToHost, b->st), "norm")) ||
       (rc = cuda_check(c0, cudaStreamSynchronize(b->st), "sync")))
     return rc;
-  // ---- C: trials
+  // ---- C: trials, every scene on its own stream (after phase B), several
+  // host threads taking the scenes in turn
   std::vector<double> used((size_t)S * T, 0.0);
   std::vector<char> ok((size_t)S * T, 0);
-  b->hjobs[1].resize((size_t)S * T);
-  for (int s = 0; s < S; ++s) {
+  std::vector<BatchJob> trial_jobs((size_t)S * T);
+  if ((rc = cuda_check(c0, cudaEventRecord(b->ev_b, b->st), "event"))) return rc;
+  for (int s = 0; s < S; ++s)
+    if ((rc = cuda_check(c0, cudaStreamWaitEvent(b->sst[s], b->ev_b, 0), "event"))) return rc;
+  std::vector<int> src(S, BEM_OK);
+  auto scene_trials = [&](int s) -> int {
+    int rc = BEM_OK;
     bem_ctx* c = b->sc[s];
+    c->cur = b->sst[s];
     const int nth = c->sc.nth;
     const double* g = (const double*)b->gvec[s].p;
     for (int t = 0; t < T; ++t) {
@@ -340,7 +370,8 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
       BatchJob j{};
       if (rc == BEM_ENOTSPD) {
         j.a.n = 0;                   // no tiles; the trial is skipped
-        b->hjobs[1][i] = j;
+        trial_jobs[i] = j;
+        rc = BEM_OK;
         continue;
       }
       if (rc) return rc;
@@ -352,9 +383,9 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
         return rc;
       if ((rc = cuda_check(c, cudaMemcpyAsync(b->tpan[i].p, c->d_pan32,
                                               sizeof(Panel<float>) * (size_t)c->sc.P,
-                                              cudaMemcpyDeviceToDevice, b->st), "trial panels")) ||
+                                              cudaMemcpyDeviceToDevice, c->cur), "trial panels")) ||
           (rc = cuda_check(c, cudaMemcpyAsync(b->tub[i].p, c->d_ub, sizeof(double) * 3 * c->bd.Nb,
-                                              cudaMemcpyDeviceToDevice, b->st), "trial ub")))
+                                              cudaMemcpyDeviceToDevice, c->cur), "trial ub")))
         return rc;
       j = scene_job(c, n[s], xy[s], target[s]);
       j.a.pan = (const Panel<float>*)b->tpan[i].p;
@@ -364,10 +395,60 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
         if ((rc = near_forward(c, n[s], (const float*)xy[s], nb))) return rc;
         j.a.near_add = nb;
       }
-      b->hjobs[1][i] = j;
+      trial_jobs[i] = j;
     }
+    return rc;
+  };
+  {
+    const int nthreads = std::min(S, 8);
+    std::atomic<int> next(0);
+    auto worker = [&]() {
+      // the runtime's current device is per host thread
+      if (cudaSetDevice(c0->device) != cudaSuccess) return;
+      for (int s = next++; s < S; s = next++) src[s] = scene_trials(s);
+    };
+    std::vector<std::thread> pool;
+    for (int k = 1; k < nthreads; ++k) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
   }
-  // ---- D: one persistent launch over all (scene, trial) pairs
+  for (int s = 0; s < S; ++s) {
+    b->sc[s]->cur = b->st;
+    cudaEventRecord(b->sev[s], b->sst[s]);
+    cudaStreamWaitEvent(b->st, b->sev[s], 0);
+  }
+  for (int s = 0; s < S; ++s)
+    if (src[s]) return src[s];
+  // ---- D: one persistent launch over all scenes and trials: with 2 to
+  // kJobTrials trials one job per scene evaluates them all (a skipped
+  // trial points at a factored one's data; its loss is not used), else one
+  // job per (scene, trial)
+  b->nt[1] = (T >= 2 && T <= kJobTrials) ? T : 1;
+  if (b->nt[1] > 1) {
+    b->hjobs[1].assign(S, BatchJob{});
+    for (int s = 0; s < S; ++s) {
+      int first = -1;
+      for (int t = 0; t < T && first < 0; ++t)
+        if (ok[(size_t)s * T + t]) first = t;
+      BatchJob& j = b->hjobs[1][s];
+      if (first < 0) {               // no trial factored: no tiles (reported below)
+        j.a.n = 0;
+        j.nt = T;
+        continue;
+      }
+      j = trial_jobs[(size_t)s * T + first];
+      j.nt = T;
+      for (int t = 0; t < T; ++t) {
+        const BatchJob& tj = trial_jobs[(size_t)s * T + (ok[(size_t)s * T + t] ? t : first)];
+        j.tpan[t] = tj.a.pan;
+        j.tub[t] = tj.a.ub;
+        j.tnear[t] = tj.a.near_add;
+      }
+    }
+  } else {
+    b->hjobs[1] = trial_jobs;
+    for (auto& j : b->hjobs[1]) j.nt = 1;
+  }
   if (!b->tuned && (rc = autotune(b, 1))) return rc;
   number_tiles(b, 1, b->spt);
   bind_partials(b, 1);
@@ -446,10 +527,19 @@ int bem_batch_create(bem_batch** out, bem_ctx* const* scenes, int n_scenes) {
   b->htotal.assign(2, 0);
   if ((rc = cuda_check(c0, cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking), "stream")) ||
       (rc = cuda_check(c0, cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "event")) ||
-      (rc = cuda_check(c0, cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "event"))) {
+      (rc = cuda_check(c0, cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "event")) ||
+      (rc = cuda_check(c0, cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming), "event"))) {
     bem_batch_destroy(b);
     return rc;
   }
+  b->sst.assign(n_scenes, nullptr);
+  b->sev.assign(n_scenes, nullptr);
+  for (int s = 0; s < n_scenes; ++s)
+    if ((rc = cuda_check(c0, cudaStreamCreateWithFlags(&b->sst[s], cudaStreamNonBlocking), "stream")) ||
+        (rc = cuda_check(c0, cudaEventCreateWithFlags(&b->sev[s], cudaEventDisableTiming), "event"))) {
+      bem_batch_destroy(b);
+      return rc;
+    }
   *out = b;
   return BEM_OK;
 }
@@ -472,6 +562,11 @@ void bem_batch_destroy(bem_batch* b) {
   for (bem_ctx* c : b->sc) c->scratch = nullptr;
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->ev_b) cudaEventDestroy(b->ev_b);
+  for (cudaStream_t st : b->sst)
+    if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+  for (cudaEvent_t e : b->sev)
+    if (e) cudaEventDestroy(e);
   if (b->st) cudaStreamDestroy(b->st);
   delete b;
 }

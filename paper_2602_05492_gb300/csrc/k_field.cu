@@ -160,39 +160,18 @@ struct FieldSmemF {
   int wcnt[kFB / 32];
 };
 
-// One tile of kFB * SPT points, thread t owning points t, t + kFB, ...:
-// handle sums with near-zone culling, the boundary term and the epilogue
-// (colour, residual, the tile's loss partial in loss_part[tile]).  `ys` is
-// the panel slice in split mode.  Every CTA-wide barrier is reached by all
-// threads.
+// Handle sums of the points of a tile against the panels [p0, p1) of pan,
+// added into s: the panels staged as PanelF kFB at a time; with NEAR, each
+// staged tile puts first the panels whose near zone meets the block's
+// bounding box bb, and only those pairs take the near test.  Every CTA-wide
+// barrier is reached by all threads.
 template <bool SAME, bool NEAR, int SPT>
-__device__ __forceinline__ void field_tile_f32(const FieldArgs<float>& a, int64_t tile, int ys,
-                                               FieldSmemF& sm) {
+__device__ __forceinline__ void tile_handle_sums(const FieldArgs<float>& a,
+                                                 const Panel<float>* __restrict__ pan, int p0,
+                                                 int p1, const float (&x)[SPT],
+                                                 const float (&y)[SPT], float4 bb,
+                                                 float (&s)[SPT][3], FieldSmemF& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int64_t i[SPT];
-  bool live[SPT];
-  float x[SPT], y[SPT];
-  float x0 = __int_as_float(0x7f800000), y0 = x0, x1 = -x0, y1 = -x0;
-  bool any = false;
-#pragma unroll
-  for (int k = 0; k < SPT; ++k) {
-    i[k] = tile * (kFB * SPT) + k * kFB + tid;
-    live[k] = i[k] < a.n;
-    x[k] = 0.5f; y[k] = 0.5f;
-    if (live[k]) {
-      x[k] = a.xy[2 * i[k]];
-      y[k] = a.xy[2 * i[k] + 1];
-      x0 = fminf(x0, x[k]); y0 = fminf(y0, y[k]); x1 = fmaxf(x1, x[k]); y1 = fmaxf(y1, y[k]);
-      any = true;
-    }
-  }
-  float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
-  if constexpr (NEAR) bb = block_bbox(x0, y0, x1, y1, any, sm.bred);
-  float s[SPT][3];
-#pragma unroll
-  for (int k = 0; k < SPT; ++k) s[k][0] = s[k][1] = s[k][2] = 0.f;
-  const int p0 = a.split_out ? ys * a.pchunk : 0;
-  const int p1 = a.split_out ? min(a.P, p0 + a.pchunk) : a.P;
   for (int base = p0; base < p1; base += kFB) {
     const int cnt = min(kFB, p1 - base);
     int nf = 0;   // panels [0, nf) of the tile may have near pairs
@@ -201,7 +180,7 @@ __device__ __forceinline__ void field_tile_f32(const FieldArgs<float>& a, int64_
       Panel<float> p{};
       bool cand = false;
       if (tid < cnt) {
-        p = a.pan[base + tid];
+        p = pan[base + tid];
         cand = boxes_meet(near_zone(p, a.nfac), bb);
       }
       const unsigned m = __ballot_sync(0xffffffffu, cand);
@@ -219,7 +198,7 @@ __device__ __forceinline__ void field_tile_f32(const FieldArgs<float>& a, int64_
         reinterpret_cast<PanelF*>(sm.tile)[slot] = stage_panel(p, a.near2);
       }
     } else {
-      if (tid < cnt) reinterpret_cast<PanelF*>(sm.tile)[tid] = stage_panel(a.pan[base + tid], 0.f);
+      if (tid < cnt) reinterpret_cast<PanelF*>(sm.tile)[tid] = stage_panel(pan[base + tid], 0.f);
     }
     __syncthreads();
     for (int k = 0; k < nf; ++k) {
@@ -241,53 +220,64 @@ __device__ __forceinline__ void field_tile_f32(const FieldArgs<float>& a, int64_
       }
     }
   }
-  if (a.split_out) {
+}
+
+// Boundary angle sums of the points of a tile for NT boundary solutions at
+// once: b[t][q][c] += phi_j(x_q) u_t[j][c] over the segments j (without the
+// 1/(2 pi)).  The angle of a segment does not depend on the handles, so the
+// trials of one LM step share it.  su holds kFB entries per solution.
+template <int SPT, int NT>
+__device__ __forceinline__ void tile_boundary_sums(const float* __restrict__ vert, int Nb,
+                                                   const double* const (&ub)[NT],
+                                                   const float (&x)[SPT], const float (&y)[SPT],
+                                                   float (&b)[NT][SPT][3], float2* sv, float4* su) {
+  const int tid = threadIdx.x;
+  for (int base = 0; base < Nb; base += kFB) {
+    __syncthreads();
+    const int cnt = min(kFB, Nb - base);
+    if (tid < cnt) {
+      const int j = base + tid;
+      sv[tid] = make_float2(vert[2 * j], vert[2 * j + 1]);
 #pragma unroll
-    for (int q = 0; q < SPT; ++q)
-      if (live[q]) {
-        double* o = a.split_out + ((size_t)ys * a.n + i[q]) * 3;
-        o[0] = double(s[q][0]);
-        o[1] = double(s[q][1]);
-        o[2] = double(s[q][2]);
-      }
-    return;
-  }
-  float b[SPT][3];
+      for (int t = 0; t < NT; ++t)
+        su[t * kFB + tid] = make_float4(float(ub[t][3 * j]), float(ub[t][3 * j + 1]),
+                                        float(ub[t][3 * j + 2]), 0.f);
+    }
+    if (tid == 0) sv[cnt] = make_float2(vert[2 * (base + cnt)], vert[2 * (base + cnt) + 1]);
+    __syncthreads();
+    float dax[SPT], day[SPT];
 #pragma unroll
-  for (int q = 0; q < SPT; ++q) b[q][0] = b[q][1] = b[q][2] = 0.f;
-  if (a.ub) {
-    for (int base = 0; base < a.Nb; base += kFB) {
-      __syncthreads();
-      const int cnt = min(kFB, a.Nb - base);
-      if (tid < cnt) {
-        const int j = base + tid;
-        sm.sv[tid] = make_float2(a.vert[2 * j], a.vert[2 * j + 1]);
-        sm.su[tid] = make_float4(float(a.ub[3 * j]), float(a.ub[3 * j + 1]),
-                                 float(a.ub[3 * j + 2]), 0.f);
-      }
-      if (tid == 0)
-        sm.sv[cnt] = make_float2(a.vert[2 * (base + cnt)], a.vert[2 * (base + cnt) + 1]);
-      __syncthreads();
-      float dax[SPT], day[SPT];
+    for (int q = 0; q < SPT; ++q) { dax[q] = sv[0].x - x[q]; day[q] = sv[0].y - y[q]; }
+    for (int k = 0; k < cnt; ++k) {
+      const float2 w = sv[k + 1];
 #pragma unroll
-      for (int q = 0; q < SPT; ++q) { dax[q] = sm.sv[0].x - x[q]; day[q] = sm.sv[0].y - y[q]; }
-      for (int k = 0; k < cnt; ++k) {
-        const float2 w = sm.sv[k + 1];
-        const float4 u = sm.su[k];
+      for (int q = 0; q < SPT; ++q) {
+        const float dbx = w.x - x[q], dby = w.y - y[q];
+        const float phi = fm_atan2(dax[q] * dby - day[q] * dbx, dax[q] * dbx + day[q] * dby);
 #pragma unroll
-        for (int q = 0; q < SPT; ++q) {
-          const float dbx = w.x - x[q], dby = w.y - y[q];
-          const float phi = fm_atan2(dax[q] * dby - day[q] * dbx, dax[q] * dbx + day[q] * dby);
-          b[q][0] = fmaf(phi, u.x, b[q][0]);
-          b[q][1] = fmaf(phi, u.y, b[q][1]);
-          b[q][2] = fmaf(phi, u.z, b[q][2]);
-          dax[q] = dbx;
-          day[q] = dby;
+        for (int t = 0; t < NT; ++t) {
+          const float4 u = su[t * kFB + k];
+          b[t][q][0] = fmaf(phi, u.x, b[t][q][0]);
+          b[t][q][1] = fmaf(phi, u.y, b[t][q][1]);
+          b[t][q][2] = fmaf(phi, u.z, b[t][q][2]);
         }
+        dax[q] = dbx;
+        day[q] = dby;
       }
     }
   }
-  // colour, residual and the tile's loss partial
+}
+
+// Colour, residual and the tile's loss partial (loss_part[tile]) from the
+// handle sums s, the boundary angle sums b and the double near-field sums
+// near_add (or null).
+template <int SPT>
+__device__ __forceinline__ void tile_finish(const FieldArgs<float>& a, int64_t tile,
+                                            const int64_t (&i)[SPT], const bool (&live)[SPT],
+                                            const float (&s)[SPT][3], const float (&b)[SPT][3],
+                                            const double* __restrict__ near_add,
+                                            double* __restrict__ loss_part, FieldSmemF& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double r2 = 0.0;
 #pragma unroll
   for (int q = 0; q < SPT; ++q) {
@@ -296,10 +286,10 @@ __device__ __forceinline__ void field_tile_f32(const FieldArgs<float>& a, int64_
     double u2 = a.mean2 + double(b[q][2]) * kInv2Pi + double(s[q][2]);
     if (!live[q]) continue;
     const int64_t ii = i[q];
-    if (a.near_add) {
-      u0 += a.near_add[3 * ii];
-      u1 += a.near_add[3 * ii + 1];
-      u2 += a.near_add[3 * ii + 2];
+    if (near_add) {
+      u0 += near_add[3 * ii];
+      u1 += near_add[3 * ii + 1];
+      u2 += near_add[3 * ii + 2];
     }
     if (a.out) {
       a.out[3 * ii] = float(u0);
@@ -318,7 +308,7 @@ __device__ __forceinline__ void field_tile_f32(const FieldArgs<float>& a, int64_
       r2 += r0 * r0 + r1 * r1 + rr * rr;
     }
   }
-  if (a.loss_part) {
+  if (loss_part) {
     for (int o = 16; o; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
     __syncthreads();
     if (lane == 0) sm.red[warp] = r2;
@@ -326,8 +316,103 @@ __device__ __forceinline__ void field_tile_f32(const FieldArgs<float>& a, int64_
     if (tid == 0) {
       double t = 0;
       for (int w = 0; w < kFB / 32; ++w) t += sm.red[w];
-      a.loss_part[tile] = t;
+      loss_part[tile] = t;
     }
+  }
+}
+
+// The points of tile `tile` (kFB * SPT of them, thread t owning points t,
+// t + kFB, ...), their bounding box and their coordinates.
+template <bool NEAR, int SPT>
+__device__ __forceinline__ float4 tile_points(const FieldArgs<float>& a, int64_t tile,
+                                              int64_t (&i)[SPT], bool (&live)[SPT], float (&x)[SPT],
+                                              float (&y)[SPT], FieldSmemF& sm) {
+  const int tid = threadIdx.x;
+  float x0 = __int_as_float(0x7f800000), y0 = x0, x1 = -x0, y1 = -x0;
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    i[k] = tile * (kFB * SPT) + k * kFB + tid;
+    live[k] = i[k] < a.n;
+    x[k] = 0.5f; y[k] = 0.5f;
+    if (live[k]) {
+      x[k] = a.xy[2 * i[k]];
+      y[k] = a.xy[2 * i[k] + 1];
+      x0 = fminf(x0, x[k]); y0 = fminf(y0, y[k]); x1 = fmaxf(x1, x[k]); y1 = fmaxf(y1, y[k]);
+      any = true;
+    }
+  }
+  float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
+  if constexpr (NEAR) bb = block_bbox(x0, y0, x1, y1, any, sm.bred);
+  return bb;
+}
+
+// One tile of kFB * SPT points: handle sums with near-zone culling, the
+// boundary term and the epilogue (colour, residual, the tile's loss partial
+// in loss_part[tile]).  `ys` is the panel slice in split mode.  Every
+// CTA-wide barrier is reached by all threads.
+template <bool SAME, bool NEAR, int SPT>
+__device__ __forceinline__ void field_tile_f32(const FieldArgs<float>& a, int64_t tile, int ys,
+                                               FieldSmemF& sm) {
+  int64_t i[SPT];
+  bool live[SPT];
+  float x[SPT], y[SPT];
+  const float4 bb = tile_points<NEAR, SPT>(a, tile, i, live, x, y, sm);
+  float s[SPT][3];
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) s[k][0] = s[k][1] = s[k][2] = 0.f;
+  const int p0 = a.split_out ? ys * a.pchunk : 0;
+  const int p1 = a.split_out ? min(a.P, p0 + a.pchunk) : a.P;
+  tile_handle_sums<SAME, NEAR, SPT>(a, a.pan, p0, p1, x, y, bb, s, sm);
+  if (a.split_out) {
+#pragma unroll
+    for (int q = 0; q < SPT; ++q)
+      if (live[q]) {
+        double* o = a.split_out + ((size_t)ys * a.n + i[q]) * 3;
+        o[0] = double(s[q][0]);
+        o[1] = double(s[q][1]);
+        o[2] = double(s[q][2]);
+      }
+    return;
+  }
+  float b[1][SPT][3];
+#pragma unroll
+  for (int q = 0; q < SPT; ++q) b[0][q][0] = b[0][q][1] = b[0][q][2] = 0.f;
+  if (a.ub) {
+    const double* const ub[1] = {a.ub};
+    tile_boundary_sums<SPT, 1>(a.vert, a.Nb, ub, x, y, b, sm.sv, sm.su);
+  }
+  tile_finish<SPT>(a, tile, i, live, s, b[0], a.near_add, a.loss_part, sm);
+}
+
+// Several damping trials of one scene on one tile: the points and their
+// boundary angles once, then per trial the handle sums against that
+// trial's panels and the epilogue with that trial's boundary solution,
+// near-field sums and loss partials (j.tloss[t][tile]).
+template <bool SAME, bool NEAR, int SPT, int NT>
+__device__ __forceinline__ void field_tile_trials_f32(const BatchJob& j, int64_t tile,
+                                                      FieldSmemF& sm, float4* su) {
+  const FieldArgs<float>& a = j.a;
+  int64_t i[SPT];
+  bool live[SPT];
+  float x[SPT], y[SPT];
+  const float4 bb = tile_points<NEAR, SPT>(a, tile, i, live, x, y, sm);
+  float b[NT][SPT][3];
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) b[t][q][0] = b[t][q][1] = b[t][q][2] = 0.f;
+  double const* ub[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) ub[t] = j.tub[t];
+  tile_boundary_sums<SPT, NT>(a.vert, a.Nb, ub, x, y, b, sm.sv, su);
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    float s[SPT][3];
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) s[q][0] = s[q][1] = s[q][2] = 0.f;
+    tile_handle_sums<SAME, NEAR, SPT>(a, j.tpan[t], 0, a.P, x, y, bb, s, sm);
+    tile_finish<SPT>(a, tile, i, live, s, b[t], j.tnear[t], j.tloss[t], sm);
   }
 }
 
@@ -346,11 +431,12 @@ constexpr int kSptEval = 2;
 // jobs' first-tile offsets.  Each tile runs the same code as k_field_f32, so
 // with SPT = 1 a scene's colours, residuals and loss partials are those of a
 // single-scene evaluation bit for bit.
-template <bool SAME, bool NEAR, int SPT>
+template <bool SAME, bool NEAR, int SPT, int NT>
 __global__ void __launch_bounds__(kFB) k_field_batch_f32(const BatchJob* __restrict__ jobs, int njobs,
                                                          const int64_t* __restrict__ total_p,
                                                          unsigned long long* __restrict__ counter) {
   __shared__ FieldSmemF sm;
+  __shared__ float4 su_more[NT > 1 ? NT * kFB : 1];   // boundary solutions of NT trials
   __shared__ int64_t item_s;
   const int64_t total = *total_p;
   for (;;) {
@@ -364,7 +450,10 @@ __global__ void __launch_bounds__(kFB) k_field_batch_f32(const BatchJob* __restr
       const int mid = (lo + hi + 1) >> 1;
       if (jobs[mid].tile0 <= item) lo = mid; else hi = mid - 1;
     }
-    field_tile_f32<SAME, NEAR, SPT>(jobs[lo].a, item - jobs[lo].tile0, 0, sm);
+    if constexpr (NT > 1)
+      field_tile_trials_f32<SAME, NEAR, SPT, NT>(jobs[lo], item - jobs[lo].tile0, sm, su_more);
+    else
+      field_tile_f32<SAME, NEAR, SPT>(jobs[lo].a, item - jobs[lo].tile0, 0, sm);
   }
 }
 
@@ -535,21 +624,25 @@ int field_sum_loss(bem_ctx* c, const double* loss_part, int64_t nblk) {
 }
 
 int field_batch_launch(bem_ctx* c, const BatchJob* jobs, int njobs, const int64_t* total_tiles,
-                       unsigned long long* counter, int spt, int blocks_per_sm) {
+                       unsigned long long* counter, int spt, int blocks_per_sm, int nt) {
   int rc;
   if ((rc = cuda_check(c, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), S(c)), "memset")))
     return rc;
   const unsigned grid = (unsigned)std::max(1, c->sms * blocks_per_sm);
   const bool same = c->opts.eps_c == c->opts.eps_d, near = c->opts.near_factor > 0;
-#define BEM_BATCH_LAUNCH(SM_, NR_, SPT_) \
-  k_field_batch_f32<SM_, NR_, SPT_><<<grid, kFB, 0, S(c)>>>(jobs, njobs, total_tiles, counter)
-  if (spt == 2) {
-    if (same) { if (near) BEM_BATCH_LAUNCH(true, true, 2); else BEM_BATCH_LAUNCH(true, false, 2); }
-    else { if (near) BEM_BATCH_LAUNCH(false, true, 2); else BEM_BATCH_LAUNCH(false, false, 2); }
-  } else {
-    if (same) { if (near) BEM_BATCH_LAUNCH(true, true, 1); else BEM_BATCH_LAUNCH(true, false, 1); }
-    else { if (near) BEM_BATCH_LAUNCH(false, true, 1); else BEM_BATCH_LAUNCH(false, false, 1); }
-  }
+#define BEM_BATCH_LAUNCH(SM_, NR_, SPT_, NT_) \
+  k_field_batch_f32<SM_, NR_, SPT_, NT_><<<grid, kFB, 0, S(c)>>>(jobs, njobs, total_tiles, counter)
+#define BEM_BATCH_NT(SPT_, NT_)                                                                 \
+  do {                                                                                          \
+    if (same) { if (near) BEM_BATCH_LAUNCH(true, true, SPT_, NT_); else BEM_BATCH_LAUNCH(true, false, SPT_, NT_); } \
+    else { if (near) BEM_BATCH_LAUNCH(false, true, SPT_, NT_); else BEM_BATCH_LAUNCH(false, false, SPT_, NT_); }   \
+  } while (0)
+  // trial jobs of 2 to kJobTrials trials per scene, or one evaluation per job
+  if (nt == 4) { if (spt == 2) BEM_BATCH_NT(2, 4); else BEM_BATCH_NT(1, 4); }
+  else if (nt == 3) { if (spt == 2) BEM_BATCH_NT(2, 3); else BEM_BATCH_NT(1, 3); }
+  else if (nt == 2) { if (spt == 2) BEM_BATCH_NT(2, 2); else BEM_BATCH_NT(1, 2); }
+  else { if (spt == 2) BEM_BATCH_NT(2, 1); else BEM_BATCH_NT(1, 1); }
+#undef BEM_BATCH_NT
 #undef BEM_BATCH_LAUNCH
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_field_batch_f32");

@@ -47,8 +47,10 @@ namespace {
 constexpr int BM = 128, BN = 128;
 constexpr int STAGES = 3;
 constexpr int TILE_BYTES = BM * 128;        // 16 KB: 128 rows x 128 bytes per operand part
-template <bool X3> struct Scheme {
-  static constexpr int BK = X3 ? 32 : 64;             // elements per 128-byte row
+template <int SCH> struct Scheme {
+  static constexpr bool X3 = SCH != SCH_BF16;
+  static constexpr bool TF32 = SCH == SCH_TF32X3;
+  static constexpr int BK = TF32 ? 32 : 64;           // elements per 128-byte row
   static constexpr int PARTS = X3 ? 4 : 2;            // A(hi, lo), B(hi, lo) / A, B
   static constexpr int SMEM = 1024 + STAGES * PARTS * TILE_BYTES + 256;
 };
@@ -69,8 +71,8 @@ struct TcArgs {
   const float* F;           // EPI_JROWS
   int ldf;
   __nv_bfloat16* J;          // bf16 scheme
-  float* Jhi;                 // 3xtf32 scheme
-  float* Jlo;
+  void* Jhi;                  // split schemes: tf32 parts as fp32, or bf16 parts
+  void* Jlo;
   int ldj;
   int nc, tiles, npairs;    // EPI_SYRK
   int k_per_split;
@@ -88,12 +90,13 @@ struct TcArgs {
   int64_t gstride;
 };
 
-template <bool X3>
-__global__ void __launch_bounds__(128, X3 ? 1 : 2)
+template <int SCH>
+__global__ void __launch_bounds__(128, Scheme<SCH>::X3 ? 1 : 2)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
               const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB2,
               TcArgs g) {
-  constexpr int BK = Scheme<X3>::BK, PARTS = Scheme<X3>::PARTS;
+  constexpr int BK = Scheme<SCH>::BK, PARTS = Scheme<SCH>::PARTS;
+  constexpr bool X3 = Scheme<SCH>::X3, TF = Scheme<SCH>::TF32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // stage s holds parts p = 0..PARTS-1 at smem + (s * PARTS + p) * TILE_BYTES:
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
       umma::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, g.err);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    const uint32_t id = umma::idesc(X3 ? 2 : 1, BM, BN);
+    const uint32_t id = umma::idesc(TF ? 2 : 1, BM, BN);
     for (int it = 0; it < nk; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
@@ -194,9 +197,15 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
         if (X3) {
           const uint64_t dal = umma::sdesc_sw128(a0 + 2 * TILE_BYTES + kk * 32);
           const uint64_t dbl = umma::sdesc_sw128(b0 + 2 * TILE_BYTES + kk * 32);
-          umma::mma_tf32(tmem, dal, db, id, (it | kk) != 0);   // lo . hi
-          umma::mma_tf32(tmem, da, dbl, id, 1);                 // hi . lo
-          umma::mma_tf32(tmem, da, db, id, 1);                  // hi . hi
+          if (TF) {
+            umma::mma_tf32(tmem, dal, db, id, (it | kk) != 0);   // lo . hi
+            umma::mma_tf32(tmem, da, dbl, id, 1);                 // hi . lo
+            umma::mma_tf32(tmem, da, db, id, 1);                  // hi . hi
+          } else {
+            umma::mma_bf16(tmem, dal, db, id, (it | kk) != 0);
+            umma::mma_bf16(tmem, da, dbl, id, 1);
+            umma::mma_bf16(tmem, da, db, id, 1);
+          }
         } else {
           umma::mma_bf16(tmem, da, db, id, (it | kk) != 0);
         }
@@ -255,14 +264,19 @@ __global__ void __launch_bounds__(128, X3 ? 1 : 2)
       const int row = arow + r;
       if (row < g.M) {
         const float* f = g.F + (size_t)row * g.ldf + brow + cb;
-        float* oh = g.Jhi + (size_t)row * g.ldj + brow + cb;
-        float* ol = g.Jlo + (size_t)row * g.ldj + brow + cb;
+        const size_t o = (size_t)row * g.ldj + brow + cb;
         for (int j = 0; j < 32; ++j)
           if (brow + cb + j < g.N) {
             const float x = v[j] + f[j];
-            const float hi = tf32_rna(x);
-            oh[j] = hi;
-            ol[j] = tf32_rna(x - hi);
+            if (TF) {
+              const float hi = tf32_rna(x);
+              ((float*)g.Jhi)[o + j] = hi;
+              ((float*)g.Jlo)[o + j] = tf32_rna(x - hi);
+            } else {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+              ((__nv_bfloat16*)g.Jhi)[o + j] = hi;
+              ((__nv_bfloat16*)g.Jlo)[o + j] = __float2bfloat16_rn(x - __bfloat162float(hi));
+            }
           }
       }
     } else if (g.mode == EPI_JROWS) {
@@ -361,7 +375,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __global__ void __launch_bounds__(kPersThreads, 1)
     k_tc_jrows_pers(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
                     TcArgs g) {
-  constexpr int BK = Scheme<false>::BK;
+  constexpr int BK = Scheme<SCH_BF16>::BK;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* fs = reinterpret_cast<float*>(smem + PSTAGES * kPersStage);        // [BM][BN] F rows
@@ -673,7 +687,7 @@ constexpr int kSySmem = 1024 + SY_STAGES * kSyStage + 256;
 // K slice.  g.tiles = T channel-order tiles.
 __global__ void __launch_bounds__(128, 1)
     k_tc_syrk_pair(const __grid_constant__ CUtensorMap tJ, TcArgs g) {
-  constexpr int BK = Scheme<false>::BK;
+  constexpr int BK = Scheme<SCH_BF16>::BK;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + SY_STAGES * kSyStage);
@@ -829,17 +843,17 @@ int make_map(bem_ctx* c, CUtensorMap* m, const void* base, uint64_t k, uint64_t 
   return BEM_OK;
 }
 
-template <bool X3>
+template <int SCH>
 int launch(bem_ctx* c, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& a2,
            const CUtensorMap& b2, const TcArgs& g, dim3 grid) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Scheme<X3>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Scheme<SCH>::SMEM);
     if (e != cudaSuccess) return cuda_check(c, e, "tc gemm smem attribute");
     attr = true;
   }
-  k_tc_gemm<X3><<<grid, 128, Scheme<X3>::SMEM, S(c)>>>(a, b, a2, b2, g);
+  k_tc_gemm<SCH><<<grid, 128, Scheme<SCH>::SMEM, S(c)>>>(a, b, a2, b2, g);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_tc_gemm");
 }
@@ -856,24 +870,25 @@ int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const
   TcArgs g{};
   g.M = M; g.N = N; g.K = K; g.mode = EPI_STORE; g.D = D; g.ldd = ldd; g.err = c->d_status;
   g.wait_ns = c->wait_ns;
-  return launch<false>(c, ta, tb, ta, tb, g, dim3((M + BM - 1) / BM, (N + BN - 1) / BN));
+  return launch<SCH_BF16>(c, ta, tb, ta, tb, g, dim3((M + BM - 1) / BM, (N + BN - 1) / BN));
 }
 
 // J^T rows: J[rows][m] = Mt[rows][Nb] Phi[m][Nb]^T + F[rows][m].
 //   bf16:   Mt, Phi bf16; J bf16 (Jout[0]); with gpart, also the handle part
 //           of the gradient per 128-sample tile (see TcArgs)
 //   3xtf32: Mt = (Mt[0] hi, Mt[1] lo), Phi likewise, fp32; J hi/lo fp32 (Jout[0], Jout[1])
-int tc_jrows(bem_ctx* c, bool x3, const JLayout& L, int m, int Nb, const void* const* Mt, int ldm,
+int tc_jrows(bem_ctx* c, int sch, const JLayout& L, int m, int Nb, const void* const* Mt, int ldm,
              const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj,
              const float* resid, int nc, double* gpart, int64_t gstride) {
   const int rows = L.rows();
+  const bool x3 = sch != SCH_BF16, f32 = sch == SCH_TF32X3;
   int rc;
   CUtensorMap ta, tb, ta2, tb2;
-  if ((rc = make_map(c, &ta, Mt[0], Nb, rows, ldm, x3)) ||
-      (rc = make_map(c, &tb, Phi[0], Nb, m, ldp, x3)))
+  if ((rc = make_map(c, &ta, Mt[0], Nb, rows, ldm, f32)) ||
+      (rc = make_map(c, &tb, Phi[0], Nb, m, ldp, f32)))
     return rc;
-  if (x3 && ((rc = make_map(c, &ta2, Mt[1], Nb, rows, ldm, true)) ||
-             (rc = make_map(c, &tb2, Phi[1], Nb, m, ldp, true))))
+  if (x3 && ((rc = make_map(c, &ta2, Mt[1], Nb, rows, ldm, f32)) ||
+             (rc = make_map(c, &tb2, Phi[1], Nb, m, ldp, f32))))
     return rc;
   if ((ldf % 4) || ((uintptr_t)F & 15)) return fail(c, BEM_EINVAL, "F rows not 16-byte aligned");
   TcArgs g{};
@@ -881,7 +896,7 @@ int tc_jrows(bem_ctx* c, bool x3, const JLayout& L, int m, int Nb, const void* c
   g.err = c->d_status;
   g.wait_ns = c->wait_ns;
   g.L = L;
-  if (x3) { g.Jhi = (float*)Jout[0]; g.Jlo = (float*)Jout[1]; }
+  if (x3) { g.Jhi = Jout[0]; g.Jlo = Jout[1]; }
   else g.J = (__nv_bfloat16*)Jout[0];
   if (!x3 && gpart) {
     g.resid = resid;
@@ -905,7 +920,8 @@ int tc_jrows(bem_ctx* c, bool x3, const JLayout& L, int m, int Nb, const void* c
     return cuda_check(c, cudaGetLastError(), "k_tc_jrows_pers");
   }
   dim3 grid((rows + BM - 1) / BM, (m + BN - 1) / BN);
-  return launch<true>(c, ta, tb, ta2, tb2, g, grid);
+  if (f32) return launch<SCH_TF32X3>(c, ta, tb, ta2, tb2, g, grid);
+  return launch<SCH_BF16X3>(c, ta, tb, ta2, tb2, g, grid);
 }
 
 // CTAs of one K slice of the Gram kernels: bf16 paired units, 3xtf32 single
@@ -920,17 +936,18 @@ static int gram_ctas(const JLayout& L, bool x3) {
 // part[split][ch][cdim][cdim] += upper blocks of J_ch^T J_ch (channel order,
 // JLayout) over the m samples of J, K split into `splits` slices.
 // bf16: J[0] bf16.  3xtf32: J[0] hi, J[1] lo, fp32.
-int tc_syrk(bem_ctx* c, bool x3, const JLayout& L, int m, const void* const* J, int ldj,
+int tc_syrk(bem_ctx* c, int sch, const JLayout& L, int m, const void* const* J, int ldj,
             float* part, int splits) {
   int rc;
+  const bool x3 = sch != SCH_BF16, f32 = sch == SCH_TF32X3;
   CUtensorMap tj, tj2;
-  if ((rc = make_map(c, &tj, J[0], m, L.rows(), ldj, x3))) return rc;
-  if (x3 && (rc = make_map(c, &tj2, J[1], m, L.rows(), ldj, true))) return rc;
+  if ((rc = make_map(c, &tj, J[0], m, L.rows(), ldj, f32))) return rc;
+  if (x3 && (rc = make_map(c, &tj2, J[1], m, L.rows(), ldj, f32))) return rc;
   TcArgs g{};
   g.M = g.N = L.cdim(); g.K = m; g.mode = EPI_SYRK; g.nc = L.cdim(); g.L = L;
   g.tiles = L.tiles();
   g.npairs = g.tiles * (g.tiles + 1) / 2;
-  const int bk = x3 ? Scheme<true>::BK : Scheme<false>::BK;
+  const int bk = f32 ? Scheme<SCH_TF32X3>::BK : Scheme<SCH_BF16>::BK;
   g.k_per_split = ((m + splits - 1) / splits + bk - 1) / bk * bk;
   g.part = part; g.err = c->d_status;
   g.wait_ns = c->wait_ns;
@@ -950,7 +967,8 @@ int tc_syrk(bem_ctx* c, bool x3, const JLayout& L, int m, const void* const* J, 
     return cuda_check(c, cudaGetLastError(), "k_tc_syrk_pair");
   }
   dim3 grid(gram_ctas(L, true), sp);
-  return launch<true>(c, tj, tj, tj2, tj2, g, grid);
+  if (f32) return launch<SCH_TF32X3>(c, tj, tj, tj2, tj2, g, grid);
+  return launch<SCH_BF16X3>(c, tj, tj, tj2, tj2, g, grid);
 }
 
 // K slices per block pair: as many as fill the resident CTA slots in one

@@ -238,11 +238,29 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
+// One operand value in the scheme's format at element o: bf16; or the high
+// part rounded to tf32 (fp32 storage) or bf16 and the low part the rounded
+// rest, x = hi + lo
+template <int SCH>
+__device__ __forceinline__ void put_operand(void* p0, void* p1, size_t o, float x) {
+  if constexpr (SCH == SCH_TF32X3) {
+    const float h = tf32_round(x);
+    ((float*)p0)[o] = h;
+    ((float*)p1)[o] = tf32_round(x - h);
+  } else if constexpr (SCH == SCH_BF16X3) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    ((__nv_bfloat16*)p0)[o] = h;
+    ((__nv_bfloat16*)p1)[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+  } else {
+    ((__nv_bfloat16*)p0)[o] = __float2bfloat16_rn(x);
+  }
+}
+
 // Phi rows of a chunk of samples written from the segment side: thread j
 // (boundary segment) walks the block's sample slice, writes phi_j(x_s)/(2 pi)
-// into row s (bf16, or tf32 hi/lo) and, when residuals are given, sums
+// into row s (in the scheme's operand format) and, when residuals are given, sums
 // q_j += phi_j(x_s)/(2 pi) r_s into a per-slice double partial qpart[slice][j][3].
-template <bool X3>
+template <int SCH>
 __global__ void __launch_bounds__(128) k_phi_q(const float* __restrict__ xy, const float* __restrict__ r,
                                                int m, int slice_len, const float* __restrict__ vert,
                                                int Nb, void* __restrict__ phi0,
@@ -271,14 +289,7 @@ __global__ void __launch_bounds__(128) k_phi_q(const float* __restrict__ xy, con
     for (int k = 0; k < cnt; ++k) {
       const float4 p = sxr[k];
       const float phi = seg_angle(ax, ay, bx, by, p.x, p.y) * float(kInv2Pi);
-      const size_t o = (size_t)(base + k) * Nb + j;
-      if (X3) {
-        const float h = tf32_round(phi);
-        ((float*)phi0)[o] = h;
-        ((float*)phi1)[o] = tf32_round(phi - h);
-      } else {
-        ((__nv_bfloat16*)phi0)[o] = __float2bfloat16_rn(phi);
-      }
+      put_operand<SCH>(phi0, phi1, (size_t)(base + k) * Nb + j, phi);
       if (r) { a0 = fmaf(phi, p.z, a0); a1 = fmaf(phi, p.w, a1); a2 = fmaf(phi, sr2[k], a2); }
     }
     q0 += a0; q1 += a1; q2 += a2;
@@ -588,10 +599,10 @@ static int jtj_t(bem_ctx* c, int64_t n, const T* xy, double* Hout) {
 //   Mt[row][j] = M_c[j][col] = sum_i W[j][i] Df_c[i][col]
 // for the channel and column of each J^T row (jrow_col; padding rows 0), in
 // fp32 (W = A^+ as float, Df converted on load), 64 x 64 tiles of 4 x 4
-// outputs per thread, written as bf16 or as the tf32 hi/lo pair.  The result
-// is rounded to bf16 / tf32 at once, so fp32 accumulation loses nothing the
-// J rows keep.
-template <bool X3>
+// outputs per thread, written in the scheme's operand format.  The result is
+// rounded to bf16 / tf32 (or split into two such parts) at once, so fp32
+// accumulation loses nothing the J rows keep.
+template <int SCH>
 __global__ void __launch_bounds__(256) k_mt_sgemm(const float* __restrict__ W,
                                                   const double* __restrict__ Df, int Nb, int nc,
                                                   JLayout L, void* __restrict__ out0,
@@ -642,14 +653,7 @@ __global__ void __launch_bounds__(256) k_mt_sgemm(const float* __restrict__ W,
     for (int q = 0; q < 4; ++q) {
       const int j = j0 + tx * 4 + q;
       if (j >= Nb) continue;
-      const size_t o = (size_t)r * Nb + j;
-      if (X3) {
-        const float hi = tf32_round(acc[p][q]);
-        ((float*)out0)[o] = hi;
-        ((float*)out1)[o] = tf32_round(acc[p][q] - hi);
-      } else {
-        ((__nv_bfloat16*)out0)[o] = __float2bfloat16_rn(acc[p][q]);
-      }
+      put_operand<SCH>(out0, out1, (size_t)r * Nb + j, acc[p][q]);
     }
   }
 }
@@ -726,7 +730,7 @@ bool jtj_fuses_eval(const bem_ctx* c) {
   return jtj_gives_gradient(c) && c->sc.P > 6 * c->sc.NH;
 }
 
-static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
+static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
                   const float* resid, double* gout, const float* target) {
   int rc;
   int C = c->sc.C, nc = c->sc.nc, Nb = c->bd.Nb, nth = c->sc.nth;
@@ -740,20 +744,26 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
   // J^T rows: the position columns per channel, the jump columns once (JLayout)
   const JLayout L = jlayout(c->sc.pp, c->sc.NH);
   const int rows = L.rows();
-  const size_t es = x3 ? 2 * sizeof(float) : sizeof(__nv_bfloat16);   // bytes per element (all parts)
+  const bool x3 = sch != SCH_BF16;                  // split operands, three products
+  const size_t pb = sch == SCH_TF32X3 ? 4 : 2;      // bytes per element of one part
+  const size_t es = (x3 ? 2 : 1) * pb;              // bytes per element (all parts)
   // M^T in the J-row layout, [rows][Nb]
-  const size_t mt_part = (x3 ? 4 : 2) * (size_t)rows * Nb;
+  const size_t mt_part = pb * (size_t)rows * Nb;
   if ((rc = grow(c, c->tcMt, es * (size_t)rows * Nb))) return rc;
   const void* Mt[2] = {c->tcMt.p, (char*)c->tcMt.p + mt_part};
   {
     ProfScope _pm(c, "k_mt_sgemm");
     dim3 grid((Nb + 63) / 64, (rows + 63) / 64);
-    if (x3)
-      k_mt_sgemm<true><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, (const double*)c->Dfc.p, Nb, nc, L,
-                                               (void*)Mt[0], (void*)Mt[1]);
+    const double* Df = (const double*)c->Dfc.p;
+    if (sch == SCH_TF32X3)
+      k_mt_sgemm<SCH_TF32X3><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, Df, Nb, nc, L, (void*)Mt[0],
+                                                     (void*)Mt[1]);
+    else if (sch == SCH_BF16X3)
+      k_mt_sgemm<SCH_BF16X3><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, Df, Nb, nc, L, (void*)Mt[0],
+                                                     (void*)Mt[1]);
     else
-      k_mt_sgemm<false><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, (const double*)c->Dfc.p, Nb, nc, L,
-                                                (void*)Mt[0], nullptr);
+      k_mt_sgemm<SCH_BF16><<<grid, 256, 0, S(c)>>>(c->bd.d_W32, Df, Nb, nc, L, (void*)Mt[0],
+                                                   nullptr);
     BEM_LAUNCHED(c);
   }
   // per-chunk buffers: Phi [m][Nb], F^T f32 [rows][ld], J^T [rows][ld]
@@ -761,10 +771,10 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
                                           c->opts.gn_chunk > 0 ? c->opts.gn_chunk : 262144);
   const int nchunks = (int)((n + chunk - 1) / chunk);
   const int ld = (int)((chunk + 63) / 64 * 64);
-  const size_t phi_part = (x3 ? 4 : 2) * (size_t)chunk * Nb;
+  const size_t phi_part = pb * (size_t)chunk * Nb;
   const size_t phi_b = (x3 ? 2 : 1) * phi_part;
   const size_t f_b = sizeof(float) * (size_t)rows * ld;
-  const size_t j_part = (x3 ? 4 : 2) * (size_t)rows * ld;
+  const size_t j_part = pb * (size_t)rows * ld;
   const size_t j_b = (x3 ? 2 : 1) * j_part;
   // gradient work: per chunk handle partial [3nc], q partials per slice
   // sample slices of the Phi-row pass: 1,024 samples each, up to 256 (a
@@ -852,12 +862,15 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
       const float* rr = want_g ? resid + 3 * s0 : nullptr;
       if (want_g && (int)grid.y < qslices)      // unused slices of a short chunk hold zeros
         cudaMemsetAsync(q, 0, sizeof(double) * qslices * Nb * 3, S(c));
-      if (x3)
-        k_phi_q<true><<<grid, 128, 0, S(c)>>>(xy + 2 * s0, rr, m, len, c->bd.d_vert32, Nb,
-                                              (void*)phi[0], (void*)phi[1], q);
+      if (sch == SCH_TF32X3)
+        k_phi_q<SCH_TF32X3><<<grid, 128, 0, S(c)>>>(xy + 2 * s0, rr, m, len, c->bd.d_vert32, Nb,
+                                                    (void*)phi[0], (void*)phi[1], q);
+      else if (sch == SCH_BF16X3)
+        k_phi_q<SCH_BF16X3><<<grid, 128, 0, S(c)>>>(xy + 2 * s0, rr, m, len, c->bd.d_vert32, Nb,
+                                                    (void*)phi[0], (void*)phi[1], q);
       else
-        k_phi_q<false><<<grid, 128, 0, S(c)>>>(xy + 2 * s0, rr, m, len, c->bd.d_vert32, Nb,
-                                               (void*)phi[0], nullptr, q);
+        k_phi_q<SCH_BF16><<<grid, 128, 0, S(c)>>>(xy + 2 * s0, rr, m, len, c->bd.d_vert32, Nb,
+                                                  (void*)phi[0], nullptr, q);
       BEM_LAUNCHED(c);
     }
     if (want_g && !fused_g) {
@@ -866,13 +879,13 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, bool x3,
           F, ld, L, nc, m, resid + 3 * s0, gh + (size_t)ci * kGemvSegs * 3 * nc);
       BEM_LAUNCHED(c);
     }
-    if ((rc = tc_jrows(c, x3, L, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld,
+    if ((rc = tc_jrows(c, sch, L, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld,
                        fused_g ? resid + 3 * s0 : nullptr, nc,
                        fused_g ? gh + tile_col : nullptr, tiles_all)))
       return rc;
     tile_col += (m + 127) / 128;
     const void* Jc[2] = {J[0], J[1]};
-    if ((rc = tc_syrk(c, x3, L, m, Jc, ld, part, splits))) return rc;
+    if ((rc = tc_syrk(c, sch, L, m, Jc, ld, part, splits))) return rc;
   }
   if (fuse_r && (rc = field_sum_loss(c, lossp, lblk))) return rc;
   k_syrk_reduce<<<dim3((nc + 127) / 128, nc, 3), 128, 0, S(c)>>>(part, splits, nc, L,
@@ -915,15 +928,20 @@ int jtj_build(bem_ctx* c, int64_t n, const void* xy, double* H, const void* resi
     return fail(c, BEM_EINVAL, "jtj: residual formed in the pass only in the tensor-core modes");
   if (c->opts.precision == BEM_FP64) return jtj_t<double>(c, n, (const double*)xy, H);
   if (c->opts.jtj_mode == BEM_JTJ_BF16)
-    return jtj_tc(c, n, (const float*)xy, H, false, (const float*)resid, g, (const float*)target);
+    return jtj_tc(c, n, (const float*)xy, H, SCH_BF16, (const float*)resid, g, (const float*)target);
   if (c->opts.jtj_mode == BEM_JTJ_3XTF32)
-    return jtj_tc(c, n, (const float*)xy, H, true, (const float*)resid, g, (const float*)target);
+    return jtj_tc(c, n, (const float*)xy, H, SCH_TF32X3, (const float*)resid, g,
+                  (const float*)target);
+  if (c->opts.jtj_mode == BEM_JTJ_BF16X3)
+    return jtj_tc(c, n, (const float*)xy, H, SCH_BF16X3, (const float*)resid, g,
+                  (const float*)target);
   return jtj_t<float>(c, n, (const float*)xy, H);
 }
 
 bool jtj_gives_gradient(const bem_ctx* c) {
   return c->opts.precision == BEM_MIXED &&
-         (c->opts.jtj_mode == BEM_JTJ_BF16 || c->opts.jtj_mode == BEM_JTJ_3XTF32);
+         (c->opts.jtj_mode == BEM_JTJ_BF16 || c->opts.jtj_mode == BEM_JTJ_3XTF32 ||
+          c->opts.jtj_mode == BEM_JTJ_BF16X3);
 }
 
 }  // namespace bem

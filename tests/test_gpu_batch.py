@@ -54,7 +54,10 @@ def _t(a):
     return torch.tensor(np.ascontiguousarray(a), device="cuda:0")
 
 
-def test_batch_matches_single_scene_steps(scenes):
+# 4 and 2 trials: one job per scene evaluates all of them on each tile
+# (sharing the boundary angles); 5 trials: one job per (scene, trial)
+@pytest.mark.parametrize("lams", [LAMBDAS, [1e-2, 1e-1], [1e-3, 3e-3, 1e-2, 1e-1, 1.0]])
+def test_batch_matches_single_scene_steps(scenes, lams):
     bg = _bg()
     single = _contexts(scenes)
     batched = _contexts(scenes)
@@ -63,9 +66,9 @@ def test_batch_matches_single_scene_steps(scenes):
     ts = [_t(tg) for _, _, tg, _ in scenes]
     for it in range(2):
         before = [m.get_params() for m in single]
-        rb = b.lm_step(xs, ts, LAMBDAS)
+        rb = b.lm_step(xs, ts, lams)
         for s, m in enumerate(single):
-            r = m.lm_step(xs[s], ts[s], LAMBDAS)
+            r = m.lm_step(xs[s], ts[s], lams)
             assert rb[s]["loss_before"] == pytest.approx(r["loss_before"], rel=1e-6)
             assert rb[s]["accepted"] == r["accepted"]
             assert rb[s]["best_trial"] == r["best_trial"]

@@ -329,12 +329,15 @@ def test_vjp_mixed(cfg1):
 # H on 2,048 samples.  Rounding J to bf16 (8 mantissa bits) perturbs each
 # product of H by about 2^-8 relative with a random sign, so the relative
 # error of the sum falls with the number of samples: measured 1.06e-3 here
-# (1.7e-4 on 32,691 samples, test_gn_products_across_chunks); 3xtf32 1.0e-6,
-# fp64 J^T J of float J rows 7e-7.  The bounds are five times those.
-@pytest.mark.parametrize("mode,tol", [("bf16", 5e-3), ("3xtf32", 5e-6), ("fp64", 4e-6)])
+# (1.7e-4 on 32,691 samples, test_gn_products_across_chunks); compensated
+# bf16 4.8e-6, 3xtf32 1.0e-6 to 1.4e-6, fp64 J^T J of float J rows 7e-7.  The
+# bounds are about five times those.
+@pytest.mark.parametrize("mode,tol", [("bf16", 5e-3), ("3xtf32", 5e-6), ("bf16x3", 2.5e-5),
+                                      ("fp64", 4e-6)])
 def test_jtj_mixed(cfg1, mode, tol):
     bg = _bg()
-    jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32, "fp64": bg.BEM_JTJ_FP64}[mode]
+    jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32, "bf16x3": bg.BEM_JTJ_BF16X3,
+          "fp64": bg.BEM_JTJ_FP64}[mode]
     sc, xy, target, mean, o = cfg1
     sub = xy[::16]
     m = _ctx(sc, mean, bg.BEM_MIXED, jtj_mode=jm)
@@ -343,12 +346,12 @@ def test_jtj_mixed(cfg1, mode, tol):
     assert np.linalg.norm(H - want) / np.linalg.norm(want) < tol
 
 
-@pytest.mark.parametrize("mode", ["bf16", "3xtf32"])
+@pytest.mark.parametrize("mode", ["bf16", "3xtf32", "bf16x3"])
 def test_lm_step_mixed(cfg1, mode):
     """One mixed LM step: the loss it reports at the new theta matches the
     oracle's loss there, and the step lowers the loss like the FP64 step."""
     bg = _bg()
-    jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32}[mode]
+    jm = {"bf16": bg.BEM_JTJ_BF16, "3xtf32": bg.BEM_JTJ_3XTF32, "bf16x3": bg.BEM_JTJ_BF16X3}[mode]
     sc, xy, target, mean, o = cfg1
     sub, tsub = xy[::8], target[::8]
     m = _ctx(sc, mean, bg.BEM_MIXED, jtj_mode=jm)
@@ -361,9 +364,11 @@ def test_lm_step_mixed(cfg1, mode):
     # gradient of the step (from the same J rows as H) against the oracle's
     assert res["grad_norm"] == pytest.approx(np.linalg.norm(want["g"]), rel=1e-4)
     assert res["accepted"] == want["accepted"]
-    # the step's loss moves with the error of H: measured about 5e-4 (bf16)
-    # and 5e-7 (3xtf32) relative on 2,048 samples at lambda = 1e-3
-    assert res["loss_after"] == pytest.approx(want["loss_after"], rel=5e-3 if mode == "bf16" else 5e-6)
+    # the step's loss moves with the error of H: measured about 5e-4 (bf16),
+    # 1.6e-5 (compensated bf16) and 5e-7 to 1.2e-6 (3xtf32) relative on 4,096
+    # samples at lambda = 1e-3
+    assert res["loss_after"] == pytest.approx(want["loss_after"],
+                                              rel={"bf16": 5e-3, "3xtf32": 6e-6, "bf16x3": 8e-5}[mode])
 
 
 @pytest.mark.parametrize("nf", [0.0, 0.5, 1000.0])
@@ -396,11 +401,13 @@ def test_lm_step_residual_from_jrow_pass(cfg1, mode, nf):
 
 N_CHUNKED = 32768 - 77
 GN_TOL = {  # (loss rel, g rel 2-norm, H rel Frobenius); measured on 32,691
-    # samples: loss 3.5e-7, g 2.1e-6 (mixed), H 1.5e-7 (fp64 J^T J), 1.2e-6
-    # (3xtf32), 1.7e-4 (bf16); the bounds are about five times those
+    # samples: loss 3.5e-7, g 2.1e-6 (mixed), H 1.5e-7 (fp64 J^T J), 1.2e-6 to
+    # 2.3e-6 (3xtf32), 3.6e-6 (compensated bf16), 1.7e-4 (bf16); the bounds
+    # are about five times those
     "fp64": (1e-12, 1e-10, 1e-10),
     "fp64_jtj": (2e-6, 1e-5, 1e-6),
-    "3xtf32": (2e-6, 1e-5, 6e-6),
+    "3xtf32": (2e-6, 1e-5, 1.2e-5),
+    "bf16x3": (2e-6, 1e-5, 2e-5),
     "bf16": (2e-6, 1e-5, 8e-4),
 }
 
@@ -416,11 +423,12 @@ def _gn_ctx(sc, mean, mode, chunk):
     bg = _bg()
     if mode == "fp64":
         return _ctx(sc, mean, bg.BEM_FP64, gn_chunk=chunk), torch.float64
-    jm = {"fp64_jtj": bg.BEM_JTJ_FP64, "3xtf32": bg.BEM_JTJ_3XTF32, "bf16": bg.BEM_JTJ_BF16}[mode]
+    jm = {"fp64_jtj": bg.BEM_JTJ_FP64, "3xtf32": bg.BEM_JTJ_3XTF32, "bf16": bg.BEM_JTJ_BF16,
+          "bf16x3": bg.BEM_JTJ_BF16X3}[mode]
     return _ctx(sc, mean, bg.BEM_MIXED, jtj_mode=jm, gn_chunk=chunk), torch.float32
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp64_jtj", "3xtf32", "bf16"])
+@pytest.mark.parametrize("mode", ["fp64", "fp64_jtj", "3xtf32", "bf16x3", "bf16"])
 def test_gn_products_across_chunks(cfg1, cfg1_gn, mode):
     sc, xy, target, mean, o = cfg1
     x, t, (L, g, H) = cfg1_gn
