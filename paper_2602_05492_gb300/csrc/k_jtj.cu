@@ -542,7 +542,7 @@ static void launch_frows(bem_ctx* c, const T* xy, int ns, void* F, int ldf = 0,
 template <typename T>
 static int jtj_t(bem_ctx* c, int64_t n, const T* xy, double* Hout) {
   int rc;
-  int C = c->sc.C, nc = c->sc.nc, Nb = c->bd.Nb, nth = c->sc.nth;
+  int nc = c->sc.nc, Nb = c->bd.Nb, nth = c->sc.nth;
   // stacked right-hand sides: F at the boundary Gauss points -> Df -> M_c = A^+ Df_c
   int n3 = 3 * Nb;
   if ((rc = grow(c, c->Fg, sizeof(double) * 3 * (size_t)n3 * nc))) return rc;
@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(256) k_mt_sgemm(const float* __restrict__ W,
 template <typename T>
 static int jtj_stacked_rhs(bem_ctx* c, bool solve = true) {
   int rc;
-  int C = c->sc.C, nc = c->sc.nc, Nb = c->bd.Nb, n3 = 3 * Nb;
+  int nc = c->sc.nc, Nb = c->bd.Nb, n3 = 3 * Nb;
   if ((rc = grow(c, c->Fg, sizeof(double) * 3 * (size_t)n3 * nc))) return rc;
   if ((rc = grow(c, c->Dfc, sizeof(double) * 3 * (size_t)Nb * nc))) return rc;
   if ((rc = grow(c, c->Mc, sizeof(double) * 3 * (size_t)Nb * nc))) return rc;
@@ -811,10 +811,19 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
   double* lossp = nullptr;
   int64_t lblk = 0;
   if (fuse_r) {
-    if ((rc = grow(c, c->nearF, sizeof(double) * 3 * (size_t)chunk))) return rc;
+    // the near-field correction of every sample in one launch before the
+    // chunks (one launch balances the uneven near pairs across the SMs);
+    // each chunk then adds its F-row shares into its slice
+    if ((rc = grow(c, c->nearF, sizeof(double) * 3 * (size_t)n))) return rc;
     if ((rc = grow(c, c->loss, sizeof(double) * (size_t)(field_blocks(n) + nchunks + 1)))) return rc;
     hand = (double*)c->nearF.p;
     lossp = (double*)c->loss.p;
+    if (c->opts.near_factor > 0) {
+      if ((rc = near_forward_minus_float(c, n, xy, hand))) return rc;
+    } else if ((rc = cuda_check(c, cudaMemsetAsync(hand, 0, sizeof(double) * 3 * (size_t)n, S(c)),
+                                "memset"))) {
+      return rc;
+    }
   }
   if ((rc = cuda_check(c, cudaMemsetAsync(part, 0, part_b, S(c)), "memset"))) return rc;
   if ((rc = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), S(c)), "memset"))) return rc;
@@ -837,18 +846,13 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
     const int m = (int)std::min<int64_t>(chunk, n - s0);
     launch_frows<float, true>(c, xy + 2 * s0, m, F, ld, hw, ld);
     if (fuse_r) {
-      if (c->opts.near_factor > 0) {
-        if ((rc = near_forward_minus_float(c, m, xy + 2 * s0, hand))) return rc;
-      } else if ((rc = cuda_check(c, cudaMemsetAsync(hand, 0, sizeof(double) * 3 * (size_t)m, S(c)),
-                                  "memset"))) {
-        return rc;
-      }
+      double* hs = hand + 3 * s0;
       {
         ProfScope _ph(c, "k_hand_sum");
-        k_hand_sum<<<(m + 255) / 256, 256, 0, S(c)>>>(hw, ld, C, m, hand);
+        k_hand_sum<<<(m + 255) / 256, 256, 0, S(c)>>>(hw, ld, C, m, hs);
         BEM_LAUNCHED(c);
       }
-      if ((rc = field_finish_hand(c, m, xy + 2 * s0, hand, target + 3 * s0,
+      if ((rc = field_finish_hand(c, m, xy + 2 * s0, hs, target + 3 * s0,
                                   const_cast<float*>(resid) + 3 * s0, lossp + lblk)))
         return rc;
       lblk += field_blocks(m);
