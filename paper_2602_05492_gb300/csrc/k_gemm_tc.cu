@@ -348,15 +348,16 @@ __global__ void __launch_bounds__(128, Scheme<SCH>::X3 ? 1 : 2)
 // accumulators, and warps 2..9 drain the other in two passes of 128 columns:
 // warp w owns TMEM lanes 32 (w % 4) .. +31 and the columns 64 ((w - 2) / 4)
 // .. +63 of the pass.  The epilogue of a tile (F rows added, bf16 packing,
-// the handle part of the gradient, coalesced stores) overlaps the MMAs of
-// the next.  One 256-sample tile per MMA halves the operand bytes per output
-// of the A slabs against 128-sample tiles, the share of the L2 traffic that
-// bounds this contraction.  Per pass the F rows are copied by cp.async into
-// fs (the first pass's once the previous tile's rows are stored); row r holds
-// 32 chunks of 16 bytes, logical chunk c at position c ^ (r & 7).  The bf16
-// result is written back in place: output chunk o of column half h goes to
-// position (16 h + o) ^ (r & 7), which held an F chunk of the same half that
-// has already been read, so the two warps of a row never overlap.
+// the handle part of the gradient) overlaps the MMAs of the next.  One
+// 256-sample tile per MMA halves the operand bytes per output of the A slabs
+// against 128-sample tiles, the share of the L2 traffic that bounds this
+// contraction.  The epilogue moves its data with TMA as well: one thread
+// loads a pass's F rows as four 128-row x 32-column boxes (128-byte
+// swizzle: row r at 128 r bytes, 16-byte chunk c at position c ^ (r & 7))
+// and its residuals by one bulk copy, and stores the pass's J^T rows as two
+// 64-column bf16 boxes in the same swizzle.  The bf16 rows of column half h
+// are packed in place over F box 2 h, which only that half's warps read,
+// and each thread reads its row of both of its boxes before it writes there.
 constexpr int PSTAGES = 3;
 constexpr int kPersBN = 256;                          // samples per tile
 constexpr int kPersPass = kPersBN / BN;               // epilogue passes of BN columns
@@ -374,18 +375,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __global__ void __launch_bounds__(kPersThreads, 1)
     k_tc_jrows_pers(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+                    const __grid_constant__ CUtensorMap tF, const __grid_constant__ CUtensorMap tJ,
                     TcArgs g) {
   constexpr int BK = Scheme<SCH_BF16>::BK;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* fs = reinterpret_cast<float*>(smem + PSTAGES * kPersStage);        // [BM][BN] F rows
-  float* rs = fs + BM * BN;                                                  // [BN][3] residuals
+  float* fs = reinterpret_cast<float*>(smem + PSTAGES * kPersStage);  // 4 boxes [BM][32] F rows
+  float* rs = fs + BM * BN;                                            // [BN][3] residuals
   float* gsum = rs + 3 * BN;                                                 // [3][2][BM]
   uint64_t* full = reinterpret_cast<uint64_t*>(gsum + 6 * BM);
   uint64_t* empty = full + PSTAGES;
   uint64_t* tfull = empty + PSTAGES;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* fbar = tempty + 2;                              // F rows of a pass landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fbar + 1);
   int* fail_flag = reinterpret_cast<int*>(tmem_slot + 1);   // set when an epilogue wait gave up
   int* stop_flag = fail_flag + 1;                           // set when the MMA warp gave up
 
@@ -404,6 +407,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       umma::mbar_init(&tfull[b], 1);
       umma::mbar_init(&tempty[b], 8);
     }
+    umma::mbar_init(fbar, 1);
     umma::fence_barrier_init();
   }
   if (warp == 0) umma::tmem_alloc(tmem_slot, 2 * kPersBN);
@@ -476,148 +480,145 @@ __global__ void __launch_bounds__(kPersThreads, 1)
     const int et = threadIdx.x - 64;                 // 0 .. 255
     const int q = warp & 3, half = (warp - 2) >> 2;  // TMEM lane quarter, column half
     const int r = 32 * q + lane;                     // tile row of this thread
-    // F rows and residuals of pass p of tile t (columns col0 .. col0 + BN - 1)
-    auto stage = [&](int t, int p) {
+    const int sw = r & 7;
+    // thread et == 0: the F rows (four TMA boxes of 32 columns) and the
+    // residuals of pass p of tile t into fs / rs, completion on fbar
+    auto load_pass = [&](int t, int p) {
       const int arow = (t % rtiles) * BM, col0 = (t / rtiles) * kPersBN + p * BN;
-      for (int e = et; e < BM * (BN / 4); e += 256) {
-        const int rr = e / (BN / 4), cc = e % (BN / 4);
-        const int row = arow + rr, col = col0 + cc * 4;
-        float* d = fs + rr * BN + ((cc ^ (rr & 7)) << 2);
-        if (row < g.M && col + 3 < g.N) {
-          umma::cp_async16(d, g.F + (size_t)row * g.ldf + col);
-        } else {
-          const float* src = g.F + (size_t)row * g.ldf + col;
-          d[0] = (row < g.M && col < g.N) ? src[0] : 0.f;
-          d[1] = (row < g.M && col + 1 < g.N) ? src[1] : 0.f;
-          d[2] = (row < g.M && col + 2 < g.N) ? src[2] : 0.f;
-          d[3] = 0.f;
-        }
-      }
-      if (g.gpart)
-        for (int e = et; e < 3 * BN; e += 256) {
+      const bool rbulk = g.gpart && col0 + BN <= g.N;
+      if (g.gpart && !rbulk)   // the chunk's ragged end: zeros past it
+        for (int e = 0; e < 3 * BN; ++e) {
           const int col = col0 + e / 3;
           rs[e] = col < g.N ? g.resid[3 * (size_t)col + e % 3] : 0.f;
         }
+      umma::mbar_expect_tx(fbar, BM * BN * 4 + (rbulk ? 3 * BN * 4 : 0));
+      if (rbulk) umma::bulk_load(rs, g.resid + 3 * (size_t)col0, 3 * BN * 4, fbar);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) umma::tma_load_2d(fs + j * (BM * 32), &tF, fbar, col0 + 32 * j, arow);
     };
-    if (blockIdx.x < ntiles) stage(blockIdx.x, 0);
-    int i = 0;
+    // pass k of this CTA: tile blockIdx.x + (k / passes) gridDim.x, pass k % passes
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int npass = my_tiles * kPersPass;
+    if (et == 0 && npass > 0) load_pass(blockIdx.x, 0);
+    int issued = npass > 0 ? 1 : 0;   // F loads issued (thread et == 0)
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
-      const int b = i & 1;
+    int k = 0;
+    for (; k < npass && ok; ++k) {
+      const int t = (int)blockIdx.x + (k / kPersPass) * (int)gridDim.x, p = k % kPersPass;
+      const int i = k / kPersPass, b = i & 1;
       const int arow = (t % rtiles) * BM, ct = t / rtiles;
-      // (the guard limit: MMAs of this buffer may still be in flight)
-      if (!umma::mbar_wait(&tfull[b], (i >> 1) & 1, g.err)) atomicOr(fail_flag, 1);
-      umma::fence_after();
-      if (*(volatile int*)stop_flag) atomicOr(fail_flag, 1);
-      for (int p = 0; p < kPersPass; ++p) {
-        const int col0 = ct * kPersBN + p * BN;
-        // fs holds pass 0's rows already (staged after the previous tile's stores)
-        if (p > 0) stage(t, p);
-        umma::cp_async_wait_all();
-        bar_epi();
-        ok = *(volatile int*)fail_flag == 0;   // the same for all epilogue threads
-        // gradient rows: a position row sums against its channel's
-        // residual; a jump row (the whole tile, since the jump range starts
-        // on a tile) against all three
-        const bool jump = arow >= 3 * g.L.Pp;
-        int gch = 0;
-        if (g.gpart && !jump) gch = (arow + r) / g.L.Pp;
-        float gacc = 0.f, gacc1 = 0.f, gacc2 = 0.f;
-        const float* fr = fs + r * BN;
-        const int sw = r & 7;
-#pragma unroll 1
-        for (int cb = 64 * half; cb < 64 * half + 64; cb += 32) {
-          float v[32];
-          umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kPersBN + p * BN + cb), v);
-          if (!ok) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = 0.f;
-          }
-          float f[32];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float4 w4 = *reinterpret_cast<const float4*>(fr + ((((cb >> 2) + k) ^ sw) << 2));
-            f[4 * k] = w4.x; f[4 * k + 1] = w4.y; f[4 * k + 2] = w4.z; f[4 * k + 3] = w4.w;
-          }
-          if (g.gpart && !jump) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rs[3 * (cb + j) + gch], gacc);
-          } else if (g.gpart) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              gacc = fmaf(f[j], rs[3 * (cb + j)], gacc);
-              gacc1 = fmaf(f[j], rs[3 * (cb + j) + 1], gacc1);
-              gacc2 = fmaf(f[j], rs[3 * (cb + j) + 2], gacc2);
-            }
-          }
-          // output chunks of this 32-column block: o = ((cb - 64 half) >> 3) + k
-          uint8_t* jr = reinterpret_cast<uint8_t*>(fs + r * BN);
-          const int o0 = 16 * half + ((cb - 64 * half) >> 3);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            uint4 w;
-            uint32_t* wp = &w.x;
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * k + 2 * h] + f[8 * k + 2 * h],
-                                                              v[8 * k + 2 * h + 1] + f[8 * k + 2 * h + 1]);
-              wp[h] = *reinterpret_cast<const uint32_t*>(&b2);
-            }
-            *reinterpret_cast<uint4*>(jr + (((o0 + k) ^ sw) << 4)) = w;
-          }
-        }
-        gsum[half * BM + r] = gacc;
-        gsum[(2 + half) * BM + r] = gacc1;
-        gsum[(4 + half) * BM + r] = gacc2;
-        if (p == kPersPass - 1 || !ok) {
-          // this warp's TMEM reads of the tile are complete (or given up, and
-          // the loop ends after this pass): release the buffer
-          umma::fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&tempty[b]);
-        }
-        bar_epi();
-        // the gradient partial of each 128-sample column block (a block past
-        // the chunk's end holds nothing and is not written)
-        if (g.gpart && et < BM && arow + et < g.M && col0 < g.N) {
-          const int row = arow + et;
-          const int64_t cb = kPersPass * ct + p;
-          if (!jump) {
-            const int c0 = row / g.L.Pp, col = row - c0 * g.L.Pp;
-            if (col < g.L.npos)
-              g.gpart[((size_t)c0 * g.gnc + col) * g.gstride + cb] = (double)(gsum[et] + gsum[BM + et]);
-          } else {
-            const int w = row - 3 * g.L.Pp;
-            if (w < 2 * g.L.nh)
-              for (int k = 0; k < 3; ++k)
-                g.gpart[((size_t)k * g.gnc + g.L.npos + w) * g.gstride + cb] =
-                    (double)(gsum[2 * k * BM + et] + gsum[(2 * k + 1) * BM + et]);
-          }
-        }
-        // bf16 rows: one warp writes a 256-byte row per step, 8 bytes per lane
-        for (int rr = warp - 2; rr < BM; rr += 8) {
-          const int row = arow + rr;
-          if (row >= g.M) continue;
-          const int col = col0 + lane * 4;
-          const int oc = lane >> 1;                      // output chunk 0..15 of the row
-          const int pos = (oc < 8 ? oc : oc + 8) ^ (rr & 7);
-          const uint8_t* src = reinterpret_cast<const uint8_t*>(fs + rr * BN) + ((pos << 4) | ((lane & 1) << 3));
-          __nv_bfloat16* dst = g.J + (size_t)row * g.ldj + col;
-          if (col + 3 < g.N) {
-            *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
-          } else {
-            const __nv_bfloat16* sb = reinterpret_cast<const __nv_bfloat16*>(src);
-            for (int u = 0; u < 4; ++u)
-              if (col + u < g.N) dst[u] = sb[u];
-          }
-        }
-        bar_epi();
-        if (!ok) break;
+      const int col0 = ct * kPersBN + p * BN;
+      if (p == 0) {
+        // (the guard limit: MMAs of this buffer may still be in flight)
+        if (!umma::mbar_wait(&tfull[b], (i >> 1) & 1, g.err)) atomicOr(fail_flag, 1);
+        umma::fence_after();
+        if (*(volatile int*)stop_flag) atomicOr(fail_flag, 1);
       }
-      // fs now free: the next tile's first F rows come in while its MMAs run
-      if (ok && t + (int)gridDim.x < ntiles) stage(t + gridDim.x, 0);
+      // (guard limit: the copies of this pass are in flight)
+      if (!umma::mbar_wait(fbar, k & 1, g.err)) atomicOr(fail_flag, 1);
+      bar_epi();   // also: the last pass's gradient reads of gsum are done
+      ok = *(volatile int*)fail_flag == 0;   // the same for all epilogue threads
+      // gradient rows: a position row sums against its channel's
+      // residual; a jump row (the whole tile, since the jump range starts
+      // on a tile) against all three
+      const bool jump = arow >= 3 * g.L.Pp;
+      int gch = 0;
+      if (g.gpart && !jump) gch = (arow + r) / g.L.Pp;
+      float gacc = 0.f, gacc1 = 0.f, gacc2 = 0.f;
+      // the output box of this half (columns 64 half .. +63 of the pass, bf16)
+      // goes over F box 2 half, whose rows this half has read first
+      uint8_t* ob = reinterpret_cast<uint8_t*>(fs + 2 * half * (BM * 32)) + r * 128;
+#pragma unroll 1
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int cb = 64 * half + 32 * s2;          // columns of this block within the pass
+        float v[32];
+        umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kPersBN + p * BN + cb), v);
+        if (!ok) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        }
+        const uint8_t* fr = reinterpret_cast<const uint8_t*>(fs + (cb >> 5) * (BM * 32)) + r * 128;
+        float f[32];
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+          const float4 w4 = *reinterpret_cast<const float4*>(fr + ((c8 ^ sw) << 4));
+          f[4 * c8] = w4.x; f[4 * c8 + 1] = w4.y; f[4 * c8 + 2] = w4.z; f[4 * c8 + 3] = w4.w;
+        }
+        if (g.gpart && !jump) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rs[3 * (cb + j) + gch], gacc);
+        } else if (g.gpart) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            gacc = fmaf(f[j], rs[3 * (cb + j)], gacc);
+            gacc1 = fmaf(f[j], rs[3 * (cb + j) + 1], gacc1);
+            gacc2 = fmaf(f[j], rs[3 * (cb + j) + 2], gacc2);
+          }
+        }
+        // output chunks 4 s2 .. 4 s2 + 3 of the row (8 bf16 each)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          uint4 w;
+          uint32_t* wp = &w.x;
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * kk + 2 * h] + f[8 * kk + 2 * h],
+                                                            v[8 * kk + 2 * h + 1] + f[8 * kk + 2 * h + 1]);
+            wp[h] = *reinterpret_cast<const uint32_t*>(&b2);
+          }
+          *reinterpret_cast<uint4*>(ob + (((4 * s2 + kk) ^ sw) << 4)) = w;
+        }
+      }
+      if (p == kPersPass - 1 || !ok) {
+        // this warp's TMEM reads of the tile are complete (or given up, and
+        // the loop ends after this pass): release the buffer
+        umma::fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+      }
+      gsum[half * BM + r] = gacc;
+      gsum[(2 + half) * BM + r] = gacc1;
+      gsum[(4 + half) * BM + r] = gacc2;
+      umma::fence_proxy_async();   // the bf16 rows, for the TMA stores
+      bar_epi();
+      if (et == 0) {
+        // J^T rows of the pass (two 64-column boxes; rows and columns past
+        // the matrix are not written), then the next pass's F rows once the
+        // stores have read fs
+        umma::tma_store_2d(&tJ, fs, col0, arow);
+        umma::tma_store_2d(&tJ, fs + 2 * (BM * 32), col0 + 64, arow);
+        umma::bulk_commit();
+        umma::bulk_wait_read0();
+        if (ok && k + 1 < npass) {
+          const int k1 = k + 1;
+          load_pass((int)blockIdx.x + (k1 / kPersPass) * (int)gridDim.x, k1 % kPersPass);
+          ++issued;
+        }
+      }
+      // the gradient partial of this 128-sample column block (a block past
+      // the chunk's end holds nothing and is not written)
+      if (g.gpart && et < BM && arow + et < g.M && col0 < g.N) {
+        const int row = arow + et;
+        const int64_t cbk = kPersPass * ct + p;
+        if (!jump) {
+          const int c0 = row / g.L.Pp, col = row - c0 * g.L.Pp;
+          if (col < g.L.npos)
+            g.gpart[((size_t)c0 * g.gnc + col) * g.gstride + cbk] = (double)(gsum[et] + gsum[BM + et]);
+        } else {
+          const int w = row - 3 * g.L.Pp;
+          if (w < 2 * g.L.nh)
+            for (int c3 = 0; c3 < 3; ++c3)
+              g.gpart[((size_t)c3 * g.gnc + g.L.npos + w) * g.gstride + cbk] =
+                  (double)(gsum[2 * c3 * BM + et] + gsum[(2 * c3 + 1) * BM + et]);
+        }
+      }
     }
-    umma::cp_async_wait_all();
+    if (et == 0) {
+      // a load issued for a pass the loop did not reach lands before the CTA
+      // leaves (guard limit), and the stores complete
+      if (issued > k) umma::mbar_wait(fbar, (issued - 1) & 1, g.err);
+      umma::bulk_wait0();
+    }
   }
   __syncwarp();
   umma::fence_before();
@@ -906,6 +907,11 @@ int tc_jrows(bem_ctx* c, int sch, const JLayout& L, int m, int Nb, const void* c
   }
   ProfScope _ps(c, "tc_jrows");
   if (!x3) {
+    // the epilogue's TMA views: F^T (fp32) and J^T (bf16), m columns x rows
+    CUtensorMap tf, tj;
+    if ((rc = make_map(c, &tf, F, m, rows, ldf, true)) ||
+        (rc = make_map(c, &tj, Jout[0], m, rows, ldj, false)))
+      return rc;
     static bool attr = false;
     if (!attr) {
       cudaError_t e = cudaFuncSetAttribute(k_tc_jrows_pers, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -915,7 +921,7 @@ int tc_jrows(bem_ctx* c, int sch, const JLayout& L, int m, int Nb, const void* c
     }
     const int ntiles = ((rows + BM - 1) / BM) * ((m + kPersBN - 1) / kPersBN);
     const int grid = std::max(1, std::min(ntiles, c->sms));
-    k_tc_jrows_pers<<<grid, kPersThreads, kPersSmem, S(c)>>>(ta, tb, g);
+    k_tc_jrows_pers<<<grid, kPersThreads, kPersSmem, S(c)>>>(ta, tb, tf, tj, g);
     BEM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "k_tc_jrows_pers");
   }
