@@ -318,6 +318,14 @@ int bem_gemm_bf16(bem_ctx *ctx, int M, int N, int K, const void *A, int lda, con
 int bem_fastmath_eval(bem_ctx *ctx, int which, int64_t n, const float *a, const float *b,
                       float *out_fast, float *out_ref, void *stream);
 
+/* The double logarithm of the FP64 near field (a table-driven reduction,
+ * Tang 1990), next to CUDA's log, for validation (no counterpart in the
+ * paper): out_lib[i] = the library's log(x[i]), out_ref[i] = CUDA's log(x[i]).
+ * x: device double [n], positive, normal and finite; out_lib, out_ref:
+ * device double [n].  Errors: BEM_EINVAL for bad arguments. */
+int bem_dlog_eval(bem_ctx *ctx, int64_t n, const double *x, double *out_lib, double *out_ref,
+                  void *stream);
+
 /* The pairing of the bf16 Gram kernel, exposed for validation (host only, no
  * context, no GPU).  The upper 128 x 128 blocks (i <= j) of a channel's Gram
  * matrix in its J-row order, tiles block rows, are computed in units of two

@@ -92,6 +92,7 @@ def _load():
         "bem_profile_enable": (ci, [vp, ci]),
         "bem_gemm_bf16": (ci, [vp, ci, ci, ci, vp, ci, vp, ci, vp, ci, vp]),
         "bem_fastmath_eval": (ci, [vp, ci, i64, vp, vp, vp, vp, vp]),
+        "bem_dlog_eval": (ci, [vp, i64, vp, vp, vp, vp]),
         "bem_vjp_noalloc": (ci, [vp, i64, vp, vp, vp, vp]),
         "bem_profile_read": (ci, [vp, ci, ctypes.c_char_p, dp, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ci)]),
@@ -121,7 +122,7 @@ EXPORTED = [
     "bem_set_params", "bem_get_params", "bem_set_mean_color", "bem_sample_mean", "bem_eval",
     "bem_loss", "bem_vjp", "bem_jtj", "lm_step", "bem_sizes", "bem_boundary_values",
     "bem_launch_count", "bem_profile_enable", "bem_profile_read", "bem_gemm_bf16",
-    "bem_fastmath_eval", "bem_vjp_noalloc", "bem_batch_create", "bem_batch_destroy",
+    "bem_fastmath_eval", "bem_dlog_eval", "bem_vjp_noalloc", "bem_batch_create", "bem_batch_destroy",
     "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors", "lm_step_split",
     "bem_set_boundary", "bem_setup_segments", "bem_set_regularizers", "bem_prune",
     "bem_init_segments", "bem_gram_unit", "bem_alloc_count", "bem_set_wait_limit",
@@ -432,6 +433,17 @@ class BEM:
                                            _ptr(b) if b is not None else None, _ptr(fast),
                                            _ptr(ref), _stream(stream)))
         return fast, ref
+
+    def dlog(self, x, stream=None):
+        """(library, CUDA) double logarithm of the positive double CUDA tensor x
+        (bem_dlog_eval)."""
+        import torch
+        assert x.dtype == torch.float64 and x.is_cuda
+        own = torch.empty_like(x)
+        ref = torch.empty_like(x)
+        self._check(_lib.bem_dlog_eval(self.h, x.numel(), _ptr(x), _ptr(own), _ptr(ref),
+                                       _stream(stream)))
+        return own, ref
 
     def profile(self, on: bool = True):
         self._check(_lib.bem_profile_enable(self.h, 1 if on else 0))

@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "ctx.h"
+#include "dmath.cuh"
 
 namespace bem {
 
@@ -219,6 +220,46 @@ static int build_bins(bem_ctx* c, DevBuf& buf, bool panels, int64_t n, const flo
 // ---------------------------------------------------------------------------
 // double evaluation of the near pairs
 
+// (ic_j, lc_j) of dlog, per device
+__device__ double2 g_dlog_tab[kDlogTab];
+
+__global__ void k_dlog_init() {
+  const int j = threadIdx.x;
+  if (j < kDlogTab) {
+    const double ic = 1.0 / (1.0 + (j + 0.5) / kDlogTab);
+    g_dlog_tab[j] = make_double2(ic, -log(ic));
+  }
+}
+
+// The layer values of a near pair in double: the integrals of layer_values,
+// with log(q2/q1) taken as the difference of two logarithms (dlog) instead of
+// log1p of a quotient, and 1/h' from one reciprocal square root.  For a near
+// pair q1 and q2 are of the scale of a few squared panel lengths, so the
+// difference keeps an absolute accuracy of a few units of 2^-53 times
+// |log q|, far below what the float far field carries.
+template <bool SAME>
+__device__ __forceinline__ LayerVals<double> layer_values_near(const Frame<double>& f, double ec2,
+                                                              double ed2) {
+  LayerVals<double> v;
+  const double hh = f.h * f.h;
+  const double hc2 = hh + ec2;
+  const double rc = rsqrt(hc2);
+  const double hc = hc2 * rc;
+  const double tt = f.t1 * f.t2;
+  const double q1 = fma(f.t1, f.t1, hc2), q2 = fma(f.t2, f.t2, hc2);
+  const double phic = atan2(hc * f.L, hc2 + tt);
+  const double lg1 = dlog(q1, g_dlog_tab), lg2 = dlog(q2, g_dlog_tab);
+  v.S = -(f.L * (lg2 - 2.0) + f.t1 * (lg2 - lg1) + 2.0 * hc * phic) * kInv4Pi;
+  if constexpr (SAME) {
+    v.Dl = -(f.h * rc) * phic * kInv2Pi;
+  } else {
+    const double hd2 = hh + ed2;
+    const double rd = rsqrt(hd2);
+    v.Dl = -(f.h * rd) * atan2(hd2 * rd * f.L, hd2 + tt) * kInv2Pi;
+  }
+  return v;
+}
+
 // SUBF: the sum of (double - float) pair values instead, the float value
 // being the one the F rows hold (frame_rn, layer_grad_hat); added to the
 // float handle term F w it gives the same near-field treatment as the
@@ -238,7 +279,7 @@ __global__ void k_near_forward(const float* __restrict__ xy, int64_t n,
     if (!near_pair(pan32[p], x, y, near2)) continue;
     const Panel<double>& q = pan64[p];
     Frame<double> f = frame(q, double(x), double(y));
-    LayerVals<double> v = layer_values(f, ec2, ed2, SAME);
+    const LayerVals<double> v = layer_values_near<SAME>(f, ec2, ed2);
     s0 += -q.wd[0] * v.Dl + q.wc[0] * v.S;
     s1 += -q.wd[1] * v.Dl + q.wc[1] * v.S;
     s2 += -q.wd[2] * v.Dl + q.wc[2] * v.S;
@@ -361,6 +402,11 @@ static int near_forward_t(bem_ctx* c, int64_t n, const float* xy, double* out, b
     b.items = (int*)((char*)c->nearP.p + sizeof(int) * ((size_t)ncell + 1 + ncell + nb + 1));
   }
 
+  if (!c->dlog_ready) {
+    k_dlog_init<<<1, kDlogTab, 0, S(c)>>>();
+    BEM_LAUNCHED(c);
+    c->dlog_ready = true;
+  }
   const float near2 = (float)(c->opts.near_factor * c->opts.near_factor);
   const double ec2 = c->opts.eps_c * c->opts.eps_c, ed2 = c->opts.eps_d * c->opts.eps_d;
   ProfScope _ps(c, "k_near_forward");
@@ -401,4 +447,34 @@ int near_adjoint(bem_ctx* c, int64_t n, const float* xy, const float* w, double*
   return cuda_check(c, cudaGetLastError(), "near adjoint");
 }
 
+__global__ void k_dlog_eval(int64_t n, const double* __restrict__ x, double* __restrict__ own,
+                            double* __restrict__ ref) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    own[i] = dlog(x[i], g_dlog_tab);
+    ref[i] = log(x[i]);
+  }
+}
+
 }  // namespace bem
+
+extern "C" int bem_dlog_eval(bem_ctx* c, int64_t n, const double* x, double* out_lib,
+                             double* out_ref, void* stream) {
+  using namespace bem;
+  if (!c) return BEM_EINVAL;
+  if (n < 0 || (n > 0 && (!x || !out_lib || !out_ref)))
+    return fail(c, BEM_EINVAL, "bem_dlog_eval: bad arguments");
+  int rc;
+  if ((rc = ctx_set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  if (!c->dlog_ready) {
+    k_dlog_init<<<1, kDlogTab, 0, S(c)>>>();
+    BEM_LAUNCHED(c);
+    c->dlog_ready = true;
+  }
+  if (n > 0) {
+    k_dlog_eval<<<(unsigned)((n + 255) / 256), 256, 0, S(c)>>>(n, x, out_lib, out_ref);
+    BEM_LAUNCHED(c);
+  }
+  return cuda_check(c, cudaGetLastError(), "k_dlog_eval");
+}
