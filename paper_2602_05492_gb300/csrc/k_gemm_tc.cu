@@ -82,7 +82,7 @@ struct TcArgs {
   JLayout L;                // J^T row layout (EPI_JROWS gradient, EPI_SYRK tiles)
   // bf16 J rows (k_tc_jrows_pers) with residuals: for each J^T row and each
   // channel c whose column col it holds (JLayout), gpart[(c gnc + col) *
-  // gstride + column block] = sum over the block's samples s of F[row][s]
+  // gstride + 64-sample block] = sum over the block's samples s of F[row][s]
   // resid[s][c]
   const float* resid;
   int gnc;
@@ -363,11 +363,14 @@ constexpr int kPersBN = 256;                          // samples per tile
 constexpr int kPersPass = kPersBN / BN;               // epilogue passes of BN columns
 constexpr int kPersStage = TILE_BYTES * (1 + kPersPass);   // A slab + B slab (48 KB)
 constexpr int kPersThreads = 320;           // 2 control warps + 8 epilogue warps
-constexpr int kPersSmem = 1024 + PSTAGES * kPersStage + BM * BN * 4 + 3 * BN * 4 + 6 * BM * 4 +
-                          256;
+constexpr int kPersSmem = 1024 + PSTAGES * kPersStage + BM * BN * 4 + 3 * BN * 4 + 256;
 static_assert(kPersSmem <= 227 * 1024, "persistent J-row kernel exceeds shared memory");
 
-__device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// the named barrier of epilogue half h (its four warps)
+__device__ __forceinline__ void bar_half(int h) {
+  if (h) asm volatile("bar.sync 3, 128;" ::: "memory");
+  else asm volatile("bar.sync 2, 128;" ::: "memory");
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(bar)) : "memory");
@@ -382,15 +385,15 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* fs = reinterpret_cast<float*>(smem + PSTAGES * kPersStage);  // 4 boxes [BM][32] F rows
   float* rs = fs + BM * BN;                                            // [BN][3] residuals
-  float* gsum = rs + 3 * BN;                                                 // [3][2][BM]
-  uint64_t* full = reinterpret_cast<uint64_t*>(gsum + 6 * BM);
+  uint64_t* full = reinterpret_cast<uint64_t*>(rs + 3 * BN);
   uint64_t* empty = full + PSTAGES;
   uint64_t* tfull = empty + PSTAGES;
   uint64_t* tempty = tfull + 2;
-  uint64_t* fbar = tempty + 2;                              // F rows of a pass landed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fbar + 1);
+  uint64_t* fbar = tempty + 2;                              // [2] a half's F rows landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fbar + 2);
   int* fail_flag = reinterpret_cast<int*>(tmem_slot + 1);   // set when an epilogue wait gave up
   int* stop_flag = fail_flag + 1;                           // set when the MMA warp gave up
+  int* half_ok = stop_flag + 1;                             // [2] a half's view of fail_flag
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rtiles = (g.M + BM - 1) / BM, ctiles = (g.N + kPersBN - 1) / kPersBN;
@@ -407,7 +410,8 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       umma::mbar_init(&tfull[b], 1);
       umma::mbar_init(&tempty[b], 8);
     }
-    umma::mbar_init(fbar, 1);
+    umma::mbar_init(&fbar[0], 1);
+    umma::mbar_init(&fbar[1], 1);
     umma::fence_barrier_init();
   }
   if (warp == 0) umma::tmem_alloc(tmem_slot, 2 * kPersBN);
@@ -476,38 +480,45 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       }
     }
   } else {
-    // epilogue, 256 threads
+    // epilogue, 256 threads in two halves of four warps; half h owns the
+    // columns 64 h .. 64 h + 63 of every pass (F boxes 2 h and 2 h + 1, the
+    // J^T box over F box 2 h) and runs its own pipeline: its leader thread
+    // loads and stores its boxes, its warps sync on their own named barrier,
+    // and each thread writes the gradient partial of its row and 64 columns
     const int et = threadIdx.x - 64;                 // 0 .. 255
     const int q = warp & 3, half = (warp - 2) >> 2;  // TMEM lane quarter, column half
     const int r = 32 * q + lane;                     // tile row of this thread
     const int sw = r & 7;
-    // thread et == 0: the F rows (four TMA boxes of 32 columns) and the
-    // residuals of pass p of tile t into fs / rs, completion on fbar
-    auto load_pass = [&](int t, int p) {
-      const int arow = (t % rtiles) * BM, col0 = (t / rtiles) * kPersBN + p * BN;
-      const bool rbulk = g.gpart && col0 + BN <= g.N;
+    const bool leader = (et & 127) == 0;
+    float* rh = rs + half * (3 * 64);                // residuals of the half's 64 columns
+    float* fb = fs + 2 * half * (BM * 32);           // the half's two F boxes
+    uint64_t* fh = fbar + half;
+    // leader: the half's F rows (two TMA boxes) and residuals of pass p of tile t
+    auto load_half = [&](int t, int p) {
+      const int arow = (t % rtiles) * BM, c0 = (t / rtiles) * kPersBN + p * BN + 64 * half;
+      const bool rbulk = g.gpart && c0 + 64 <= g.N;
       if (g.gpart && !rbulk)   // the chunk's ragged end: zeros past it
-        for (int e = 0; e < 3 * BN; ++e) {
-          const int col = col0 + e / 3;
-          rs[e] = col < g.N ? g.resid[3 * (size_t)col + e % 3] : 0.f;
+        for (int e = 0; e < 3 * 64; ++e) {
+          const int col = c0 + e / 3;
+          rh[e] = col < g.N ? g.resid[3 * (size_t)col + e % 3] : 0.f;
         }
-      umma::mbar_expect_tx(fbar, BM * BN * 4 + (rbulk ? 3 * BN * 4 : 0));
-      if (rbulk) umma::bulk_load(rs, g.resid + 3 * (size_t)col0, 3 * BN * 4, fbar);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) umma::tma_load_2d(fs + j * (BM * 32), &tF, fbar, col0 + 32 * j, arow);
+      umma::mbar_expect_tx(fh, 2 * BM * 32 * 4 + (rbulk ? 3 * 64 * 4 : 0));
+      if (rbulk) umma::bulk_load(rh, g.resid + 3 * (size_t)c0, 3 * 64 * 4, fh);
+      umma::tma_load_2d(fb, &tF, fh, c0, arow);
+      umma::tma_load_2d(fb + BM * 32, &tF, fh, c0 + 32, arow);
     };
     // pass k of this CTA: tile blockIdx.x + (k / passes) gridDim.x, pass k % passes
     const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int npass = my_tiles * kPersPass;
-    if (et == 0 && npass > 0) load_pass(blockIdx.x, 0);
-    int issued = npass > 0 ? 1 : 0;   // F loads issued (thread et == 0)
+    if (leader && npass > 0) load_half(blockIdx.x, 0);
+    int issued = npass > 0 ? 1 : 0;   // loads issued (leader)
     bool ok = true;
     int k = 0;
     for (; k < npass && ok; ++k) {
       const int t = (int)blockIdx.x + (k / kPersPass) * (int)gridDim.x, p = k % kPersPass;
       const int i = k / kPersPass, b = i & 1;
       const int arow = (t % rtiles) * BM, ct = t / rtiles;
-      const int col0 = ct * kPersBN + p * BN;
+      const int c0 = ct * kPersBN + p * BN + 64 * half;
       if (p == 0) {
         // (the guard limit: MMAs of this buffer may still be in flight)
         if (!umma::mbar_wait(&tfull[b], (i >> 1) & 1, g.err)) atomicOr(fail_flag, 1);
@@ -515,9 +526,10 @@ __global__ void __launch_bounds__(kPersThreads, 1)
         if (*(volatile int*)stop_flag) atomicOr(fail_flag, 1);
       }
       // (guard limit: the copies of this pass are in flight)
-      if (!umma::mbar_wait(fbar, k & 1, g.err)) atomicOr(fail_flag, 1);
-      bar_epi();   // also: the last pass's gradient reads of gsum are done
-      ok = *(volatile int*)fail_flag == 0;   // the same for all epilogue threads
+      if (!umma::mbar_wait(fh, k & 1, g.err)) atomicOr(fail_flag, 1);
+      if (leader) half_ok[half] = *(volatile int*)fail_flag == 0;
+      bar_half(half);
+      ok = half_ok[half] != 0;   // one value for the whole half
       // gradient rows: a position row sums against its channel's
       // residual; a jump row (the whole tile, since the jump range starts
       // on a tile) against all three
@@ -525,34 +537,36 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       int gch = 0;
       if (g.gpart && !jump) gch = (arow + r) / g.L.Pp;
       float gacc = 0.f, gacc1 = 0.f, gacc2 = 0.f;
-      // the output box of this half (columns 64 half .. +63 of the pass, bf16)
-      // goes over F box 2 half, whose rows this half has read first
-      uint8_t* ob = reinterpret_cast<uint8_t*>(fs + 2 * half * (BM * 32)) + r * 128;
+      // the half's bf16 rows go over its F box 2 h, after this thread has
+      // read its row of both boxes
+      uint8_t* ob = reinterpret_cast<uint8_t*>(fb) + r * 128;
 #pragma unroll 1
       for (int s2 = 0; s2 < 2; ++s2) {
-        const int cb = 64 * half + 32 * s2;          // columns of this block within the pass
         float v[32];
-        umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kPersBN + p * BN + cb), v);
+        umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) +
+                            (uint32_t)(b * kPersBN + p * BN + 64 * half + 32 * s2),
+                        v);
         if (!ok) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = 0.f;
         }
-        const uint8_t* fr = reinterpret_cast<const uint8_t*>(fs + (cb >> 5) * (BM * 32)) + r * 128;
+        const uint8_t* fr = reinterpret_cast<const uint8_t*>(fb + s2 * (BM * 32)) + r * 128;
         float f[32];
 #pragma unroll
         for (int c8 = 0; c8 < 8; ++c8) {
           const float4 w4 = *reinterpret_cast<const float4*>(fr + ((c8 ^ sw) << 4));
           f[4 * c8] = w4.x; f[4 * c8 + 1] = w4.y; f[4 * c8 + 2] = w4.z; f[4 * c8 + 3] = w4.w;
         }
+        const float* rr = rh + 3 * 32 * s2;
         if (g.gpart && !jump) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rs[3 * (cb + j) + gch], gacc);
+          for (int j = 0; j < 32; ++j) gacc = fmaf(f[j], rr[3 * j + gch], gacc);
         } else if (g.gpart) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            gacc = fmaf(f[j], rs[3 * (cb + j)], gacc);
-            gacc1 = fmaf(f[j], rs[3 * (cb + j) + 1], gacc1);
-            gacc2 = fmaf(f[j], rs[3 * (cb + j) + 2], gacc2);
+            gacc = fmaf(f[j], rr[3 * j], gacc);
+            gacc1 = fmaf(f[j], rr[3 * j + 1], gacc1);
+            gacc2 = fmaf(f[j], rr[3 * j + 2], gacc2);
           }
         }
         // output chunks 4 s2 .. 4 s2 + 3 of the row (8 bf16 each)
@@ -576,47 +590,44 @@ __global__ void __launch_bounds__(kPersThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
       }
-      gsum[half * BM + r] = gacc;
-      gsum[(2 + half) * BM + r] = gacc1;
-      gsum[(4 + half) * BM + r] = gacc2;
-      umma::fence_proxy_async();   // the bf16 rows, for the TMA stores
-      bar_epi();
-      if (et == 0) {
-        // J^T rows of the pass (two 64-column boxes; rows and columns past
-        // the matrix are not written), then the next pass's F rows once the
-        // stores have read fs
-        umma::tma_store_2d(&tJ, fs, col0, arow);
-        umma::tma_store_2d(&tJ, fs + 2 * (BM * 32), col0 + 64, arow);
+      // the gradient partial of the row over the half's 64 samples, 64-sample
+      // block 2 (128-sample block) + half (a block past the chunk's end holds
+      // nothing and is not written)
+      if (g.gpart && ok && arow + r < g.M && c0 < g.N) {
+        const int row = arow + r;
+        const int64_t blk = 2 * (kPersPass * ct + p) + half;
+        if (!jump) {
+          const int ch = row / g.L.Pp, col = row - ch * g.L.Pp;
+          if (col < g.L.npos) g.gpart[((size_t)ch * g.gnc + col) * g.gstride + blk] = (double)gacc;
+        } else {
+          const int w = row - 3 * g.L.Pp;
+          if (w < 2 * g.L.nh) {
+            const size_t o = (size_t)(g.L.npos + w) * g.gstride + blk;
+            g.gpart[o] = (double)gacc;
+            g.gpart[(size_t)g.gnc * g.gstride + o] = (double)gacc1;
+            g.gpart[2 * (size_t)g.gnc * g.gstride + o] = (double)gacc2;
+          }
+        }
+      }
+      umma::fence_proxy_async();   // the bf16 rows, for the TMA store
+      bar_half(half);
+      if (leader) {
+        // the half's J^T rows (rows and columns past the matrix are not
+        // written), then its next F rows once the store has read fb
+        umma::tma_store_2d(&tJ, fb, c0, arow);
         umma::bulk_commit();
         umma::bulk_wait_read0();
         if (ok && k + 1 < npass) {
           const int k1 = k + 1;
-          load_pass((int)blockIdx.x + (k1 / kPersPass) * (int)gridDim.x, k1 % kPersPass);
+          load_half((int)blockIdx.x + (k1 / kPersPass) * (int)gridDim.x, k1 % kPersPass);
           ++issued;
         }
       }
-      // the gradient partial of this 128-sample column block (a block past
-      // the chunk's end holds nothing and is not written)
-      if (g.gpart && et < BM && arow + et < g.M && col0 < g.N) {
-        const int row = arow + et;
-        const int64_t cbk = kPersPass * ct + p;
-        if (!jump) {
-          const int c0 = row / g.L.Pp, col = row - c0 * g.L.Pp;
-          if (col < g.L.npos)
-            g.gpart[((size_t)c0 * g.gnc + col) * g.gstride + cbk] = (double)(gsum[et] + gsum[BM + et]);
-        } else {
-          const int w = row - 3 * g.L.Pp;
-          if (w < 2 * g.L.nh)
-            for (int c3 = 0; c3 < 3; ++c3)
-              g.gpart[((size_t)c3 * g.gnc + g.L.npos + w) * g.gstride + cbk] =
-                  (double)(gsum[2 * c3 * BM + et] + gsum[(2 * c3 + 1) * BM + et]);
-        }
-      }
     }
-    if (et == 0) {
+    if (leader) {
       // a load issued for a pass the loop did not reach lands before the CTA
       // leaves (guard limit), and the stores complete
-      if (issued > k) umma::mbar_wait(fbar, (issued - 1) & 1, g.err);
+      if (issued > k) umma::mbar_wait(fh, (issued - 1) & 1, g.err);
       umma::bulk_wait0();
     }
   }

@@ -312,16 +312,18 @@ __global__ void k_sum_rows(const double* __restrict__ part, int nparts, int m, d
 }
 
 // out[row] = sum over k of part[row][k] (fixed order; one warp per row)
+// out[row] (+)= sum of part[row stride + k], k < nparts, one warp per row in
+// a fixed order
 __global__ void k_row_sums(const double* __restrict__ part, int rows, int64_t nparts,
-                           double* __restrict__ out) {
+                           int64_t stride, bool add, double* __restrict__ out) {
   const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
-  const double* p = part + (size_t)row * nparts;
+  const double* p = part + (size_t)row * stride;
   double s = 0;
   for (int64_t k = lane; k < nparts; k += 32) s += p[k];
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) out[row] = s;
+  if (lane == 0) out[row] = add ? out[row] + s : s;
 }
 
 // The handle part of the gradient over segment seg of the chunk's samples:
@@ -781,11 +783,12 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
   // 262,144-sample chunk gives 8 x 256 CTAs, enough to fill the SMs to the
   // kernel's register limit of 12 CTAs)
   const int qslices = (int)std::max<int64_t>(1, std::min<int64_t>(256, (chunk + 1023) / 1024));
-  // handle part of the gradient: bf16 J rows form it per 128-sample tile in
-  // their epilogue ([3nc][tiles]); 3xtf32 runs a GEMV per chunk ([chunks x segs][3nc])
+  // handle part of the gradient: bf16 J rows form it per 64-sample block of
+  // a chunk in their epilogue ([3nc][blocks of the chunk]), summed into
+  // [3nc] after each chunk; 3xtf32 runs a GEMV per chunk ([chunks x segs][3nc])
   const bool fused_g = want_g && !x3;
-  const int64_t tiles_all = (n + 127) / 128 + nchunks;   // tile columns, a little slack per chunk
-  const size_t gh_b = sizeof(double) * (fused_g ? (size_t)tiles_all * 3 * nc + 3 * (size_t)nc
+  const int64_t cblk = (chunk + 63) / 64;   // 64-sample blocks of a chunk
+  const size_t gh_b = sizeof(double) * (fused_g ? (size_t)cblk * 3 * nc + 3 * (size_t)nc
                                                 : (size_t)std::max(nchunks, 1) * kGemvSegs * 3 * nc);
   const size_t q_b = sizeof(double) * (size_t)std::max(nchunks, 1) * qslices * Nb * 3;
   const size_t gb_b = sizeof(double) * 3 * (size_t)nc;
@@ -838,9 +841,9 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
       return rc;
   }
   int ci = 0;
-  int64_t tile_col = 0;
+  double* ghr = fused_g ? gh + (size_t)cblk * 3 * nc : nullptr;   // [3nc] running sums
   if (fused_g &&
-      (rc = cuda_check(c, cudaMemsetAsync(gh, 0, sizeof(double) * (size_t)tiles_all * 3 * nc, S(c)), "memset")))
+      (rc = cuda_check(c, cudaMemsetAsync(ghr, 0, sizeof(double) * 3 * (size_t)nc, S(c)), "memset")))
     return rc;
   for (int64_t s0 = 0; s0 < n; s0 += chunk, ++ci) {
     const int m = (int)std::min<int64_t>(chunk, n - s0);
@@ -884,10 +887,14 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
       BEM_LAUNCHED(c);
     }
     if ((rc = tc_jrows(c, sch, L, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld,
-                       fused_g ? resid + 3 * s0 : nullptr, nc,
-                       fused_g ? gh + tile_col : nullptr, tiles_all)))
+                       fused_g ? resid + 3 * s0 : nullptr, nc, fused_g ? gh : nullptr, cblk)))
       return rc;
-    tile_col += (m + 127) / 128;
+    if (fused_g) {
+      // every (channel, column) row of the chunk's blocks is written by the
+      // J-row epilogue; their sums are added in a fixed order
+      k_row_sums<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>(gh, 3 * nc, (m + 63) / 64, cblk, true, ghr);
+      BEM_LAUNCHED(c);
+    }
     const void* Jc[2] = {J[0], J[1]};
     if ((rc = tc_syrk(c, sch, L, m, Jc, ld, part, splits))) return rc;
   }
@@ -905,11 +912,9 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
     if ((rc = la_apply3_refined(c, c->bd.d_WT32, c->bd.d_A, c->d_q, c->d_lb, true))) return rc;
     k_g_boundary<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>((const double*)c->Dfc.p, Nb, nc, c->d_lb, gb);
     if (fused_g) {
-      double* ghr = gh + (size_t)tiles_all * 3 * nc;
-      k_row_sums<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>(gh, 3 * nc, tiles_all, ghr);
       k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(ghr, 1, 3 * nc, gb, c->sc.pp, c->sc.NH,
                                                          n > 0 ? 1.0 / double(n) : 0.0, gout);
-      c->launches += 3;
+      c->launches += 2;
     } else {
       k_g_assemble<<<(nth + 127) / 128, 128, 0, S(c)>>>(gh, nchunks * kGemvSegs, 3 * nc, gb, c->sc.pp, c->sc.NH,
                                                          n > 0 ? 1.0 / double(n) : 0.0, gout);
