@@ -237,13 +237,15 @@ def measure_pipes(m):
                    "thread, median of 20 launches of about 30 ms"}
 
 
-def rooflines(prof, steps, n, P, Nb, nc, pipes, cfg=CFG):
+def rooflines(prof, steps, n, P, Nb, nc, pipes, cfg=CFG, jtj="bf16"):
     """One entry per modelled kernel.  ALU kernels: the FP32/SFU roofline of
     two pipes that run side by side, t_roof = max(flops / FP32 peak, special
     ops / SFU peak), peaks measured by bem_pipe_peak; `bound` names the
     binding pipe and `frac` = t_roof / measured time.  `fp32_only` gives the
     FP32-peak fraction with each special op counted as one flop.  Tensor
-    kernels: flops against the measured sustained bf16 rate."""
+    kernels: flops against the measured sustained bf16 rate; the compensated
+    schemes count their three products per block, 3xtf32 against the bf16
+    rate times the nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s)."""
     peaks, src = read_peaks()
     out = []
     fp32 = pipes["fp32_tflops"] * 1e12
@@ -270,13 +272,19 @@ def rooflines(prof, steps, n, P, Nb, nc, pipes, cfg=CFG):
                                       "frac": (F + T) / t / fp32},
                         "peak_source": "measured by bem_pipe_peak in this run"})
         else:
-            per_launch = work * steps / cnt
+            products = 1 if jtj == "bf16" else 3
+            per_launch = work * steps / cnt * products
             ach = per_launch / t / 1e12
             peak = peaks["bf16_tflops_sustained"]
+            psrc = f"bf16 dense, sustained ({src}, MEASURED_PEAKS.json)"
+            if jtj == "3xtf32":
+                peak *= 1.1 / 2.25
+                psrc = f"tf32: bf16 dense sustained ({src}) x nominal tf32/bf16 1.1/2.25"
             rec = {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak,
-                   "unit": "TFLOP/s", "frac": ach / peak, "traffic": kernel_traffic(name, cfg),
-                   "flops_per_launch": per_launch,
-                   "peak_source": f"bf16 dense, sustained ({src}, MEASURED_PEAKS.json)"}
+                   "unit": "TFLOP/s", "frac": ach / peak,
+                   "traffic": kernel_traffic(name, cfg) if jtj == "bf16" else None,
+                   "flops_per_launch": per_launch, "products_per_block": products,
+                   "peak_source": psrc}
         rec["share_ms"] = ms
         out.append(rec)
     out.sort(key=lambda r: -r.pop("share_ms"))
@@ -693,7 +701,7 @@ def run_ours(args, rank, world, dist):
         return
     # ---- per-kernel live timing -> roofline of the dominant modelled kernel
     P, Nb, nc = sc.n_panels, 1024, 16 * sc.n_curves
-    roofs = rooflines(prof, args.steps, n, P, Nb, nc, pipes, cfg)
+    roofs = rooflines(prof, args.steps, n, P, Nb, nc, pipes, cfg, args.jtj)
     roof = roofs[0] if roofs else None
     kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
                    "share": v[0] / total_ms} for k, v in sorted(prof.items())}

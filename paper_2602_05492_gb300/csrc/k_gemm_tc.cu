@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(128, Scheme<SCH>::X3 ? 1 : 2)
 // One CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
 // of 128 rows x 256 samples (t = row tile + col tile * row tiles, so
 // consecutive tiles share their Phi tile).  Warp 0 lane 0 streams A/B slabs
-// (A 128 rows, B 256 rows as two 128-row boxes) through a PSTAGES ring (TMA),
+// (A 128 rows, B 256 rows as two 128-row boxes) through a ring of stages (TMA),
 // warp 1 lane 0 issues M = 128, N = 256 MMAs into one of two 256-column TMEM
 // accumulators, and warps 2..9 drain the other in two passes of 128 columns:
 // warp w owns TMEM lanes 32 (w % 4) .. +31 and the columns 64 ((w - 2) / 4)
@@ -358,13 +358,22 @@ __global__ void __launch_bounds__(128, Scheme<SCH>::X3 ? 1 : 2)
 // 64-column bf16 boxes in the same swizzle.  The bf16 rows of column half h
 // are packed in place over F box 2 h, which only that half's warps read,
 // and each thread reads its row of both of its boxes before it writes there.
-constexpr int PSTAGES = 3;
-constexpr int kPersBN = 256;                          // samples per tile
-constexpr int kPersPass = kPersBN / BN;               // epilogue passes of BN columns
-constexpr int kPersStage = TILE_BYTES * (1 + kPersPass);   // A slab + B slab (48 KB)
+// Compensated bf16 (BF16X3) runs the same kernel on 128-sample tiles: a
+// stage holds the hi and lo parts of the A and B slabs (64 KB, two stages),
+// each K step issues the three products lo.hi, hi.lo, hi.hi into one
+// 128-column accumulator, and the epilogue writes the hi and lo parts of
+// J^T, hi over F box 2 h and lo over F box 2 h + 1 after the thread has read
+// its row of both.
+template <bool X3>
+struct Pers {
+  static constexpr int BNT = X3 ? 128 : 256;               // samples per tile
+  static constexpr int PASSES = BNT / BN;                  // epilogue passes of BN columns
+  static constexpr int STAGES = X3 ? 2 : 3;
+  static constexpr int STAGE = X3 ? 4 * TILE_BYTES : TILE_BYTES * (1 + PASSES);
+  static constexpr int SMEM = 1024 + STAGES * STAGE + BM * BN * 4 + 3 * BN * 4 + 256;
+  static_assert(SMEM <= 227 * 1024, "persistent J-row kernel exceeds shared memory");
+};
 constexpr int kPersThreads = 320;           // 2 control warps + 8 epilogue warps
-constexpr int kPersSmem = 1024 + PSTAGES * kPersStage + BM * BN * 4 + 3 * BN * 4 + 256;
-static_assert(kPersSmem <= 227 * 1024, "persistent J-row kernel exceeds shared memory");
 
 // the named barrier of epilogue half h (its four warps)
 __device__ __forceinline__ void bar_half(int h) {
@@ -376,18 +385,30 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(bar)) : "memory");
 }
 
+// bf16 of x and of its rounding remainder
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// tA, tB: the hi (or only) parts of M^T and Phi; tA2, tB2: their lo parts
+// (X3); tF: F^T; tJ, tJ2: J^T (hi and lo parts for X3)
+template <bool X3>
 __global__ void __launch_bounds__(kPersThreads, 1)
     k_tc_jrows_pers(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+                    const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB2,
                     const __grid_constant__ CUtensorMap tF, const __grid_constant__ CUtensorMap tJ,
-                    TcArgs g) {
+                    const __grid_constant__ CUtensorMap tJ2, TcArgs g) {
+  using P = Pers<X3>;
   constexpr int BK = Scheme<SCH_BF16>::BK;
+  constexpr int BNT = P::BNT, PASSES = P::PASSES, STAGES = P::STAGES, STAGE = P::STAGE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* fs = reinterpret_cast<float*>(smem + PSTAGES * kPersStage);  // 4 boxes [BM][32] F rows
+  float* fs = reinterpret_cast<float*>(smem + STAGES * STAGE);         // 4 boxes [BM][32] F rows
   float* rs = fs + BM * BN;                                            // [BN][3] residuals
   uint64_t* full = reinterpret_cast<uint64_t*>(rs + 3 * BN);
-  uint64_t* empty = full + PSTAGES;
-  uint64_t* tfull = empty + PSTAGES;
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
   uint64_t* fbar = tempty + 2;                              // [2] a half's F rows landed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fbar + 2);
@@ -396,13 +417,13 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   int* half_ok = stop_flag + 1;                             // [2] a half's view of fail_flag
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rtiles = (g.M + BM - 1) / BM, ctiles = (g.N + kPersBN - 1) / kPersBN;
+  const int rtiles = (g.M + BM - 1) / BM, ctiles = (g.N + BNT - 1) / BNT;
   const int ntiles = rtiles * ctiles;
   const int nk = (g.K + BK - 1) / BK;
   if (threadIdx.x == 0) {
     *fail_flag = 0;
     *stop_flag = 0;
-    for (int s = 0; s < PSTAGES; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       umma::mbar_init(&full[s], 1);
       umma::mbar_init(&empty[s], 1);
     }
@@ -414,7 +435,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
     umma::mbar_init(&fbar[1], 1);
     umma::fence_barrier_init();
   }
-  if (warp == 0) umma::tmem_alloc(tmem_slot, 2 * kPersBN);
+  if (warp == 0) umma::tmem_alloc(tmem_slot, 2 * BNT);
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
@@ -426,27 +447,34 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       int it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int arow = (t % rtiles) * BM, brow = (t / rtiles) * kPersBN;
+        const int arow = (t % rtiles) * BM, brow = (t / rtiles) * BNT;
         for (int kk = 0; kk < nk; ++kk, ++it) {
-          const int s = it % PSTAGES;
-          const uint32_t ph = (it / PSTAGES) & 1;
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
           if (!umma::mbar_wait(&empty[s], ph ^ 1, g.err, g.wait_ns)) { ok = false; break; }
-          umma::mbar_expect_tx(&full[s], kPersStage);
-          uint8_t* st = smem + (size_t)s * kPersStage;
+          umma::mbar_expect_tx(&full[s], STAGE);
+          uint8_t* st = smem + (size_t)s * STAGE;
           umma::tma_load_2d(st, &tA, &full[s], kk * BK, arow);
+          if constexpr (X3) {
+            // A hi, B hi, A lo, B lo
+            umma::tma_load_2d(st + TILE_BYTES, &tB, &full[s], kk * BK, brow);
+            umma::tma_load_2d(st + 2 * TILE_BYTES, &tA2, &full[s], kk * BK, arow);
+            umma::tma_load_2d(st + 3 * TILE_BYTES, &tB2, &full[s], kk * BK, brow);
+          } else {
 #pragma unroll
-          for (int p = 0; p < kPersPass; ++p)
-            umma::tma_load_2d(st + (1 + p) * TILE_BYTES, &tB, &full[s], kk * BK, brow + p * BN);
+            for (int p = 0; p < PASSES; ++p)
+              umma::tma_load_2d(st + (1 + p) * TILE_BYTES, &tB, &full[s], kk * BK, brow + p * BN);
+          }
         }
       }
       // the last loads of every slot have landed before the CTA can leave
-      for (int j = it > PSTAGES ? it - PSTAGES : 0; j < it; ++j)
-        umma::mbar_wait(&full[j % PSTAGES], (j / PSTAGES) & 1, g.err);
+      for (int j = it > STAGES ? it - STAGES : 0; j < it; ++j)
+        umma::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, g.err);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer: tile i of this CTA accumulates into TMEM buffer i & 1
-      const uint32_t id = umma::idesc(1, BM, kPersBN);
+      const uint32_t id = umma::idesc(1, BM, BNT);
       int it = 0, i = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
@@ -456,10 +484,10 @@ __global__ void __launch_bounds__(kPersThreads, 1)
           break;
         }
         umma::fence_after();
-        const uint32_t acc = tmem + (uint32_t)(b * kPersBN);
+        const uint32_t acc = tmem + (uint32_t)(b * BNT);
         for (int kk = 0; kk < nk; ++kk, ++it) {
-          const int s = it % PSTAGES;
-          const uint32_t ph = (it / PSTAGES) & 1;
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
           if (!umma::mbar_wait(&full[s], ph, g.err, g.wait_ns)) {
             // the epilogue learns from stop_flag, after this tile's commit,
             // that no further tile follows
@@ -468,12 +496,21 @@ __global__ void __launch_bounds__(kPersThreads, 1)
             break;
           }
           umma::fence_after();
-          const uint32_t a0 = umma::smem_u32(smem + (size_t)s * kPersStage);
-          const uint32_t b0 = a0 + TILE_BYTES;   // 256 rows: two 128-row boxes back to back
+          const uint32_t a0 = umma::smem_u32(smem + (size_t)s * STAGE);
+          const uint32_t b0 = a0 + TILE_BYTES;   // bf16: 256 rows, two 128-row boxes back to back
 #pragma unroll
-          for (int k4 = 0; k4 < 4; ++k4)
-            umma::mma_bf16(acc, umma::sdesc_sw128(a0 + k4 * 32), umma::sdesc_sw128(b0 + k4 * 32), id,
-                           (kk | k4) != 0);
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const uint64_t da = umma::sdesc_sw128(a0 + k4 * 32), db = umma::sdesc_sw128(b0 + k4 * 32);
+            if constexpr (X3) {
+              const uint64_t dal = umma::sdesc_sw128(a0 + 2 * TILE_BYTES + k4 * 32);
+              const uint64_t dbl = umma::sdesc_sw128(b0 + 2 * TILE_BYTES + k4 * 32);
+              umma::mma_bf16(acc, dal, db, id, (kk | k4) != 0);   // lo . hi
+              umma::mma_bf16(acc, da, dbl, id, 1);                // hi . lo
+              umma::mma_bf16(acc, da, db, id, 1);                 // hi . hi
+            } else {
+              umma::mma_bf16(acc, da, db, id, (kk | k4) != 0);
+            }
+          }
           umma::mma_commit(&empty[s]);
         }
         umma::mma_commit(&tfull[b]);
@@ -482,9 +519,10 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   } else {
     // epilogue, 256 threads in two halves of four warps; half h owns the
     // columns 64 h .. 64 h + 63 of every pass (F boxes 2 h and 2 h + 1, the
-    // J^T box over F box 2 h) and runs its own pipeline: its leader thread
-    // loads and stores its boxes, its warps sync on their own named barrier,
-    // and each thread writes the gradient partial of its row and 64 columns
+    // J^T box or boxes over them) and runs its own pipeline: its leader
+    // thread loads and stores its boxes, its warps sync on their own named
+    // barrier, and each thread writes the gradient partial of its row and 64
+    // columns
     const int et = threadIdx.x - 64;                 // 0 .. 255
     const int q = warp & 3, half = (warp - 2) >> 2;  // TMEM lane quarter, column half
     const int r = 32 * q + lane;                     // tile row of this thread
@@ -495,7 +533,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
     uint64_t* fh = fbar + half;
     // leader: the half's F rows (two TMA boxes) and residuals of pass p of tile t
     auto load_half = [&](int t, int p) {
-      const int arow = (t % rtiles) * BM, c0 = (t / rtiles) * kPersBN + p * BN + 64 * half;
+      const int arow = (t % rtiles) * BM, c0 = (t / rtiles) * BNT + p * BN + 64 * half;
       const bool rbulk = g.gpart && c0 + 64 <= g.N;
       if (g.gpart && !rbulk)   // the chunk's ragged end: zeros past it
         for (int e = 0; e < 3 * 64; ++e) {
@@ -509,16 +547,16 @@ __global__ void __launch_bounds__(kPersThreads, 1)
     };
     // pass k of this CTA: tile blockIdx.x + (k / passes) gridDim.x, pass k % passes
     const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int npass = my_tiles * kPersPass;
+    const int npass = my_tiles * PASSES;
     if (leader && npass > 0) load_half(blockIdx.x, 0);
     int issued = npass > 0 ? 1 : 0;   // loads issued (leader)
     bool ok = true;
     int k = 0;
     for (; k < npass && ok; ++k) {
-      const int t = (int)blockIdx.x + (k / kPersPass) * (int)gridDim.x, p = k % kPersPass;
-      const int i = k / kPersPass, b = i & 1;
+      const int t = (int)blockIdx.x + (k / PASSES) * (int)gridDim.x, p = k % PASSES;
+      const int i = k / PASSES, b = i & 1;
       const int arow = (t % rtiles) * BM, ct = t / rtiles;
-      const int c0 = ct * kPersBN + p * BN + 64 * half;
+      const int c0 = ct * BNT + p * BN + 64 * half;
       if (p == 0) {
         // (the guard limit: MMAs of this buffer may still be in flight)
         if (!umma::mbar_wait(&tfull[b], (i >> 1) & 1, g.err)) atomicOr(fail_flag, 1);
@@ -537,25 +575,41 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       int gch = 0;
       if (g.gpart && !jump) gch = (arow + r) / g.L.Pp;
       float gacc = 0.f, gacc1 = 0.f, gacc2 = 0.f;
-      // the half's bf16 rows go over its F box 2 h, after this thread has
-      // read its row of both boxes
+      // bf16: the half's rows go over its F box 2 h, after this thread has
+      // read its row of that box; X3: hi over box 2 h and lo over box 2 h + 1,
+      // after it has read its row of both
       uint8_t* ob = reinterpret_cast<uint8_t*>(fb) + r * 128;
+      uint8_t* ob2 = reinterpret_cast<uint8_t*>(fb + BM * 32) + r * 128;
+      float fx[X3 ? 32 : 1];   // X3: the row of box 2 h + 1, read up front
+      if constexpr (X3) {
+        const uint8_t* fr1 = reinterpret_cast<const uint8_t*>(fb + BM * 32) + r * 128;
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+          const float4 w4 = *reinterpret_cast<const float4*>(fr1 + ((c8 ^ sw) << 4));
+          fx[4 * c8] = w4.x; fx[4 * c8 + 1] = w4.y; fx[4 * c8 + 2] = w4.z; fx[4 * c8 + 3] = w4.w;
+        }
+      }
 #pragma unroll 1
       for (int s2 = 0; s2 < 2; ++s2) {
         float v[32];
         umma::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) +
-                            (uint32_t)(b * kPersBN + p * BN + 64 * half + 32 * s2),
+                            (uint32_t)(b * BNT + p * BN + 64 * half + 32 * s2),
                         v);
         if (!ok) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = 0.f;
         }
-        const uint8_t* fr = reinterpret_cast<const uint8_t*>(fb + s2 * (BM * 32)) + r * 128;
         float f[32];
+        if (X3 && s2 == 1) {
 #pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) {
-          const float4 w4 = *reinterpret_cast<const float4*>(fr + ((c8 ^ sw) << 4));
-          f[4 * c8] = w4.x; f[4 * c8 + 1] = w4.y; f[4 * c8 + 2] = w4.z; f[4 * c8 + 3] = w4.w;
+          for (int j = 0; j < 32; ++j) f[j] = fx[X3 ? j : 0];
+        } else {
+          const uint8_t* fr = reinterpret_cast<const uint8_t*>(fb + s2 * (BM * 32)) + r * 128;
+#pragma unroll
+          for (int c8 = 0; c8 < 8; ++c8) {
+            const float4 w4 = *reinterpret_cast<const float4*>(fr + ((c8 ^ sw) << 4));
+            f[4 * c8] = w4.x; f[4 * c8 + 1] = w4.y; f[4 * c8 + 2] = w4.z; f[4 * c8 + 3] = w4.w;
+          }
         }
         const float* rr = rh + 3 * 32 * s2;
         if (g.gpart && !jump) {
@@ -572,18 +626,30 @@ __global__ void __launch_bounds__(kPersThreads, 1)
         // output chunks 4 s2 .. 4 s2 + 3 of the row (8 bf16 each)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          uint4 w;
+          uint4 w, w2;
           uint32_t* wp = &w.x;
+          uint32_t* wp2 = &w2.x;
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * kk + 2 * h] + f[8 * kk + 2 * h],
-                                                            v[8 * kk + 2 * h + 1] + f[8 * kk + 2 * h + 1]);
-            wp[h] = *reinterpret_cast<const uint32_t*>(&b2);
+            const float x0 = v[8 * kk + 2 * h] + f[8 * kk + 2 * h];
+            const float x1 = v[8 * kk + 2 * h + 1] + f[8 * kk + 2 * h + 1];
+            if constexpr (X3) {
+              __nv_bfloat16 h0, l0, h1, l1;
+              split_bf16(x0, h0, l0);
+              split_bf16(x1, h1, l1);
+              const __nv_bfloat162 bh(h0, h1), bl(l0, l1);
+              wp[h] = *reinterpret_cast<const uint32_t*>(&bh);
+              wp2[h] = *reinterpret_cast<const uint32_t*>(&bl);
+            } else {
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
+              wp[h] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
           }
           *reinterpret_cast<uint4*>(ob + (((4 * s2 + kk) ^ sw) << 4)) = w;
+          if constexpr (X3) *reinterpret_cast<uint4*>(ob2 + (((4 * s2 + kk) ^ sw) << 4)) = w2;
         }
       }
-      if (p == kPersPass - 1 || !ok) {
+      if (p == PASSES - 1 || !ok) {
         // this warp's TMEM reads of the tile are complete (or given up, and
         // the loop ends after this pass): release the buffer
         umma::fence_before();
@@ -595,7 +661,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       // nothing and is not written)
       if (g.gpart && ok && arow + r < g.M && c0 < g.N) {
         const int row = arow + r;
-        const int64_t blk = 2 * (kPersPass * ct + p) + half;
+        const int64_t blk = 2 * (PASSES * ct + p) + half;
         if (!jump) {
           const int ch = row / g.L.Pp, col = row - ch * g.L.Pp;
           if (col < g.L.npos) g.gpart[((size_t)ch * g.gnc + col) * g.gstride + blk] = (double)gacc;
@@ -613,13 +679,14 @@ __global__ void __launch_bounds__(kPersThreads, 1)
       bar_half(half);
       if (leader) {
         // the half's J^T rows (rows and columns past the matrix are not
-        // written), then its next F rows once the store has read fb
+        // written), then its next F rows once the stores have read fb
         umma::tma_store_2d(&tJ, fb, c0, arow);
+        if constexpr (X3) umma::tma_store_2d(&tJ2, fb + BM * 32, c0, arow);
         umma::bulk_commit();
         umma::bulk_wait_read0();
         if (ok && k + 1 < npass) {
           const int k1 = k + 1;
-          load_half((int)blockIdx.x + (k1 / kPersPass) * (int)gridDim.x, k1 % kPersPass);
+          load_half((int)blockIdx.x + (k1 / PASSES) * (int)gridDim.x, k1 % PASSES);
           ++issued;
         }
       }
@@ -634,7 +701,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   __syncwarp();
   umma::fence_before();
   __syncthreads();
-  if (warp == 0) umma::tmem_dealloc(tmem, 2 * kPersBN);
+  if (warp == 0) umma::tmem_dealloc(tmem, 2 * BNT);
 }
 
 // ---- bf16 Gram blocks on paired tiles ----------------------------------------
@@ -910,35 +977,55 @@ int tc_jrows(bem_ctx* c, int sch, const JLayout& L, int m, int Nb, const void* c
   g.L = L;
   if (x3) { g.Jhi = Jout[0]; g.Jlo = Jout[1]; }
   else g.J = (__nv_bfloat16*)Jout[0];
-  if (!x3 && gpart) {
+  // bf16 and compensated bf16 run the persistent kernel, whose epilogue
+  // forms the handle part of the gradient; 3xtf32 the per-tile kernel
+  const bool pers = sch != SCH_TF32X3;
+  if (pers && gpart) {
     g.resid = resid;
     g.gnc = nc;
     g.gpart = gpart;
     g.gstride = gstride;
   }
   ProfScope _ps(c, "tc_jrows");
-  if (!x3) {
-    // the epilogue's TMA views: F^T (fp32) and J^T (bf16), m columns x rows
-    CUtensorMap tf, tj;
+  if (pers) {
+    // the epilogue's TMA views: F^T (fp32) and J^T (bf16; hi and lo parts
+    // for the compensated scheme), m columns x rows
+    CUtensorMap tf, tj, tj2;
     if ((rc = make_map(c, &tf, F, m, rows, ldf, true)) ||
-        (rc = make_map(c, &tj, Jout[0], m, rows, ldj, false)))
+        (rc = make_map(c, &tj, Jout[0], m, rows, ldj, false)) ||
+        (rc = make_map(c, &tj2, x3 ? Jout[1] : Jout[0], m, rows, ldj, false)))
       return rc;
+    if (!x3) { ta2 = ta; tb2 = tb; }   // not read by the bf16 kernel
+    auto run = [&](auto kern, int smem, int bnt) -> int {
+      const int ntiles = ((rows + BM - 1) / BM) * ((m + bnt - 1) / bnt);
+      const int grid = std::max(1, std::min(ntiles, c->sms));
+      kern<<<grid, kPersThreads, smem, S(c)>>>(ta, tb, ta2, tb2, tf, tj, tj2, g);
+      BEM_LAUNCHED(c);
+      return cuda_check(c, cudaGetLastError(), "k_tc_jrows_pers");
+    };
+    if (x3) {
+      static bool attr = false;
+      if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_jrows_pers<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Pers<true>::SMEM);
+        if (e != cudaSuccess) return cuda_check(c, e, "persistent J rows smem attribute");
+        attr = true;
+      }
+      return run(k_tc_jrows_pers<true>, Pers<true>::SMEM, Pers<true>::BNT);
+    }
     static bool attr = false;
     if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_tc_jrows_pers, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           kPersSmem);
+      cudaError_t e = cudaFuncSetAttribute(k_tc_jrows_pers<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           Pers<false>::SMEM);
       if (e != cudaSuccess) return cuda_check(c, e, "persistent J rows smem attribute");
       attr = true;
     }
-    const int ntiles = ((rows + BM - 1) / BM) * ((m + kPersBN - 1) / kPersBN);
-    const int grid = std::max(1, std::min(ntiles, c->sms));
-    k_tc_jrows_pers<<<grid, kPersThreads, kPersSmem, S(c)>>>(ta, tb, tf, tj, g);
-    BEM_LAUNCHED(c);
-    return cuda_check(c, cudaGetLastError(), "k_tc_jrows_pers");
+    return run(k_tc_jrows_pers<false>, Pers<false>::SMEM, Pers<false>::BNT);
   }
   dim3 grid((rows + BM - 1) / BM, (m + BN - 1) / BN);
-  if (f32) return launch<SCH_TF32X3>(c, ta, tb, ta2, tb2, g, grid);
-  return launch<SCH_BF16X3>(c, ta, tb, ta2, tb2, g, grid);
+  return launch<SCH_TF32X3>(c, ta, tb, ta2, tb2, g, grid);
 }
 
 // CTAs of one K slice of the Gram kernels: bf16 paired units, 3xtf32 single

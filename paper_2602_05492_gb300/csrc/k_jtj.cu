@@ -783,10 +783,11 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
   // 262,144-sample chunk gives 8 x 256 CTAs, enough to fill the SMs to the
   // kernel's register limit of 12 CTAs)
   const int qslices = (int)std::max<int64_t>(1, std::min<int64_t>(256, (chunk + 1023) / 1024));
-  // handle part of the gradient: bf16 J rows form it per 64-sample block of
-  // a chunk in their epilogue ([3nc][blocks of the chunk]), summed into
-  // [3nc] after each chunk; 3xtf32 runs a GEMV per chunk ([chunks x segs][3nc])
-  const bool fused_g = want_g && !x3;
+  // handle part of the gradient: the bf16 and compensated-bf16 J rows form
+  // it per 64-sample block of a chunk in their epilogue ([3nc][blocks of the
+  // chunk]), summed into [3nc] after each chunk; 3xtf32 runs a GEMV per
+  // chunk ([chunks x segs][3nc])
+  const bool fused_g = want_g && sch != SCH_TF32X3;
   const int64_t cblk = (chunk + 63) / 64;   // 64-sample blocks of a chunk
   const size_t gh_b = sizeof(double) * (fused_g ? (size_t)cblk * 3 * nc + 3 * (size_t)nc
                                                 : (size_t)std::max(nchunks, 1) * kGemvSegs * 3 * nc);

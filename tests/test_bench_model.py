@@ -52,3 +52,17 @@ def test_per_step_work_is_split_over_launches():
     assert r["flops_per_launch"] == pytest.approx(per, rel=1e-12)
     assert r["bound"] == "fp32"
     assert r["achieved"] == pytest.approx(per / 10e-3 / 1e12, rel=1e-12)
+
+
+def test_compensated_schemes_count_three_products():
+    n, P, Nb, nc = 262144, 8192, 1024, 2048
+    jr, _ = bench.step_work("tc_jrows", n, P, Nb, nc)
+    ms = 5.0
+    prof = {"tc_jrows": (ms, 1)}
+    (b,) = bench.rooflines(prof, 1, n, P, Nb, nc, PIPES, cfg=4, jtj="bf16")
+    (x,) = bench.rooflines(prof, 1, n, P, Nb, nc, PIPES, cfg=4, jtj="bf16x3")
+    (t,) = bench.rooflines(prof, 1, n, P, Nb, nc, PIPES, cfg=4, jtj="3xtf32")
+    assert b["flops_per_launch"] == jr and x["flops_per_launch"] == 3 * jr
+    assert x["frac"] == pytest.approx(3 * b["frac"], rel=1e-12)
+    assert t["peak"] == pytest.approx(b["peak"] * 1.1 / 2.25, rel=1e-12)
+    assert x["traffic"] is None and t["traffic"] is None
