@@ -765,7 +765,8 @@ constexpr int kSySmem = 1024 + SY_STAGES * kSyStage + 256;
 // position range only: the jump-jump blocks are channel 0's), blockIdx.y =
 // K slice.  g.tiles = T channel-order tiles.
 __global__ void __launch_bounds__(128, 1)
-    k_tc_syrk_pair(const __grid_constant__ CUtensorMap tJ, TcArgs g) {
+    k_tc_syrk_pair(const __grid_constant__ CUtensorMap tJ, const __grid_constant__ CUtensorMap tP,
+                   TcArgs g) {
   constexpr int BK = Scheme<SCH_BF16>::BK;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -859,33 +860,48 @@ __global__ void __launch_bounds__(128, 1)
     umma::mma_commit(done);
   }
   __syncwarp();
-  // ---- epilogue: all four warps, thread r = row of the unit's row tile(s)
+  // ---- epilogue: the unit's blocks are added into this K slice's partial
+  // sums by TMA reductions.  Thread r (row r of the unit's row tiles) moves
+  // its accumulator row through shared memory (the ring, idle once the MMAs
+  // are done) into 128-row x 32-column fp32 boxes in the 128-byte swizzle
+  // (row r at 128 r bytes, 16-byte chunk c at position c ^ (r & 7)), and one
+  // thread issues the reductions.
   // (the guard limit: MMAs may be in flight)
   const bool ok = umma::mbar_wait(done, 0, g.err) && *(volatile int*)gave_up == 0;
   umma::fence_after();
   const int r = warp * 32 + lane;
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
   const int nout = un.kind == 0 ? 1 : 2;
-  for (int o = 0; o < nout; ++o) {
-    const int ti = (un.kind == 2 && o == 1) ? un.a1 : un.a0;
-    const int tj = un.kind == 1 ? un.b + o : un.b;
-    const int i = ti * BM + r;
-    const int D = g.L.cdim();
+  float* stage = reinterpret_cast<float*>(smem);   // box (o, c4) at stage + (4 o + c4) BM 32
+  if (ok) {
+    for (int o = 0; o < nout; ++o) {
 #pragma unroll 1
-    for (int cb = 0; cb < BN; cb += 32) {
-      float v[32];
-      umma::tmem_ld32(trow + o * BN + cb, v);
-      if (!ok || nk == 0) {
+      for (int c4 = 0; c4 < 4; ++c4) {
+        float v[32];
+        umma::tmem_ld32(trow + o * BN + 32 * c4, v);
+        uint8_t* row = reinterpret_cast<uint8_t*>(stage + (4 * o + c4) * (BM * 32)) + r * 128;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        for (int c8 = 0; c8 < 8; ++c8)
+          *reinterpret_cast<float4*>(row + ((c8 ^ (r & 7)) << 4)) =
+              make_float4(v[4 * c8], v[4 * c8 + 1], v[4 * c8 + 2], v[4 * c8 + 3]);
       }
-      float* d = g.part + (((size_t)blockIdx.y * 3 + ch) * D + i) * D;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) d[tj * BN + cb + j] += v[j];
     }
   }
+  umma::fence_proxy_async();   // the staged rows, for the TMA
   umma::fence_before();
   __syncthreads();
+  if (threadIdx.x == 0 && ok && nk > 0) {
+    const int D = g.L.cdim();
+    for (int o = 0; o < nout; ++o) {
+      const int ti = (un.kind == 2 && o == 1) ? un.a1 : un.a0;
+      const int tj = un.kind == 1 ? un.b + o : un.b;
+      const int y = ((int)blockIdx.y * 3 + ch) * D + ti * BM;   // row of part[slice][ch][ti BM]
+      for (int c4 = 0; c4 < 4; ++c4)
+        umma::tma_reduce_add_2d(&tP, stage + (4 * o + c4) * (BM * 32), tj * BN + 32 * c4, y);
+    }
+    umma::bulk_commit();
+    umma::bulk_wait0();
+  }
   if (warp == 0) umma::tmem_dealloc(tmem, 256);
 }
 
@@ -1066,7 +1082,12 @@ int tc_syrk(bem_ctx* c, int sch, const JLayout& L, int m, const void* const* J, 
       attr = true;
     }
     g.npairs = syrk_units(g.tiles, g.tiles);
-    k_tc_syrk_pair<<<dim3(gram_ctas(L, false), sp), 128, kSySmem, S(c)>>>(tj, g);
+    // the partial sums as one fp32 matrix of splits x 3 x cdim rows, for the
+    // epilogue's TMA reductions
+    CUtensorMap tp;
+    if ((rc = make_map(c, &tp, part, L.cdim(), (uint64_t)splits * 3 * L.cdim(), L.cdim(), true)))
+      return rc;
+    k_tc_syrk_pair<<<dim3(gram_ctas(L, false), sp), 128, kSySmem, S(c)>>>(tj, tp, g);
     BEM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "k_tc_syrk_pair");
   }

@@ -92,6 +92,18 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
                : "memory");
 }
 
+// 2-D tiled TMA reduction: the box at (c0 = inner, c1 = outer) of the
+// tensor += the fp32 box at src in shared memory, as one bulk group of this
+// thread.
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, const void* src, int c0,
+                                                  int c1) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+          (uint64_t)map),
+      "r"(smem_u32(src)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
 // 1-D bulk copy of bytes (a multiple of 16, both addresses 16-byte aligned)
 // from global to shared memory; completion counted in bytes on bar.
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
