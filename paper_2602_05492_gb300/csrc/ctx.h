@@ -256,7 +256,7 @@ int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const
                   float* D, int ldd);
 int tc_jrows(bem_ctx* c, int sch, const JLayout& L, int m, int Nb, const void* const* Mt, int ldm,
              const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj,
-             const float* resid = nullptr, int nc = 0, double* gpart = nullptr,
+             const float* resid = nullptr, int nc = 0, float* gpart = nullptr,
              int64_t gstride = 0);
 int tc_syrk(bem_ctx* c, int sch, const JLayout& L, int m, const void* const* J, int ldj,
             float* part, int splits);

@@ -86,7 +86,7 @@ struct TcArgs {
   // resid[s][c]
   const float* resid;
   int gnc;
-  double* gpart;
+  float* gpart;
   int64_t gstride;
 };
 
@@ -664,14 +664,14 @@ __global__ void __launch_bounds__(kPersThreads, 1)
         const int64_t blk = 2 * (PASSES * ct + p) + half;
         if (!jump) {
           const int ch = row / g.L.Pp, col = row - ch * g.L.Pp;
-          if (col < g.L.npos) g.gpart[((size_t)ch * g.gnc + col) * g.gstride + blk] = (double)gacc;
+          if (col < g.L.npos) g.gpart[((size_t)ch * g.gnc + col) * g.gstride + blk] = gacc;
         } else {
           const int w = row - 3 * g.L.Pp;
           if (w < 2 * g.L.nh) {
             const size_t o = (size_t)(g.L.npos + w) * g.gstride + blk;
-            g.gpart[o] = (double)gacc;
-            g.gpart[(size_t)g.gnc * g.gstride + o] = (double)gacc1;
-            g.gpart[2 * (size_t)g.gnc * g.gstride + o] = (double)gacc2;
+            g.gpart[o] = gacc;
+            g.gpart[(size_t)g.gnc * g.gstride + o] = gacc1;
+            g.gpart[2 * (size_t)g.gnc * g.gstride + o] = gacc2;
           }
         }
       }
@@ -974,7 +974,7 @@ int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const
 //   3xtf32: Mt = (Mt[0] hi, Mt[1] lo), Phi likewise, fp32; J hi/lo fp32 (Jout[0], Jout[1])
 int tc_jrows(bem_ctx* c, int sch, const JLayout& L, int m, int Nb, const void* const* Mt, int ldm,
              const void* const* Phi, int ldp, const float* F, int ldf, void* const* Jout, int ldj,
-             const float* resid, int nc, double* gpart, int64_t gstride) {
+             const float* resid, int nc, float* gpart, int64_t gstride) {
   const int rows = L.rows();
   const bool x3 = sch != SCH_BF16, f32 = sch == SCH_TF32X3;
   int rc;

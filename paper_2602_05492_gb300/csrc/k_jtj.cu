@@ -303,25 +303,38 @@ __global__ void __launch_bounds__(128) k_phi_q(const float* __restrict__ xy, con
 constexpr int kGemvSegs = 16;   // sample segments per row in k_ft_gemv
 
 // out[t] = sum over k of part[k][t] (fixed order)
-__global__ void k_sum_rows(const double* __restrict__ part, int nparts, int m, double* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= m) return;
+// out[t] = sum over k < nparts of part[k m + t]: 32 outputs per block of 32 x
+// 32 threads, thread row ty summing k = ty, ty + 32, ...; the 32 row sums
+// are added in a fixed order
+__global__ void __launch_bounds__(1024) k_sum_rows(const double* __restrict__ part, int nparts,
+                                                   int m, double* __restrict__ out) {
+  __shared__ double acc[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + tx;
   double s = 0;
-  for (int k = 0; k < nparts; ++k) s += part[(size_t)k * m + t];
-  out[t] = s;
+  if (t < m)
+    for (int k = ty; k < nparts; k += 32) s += part[(size_t)k * m + t];
+  acc[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && t < m) {
+    double v = 0;
+    for (int y = 0; y < 32; ++y) v += acc[y][tx];
+    out[t] = v;
+  }
 }
 
 // out[row] = sum over k of part[row][k] (fixed order; one warp per row)
-// out[row] (+)= sum of part[row stride + k], k < nparts, one warp per row in
-// a fixed order
-__global__ void k_row_sums(const double* __restrict__ part, int rows, int64_t nparts,
+// out[row] (+)= sum of part[row stride + k], k < nparts, in double, one warp
+// per row in a fixed order
+template <typename P>
+__global__ void k_row_sums(const P* __restrict__ part, int rows, int64_t nparts,
                            int64_t stride, bool add, double* __restrict__ out) {
   const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
-  const double* p = part + (size_t)row * stride;
+  const P* p = part + (size_t)row * stride;
   double s = 0;
-  for (int64_t k = lane; k < nparts; k += 32) s += p[k];
+  for (int64_t k = lane; k < nparts; k += 32) s += (double)p[k];
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) out[row] = add ? out[row] + s : s;
 }
@@ -842,6 +855,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
       return rc;
   }
   int ci = 0;
+  float* ghf = reinterpret_cast<float*>(gh);                          // fp32 partials of a chunk
   double* ghr = fused_g ? gh + (size_t)cblk * 3 * nc : nullptr;   // [3nc] running sums
   if (fused_g &&
       (rc = cuda_check(c, cudaMemsetAsync(ghr, 0, sizeof(double) * 3 * (size_t)nc, S(c)), "memset")))
@@ -888,12 +902,12 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
       BEM_LAUNCHED(c);
     }
     if ((rc = tc_jrows(c, sch, L, m, Nb, Mt, Nb, phi, Nb, F, ld, J, ld,
-                       fused_g ? resid + 3 * s0 : nullptr, nc, fused_g ? gh : nullptr, cblk)))
+                       fused_g ? resid + 3 * s0 : nullptr, nc, fused_g ? ghf : nullptr, cblk)))
       return rc;
     if (fused_g) {
       // every (channel, column) row of the chunk's blocks is written by the
       // J-row epilogue; their sums are added in a fixed order
-      k_row_sums<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>(gh, 3 * nc, (m + 63) / 64, cblk, true, ghr);
+      k_row_sums<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>(ghf, 3 * nc, (m + 63) / 64, cblk, true, ghr);
       BEM_LAUNCHED(c);
     }
     const void* Jc[2] = {J[0], J[1]};
@@ -908,7 +922,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
   if (want_g) {
     // q = sum over chunks and slices (fixed order) -> lambda = (A^+)^T q
     const int nq = nchunks * qslices;
-    k_sum_rows<<<(3 * Nb + 255) / 256, 256, 0, S(c)>>>(qp, nq, 3 * Nb, c->d_q);
+    k_sum_rows<<<(3 * Nb + 31) / 32, 1024, 0, S(c)>>>(qp, nq, 3 * Nb, c->d_q);
     BEM_LAUNCHED(c);
     if ((rc = la_apply3_refined(c, c->bd.d_WT32, c->bd.d_A, c->d_q, c->d_lb, true))) return rc;
     k_g_boundary<<<(3 * nc + 7) / 8, 256, 0, S(c)>>>((const double*)c->Dfc.p, Nb, nc, c->d_lb, gb);
