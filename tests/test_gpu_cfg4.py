@@ -51,3 +51,37 @@ def test_vjp_mixed_cfg4_sampled(cfg4):
     g = m.vjp(xt, r).cpu().numpy()
     want = o.grad(sc.theta_init, xy[idx].astype(np.float64), rs.astype(np.float64))
     assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-4
+
+
+def test_gn_products_cfg4_halves(cfg4):
+    """The Gauss-Newton products over all 67,108,864 samples (256 chunks of
+    262,144, the bench's configuration) are the mean of those over the two
+    halves (128 chunks each, the same chunk boundaries): the loss to rounding,
+    the gradient to the refined boundary solve, H to the fp32 accumulation of
+    the Gram partials;
+    H is symmetric positive semidefinite (Eq. (losshessian), (lossjacobian))."""
+    sc, xy, xt, idx, o, m = cfg4
+    n = xy.shape[0]
+    h = n // 2
+    assert h % 262144 == 0
+    tgt = gen.add_noise(gen.analytic_truth(xy, sc.seed), sc.noise, sc.seed).astype(np.float32)
+    tt = torch.from_numpy(tgt).to("cuda:0")
+    L, g, H = m.gn_products(xt, tt)
+    L1, g1, H1 = m.gn_products(xt[:h].contiguous(), tt[:h].contiguous())
+    L2, g2, H2 = m.gn_products(xt[h:].contiguous(), tt[h:].contiguous())
+    g, g1, g2 = g.cpu().numpy(), g1.cpu().numpy(), g2.cpu().numpy()
+    H, H1, H2 = H.cpu().numpy(), H1.cpu().numpy(), H2.cpu().numpy()
+    assert np.isfinite(L) and np.all(np.isfinite(g)) and np.all(np.isfinite(H))
+    assert L == pytest.approx(0.5 * (L1 + L2), rel=1e-9)
+    # the boundary part of g goes through the refined float solve with
+    # (A^+)^T (one double-residual correction: about 1e-8 relative), which
+    # does not add exactly; measured 8.8e-9
+    assert np.linalg.norm(g - 0.5 * (g1 + g2)) / np.linalg.norm(g) < 5e-8
+    assert np.linalg.norm(H - 0.5 * (H1 + H2)) / np.linalg.norm(H) < 1e-5
+    # symmetric up to the fp32 sums of the diagonal Gram blocks (both
+    # triangles formed); positive semidefinite up to their rounding (the
+    # smallest eigenvalues of the bf16 Gram matrix are about 1e-6 of the
+    # largest, and rounding moves some of them below zero)
+    assert np.linalg.norm(H - H.T) / np.linalg.norm(H) < 1e-6
+    ev = np.linalg.eigvalsh(0.5 * (H + H.T))
+    assert ev[0] > -1e-4 * ev[-1], (ev[0], ev[-1])
