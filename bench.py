@@ -921,10 +921,11 @@ def run_batch(args, rank, world):
                               "ms_per_step": tsq / args.steps},
             "batched_over_one_at_a_time": value / seq, "clocks": clk,
             "kernels_batched": kb, "kernels_one_at_a_time": ks,
-            "kernels_note": "event times per kernel name; in the batched call the per-scene "
-                            "trial setup (damped solves, trial geometry) runs on one stream per "
-                            "scene at once, so those kernels' times overlap and their sum "
-                            "exceeds the wall time they take"}
+            "kernels_note": "event times per kernel name; in the batched call the scenes' "
+                            "Gauss-Newton passes and trial setups (damped solves, trial "
+                            "geometry) run on one stream per scene, several at once, so those "
+                            "kernels' times overlap and their sum exceeds the wall time they "
+                            "take"}
     print(json.dumps(line), flush=True)
 
 

@@ -314,9 +314,21 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
   number_tiles(b, 0, b->spt);
   bind_partials(b, 0);
   if ((rc = upload(b, 0)) || (rc = eval_graph(b, 0))) return rc;
-  // ---- B: H and g per scene
-  for (int s = 0; s < S; ++s) {
+  // ---- B: H and g per scene, the scenes on their own streams (after phase
+  // A) from several host threads.  Worker w takes the scenes w, w + K, ...
+  // one after another and lends them scene w's chunk buffers (the J-row
+  // pass ends with a synchronisation of the scene's stream, so a worker's
+  // scenes never use those buffers at the same time).
+  if ((rc = cuda_check(c0, cudaEventRecord(b->ev_b, b->st), "event"))) return rc;
+  for (int s = 0; s < S; ++s)
+    if ((rc = cuda_check(c0, cudaStreamWaitEvent(b->sst[s], b->ev_b, 0), "event"))) return rc;
+  std::vector<int> brc(S, BEM_OK);
+  const int nworkers = std::min(S, 8);
+  auto scene_gn = [&](int s, int w) -> int {
+    int rc = BEM_OK;
     bem_ctx* c = b->sc[s];
+    c->cur = b->sst[s];
+    c->scratch = s == w ? nullptr : b->sc[w];
     const int nth = c->sc.nth;
     double* g = (double*)b->gvec[s].p;
     if ((rc = grow(c, c->H, sizeof(double) * (size_t)nth * nth))) return rc;
@@ -324,7 +336,7 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
       // residual, loss sum, g and H from one pass; the loss sum joins the others
       if ((rc = jtj_build(c, n[s], xy[s], (double*)c->H.p, b->resid[s].p, g, target[s])) ||
           (rc = cuda_check(c, cudaMemcpyAsync((double*)b->sums[0].p + s, c->d_scal, sizeof(double),
-                                              cudaMemcpyDeviceToDevice, b->st), "loss")))
+                                              cudaMemcpyDeviceToDevice, c->cur), "loss")))
         return rc;
       ctx_scale_norm(c, g, nth, 1.0, (double*)b->gn2.p + s);
     } else if (jtj_gives_gradient(c)) {
@@ -335,7 +347,31 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
       ctx_scale_norm(c, g, nth, 1.0 / double(n[s]), (double*)b->gn2.p + s);
       if ((rc = jtj_build(c, n[s], xy[s], (double*)c->H.p))) return rc;
     }
+    return rc;
+  };
+  {
+    auto worker = [&](int w) {
+      // the runtime's current device is per host thread
+      if (cudaSetDevice(c0->device) != cudaSuccess) {
+        for (int s = w; s < S; s += nworkers) brc[s] = BEM_ECUDA;
+        return;
+      }
+      for (int s = w; s < S; s += nworkers) brc[s] = scene_gn(s, w);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nworkers; ++w) pool.emplace_back(worker, w);
+    worker(0);
+    for (auto& th : pool) th.join();
   }
+  for (int s = 0; s < S; ++s) {
+    bem_ctx* c = b->sc[s];
+    c->cur = b->st;
+    c->scratch = s == 0 ? nullptr : c0;
+    cudaEventRecord(b->sev[s], b->sst[s]);
+    cudaStreamWaitEvent(b->st, b->sev[s], 0);
+  }
+  for (int s = 0; s < S; ++s)
+    if (brc[s]) return brc[s];
   std::vector<double> L0(S), gn2(S);
   if ((rc = cuda_check(c0, cudaMemcpyAsync(L0.data(), b->sums[0].p, sizeof(double) * S,
                                            cudaMemcpyDeviceToHost, b->st), "loss")) ||

@@ -905,16 +905,18 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) umma::tmem_dealloc(tmem, 256);
 }
 
+// looked up once (a function-local static: initialised once even when several
+// host threads call it first at the same time)
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
+      return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -941,13 +943,11 @@ int make_map(bem_ctx* c, CUtensorMap* m, const void* base, uint64_t k, uint64_t 
 template <int SCH>
 int launch(bem_ctx* c, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& a2,
            const CUtensorMap& b2, const TcArgs& g, dim3 grid) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Scheme<SCH>::SMEM);
-    if (e != cudaSuccess) return cuda_check(c, e, "tc gemm smem attribute");
-    attr = true;
-  }
+  // set once per process (a function-local static; safe when several host
+  // threads launch at the same time)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_tc_gemm<SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, Scheme<SCH>::SMEM);
+  if (attr != cudaSuccess) return cuda_check(c, attr, "tc gemm smem attribute");
   k_tc_gemm<SCH><<<grid, 128, Scheme<SCH>::SMEM, S(c)>>>(a, b, a2, b2, g);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_tc_gemm");
@@ -1020,24 +1020,18 @@ int tc_jrows(bem_ctx* c, int sch, const JLayout& L, int m, int Nb, const void* c
       return cuda_check(c, cudaGetLastError(), "k_tc_jrows_pers");
     };
     if (x3) {
-      static bool attr = false;
-      if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_jrows_pers<true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             Pers<true>::SMEM);
-        if (e != cudaSuccess) return cuda_check(c, e, "persistent J rows smem attribute");
-        attr = true;
-      }
+      // set once per process (a function-local static; safe when several host
+      // threads launch at the same time)
+      static const cudaError_t attr = cudaFuncSetAttribute(
+          k_tc_jrows_pers<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Pers<true>::SMEM);
+      if (attr != cudaSuccess) return cuda_check(c, attr, "persistent J rows smem attribute");
       return run(k_tc_jrows_pers<true>, Pers<true>::SMEM, Pers<true>::BNT);
     }
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_tc_jrows_pers<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           Pers<false>::SMEM);
-      if (e != cudaSuccess) return cuda_check(c, e, "persistent J rows smem attribute");
-      attr = true;
-    }
+    // set once per process (a function-local static; safe when several host
+    // threads launch at the same time)
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_tc_jrows_pers<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Pers<false>::SMEM);
+    if (attr != cudaSuccess) return cuda_check(c, attr, "persistent J rows smem attribute");
     return run(k_tc_jrows_pers<false>, Pers<false>::SMEM, Pers<false>::BNT);
   }
   dim3 grid((rows + BM - 1) / BM, (m + BN - 1) / BN);
@@ -1074,13 +1068,11 @@ int tc_syrk(bem_ctx* c, int sch, const JLayout& L, int m, const void* const* J, 
   int sp = (m + g.k_per_split - 1) / g.k_per_split;
   ProfScope _ps(c, "tc_syrk");
   if (!x3) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_tc_syrk_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           kSySmem);
-      if (e != cudaSuccess) return cuda_check(c, e, "paired Gram smem attribute");
-      attr = true;
-    }
+    // set once per process (a function-local static; safe when several host
+    // threads launch at the same time)
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_tc_syrk_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, kSySmem);
+    if (attr != cudaSuccess) return cuda_check(c, attr, "paired Gram smem attribute");
     g.npairs = syrk_units(g.tiles, g.tiles);
     // the partial sums as one fp32 matrix of splits x 3 x cdim rows, for the
     // epilogue's TMA reductions
