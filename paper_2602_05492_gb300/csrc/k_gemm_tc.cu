@@ -94,7 +94,7 @@ template <int SCH>
 __global__ void __launch_bounds__(128, Scheme<SCH>::X3 ? 1 : 2)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
               const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB2,
-              TcArgs g) {
+              const __grid_constant__ CUtensorMap tP, TcArgs g) {
   constexpr int BK = Scheme<SCH>::BK, PARTS = Scheme<SCH>::PARTS;
   constexpr bool X3 = Scheme<SCH>::X3, TF = Scheme<SCH>::TF32;
   extern __shared__ uint8_t smem_raw[];
@@ -306,11 +306,25 @@ __global__ void __launch_bounds__(128, Scheme<SCH>::X3 ? 1 : 2)
         *reinterpret_cast<uint4*>(fr + ((((cb >> 3) + k) ^ sw) << 2)) = w;
       }
     } else {
-      const int i = ti * BM + r;
-      const int D = g.L.cdim();
-      float* d = g.part + (((size_t)blockIdx.y * 3 + ch) * D + i) * D;
+      // EPI_SYRK: stage the row in box cb / 32 (128 rows x 32 fp32 columns,
+      // 128-byte swizzle) of the idle ring, for the TMA reduction below
+      uint8_t* row = reinterpret_cast<uint8_t*>(fs + (cb >> 5) * (BM * 32)) + r * 128;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) d[tj * BN + cb + j] += v[j];
+      for (int c8 = 0; c8 < 8; ++c8)
+        *reinterpret_cast<float4*>(row + ((c8 ^ (r & 7)) << 4)) =
+            make_float4(v[4 * c8], v[4 * c8 + 1], v[4 * c8 + 2], v[4 * c8 + 3]);
+    }
+  }
+  if (g.mode == EPI_SYRK) {
+    // the block += into this K slice's partial sums (rows of part[slice][ch])
+    umma::fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0 && ok && nk > 0) {
+      const int y = ((int)blockIdx.y * 3 + ch) * g.L.cdim() + ti * BM;
+      for (int k4 = 0; k4 < 4; ++k4)
+        umma::tma_reduce_add_2d(&tP, fs + k4 * (BM * 32), tj * BN + 32 * k4, y);
+      umma::bulk_commit();
+      umma::bulk_wait0();
     }
   }
   if (!X3 && g.mode == EPI_JROWS) {
@@ -940,15 +954,16 @@ int make_map(bem_ctx* c, CUtensorMap* m, const void* base, uint64_t k, uint64_t 
   return BEM_OK;
 }
 
+// tp: the Gram partial sums (EPI_SYRK); any valid map otherwise (not read)
 template <int SCH>
 int launch(bem_ctx* c, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& a2,
-           const CUtensorMap& b2, const TcArgs& g, dim3 grid) {
+           const CUtensorMap& b2, const CUtensorMap& tp, const TcArgs& g, dim3 grid) {
   // set once per process (a function-local static; safe when several host
   // threads launch at the same time)
   static const cudaError_t attr = cudaFuncSetAttribute(
       k_tc_gemm<SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, Scheme<SCH>::SMEM);
   if (attr != cudaSuccess) return cuda_check(c, attr, "tc gemm smem attribute");
-  k_tc_gemm<SCH><<<grid, 128, Scheme<SCH>::SMEM, S(c)>>>(a, b, a2, b2, g);
+  k_tc_gemm<SCH><<<grid, 128, Scheme<SCH>::SMEM, S(c)>>>(a, b, a2, b2, tp, g);
   BEM_LAUNCHED(c);
   return cuda_check(c, cudaGetLastError(), "k_tc_gemm");
 }
@@ -965,7 +980,7 @@ int tc_gemm_store(bem_ctx* c, int M, int N, int K, const void* A, int lda, const
   TcArgs g{};
   g.M = M; g.N = N; g.K = K; g.mode = EPI_STORE; g.D = D; g.ldd = ldd; g.err = c->d_status;
   g.wait_ns = c->wait_ns;
-  return launch<SCH_BF16>(c, ta, tb, ta, tb, g, dim3((M + BM - 1) / BM, (N + BN - 1) / BN));
+  return launch<SCH_BF16>(c, ta, tb, ta, tb, ta, g, dim3((M + BM - 1) / BM, (N + BN - 1) / BN));
 }
 
 // J^T rows: J[rows][m] = Mt[rows][Nb] Phi[m][Nb]^T + F[rows][m].
@@ -1035,7 +1050,7 @@ int tc_jrows(bem_ctx* c, int sch, const JLayout& L, int m, int Nb, const void* c
     return run(k_tc_jrows_pers<false>, Pers<false>::SMEM, Pers<false>::BNT);
   }
   dim3 grid((rows + BM - 1) / BM, (m + BN - 1) / BN);
-  return launch<SCH_TF32X3>(c, ta, tb, ta2, tb2, g, grid);
+  return launch<SCH_TF32X3>(c, ta, tb, ta2, tb2, ta, g, grid);
 }
 
 // CTAs of one K slice of the Gram kernels: bf16 paired units, 3xtf32 single
@@ -1084,8 +1099,11 @@ int tc_syrk(bem_ctx* c, int sch, const JLayout& L, int m, const void* const* J, 
     return cuda_check(c, cudaGetLastError(), "k_tc_syrk_pair");
   }
   dim3 grid(gram_ctas(L, true), sp);
-  if (f32) return launch<SCH_TF32X3>(c, tj, tj, tj2, tj2, g, grid);
-  return launch<SCH_BF16X3>(c, tj, tj, tj2, tj2, g, grid);
+  CUtensorMap tp;
+  if ((rc = make_map(c, &tp, part, L.cdim(), (uint64_t)splits * 3 * L.cdim(), L.cdim(), true)))
+    return rc;
+  if (f32) return launch<SCH_TF32X3>(c, tj, tj, tj2, tj2, tp, g, grid);
+  return launch<SCH_BF16X3>(c, tj, tj, tj2, tj2, tp, g, grid);
 }
 
 // K slices per block pair: as many as fill the resident CTA slots in one
