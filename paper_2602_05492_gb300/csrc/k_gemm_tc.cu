@@ -8,24 +8,24 @@
 // 128-column fp32 accumulator in TMEM and releases ring slots with
 // tcgen05.commit, and all four warps drain the accumulator (warp w owns TMEM
 // lanes 32w..32w+31) through the epilogue of the launch mode.
-// Two operand schemes:
-//   bf16   one kind::f16 product, 64-element slabs, K = 16 per instruction
-//   3xtf32 fp32 operands stored as tf32 hi + lo parts (x = hi + lo, both
-//          rounded to tf32); three kind::tf32 products hi.hi + hi.lo + lo.hi
-//          accumulate into the same TMEM tile (32-element slabs, K = 8)
-// Epilogues:
-//   EPI_STORE  D -> fp32 [M][N]
-//   EPI_JROWS  J^T = M_c^T Phi^T + F^T: D + F (fp32) -> bf16 [M][N], or the
-//              tf32 hi/lo pair of D + F in the 3xtf32 scheme
-//   EPI_SYRK   one upper-triangular 128 x 128 block of J_c^T J_c over a K
-//              slice of samples, added to that slice's fp32 partial sum
-//              (3xtf32; the bf16 Gram blocks run in k_tc_syrk_pair, two
-//              blocks per CTA that share an operand slab)
-// The bf16 J rows run in a persistent, warp-specialised variant
+// Three operand schemes:
+//   bf16    one kind::f16 product, 64-element slabs, K = 16 per instruction
+//   bf16x3  (compensated bf16) bf16 hi + lo parts of every operand (x = hi +
+//           lo, lo the rounded rest); three kind::f16 products lo.hi + hi.lo
+//           + hi.hi accumulate into the same TMEM tile
+//   3xtf32  fp32 operands stored as tf32 hi + lo parts; three kind::tf32
+//           products (32-element slabs, K = 8)
+// Epilogues of the per-tile kernel k_tc_gemm:
+//   EPI_STORE  D -> fp32 [M][N] (bem_gemm_bf16)
+//   EPI_JROWS  J^T = M_c^T Phi^T + F^T: the tf32 hi/lo pair of D + F (3xtf32)
+//   EPI_SYRK   one 128 x 128 block of J_c^T J_c over a K slice of samples,
+//              added to that slice's fp32 partial sums by TMA reductions
+//              (bf16x3 and 3xtf32; the bf16 Gram blocks run in
+//              k_tc_syrk_pair, two blocks per CTA that share an operand slab)
+// The bf16 and bf16x3 J rows run in a persistent, warp-specialised kernel
 // (k_tc_jrows_pers): one CTA per SM, a producer warp, an MMA warp and eight
-// epilogue warps, 128 x 256 tiles (M = 128, N = 256 MMAs), with two
-// 256-column TMEM accumulators so that a tile's epilogue overlaps the next
-// tile's MMAs.
+// epilogue warps, with two TMEM accumulators so that a tile's epilogue
+// overlaps the next tile's MMAs, and TMA loads and stores in the epilogue.
 // Every wait is bounded.  The pipeline waits (a ring slot, a TMEM buffer)
 // give up after the context's limit (bem_set_wait_limit, one second by
 // default); the waits that guard work already in flight (copies landing in
@@ -220,30 +220,9 @@ __global__ void __launch_bounds__(128, Scheme<SCH>::X3 ? 1 : 2)
   umma::fence_after();
   const int r = warp * 32 + lane;     // row of the tile owned by this thread
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-  // bf16 J rows: the stage ring is free once the accumulator is complete;
-  // F's 128 x 128 fp32 tile is copied there with cp.async, all 16-byte
-  // chunks in flight at once.  Row rr holds 32 chunks of 16 bytes; logical
-  // chunk cc sits at position cc ^ (rr & 7), so that the per-row reads below
-  // (lane = row) and the in-place bf16 writes are free of bank conflicts.
+  // the stage ring is free once the accumulator is complete (EPI_SYRK stages
+  // its boxes there)
   float* fs = reinterpret_cast<float*>(smem);
-  if (!X3 && g.mode == EPI_JROWS) {
-    for (int e = threadIdx.x; e < BM * (BN / 4); e += 128) {
-      const int rr = e / (BN / 4), cc = e % (BN / 4);
-      const int row = arow + rr, col = brow + cc * 4;
-      float* d = fs + rr * BN + ((cc ^ (rr & 7)) << 2);
-      if (row < g.M && col + 3 < g.N) {
-        umma::cp_async16(d, g.F + (size_t)row * g.ldf + col);
-      } else {
-        const float* src = g.F + (size_t)row * g.ldf + col;
-        d[0] = (row < g.M && col < g.N) ? src[0] : 0.f;
-        d[1] = (row < g.M && col + 1 < g.N) ? src[1] : 0.f;
-        d[2] = (row < g.M && col + 2 < g.N) ? src[2] : 0.f;
-        d[3] = 0.f;
-      }
-    }
-    umma::cp_async_wait_all();
-    __syncthreads();
-  }
 #pragma unroll 1
   for (int cb = 0; cb < BN; cb += 32) {
     float v[32];
@@ -279,32 +258,6 @@ __global__ void __launch_bounds__(128, Scheme<SCH>::X3 ? 1 : 2)
             }
           }
       }
-    } else if (g.mode == EPI_JROWS) {
-      // F row r of the tile was staged in shared memory (fs, swizzled
-      // 16-byte chunks); this chunk's bf16 result goes to the front of the
-      // same row, bf16 chunk k (8 values) at position k ^ (r & 7): those
-      // positions hold F chunks of this or an earlier 32-column block only,
-      // already read
-      float* fr = fs + r * BN;
-      const int sw = r & 7;
-      float f[32];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float4 q = *reinterpret_cast<const float4*>(fr + ((((cb >> 2) + k) ^ sw) << 2));
-        f[4 * k] = q.x; f[4 * k + 1] = q.y; f[4 * k + 2] = q.z; f[4 * k + 3] = q.w;
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        uint4 w;
-        uint32_t* wp = &w.x;
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * k + 2 * h] + f[8 * k + 2 * h],
-                                                          v[8 * k + 2 * h + 1] + f[8 * k + 2 * h + 1]);
-          wp[h] = *reinterpret_cast<const uint32_t*>(&b2);
-        }
-        *reinterpret_cast<uint4*>(fr + ((((cb >> 3) + k) ^ sw) << 2)) = w;
-      }
     } else {
       // EPI_SYRK: stage the row in box cb / 32 (128 rows x 32 fp32 columns,
       // 128-byte swizzle) of the idle ring, for the TMA reduction below
@@ -325,27 +278,6 @@ __global__ void __launch_bounds__(128, Scheme<SCH>::X3 ? 1 : 2)
         umma::tma_reduce_add_2d(&tP, fs + k4 * (BM * 32), tj * BN + 32 * k4, y);
       umma::bulk_commit();
       umma::bulk_wait0();
-    }
-  }
-  if (!X3 && g.mode == EPI_JROWS) {
-    __syncthreads();
-    // row rr of the bf16 tile sits at the front of fs row rr (bf16 chunk k
-    // at position k ^ (rr & 7)): one warp writes a 256-byte row per step,
-    // 8 bytes per lane
-    for (int rr = warp; rr < BM; rr += 4) {
-      const int row = arow + rr;
-      if (row >= g.M) continue;
-      const int col = brow + lane * 4;
-      const char* src = reinterpret_cast<const char*>(fs + rr * BN) +
-                        ((((lane >> 1) ^ (rr & 7)) << 4) | ((lane & 1) << 3));
-      __nv_bfloat16* dst = g.J + (size_t)row * g.ldj + col;
-      if (col + 3 < g.N) {
-        *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(src);
-      } else {
-        const __nv_bfloat16* sb = reinterpret_cast<const __nv_bfloat16*>(src);
-        for (int q = 0; q < 4; ++q)
-          if (col + q < g.N) dst[q] = sb[q];
-      }
     }
   }
   umma::fence_before();

@@ -1,6 +1,7 @@
 // sm_100-family tensor-core building blocks written as inline PTX:
-// mbarriers with bounded waits, 2-D TMA loads, tcgen05 MMA / commit / TMEM
-// allocation and loads, shared-memory and instruction descriptors.
+// mbarriers with bounded waits, 2-D TMA loads, stores and reductions, 1-D bulk
+// copies and bulk-group waits, the async-proxy fence, tcgen05 MMA / commit /
+// TMEM allocation and loads, shared-memory and instruction descriptors.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -199,17 +200,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
       : "memory");
-}
-
-// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
-               : "memory");
-}
-
-// wait for every cp.async issued by this thread
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // 32 consecutive fp32 columns of this warp's 32 TMEM lanes.
