@@ -260,6 +260,46 @@ __device__ __forceinline__ LayerVals<double> layer_values_near(const Frame<doubl
   return v;
 }
 
+// The layer values and frame partials of a near pair in double (the
+// adjoint's near field): the integrals and derivatives of layer_grad, with
+// both logarithms from dlog (log(q2/q1) as their difference), 1/h' from one
+// reciprocal square root and 1/q1, 1/q2 from one reciprocal of q1 q2.
+template <bool SAME>
+__device__ __forceinline__ LayerGrad<double> layer_grad_near(const Frame<double>& f, double ec2,
+                                                             double ed2) {
+  LayerGrad<double> g;
+  const double tt = f.t1 * f.t2, hh = f.h * f.h;
+  // single layer, eps_c
+  const double hc2 = hh + ec2;
+  const double rc = rsqrt(hc2);
+  const double hc = hc2 * rc;
+  const double q1 = fma(f.t1, f.t1, hc2), q2 = fma(f.t2, f.t2, hc2);
+  const double phic = atan2(hc * f.L, hc2 + tt);
+  const double lg1 = dlog(q1, g_dlog_tab), lg2 = dlog(q2, g_dlog_tab);
+  g.S = -(f.L * (lg2 - 2.0) + f.t1 * (lg2 - lg1) + 2.0 * hc * phic) * kInv4Pi;
+  g.S_t1 = lg1 * kInv4Pi;
+  g.S_t2 = -lg2 * kInv4Pi;
+  g.S_h = -(f.h * rc) * phic * kInv2Pi;
+  // double layer, eps_d
+  double hd2, rd, phid, r1, r2;
+  if constexpr (SAME) {
+    hd2 = hc2; rd = rc; phid = phic; r1 = q1; r2 = q2;
+  } else {
+    hd2 = hh + ed2;
+    rd = rsqrt(hd2);
+    phid = atan2(hd2 * rd * f.L, hd2 + tt);
+    r1 = fma(f.t1, f.t1, hd2);
+    r2 = fma(f.t2, f.t2, hd2);
+  }
+  const double ir12 = 1.0 / (r1 * r2);
+  const double ir1 = r2 * ir12, ir2 = r1 * ir12;
+  g.Dl = -(f.h * rd) * phid * kInv2Pi;
+  g.D_t1 = f.h * ir1 * kInv2Pi;
+  g.D_t2 = -f.h * ir2 * kInv2Pi;
+  g.D_h = -(ed2 * phid * rd - hh * f.L * (hd2 - tt) * ir12) * (rd * rd) * kInv2Pi;
+  return g;
+}
+
 // SUBF: the sum of (double - float) pair values instead, the float value
 // being the one the F rows hold (frame_rn, layer_grad_hat); added to the
 // float handle term F w it gives the same near-field treatment as the
@@ -311,7 +351,7 @@ __device__ __forceinline__ void near_adj_pair(const Panel<double>& q, float x, f
                                               double r1, double r2, double ec2, double ed2,
                                               double* acc) {
   Frame<double> f = frame(q, double(x), double(y));
-  LayerGrad<double> g = layer_grad(f, ec2, ed2, SAME);
+  const LayerGrad<double> g = layer_grad_near<SAME>(f, ec2, ed2);
   const double al = -(r0 * q.wd[0] + r1 * q.wd[1] + r2 * q.wd[2]);
   const double be = r0 * q.wc[0] + r1 * q.wc[1] + r2 * q.wc[2];
   const double gt1 = al * g.D_t1 + be * g.S_t1;
@@ -387,6 +427,15 @@ __global__ void __launch_bounds__(32 * kNearWarps)
     for (int k = 0; k < 11; ++k) out[(size_t)p * 11 + k] = acc[k];
 }
 
+// the table of dlog on this context's device, built before its first use
+static void dlog_ready(bem_ctx* c) {
+  if (!c->dlog_ready) {
+    k_dlog_init<<<1, kDlogTab, 0, S(c)>>>();
+    BEM_LAUNCHED(c);
+    c->dlog_ready = true;
+  }
+}
+
 static int near_forward_t(bem_ctx* c, int64_t n, const float* xy, double* out, bool subf) {
   int rc;
   Bins b;
@@ -402,11 +451,7 @@ static int near_forward_t(bem_ctx* c, int64_t n, const float* xy, double* out, b
     b.items = (int*)((char*)c->nearP.p + sizeof(int) * ((size_t)ncell + 1 + ncell + nb + 1));
   }
 
-  if (!c->dlog_ready) {
-    k_dlog_init<<<1, kDlogTab, 0, S(c)>>>();
-    BEM_LAUNCHED(c);
-    c->dlog_ready = true;
-  }
+  dlog_ready(c);
   const float near2 = (float)(c->opts.near_factor * c->opts.near_factor);
   const double ec2 = c->opts.eps_c * c->opts.eps_c, ed2 = c->opts.eps_d * c->opts.eps_d;
   ProfScope _ps(c, "k_near_forward");
@@ -436,6 +481,7 @@ int near_adjoint(bem_ctx* c, int64_t n, const float* xy, const float* w, double*
   const int P = c->sc.P;
   const float nf = (float)c->opts.near_factor, near2 = nf * nf;
   const double ec2 = c->opts.eps_c * c->opts.eps_c, ed2 = c->opts.eps_d * c->opts.eps_d;
+  dlog_ready(c);
   ProfScope _ps(c, "k_near_adjoint");
   if (c->opts.eps_c == c->opts.eps_d)
     k_near_adjoint<true><<<(P + kNearWarps - 1) / kNearWarps, 32 * kNearWarps, 0, S(c)>>>(
@@ -467,11 +513,7 @@ extern "C" int bem_dlog_eval(bem_ctx* c, int64_t n, const double* x, double* out
   int rc;
   if ((rc = ctx_set_device(c))) return rc;
   c->cur = (cudaStream_t)stream;
-  if (!c->dlog_ready) {
-    k_dlog_init<<<1, kDlogTab, 0, S(c)>>>();
-    BEM_LAUNCHED(c);
-    c->dlog_ready = true;
-  }
+  dlog_ready(c);
   if (n > 0) {
     k_dlog_eval<<<(unsigned)((n + 255) / 256), 256, 0, S(c)>>>(n, x, out_lib, out_ref);
     BEM_LAUNCHED(c);

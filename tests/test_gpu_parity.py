@@ -486,6 +486,19 @@ def test_mixed_all_pairs_near(cfg1):
     assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-5
 
 
+def test_mixed_all_pairs_near_adjoint_first(cfg1):
+    """The adjoint's double near field on a fresh context (its logarithm table
+    built by the adjoint itself, before any evaluation): every handle pair
+    near, gradient against the oracle."""
+    sc, xy, target, mean, o = cfg1
+    sub = xy[1::8]
+    m = _ctx(sc, mean, _bg().BEM_MIXED, near_factor=1000.0)
+    r = np.random.default_rng(4).normal(size=(sub.shape[0], 3)).astype(np.float32)
+    g = m.vjp(_t(sub, torch.float32), _t(r, torch.float32)).cpu().numpy()
+    want = o.grad(sc.theta_init, sub, r.astype(np.float64))
+    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-5
+
+
 def test_mixed_without_near_field(cfg1):
     sc, xy, target, mean, o = cfg1
     m = _ctx(sc, mean, _bg().BEM_MIXED, near_factor=0.0)
