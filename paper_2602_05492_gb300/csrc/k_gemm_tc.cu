@@ -297,13 +297,15 @@ __global__ void __launch_bounds__(128, Scheme<SCH>::X3 ? 1 : 2)
 // the handle part of the gradient) overlaps the MMAs of the next.  One
 // 256-sample tile per MMA halves the operand bytes per output of the A slabs
 // against 128-sample tiles, the share of the L2 traffic that bounds this
-// contraction.  The epilogue moves its data with TMA as well: one thread
-// loads a pass's F rows as four 128-row x 32-column boxes (128-byte
-// swizzle: row r at 128 r bytes, 16-byte chunk c at position c ^ (r & 7))
-// and its residuals by one bulk copy, and stores the pass's J^T rows as two
-// 64-column bf16 boxes in the same swizzle.  The bf16 rows of column half h
-// are packed in place over F box 2 h, which only that half's warps read,
-// and each thread reads its row of both of its boxes before it writes there.
+// contraction.  The epilogue runs as two independent halves of four warps,
+// half h owning the columns 64 h .. 64 h + 63 of every pass, with their own
+// load barrier, named barrier and leader thread, and it moves its data with
+// TMA as well: the leader loads the half's F rows of a pass as two 128-row x
+// 32-column boxes (128-byte swizzle: row r at 128 r bytes, 16-byte chunk c at
+// position c ^ (r & 7)) and its residuals by one bulk copy, and stores the
+// half's J^T rows as a 64-column bf16 box in the same swizzle.  The bf16 rows
+// of half h are packed in place over F box 2 h, which only that half's warps
+// read, and each thread reads its row of the box before it writes there.
 // Compensated bf16 (BF16X3) runs the same kernel on 128-sample tiles: a
 // stage holds the hi and lo parts of the A and B slabs (64 KB, two stages),
 // each K step issues the three products lo.hi, hi.lo, hi.hi into one
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(kPersThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* fs = reinterpret_cast<float*>(smem + STAGES * STAGE);         // 4 boxes [BM][32] F rows
-  float* rs = fs + BM * BN;                                            // [BN][3] residuals
+  float* rs = fs + BM * BN;                                            // [2][64][3] residuals
   uint64_t* full = reinterpret_cast<uint64_t*>(rs + 3 * BN);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
