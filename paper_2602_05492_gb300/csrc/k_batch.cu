@@ -9,11 +9,12 @@
 //      residuals and loss partials (k_field_batch_f32);
 //   B  per scene: H and g = (1/n) J^T r from the J rows (tensor cores);
 //   C  per scene and trial: the damped KKT solve, theta_t = theta + delta,
-//      projection, panels, boundary solution and near sums of theta_t.  The
-//      scenes are independent here and their work is chains of small,
-//      latency-bound kernels with host checks (the solves' refinement), so
-//      each scene runs on its own stream, driven by one of several host
-//      threads, and the chains of different scenes overlap on the GPU;
+//      projection, panels, boundary solution and near sums of theta_t.
+//   The scenes are independent in B and C, so each scene runs them on its
+//      own stream, right after one another, driven by one of eight host
+//      threads (worker w takes scenes w, w + 8, ...): the passes and the
+//      chains of small, latency-bound kernels with host checks (the solves'
+//      refinement) of different scenes overlap on the GPU;
 //   D  one persistent launch over the sample tiles of all scenes: the trial
 //      losses, the (up to four) trials of a scene on the same tile so that
 //      they share the boundary angles of its points, which do not depend on
@@ -25,11 +26,10 @@
 // autotuner times the tile shapes (128 or 256 points per tile) and CTAs per
 // SM on the real job list and keeps the fastest.
 //
-// All scenes run on one internal stream, ordered after the caller's stream
-// and before its next work; the Gauss-Newton chunk buffers of scene 0 serve
-// every scene.
+// The batch runs on an internal stream (and, in B and C, one stream per
+// scene), ordered after the caller's stream and before its next work; in B
+// the Gauss-Newton chunk buffers of scene w serve the scenes of worker w.
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <string>
 #include <thread>
@@ -315,10 +315,11 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
   bind_partials(b, 0);
   if ((rc = upload(b, 0)) || (rc = eval_graph(b, 0))) return rc;
   // ---- B: H and g per scene, the scenes on their own streams (after phase
-  // A) from several host threads.  Worker w takes the scenes w, w + K, ...
-  // one after another and lends them scene w's chunk buffers (the J-row
-  // pass ends with a synchronisation of the scene's stream, so a worker's
-  // scenes never use those buffers at the same time).
+  // A) from several host threads, each scene's trials (phase C) right after
+  // its pass.  Worker w takes the scenes w, w + K, ... one after another and
+  // lends them scene w's chunk buffers (the J-row pass ends with a
+  // synchronisation of the scene's stream, so a worker's scenes never use
+  // those buffers at the same time; the trials use none of them).
   if ((rc = cuda_check(c0, cudaEventRecord(b->ev_b, b->st), "event"))) return rc;
   for (int s = 0; s < S; ++s)
     if ((rc = cuda_check(c0, cudaStreamWaitEvent(b->sst[s], b->ev_b, 0), "event"))) return rc;
@@ -349,45 +350,12 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
     }
     return rc;
   };
-  {
-    auto worker = [&](int w) {
-      // the runtime's current device is per host thread
-      if (cudaSetDevice(c0->device) != cudaSuccess) {
-        for (int s = w; s < S; s += nworkers) brc[s] = BEM_ECUDA;
-        return;
-      }
-      for (int s = w; s < S; s += nworkers) brc[s] = scene_gn(s, w);
-    };
-    std::vector<std::thread> pool;
-    for (int w = 1; w < nworkers; ++w) pool.emplace_back(worker, w);
-    worker(0);
-    for (auto& th : pool) th.join();
-  }
-  for (int s = 0; s < S; ++s) {
-    bem_ctx* c = b->sc[s];
-    c->cur = b->st;
-    c->scratch = s == 0 ? nullptr : c0;
-    cudaEventRecord(b->sev[s], b->sst[s]);
-    cudaStreamWaitEvent(b->st, b->sev[s], 0);
-  }
-  for (int s = 0; s < S; ++s)
-    if (brc[s]) return brc[s];
-  std::vector<double> L0(S), gn2(S);
-  if ((rc = cuda_check(c0, cudaMemcpyAsync(L0.data(), b->sums[0].p, sizeof(double) * S,
-                                           cudaMemcpyDeviceToHost, b->st), "loss")) ||
-      (rc = cuda_check(c0, cudaMemcpyAsync(gn2.data(), b->gn2.p, sizeof(double) * S,
-                                           cudaMemcpyDeviceToHost, b->st), "norm")) ||
-      (rc = cuda_check(c0, cudaStreamSynchronize(b->st), "sync")))
-    return rc;
-  // ---- C: trials, every scene on its own stream (after phase B), several
-  // host threads taking the scenes in turn
+  // ---- C, in the same workers: each scene's trials (damped solves, trial
+  // geometry, boundary values and near-field sums) on its stream right after
+  // its Gauss-Newton pass, so that they overlap the other scenes' passes
   std::vector<double> used((size_t)S * T, 0.0);
   std::vector<char> ok((size_t)S * T, 0);
   std::vector<BatchJob> trial_jobs((size_t)S * T);
-  if ((rc = cuda_check(c0, cudaEventRecord(b->ev_b, b->st), "event"))) return rc;
-  for (int s = 0; s < S; ++s)
-    if ((rc = cuda_check(c0, cudaStreamWaitEvent(b->sst[s], b->ev_b, 0), "event"))) return rc;
-  std::vector<int> src(S, BEM_OK);
   auto scene_trials = [&](int s) -> int {
     int rc = BEM_OK;
     bem_ctx* c = b->sc[s];
@@ -436,25 +404,38 @@ int batch_lm(bem_batch* b, const int64_t* n, const void* const* xy, const void* 
     return rc;
   };
   {
-    const int nthreads = std::min(S, 8);
-    std::atomic<int> next(0);
-    auto worker = [&]() {
+    auto worker = [&](int w) {
       // the runtime's current device is per host thread
-      if (cudaSetDevice(c0->device) != cudaSuccess) return;
-      for (int s = next++; s < S; s = next++) src[s] = scene_trials(s);
+      if (cudaSetDevice(c0->device) != cudaSuccess) {
+        for (int s = w; s < S; s += nworkers) brc[s] = BEM_ECUDA;
+        return;
+      }
+      for (int s = w; s < S; s += nworkers) {
+        brc[s] = scene_gn(s, w);
+        if (brc[s] == BEM_OK) brc[s] = scene_trials(s);
+      }
     };
     std::vector<std::thread> pool;
-    for (int k = 1; k < nthreads; ++k) pool.emplace_back(worker);
-    worker();
+    for (int w = 1; w < nworkers; ++w) pool.emplace_back(worker, w);
+    worker(0);
     for (auto& th : pool) th.join();
   }
   for (int s = 0; s < S; ++s) {
-    b->sc[s]->cur = b->st;
+    bem_ctx* c = b->sc[s];
+    c->cur = b->st;
+    c->scratch = s == 0 ? nullptr : c0;
     cudaEventRecord(b->sev[s], b->sst[s]);
     cudaStreamWaitEvent(b->st, b->sev[s], 0);
   }
   for (int s = 0; s < S; ++s)
-    if (src[s]) return src[s];
+    if (brc[s]) return brc[s];
+  std::vector<double> L0(S), gn2(S);
+  if ((rc = cuda_check(c0, cudaMemcpyAsync(L0.data(), b->sums[0].p, sizeof(double) * S,
+                                           cudaMemcpyDeviceToHost, b->st), "loss")) ||
+      (rc = cuda_check(c0, cudaMemcpyAsync(gn2.data(), b->gn2.p, sizeof(double) * S,
+                                           cudaMemcpyDeviceToHost, b->st), "norm")) ||
+      (rc = cuda_check(c0, cudaStreamSynchronize(b->st), "sync")))
+    return rc;
   // ---- D: one persistent launch over all scenes and trials: with 2 to
   // kJobTrials trials one job per scene evaluates them all (a skipped
   // trial points at a factored one's data; its loss is not used), else one
