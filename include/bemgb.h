@@ -300,6 +300,20 @@ int lm_step_split(bem_ctx *ctx, int64_t n, const void *xy, const void *target, i
                   const void *xy_h, int n_trials, const double *lambdas, lm_result *out,
                   void *stream);
 
+/* lm_step on samples and targets in host memory (Eq. (optimstep), as
+ * lm_step): the call copies them into device buffers that the context owns
+ * (kept for the next call), on a copy stream of its own, the samples first
+ * and then the targets in the chunks of the Gauss-Newton pass, and the pass
+ * starts on each chunk as soon as its targets have arrived, so that the
+ * copies overlap the step's work.  Page-locked host memory lets the copies
+ * run alongside; pageable memory gives the same results with the copies
+ * taken before the step.
+ *   xy: host [n][2], target: host [n][3] (sample type: float in BEM_MIXED,
+ *   double in BEM_FP64); out: host.  The host buffers may be reused once the
+ *   call returns.  Synchronises `stream`.  Errors: as lm_step. */
+int lm_step_host(bem_ctx *ctx, int64_t n, const void *xy, const void *target, int n_trials,
+                 const double *lambdas, lm_result *out, void *stream);
+
 /* D[M][N] = A[M][K] B[N][K]^T on the tensor cores (tcgen05, fp32
  * accumulate): the contraction behind bem_jtj in BEM_MIXED contexts with
  * BEM_JTJ_BF16, exposed for validation.  A, B: device bf16, row-major, row

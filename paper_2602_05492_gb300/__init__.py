@@ -82,6 +82,7 @@ def _load():
         "bem_jtj": (ci, [vp, i64, vp, vp, vp]),
         "lm_step": (ci, [vp, i64, vp, vp, ci, dp, ctypes.POINTER(lm_result), vp]),
         "lm_step_split": (ci, [vp, i64, vp, vp, i64, vp, ci, dp, ctypes.POINTER(lm_result), vp]),
+        "lm_step_host": (ci, [vp, i64, vp, vp, ci, dp, ctypes.POINTER(lm_result), vp]),
         "bem_sizes": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]),
         "bem_boundary_values": (ci, [vp, dp, vp]),
         "bem_launch_count": (i64, [vp]),
@@ -126,7 +127,7 @@ EXPORTED = [
     "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors", "lm_step_split",
     "bem_set_boundary", "bem_setup_segments", "bem_set_regularizers", "bem_prune",
     "bem_init_segments", "bem_gram_unit", "bem_alloc_count", "bem_set_wait_limit",
-    "bem_gn_products", "bem_pipe_peak",
+    "bem_gn_products", "bem_pipe_peak", "lm_step_host",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -340,6 +341,33 @@ class BEM:
         r = lm_result()
         self._check(_lib.lm_step(self.h, xy.shape[0], _ptr(xy), _ptr(target), len(lam), _dp(lam),
                                  ctypes.byref(r), _stream(stream)))
+        return dict(loss_before=r.loss_before, loss_after=r.loss_after, accepted=bool(r.accepted),
+                    best_trial=r.best_trial, lambda_next=r.lambda_next, grad_norm=r.grad_norm)
+
+    def _host_samples(self, t, cols):
+        """Pointer and row count of a host array or CPU tensor [n, cols] of
+        the sample type, C-contiguous."""
+        import torch
+        if isinstance(t, torch.Tensor):
+            assert not t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and \
+                t.dim() == 2 and t.shape[1] == cols, \
+                f"expected a contiguous CPU {self.dtype} tensor [n, {cols}]"
+            return ctypes.c_void_p(t.data_ptr()), t.shape[0]
+        want = np.float64 if self.dtype == torch.float64 else np.float32
+        assert isinstance(t, np.ndarray) and t.dtype == want and t.flags.c_contiguous and \
+            t.ndim == 2 and t.shape[1] == cols, f"expected a C-contiguous {want.__name__} array [n, {cols}]"
+        return ctypes.c_void_p(t.ctypes.data), t.shape[0]
+
+    def lm_step_host(self, xy, target, lambdas, stream=None) -> dict:
+        """lm_step on host samples and targets (numpy arrays or CPU tensors;
+        page-locked memory lets the library's copies overlap the step)."""
+        px, n = self._host_samples(xy, 2)
+        pt, nt = self._host_samples(target, 3)
+        assert n == nt, "xy and target must have the same number of rows"
+        lam = np.ascontiguousarray(np.atleast_1d(lambdas), np.float64)
+        r = lm_result()
+        self._check(_lib.lm_step_host(self.h, n, px, pt, len(lam), _dp(lam), ctypes.byref(r),
+                                      _stream(stream)))
         return dict(loss_before=r.loss_before, loss_after=r.loss_after, accepted=bool(r.accepted),
                     best_trial=r.best_trial, lambda_next=r.lambda_next, grad_norm=r.grad_norm)
 

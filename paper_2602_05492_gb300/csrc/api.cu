@@ -306,8 +306,13 @@ void bem_destroy(bem_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   DevBuf* bufs[] = {&c->part, &c->part2, &c->loss, &c->gpart, &c->jrow, &c->phi, &c->Hc, &c->Mc,
                     &c->Dfc, &c->Fg, &c->lmK, &c->lmL, &c->lmLt, &c->lmW, &c->H, &c->g, &c->rend,
-                    &c->tcJ, &c->tcPart, &c->tcMt, &c->nearP, &c->nearS, &c->nearF, &c->gwork};
+                    &c->tcJ, &c->tcPart, &c->tcMt, &c->nearP, &c->nearS, &c->nearF, &c->gwork,
+                    &c->regw, &c->hin_xy, &c->hin_t};
   for (DevBuf* b : bufs) free_buf(*b);
+  if (c->hin_stream) cudaStreamDestroy(c->hin_stream);
+  if (c->hin_start) cudaEventDestroy(c->hin_start);
+  if (c->hin_xy_ready) cudaEventDestroy(c->hin_xy_ready);
+  for (cudaEvent_t e : c->hin_t_ready) cudaEventDestroy(e);
   delete c;
 }
 
@@ -776,6 +781,63 @@ int lm_step_split(bem_ctx* c, int64_t n, const void* xy, const void* target, int
                   void* stream) {
   if (c && !xy_h) return fail(c, BEM_EINVAL, "lm_step_split: xy_h is NULL");
   return lm_step_impl(c, n, xy, target, n_h, xy_h, n_trials, lambdas, out, stream);
+}
+
+int lm_step_host(bem_ctx* c, int64_t n, const void* xy, const void* target, int n_trials,
+                 const double* lambdas, lm_result* out, void* stream) {
+  if (!c) return BEM_EINVAL;
+  if (n <= 0 || !xy || !target) return fail(c, BEM_EINVAL, "lm_step_host: bad arguments");
+  int rc;
+  if ((rc = need_ready(c)) || (rc = set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  const size_t es = c->opts.precision == BEM_FP64 ? 8 : 4;
+  if ((rc = grow(c, c->hin_xy, es * 2 * (size_t)n)) || (rc = grow(c, c->hin_t, es * 3 * (size_t)n)))
+    return rc;
+  const int64_t chunk = gn_chunk_tc(c, n);
+  const int nchunks = (int)((n + chunk - 1) / chunk);
+  if (!c->hin_stream &&
+      (rc = cuda_check(c, cudaStreamCreateWithFlags(&c->hin_stream, cudaStreamNonBlocking), "stream")))
+    return rc;
+  if (!c->hin_start &&
+      ((rc = cuda_check(c, cudaEventCreateWithFlags(&c->hin_start, cudaEventDisableTiming), "event")) ||
+       (rc = cuda_check(c, cudaEventCreateWithFlags(&c->hin_xy_ready, cudaEventDisableTiming), "event"))))
+    return rc;
+  while ((int)c->hin_t_ready.size() < nchunks) {
+    cudaEvent_t e;
+    if ((rc = cuda_check(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event"))) return rc;
+    c->hin_t_ready.push_back(e);
+  }
+  // the copies start once the work queued before this call (which may still
+  // read the device copies) is done: the samples first, then the targets
+  // chunk by chunk, each marked by its event
+  char* dxy = (char*)c->hin_xy.p;
+  char* dt = (char*)c->hin_t.p;
+  if ((rc = cuda_check(c, cudaEventRecord(c->hin_start, S(c)), "record")) ||
+      (rc = cuda_check(c, cudaStreamWaitEvent(c->hin_stream, c->hin_start, 0), "wait")) ||
+      (rc = cuda_check(c, cudaMemcpyAsync(dxy, xy, es * 2 * (size_t)n, cudaMemcpyHostToDevice,
+                                          c->hin_stream), "copy xy")) ||
+      (rc = cuda_check(c, cudaEventRecord(c->hin_xy_ready, c->hin_stream), "record")))
+    return rc;
+  for (int k = 0; k < nchunks; ++k) {
+    const int64_t s0 = (int64_t)k * chunk, m = std::min<int64_t>(chunk, n - s0);
+    if ((rc = cuda_check(c, cudaMemcpyAsync(dt + es * 3 * (size_t)s0, (const char*)target + es * 3 * (size_t)s0,
+                                            es * 3 * (size_t)m, cudaMemcpyHostToDevice, c->hin_stream),
+                         "copy target")) ||
+        (rc = cuda_check(c, cudaEventRecord(c->hin_t_ready[k], c->hin_stream), "record")))
+      break;
+  }
+  // the one-pass Gauss-Newton pass consumes the targets chunk by chunk as
+  // they arrive; every other path waits for all of them first
+  if (!rc) {
+    c->hin_on = jtj_fuses_eval(c);
+    if (!c->hin_on)
+      rc = cuda_check(c, cudaStreamWaitEvent(S(c), c->hin_t_ready[nchunks - 1], 0), "wait");
+  }
+  if (!rc) rc = lm_step_impl(c, n, dxy, dt, 0, nullptr, n_trials, lambdas, out, stream);
+  c->hin_on = false;
+  // the caller may reuse its host buffers once this returns
+  const int rc2 = cuda_check(c, cudaStreamSynchronize(c->hin_stream), "sync");
+  return rc ? rc : rc2;
 }
 
 int bem_gemm_bf16(bem_ctx* c, int M, int N, int K, const void* A, int lda, const void* B, int ldb,

@@ -104,6 +104,16 @@ struct bem_ctx {
   // taken from this context: a batch of scenes processed one after another
   // on one stream shares them.
   bem_ctx* scratch = nullptr;
+  // Host inputs of lm_step_host: their device copies, the copy stream, and
+  // the events that mark the samples (all of them) and each Gauss-Newton
+  // chunk's targets as arrived.  While hin_on is set, the Gauss-Newton pass
+  // waits on those events before it first reads the samples and before each
+  // chunk reads its targets.
+  bem::DevBuf hin_xy, hin_t;
+  cudaStream_t hin_stream = nullptr;
+  cudaEvent_t hin_start = nullptr, hin_xy_ready = nullptr;
+  std::vector<cudaEvent_t> hin_t_ready;
+  bool hin_on = false;
 };
 
 namespace bem {
@@ -150,6 +160,12 @@ int fail(bem_ctx* c, int code, const std::string& msg);
 int cuda_check(bem_ctx* c, cudaError_t e, const char* what);
 int grow(bem_ctx* c, DevBuf& b, size_t bytes);
 inline cudaStream_t S(bem_ctx* c) { return c->cur; }
+
+// Samples per chunk of the tensor-core Gauss-Newton pass over n samples
+inline int64_t gn_chunk_tc(const bem_ctx* c, int64_t n) {
+  const int64_t ch = c->opts.gn_chunk > 0 ? c->opts.gn_chunk : 262144;
+  return n < 1 ? 1 : (n < ch ? n : ch);
+}
 
 // ---- context helpers (api.cu) --------------------------------------------------
 int ctx_set_device(bem_ctx* c);

@@ -782,8 +782,7 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
     BEM_LAUNCHED(c);
   }
   // per-chunk buffers: Phi [m][Nb], F^T f32 [rows][ld], J^T [rows][ld]
-  const int64_t chunk = std::min<int64_t>(std::max<int64_t>(n, 1),
-                                          c->opts.gn_chunk > 0 ? c->opts.gn_chunk : 262144);
+  const int64_t chunk = gn_chunk_tc(c, n);
   const int nchunks = (int)((n + chunk - 1) / chunk);
   const int ld = (int)((chunk + 63) / 64 * 64);
   const size_t phi_part = pb * (size_t)chunk * Nb;
@@ -827,6 +826,9 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
   double* hand = nullptr;
   double* lossp = nullptr;
   int64_t lblk = 0;
+  // host inputs (lm_step_host): nothing above reads the samples
+  if (c->hin_on && (rc = cuda_check(c, cudaStreamWaitEvent(S(c), c->hin_xy_ready, 0), "wait")))
+    return rc;
   if (fuse_r) {
     // the near-field correction of every sample in one launch before the
     // chunks (one launch balances the uneven near pairs across the SMs);
@@ -865,6 +867,8 @@ static int jtj_tc(bem_ctx* c, int64_t n, const float* xy, double* Hout, int sch,
     launch_frows<float, true>(c, xy + 2 * s0, m, F, ld, hw, ld);
     if (fuse_r) {
       double* hs = hand + 3 * s0;
+      if (c->hin_on && (rc = cuda_check(c, cudaStreamWaitEvent(S(c), c->hin_t_ready[ci], 0), "wait")))
+        return rc;
       {
         ProfScope _ph(c, "k_hand_sum");
         k_hand_sum<<<(m + 255) / 256, 256, 0, S(c)>>>(hw, ld, C, m, hs);

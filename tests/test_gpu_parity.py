@@ -471,6 +471,46 @@ def test_lm_step_across_chunks(cfg1, mode):
     assert res["loss_after"] == pytest.approx(want["loss_after"], rel=1e-9 if exact else 1e-4)
 
 
+@pytest.mark.parametrize("mode,pinned", [("bf16", True), ("bf16", False), ("fp64", True)])
+def test_lm_step_host_inputs(cfg1, mode, pinned):
+    """lm_step_host (host samples and targets, copied in by the library chunk
+    by chunk while the pass runs) takes the step lm_step takes on device
+    copies of the same inputs, over 8 chunks, twice in a row (the second step
+    with other targets in the same device buffers); the first step also
+    against the oracle's."""
+    sc, xy, target, mean, o = cfg1
+    x, t = xy[:N_CHUNKED], target[:N_CHUNKED]
+    t2 = np.ascontiguousarray(t[::-1])
+    m_dev, dt = _gn_ctx(sc, mean, mode, 4096)
+    m_host, _ = _gn_ctx(sc, mean, mode, 4096)
+    npdt = np.float64 if dt == torch.float64 else np.float32
+
+    def host(a):
+        a = np.ascontiguousarray(a, npdt)
+        return torch.from_numpy(a).pin_memory() if pinned else a
+
+    for k, tk in enumerate((t, t2)):
+        rd = m_dev.lm_step(_t(x, dt), _t(tk, dt), [1e-2])
+        rh = m_host.lm_step_host(host(x), host(tk), [1e-2])
+        for key in ("loss_before", "loss_after", "grad_norm", "lambda_next"):
+            assert rh[key] == pytest.approx(rd[key], rel=1e-12), key
+        assert rh["accepted"] == rd["accepted"] and rh["best_trial"] == rd["best_trial"]
+        assert np.abs(m_host.get_params() - m_dev.get_params()).max() <= \
+            1e-12 * np.abs(m_dev.get_params()).max()
+        if k == 0:
+            want = o.lm_step(sc.theta_init, x, t, 1e-2)
+            exact = mode == "fp64"
+            assert rh["loss_before"] == pytest.approx(want["loss_before"], rel=1e-12 if exact else 1e-5)
+            assert rh["accepted"] == want["accepted"]
+
+
+def test_lm_step_host_rejects_device_tensors(cfg1):
+    sc, xy, target, mean, o = cfg1
+    m, dt = _gn_ctx(sc, mean, "bf16", 4096)
+    with pytest.raises(AssertionError):
+        m.lm_step_host(_t(xy[:256], dt), _t(target[:256], dt), [1e-2])
+
+
 def test_mixed_all_pairs_near(cfg1):
     """near_factor = 1000 sends every handle pair through the double near-field
     kernels: colours and gradient then match the oracle to float rounding of
