@@ -340,6 +340,16 @@ int bem_fastmath_eval(bem_ctx *ctx, int which, int64_t n, const float *a, const 
 int bem_dlog_eval(bem_ctx *ctx, int64_t n, const double *x, double *out_lib, double *out_ref,
                   void *stream);
 
+/* The double arctangent of the FP64 near field (octant reduction, a table of
+ * 64 breakpoints and the addition theorem), next to CUDA's atan2, for
+ * validation (no counterpart in the paper): out_lib[i] = the library's
+ * atan2(y[i], x[i]), out_ref[i] = CUDA's.  y: device double [n], y >= 0;
+ * x: device double [n]; both finite, of magnitude within [2^-1000, 2^1000]
+ * or zero; out_lib, out_ref: device double [n].  Errors: BEM_EINVAL for bad
+ * arguments. */
+int bem_datan2_eval(bem_ctx *ctx, int64_t n, const double *y, const double *x, double *out_lib,
+                    double *out_ref, void *stream);
+
 /* The pairing of the bf16 Gram kernel, exposed for validation (host only, no
  * context, no GPU).  The upper 128 x 128 blocks (i <= j) of a channel's Gram
  * matrix in its J-row order, tiles block rows, are computed in units of two

@@ -94,6 +94,7 @@ def _load():
         "bem_gemm_bf16": (ci, [vp, ci, ci, ci, vp, ci, vp, ci, vp, ci, vp]),
         "bem_fastmath_eval": (ci, [vp, ci, i64, vp, vp, vp, vp, vp]),
         "bem_dlog_eval": (ci, [vp, i64, vp, vp, vp, vp]),
+        "bem_datan2_eval": (ci, [vp, i64, vp, vp, vp, vp, vp]),
         "bem_vjp_noalloc": (ci, [vp, i64, vp, vp, vp, vp]),
         "bem_profile_read": (ci, [vp, ci, ctypes.c_char_p, dp, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ci)]),
@@ -127,7 +128,7 @@ EXPORTED = [
     "bem_batch_lm", "bem_batch_tile_shape", "bem_render", "bem_handle_colors", "lm_step_split",
     "bem_set_boundary", "bem_setup_segments", "bem_set_regularizers", "bem_prune",
     "bem_init_segments", "bem_gram_unit", "bem_alloc_count", "bem_set_wait_limit",
-    "bem_gn_products", "bem_pipe_peak", "lm_step_host",
+    "bem_gn_products", "bem_pipe_peak", "lm_step_host", "bem_datan2_eval",
 ]
 globals().update({name: getattr(_lib, name) for name in EXPORTED})
 
@@ -471,6 +472,19 @@ class BEM:
         ref = torch.empty_like(x)
         self._check(_lib.bem_dlog_eval(self.h, x.numel(), _ptr(x), _ptr(own), _ptr(ref),
                                        _stream(stream)))
+        return own, ref
+
+    def datan2(self, y, x, stream=None):
+        """(library, CUDA) double atan2(y, x) of double CUDA tensors, y >= 0
+        (bem_datan2_eval)."""
+        import torch
+        assert y.dtype == torch.float64 and y.is_cuda and y.is_contiguous()
+        assert x.dtype == torch.float64 and x.is_cuda and x.is_contiguous()
+        assert x.shape == y.shape
+        own = torch.empty_like(x)
+        ref = torch.empty_like(x)
+        self._check(_lib.bem_datan2_eval(self.h, x.numel(), _ptr(y), _ptr(x), _ptr(own), _ptr(ref),
+                                         _stream(stream)))
         return own, ref
 
     def profile(self, on: bool = True):

@@ -99,7 +99,7 @@ struct bem_ctx {
       tcJ, tcPart, tcMt, nearP, nearS, nearF, gwork, rend, regw;
   bem_reg reg{};                   // Sec. 4.4 regularisers (segment handles)
   bool pbins_valid = false;        // panel -> cell bins match the current panels
-  bool dlog_ready = false;         // the double logarithm table is on this device
+  bool dmath_ready = false;        // the tables of the double logarithm and arctangent are on this device
   // When set, the Gauss-Newton chunk buffers (jrow, tcJ, tcPart, gwork) are
   // taken from this context: a batch of scenes processed one after another
   // on one stream shares them.

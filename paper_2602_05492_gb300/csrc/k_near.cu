@@ -220,14 +220,19 @@ static int build_bins(bem_ctx* c, DevBuf& buf, bool panels, int64_t n, const flo
 // ---------------------------------------------------------------------------
 // double evaluation of the near pairs
 
-// (ic_j, lc_j) of dlog, per device
+// (ic_j, lc_j) of dlog and (c_j, atan(c_j)) of datan2_ypos, per device
 __device__ double2 g_dlog_tab[kDlogTab];
+__device__ double2 g_datan_tab[kDatanTab];
 
-__global__ void k_dlog_init() {
+__global__ void k_dmath_init() {
   const int j = threadIdx.x;
   if (j < kDlogTab) {
     const double ic = 1.0 / (1.0 + (j + 0.5) / kDlogTab);
     g_dlog_tab[j] = make_double2(ic, -log(ic));
+  }
+  if (j < kDatanTab) {
+    const double cj = (double)j / kDatanTab;
+    g_datan_tab[j] = make_double2(cj, atan(cj));
   }
 }
 
@@ -247,7 +252,7 @@ __device__ __forceinline__ LayerVals<double> layer_values_near(const Frame<doubl
   const double hc = hc2 * rc;
   const double tt = f.t1 * f.t2;
   const double q1 = fma(f.t1, f.t1, hc2), q2 = fma(f.t2, f.t2, hc2);
-  const double phic = atan2(hc * f.L, hc2 + tt);
+  const double phic = datan2_ypos(hc * f.L, hc2 + tt, g_datan_tab);
   const double lg1 = dlog(q1, g_dlog_tab), lg2 = dlog(q2, g_dlog_tab);
   v.S = -(f.L * (lg2 - 2.0) + f.t1 * (lg2 - lg1) + 2.0 * hc * phic) * kInv4Pi;
   if constexpr (SAME) {
@@ -255,7 +260,7 @@ __device__ __forceinline__ LayerVals<double> layer_values_near(const Frame<doubl
   } else {
     const double hd2 = hh + ed2;
     const double rd = rsqrt(hd2);
-    v.Dl = -(f.h * rd) * atan2(hd2 * rd * f.L, hd2 + tt) * kInv2Pi;
+    v.Dl = -(f.h * rd) * datan2_ypos(hd2 * rd * f.L, hd2 + tt, g_datan_tab) * kInv2Pi;
   }
   return v;
 }
@@ -274,7 +279,7 @@ __device__ __forceinline__ LayerGrad<double> layer_grad_near(const Frame<double>
   const double rc = rsqrt(hc2);
   const double hc = hc2 * rc;
   const double q1 = fma(f.t1, f.t1, hc2), q2 = fma(f.t2, f.t2, hc2);
-  const double phic = atan2(hc * f.L, hc2 + tt);
+  const double phic = datan2_ypos(hc * f.L, hc2 + tt, g_datan_tab);
   const double lg1 = dlog(q1, g_dlog_tab), lg2 = dlog(q2, g_dlog_tab);
   g.S = -(f.L * (lg2 - 2.0) + f.t1 * (lg2 - lg1) + 2.0 * hc * phic) * kInv4Pi;
   g.S_t1 = lg1 * kInv4Pi;
@@ -287,7 +292,7 @@ __device__ __forceinline__ LayerGrad<double> layer_grad_near(const Frame<double>
   } else {
     hd2 = hh + ed2;
     rd = rsqrt(hd2);
-    phid = atan2(hd2 * rd * f.L, hd2 + tt);
+    phid = datan2_ypos(hd2 * rd * f.L, hd2 + tt, g_datan_tab);
     r1 = fma(f.t1, f.t1, hd2);
     r2 = fma(f.t2, f.t2, hd2);
   }
@@ -427,12 +432,13 @@ __global__ void __launch_bounds__(32 * kNearWarps)
     for (int k = 0; k < 11; ++k) out[(size_t)p * 11 + k] = acc[k];
 }
 
-// the table of dlog on this context's device, built before its first use
-static void dlog_ready(bem_ctx* c) {
-  if (!c->dlog_ready) {
-    k_dlog_init<<<1, kDlogTab, 0, S(c)>>>();
+// the tables of dlog and datan2_ypos on this context's device, built before
+// their first use
+static void dmath_ready(bem_ctx* c) {
+  if (!c->dmath_ready) {
+    k_dmath_init<<<1, kDlogTab > kDatanTab ? kDlogTab : kDatanTab, 0, S(c)>>>();
     BEM_LAUNCHED(c);
-    c->dlog_ready = true;
+    c->dmath_ready = true;
   }
 }
 
@@ -451,7 +457,7 @@ static int near_forward_t(bem_ctx* c, int64_t n, const float* xy, double* out, b
     b.items = (int*)((char*)c->nearP.p + sizeof(int) * ((size_t)ncell + 1 + ncell + nb + 1));
   }
 
-  dlog_ready(c);
+  dmath_ready(c);
   const float near2 = (float)(c->opts.near_factor * c->opts.near_factor);
   const double ec2 = c->opts.eps_c * c->opts.eps_c, ed2 = c->opts.eps_d * c->opts.eps_d;
   ProfScope _ps(c, "k_near_forward");
@@ -481,7 +487,7 @@ int near_adjoint(bem_ctx* c, int64_t n, const float* xy, const float* w, double*
   const int P = c->sc.P;
   const float nf = (float)c->opts.near_factor, near2 = nf * nf;
   const double ec2 = c->opts.eps_c * c->opts.eps_c, ed2 = c->opts.eps_d * c->opts.eps_d;
-  dlog_ready(c);
+  dmath_ready(c);
   ProfScope _ps(c, "k_near_adjoint");
   if (c->opts.eps_c == c->opts.eps_d)
     k_near_adjoint<true><<<(P + kNearWarps - 1) / kNearWarps, 32 * kNearWarps, 0, S(c)>>>(
@@ -502,7 +508,33 @@ __global__ void k_dlog_eval(int64_t n, const double* __restrict__ x, double* __r
   }
 }
 
+__global__ void k_datan2_eval(int64_t n, const double* __restrict__ y, const double* __restrict__ x,
+                              double* __restrict__ own, double* __restrict__ ref) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    own[i] = datan2_ypos(y[i], x[i], g_datan_tab);
+    ref[i] = atan2(y[i], x[i]);
+  }
+}
+
 }  // namespace bem
+
+extern "C" int bem_datan2_eval(bem_ctx* c, int64_t n, const double* y, const double* x,
+                               double* out_lib, double* out_ref, void* stream) {
+  using namespace bem;
+  if (!c) return BEM_EINVAL;
+  if (n < 0 || (n > 0 && (!y || !x || !out_lib || !out_ref)))
+    return fail(c, BEM_EINVAL, "bem_datan2_eval: bad arguments");
+  int rc;
+  if ((rc = ctx_set_device(c))) return rc;
+  c->cur = (cudaStream_t)stream;
+  dmath_ready(c);
+  if (n > 0) {
+    k_datan2_eval<<<(unsigned)((n + 255) / 256), 256, 0, S(c)>>>(n, y, x, out_lib, out_ref);
+    BEM_LAUNCHED(c);
+  }
+  return cuda_check(c, cudaGetLastError(), "k_datan2_eval");
+}
 
 extern "C" int bem_dlog_eval(bem_ctx* c, int64_t n, const double* x, double* out_lib,
                              double* out_ref, void* stream) {
@@ -513,7 +545,7 @@ extern "C" int bem_dlog_eval(bem_ctx* c, int64_t n, const double* x, double* out
   int rc;
   if ((rc = ctx_set_device(c))) return rc;
   c->cur = (cudaStream_t)stream;
-  dlog_ready(c);
+  dmath_ready(c);
   if (n > 0) {
     k_dlog_eval<<<(unsigned)((n + 255) / 256), 256, 0, S(c)>>>(n, x, out_lib, out_ref);
     BEM_LAUNCHED(c);
