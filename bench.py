@@ -729,6 +729,27 @@ def run_ours(args, rank, world, dist):
     pairs_per_s = 2 * pairs / ((fwd_ms + adj_ms) / 1e3)
     del out, res
 
+    # ---- the same LM step with the compensated bf16 Gauss-Newton matrix
+    # (every operand split into two bf16 parts, three products), device time
+    comp = None
+    if cfg == 4 and args.jtj == "bf16" and not args.samples and not args.no_extras:
+        mc = bg.BEM(precision=bg.BEM_MIXED, device=local, jtj_mode=bg.BEM_JTJ_BF16X3, near_factor=nf)
+        mc.setup(sc.n_curves, sc.panels_per_curve, sc.closed, sc.theta_init, mean)
+        mc.factor()
+        lam_c = [1e-3]
+
+        def step_c():
+            r = mc.lm_step(xt, tt, lam_c)
+            lam_c[0] = r["lambda_next"]
+
+        step_c()
+        torch.cuda.synchronize()
+        ms_c = _timed(step_c, 3, flush, stream)
+        comp = {"jtj": "bf16x3", "ms_per_step": sum(ms_c) / len(ms_c),
+                "lm_iters_per_s": 1e3 * len(ms_c) / sum(ms_c), "steps": len(ms_c), "warmup": 1,
+                "note": "the benched workload with the Gauss-Newton matrix in compensated bf16"}
+        mc.close()
+
     # ---- FP64 GPU path: LM iterations on two leading sample sets (fitted
     # a + b S when they are smaller than the workload), colour and gradient
     # error of the mixed path against it
@@ -803,7 +824,7 @@ def run_ours(args, rank, world, dist):
             "wall_s_timed_region": t_wall,
             "pairs_per_s": {"value": pairs_per_s, "unit": "sample x panel evals/s (fwd+adjoint)",
                             "fwd_ms": fwd_ms, "adj_ms": adj_ms, "pairs_per_pass": pairs},
-            "fp64_gpu": fp64, "accuracy": accuracy, "config2": extras,
+            "fp64_gpu": fp64, "accuracy": accuracy, "compensated_bf16": comp, "config2": extras,
             "pipe_peaks": pipes,
             "kernels": kernels,
             "roofline": roof, "rooflines_other": roofs[1:], "cpu_baseline": cpu, "e2e": e2e,

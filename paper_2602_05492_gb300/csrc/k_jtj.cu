@@ -324,17 +324,29 @@ __global__ void __launch_bounds__(1024) k_sum_rows(const double* __restrict__ pa
 }
 
 // out[row] = sum over k of part[row][k] (fixed order; one warp per row)
-// out[row] (+)= sum of part[row stride + k], k < nparts, in double, one warp
-// per row in a fixed order
-template <typename P>
-__global__ void k_row_sums(const P* __restrict__ part, int rows, int64_t nparts,
+// out[row] (+)= sum of the float partials part[row stride + k], k < nparts,
+// one warp per row in a fixed order: with 16-byte aligned rows, each lane
+// adds four consecutive partials in float ((a + b) + (c + d)) and those sums
+// in double (a quarter of the double additions, which bound this kernel on
+// the FP64 pipe); otherwise every partial in double
+__global__ void k_row_sums(const float* __restrict__ part, int rows, int64_t nparts,
                            int64_t stride, bool add, double* __restrict__ out) {
   const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
-  const P* p = part + (size_t)row * stride;
+  const float* p = part + (size_t)row * stride;
   double s = 0;
-  for (int64_t k = lane; k < nparts; k += 32) s += (double)p[k];
+  int64_t k0 = 0;
+  if ((stride & 3) == 0 && ((uintptr_t)part & 15) == 0) {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    const int64_t n4 = nparts >> 2;
+    for (int64_t k = lane; k < n4; k += 32) {
+      const float4 v = p4[k];
+      s += (double)((v.x + v.y) + (v.z + v.w));
+    }
+    k0 = 4 * n4;
+  }
+  for (int64_t k = k0 + lane; k < nparts; k += 32) s += (double)p[k];
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) out[row] = add ? out[row] + s : s;
 }
