@@ -66,3 +66,39 @@ def test_compensated_schemes_count_three_products():
     assert x["frac"] == pytest.approx(3 * b["frac"], rel=1e-12)
     assert t["peak"] == pytest.approx(b["peak"] * 1.1 / 2.25, rel=1e-12)
     assert x["traffic"] is None and t["traffic"] is None
+
+
+def test_traffic_record_is_dropped_when_its_kernel_source_changes(tmp_path, monkeypatch):
+    """`traffic` comes from the committed ncu record only while the kernel's
+    sources hash to the recorded SHA-256 and the workload is the recorded one."""
+    import hashlib
+    import json
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    (tmp_path / "profiles").mkdir()
+    rec = {"k": {"bytes_per_launch": 123, "sources": ["k.cu"], "config": 4,
+                 "sha256": hashlib.sha256(src.read_bytes()).hexdigest()}}
+    (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_traffic("k", 4) == 123
+    assert bench.kernel_traffic("k", 2) is None          # another workload
+    assert bench.kernel_traffic("other", 4) is None      # no record
+    src.write_text("__global__ void k() { }\n")         # the kernel changed
+    assert bench.kernel_traffic("k", 4) is None
+
+
+def test_committed_traffic_records_match_their_sources():
+    """Every committed DRAM-traffic record is keyed to the sources as they
+    stand, so the bench reports it (a source change re-captures or re-keys)."""
+    import hashlib
+    import json
+    import os
+    with open(os.path.join(bench.ROOT, "profiles", "dram_traffic.json")) as f:
+        recs = json.load(f)
+    for name, rec in recs.items():
+        h = hashlib.sha256()
+        for s in rec["sources"]:
+            with open(os.path.join(bench.ROOT, s), "rb") as f:
+                h.update(f.read())
+        assert h.hexdigest() == rec["sha256"], name
+        assert bench.kernel_traffic(name, rec["config"]) == rec["bytes_per_launch"]
