@@ -813,18 +813,18 @@ int lm_step_host(bem_ctx* c, int64_t n, const void* xy, const void* target, int 
   char* dxy = (char*)c->hin_xy.p;
   char* dt = (char*)c->hin_t.p;
   if ((rc = cuda_check(c, cudaEventRecord(c->hin_start, S(c)), "record")) ||
-      (rc = cuda_check(c, cudaStreamWaitEvent(c->hin_stream, c->hin_start, 0), "wait")) ||
-      (rc = cuda_check(c, cudaMemcpyAsync(dxy, xy, es * 2 * (size_t)n, cudaMemcpyHostToDevice,
-                                          c->hin_stream), "copy xy")) ||
-      (rc = cuda_check(c, cudaEventRecord(c->hin_xy_ready, c->hin_stream), "record")))
+      (rc = cuda_check(c, cudaStreamWaitEvent(c->hin_stream, c->hin_start, 0), "wait")))
     return rc;
-  for (int k = 0; k < nchunks; ++k) {
+  // from here on every exit waits for the copies already issued
+  rc = cuda_check(c, cudaMemcpyAsync(dxy, xy, es * 2 * (size_t)n, cudaMemcpyHostToDevice,
+                                     c->hin_stream), "copy xy");
+  if (!rc) rc = cuda_check(c, cudaEventRecord(c->hin_xy_ready, c->hin_stream), "record");
+  for (int k = 0; !rc && k < nchunks; ++k) {
     const int64_t s0 = (int64_t)k * chunk, m = std::min<int64_t>(chunk, n - s0);
     if ((rc = cuda_check(c, cudaMemcpyAsync(dt + es * 3 * (size_t)s0, (const char*)target + es * 3 * (size_t)s0,
                                             es * 3 * (size_t)m, cudaMemcpyHostToDevice, c->hin_stream),
-                         "copy target")) ||
-        (rc = cuda_check(c, cudaEventRecord(c->hin_t_ready[k], c->hin_stream), "record")))
-      break;
+                         "copy target")) == BEM_OK)
+      rc = cuda_check(c, cudaEventRecord(c->hin_t_ready[k], c->hin_stream), "record");
   }
   // the one-pass Gauss-Newton pass consumes the targets chunk by chunk as
   // they arrive; every other path waits for all of them first
