@@ -1,0 +1,45 @@
+"""The float arctangent's polynomial (CPU only): the coefficients compiled into
+the pair kernels come from the project's own minimax fit, and with float
+Horner evaluation they keep atan within the 2e-7 the kernels' header states."""
+import os
+import re
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _kernel_coefficients():
+    src = open(os.path.join(ROOT, "paper_2602_05492_gb300", "csrc", "fastmath.cuh")).read()
+    body = src[src.index("fm_atan01"):]
+    body = body[:body.index("return")]
+    # p = c7; p = fmaf(p, s, c6); ... ; p = fmaf(p, s, c0)
+    vals = [float(v) for v in re.findall(r"([-+]?\d\.\d+e[-+]\d+)f", body)]
+    assert len(vals) == 8
+    return np.array(vals[::-1], np.float32)      # c0 .. c7
+
+
+def _horner32(c, a):
+    s = (a * a).astype(np.float32)
+    p = np.float32(c[-1])
+    for k in range(len(c) - 2, -1, -1):
+        p = (p * s + c[k]).astype(np.float32)
+    return (a.astype(np.float32) * p).astype(np.float64)
+
+
+def test_kernel_polynomial_error_bound():
+    c = _kernel_coefficients()
+    a = np.linspace(0.0, 1.0, 400001)
+    err = np.abs(_horner32(c, a) - np.arctan(a)).max()
+    assert err < 2e-7, err
+
+
+def test_kernel_coefficients_are_the_fit():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "fit_atan", os.path.join(ROOT, "paper_2602_05492_gb300", "fit_atan.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    c, err = mod.fit(7, iters=200)
+    assert err < 1.2e-7
+    np.testing.assert_allclose(c.astype(np.float32), _kernel_coefficients(), rtol=2e-4, atol=2e-7)
