@@ -43,3 +43,24 @@ def test_kernel_coefficients_are_the_fit():
     c, err = mod.fit(7, iters=200)
     assert err < 1.2e-7
     np.testing.assert_allclose(c.astype(np.float32), _kernel_coefficients(), rtol=2e-4, atol=2e-7)
+
+
+def _const(path, name):
+    src = open(os.path.join(ROOT, "paper_2602_05492_gb300", "csrc", path)).read()
+    m = re.search(name + r"\s*=\s*([-+]?[0-9.]+(?:e[-+]?\d+)?)(f?)", src)
+    assert m, name
+    v = float(m.group(1))
+    return np.float32(v) if m.group(2) else np.float64(v)
+
+
+def test_kernel_constants_round_to_their_values():
+    """Each written-out constant of the kernels is its value rounded to the
+    constant's type."""
+    d = {("common.cuh", "kPi"): np.pi, ("common.cuh", "kInv2Pi"): 1 / (2 * np.pi),
+         ("common.cuh", "kInv4Pi"): 1 / (4 * np.pi), ("dmath.cuh", "kLn2d"): np.log(2.0),
+         ("dmath.cuh", "kPiD"): np.pi, ("dmath.cuh", "kPi2D"): np.pi / 2,
+         ("fastmath.cuh", "kLn2f"): np.log(2.0), ("fastmath.cuh", "kLn2Halff"): np.log(2.0) / 2,
+         ("fastmath.cuh", "kFltMinNormal"): float(np.finfo(np.float32).tiny)}
+    for (f, name), want in d.items():
+        got = _const(f, name)
+        assert got == type(got)(want), (f, name, got, want)
