@@ -1,6 +1,7 @@
-"""The float arctangent's polynomial (CPU only): the coefficients compiled into
-the pair kernels come from the project's own minimax fit, and with float
-Horner evaluation they keep atan within the 2e-7 the kernels' header states."""
+"""Numbers written out in the kernel sources (CPU only): the float
+arctangent's polynomial (the project's own minimax fit, within the 2e-7 its
+header states under float Horner evaluation), the mathematical constants,
+and the 3-point Gauss-Legendre rule of the Galerkin integrals."""
 import os
 import re
 
@@ -64,3 +65,20 @@ def test_kernel_constants_round_to_their_values():
     for (f, name), want in d.items():
         got = _const(f, name)
         assert got == type(got)(want), (f, name, got, want)
+
+
+def test_gauss_rule_is_three_point_gauss_legendre():
+    """Nodes 1/2 -+ sqrt(15)/10 and weights 5/18, 8/18, 5/18 on [0, 1]: exact
+    for polynomials up to degree 5, not for degree 6."""
+    src = open(os.path.join(ROOT, "paper_2602_05492_gb300", "csrc", "common.cuh")).read()
+    body = src[src.index("gauss_node"):src.index("gauss_weight")]
+    lo, mid, hi = sorted(float(v) for v in re.findall(r"(0\.\d{6,}|0\.5)", body))
+    assert mid == 0.5
+    import decimal
+    decimal.getcontext().prec = 40
+    r = decimal.Decimal(15).sqrt() / 10                 # the nodes to 40 digits, rounded once
+    assert lo == float(decimal.Decimal("0.5") - r) and hi == float(decimal.Decimal("0.5") + r)
+    x, w = np.array([lo, mid, hi]), np.array([5, 8, 5]) / 18
+    for k in range(6):
+        assert abs(w @ x ** k - 1 / (k + 1)) < 1e-15
+    assert abs(w @ x ** 6 - 1 / 7) > 1e-6
